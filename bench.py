@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Benchmark of the batched fifth-order Taylor update on one or more GB300s.
+
+Workload (the 14-qubit configuration the headline metric is quoted on):
+8192 complex64 states of 14 qubits (7 spatial orbitals, 6 electrons,
+Bravyi-Kitaev, strongly correlated synthetic integrals), each prepared from
+the Hartree-Fock state by three Taylor updates and then updated in place,
+once per step, with its own pool generator (204 spin-conserving singles and
+doubles) and angle.  One step = one launch of the pair kernel over all 8192
+states (1 GiB read + 1 GiB written, larger than L2) plus the float64
+per-state norm reduction.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs its own 8192 states (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Taylor-5 state updates/s at 14 qubits"
+UNIT = "updates/s"
+N_SPATIAL, N_ELECTRONS, MAPPING = 7, 6, 1      # 14 qubits, BK
+NQ = 2 * N_SPATIAL
+D = 1 << NQ
+FALLBACK_HBM_GBS = 6800.0
+PROFILE = os.path.join(ROOT, "profiles", "taylor5_pair_c64_14q.md")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2606_29692_gb300", "csrc", f)
+                  for f in ("evolve_kernels.cu", "dev.cuh")]
+
+
+def workload_config(n_states):
+    return {
+        "workload": (f"batched Taylor-5: {n_states} complex64 states, 14 qubits "
+                     "(7 spatial orbitals, 6 electrons), Bravyi-Kitaev, strongly correlated "
+                     "synthetic integrals (seed 2), pool of 204 singles+doubles, per-state op "
+                     "and angle N(0,0.1) (seed 3), states prepared by 3 updates from HF"),
+        "n_states": n_states,
+        "n_qubits": NQ,
+        "pool_size": 204,
+        "mapping": "BK",
+        "state_precision": "complex64 (float32 products), float64 norm reduction",
+        "l2_policy": "inputs larger than L2 (1 GiB per sweep, in place)",
+    }
+
+
+# ------------------------------------------------------------------ helpers
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(n_states):
+    """DRAM bytes per launch from the committed ncu summary, if still valid."""
+    if not os.path.exists(PROFILE):
+        return None
+    txt = open(PROFILE).read()
+    m = re.search(r"traffic_bytes_per_state:\s*([0-9.eE+]+)", txt)
+    h = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", txt)
+    if not m or not h or h.group(1) != kernel_source_hash():
+        return None
+    return float(m.group(1)) * n_states
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu_id), "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# -------------------------------------------------------- CPU oracle timing
+
+def _oracle_worker(args):
+    """Oracle Taylor-5 updates on a slice of sample states for ~`seconds`."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    idx, seconds = args
+    import numpy as np
+    import synth
+    from oracle import adapt, evolve, pauli
+    exc, pps = pauli.pool_pauli(N_SPATIAL, N_ELECTRONS, MAPPING)
+    prep_k, prep_th, k, th = synth.t5_batch(8192, len(exc))
+    cache = {}
+
+    def A(j):
+        if j not in cache:
+            cache[j] = pauli.pauli_to_csr(pps[j])
+        return cache[j]
+
+    states = []
+    for b in idx:
+        psi = adapt.hf_state(NQ, N_ELECTRONS, MAPPING)
+        for j in range(prep_k.shape[1]):
+            psi = evolve.taylor5(A(int(prep_k[b, j])), psi, prep_th[b, j])
+        A(int(k[b]))
+        states.append(psi)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        for b, psi in zip(idx, states):
+            evolve.taylor5(A(int(k[b])), psi, th[b])
+            n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            return n, el
+
+
+def cpu_oracle_rate(seconds=12.0, states_per_core=4, cores=None):
+    cores = cores or os.cpu_count() or 1
+    jobs = [(list(range(c * states_per_core, (c + 1) * states_per_core)), seconds) for c in range(cores)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    n = sum(r[0] for r in res)
+    t = max(r[1] for r in res)
+    return n / t, cores, n, t
+
+
+# --------------------------------------------------------------- GPU arm
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_2606_29692_gb300 as tq
+    import synth
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    S = args.states
+    ctx = tq.Context(local_rank)
+    pool = tq.build_pool(ctx, N_SPATIAL, N_ELECTRONS, MAPPING)
+    prep_k, prep_th, k, th = synth.t5_batch(S, pool.M)
+    hf = tq.hf_index(NQ, N_ELECTRONS, MAPPING)
+    psi = torch.zeros((S, D), dtype=torch.complex64, device="cuda")
+    psi[:, hf] = 1.0
+    for j in range(prep_k.shape[1]):
+        tq.evolve_taylor5_batch(ctx, pool, psi, torch.as_tensor(prep_k[:, j].copy()).cuda(),
+                                torch.as_tensor(prep_th[:, j].copy()).cuda())
+    dk = torch.as_tensor(k).cuda()
+    dth = torch.as_tensor(th).cuda()
+    dn = torch.zeros(S, dtype=torch.float64, device="cuda")
+
+    def step():
+        tq.evolve_taylor5_batch(ctx, pool, psi, dk, dth, dn)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local_rank).uuid)
+    except Exception:
+        gpu_id = str(local_rank)
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = ctx.launches()
+    ctx.trace(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = ctx.launches() - launches0
+    rep = ctx.trace_report()
+    ctx.trace(False)
+    t = max_over_ranks(e0.elapsed_time(e1) / 1e3)
+    value = world * S * args.steps / t
+    pair_n, pair_ms = rep.get("taylor5_pair", (0, float("nan")))
+    pair_s = pair_ms / max(pair_n, 1) / 1e3
+    alg_bytes = S * 2 * D * 8                       # read + write each amplitude once
+    peak, peak_src = peaks()
+    achieved = alg_bytes / pair_s / 1e9
+    traffic = profiled_traffic(S)
+
+    # end to end: the same update through the host-buffer entry point
+    psi_h = torch.empty((S, D), dtype=torch.complex64).pin_memory()
+    psi_h.copy_(psi)
+    k_h = torch.as_tensor(k).pin_memory()
+    th_h = torch.as_tensor(th).pin_memory()
+    n_h = torch.zeros(S, dtype=torch.float64).pin_memory()
+    tq.evolve_taylor5_batch_host(ctx, pool, psi_h, k_h, th_h, n_h)     # warm
+    e2e_steps = max(1, min(args.steps, 5))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        tq.evolve_taylor5_batch_host(ctx, pool, psi_h, k_h, th_h, n_h)
+    t_e2e = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": world * S * e2e_steps / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": S * D * 8 + S * 4 + S * 8,
+           "d2h_bytes_per_step": S * D * 8 + S * 8,
+           "api": "tq_evolve_taylor5_batch_host (pinned host buffers, 3-stream chunked copies)"}
+    finite = bool(torch.isfinite(dn).all().item()) and float(dn.min().item()) > 0.5
+    out = None
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+            "data": "synthetic", "config": workload_config(S),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_taylor5_pair<float>",
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "kernel_ms_per_launch": pair_s * 1e3,
+                         "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
+                         else "fallback"},
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "kernels": {k_: {"launches": v[0], "ms": v[1]} for k_, v in rep.items()},
+            "clocks": clk,
+            "norms_finite": finite,
+        }
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--states", type=int, default=8192)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        return run_reference(args, world)
+
+    out = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            rate, cores, n, t = cpu_oracle_rate(args.cpu_seconds)
+            out["cpu_baseline"] = {
+                "value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": (f"{n} oracle updates (scipy CSR complex128, 5 SpMV + Eq. (8) sum) of "
+                           f"{4 * cores} states of the same workload, {cores} spawn workers, "
+                           f"{t:.1f} s")}
+        else:
+            out["cpu_baseline"] = None
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_reference(args, world):
+    """The oracle timed on the host cores on the same metric (reference arm)."""
+    cores = os.cpu_count() or 1
+    per_step = max(1.0, min(6.0, 150.0 / max(1, args.steps + args.warmup)))
+    rates = []
+    for i in range(args.warmup + args.steps):
+        rate, c, n, t = cpu_oracle_rate(per_step, states_per_core=2, cores=cores)
+        if i >= args.warmup:
+            rates.append((n, t))
+    n = sum(r[0] for r in rates)
+    t = sum(r[1] for r in rates)
+    value = n / t
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic", "config": workload_config(args.states),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": (f"each step: {per_step:.1f} s of oracle updates on "
+                                    f"{2 * cores} states of the workload across {cores} spawn workers")},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,287 @@
+/*
+ * tq.h -- C ABI of the GB300 (sm_103a) library for the ADAPT-VQE fifth-order
+ * Taylor hot path of "Alleviating the Sparse Matrix Scaling Bottleneck in
+ * Adaptive VQE via High-Order Taylor State Evolution".
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every function returns an int status: TQ_OK (0) or a negative TQ_E*
+ *    code.  No function throws or aborts.  tq_last_error() returns a
+ *    thread-local, human-readable reason for the last failure on the
+ *    calling thread (the pointer stays valid until the next failing call on
+ *    that thread).
+ *  - Qubit j is bit j of a basis index (little-endian).  A state of N qubits
+ *    is D = 2^N complex amplitudes stored contiguously, real part first:
+ *    TQ_C128 = two float64 per amplitude (16 B), TQ_C64 = two float32 (8 B).
+ *  - Spin orbitals are interleaved: spin orbital P = 2p + sigma (sigma 0 is
+ *    alpha, 1 is beta); N = 2 * n_spatial qubits.
+ *  - Host arrays passed in are read during the call and copied; the caller
+ *    keeps ownership.  Handles (tq_ctx, tq_ham, tq_pool, tq_state, ...) are
+ *    owned by the library and released by the matching *_free / *_destroy
+ *    function, each of which accepts NULL.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it.  Functions that write a HOST scalar or
+ *    array synchronise that stream before returning; functions that write
+ *    DEVICE memory only are asynchronous.
+ *  - A tq_ctx owns device scratch that its calls share: calls on one context
+ *    must be issued from one host thread at a time, on one stream (or on
+ *    streams the caller orders).  Use one context per concurrent stream.
+ *  - Operator values are real: the Jordan-Wigner and Bravyi-Kitaev images of
+ *    real integrals and of real excitation generators have real matrix
+ *    elements in the computational basis.  States are complex.
+ */
+#ifndef TQ_H
+#define TQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Mappings (Sec. II-A): Jordan-Wigner (Eq. (4), parity string on the lower
+ * qubits) and Bravyi-Kitaev (Fenwick-tree encoding: qubit k stores the
+ * parity of modes k+1-lowbit(k+1) .. k). */
+enum { TQ_JW = 0, TQ_BK = 1 };
+
+/* Precisions: TQ_C128 runs every product and sum in float64.  TQ_C64 keeps
+ * states and sparse products in complex64 (float32) while Hamiltonian
+ * diagonals, energy and gradient dot reductions, norms and the convergence
+ * test stay in float64. */
+enum { TQ_C128 = 0, TQ_C64 = 1 };
+
+enum {
+    TQ_OK = 0,
+    TQ_EINVAL = -1,    /* invalid argument (range, size, null, mismatch)   */
+    TQ_ENOMEM = -2,    /* device or host allocation failed                 */
+    TQ_ECUDA = -3,     /* a CUDA runtime call failed                       */
+    TQ_ETIMEOUT = -4,  /* a bounded wait ran out                           */
+    TQ_EBUSY = -5,     /* admission refused (memory budget or slots)       */
+    TQ_ENUMERIC = -6   /* non-finite or inconsistent numerical result      */
+};
+
+/* Limits.  States up to 2^26 amplitudes; CSR indices are int32, so a
+ * Hamiltonian build fails with TQ_ENOMEM when nnz would reach 2^31. */
+#define TQ_MAX_SPATIAL 15
+#define TQ_MAX_STATE_QUBITS 26
+
+typedef struct tq_ctx tq_ctx;
+typedef struct tq_ham tq_ham;
+typedef struct tq_pool tq_pool;
+typedef struct tq_state tq_state;
+
+const char* tq_last_error(void);
+int tq_version(void); /* 100 * major + minor */
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device` (makes it current on the calling
+ * thread).  Queries the SM count and per-kernel occupancy used to size
+ * persistent grids. */
+int tq_ctx_create(int device, tq_ctx** out);
+int tq_ctx_destroy(tq_ctx* ctx);
+/* Number of kernel launches this context has issued since creation. */
+int tq_ctx_launch_count(const tq_ctx* ctx, long long* launches);
+
+/* Kernel tracing.  With tracing on, every kernel this context launches is
+ * bracketed by two CUDA events recorded on the stream it is launched on.
+ * tq_ctx_trace_report synchronises those events and writes one line per
+ * kernel name, "name launches total_ms\n", into buf (NUL-terminated,
+ * truncated to buf_size), then clears the record.  Tracing adds two event
+ * records per launch and nothing else. */
+int tq_ctx_trace(tq_ctx* ctx, int enable);
+int tq_ctx_trace_report(tq_ctx* ctx, char* buf, size_t buf_size);
+
+/* ------------------------------------------------- host-side construction */
+
+/* Qubit Hamiltonian as a Pauli sum (Eq. (3)) from the fermionic Hamiltonian
+ * of Eq. (2).  The paper writes the two-body part with physicist integrals
+ * h_ijkl; this entry point takes chemist integrals, (ik|jl) = <ij|kl>, so
+ *   H = sum_PQ h_PQ a+_P a_Q + 1/2 sum_PQRS (PQ|RS) a+_P a+_R a_S a_Q + e_const
+ * with h_PQ = h1[p*n+q] for equal spins and
+ * (PQ|RS) = g2[((p*n+q)*n+r)*n+s] for sigma_P = sigma_Q, sigma_R = sigma_S.
+ * Output terms are c * X^x Z^z (Z acts first), i.e. <r|term|c_> =
+ * c * (-1)^popcount(c_ & z) when r = c_ xor x, with real c; sorted by
+ * (x, z); like terms merged; |c| <= 1e-12 max|c| dropped.  Two-call
+ * pattern: with x == NULL only *n_terms is written; otherwise `capacity`
+ * must be >= the count.  Host only; needs no GPU. */
+int tq_pauli_hamiltonian(int n_spatial, const double* h1, const double* g2,
+                         double e_const, int mapping, long long* n_terms,
+                         uint64_t* x, uint64_t* z, double* c,
+                         long long capacity);
+
+/* Excitation pool (Sec. III-E; sizes of Table II): spin-conserving
+ * occupied -> virtual singles (i, a) then doubles (i, j, a, b), i < j,
+ * a < b, S_z conserved, each list lexicographic; occupied spin orbitals are
+ * P < n_electrons.  idx4 receives 4 ints per op, -1 padded (singles use
+ * the first two).  Two-call pattern on idx4 == NULL.  Host only. */
+int tq_pool_excitations(int n_spatial, int n_electrons, int* n_ops,
+                        int* idx4, int capacity);
+
+/* Generator A_k = tau_k - tau_k^+ of each pool op as a Pauli sum in the
+ * same c * X^x Z^z form: x[k], nterm[k] (2 or 8), z[8k + t], c[8k + t]
+ * (unused slots zero).  Host only. */
+int tq_pauli_pool(int n_spatial, int n_electrons, int mapping, int capacity,
+                  uint64_t* x, int* nterm, uint64_t* z, double* c);
+
+/* Qubit-basis index of the Hartree-Fock determinant (spin orbitals
+ * P < n_electrons occupied) under `mapping`.  Host only. */
+int tq_hf_index(int n_qubits, int n_electrons, int mapping, long long* index);
+
+/* ------------------------------------------------------------ Hamiltonian */
+
+/* Build the Hamiltonian on the device (Sec. III-D step 1; CSR compilation
+ * of Sec. III-E step 3).  The Pauli sum is formed on the host, uploaded once,
+ * and compiled on the GPU into
+ *   - diag:   float64[D], H[r][r] (the X-mask-0 group);
+ *   - CSR of the off-diagonal part: rowptr int32[D+1], col int32[nnz]
+ *     ascending within each row, val float64 (TQ_C128) or float32 (TQ_C64)
+ *     [nnz].  An entry H[r][r^x] is the sum, in (x, z) order, of
+ *     c_p (-1)^popcount((r^x) & z_p) over the terms of X-mask x; entries with
+ *     |v| <= 1e-12 max|c| are dropped;
+ *   - the X-mask-grouped matrix-free layout (group masks, term offsets,
+ *     z masks, coefficients) used by tq_energy_matrix_free.
+ * Synchronises the device.  Errors: TQ_EINVAL (sizes, mapping, precision,
+ * null), TQ_ENOMEM, TQ_ECUDA, TQ_ENUMERIC (a term with an odd number of Y
+ * survived, which real symmetric integrals cannot produce). */
+int tq_build_hamiltonian(tq_ctx* ctx, int n_spatial, const double* h1,
+                         const double* g2, double e_const, int mapping,
+                         int prec, tq_ham** out);
+/* Any output pointer may be NULL.  n_ambiguous counts CSR entries whose
+ * magnitude fell in (1e-12, 1e-9] * max|c|, where the zero-drop decision
+ * would be fragile (expected 0). */
+int tq_ham_info(const tq_ham* ham, int* n_qubits, int* prec, long long* nnz,
+                long long* n_pauli, long long* n_xgroups, long long* n_ambiguous,
+                size_t* device_bytes);
+/* Borrowed device pointers (valid until tq_ham_free). */
+int tq_ham_csr(const tq_ham* ham, const int** rowptr, const int** col,
+               const void** val, const double** diag);
+int tq_ham_free(tq_ham* ham);
+
+/* ------------------------------------------------------------------- pool */
+
+/* Build the pool (Sec. III-D step 2) in the vectorised device layout of
+ * Sec. III-E: structure-of-arrays x[M], nterm[M], z[8M], c[8M].  Every
+ * generator has one X-mask, at most one non-zero per row and column, and
+ * entries in {0, +1, -1}. */
+int tq_build_pool(tq_ctx* ctx, int n_spatial, int n_electrons, int mapping,
+                  tq_pool** out);
+/* M, qubit count, and (if idx4 != NULL) 4 ints per op as in
+ * tq_pool_excitations. */
+int tq_pool_info(const tq_pool* pool, int* n_ops, int* n_qubits, int* idx4);
+/* On-the-fly sparse compilation (Sec. III-E step 3): CSR of generator k,
+ * built on the device the first time it is asked for and cached.  Values
+ * are float64 (TQ_C128) or float32 (TQ_C64).  Borrowed device pointers. */
+int tq_pool_csr(tq_ctx* ctx, tq_pool* pool, int k, int prec,
+                const int** rowptr, const int** col, const void** val,
+                long long* nnz);
+int tq_pool_free(tq_pool* pool);
+
+/* ------------------------------------------------------------------ state */
+
+int tq_state_create(tq_ctx* ctx, int n_qubits, int prec, tq_state** out);
+/* Borrow caller memory (e.g. a torch tensor's data_ptr()): D amplitudes,
+ * 16-byte aligned.  The caller keeps it alive and orders streams. */
+int tq_state_wrap(tq_ctx* ctx, int n_qubits, int prec, void* dev_ptr,
+                  tq_state** out);
+int tq_state_data(const tq_state* st, void** dev_ptr, int* n_qubits, int* prec);
+/* |HF>: the basis state of tq_hf_index, amplitude 1 (async). */
+int tq_state_set_hf(tq_state* st, int n_electrons, int mapping, void* stream);
+int tq_state_free(tq_state* st);
+
+/* ------------------------------------------------------------- hot path */
+
+/* Fifth-order Taylor update of Sec. III-C, Eqs. (6)-(8):
+ *   v_0 = psi, v_k = A v_{k-1} (k = 1..5),
+ *   psi <- psi + theta v_1 + theta^2/2 v_2 + ... + theta^5/120 v_5,
+ * with A = pool generator k, applied matrix-free from the pool layout.  The
+ * five products and the running sum stay in registers; psi is read once
+ * and written once.  If renormalize != 0 the result is divided by its
+ * float64 norm (a second, L2-resident pass).  Async.  Errors: TQ_EINVAL
+ * (k out of range, qubit mismatch, non-finite theta). */
+int tq_evolve_taylor5(tq_ctx* ctx, const tq_pool* pool, int k, double theta,
+                      tq_state* psi, int renormalize, void* stream);
+
+/* The same update for an arbitrary CSR operator A (rowptr int32[D+1], col
+ * int32[nnz], val float64 for TQ_C128 / float32 for TQ_C64 states, device
+ * pointers).  The caller guarantees rowptr is non-decreasing with
+ * rowptr[0] = 0 and rowptr[D] = nnz; column indices outside [0, D) are
+ * skipped (treated as zero entries).  The state is staged in shared memory -- across a thread-block
+ * cluster of up to 16 CTAs, read through distributed shared memory -- and
+ * never returns to global memory between the five products; the float64
+ * norm is reduced across the cluster and, if renormalize != 0, applied
+ * before the single store.  Larger states use one L2-resident pass per
+ * product.  Async. */
+int tq_evolve_taylor5_csr(tq_ctx* ctx, int n_qubits, const int* rowptr,
+                          const int* col, const void* val, double theta,
+                          tq_state* psi, int renormalize, void* stream);
+
+/* Energy of Eq. (1): E = Re<psi|H|psi> / <psi|psi>, float64.  One fused
+ * pass: CSR SpMV (w = H psi, kept in context scratch for
+ * tq_pool_gradients) and float64 warp-shuffle dot products.  Writes the
+ * host scalar *E (synchronises the stream). */
+int tq_energy(tq_ctx* ctx, const tq_ham* ham, const tq_state* psi, double* E,
+              void* stream);
+/* Same energy, computed from the X-mask-grouped Pauli layout without the
+ * CSR (cross-check of the CSR build; arithmetic-bound). */
+int tq_energy_matrix_free(tq_ctx* ctx, const tq_ham* ham, const tq_state* psi,
+                          double* E, void* stream);
+
+/* Pool gradients of Eq. (5): g_k = <psi|[H, A_k]|psi> / <psi|psi>
+ *                                = 2 Re<H psi|A_k psi> / <psi|psi>
+ * for all k in one persistent launch after one H pass; float64 sums.
+ * `g` has M entries; g_on_device != 0 means `g` is a device pointer (async),
+ * otherwise a host pointer (synchronises). */
+int tq_pool_gradients(tq_ctx* ctx, const tq_ham* ham, const tq_pool* pool,
+                      const tq_state* psi, double* g, int g_on_device,
+                      void* stream);
+
+/* One ADAPT iteration (Sec. III-D steps 3-4) entirely on the device:
+ * energy, all gradients, k* = argmax |g_k| (tie rule: the lowest k with
+ * |g_k| >= max|g| - tau, tau = 1e-9 max(1, max|g|) in TQ_C128 and 1e-5 in
+ * TQ_C64), converged = max|g| < eps; if not converged, the Taylor-5 update
+ * with A_{k*} and angle `theta`, or, when theta is NaN, the angle that
+ * minimises the energy along exp(theta A_{k*}) psi on (-pi, pi] (4096
+ * samples, ties within 1e-10 to the smallest |theta|, Newton polish), then
+ * renormalisation.  `energy` is the energy before the update.  Writes *out
+ * (synchronises). */
+typedef struct {
+    double energy;
+    double max_grad;
+    double theta;
+    int selected;
+    int converged;
+} tq_adapt_result;
+int tq_adapt_step(tq_ctx* ctx, const tq_ham* ham, const tq_pool* pool,
+                  tq_state* psi, double eps, double theta,
+                  tq_adapt_result* out, void* stream);
+
+/* ------------------------------------------------------------ batched */
+
+/* Batched Taylor-5: n_states states of the pool's qubit count, stored
+ * back to back from psi (device, D amplitudes each, in place); state b is
+ * updated with generator k[b] and angle theta[b] (device arrays).  If norm2
+ * is not NULL it receives float64 ||psi_b'||^2 per state (renormalisation
+ * is left to the consumer: every energy and gradient here is a Rayleigh
+ * quotient).  A state whose k[b] is outside [0, M) is left unchanged and
+ * its norm2 is NaN.  One streaming launch plus a per-state reduction.
+ * Async. */
+int tq_evolve_taylor5_batch(tq_ctx* ctx, const tq_pool* pool, int n_states,
+                            int prec, void* psi, const int* k,
+                            const double* theta, double* norm2, void* stream);
+
+/* The same batch with HOST buffers (psi, k, theta, norm2 in host memory;
+ * pinned memory gives full copy speed): the batch is cut into chunks whose
+ * host-to-device copy, update and device-to-host copy overlap on three
+ * streams.  Synchronises.  Device staging comes from the context. */
+int tq_evolve_taylor5_batch_host(tq_ctx* ctx, const tq_pool* pool,
+                                 int n_states, int prec, void* psi_host,
+                                 const int* k_host, const double* theta_host,
+                                 double* norm2_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TQ_H */

@@ -1,0 +1,297 @@
+"""GB300 (sm_103a) library for the ADAPT-VQE fifth-order Taylor hot path.
+
+Thin Python binding over the C ABI of ``include/tq.h``: every function here
+only marshals arguments (numpy arrays for host data, torch tensors for device
+memory, torch streams) and calls the native library, where all of the
+method's steps run.  Names follow the C entry points without the ``tq_``
+prefix.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from ._native import (TQ_BK, TQ_C64, TQ_C128, TQ_JW, AdaptResult, TQError, call, lib)
+
+__all__ = [
+    "TQ_JW", "TQ_BK", "TQ_C128", "TQ_C64", "TQError", "Context", "Hamiltonian", "Pool", "State",
+    "pauli_hamiltonian", "pool_excitations", "pauli_pool", "hf_index", "build_hamiltonian",
+    "build_pool", "evolve_taylor5", "evolve_taylor5_csr", "energy", "energy_matrix_free",
+    "pool_gradients", "adapt_step", "evolve_taylor5_batch", "evolve_taylor5_batch_host",
+    "state_set_hf", "pool_csr", "ham_csr", "lib",
+]
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return C.c_void_p(a.ctypes.data)
+    return C.c_void_p(a.data_ptr())      # torch tensor
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _torch_dtype(prec):
+    import torch
+    return torch.complex128 if prec == TQ_C128 else torch.complex64
+
+
+# ------------------------------------------------------------- host algebra
+
+def pauli_hamiltonian(h1, g2, e_const, mapping):
+    """Pauli sum of the qubit Hamiltonian: arrays (x, z, c) of ``c X^x Z^z``."""
+    h1 = np.ascontiguousarray(h1, dtype=np.float64)
+    g2 = np.ascontiguousarray(g2, dtype=np.float64)
+    n = h1.shape[0]
+    cnt = C.c_longlong()
+    call("tq_pauli_hamiltonian", n, _ptr(h1), _ptr(g2), float(e_const), mapping, C.byref(cnt),
+         None, None, None, 0)
+    x = np.zeros(cnt.value, dtype=np.uint64)
+    z = np.zeros(cnt.value, dtype=np.uint64)
+    c = np.zeros(cnt.value, dtype=np.float64)
+    call("tq_pauli_hamiltonian", n, _ptr(h1), _ptr(g2), float(e_const), mapping, C.byref(cnt),
+         _ptr(x), _ptr(z), _ptr(c), cnt.value)
+    return x, z, c
+
+
+def pool_excitations(n_spatial, n_electrons):
+    """Pool excitations as an (M, 4) int array, -1 padded."""
+    m = C.c_int()
+    call("tq_pool_excitations", n_spatial, n_electrons, C.byref(m), None, 0)
+    idx = np.zeros((m.value, 4), dtype=np.int32)
+    call("tq_pool_excitations", n_spatial, n_electrons, C.byref(m), _ptr(idx), m.value)
+    return idx
+
+
+def pauli_pool(n_spatial, n_electrons, mapping):
+    """Generators as Pauli sums: x[M], nterm[M], z[M, 8], c[M, 8]."""
+    M = pool_excitations(n_spatial, n_electrons).shape[0]
+    x = np.zeros(M, dtype=np.uint64)
+    nt = np.zeros(M, dtype=np.int32)
+    z = np.zeros((M, 8), dtype=np.uint64)
+    c = np.zeros((M, 8), dtype=np.float64)
+    call("tq_pauli_pool", n_spatial, n_electrons, mapping, M, _ptr(x), _ptr(nt), _ptr(z), _ptr(c))
+    return x, nt, z, c
+
+
+def hf_index(n_qubits, n_electrons, mapping):
+    out = C.c_longlong()
+    call("tq_hf_index", n_qubits, n_electrons, mapping, C.byref(out))
+    return out.value
+
+
+# ----------------------------------------------------------------- handles
+
+class Context:
+    """Device context (owns scratch); one per concurrent stream."""
+
+    def __init__(self, device=0):
+        h = C.c_void_p()
+        call("tq_ctx_create", int(device), C.byref(h))
+        self.handle = h
+        self.device = device
+
+    def launches(self):
+        n = C.c_longlong()
+        call("tq_ctx_launch_count", self.handle, C.byref(n))
+        return n.value
+
+    def trace(self, enable=True):
+        """Bracket every kernel launch with CUDA events on its stream."""
+        call("tq_ctx_trace", self.handle, 1 if enable else 0)
+
+    def trace_report(self):
+        """{kernel name: (launches, total ms)} since the last report (synchronises)."""
+        buf = C.create_string_buffer(1 << 16)
+        call("tq_ctx_trace_report", self.handle, buf, len(buf))
+        out = {}
+        for line in buf.value.decode().splitlines():
+            name, n, ms = line.split()
+            out[name] = (int(n), float(ms))
+        return out
+
+    def close(self):
+        if self.handle:
+            lib().tq_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Hamiltonian:
+    def __init__(self, ctx, handle):
+        self.ctx = ctx
+        self.handle = handle
+        nq, prec, nnz, npl, ng, namb, nb = (C.c_int(), C.c_int(), C.c_longlong(), C.c_longlong(),
+                                            C.c_longlong(), C.c_longlong(), C.c_size_t())
+        call("tq_ham_info", handle, C.byref(nq), C.byref(prec), C.byref(nnz), C.byref(npl),
+             C.byref(ng), C.byref(namb), C.byref(nb))
+        self.n_qubits, self.prec, self.nnz = nq.value, prec.value, nnz.value
+        self.n_pauli, self.n_xgroups, self.n_ambiguous = npl.value, ng.value, namb.value
+        self.device_bytes = nb.value
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().tq_ham_free(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+class Pool:
+    def __init__(self, ctx, handle):
+        self.ctx = ctx
+        self.handle = handle
+        m, nq = C.c_int(), C.c_int()
+        call("tq_pool_info", handle, C.byref(m), C.byref(nq), None)
+        self.M, self.n_qubits = m.value, nq.value
+        self.idx4 = np.zeros((self.M, 4), dtype=np.int32)
+        call("tq_pool_info", handle, None, None, _ptr(self.idx4))
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().tq_pool_free(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+class State:
+    """A state backed by a torch tensor (device memory comes from torch)."""
+
+    def __init__(self, ctx, n_qubits, prec=TQ_C128, tensor=None):
+        import torch
+        self.ctx = ctx
+        self.n_qubits = n_qubits
+        self.prec = prec
+        if tensor is None:
+            tensor = torch.zeros(1 << n_qubits, dtype=_torch_dtype(prec), device=f"cuda:{ctx.device}")
+        assert tensor.is_contiguous() and tensor.numel() == (1 << n_qubits)
+        assert tensor.dtype == _torch_dtype(prec)
+        self.tensor = tensor
+        h = C.c_void_p()
+        call("tq_state_wrap", ctx.handle, n_qubits, prec, _ptr(tensor), C.byref(h))
+        self.handle = h
+
+    def numpy(self):
+        import torch
+        torch.cuda.synchronize()
+        return self.tensor.cpu().numpy().astype(np.complex128)
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().tq_state_free(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ builders
+
+def build_hamiltonian(ctx, h1, g2, e_const=0.0, mapping=TQ_JW, prec=TQ_C128):
+    h1 = np.ascontiguousarray(h1, dtype=np.float64)
+    g2 = np.ascontiguousarray(g2, dtype=np.float64)
+    h = C.c_void_p()
+    call("tq_build_hamiltonian", ctx.handle, h1.shape[0], _ptr(h1), _ptr(g2), float(e_const), mapping,
+         prec, C.byref(h))
+    return Hamiltonian(ctx, h)
+
+
+def build_pool(ctx, n_spatial, n_electrons, mapping=TQ_JW):
+    h = C.c_void_p()
+    call("tq_build_pool", ctx.handle, n_spatial, n_electrons, mapping, C.byref(h))
+    return Pool(ctx, h)
+
+
+def ham_csr(ham):
+    """(rowptr, col, val, diag) device pointers of the Hamiltonian (borrowed)."""
+    rp, cl, vl, dg = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
+    call("tq_ham_csr", ham.handle, C.byref(rp), C.byref(cl), C.byref(vl), C.byref(dg))
+    return rp.value, cl.value, vl.value, dg.value
+
+
+def pool_csr(ctx, pool, k, prec=TQ_C128):
+    """(rowptr, col, val, nnz) of generator k (device pointers, built on demand)."""
+    rp, cl, vl, nnz = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_longlong()
+    call("tq_pool_csr", ctx.handle, pool.handle, k, prec, C.byref(rp), C.byref(cl), C.byref(vl),
+         C.byref(nnz))
+    return rp.value, cl.value, vl.value, nnz.value
+
+
+def state_set_hf(state, n_electrons, mapping, stream=None):
+    call("tq_state_set_hf", state.handle, n_electrons, mapping, _stream(stream))
+
+
+# ------------------------------------------------------------------ hot path
+
+def evolve_taylor5(ctx, pool, k, theta, state, renormalize=False, stream=None):
+    call("tq_evolve_taylor5", ctx.handle, pool.handle, int(k), float(theta), state.handle,
+         1 if renormalize else 0, _stream(stream))
+
+
+def evolve_taylor5_csr(ctx, n_qubits, rowptr, col, val, theta, state, renormalize=False, stream=None):
+    call("tq_evolve_taylor5_csr", ctx.handle, n_qubits, C.c_void_p(rowptr), C.c_void_p(col),
+         C.c_void_p(val), float(theta), state.handle, 1 if renormalize else 0, _stream(stream))
+
+
+def energy(ctx, ham, state, stream=None):
+    e = C.c_double()
+    call("tq_energy", ctx.handle, ham.handle, state.handle, C.byref(e), _stream(stream))
+    return e.value
+
+
+def energy_matrix_free(ctx, ham, state, stream=None):
+    e = C.c_double()
+    call("tq_energy_matrix_free", ctx.handle, ham.handle, state.handle, C.byref(e), _stream(stream))
+    return e.value
+
+
+def pool_gradients(ctx, ham, pool, state, out=None, stream=None):
+    """Gradients of every pool op; ``out`` may be a float64 CUDA tensor (async)."""
+    if out is not None:
+        call("tq_pool_gradients", ctx.handle, ham.handle, pool.handle, state.handle, _ptr(out), 1,
+             _stream(stream))
+        return out
+    g = np.zeros(pool.M, dtype=np.float64)
+    call("tq_pool_gradients", ctx.handle, ham.handle, pool.handle, state.handle, _ptr(g), 0,
+         _stream(stream))
+    return g
+
+
+def adapt_step(ctx, ham, pool, state, eps, theta=float("nan"), stream=None):
+    r = AdaptResult()
+    call("tq_adapt_step", ctx.handle, ham.handle, pool.handle, state.handle, float(eps),
+         float(theta), C.byref(r), _stream(stream))
+    return {"energy": r.energy, "max_grad": r.max_grad, "theta": r.theta,
+            "selected": r.selected, "converged": bool(r.converged)}
+
+
+def evolve_taylor5_batch(ctx, pool, psi, k, theta, norm2=None, prec=TQ_C64, stream=None):
+    """In-place batched update of ``psi`` (CUDA tensor, n_states x 2^N)."""
+    n_states = psi.shape[0]
+    call("tq_evolve_taylor5_batch", ctx.handle, pool.handle, n_states, prec, _ptr(psi), _ptr(k),
+         _ptr(theta), _ptr(norm2), _stream(stream))
+
+
+def evolve_taylor5_batch_host(ctx, pool, psi, k, theta, norm2=None, prec=TQ_C64):
+    """Batched update of HOST arrays (numpy or pinned torch CPU tensors)."""
+    n_states = psi.shape[0]
+    call("tq_evolve_taylor5_batch_host", ctx.handle, pool.handle, n_states, prec, _ptr(psi), _ptr(k),
+         _ptr(theta), _ptr(norm2))

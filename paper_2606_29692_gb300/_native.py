@@ -1,0 +1,102 @@
+"""ctypes declarations of the C ABI in ``include/tq.h`` (marshalling only).
+
+The library is loaded from ``lib/libtq.so`` inside this package.  There is no
+fallback: if the library has not been built, ``lib()`` raises, so a missing
+extension can never silently turn into some other code path.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libtq.so")
+
+TQ_JW, TQ_BK = 0, 1
+TQ_C128, TQ_C64 = 0, 1
+STATUS = {0: "TQ_OK", -1: "TQ_EINVAL", -2: "TQ_ENOMEM", -3: "TQ_ECUDA", -4: "TQ_ETIMEOUT",
+          -5: "TQ_EBUSY", -6: "TQ_ENUMERIC"}
+
+
+class TQError(RuntimeError):
+    def __init__(self, code, func, msg):
+        super().__init__(f"{func}: {STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class AdaptResult(C.Structure):
+    _fields_ = [("energy", C.c_double), ("max_grad", C.c_double), ("theta", C.c_double),
+                ("selected", C.c_int), ("converged", C.c_int)]
+
+
+vp = C.c_void_p
+i32 = C.c_int
+i64 = C.c_longlong
+f64 = C.c_double
+P = C.POINTER
+
+# name -> argument types (every function returns int unless listed in _RET)
+SIGNATURES = {
+    "tq_last_error": [],
+    "tq_version": [],
+    "tq_ctx_create": [i32, P(vp)],
+    "tq_ctx_destroy": [vp],
+    "tq_ctx_launch_count": [vp, P(i64)],
+    "tq_ctx_trace": [vp, i32],
+    "tq_ctx_trace_report": [vp, vp, C.c_size_t],
+    "tq_pauli_hamiltonian": [i32, vp, vp, f64, i32, P(i64), vp, vp, vp, i64],
+    "tq_pool_excitations": [i32, i32, P(i32), vp, i32],
+    "tq_pauli_pool": [i32, i32, i32, i32, vp, vp, vp, vp],
+    "tq_hf_index": [i32, i32, i32, P(i64)],
+    "tq_build_hamiltonian": [vp, i32, vp, vp, f64, i32, i32, P(vp)],
+    "tq_ham_info": [vp, P(i32), P(i32), P(i64), P(i64), P(i64), P(i64), P(C.c_size_t)],
+    "tq_ham_csr": [vp, P(vp), P(vp), P(vp), P(vp)],
+    "tq_ham_free": [vp],
+    "tq_build_pool": [vp, i32, i32, i32, P(vp)],
+    "tq_pool_info": [vp, P(i32), P(i32), vp],
+    "tq_pool_csr": [vp, vp, i32, i32, P(vp), P(vp), P(vp), P(i64)],
+    "tq_pool_free": [vp],
+    "tq_state_create": [vp, i32, i32, P(vp)],
+    "tq_state_wrap": [vp, i32, i32, vp, P(vp)],
+    "tq_state_data": [vp, P(vp), P(i32), P(i32)],
+    "tq_state_set_hf": [vp, i32, i32, vp],
+    "tq_state_free": [vp],
+    "tq_evolve_taylor5": [vp, vp, i32, f64, vp, i32, vp],
+    "tq_evolve_taylor5_csr": [vp, i32, vp, vp, vp, f64, vp, i32, vp],
+    "tq_energy": [vp, vp, vp, P(f64), vp],
+    "tq_energy_matrix_free": [vp, vp, vp, P(f64), vp],
+    "tq_pool_gradients": [vp, vp, vp, vp, vp, i32, vp],
+    "tq_adapt_step": [vp, vp, vp, vp, f64, f64, P(AdaptResult), vp],
+    "tq_evolve_taylor5_batch": [vp, vp, i32, i32, vp, vp, vp, vp, vp],
+    "tq_evolve_taylor5_batch_host": [vp, vp, i32, i32, vp, vp, vp, vp],
+}
+_RET = {"tq_last_error": C.c_char_p}
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"native library {LIB_PATH} is missing: build it with "
+                "`python -m paper_2606_29692_gb300.build` (needs nvcc); there is no fallback")
+        l = C.CDLL(LIB_PATH)
+        for name, args in SIGNATURES.items():
+            f = getattr(l, name)
+            f.argtypes = args
+            f.restype = _RET.get(name, C.c_int)
+        _lib = l
+    return _lib
+
+
+def call(name, *args):
+    """Call ``name``; raise TQError with the library's reason on failure."""
+    rc = getattr(lib(), name)(*args)
+    if rc != 0:
+        msg = lib().tq_last_error()
+        raise TQError(rc, name, msg.decode() if msg else "")
+    return rc

@@ -1,0 +1,905 @@
+// C ABI of the library (declared in include/tq.h).  Argument checking,
+// handle lifetime, device memory, and the launch sequences of each call.
+#include "dev.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+using namespace tq;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+void set_error(const std::string& m) { g_last_error = m; }
+
+#define TQ_CUDA(call)                                                                    \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            throw Error(e_ == cudaErrorMemoryAllocation ? TQ_ENOMEM : TQ_ECUDA,          \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));             \
+    } while (0)
+
+#define TQ_REQUIRE(cond, msg)                              \
+    do {                                                   \
+        if (!(cond)) throw Error(TQ_EINVAL, (msg));        \
+    } while (0)
+
+#define API_BEGIN try {
+#define API_END                                            \
+    }                                                      \
+    catch (const Error& e) {                               \
+        set_error(e.what());                               \
+        return e.code;                                     \
+    }                                                      \
+    catch (const std::bad_alloc&) {                        \
+        set_error("host allocation failed");               \
+        return TQ_ENOMEM;                                  \
+    }                                                      \
+    catch (const std::exception& e) {                      \
+        set_error(e.what());                               \
+        return TQ_ECUDA;                                   \
+    }                                                      \
+    return TQ_OK;
+
+// Brackets the launches made in its scope with events when tracing is on.
+struct Traced {
+    tq_ctx* c;
+    cudaStream_t s;
+    tq_trace_rec rec{};
+    Traced(tq_ctx* ctx, const char* name, cudaStream_t st) : c(ctx), s(st) {
+        if (!c->tracing) return;
+        rec.name = name;
+        rec.start = take();
+        rec.stop = take();
+        cudaEventRecord(rec.start, s);
+    }
+    ~Traced() {
+        if (!c->tracing || !rec.start) return;
+        cudaEventRecord(rec.stop, s);
+        c->trace.push_back(rec);
+    }
+    cudaEvent_t take() {
+        cudaEvent_t e = nullptr;
+        if (!c->event_pool.empty()) {
+            e = c->event_pool.back();
+            c->event_pool.pop_back();
+        } else {
+            cudaEventCreate(&e);
+        }
+        return e;
+    }
+};
+
+void check_launch(tq_ctx* c, int n) {
+    c->launches += n;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) throw Error(TQ_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+}
+
+// Launch through `f` (which returns its launch count), traced under `name`.
+template <typename F>
+void launch(tq_ctx* c, const char* name, cudaStream_t s, F&& f) {
+    Traced t(c, name, s);
+    check_launch(c, f());
+}
+
+void* dev_alloc(size_t bytes) {
+    void* p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error(TQ_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    return p;
+}
+
+template <typename T>
+T* upload(std::vector<void*>& allocs, const std::vector<T>& v) {
+    T* p = static_cast<T*>(dev_alloc(v.size() * sizeof(T)));
+    allocs.push_back(p);
+    if (!v.empty()) TQ_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return p;
+}
+
+void* scratch(tq_ctx* c, int slot, size_t bytes) {
+    if (c->scratch_bytes[slot] < bytes) {
+        if (c->scratch[slot]) TQ_CUDA(cudaFree(c->scratch[slot]));
+        c->scratch[slot] = nullptr;
+        c->scratch_bytes[slot] = 0;
+        c->scratch[slot] = dev_alloc(bytes);
+        c->scratch_bytes[slot] = bytes;
+    }
+    return c->scratch[slot];
+}
+
+unsigned* tickets(tq_ctx* c, size_t n) {
+    if (c->tickets_n < n) {
+        if (c->tickets) TQ_CUDA(cudaFree(c->tickets));
+        c->tickets = nullptr;
+        c->tickets_n = 0;
+        c->tickets = static_cast<unsigned*>(dev_alloc(n * sizeof(unsigned)));
+        TQ_CUDA(cudaMemset(c->tickets, 0, n * sizeof(unsigned)));
+        c->tickets_n = n;
+    }
+    return c->tickets;
+}
+
+enum { S_PART = 0, S_W0, S_U1, S_U2, S_W1, S_W2, S_G, S_STAGE };
+
+size_t elem_bytes(int prec) { return prec == TQ_C128 ? 16 : 8; }
+
+void check_prec(int prec) {
+    TQ_REQUIRE(prec == TQ_C128 || prec == TQ_C64, "prec must be TQ_C128 or TQ_C64");
+}
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+void set_device(const tq_ctx* c) { TQ_CUDA(cudaSetDevice(c->device)); }
+
+// Build the CSR of a grouped Pauli sum into (rowptr, col, val); returns nnz.
+long long build_csr(tq_ctx* c, HamView& h, double maxc, int prec, std::vector<void*>& allocs,
+                    long long* n_amb, int* max_row) {
+    const long long D = h.D;
+    int* counts = static_cast<int*>(scratch(c, S_G, (size_t)D * sizeof(int)));
+    int* rowptr = static_cast<int*>(dev_alloc((size_t)(D + 1) * sizeof(int)));
+    allocs.push_back(rowptr);
+    struct Out { long long total; int max_row; int pad; unsigned long long amb; };
+    Out* dout = static_cast<Out*>(scratch(c, S_PART, sizeof(Out)));
+    TQ_CUDA(cudaMemset(dout, 0, sizeof(Out)));
+    const double tol = 1e-12 * maxc, amb_hi = 1e-9 * maxc;
+    if (h.G > 0) {
+        launch(c, "csr_count", 0, [&] { return launch_csr_count(h, tol, amb_hi, counts, &dout->amb, c->sm_count, 0); });
+    } else {
+        TQ_CUDA(cudaMemset(counts, 0, (size_t)D * sizeof(int)));
+    }
+    launch(c, "scan", 0, [&] { return launch_scan(counts, D, rowptr, &dout->total, &dout->max_row, 0); });
+    Out hout;
+    TQ_CUDA(cudaMemcpy(&hout, dout, sizeof(Out), cudaMemcpyDeviceToHost));
+    if (hout.total >= 2147483647ll)
+        throw Error(TQ_ENOMEM, "CSR has 2^31 or more non-zeros; int32 indices cannot address it");
+    const long long nnz = hout.total;
+    int* col = static_cast<int*>(dev_alloc((size_t)nnz * sizeof(int)));
+    allocs.push_back(col);
+    void* val = dev_alloc((size_t)nnz * (prec == TQ_C128 ? sizeof(double) : sizeof(float)));
+    allocs.push_back(val);
+    h.rowptr = rowptr;
+    h.col = col;
+    h.val = val;
+    h.nnz = nnz;
+    if (nnz > 0) launch(c, "csr_fill", 0, [&] { return launch_csr_fill(h, tol, hout.max_row, col, val, prec, c->sm_count, 0); });
+    TQ_CUDA(cudaDeviceSynchronize());
+    if (n_amb) *n_amb = (long long)hout.amb;
+    if (max_row) *max_row = hout.max_row;
+    return nnz;
+}
+
+void free_all(std::vector<void*>& allocs) {
+    for (void* p : allocs)
+        if (p) cudaFree(p);
+    allocs.clear();
+}
+
+}  // namespace
+
+// ===================================================================== misc
+
+extern "C" const char* tq_last_error(void) { return g_last_error.c_str(); }
+extern "C" int tq_version(void) { return 100; }
+
+extern "C" int tq_ctx_create(int device, tq_ctx** out) {
+    API_BEGIN
+    TQ_REQUIRE(out != nullptr, "out is null");
+    *out = nullptr;
+    int n = 0;
+    TQ_CUDA(cudaGetDeviceCount(&n));
+    TQ_REQUIRE(device >= 0 && device < n, "device index out of range");
+    TQ_CUDA(cudaSetDevice(device));
+    auto* c = new tq_ctx();
+    c->device = device;
+    cudaError_t e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
+        delete c;
+        throw Error(TQ_ECUDA, cudaGetErrorString(e));
+    }
+    try {
+        c->step = static_cast<DevStep*>(dev_alloc(sizeof(DevStep)));
+        TQ_CUDA(cudaMemset(c->step, 0, sizeof(DevStep)));
+        tickets(c, 4096);
+    } catch (...) {
+        tq_ctx_destroy(c);
+        throw;
+    }
+    *out = c;
+    API_END
+}
+
+extern "C" int tq_ctx_destroy(tq_ctx* c) {
+    if (!c) return TQ_OK;
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (int i = 0; i < 8; ++i)
+        if (c->scratch[i]) cudaFree(c->scratch[i]);
+    if (c->step) cudaFree(c->step);
+    if (c->tickets) cudaFree(c->tickets);
+    for (auto& s : c->aux)
+        if (s) cudaStreamDestroy(s);
+    for (auto& r : c->trace) {
+        cudaEventDestroy(r.start);
+        cudaEventDestroy(r.stop);
+    }
+    for (auto& e : c->event_pool) cudaEventDestroy(e);
+    delete c;
+    return TQ_OK;
+}
+
+extern "C" int tq_ctx_launch_count(const tq_ctx* c, long long* launches) {
+    API_BEGIN
+    TQ_REQUIRE(c && launches, "null argument");
+    *launches = c->launches;
+    API_END
+}
+
+extern "C" int tq_ctx_trace(tq_ctx* c, int enable) {
+    API_BEGIN
+    TQ_REQUIRE(c != nullptr, "ctx is null");
+    c->tracing = enable ? 1 : 0;
+    API_END
+}
+
+extern "C" int tq_ctx_trace_report(tq_ctx* c, char* buf, size_t buf_size) {
+    API_BEGIN
+    TQ_REQUIRE(c && buf && buf_size > 0, "null argument");
+    set_device(c);
+    std::vector<std::string> names;
+    std::vector<long long> counts;
+    std::vector<double> ms;
+    for (auto& r : c->trace) {
+        TQ_CUDA(cudaEventSynchronize(r.stop));
+        float t = 0.f;
+        TQ_CUDA(cudaEventElapsedTime(&t, r.start, r.stop));
+        size_t i = 0;
+        while (i < names.size() && names[i] != r.name) ++i;
+        if (i == names.size()) {
+            names.push_back(r.name);
+            counts.push_back(0);
+            ms.push_back(0.0);
+        }
+        counts[i] += 1;
+        ms[i] += t;
+        c->event_pool.push_back(r.start);
+        c->event_pool.push_back(r.stop);
+    }
+    c->trace.clear();
+    std::string out;
+    for (size_t i = 0; i < names.size(); ++i) {
+        char line[256];
+        snprintf(line, sizeof line, "%s %lld %.6f\n", names[i].c_str(), counts[i], ms[i]);
+        out += line;
+    }
+    const size_t n = std::min(out.size(), buf_size - 1);
+    std::memcpy(buf, out.data(), n);
+    buf[n] = '\0';
+    API_END
+}
+
+// ============================================================ host algebra
+
+extern "C" int tq_pauli_hamiltonian(int n_spatial, const double* h1, const double* g2, double e_const,
+                                    int mapping, long long* n_terms, uint64_t* x, uint64_t* z, double* c,
+                                    long long capacity) {
+    API_BEGIN
+    TQ_REQUIRE(n_terms != nullptr, "n_terms is null");
+    auto t = pauli_hamiltonian(n_spatial, h1, g2, e_const, mapping);
+    *n_terms = (long long)t.size();
+    if (x) {
+        TQ_REQUIRE(z && c, "z and c must be given with x");
+        TQ_REQUIRE(capacity >= (long long)t.size(), "capacity too small");
+        for (size_t i = 0; i < t.size(); ++i) {
+            x[i] = t[i].x;
+            z[i] = t[i].z;
+            c[i] = t[i].c;
+        }
+    }
+    API_END
+}
+
+extern "C" int tq_pool_excitations(int n_spatial, int n_electrons, int* n_ops, int* idx4, int capacity) {
+    API_BEGIN
+    TQ_REQUIRE(n_ops != nullptr, "n_ops is null");
+    auto ex = excitations(n_spatial, n_electrons);
+    *n_ops = (int)ex.size();
+    if (idx4) {
+        TQ_REQUIRE(capacity >= (int)ex.size(), "capacity too small");
+        for (size_t k = 0; k < ex.size(); ++k)
+            for (int j = 0; j < 4; ++j) idx4[4 * k + j] = ex[k].idx[j];
+    }
+    API_END
+}
+
+extern "C" int tq_pauli_pool(int n_spatial, int n_electrons, int mapping, int capacity, uint64_t* x,
+                             int* nterm, uint64_t* z, double* c) {
+    API_BEGIN
+    TQ_REQUIRE(x && nterm && z && c, "null output array");
+    auto ex = excitations(n_spatial, n_electrons);
+    TQ_REQUIRE(capacity >= (int)ex.size(), "capacity too small");
+    const int N = 2 * n_spatial;
+    for (size_t k = 0; k < ex.size(); ++k) {
+        auto t = pauli_generator(ex[k], N, mapping);
+        if (t.size() > 8) throw Error(TQ_ENUMERIC, "generator with more than 8 terms");
+        x[k] = t.empty() ? 0 : t[0].x;
+        nterm[k] = (int)t.size();
+        for (int j = 0; j < 8; ++j) {
+            z[8 * k + j] = j < (int)t.size() ? t[j].z : 0;
+            c[8 * k + j] = j < (int)t.size() ? t[j].c : 0.0;
+        }
+    }
+    API_END
+}
+
+extern "C" int tq_hf_index(int n_qubits, int n_electrons, int mapping, long long* index) {
+    API_BEGIN
+    TQ_REQUIRE(index != nullptr, "index is null");
+    TQ_REQUIRE(n_qubits >= 1 && n_qubits <= 2 * TQ_MAX_SPATIAL, "n_qubits out of range");
+    *index = (long long)hf_index(n_qubits, n_electrons, mapping);
+    API_END
+}
+
+// ============================================================ Hamiltonian
+
+extern "C" int tq_build_hamiltonian(tq_ctx* c, int n_spatial, const double* h1, const double* g2,
+                                    double e_const, int mapping, int prec, tq_ham** out) {
+    API_BEGIN
+    TQ_REQUIRE(c && out, "null argument");
+    *out = nullptr;
+    check_prec(prec);
+    TQ_REQUIRE(std::isfinite(e_const), "e_const is not finite");
+    TQ_REQUIRE(n_spatial >= 1 && 2 * n_spatial <= TQ_MAX_STATE_QUBITS,
+               "n_spatial must give at most 26 qubits for a device Hamiltonian");
+    set_device(c);
+    auto terms = pauli_hamiltonian(n_spatial, h1, g2, e_const, mapping);
+    auto* h = new tq_ham();
+    try {
+        h->ctx = c;
+        h->n_spatial = n_spatial;
+        h->nq = 2 * n_spatial;
+        h->prec = prec;
+        h->mapping = mapping;
+        h->D = 1ll << h->nq;
+        h->n_pauli = (long long)terms.size();
+        std::vector<uint32_t> gx, tz, dz;
+        std::vector<int> goff;
+        std::vector<double> tc, dc;
+        double maxc = 0.0;
+        for (size_t i = 0; i < terms.size(); ++i) {
+            maxc = std::max(maxc, std::fabs(terms[i].c));
+            if (terms[i].x == 0) {
+                dz.push_back((uint32_t)terms[i].z);
+                dc.push_back(terms[i].c);
+                continue;
+            }
+            if (gx.empty() || gx.back() != (uint32_t)terms[i].x) {
+                gx.push_back((uint32_t)terms[i].x);
+                goff.push_back((int)tz.size());
+            }
+            tz.push_back((uint32_t)terms[i].z);
+            tc.push_back(terms[i].c);
+        }
+        goff.push_back((int)tz.size());
+        HamView& v = h->view;
+        v.nq = h->nq;
+        v.prec = prec;
+        v.D = h->D;
+        v.G = (int)gx.size();
+        v.gx = upload(h->allocs, gx);
+        v.goff = upload(h->allocs, goff);
+        v.tz = upload(h->allocs, tz);
+        v.tc = upload(h->allocs, tc);
+        v.Kd = (int)dz.size();
+        v.dz = upload(h->allocs, dz);
+        v.dc = upload(h->allocs, dc);
+        double* diag = static_cast<double*>(dev_alloc((size_t)h->D * sizeof(double)));
+        h->allocs.push_back(diag);
+        v.diag = diag;
+        launch(c, "diag", 0, [&] { return launch_diag(v, diag, c->sm_count, 0); });
+        h->nnz = build_csr(c, v, maxc, prec, h->allocs, &h->n_amb, &h->max_row);
+        h->bytes = (size_t)h->D * 8 + (size_t)(h->D + 1) * 4 + (size_t)h->nnz * (4 + (prec == TQ_C128 ? 8 : 4)) +
+                   (gx.size() + goff.size() + tz.size() + dz.size()) * 4 + (tc.size() + dc.size()) * 8;
+    } catch (...) {
+        tq_ham_free(h);
+        throw;
+    }
+    *out = h;
+    API_END
+}
+
+extern "C" int tq_ham_info(const tq_ham* h, int* n_qubits, int* prec, long long* nnz, long long* n_pauli,
+                           long long* n_xgroups, long long* n_ambiguous, size_t* device_bytes) {
+    API_BEGIN
+    TQ_REQUIRE(h != nullptr, "ham is null");
+    if (n_qubits) *n_qubits = h->nq;
+    if (prec) *prec = h->prec;
+    if (nnz) *nnz = h->nnz;
+    if (n_pauli) *n_pauli = h->n_pauli;
+    if (n_xgroups) *n_xgroups = h->view.G + (h->view.Kd > 0 ? 1 : 0);
+    if (n_ambiguous) *n_ambiguous = h->n_amb;
+    if (device_bytes) *device_bytes = h->bytes;
+    API_END
+}
+
+extern "C" int tq_ham_csr(const tq_ham* h, const int** rowptr, const int** col, const void** val,
+                          const double** diag) {
+    API_BEGIN
+    TQ_REQUIRE(h != nullptr, "ham is null");
+    if (rowptr) *rowptr = h->view.rowptr;
+    if (col) *col = h->view.col;
+    if (val) *val = h->view.val;
+    if (diag) *diag = h->view.diag;
+    API_END
+}
+
+extern "C" int tq_ham_free(tq_ham* h) {
+    if (!h) return TQ_OK;
+    if (h->ctx) cudaSetDevice(h->ctx->device);
+    free_all(h->allocs);
+    delete h;
+    return TQ_OK;
+}
+
+// =================================================================== pool
+
+extern "C" int tq_build_pool(tq_ctx* c, int n_spatial, int n_electrons, int mapping, tq_pool** out) {
+    API_BEGIN
+    TQ_REQUIRE(c && out, "null argument");
+    *out = nullptr;
+    TQ_REQUIRE(n_spatial >= 1 && 2 * n_spatial <= TQ_MAX_STATE_QUBITS, "n_spatial out of range");
+    check_mapping(mapping);
+    set_device(c);
+    auto ex = excitations(n_spatial, n_electrons);
+    TQ_REQUIRE(!ex.empty(), "the pool is empty for this electron count");
+    auto* p = new tq_pool();
+    try {
+        p->ctx = c;
+        p->n_spatial = n_spatial;
+        p->n_electrons = n_electrons;
+        p->nq = 2 * n_spatial;
+        p->mapping = mapping;
+        p->M = (int)ex.size();
+        const int M = p->M;
+        std::vector<uint32_t> x(M), z(8 * M, 0), fz0(M, 0), fd(3 * M, 0);
+        std::vector<int> nterm(M), fok(M, 0), fm(M, 0), ft(M, 0);
+        std::vector<float> cf(8 * M, 0.f), fc0f(M, 0.f);
+        std::vector<double> cd(8 * M, 0.0), fc0d(M, 0.0);
+        p->idx4.resize(4 * M);
+        p->terms.assign(8 * M, PauliTerm{0, 0, 0.0});
+        for (int k = 0; k < M; ++k) {
+            for (int j = 0; j < 4; ++j) p->idx4[4 * k + j] = ex[k].idx[j];
+            auto t = pauli_generator(ex[k], p->nq, mapping);
+            if (t.empty() || t.size() > 8) throw Error(TQ_ENUMERIC, "generator term count not in 1..8");
+            x[k] = (uint32_t)t[0].x;
+            nterm[k] = (int)t.size();
+            for (size_t j = 0; j < t.size(); ++j) {
+                if (t[j].x != t[0].x) throw Error(TQ_ENUMERIC, "generator with more than one X-mask");
+                z[8 * k + j] = (uint32_t)t[j].z;
+                cd[8 * k + j] = t[j].c;
+                cf[8 * k + j] = (float)t[j].c;
+                p->terms[8 * k + j] = t[j];
+            }
+            SignForm f = factor_generator(t);
+            if (f.ok) {
+                fok[k] = 1;
+                fm[k] = f.m;
+                fz0[k] = (uint32_t)f.z0;
+                for (int i = 0; i < 3; ++i) fd[3 * k + i] = (uint32_t)f.d[i];
+                ft[k] = f.t;
+                fc0d[k] = f.c0;
+                fc0f[k] = (float)f.c0;
+            }
+        }
+        p->nterm = nterm;
+        PoolView& v = p->view;
+        v.M = M;
+        v.nq = p->nq;
+        v.x = upload(p->allocs, x);
+        v.nterm = upload(p->allocs, nterm);
+        v.z = upload(p->allocs, z);
+        v.cf = upload(p->allocs, cf);
+        v.cd = upload(p->allocs, cd);
+        v.fok = upload(p->allocs, fok);
+        v.fm = upload(p->allocs, fm);
+        v.fz0 = upload(p->allocs, fz0);
+        v.fd = upload(p->allocs, fd);
+        v.ft = upload(p->allocs, ft);
+        v.fc0f = upload(p->allocs, fc0f);
+        v.fc0d = upload(p->allocs, fc0d);
+        for (int q = 0; q < 2; ++q) {
+            p->csr_rowptr[q].assign(M, nullptr);
+            p->csr_col[q].assign(M, nullptr);
+            p->csr_val[q].assign(M, nullptr);
+            p->csr_nnz[q].assign(M, -1);
+        }
+    } catch (...) {
+        tq_pool_free(p);
+        throw;
+    }
+    *out = p;
+    API_END
+}
+
+extern "C" int tq_pool_info(const tq_pool* p, int* n_ops, int* n_qubits, int* idx4) {
+    API_BEGIN
+    TQ_REQUIRE(p != nullptr, "pool is null");
+    if (n_ops) *n_ops = p->M;
+    if (n_qubits) *n_qubits = p->nq;
+    if (idx4) std::memcpy(idx4, p->idx4.data(), p->idx4.size() * sizeof(int));
+    API_END
+}
+
+extern "C" int tq_pool_csr(tq_ctx* c, tq_pool* p, int k, int prec, const int** rowptr, const int** col,
+                           const void** val, long long* nnz) {
+    API_BEGIN
+    TQ_REQUIRE(c && p, "null argument");
+    check_prec(prec);
+    TQ_REQUIRE(k >= 0 && k < p->M, "pool index out of range");
+    const int q = prec == TQ_C128 ? 0 : 1;
+    if (p->csr_nnz[q][k] < 0) {
+        set_device(c);
+        std::vector<void*> allocs;
+        try {
+            const int nt = p->nterm[k];
+            std::vector<uint32_t> gx = {(uint32_t)p->terms[8 * k].x}, tz(nt);
+            std::vector<int> goff = {0, nt};
+            std::vector<double> tc(nt);
+            double maxc = 0.0;
+            for (int j = 0; j < nt; ++j) {
+                tz[j] = (uint32_t)p->terms[8 * k + j].z;
+                tc[j] = p->terms[8 * k + j].c;
+                maxc = std::max(maxc, std::fabs(tc[j]));
+            }
+            HamView v{};
+            v.nq = p->nq;
+            v.prec = prec;
+            v.D = 1ll << p->nq;
+            v.G = 1;
+            v.gx = upload(allocs, gx);
+            v.goff = upload(allocs, goff);
+            v.tz = upload(allocs, tz);
+            v.tc = upload(allocs, tc);
+            std::vector<void*> keep;
+            const long long n = build_csr(c, v, maxc, prec, keep, nullptr, nullptr);
+            free_all(allocs);
+            for (void* ptr : keep) p->allocs.push_back(ptr);
+            p->csr_rowptr[q][k] = v.rowptr;
+            p->csr_col[q][k] = v.col;
+            p->csr_val[q][k] = v.val;
+            p->csr_nnz[q][k] = n;
+        } catch (...) {
+            free_all(allocs);
+            throw;
+        }
+    }
+    if (rowptr) *rowptr = p->csr_rowptr[q][k];
+    if (col) *col = p->csr_col[q][k];
+    if (val) *val = p->csr_val[q][k];
+    if (nnz) *nnz = p->csr_nnz[q][k];
+    API_END
+}
+
+extern "C" int tq_pool_free(tq_pool* p) {
+    if (!p) return TQ_OK;
+    if (p->ctx) cudaSetDevice(p->ctx->device);
+    free_all(p->allocs);
+    delete p;
+    return TQ_OK;
+}
+
+// ================================================================== state
+
+extern "C" int tq_state_create(tq_ctx* c, int n_qubits, int prec, tq_state** out) {
+    API_BEGIN
+    TQ_REQUIRE(c && out, "null argument");
+    *out = nullptr;
+    check_prec(prec);
+    TQ_REQUIRE(n_qubits >= 1 && n_qubits <= TQ_MAX_STATE_QUBITS, "n_qubits out of range [1, 26]");
+    set_device(c);
+    auto* s = new tq_state();
+    s->ctx = c;
+    s->nq = n_qubits;
+    s->prec = prec;
+    s->D = 1ll << n_qubits;
+    s->owned = 1;
+    try {
+        s->data = dev_alloc((size_t)s->D * elem_bytes(prec));
+        TQ_CUDA(cudaMemset(s->data, 0, (size_t)s->D * elem_bytes(prec)));
+    } catch (...) {
+        delete s;
+        throw;
+    }
+    *out = s;
+    API_END
+}
+
+extern "C" int tq_state_wrap(tq_ctx* c, int n_qubits, int prec, void* dev_ptr, tq_state** out) {
+    API_BEGIN
+    TQ_REQUIRE(c && out && dev_ptr, "null argument");
+    *out = nullptr;
+    check_prec(prec);
+    TQ_REQUIRE(n_qubits >= 1 && n_qubits <= TQ_MAX_STATE_QUBITS, "n_qubits out of range [1, 26]");
+    TQ_REQUIRE(((uintptr_t)dev_ptr & 15u) == 0, "state pointer must be 16-byte aligned");
+    auto* s = new tq_state();
+    s->ctx = c;
+    s->nq = n_qubits;
+    s->prec = prec;
+    s->D = 1ll << n_qubits;
+    s->owned = 0;
+    s->data = dev_ptr;
+    *out = s;
+    API_END
+}
+
+extern "C" int tq_state_data(const tq_state* s, void** dev_ptr, int* n_qubits, int* prec) {
+    API_BEGIN
+    TQ_REQUIRE(s != nullptr, "state is null");
+    if (dev_ptr) *dev_ptr = s->data;
+    if (n_qubits) *n_qubits = s->nq;
+    if (prec) *prec = s->prec;
+    API_END
+}
+
+extern "C" int tq_state_set_hf(tq_state* s, int n_electrons, int mapping, void* stream) {
+    API_BEGIN
+    TQ_REQUIRE(s != nullptr, "state is null");
+    set_device(s->ctx);
+    const long long idx = (long long)hf_index(s->nq, n_electrons, mapping);
+    check_launch(s->ctx, launch_set_basis(s->data, s->prec, s->D, idx, as_stream(stream)));
+    API_END
+}
+
+extern "C" int tq_state_free(tq_state* s) {
+    if (!s) return TQ_OK;
+    if (s->owned && s->data) {
+        cudaSetDevice(s->ctx->device);
+        cudaFree(s->data);
+    }
+    delete s;
+    return TQ_OK;
+}
+
+// ================================================================ hot path
+
+extern "C" int tq_evolve_taylor5(tq_ctx* c, const tq_pool* p, int k, double theta, tq_state* psi,
+                                 int renormalize, void* stream) {
+    API_BEGIN
+    TQ_REQUIRE(c && p && psi, "null argument");
+    TQ_REQUIRE(k >= 0 && k < p->M, "pool index out of range");
+    TQ_REQUIRE(std::isfinite(theta), "theta is not finite");
+    TQ_REQUIRE(psi->nq == p->nq, "state and pool qubit counts differ");
+    set_device(c);
+    cudaStream_t s = as_stream(stream);
+    const int tiles = taylor5_pair_tiles(p->nq);
+    double* part = static_cast<double*>(scratch(c, S_PART, (size_t)tiles * sizeof(double)));
+    launch(c, "taylor5_pair", s, [&] { return launch_taylor5_pair(p->view, 1, psi->prec, psi->data, nullptr, nullptr, k, theta, part,
+                                        tiles, taylor5_pair_grid(c->sm_count), s); });
+    if (renormalize) {
+        launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, 1, tiles, nullptr, &c->step->norm2, s); });
+        launch(c, "scale", s, [&] { return launch_scale(psi->data, psi->prec, psi->D, &c->step->norm2, s); });
+    }
+    API_END
+}
+
+extern "C" int tq_evolve_taylor5_csr(tq_ctx* c, int n_qubits, const int* rowptr, const int* col,
+                                     const void* val, double theta, tq_state* psi, int renormalize,
+                                     void* stream) {
+    API_BEGIN
+    TQ_REQUIRE(c && rowptr && col && val && psi, "null argument");
+    TQ_REQUIRE(std::isfinite(theta), "theta is not finite");
+    TQ_REQUIRE(psi->nq == n_qubits, "state and operator qubit counts differ");
+    set_device(c);
+    const long long D = psi->D;
+    const size_t vb = (size_t)D * elem_bytes(psi->prec);
+    double* acc = static_cast<double*>(scratch(c, S_U1, vb));
+    double* v0 = static_cast<double*>(scratch(c, S_U2, vb));
+    double* v1 = static_cast<double*>(scratch(c, S_W1, vb));
+    double* part = static_cast<double*>(scratch(c, S_PART, (size_t)c->sm_count * 4 * sizeof(double)));
+    launch(c, "taylor5_csr", as_stream(stream), [&] { return launch_taylor5_csr(n_qubits, psi->prec, rowptr, col, val, theta, psi->data, renormalize,
+                                       acc, v0, v1, part, &c->step->norm2, c->sm_count, as_stream(stream)); });
+    API_END
+}
+
+namespace {
+
+// Partials needed by energy + gradients (+ line search) on this problem.
+size_t partials_needed(long long D, int M, int nq, int sms) {
+    size_t n = (size_t)energy_grid(D, sms) * 2;
+    if (M > 0) {
+        int nch, chunk;
+        grad_layout(nq, &nch, &chunk);
+        n = std::max(n, (size_t)M * nch);
+    }
+    n = std::max(n, (size_t)512 * 5);
+    n = std::max(n, (size_t)taylor5_pair_tiles(nq));
+    return n + 8;
+}
+
+void run_energy(tq_ctx* c, const tq_ham* h, const tq_state* psi, double* part, cudaStream_t s) {
+    TQ_REQUIRE(h->nq == psi->nq, "state and Hamiltonian qubit counts differ");
+    TQ_REQUIRE(h->prec == psi->prec, "state and Hamiltonian precisions differ");
+    double2* w = static_cast<double2*>(c->scratch[S_W0]);
+    launch(c, "energy_csr", s, [&] { return launch_energy_csr(h->view, psi->data, psi->prec, w, part, c->tickets, c->step,
+                                      c->sm_count, s); });
+}
+
+void run_gradients(tq_ctx* c, const tq_ham* h, const tq_pool* p, const tq_state* psi, double* g,
+                   double* part, cudaStream_t s) {
+    TQ_REQUIRE(p->nq == psi->nq, "state and pool qubit counts differ");
+    run_energy(c, h, psi, part, s);
+    launch(c, "pool_gradients", s, [&] { return launch_pool_gradients(p->view, static_cast<double2*>(c->scratch[S_W0]), psi->data,
+                                          psi->prec, c->step, part, c->tickets + 16, g, c->sm_count, s); });
+}
+
+// Allocate (before any launch of the call) the scratch energy/gradients use.
+double* prepare(tq_ctx* c, long long D, int M, int nq) {
+    scratch(c, S_W0, (size_t)D * sizeof(double2));
+    tickets(c, 16 + (size_t)std::max(M, 0) + 64);
+    return static_cast<double*>(scratch(c, S_PART, partials_needed(D, M, nq, c->sm_count) * sizeof(double)));
+}
+
+}  // namespace
+
+extern "C" int tq_energy(tq_ctx* c, const tq_ham* h, const tq_state* psi, double* E, void* stream) {
+    API_BEGIN
+    TQ_REQUIRE(c && h && psi && E, "null argument");
+    set_device(c);
+    cudaStream_t s = as_stream(stream);
+    double* part = prepare(c, h->D, 0, h->nq);
+    run_energy(c, h, psi, part, s);
+    TQ_CUDA(cudaMemcpyAsync(E, &c->step->energy, sizeof(double), cudaMemcpyDeviceToHost, s));
+    TQ_CUDA(cudaStreamSynchronize(s));
+    API_END
+}
+
+extern "C" int tq_energy_matrix_free(tq_ctx* c, const tq_ham* h, const tq_state* psi, double* E,
+                                     void* stream) {
+    API_BEGIN
+    TQ_REQUIRE(c && h && psi && E, "null argument");
+    TQ_REQUIRE(h->nq == psi->nq, "state and Hamiltonian qubit counts differ");
+    set_device(c);
+    cudaStream_t s = as_stream(stream);
+    double* part = prepare(c, h->D, 0, h->nq);
+    launch(c, "energy_matrix_free", s, [&] { return launch_energy_matrix_free(h->view, psi->data, psi->prec, part, c->tickets + 1,
+                                              c->step, c->sm_count, s); });
+    TQ_CUDA(cudaMemcpyAsync(E, &c->step->energy, sizeof(double), cudaMemcpyDeviceToHost, s));
+    TQ_CUDA(cudaStreamSynchronize(s));
+    API_END
+}
+
+extern "C" int tq_pool_gradients(tq_ctx* c, const tq_ham* h, const tq_pool* p, const tq_state* psi, double* g,
+                                 int g_on_device, void* stream) {
+    API_BEGIN
+    TQ_REQUIRE(c && h && p && psi && g, "null argument");
+    set_device(c);
+    cudaStream_t s = as_stream(stream);
+    double* gd = g_on_device ? g : static_cast<double*>(scratch(c, S_G, (size_t)p->M * sizeof(double)));
+    double* part = prepare(c, h->D, p->M, p->nq);
+    run_gradients(c, h, p, psi, gd, part, s);
+    if (!g_on_device) {
+        TQ_CUDA(cudaMemcpyAsync(g, gd, (size_t)p->M * sizeof(double), cudaMemcpyDeviceToHost, s));
+        TQ_CUDA(cudaStreamSynchronize(s));
+    }
+    API_END
+}
+
+extern "C" int tq_adapt_step(tq_ctx* c, const tq_ham* h, const tq_pool* p, tq_state* psi, double eps,
+                             double theta, tq_adapt_result* out, void* stream) {
+    API_BEGIN
+    TQ_REQUIRE(c && h && p && psi && out, "null argument");
+    TQ_REQUIRE(std::isfinite(eps) && eps >= 0.0, "eps must be finite and >= 0");
+    TQ_REQUIRE(std::isnan(theta) || std::isfinite(theta), "theta must be finite or NaN");
+    set_device(c);
+    cudaStream_t s = as_stream(stream);
+    const long long D = h->D;
+    double* g = static_cast<double*>(scratch(c, S_G, (size_t)p->M * sizeof(double)));
+    const size_t vb = (size_t)D * sizeof(double2);
+    double2* u1 = static_cast<double2*>(scratch(c, S_U1, vb));
+    double2* u2 = static_cast<double2*>(scratch(c, S_U2, vb));
+    double2* w1 = static_cast<double2*>(scratch(c, S_W1, vb));
+    double2* w2 = static_cast<double2*>(scratch(c, S_W2, vb));
+    double* part = prepare(c, D, p->M, p->nq);
+    double2* w0 = static_cast<double2*>(c->scratch[S_W0]);
+    run_gradients(c, h, p, psi, g, part, s);
+    launch(c, "select", s, [&] { return launch_select(g, p->M, eps, psi->prec, c->step, s); });
+    if (std::isnan(theta)) {
+        launch(c, "apply_twice", s, [&] { return launch_apply_twice(p->view, c->step, psi->data, psi->prec, u1, u2, s); });
+        launch(c, "spmv_c128_gated", s, [&] { return launch_spmv_c128_gated(h->view, u1, w1, c->step, c->sm_count, s); });
+        launch(c, "spmv_c128_gated", s, [&] { return launch_spmv_c128_gated(h->view, u2, w2, c->step, c->sm_count, s); });
+        launch(c, "line_dots", s, [&] { return launch_line_dots(w0, w1, w2, u1, u2, D, part, c->tickets + 2, c->step, s); });
+    }
+    launch(c, "line_search", s, [&] { return launch_line_search(c->step, theta, s); });
+    const int tiles = taylor5_pair_tiles(p->nq);
+    launch(c, "taylor5_pair_gated", s, [&] { return launch_taylor5_pair_gated(p->view, psi->prec, psi->data, c->step, part, tiles,
+                                              taylor5_pair_grid(c->sm_count), s); });
+    launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, 1, tiles, nullptr, &c->step->norm2, s); });
+    launch(c, "scale_gated", s, [&] { return launch_scale_gated(psi->data, psi->prec, D, &c->step->norm2, c->step, s); });
+    DevStep hs;
+    TQ_CUDA(cudaMemcpyAsync(&hs, c->step, sizeof(DevStep), cudaMemcpyDeviceToHost, s));
+    TQ_CUDA(cudaStreamSynchronize(s));
+    out->energy = hs.energy;
+    out->max_grad = hs.max_grad;
+    out->selected = hs.selected;
+    out->converged = hs.converged;
+    out->theta = hs.converged ? 0.0 : hs.theta;
+    if (!hs.converged && !(std::isfinite(hs.norm2) && hs.norm2 > 0.0))
+        throw Error(TQ_ENUMERIC, "non-finite or zero norm after the update");
+    API_END
+}
+
+// ================================================================ batched
+
+extern "C" int tq_evolve_taylor5_batch(tq_ctx* c, const tq_pool* p, int n_states, int prec, void* psi,
+                                       const int* k, const double* theta, double* norm2, void* stream) {
+    API_BEGIN
+    TQ_REQUIRE(c && p && psi && k && theta, "null argument");
+    TQ_REQUIRE(n_states >= 0, "n_states < 0");
+    check_prec(prec);
+    TQ_REQUIRE(((uintptr_t)psi & 15u) == 0, "psi must be 16-byte aligned");
+    if (n_states == 0) return TQ_OK;
+    set_device(c);
+    cudaStream_t s = as_stream(stream);
+    const int tiles = taylor5_pair_tiles(p->nq);
+    double* part = static_cast<double*>(scratch(c, S_PART, (size_t)n_states * tiles * sizeof(double)));
+    launch(c, "taylor5_pair", s, [&] { return launch_taylor5_pair(p->view, n_states, prec, psi, k, theta, 0, 0.0, part, tiles,
+                                        taylor5_pair_grid(c->sm_count), s); });
+    if (norm2) launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, n_states, tiles, norm2, nullptr, s); });
+    API_END
+}
+
+extern "C" int tq_evolve_taylor5_batch_host(tq_ctx* c, const tq_pool* p, int n_states, int prec,
+                                            void* psi_host, const int* k_host, const double* theta_host,
+                                            double* norm2_host) {
+    API_BEGIN
+    TQ_REQUIRE(c && p && psi_host && k_host && theta_host, "null argument");
+    TQ_REQUIRE(n_states >= 0, "n_states < 0");
+    check_prec(prec);
+    if (n_states == 0) return TQ_OK;
+    set_device(c);
+    for (auto& st : c->aux)
+        if (!st) TQ_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    const long long D = 1ll << p->nq;
+    const size_t sb = (size_t)D * elem_bytes(prec);
+    // chunk of about 64 MiB of states per stream
+    int chunk = (int)std::max<long long>(1, (64ll << 20) / (long long)sb);
+    chunk = std::min(chunk, n_states);
+    const int tiles = taylor5_pair_tiles(p->nq);
+    const size_t per_stream = (size_t)chunk * sb + (size_t)chunk * (sizeof(int) + 2 * sizeof(double)) +
+                              (size_t)chunk * tiles * sizeof(double) + 256;
+    unsigned char* stage = static_cast<unsigned char*>(scratch(c, S_STAGE, 3 * per_stream));
+    const int grid = taylor5_pair_grid(c->sm_count);
+    for (int c0 = 0, it = 0; c0 < n_states; c0 += chunk, ++it) {
+        const int n = std::min(chunk, n_states - c0);
+        cudaStream_t s = c->aux[it % 3];
+        unsigned char* base = stage + (size_t)(it % 3) * per_stream;
+        void* dpsi = base;
+        int* dk = reinterpret_cast<int*>(base + (size_t)chunk * sb);
+        double* dth = reinterpret_cast<double*>(
+            (reinterpret_cast<uintptr_t>(dk + chunk) + 15) & ~(uintptr_t)15);
+        double* dn = dth + chunk;
+        double* part = dn + chunk;
+        TQ_CUDA(cudaMemcpyAsync(dpsi, static_cast<unsigned char*>(psi_host) + (size_t)c0 * sb, (size_t)n * sb,
+                                cudaMemcpyHostToDevice, s));
+        TQ_CUDA(cudaMemcpyAsync(dk, k_host + c0, (size_t)n * sizeof(int), cudaMemcpyHostToDevice, s));
+        TQ_CUDA(cudaMemcpyAsync(dth, theta_host + c0, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s));
+        launch(c, "taylor5_pair", s, [&] { return launch_taylor5_pair(p->view, n, prec, dpsi, dk, dth, 0, 0.0, part, tiles, grid, s); });
+        TQ_CUDA(cudaMemcpyAsync(static_cast<unsigned char*>(psi_host) + (size_t)c0 * sb, dpsi, (size_t)n * sb,
+                                cudaMemcpyDeviceToHost, s));
+        if (norm2_host) {
+            launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, n, tiles, dn, nullptr, s); });
+            TQ_CUDA(cudaMemcpyAsync(norm2_host + c0, dn, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        }
+    }
+    for (auto& st : c->aux) TQ_CUDA(cudaStreamSynchronize(st));
+    API_END
+}

@@ -1,0 +1,224 @@
+// Internal declarations shared by the host code and the CUDA kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "tq.h"
+
+namespace tq {
+
+struct Error : std::runtime_error {
+    int code;
+    Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+// ---------------------------------------------------------------- host algebra
+
+struct PauliTerm {
+    uint64_t x, z;  // X^x Z^z, Z acting first
+    double c;       // real coefficient of that product
+};
+
+struct Excitation {
+    int idx[4];  // (i, a, -1, -1) or (i, j, a, b)
+    int order;   // 1 single, 2 double
+};
+
+// Sign function of a pool generator in factored form:
+//   A[r][r ^ x] = c0 * (-1)^{popcount(col & z0)} * prod_{i<m} [parity(col & d_i) == t_i]
+// with col = r ^ x.  ok == 0 means "use the generic term sum".
+struct SignForm {
+    int ok;
+    int m;
+    double c0;
+    uint64_t z0;
+    uint64_t d[3];
+    int t;
+};
+
+void check_mapping(int mapping);
+std::vector<PauliTerm> pauli_hamiltonian(int n, const double* h1, const double* g2,
+                                         double e_const, int mapping);
+std::vector<Excitation> excitations(int n, int ne);
+std::vector<PauliTerm> pauli_generator(const Excitation& ex, int N, int mapping);
+uint64_t hf_index(int N, int ne, int mapping);
+SignForm factor_generator(const std::vector<PauliTerm>& t);
+
+// --------------------------------------------------------------- device views
+
+// Pool generators, structure of arrays (one entry per op unless noted).
+struct PoolView {
+    int M;
+    int nq;
+    const uint32_t* x;      // X-mask
+    const int* nterm;       // 2 or 8
+    const uint32_t* z;      // [8 M] Z-masks of the terms
+    const float* cf;        // [8 M] coefficients (float32 copy)
+    const double* cd;       // [8 M] coefficients (float64)
+    const int* fok;         // factored sign form available
+    const int* fm;          // number of parity conditions
+    const uint32_t* fz0;    // sign mask
+    const uint32_t* fd;     // [3 M] condition masks
+    const int* ft;          // target parities, bit i for condition i
+    const float* fc0f;      // leading coefficient, float32
+    const double* fc0d;     // leading coefficient, float64
+};
+
+// Hamiltonian: float64 diagonal + off-diagonal CSR + X-mask-grouped terms.
+struct HamView {
+    int nq;
+    int prec;
+    long long D;
+    long long nnz;
+    const double* diag;
+    const int* rowptr;
+    const int* col;
+    const void* val;        // double or float
+    int G;                  // off-diagonal X-mask groups
+    const uint32_t* gx;     // [G] group masks
+    const int* goff;        // [G + 1] term offsets
+    const uint32_t* tz;     // [K_off] term Z-masks
+    const double* tc;       // [K_off] term coefficients
+    int Kd;                 // diagonal (x = 0) terms
+    const uint32_t* dz;
+    const double* dc;
+};
+
+// Scalars an ADAPT iteration keeps on the device between its kernels.
+struct DevStep {
+    double e_num, e_den, energy;   // Rayleigh quotient pieces
+    double max_grad;
+    double theta;
+    double norm2;                  // ||psi'||^2 after the update
+    double dots[6];                // line-search matrix elements
+    int selected;
+    int converged;
+    int pad[2];
+};
+
+// ------------------------------------------------------------- kernel launchers
+// Every launcher enqueues on `stream` and returns the number of launches.
+
+// state
+int launch_set_basis(void* psi, int prec, long long D, long long index, cudaStream_t s);
+
+// CSR builder
+int launch_csr_count(const HamView& h, double tol, double amb_hi, int* counts,
+                     unsigned long long* n_amb, int sms, cudaStream_t s);
+int launch_diag(const HamView& h, double* diag, int sms, cudaStream_t s);
+int launch_scan(const int* counts, long long D, int* rowptr, long long* total,
+                int* max_row, cudaStream_t s);
+int launch_csr_fill(const HamView& h, double tol, int max_row, int* col, void* val,
+                    int prec, int sms, cudaStream_t s);
+
+// Taylor-5, matrix-free pair path: states back to back, op k[b] / theta[b]
+// (device arrays, or the immediates when the pointers are null).
+int launch_taylor5_pair(const PoolView& p, int n_states, int prec, void* psi,
+                        const int* k, const double* theta, int k_imm, double theta_imm,
+                        double* partials, int tiles_per_state, int grid, cudaStream_t s);
+int taylor5_pair_tiles(int nq);
+int taylor5_pair_grid(int sms);
+int launch_norm_reduce(const double* partials, int n_states, int tiles_per_state,
+                       double* norm2_out, double* step_norm2, cudaStream_t s);
+int launch_scale(void* psi, int prec, long long D, const double* norm2, cudaStream_t s);
+
+// Taylor-5 for a general CSR operator.
+int launch_taylor5_csr(int nq, int prec, const int* rowptr, const int* col, const void* val,
+                       double theta, void* psi, int renorm, double* scratch_acc,
+                       double* scratch_v0, double* scratch_v1, double* partials,
+                       double* norm2, int sms, cudaStream_t s);
+
+// Energy, gradients, ADAPT glue
+int launch_energy_csr(const HamView& h, const void* psi, int psi_prec, double2* w,
+                      double* partials, unsigned* ticket, DevStep* step, int sms,
+                      cudaStream_t s);
+int launch_energy_matrix_free(const HamView& h, const void* psi, int psi_prec,
+                              double* partials, unsigned* ticket, DevStep* step,
+                              int sms, cudaStream_t s);
+int launch_pool_gradients(const PoolView& p, const double2* w, const void* psi, int prec,
+                          const DevStep* step, double* partials, unsigned* tickets,
+                          double* g, int sms, cudaStream_t s);
+int launch_select(const double* g, int M, double eps, int prec, DevStep* step,
+                  cudaStream_t s);
+int launch_apply_twice(const PoolView& p, const DevStep* step, const void* psi, int prec,
+                       double2* u1, double2* u2, cudaStream_t s);
+int launch_spmv_c128(const HamView& h, const double2* x, double2* y, int sms,
+                     cudaStream_t s);
+int launch_line_dots(const double2* w0, const double2* w1, const double2* w2,
+                     const double2* u1, const double2* u2, long long D, double* partials,
+                     unsigned* ticket, DevStep* step, cudaStream_t s);
+int launch_line_search(DevStep* step, double theta_given, cudaStream_t s);
+
+// gated variants (skip when step->converged) and layout helpers
+int launch_taylor5_pair_gated(const PoolView& p, int prec, void* psi, const DevStep* step,
+                              double* partials, int tiles, int grid, cudaStream_t s);
+int launch_scale_gated(void* psi, int prec, long long D, const double* norm2,
+                       const DevStep* gate, cudaStream_t s);
+int launch_spmv_c128_gated(const HamView& h, const double2* x, double2* y,
+                           const DevStep* gate, int sms, cudaStream_t s);
+int energy_grid(long long D, int sms);
+void grad_layout(int nq, int* nch, int* chunk);
+
+}  // namespace tq
+
+// ------------------------------------------------------------------- handles
+
+struct tq_trace_rec {
+    const char* name;
+    cudaEvent_t start, stop;
+};
+
+struct tq_ctx {
+    int device = 0;
+    int sm_count = 0;
+    long long launches = 0;
+    int tracing = 0;
+    std::vector<tq_trace_rec> trace;      // recorded, not yet reported
+    std::vector<cudaEvent_t> event_pool;  // reusable events
+    // device scratch, grown on demand
+    void* scratch[8] = {nullptr};
+    size_t scratch_bytes[8] = {0};
+    tq::DevStep* step = nullptr;      // device
+    unsigned* tickets = nullptr;      // device, zero between calls
+    size_t tickets_n = 0;
+    cudaStream_t aux[3] = {nullptr, nullptr, nullptr};
+};
+
+struct tq_ham {
+    tq_ctx* ctx = nullptr;
+    int n_spatial = 0, nq = 0, prec = 0, mapping = 0;
+    long long D = 0, nnz = 0, n_pauli = 0, n_amb = 0;
+    int max_row = 0;
+    size_t bytes = 0;
+    std::vector<void*> allocs;
+    tq::HamView view{};
+};
+
+struct tq_pool {
+    tq_ctx* ctx = nullptr;
+    int n_spatial = 0, n_electrons = 0, nq = 0, mapping = 0, M = 0;
+    std::vector<int> idx4;
+    std::vector<tq::PauliTerm> terms;   // 8 slots per op (host copy)
+    std::vector<int> nterm;
+    std::vector<void*> allocs;
+    tq::PoolView view{};
+    // on-demand CSR per (op, precision)
+    std::vector<void*> csr_alloc[2];
+    std::vector<const int*> csr_rowptr[2];
+    std::vector<const int*> csr_col[2];
+    std::vector<const void*> csr_val[2];
+    std::vector<long long> csr_nnz[2];
+};
+
+struct tq_state {
+    tq_ctx* ctx = nullptr;
+    int nq = 0, prec = 0, owned = 0;
+    long long D = 0;
+    void* data = nullptr;
+};

@@ -1,0 +1,522 @@
+// Fifth-order Taylor state update, Sec. III-C, Eqs. (6)-(8):
+//   v_0 = psi, v_k = A v_{k-1} (k = 1..5),
+//   psi' = psi + theta v_1 + theta^2/2 v_2 + theta^3/6 v_3 + theta^4/24 v_4
+//              + theta^5/120 v_5.
+//
+// Pair path (pool generators).  A pool generator has one X-mask x, so row r
+// of A has its only candidate column at r ^ x, and the two-element set
+// {r, r ^ x} is closed under A.  Each thread therefore owns whole pairs: it
+// loads psi[r] and psi[r ^ x] once, runs the five products and the running
+// sum in registers, and stores both once.  Pairs are enumerated by
+// inserting a zero at the highest set bit hb of x; two consecutive
+// representatives r0, r0 + 1 and their partners form two aligned
+// two-element vectors, so every load and store is a 16-byte (complex64) or
+// 2 x 16-byte (complex128) access, coalesced across the warp.  Values of A
+// come from the generator's factored sign form (no matrix bytes are read).
+// The float64 squared norm of psi' is reduced per tile in the same pass.
+//
+// CSR path (any operator).  The state is staged in shared memory, split
+// over the CTAs of a thread-block cluster; the gather of v_{k-1} reads
+// peer CTAs' shared memory through the cluster mapping, each product is
+// followed by a cluster barrier, and the running sum lives in registers.
+// Global memory is touched by the initial load, the CSR, and the final
+// store only.  The float64 norm is reduced across the cluster and applied
+// before the store when renormalisation is asked for.
+#include "dev.cuh"
+
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
+
+namespace tq {
+
+namespace {
+
+constexpr int PAIR_BS = 256;
+constexpr int PAIR_UPT = 2;
+constexpr int TILE_UNITS = PAIR_BS * PAIR_UPT;   // 4 amplitudes per unit
+
+__device__ __forceinline__ void load2(const float2* p, uint32_t i, float2& a, float2& b) {
+    const float4 v = *reinterpret_cast<const float4*>(p + i);
+    a = make_float2(v.x, v.y);
+    b = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void store2(float2* p, uint32_t i, float2 a, float2 b) {
+    *reinterpret_cast<float4*>(p + i) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void load2(const double2* p, uint32_t i, double2& a, double2& b) {
+    a = p[i];
+    b = p[i + 1];
+}
+__device__ __forceinline__ void store2(double2* p, uint32_t i, double2 a, double2 b) {
+    p[i] = a;
+    p[i + 1] = b;
+}
+
+template <typename V, typename T>
+__device__ __forceinline__ V scal(T s, V v) {
+    V o;
+    o.x = s * v.x;
+    o.y = s * v.y;
+    return o;
+}
+template <typename V, typename T>
+__device__ __forceinline__ void axpy(V& acc, T c, V v) {
+    acc.x = fma(c, v.x, acc.x);
+    acc.y = fma(c, v.y, acc.y);
+}
+
+// Five chained products on one closed pair (r, q = r ^ x) with
+// s_r = A[r][q], s_q = A[q][r]; returns the accumulated pair in (ar, aq).
+template <typename V, typename T>
+__device__ __forceinline__ void chain_pair(T s_r, T s_q, const T (&cf)[6], V& ar, V& aq) {
+    V vr = ar, vq = aq;
+#pragma unroll
+    for (int k = 1; k <= 5; ++k) {
+        const V nr = scal(s_r, vq);   // (A v)[r] = A[r][q] v[q]
+        const V nq = scal(s_q, vr);   // (A v)[q] = A[q][r] v[r]
+        vr = nr;
+        vq = nq;
+        axpy(ar, cf[k], vr);
+        axpy(aq, cf[k], vq);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void taylor_coefs(double theta, T (&cf)[6]) {
+    double c = 1.0;
+    cf[0] = T(1);
+#pragma unroll
+    for (int k = 1; k <= 5; ++k) {
+        c = c * theta / (double)k;
+        cf[k] = (T)c;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PAIR_BS)
+k_taylor5_pair(PoolView p, int n_states, typename C2<T>::type* psi, const int* kk,
+               const double* th, int k_imm, double th_imm, double* partials,
+               int tiles_per_state, const DevStep* gate) {
+    using V = typename C2<T>::type;
+    __shared__ double sh[PAIR_BS / 32];
+    if (gate && gate->converged) return;
+    const int nq = p.nq;
+    const long long D = 1ll << nq;
+    const uint32_t units = (uint32_t)(D >> 2);
+    const long long total = (long long)n_states * tiles_per_state;
+    for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
+        const int b = (int)(tile / tiles_per_state);
+        const int tl = (int)(tile - (long long)b * tiles_per_state);
+        const int k = kk ? kk[b] : k_imm;
+        const double theta = th ? th[b] : th_imm;
+        if (k < 0 || k >= p.M) {
+            // invalid op index from device memory: leave the state untouched
+            // and poison its norm so the caller sees it
+            if (threadIdx.x == 0) partials[tile] = __longlong_as_double(0x7ff8000000000000ll);
+            continue;
+        }
+        OpSign<T> op;
+        op.load(p, k);
+        const uint32_t x = op.x;
+        const int hb = 31 - __clz(x);
+        T cf[6];
+        taylor_coefs<T>(theta, cf);
+        V* base = psi + (long long)b * D;
+        T part = T(0);
+#pragma unroll
+        for (int j = 0; j < PAIR_UPT; ++j) {
+            const uint32_t u = (uint32_t)tl * TILE_UNITS + j * PAIR_BS + threadIdx.x;
+            if (u >= units) continue;
+            V e0, e1, f0, f1;
+            if (hb > 0) {
+                // reps r0, r0+1 (one aligned vector), partners r0^x, r0^x^1
+                const uint32_t r0 = insert_zero(2u * u, hb);
+                const uint32_t q0 = r0 ^ x;
+                const uint32_t qa = q0 & ~1u;
+                load2(base, r0, e0, e1);
+                load2(base, qa, f0, f1);
+                // partner of r0 is q0, partner of r0+1 is q0^1
+                V a0 = e0, a1 = e1;
+                V b0 = (q0 & 1u) ? f1 : f0;   // psi[q0]
+                V b1 = (q0 & 1u) ? f0 : f1;   // psi[q0 ^ 1]
+                const T s_r0 = op.value(q0), s_q0 = op.value(r0);
+                const T s_r1 = op.value(q0 ^ 1u), s_q1 = op.value(r0 + 1u);
+                chain_pair(s_r0, s_q0, cf, a0, b0);
+                chain_pair(s_r1, s_q1, cf, a1, b1);
+                part += a0.x * a0.x + a0.y * a0.y + a1.x * a1.x + a1.y * a1.y;
+                part += b0.x * b0.x + b0.y * b0.y + b1.x * b1.x + b1.y * b1.y;
+                store2(base, r0, a0, a1);
+                if (q0 & 1u) store2(base, qa, b1, b0);
+                else store2(base, qa, b0, b1);
+            } else {
+                // x == 1: pairs (4u, 4u+1) and (4u+2, 4u+3)
+                const uint32_t r0 = 4u * u, r1 = r0 + 2u;
+                load2(base, r0, e0, f0);
+                load2(base, r1, e1, f1);
+                const T s_r0 = op.value(r0 + 1u), s_q0 = op.value(r0);
+                const T s_r1 = op.value(r1 + 1u), s_q1 = op.value(r1);
+                chain_pair(s_r0, s_q0, cf, e0, f0);
+                chain_pair(s_r1, s_q1, cf, e1, f1);
+                part += e0.x * e0.x + e0.y * e0.y + f0.x * f0.x + f0.y * f0.y;
+                part += e1.x * e1.x + e1.y * e1.y + f1.x * f1.x + f1.y * f1.y;
+                store2(base, r0, e0, f0);
+                store2(base, r1, e1, f1);
+            }
+        }
+        double v[1] = {(double)part};
+        block_sum<1>(v, sh);
+        if (threadIdx.x == 0) partials[tile] = v[0];
+    }
+}
+
+// One warp per state: fixed-order float64 sum of the state's tile partials.
+__global__ void k_norm_reduce(const double* partials, int n_states, int tiles,
+                              double* norm2_out, double* step_norm2) {
+    const int lane = threadIdx.x & 31;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= n_states) return;
+    double s = 0.0;
+    for (int t = lane; t < tiles; t += 32) s += partials[(long long)w * tiles + t];
+    s = warp_sum(s);
+    if (lane == 0) {
+        if (norm2_out) norm2_out[w] = s;
+        if (step_norm2 && w == 0) *step_norm2 = s;
+    }
+}
+
+template <typename V>
+__global__ void k_scale(V* psi, long long D, const double* norm2, const DevStep* gate) {
+    if (gate && gate->converged) return;
+    const double sc = 1.0 / sqrt(*norm2);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < D; i += stride) {
+        V v = psi[i];
+        v.x = (decltype(v.x))((double)v.x * sc);
+        v.y = (decltype(v.y))((double)v.y * sc);
+        psi[i] = v;
+    }
+}
+
+// ---------------------------------------------------------------- CSR path
+
+template <typename T, typename VT, int RPT>
+__global__ void __launch_bounds__(1024)
+k_taylor5_csr_cluster(int nq, int csize, const int* __restrict__ rowptr,
+                      const int* __restrict__ col, const VT* __restrict__ val, double theta,
+                      typename C2<T>::type* psi, int renorm, double* norm2_out) {
+    using V = typename C2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* sv = reinterpret_cast<V*>(smem_raw);
+    __shared__ double red[32];
+    __shared__ double cta_part;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const long long D = 1ll << nq;
+    const int per = (int)(D / csize);
+    const int shift = 31 - __clz(per);
+    const int bs = blockDim.x;
+    const int row0 = rank * per;
+    for (int i = threadIdx.x; i < per; i += bs) sv[i] = psi[row0 + i];
+    T cf[6];
+    taylor_coefs<T>(theta, cf);
+    V acc[RPT];
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+        const int i = threadIdx.x + j * bs;
+        acc[j] = i < per ? sv[i] : V{};   // written by this thread above
+    }
+    cl.sync();
+    for (int step = 1; step <= 5; ++step) {
+        V nv[RPT];
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) {
+            const int i = threadIdx.x + j * bs;
+            V s{};
+            if (i < per) {
+                const int r = row0 + i;
+                const int e1 = rowptr[r + 1];
+                for (int e = rowptr[r]; e < e1; ++e) {
+                    const int c = col[e];
+                    if ((unsigned)c >= (unsigned)D) continue;   // column outside the state
+                    const V* src = cl.map_shared_rank(sv, c >> shift);
+                    const V v = src[c & (per - 1)];
+                    const T a = (T)val[e];
+                    s.x = fma(a, v.x, s.x);
+                    s.y = fma(a, v.y, s.y);
+                }
+            }
+            nv[j] = s;
+        }
+        cl.sync();   // every CTA has finished reading v_{k-1}
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) {
+            const int i = threadIdx.x + j * bs;
+            if (i < per) {
+                sv[i] = nv[j];
+                axpy(acc[j], cf[step], nv[j]);
+            }
+        }
+        cl.sync();   // v_k visible cluster-wide
+    }
+    double part = 0.0;
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+        const int i = threadIdx.x + j * bs;
+        if (i < per) part += (double)acc[j].x * acc[j].x + (double)acc[j].y * acc[j].y;
+    }
+    double v[1] = {part};
+    block_sum<1>(v, red);
+    if (threadIdx.x == 0) cta_part = v[0];
+    cl.sync();
+    double total = 0.0;
+    for (int q = 0; q < csize; ++q) total += *cl.map_shared_rank(&cta_part, q);
+    const double sc = renorm ? 1.0 / sqrt(total) : 1.0;
+#pragma unroll
+    for (int j = 0; j < RPT; ++j) {
+        const int i = threadIdx.x + j * bs;
+        if (i < per) {
+            V o;
+            o.x = (T)((double)acc[j].x * sc);
+            o.y = (T)((double)acc[j].y * sc);
+            psi[row0 + i] = o;
+        }
+    }
+    if (rank == 0 && threadIdx.x == 0 && norm2_out) *norm2_out = total;
+    cl.sync();   // peers may still read this CTA's shared memory
+}
+
+// Unfused fallback for states too large for a cluster: one pass per product,
+// v and the running sum in global (L2-resident) buffers.
+template <typename T, typename VT>
+__global__ void k_csr_step(long long D, const int* __restrict__ rowptr,
+                           const int* __restrict__ col, const VT* __restrict__ val,
+                           const typename C2<T>::type* vin, typename C2<T>::type* vout,
+                           typename C2<T>::type* acc, double coef) {
+    using V = typename C2<T>::type;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < D; r += stride) {
+        V s{};
+        for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+            const int c = col[e];
+            if ((unsigned long long)c >= (unsigned long long)D) continue;
+            const V v = vin[c];
+            const T a = (T)val[e];
+            s.x = fma(a, v.x, s.x);
+            s.y = fma(a, v.y, s.y);
+        }
+        vout[r] = s;
+        V a = acc[r];
+        axpy(a, (T)coef, s);
+        acc[r] = a;
+    }
+}
+
+template <typename V>
+__global__ void k_copy(const V* a, V* b, long long D) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < D; i += stride) b[i] = a[i];
+}
+
+template <typename V>
+__global__ void k_norm_partials(const V* a, long long D, double* partials) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < D; i += stride)
+        s += (double)a[i].x * a[i].x + (double)a[i].y * a[i].y;
+    double v[1] = {s};
+    block_sum<1>(v, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = v[0];
+}
+
+template <typename V>
+__global__ void k_finish(const V* acc, V* psi, long long D, const double* partials, int nparts,
+                         int renorm, double* norm2_out) {
+    __shared__ double total_sh;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < nparts; ++i) t += partials[i];
+        total_sh = t;
+        if (blockIdx.x == 0 && norm2_out) *norm2_out = t;
+    }
+    __syncthreads();
+    const double sc = renorm ? 1.0 / sqrt(total_sh) : 1.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < D; i += stride) {
+        V v = acc[i];
+        v.x = (decltype(v.x))((double)v.x * sc);
+        v.y = (decltype(v.y))((double)v.y * sc);
+        psi[i] = v;
+    }
+}
+
+template <typename T, typename VT, int RPT>
+cudaError_t launch_cluster(int nq, int csize, int bs, const int* rowptr, const int* col,
+                           const VT* val, double theta, void* psi, int renorm, double* norm2,
+                           cudaStream_t s) {
+    using V = typename C2<T>::type;
+    auto kern = k_taylor5_csr_cluster<T, VT, RPT>;
+    const size_t smem = (size_t)((1ll << nq) / csize) * sizeof(V);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (csize > 8) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(csize);
+    cfg.blockDim = dim3(bs);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
+    if (e != cudaSuccess) return e;
+    if (nclusters < 1) return cudaErrorInvalidConfiguration;
+    return cudaLaunchKernelEx(&cfg, kern, nq, csize, rowptr, col, val, theta,
+                              static_cast<V*>(psi), renorm, norm2);
+}
+
+template <typename T, typename VT>
+cudaError_t dispatch_cluster(int nq, int csize, const int* rowptr, const int* col,
+                             const VT* val, double theta, void* psi, int renorm,
+                             double* norm2, cudaStream_t s) {
+    const long long per = (1ll << nq) / csize;
+    const int bs = (int)(per < 1024 ? (per < 32 ? 32 : per) : 1024);
+    const int rpt = (int)((per + bs - 1) / bs);
+    // rows per thread: at most 8 (complex64) or 4 (complex128), see the
+    // slice size chosen in launch_taylor5_csr
+    switch (rpt) {
+        case 1: return launch_cluster<T, VT, 1>(nq, csize, bs, rowptr, col, val, theta, psi, renorm, norm2, s);
+        case 2: return launch_cluster<T, VT, 2>(nq, csize, bs, rowptr, col, val, theta, psi, renorm, norm2, s);
+        case 4: return launch_cluster<T, VT, 4>(nq, csize, bs, rowptr, col, val, theta, psi, renorm, norm2, s);
+        case 8:
+            if constexpr (sizeof(T) == 4)
+                return launch_cluster<T, VT, 8>(nq, csize, bs, rowptr, col, val, theta, psi, renorm, norm2, s);
+            return cudaErrorInvalidConfiguration;
+        default: return cudaErrorInvalidConfiguration;
+    }
+}
+
+template <typename T, typename VT>
+int run_unfused(int nq, const int* rowptr, const int* col, const VT* val, double theta,
+                void* psi, int renorm, double* acc_buf, double* v0_buf, double* v1_buf,
+                double* partials, double* norm2, int sms, cudaStream_t s) {
+    using V = typename C2<T>::type;
+    const long long D = 1ll << nq;
+    V* acc = reinterpret_cast<V*>(acc_buf);
+    V* v0 = reinterpret_cast<V*>(v0_buf);
+    V* v1 = reinterpret_cast<V*>(v1_buf);
+    V* p = static_cast<V*>(psi);
+    const int bs = 256;
+    const int grid = sms * 4;
+    k_copy<V><<<grid, bs, 0, s>>>(p, acc, D);
+    k_copy<V><<<grid, bs, 0, s>>>(p, v0, D);
+    double c = 1.0;
+    for (int k = 1; k <= 5; ++k) {
+        c = c * theta / (double)k;
+        k_csr_step<T, VT><<<grid, bs, 0, s>>>(D, rowptr, col, val, v0, v1, acc, c);
+        V* t = v0;
+        v0 = v1;
+        v1 = t;
+    }
+    k_norm_partials<V><<<grid, bs, 0, s>>>(acc, D, partials);
+    k_finish<V><<<grid, bs, 0, s>>>(acc, p, D, partials, grid, renorm, norm2);
+    return 9;
+}
+
+}  // namespace
+
+int taylor5_pair_tiles(int nq) {
+    const long long units = (1ll << nq) >> 2;
+    return (int)((units + TILE_UNITS - 1) / TILE_UNITS);
+}
+
+int taylor5_pair_grid(int sms) { return sms * 8; }
+
+int launch_taylor5_pair(const PoolView& p, int n_states, int prec, void* psi, const int* k,
+                        const double* theta, int k_imm, double theta_imm, double* partials,
+                        int tiles_per_state, int grid, cudaStream_t s) {
+    const long long total = (long long)n_states * tiles_per_state;
+    if (grid > total) grid = (int)total;
+    if (grid < 1) grid = 1;
+    if (prec == TQ_C128)
+        k_taylor5_pair<double><<<grid, PAIR_BS, 0, s>>>(p, n_states, static_cast<double2*>(psi), k,
+                                                        theta, k_imm, theta_imm, partials,
+                                                        tiles_per_state, nullptr);
+    else
+        k_taylor5_pair<float><<<grid, PAIR_BS, 0, s>>>(p, n_states, static_cast<float2*>(psi), k,
+                                                       theta, k_imm, theta_imm, partials,
+                                                       tiles_per_state, nullptr);
+    return 1;
+}
+
+int launch_taylor5_pair_gated(const PoolView& p, int prec, void* psi, const DevStep* step,
+                              double* partials, int tiles, int grid, cudaStream_t s) {
+    if (grid > tiles) grid = tiles;
+    if (prec == TQ_C128)
+        k_taylor5_pair<double><<<grid, PAIR_BS, 0, s>>>(p, 1, static_cast<double2*>(psi), &step->selected,
+                                                        &step->theta, 0, 0.0, partials, tiles, step);
+    else
+        k_taylor5_pair<float><<<grid, PAIR_BS, 0, s>>>(p, 1, static_cast<float2*>(psi), &step->selected,
+                                                       &step->theta, 0, 0.0, partials, tiles, step);
+    return 1;
+}
+
+int launch_norm_reduce(const double* partials, int n_states, int tiles_per_state,
+                       double* norm2_out, double* step_norm2, cudaStream_t s) {
+    const int bs = 256;
+    const int grid = (n_states * 32 + bs - 1) / bs;
+    k_norm_reduce<<<grid, bs, 0, s>>>(partials, n_states, tiles_per_state, norm2_out, step_norm2);
+    return 1;
+}
+
+int launch_scale_gated(void* psi, int prec, long long D, const double* norm2, const DevStep* gate,
+                       cudaStream_t s) {
+    const int bs = 256;
+    const int grid = (int)((D + bs - 1) / bs < 1024 ? (D + bs - 1) / bs : 1024);
+    if (prec == TQ_C128)
+        k_scale<double2><<<grid, bs, 0, s>>>(static_cast<double2*>(psi), D, norm2, gate);
+    else
+        k_scale<float2><<<grid, bs, 0, s>>>(static_cast<float2*>(psi), D, norm2, gate);
+    return 1;
+}
+
+int launch_scale(void* psi, int prec, long long D, const double* norm2, cudaStream_t s) {
+    return launch_scale_gated(psi, prec, D, norm2, nullptr, s);
+}
+
+int launch_taylor5_csr(int nq, int prec, const int* rowptr, const int* col, const void* val,
+                       double theta, void* psi, int renorm, double* acc, double* v0, double* v1,
+                       double* partials, double* norm2, int sms, cudaStream_t s) {
+    const long long D = 1ll << nq;
+    // slice per CTA: 64 KiB of shared memory, and at most 8 rows per thread
+    // so that v_k and the running sum of each row fit in registers
+    const long long per_max = prec == TQ_C128 ? 4096 : 8192;
+    long long csize = D <= per_max ? 1 : D / per_max;
+    if (csize <= 16) {
+        cudaError_t e;
+        if (prec == TQ_C128)
+            e = dispatch_cluster<double, double>(nq, (int)csize, rowptr, col,
+                                                 static_cast<const double*>(val), theta, psi, renorm, norm2, s);
+        else
+            e = dispatch_cluster<float, float>(nq, (int)csize, rowptr, col,
+                                               static_cast<const float*>(val), theta, psi, renorm, norm2, s);
+        if (e == cudaSuccess) return 1;
+        cudaGetLastError();   // clear a refused cluster configuration; fall back below
+    }
+    if (prec == TQ_C128)
+        return run_unfused<double, double>(nq, rowptr, col, static_cast<const double*>(val), theta, psi,
+                                           renorm, acc, v0, v1, partials, norm2, sms, s);
+    return run_unfused<float, float>(nq, rowptr, col, static_cast<const float*>(val), theta, psi, renorm,
+                                     acc, v0, v1, partials, norm2, sms, s);
+}
+
+}  // namespace tq

@@ -1,0 +1,282 @@
+// Host-side fermion -> qubit algebra (Sec. II-A, Eqs. (2)-(4); pool of
+// Sec. III-E).
+//
+// Every mapping used here is a linear encoding of occupation bits over
+// GF(2): qubit bits b = B n (mod 2), with B = I for Jordan-Wigner and the
+// Fenwick-tree matrix for Bravyi-Kitaev (qubit k stores the parity of modes
+// k+1-lowbit(k+1) .. k).  For any invertible B the creation operator is
+//
+//   a+_j = X^{c_j} Z^{p_j} (1 + Z^{q_j}) / 2
+//        = 1/2 X^{c_j} Z^{p_j} + 1/2 X^{c_j} Z^{p_j ^ q_j},
+//
+// (Z factors act first) where c_j is column j of B (the qubits flipped when
+// mode j fills), q_j is row j of B^-1 (so (-1)^{q_j . b} = (-1)^{n_j}) and
+// p_j is the XOR of rows 0..j-1 of B^-1 (so (-1)^{p_j . b} is the fermionic
+// sign of the modes below j).  Because p_j . c_j = 0 and q_j . c_j = 1, the
+// annihilation operator is a_j = 1/2 X^c Z^p - 1/2 X^c Z^{p^q}.
+//
+// A term is held as (x, z, c) meaning c * X^x Z^z, which has real matrix
+// elements: <r| X^x Z^z |col> = (-1)^{popcount(col & z)} when r = col ^ x.
+// Products use X^a Z^b X^c Z^d = (-1)^{popcount(b & c)} X^{a^c} Z^{b^d}, so
+// all coefficients stay real throughout.
+#include "common.h"
+
+#include <algorithm>
+#include <cmath>
+
+namespace tq {
+
+namespace {
+
+struct Enc {
+    int N;
+    std::vector<uint64_t> c;  // column j of B, as a qubit mask
+    std::vector<uint64_t> q;  // row j of B^-1
+    std::vector<uint64_t> p;  // xor of rows 0..j-1 of B^-1
+};
+
+int lowbit(int i) { return i & (-i); }
+
+Enc make_encoding(int N, int mapping) {
+    Enc e;
+    e.N = N;
+    // rows of B as masks over modes
+    std::vector<uint64_t> rows(N, 0);
+    for (int k = 0; k < N; ++k) {
+        if (mapping == TQ_JW) {
+            rows[k] = 1ull << k;
+        } else {
+            int lo = k + 1 - lowbit(k + 1);
+            for (int i = lo; i <= k; ++i) rows[k] |= 1ull << i;
+        }
+    }
+    e.c.assign(N, 0);
+    for (int k = 0; k < N; ++k)
+        for (int j = 0; j < N; ++j)
+            if ((rows[k] >> j) & 1) e.c[j] |= 1ull << k;
+    // invert B over GF(2) by Gauss-Jordan on [B | I]
+    std::vector<uint64_t> a = rows, inv(N, 0);
+    for (int k = 0; k < N; ++k) inv[k] = 1ull << k;
+    for (int col = 0; col < N; ++col) {
+        int piv = -1;
+        for (int r = col; r < N; ++r)
+            if ((a[r] >> col) & 1) { piv = r; break; }
+        if (piv < 0) throw Error(TQ_ENUMERIC, "encoding matrix is singular");
+        std::swap(a[piv], a[col]);
+        std::swap(inv[piv], inv[col]);
+        for (int r = 0; r < N; ++r)
+            if (r != col && ((a[r] >> col) & 1)) { a[r] ^= a[col]; inv[r] ^= inv[col]; }
+    }
+    // inv[j] is row j of B^-1 as a mask over qubits
+    e.q = inv;
+    e.p.assign(N, 0);
+    uint64_t acc = 0;
+    for (int j = 0; j < N; ++j) { e.p[j] = acc; acc ^= inv[j]; }
+    return e;
+}
+
+struct Term { uint64_t x, z; double c; };
+
+inline int parity64(uint64_t v) { return __builtin_popcountll(v) & 1; }
+
+// Ladder operator as two terms.
+inline void ladder(const Enc& e, int j, bool create, Term out[2]) {
+    out[0] = {e.c[j], e.p[j], 0.5};
+    out[1] = {e.c[j], e.p[j] ^ e.q[j], create ? 0.5 : -0.5};
+}
+
+inline Term mul(const Term& a, const Term& b) {
+    double s = parity64(a.z & b.x) ? -1.0 : 1.0;
+    return {a.x ^ b.x, a.z ^ b.z, a.c * b.c * s};
+}
+
+// Expand coef * op_0 op_1 ... op_{m-1} (left to right) into `out`.
+void expand(const Enc& e, double coef, const int* modes, const bool* create, int m,
+            std::vector<Term>& out) {
+    Term lad[4][2];
+    for (int o = 0; o < m; ++o) ladder(e, modes[o], create[o], lad[o]);
+    for (int choice = 0; choice < (1 << m); ++choice) {
+        Term t = lad[0][choice & 1];
+        for (int o = 1; o < m; ++o) t = mul(t, lad[o][(choice >> o) & 1]);
+        t.c *= coef;
+        out.push_back(t);
+    }
+}
+
+// Sort by (x, z), merge like terms (summing in generation order), drop
+// |c| <= rel * max|c|.
+std::vector<PauliTerm> canonicalise(std::vector<Term>& t, double rel) {
+    std::stable_sort(t.begin(), t.end(), [](const Term& a, const Term& b) {
+        return a.x != b.x ? a.x < b.x : a.z < b.z;
+    });
+    std::vector<PauliTerm> merged;
+    for (size_t i = 0; i < t.size();) {
+        size_t j = i;
+        double s = 0.0;
+        while (j < t.size() && t[j].x == t[i].x && t[j].z == t[i].z) s += t[j++].c;
+        merged.push_back({t[i].x, t[i].z, s});
+        i = j;
+    }
+    double mx = 0.0;
+    for (auto& m : merged) mx = std::max(mx, std::fabs(m.c));
+    std::vector<PauliTerm> out;
+    for (auto& m : merged)
+        if (std::fabs(m.c) > rel * mx) out.push_back(m);
+    return out;
+}
+
+}  // namespace
+
+void check_mapping(int mapping) {
+    if (mapping != TQ_JW && mapping != TQ_BK) throw Error(TQ_EINVAL, "mapping must be TQ_JW or TQ_BK");
+}
+
+std::vector<PauliTerm> pauli_hamiltonian(int n, const double* h1, const double* g2,
+                                         double e_const, int mapping) {
+    if (n < 1 || n > TQ_MAX_SPATIAL) throw Error(TQ_EINVAL, "n_spatial out of range [1, 15]");
+    if (!h1 || !g2) throw Error(TQ_EINVAL, "null integral array");
+    check_mapping(mapping);
+    const int N = 2 * n;
+    Enc e = make_encoding(N, mapping);
+    std::vector<Term> terms;
+    terms.reserve(16ull * N * N * N * N / 4 + 4ull * N * N + 1);
+    // one-body: h_PQ a+_P a_Q, equal spins
+    for (int P = 0; P < N; ++P)
+        for (int Q = 0; Q < N; ++Q) {
+            if ((P & 1) != (Q & 1)) continue;
+            double v = h1[(P >> 1) * n + (Q >> 1)];
+            if (v == 0.0) continue;
+            int modes[2] = {P, Q};
+            bool cr[2] = {true, false};
+            expand(e, v, modes, cr, 2, terms);
+        }
+    // two-body: 1/2 (PQ|RS) a+_P a+_R a_S a_Q, sigma_P = sigma_Q, sigma_R = sigma_S
+    for (int P = 0; P < N; ++P)
+        for (int Q = 0; Q < N; ++Q) {
+            if ((P & 1) != (Q & 1)) continue;
+            for (int R = 0; R < N; ++R)
+                for (int S = 0; S < N; ++S) {
+                    if ((R & 1) != (S & 1) || P == R || Q == S) continue;
+                    size_t idx = (((size_t)(P >> 1) * n + (Q >> 1)) * n + (R >> 1)) * n + (S >> 1);
+                    double v = g2[idx];
+                    if (v == 0.0) continue;
+                    int modes[4] = {P, R, S, Q};
+                    bool cr[4] = {true, true, false, false};
+                    expand(e, 0.5 * v, modes, cr, 4, terms);
+                }
+        }
+    terms.push_back({0, 0, e_const});
+    std::vector<PauliTerm> out = canonicalise(terms, 1e-12);
+    for (auto& t : out)
+        if (parity64(t.x & t.z))
+            throw Error(TQ_ENUMERIC, "Hamiltonian term with an odd number of Y survived");
+    return out;
+}
+
+std::vector<Excitation> excitations(int n, int ne) {
+    if (n < 1 || n > TQ_MAX_SPATIAL) throw Error(TQ_EINVAL, "n_spatial out of range [1, 15]");
+    const int N = 2 * n;
+    if (ne < 0 || ne > N) throw Error(TQ_EINVAL, "n_electrons out of range [0, 2 n_spatial]");
+    std::vector<Excitation> out;
+    for (int i = 0; i < ne; ++i)
+        for (int a = ne; a < N; ++a)
+            if ((i & 1) == (a & 1)) out.push_back({{i, a, -1, -1}, 1});
+    for (int i = 0; i < ne; ++i)
+        for (int j = i + 1; j < ne; ++j)
+            for (int a = ne; a < N; ++a)
+                for (int b = a + 1; b < N; ++b)
+                    if ((i & 1) + (j & 1) == (a & 1) + (b & 1)) out.push_back({{i, j, a, b}, 2});
+    return out;
+}
+
+std::vector<PauliTerm> pauli_generator(const Excitation& ex, int N, int mapping) {
+    check_mapping(mapping);
+    Enc e = make_encoding(N, mapping);
+    std::vector<Term> t;
+    if (ex.order == 1) {
+        int i = ex.idx[0], a = ex.idx[1];
+        int m1[2] = {a, i}, m2[2] = {i, a};
+        bool cr[2] = {true, false};
+        expand(e, 1.0, m1, cr, 2, t);    // tau = a+_a a_i
+        expand(e, -1.0, m2, cr, 2, t);   // -tau+ = -a+_i a_a
+    } else {
+        int i = ex.idx[0], j = ex.idx[1], a = ex.idx[2], b = ex.idx[3];
+        int m1[4] = {a, b, j, i}, m2[4] = {i, j, b, a};
+        bool cr[4] = {true, true, false, false};
+        expand(e, 1.0, m1, cr, 4, t);    // tau = a+_a a+_b a_j a_i
+        expand(e, -1.0, m2, cr, 4, t);   // -tau+ = -a+_i a+_j a_b a_a
+    }
+    return canonicalise(t, 1e-12);
+}
+
+uint64_t hf_index(int N, int ne, int mapping) {
+    check_mapping(mapping);
+    if (ne < 0 || ne > N) throw Error(TQ_EINVAL, "n_electrons out of range");
+    Enc e = make_encoding(N, mapping);
+    uint64_t b = 0;
+    for (int P = 0; P < ne; ++P) b ^= e.c[P];
+    return b;
+}
+
+// Factor a generator's sign function (see common.h, SignForm).  The z masks
+// of its 2^m terms form an affine space z0 ^ span(d_1..d_m); when the
+// coefficients are c0 / 2^m * prod_i (-1)^{a_i t_i} (a = coordinates in that
+// basis) the sum collapses to c0 (-1)^{col.z0} prod_i [col.d_i == t_i].
+SignForm factor_generator(const std::vector<PauliTerm>& t) {
+    SignForm f{};
+    const int K = (int)t.size();
+    int m = 0;
+    while ((1 << m) < K) ++m;
+    if ((1 << m) != K || m > 3) return f;  // not factorable -> generic path
+    for (auto& x : t)
+        if (x.x != t[0].x) return f;
+    // basis of {z_p ^ z0} by elimination, remembering pivot bits
+    const uint64_t z0 = t[0].z;
+    std::vector<uint64_t> basis;
+    std::vector<int> pivot;
+    for (int p = 1; p < K && (int)basis.size() < m; ++p) {
+        uint64_t v = t[p].z ^ z0;
+        for (size_t i = 0; i < basis.size(); ++i)
+            if ((v >> pivot[i]) & 1) v ^= basis[i];
+        if (v) {
+            int pb = 63 - __builtin_clzll(v);
+            for (size_t i = 0; i < basis.size(); ++i)
+                if ((basis[i] >> pb) & 1) basis[i] ^= v;
+            basis.push_back(v);
+            pivot.push_back(pb);
+        }
+    }
+    if ((int)basis.size() != m) return f;
+    const double c0 = t[0].c * (double)K;
+    // coordinates of each term, and the implied signs t_i from unit vectors
+    auto coords = [&](uint64_t z) {
+        uint64_t v = z ^ z0;
+        int a = 0;
+        for (size_t i = 0; i < basis.size(); ++i)
+            if ((v >> pivot[i]) & 1) { v ^= basis[i]; a |= 1 << i; }
+        return v ? -1 : a;
+    };
+    int tbits = 0;
+    std::vector<int> coord(K);
+    for (int p = 0; p < K; ++p) {
+        coord[p] = coords(t[p].z);
+        if (coord[p] < 0) return f;
+    }
+    for (int p = 0; p < K; ++p)
+        for (int i = 0; i < m; ++i)
+            if (coord[p] == (1 << i) && t[p].c * c0 < 0) tbits |= 1 << i;
+    for (int p = 0; p < K; ++p) {
+        int par = __builtin_popcount(coord[p] & tbits) & 1;
+        double expect = c0 / (double)K * (par ? -1.0 : 1.0);
+        if (t[p].c != expect) return f;
+    }
+    f.ok = 1;
+    f.m = m;
+    f.c0 = c0;
+    f.z0 = z0;
+    for (int i = 0; i < m; ++i) f.d[i] = basis[i];
+    f.t = tbits;
+    return f;
+}
+
+}  // namespace tq

@@ -1,0 +1,500 @@
+// Energy (Eq. (1)), pool gradients (Eq. (5)) and the device-side ADAPT
+// glue (Sec. III-D step 3): operator choice, convergence test and the
+// line search for the new angle.
+//
+// Every float64 reduction is deterministic: warps reduce with a fixed
+// shuffle tree, CTAs write one partial each, and the last CTA to finish
+// (atomic ticket, reset by that CTA) sums the partials in index order.
+#include "dev.cuh"
+
+#include <cmath>
+
+namespace tq {
+
+namespace {
+
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+// Last-CTA finalisation: returns true in every thread of the last CTA.
+__device__ __forceinline__ bool last_block(unsigned* ticket, unsigned nblocks) {
+    __shared__ bool is_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(ticket, 1u);
+        is_last = (t == nblocks - 1);
+    }
+    __syncthreads();
+    return is_last;
+}
+
+template <typename T> __device__ __forceinline__ double2 to_d2(typename C2<T>::type v) {
+    return make_double2((double)v.x, (double)v.y);
+}
+
+// w = H psi (diagonal float64 + CSR off-diagonal), and the float64 sums
+// <psi|w> and <psi|psi>.  One warp per row.
+template <typename T, typename VT>
+__global__ void __launch_bounds__(256)
+k_energy_csr(HamView h, const typename C2<T>::type* __restrict__ psi, double2* __restrict__ w,
+             double* partials, unsigned* ticket, DevStep* step) {
+    __shared__ double sh[2 * 8];
+    const VT* __restrict__ val = static_cast<const VT*>(h.val);
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    double num = 0.0, den = 0.0;
+    for (long long r = warp; r < h.D; r += nwarps) {
+        T px = T(0), py = T(0);
+        const int e1 = h.rowptr[r + 1];
+        for (int e = h.rowptr[r] + lane; e < e1; e += 32) {
+            const T a = (T)val[e];
+            const auto v = psi[h.col[e]];
+            px = fma(a, v.x, px);
+            py = fma(a, v.y, py);
+        }
+        const double sx = warp_sum((double)px), sy = warp_sum((double)py);
+        if (lane == 0) {
+            const double2 pr = to_d2<T>(psi[r]);
+            const double d = h.diag[r];
+            const double wx = fma(d, pr.x, sx), wy = fma(d, pr.y, sy);
+            if (w) w[r] = make_double2(wx, wy);
+            num += pr.x * wx + pr.y * wy;
+            den += pr.x * pr.x + pr.y * pr.y;
+        }
+    }
+    double v[2] = {num, den};
+    block_sum<2>(v, sh);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = v[0];
+        partials[2 * blockIdx.x + 1] = v[1];
+    }
+    if (last_block(ticket, gridDim.x) && threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (unsigned i = 0; i < gridDim.x; ++i) {
+            a += __ldcg(partials + 2 * i);
+            b += __ldcg(partials + 2 * i + 1);
+        }
+        step->e_num = a;
+        step->e_den = b;
+        step->energy = a / b;
+        *ticket = 0u;
+    }
+}
+
+// Same energy from the X-mask-grouped terms (no CSR): one warp per row,
+// lanes over groups and over diagonal terms.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_energy_mf(HamView h, const typename C2<T>::type* __restrict__ psi, double* partials,
+            unsigned* ticket, DevStep* step) {
+    __shared__ double sh[2 * 8];
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    double num = 0.0, den = 0.0;
+    for (long long r = warp; r < h.D; r += nwarps) {
+        const uint32_t ru = (uint32_t)r;
+        double sx = 0.0, sy = 0.0, dg = 0.0;
+        for (int g = lane; g < h.G; g += 32) {
+            const uint32_t c = ru ^ h.gx[g];
+            double a = 0.0;
+            for (int t = h.goff[g]; t < h.goff[g + 1]; ++t)
+                a += parity32(c & h.tz[t]) ? -h.tc[t] : h.tc[t];
+            const double2 v = to_d2<T>(psi[c]);
+            sx = fma(a, v.x, sx);
+            sy = fma(a, v.y, sy);
+        }
+        for (int t = lane; t < h.Kd; t += 32) dg += parity32(ru & h.dz[t]) ? -h.dc[t] : h.dc[t];
+        sx = warp_sum(sx);
+        sy = warp_sum(sy);
+        dg = warp_sum(dg);
+        if (lane == 0) {
+            const double2 pr = to_d2<T>(psi[r]);
+            const double wx = fma(dg, pr.x, sx), wy = fma(dg, pr.y, sy);
+            num += pr.x * wx + pr.y * wy;
+            den += pr.x * pr.x + pr.y * pr.y;
+        }
+    }
+    double v[2] = {num, den};
+    block_sum<2>(v, sh);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = v[0];
+        partials[2 * blockIdx.x + 1] = v[1];
+    }
+    if (last_block(ticket, gridDim.x) && threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (unsigned i = 0; i < gridDim.x; ++i) {
+            a += __ldcg(partials + 2 * i);
+            b += __ldcg(partials + 2 * i + 1);
+        }
+        step->e_num = a;
+        step->e_den = b;
+        step->energy = a / b;
+        *ticket = 0u;
+    }
+}
+
+// g_k = 2 Re<w|A_k psi> / <psi|psi> for all k: work items (op, row chunk)
+// in one persistent launch; per-op tickets pick the CTA that finalises g_k.
+constexpr int GRAD_BS = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(GRAD_BS)
+k_pool_grad(PoolView p, const double2* __restrict__ w, const typename C2<T>::type* __restrict__ psi,
+            const DevStep* step, double* partials, unsigned* tickets, double* g, int nch,
+            int chunk) {
+    __shared__ double sh[GRAD_BS / 32];
+    const long long items = (long long)p.M * nch;
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const int k = (int)(it / nch);
+        const int c = (int)(it - (long long)k * nch);
+        OpSign<double> op;
+        op.load(p, k);
+        double acc = 0.0;
+        const uint32_t r0 = (uint32_t)c * chunk;
+        for (int i = threadIdx.x; i < chunk; i += GRAD_BS) {
+            const uint32_t r = r0 + i;
+            const uint32_t q = r ^ op.x;
+            const double s = op.value(q);
+            if (s != 0.0) {
+                const double2 wr = w[r];
+                const double2 v = to_d2<T>(psi[q]);
+                acc += s * (wr.x * v.x + wr.y * v.y);
+            }
+        }
+        double v[1] = {acc};
+        block_sum<1>(v, sh);
+        __shared__ bool last;
+        if (threadIdx.x == 0) {
+            partials[it] = v[0];
+            __threadfence();
+            const unsigned t = atomicAdd(&tickets[k], 1u);
+            last = (t == (unsigned)nch - 1);
+        }
+        __syncthreads();
+        if (last && threadIdx.x == 0) {
+            double s = 0.0;
+            for (int i = 0; i < nch; ++i) s += __ldcg(partials + (long long)k * nch + i);
+            g[k] = 2.0 * s / step->e_den;
+            tickets[k] = 0u;
+        }
+        __syncthreads();
+    }
+}
+
+// Operator choice and convergence (one CTA).
+__global__ void k_select(const double* g, int M, double eps, int prec, DevStep* step) {
+    __shared__ double smax[32];
+    __shared__ int smin[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double m = 0.0;
+    for (int k = threadIdx.x; k < M; k += blockDim.x) m = fmax(m, fabs(g[k]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    if (lane == 0) smax[wid] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mm = 0.0;
+        for (int i = 0; i < nw; ++i) mm = fmax(mm, smax[i]);
+        smax[0] = mm;
+    }
+    __syncthreads();
+    const double gmax = smax[0];
+    const double tau = prec == TQ_C128 ? 1e-9 * fmax(1.0, gmax) : 1e-5;
+    int best = M;
+    for (int k = threadIdx.x; k < M; k += blockDim.x)
+        if (fabs(g[k]) >= gmax - tau && k < best) best = k;
+    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_down_sync(0xffffffffu, best, o));
+    if (lane == 0) smin[wid] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int b = M;
+        for (int i = 0; i < nw; ++i) b = min(b, smin[i]);
+        step->selected = b < M ? b : 0;
+        step->max_grad = gmax;
+        step->converged = gmax < eps ? 1 : 0;
+    }
+}
+
+// u1 = A psi, u2 = A u1 for the selected op (float64 outputs).
+template <typename T>
+__global__ void k_apply_twice(PoolView p, const DevStep* step, const typename C2<T>::type* psi,
+                              double2* u1, double2* u2, long long D) {
+    if (step->converged) return;
+    OpSign<double> op;
+    op.load(p, step->selected);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < D; i += stride) {
+        const uint32_t r = (uint32_t)i, q = r ^ op.x;
+        const double s_r = op.value(q);   // A[r][q]
+        const double s_q = op.value(r);   // A[q][r]
+        const double2 pq = to_d2<T>(psi[q]);
+        const double2 pr = to_d2<T>(psi[r]);
+        u1[r] = make_double2(s_r * pq.x, s_r * pq.y);
+        const double s2 = s_r * s_q;
+        u2[r] = make_double2(s2 * pr.x, s2 * pr.y);
+    }
+}
+
+// y = H x for float64 complex x (line search products).
+template <typename VT>
+__global__ void __launch_bounds__(256)
+k_spmv_c128(HamView h, const double2* __restrict__ x, double2* __restrict__ y, const DevStep* gate) {
+    if (gate && gate->converged) return;
+    const VT* __restrict__ val = static_cast<const VT*>(h.val);
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long r = warp; r < h.D; r += nwarps) {
+        double sx = 0.0, sy = 0.0;
+        for (int e = h.rowptr[r] + lane; e < h.rowptr[r + 1]; e += 32) {
+            const double a = (double)val[e];
+            const double2 v = x[h.col[e]];
+            sx = fma(a, v.x, sx);
+            sy = fma(a, v.y, sy);
+        }
+        sx = warp_sum(sx);
+        sy = warp_sum(sy);
+        if (lane == 0) {
+            const double d = h.diag[r];
+            const double2 xr = x[r];
+            y[r] = make_double2(fma(d, xr.x, sx), fma(d, xr.y, sy));
+        }
+    }
+}
+
+// Five Re-dots of the line search, divided by <psi|psi>:
+// dots = {<w0|u1>, <w0|u2>, <u1|w1>, <w1|u2>, <u2|w2>}.
+__global__ void __launch_bounds__(256)
+k_line_dots(const double2* w0, const double2* w1, const double2* w2, const double2* u1,
+            const double2* u2, long long D, double* partials, unsigned* ticket, DevStep* step) {
+    __shared__ double sh[5 * 8];
+    if (step->converged) return;
+    double a[5] = {0, 0, 0, 0, 0};
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < D; i += stride) {
+        const double2 x0 = w0[i], x1 = w1[i], x2 = w2[i], v1 = u1[i], v2 = u2[i];
+        a[0] += x0.x * v1.x + x0.y * v1.y;
+        a[1] += x0.x * v2.x + x0.y * v2.y;
+        a[2] += v1.x * x1.x + v1.y * x1.y;
+        a[3] += x1.x * v2.x + x1.y * v2.y;
+        a[4] += v2.x * x2.x + v2.y * x2.y;
+    }
+    // two-stage block sum (block_sum handles up to 4 values)
+    double lo[4] = {a[0], a[1], a[2], a[3]};
+    double hi[1] = {a[4]};
+    block_sum<4>(lo, sh);
+    block_sum<1>(hi, sh + 32);
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < 4; ++j) partials[5 * blockIdx.x + j] = lo[j];
+        partials[5 * blockIdx.x + 4] = hi[0];
+    }
+    if (last_block(ticket, gridDim.x) && threadIdx.x == 0) {
+        double s[5] = {0, 0, 0, 0, 0};
+        for (unsigned b = 0; b < gridDim.x; ++b)
+            for (int j = 0; j < 5; ++j) s[j] += __ldcg(partials + 5 * b + j);
+        for (int j = 0; j < 5; ++j) step->dots[1 + j] = s[j] / step->e_den;
+        *ticket = 0u;
+    }
+}
+
+__device__ __forceinline__ double line_e(const double* c, double th) {
+    const double s = sin(th), u = 1.0 - cos(th);
+    return c[0] + 2 * s * c[1] + 2 * u * c[2] + s * s * c[3] + 2 * s * u * c[4] + u * u * c[5];
+}
+__device__ __forceinline__ double line_d1(const double* c, double th) {
+    const double s = sin(th), cc = cos(th), u = 1.0 - cc;
+    return 2 * cc * c[1] + 2 * s * c[2] + 2 * s * cc * c[3] + 2 * (cc * u + s * s) * c[4] + 2 * u * s * c[5];
+}
+__device__ __forceinline__ double line_d2(const double* c, double th) {
+    const double s = sin(th), cc = cos(th), u = 1.0 - cc;
+    return -2 * s * c[1] + 2 * cc * c[2] + 2 * (cc * cc - s * s) * c[3] +
+           2 * (3 * s * cc - s * u) * c[4] + 2 * (s * s + u * cc) * c[5];
+}
+__device__ __forceinline__ double sample_theta(int m) {
+    return -kPi + 2.0 * kPi * (double)(m + 1) / 4096.0;
+}
+
+// Angle for the update: the given one, or the line-search minimiser
+// (4096 samples over (-pi, pi], ties within 1e-10 max(1,|E_min|) to the
+// smallest |theta| then lowest index, Newton polish within one spacing).
+__global__ void k_line_search(DevStep* step, double theta_given) {
+    __shared__ double se[4096];
+    __shared__ double red[32];
+    __shared__ int redi[32];
+    if (step->converged) return;
+    if (!isnan(theta_given)) {
+        if (threadIdx.x == 0) step->theta = theta_given;
+        return;
+    }
+    double c[6];
+    c[0] = step->energy;
+    c[1] = step->dots[1];   // H01
+    c[2] = step->dots[2];   // H02
+    c[3] = step->dots[3];   // H11
+    c[4] = step->dots[4];   // H12
+    c[5] = step->dots[5];   // H22
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double mn = INFINITY;
+    for (int m = threadIdx.x; m < 4096; m += blockDim.x) {
+        const double e = line_e(c, sample_theta(m));
+        se[m] = e;
+        mn = fmin(mn, e);
+    }
+    for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));
+    if (lane == 0) red[wid] = mn;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = INFINITY;
+        for (int i = 0; i < nw; ++i) m = fmin(m, red[i]);
+        red[0] = m;
+    }
+    __syncthreads();
+    const double emin = red[0];
+    const double tol = 1e-10 * fmax(1.0, fabs(emin));
+    // candidates within tol: key = (|theta| rank, index) -> pick smallest |theta|, then m
+    int best = -1;
+    for (int m = threadIdx.x; m < 4096; m += blockDim.x) {
+        if (se[m] <= emin + tol) {
+            if (best < 0 || fabs(sample_theta(m)) < fabs(sample_theta(best)) ||
+                (fabs(sample_theta(m)) == fabs(sample_theta(best)) && m < best))
+                best = m;
+        }
+    }
+    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) {
+        const int other = __shfl_down_sync(0xffffffffu, best, o);
+        if (other >= 0 && (best < 0 || fabs(sample_theta(other)) < fabs(sample_theta(best)) ||
+                           (fabs(sample_theta(other)) == fabs(sample_theta(best)) && other < best)))
+            best = other;
+    }
+    if (lane == 0) redi[wid] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int b = -1;
+        for (int i = 0; i < nw; ++i) {
+            const int o = redi[i];
+            if (o >= 0 && (b < 0 || fabs(sample_theta(o)) < fabs(sample_theta(b)) ||
+                           (fabs(sample_theta(o)) == fabs(sample_theta(b)) && o < b)))
+                b = o;
+        }
+        const double th0 = sample_theta(b);
+        const double e0 = se[b];
+        const double h = 2.0 * kPi / 4096.0;
+        double th = th0;
+        for (int it = 0; it < 8; ++it) {
+            const double d2 = line_d2(c, th);
+            if (!(d2 > 0.0)) break;
+            const double stp = line_d1(c, th) / d2;
+            const double nt = th - stp;
+            if (fabs(nt - th0) > h) break;
+            th = nt;
+            if (fabs(stp) < 1e-15) break;
+        }
+        if (line_e(c, th) > e0) th = th0;
+        step->theta = th;
+    }
+}
+
+int grid_rows(long long D, int rows_per_block, int sms, int per_sm) {
+    long long g = (D + rows_per_block - 1) / rows_per_block;
+    const long long cap = (long long)sms * per_sm;
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+int energy_grid(long long D, int sms) { return grid_rows(D, 8, sms, 8); }
+
+int launch_energy_csr(const HamView& h, const void* psi, int psi_prec, double2* w,
+                      double* partials, unsigned* ticket, DevStep* step, int sms, cudaStream_t s) {
+    const int grid = energy_grid(h.D, sms);
+    if (psi_prec == TQ_C128)
+        k_energy_csr<double, double><<<grid, 256, 0, s>>>(h, static_cast<const double2*>(psi), w, partials,
+                                                          ticket, step);
+    else
+        k_energy_csr<float, float><<<grid, 256, 0, s>>>(h, static_cast<const float2*>(psi), w, partials,
+                                                        ticket, step);
+    return 1;
+}
+
+int launch_energy_matrix_free(const HamView& h, const void* psi, int psi_prec, double* partials,
+                              unsigned* ticket, DevStep* step, int sms, cudaStream_t s) {
+    const int grid = energy_grid(h.D, sms);
+    if (psi_prec == TQ_C128)
+        k_energy_mf<double><<<grid, 256, 0, s>>>(h, static_cast<const double2*>(psi), partials, ticket, step);
+    else
+        k_energy_mf<float><<<grid, 256, 0, s>>>(h, static_cast<const float2*>(psi), partials, ticket, step);
+    return 1;
+}
+
+void grad_layout(int nq, int* nch, int* chunk) {
+    const long long D = 1ll << nq;
+    int c = (int)(D < 2048 ? D : 2048);
+    *chunk = c;
+    *nch = (int)(D / c);
+}
+
+int launch_pool_gradients(const PoolView& p, const double2* w, const void* psi, int prec,
+                          const DevStep* step, double* partials, unsigned* tickets, double* g,
+                          int sms, cudaStream_t s) {
+    int nch, chunk;
+    grad_layout(p.nq, &nch, &chunk);
+    const long long items = (long long)p.M * nch;
+    const int grid = (int)(items < (long long)sms * 8 ? items : (long long)sms * 8);
+    if (prec == TQ_C128)
+        k_pool_grad<double><<<grid, GRAD_BS, 0, s>>>(p, w, static_cast<const double2*>(psi), step, partials,
+                                                     tickets, g, nch, chunk);
+    else
+        k_pool_grad<float><<<grid, GRAD_BS, 0, s>>>(p, w, static_cast<const float2*>(psi), step, partials,
+                                                    tickets, g, nch, chunk);
+    return 1;
+}
+
+int launch_select(const double* g, int M, double eps, int prec, DevStep* step, cudaStream_t s) {
+    k_select<<<1, 1024, 0, s>>>(g, M, eps, prec, step);
+    return 1;
+}
+
+int launch_apply_twice(const PoolView& p, const DevStep* step, const void* psi, int prec, double2* u1,
+                       double2* u2, cudaStream_t s) {
+    const long long D = 1ll << p.nq;
+    const int bs = 256;
+    const int grid = (int)((D + bs - 1) / bs < 2048 ? (D + bs - 1) / bs : 2048);
+    if (prec == TQ_C128)
+        k_apply_twice<double><<<grid, bs, 0, s>>>(p, step, static_cast<const double2*>(psi), u1, u2, D);
+    else
+        k_apply_twice<float><<<grid, bs, 0, s>>>(p, step, static_cast<const float2*>(psi), u1, u2, D);
+    return 1;
+}
+
+int launch_spmv_c128_gated(const HamView& h, const double2* x, double2* y, const DevStep* gate, int sms,
+                           cudaStream_t s) {
+    const int grid = energy_grid(h.D, sms);
+    if (h.prec == TQ_C128)
+        k_spmv_c128<double><<<grid, 256, 0, s>>>(h, x, y, gate);
+    else
+        k_spmv_c128<float><<<grid, 256, 0, s>>>(h, x, y, gate);
+    return 1;
+}
+
+int launch_spmv_c128(const HamView& h, const double2* x, double2* y, int sms, cudaStream_t s) {
+    return launch_spmv_c128_gated(h, x, y, nullptr, sms, s);
+}
+
+int launch_line_dots(const double2* w0, const double2* w1, const double2* w2, const double2* u1,
+                     const double2* u2, long long D, double* partials, unsigned* ticket, DevStep* step,
+                     cudaStream_t s) {
+    const int bs = 256;
+    const int grid = (int)((D + bs - 1) / bs < 512 ? (D + bs - 1) / bs : 512);
+    k_line_dots<<<grid, bs, 0, s>>>(w0, w1, w2, u1, u2, D, partials, ticket, step);
+    return 1;
+}
+
+int launch_line_search(DevStep* step, double theta_given, cudaStream_t s) {
+    k_line_search<<<1, 1024, 0, s>>>(step, theta_given);
+    return 1;
+}
+
+}  // namespace tq

@@ -1,0 +1,120 @@
+"""C ABI checks that need no GPU.
+
+The library must load without a device, export every entry point declared
+in include/tq.h, and its host-side algebra (Pauli sums, pool, Hartree-Fock
+index) must match the oracle: masks bit-exact, coefficients to rounding.
+"""
+
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import adapt as oadapt
+from oracle import fermion, mapping, pauli
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            names |= set(re.findall(r"^\s*(?:const\s+char\s*\*|int|void)\s+(tq_\w+)\s*\(", txt, re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def tq():
+    from paper_2606_29692_gb300 import build
+    if not os.path.exists(build.LIB):
+        build.build()
+    import paper_2606_29692_gb300 as m
+    m.lib()
+    return m
+
+
+def test_every_declared_symbol_is_exported(tq):
+    from paper_2606_29692_gb300 import _native
+    declared = _declared_symbols()
+    assert len(declared) >= 25
+    out = subprocess.run(["nm", "-D", "--defined-only", _native.LIB_PATH], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r"\bT (tq_\w+)", out))
+    assert declared <= exported, declared - exported
+    # the Python binding declares every one of them too
+    assert declared <= set(_native.SIGNATURES)
+
+
+def test_no_gpu_needed_to_load(tq):
+    assert tq.lib().tq_version() == 100
+
+
+def _oracle_matrix_coefs(ps):
+    ny = np.bitwise_count(ps.x & ps.z).astype(np.int64)
+    return (ps.c * (1j ** (ny % 4)))
+
+
+@pytest.mark.parametrize("mp", [mapping.JW, mapping.BK])
+@pytest.mark.parametrize("cfg", ["c0", "c1", "c2", "n5"])
+def test_pauli_hamiltonian_matches_oracle(tq, mp, cfg):
+    if cfg == "n5":
+        ints, ne = synth.integrals(5, 77), 4
+    else:
+        ints, ne = {"c0": synth.config0, "c1": synth.config1, "c2": synth.config2}[cfg]()
+    x, z, c = tq.pauli_hamiltonian(ints.h, ints.g, 0.5, mp)
+    ps = pauli.qubit_hamiltonian(ints.h, ints.g, 0.5, mp)
+    assert np.array_equal(x.astype(np.int64), ps.x)
+    assert np.array_equal(z.astype(np.int64), ps.z)
+    cm = _oracle_matrix_coefs(ps)
+    assert np.abs(cm.imag).max() == 0.0
+    assert np.abs(c - cm.real).max() <= 1e-14 * np.abs(c).max()
+
+
+def test_pool_excitations_match_oracle(tq):
+    for n, ne in [(4, 4), (6, 8), (7, 6), (5, 2), (8, 8)]:
+        idx = tq.pool_excitations(n, ne)
+        ref = fermion.excitations(n, ne)
+        assert idx.shape[0] == len(ref)
+        for row, e in zip(idx, ref):
+            assert tuple(int(v) for v in row[: len(e)]) == e
+            assert all(v == -1 for v in row[len(e):])
+
+
+@pytest.mark.parametrize("mp", [mapping.JW, mapping.BK])
+def test_pauli_pool_matches_oracle(tq, mp):
+    n, ne = 7, 6
+    x, nt, z, c = tq.pauli_pool(n, ne, mp)
+    _, ref = pauli.pool_pauli(n, ne, mp)
+    assert len(ref) == x.size == 204
+    for k, ps in enumerate(ref):
+        assert nt[k] == ps.n_terms
+        assert np.all(ps.x == int(x[k]))
+        assert np.array_equal(z[k, : nt[k]].astype(np.int64), ps.z)
+        cm = _oracle_matrix_coefs(ps)
+        assert np.array_equal(c[k, : nt[k]], cm.real)    # dyadic: exact
+        assert np.abs(cm.imag).max() == 0.0
+
+
+@pytest.mark.parametrize("mp", [mapping.JW, mapping.BK])
+def test_hf_index_matches_oracle(tq, mp):
+    for nq, ne in [(8, 4), (12, 8), (14, 6), (16, 8), (18, 8), (30, 10)]:
+        B = mapping.encoding_matrix(nq, mp)
+        assert tq.hf_index(nq, ne, mp) == mapping.encode_index(fermion.hf_occupation_index(ne), B)
+
+
+def test_invalid_arguments_are_rejected(tq):
+    with pytest.raises(tq.TQError) as e:
+        tq.pool_excitations(0, 0)
+    assert e.value.code == -1
+    with pytest.raises(tq.TQError):
+        tq.pool_excitations(4, 9)
+    with pytest.raises(tq.TQError):
+        tq.hf_index(8, 4, 7)
+    ints, _ = synth.config0()
+    with pytest.raises(tq.TQError):
+        tq.pauli_hamiltonian(ints.h, ints.g, 0.0, 5)

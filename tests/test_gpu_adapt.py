@@ -1,0 +1,137 @@
+"""GPU parity: the ADAPT iteration (selection, line search, update)."""
+
+import numpy as np
+import pytest
+
+import paper_2606_29692_gb300 as tq
+import synth
+from gpu_util import fidelity, rel_l2, to_state
+from oracle import adapt as oadapt
+from oracle import evolve
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return tq.Context(0)
+
+
+@pytest.mark.parametrize("mp", [0, 1])
+def test_config0_one_step(ctx, mp):
+    """8 qubits, JW/BK, complex128: one step from HF at theta = 0.05."""
+    ints, ne = synth.config0()
+    sysm = oadapt.build_system(ints, ne, mp)
+    psi0 = oadapt.hf_state(8, ne, mp)
+    ref, psi_ref = oadapt.adapt_step(sysm, psi0, 1e-3, theta=0.05)
+    ham = tq.build_hamiltonian(ctx, ints.h, ints.g, 0.0, mp, tq.TQ_C128)
+    pool = tq.build_pool(ctx, 4, ne, mp)
+    st = tq.State(ctx, 8, tq.TQ_C128)
+    tq.state_set_hf(st, ne, mp)
+    r = tq.adapt_step(ctx, ham, pool, st, 1e-3, 0.05)
+    assert abs(r["energy"] - ref.energy) <= 1e-10
+    assert abs(r["max_grad"] - ref.max_grad) <= 1e-10
+    assert r["selected"] == ref.selected and not r["converged"]
+    assert r["theta"] == 0.05
+    out = st.numpy()
+    assert rel_l2(out, psi_ref) <= 1e-12
+    ex = evolve.expm_dense(sysm.pool[ref.selected], 0.05) @ psi0
+    assert fidelity(out, ex) > 0.999999
+
+
+def _teacher_forced(ctx, mp, prec, n_iter):
+    ints, ne = synth.config1()
+    sysm = oadapt.build_system(ints, ne, mp)
+    ham = tq.build_hamiltonian(ctx, ints.h, ints.g, 0.0, mp, prec)
+    pool = tq.build_pool(ctx, 6, ne, mp)
+    psi = oadapt.hf_state(12, ne, mp)
+    precision = oadapt.FP64 if prec == tq.TQ_C128 else oadapt.C64
+    tau = 1e-9 if prec == tq.TQ_C128 else 1e-5
+    for it in range(n_iter):
+        ref, nxt = oadapt.adapt_step(sysm, psi, 1e-3, None, precision)
+        st = to_state(ctx, psi, 12, prec)
+        held = st.numpy()
+        r = tq.adapt_step(ctx, ham, pool, st, 1e-3)
+        tolE = 1e-10 if prec == tq.TQ_C128 else 1e-6
+        assert abs(r["energy"] - ref.energy) <= tolE, it
+        assert abs(r["max_grad"] - ref.max_grad) <= tolE, it
+        # selection: identical, or a tie within tau of the maximum
+        assert abs(abs(ref.gradients[r["selected"]]) - ref.max_grad) <= tau + tolE, it
+        if r["selected"] == ref.selected:
+            assert abs(r["theta"] - ref.theta) <= 1e-9 * max(1, abs(ref.theta)) + (1e-5 if prec else 0), it
+            if prec == tq.TQ_C128:
+                assert rel_l2(st.numpy(), nxt) <= 1e-12, it
+            else:
+                _, nxt_held = oadapt.adapt_step(sysm, held, 1e-3, r["theta"], precision,
+                                                force_k=r["selected"])
+                assert fidelity(st.numpy(), nxt_held) > 0.999999, it
+        psi = nxt
+        if ref.converged:
+            break
+
+
+@pytest.mark.parametrize("mp", [0, 1])
+def test_config1_teacher_forced_fp64(ctx, mp):
+    _teacher_forced(ctx, mp, tq.TQ_C128, 20)
+
+
+@pytest.mark.parametrize("mp", [0, 1])
+def test_config1_teacher_forced_c64(ctx, mp):
+    _teacher_forced(ctx, mp, tq.TQ_C64, 8)
+
+
+@pytest.mark.parametrize("prec", [tq.TQ_C128, tq.TQ_C64])
+def test_config1_free_running(ctx, prec):
+    """20 iterations on the GPU alone vs the oracle's own trajectory."""
+    ints, ne = synth.config1()
+    mp = 1
+    sysm = oadapt.build_system(ints, ne, mp)
+    res, psi_ref = oadapt.trajectory(sysm, oadapt.hf_state(12, ne, mp), 1e-3, n_iter=20)
+    ham = tq.build_hamiltonian(ctx, ints.h, ints.g, 0.0, mp, prec)
+    pool = tq.build_pool(ctx, 6, ne, mp)
+    st = tq.State(ctx, 12, prec)
+    tq.state_set_hf(st, ne, mp)
+    for it, ref in enumerate(res):
+        r = tq.adapt_step(ctx, ham, pool, st, 1e-3)
+        tolE = 1e-10 if prec == tq.TQ_C128 else 1e-6
+        assert r["selected"] == ref.selected, it
+        assert abs(r["energy"] - ref.energy) <= tolE, it
+    assert fidelity(st.numpy(), psi_ref) > 0.999999
+
+
+def test_config2_c64_vs_fp64(ctx):
+    """14 qubits, BK, strongly correlated: full-pool screen, complex64 vs float64."""
+    ints, ne = synth.config2()
+    mp = 1
+    out = {}
+    for prec in (tq.TQ_C128, tq.TQ_C64):
+        ham = tq.build_hamiltonian(ctx, ints.h, ints.g, 0.0, mp, prec)
+        pool = tq.build_pool(ctx, 7, ne, mp)
+        st = tq.State(ctx, 14, prec)
+        tq.state_set_hf(st, ne, mp)
+        es = []
+        for _ in range(4):
+            es.append(tq.adapt_step(ctx, ham, pool, st, 1e-3, 0.1))
+        out[prec] = (es, st.numpy())
+    for a, b in zip(out[tq.TQ_C128][0], out[tq.TQ_C64][0]):
+        assert a["selected"] == b["selected"]
+        assert abs(a["energy"] - b["energy"]) <= 1e-6
+    assert fidelity(out[tq.TQ_C128][1], out[tq.TQ_C64][1]) > 0.999999
+    # and the float64 path against the oracle
+    sysm = oadapt.build_system(ints, ne, mp)
+    res, psi = oadapt.trajectory(sysm, oadapt.hf_state(14, ne, mp), 1e-3, thetas=[0.1] * 4)
+    for a, ref in zip(out[tq.TQ_C128][0], res):
+        assert a["selected"] == ref.selected and abs(a["energy"] - ref.energy) <= 1e-10
+    assert rel_l2(out[tq.TQ_C128][1], psi) <= 1e-12
+
+
+def test_converged_step_leaves_state(ctx):
+    ints, ne = synth.config0()
+    ham = tq.build_hamiltonian(ctx, ints.h, ints.g, 0.0, 0, tq.TQ_C128)
+    pool = tq.build_pool(ctx, 4, ne, 0)
+    st = tq.State(ctx, 8, tq.TQ_C128)
+    tq.state_set_hf(st, ne, 0)
+    before = st.numpy()
+    r = tq.adapt_step(ctx, ham, pool, st, 1e3)     # eps above every gradient
+    assert r["converged"]
+    assert np.array_equal(st.numpy(), before)

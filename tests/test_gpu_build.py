@@ -1,0 +1,83 @@
+"""GPU parity: Pauli -> CSR compilation and the pool layout (CUDA vs oracle)."""
+
+import numpy as np
+import pytest
+
+import paper_2606_29692_gb300 as tq
+import synth
+from gpu_util import dev_to_numpy, ham_csr_numpy, oracle_split
+from oracle import pauli
+
+pytestmark = pytest.mark.gpu
+
+CFG = {"c0": synth.config0, "c1": synth.config1, "c2": synth.config2,
+       "n1": lambda: (synth.integrals(1, 5), 2), "n3": lambda: (synth.integrals(3, 6), 2)}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return tq.Context(0)
+
+
+_ORACLE = {}
+
+
+def oracle_h(cfg, mp):
+    key = (cfg, mp)
+    if key not in _ORACLE:
+        ints, ne = CFG[cfg]()
+        ps = pauli.qubit_hamiltonian(ints.h, ints.g, ints.e_const, mp)
+        _ORACLE[key] = (ints, ne, ps, pauli.pauli_to_csr(ps))
+    return _ORACLE[key]
+
+
+@pytest.mark.parametrize("prec", [tq.TQ_C128, tq.TQ_C64])
+@pytest.mark.parametrize("cfg,mp", [("n1", 0), ("n3", 1), ("c0", 0), ("c0", 1), ("c1", 0), ("c1", 1),
+                                    ("c2", 1), ("c2", 0)])
+def test_hamiltonian_csr_matches_oracle(ctx, cfg, mp, prec):
+    ints, ne, ps, H = oracle_h(cfg, mp)
+    ham = tq.build_hamiltonian(ctx, ints.h, ints.g, ints.e_const, mp, prec)
+    rowptr, col, val, diag = ham_csr_numpy(ham)
+    orp, ocol, oval, odiag = oracle_split(H)
+    assert ham.n_pauli == ps.n_terms
+    assert ham.n_ambiguous == 0
+    assert np.array_equal(rowptr, orp), "rowptr differs"
+    assert np.array_equal(col, ocol), "column indices differ"
+    if prec == tq.TQ_C128:
+        # same terms summed in the same (x, z) order: identical values
+        assert np.array_equal(val, oval)
+    else:
+        assert np.array_equal(val, oval.astype(np.float32))
+    scale = np.abs(ps.c).sum()
+    assert np.abs(diag - odiag).max() <= 1e-15 * scale
+
+
+@pytest.mark.parametrize("prec", [tq.TQ_C128, tq.TQ_C64])
+@pytest.mark.parametrize("n,ne,mp", [(2, 2, 0), (4, 4, 0), (4, 4, 1), (6, 8, 1), (7, 6, 1)])
+def test_pool_csr_matches_oracle(ctx, n, ne, mp, prec):
+    exc, pps = pauli.pool_pauli(n, ne, mp)
+    pool = tq.build_pool(ctx, n, ne, mp)
+    assert pool.M == len(exc)
+    assert [tuple(int(v) for v in row[: len(e)]) for row, e in zip(pool.idx4, exc)] == exc
+    ks = range(pool.M) if pool.M <= 92 else list(range(0, pool.M, 17)) + [pool.M - 1]
+    D = 1 << (2 * n)
+    for k in ks:
+        rp, cl, vl, nnz = tq.pool_csr(ctx, pool, k, prec)
+        A = pauli.pauli_to_csr(pps[k])
+        assert nnz == A.nnz
+        assert np.array_equal(dev_to_numpy(rp, D + 1, "<i4"), A.indptr)
+        assert np.array_equal(dev_to_numpy(cl, nnz, "<i4"), A.indices)
+        v = dev_to_numpy(vl, nnz, "<f8" if prec == tq.TQ_C128 else "<f4")
+        assert np.array_equal(v.astype(np.float64), A.data.real)
+
+
+def test_build_rejects_bad_arguments(ctx):
+    ints, _ = synth.config0()
+    with pytest.raises(tq.TQError):
+        tq.build_hamiltonian(ctx, ints.h, ints.g, 0.0, 3, tq.TQ_C128)
+    with pytest.raises(tq.TQError):
+        tq.build_hamiltonian(ctx, ints.h, ints.g, 0.0, 0, 7)
+    with pytest.raises(tq.TQError):
+        tq.build_pool(ctx, 1, 1, 0)        # empty pool
+    with pytest.raises(tq.TQError):
+        tq.build_hamiltonian(ctx, ints.h, ints.g, float("inf"), 0, tq.TQ_C128)
