@@ -490,7 +490,8 @@ extern "C" int tq_build_pool(tq_ctx* c, int n_spatial, int n_electrons, int mapp
                 p->terms[8 * k + j] = t[j];
             }
             SignForm f = factor_generator(t);
-            if (f.ok) {
+            if (!f.ok) throw Error(TQ_ENUMERIC, "generator sign function does not factor");
+            {
                 fok[k] = 1;
                 fm[k] = f.m;
                 fz0[k] = (uint32_t)f.z0;
@@ -680,10 +681,10 @@ extern "C" int tq_evolve_taylor5(tq_ctx* c, const tq_pool* p, int k, double thet
     TQ_REQUIRE(psi->nq == p->nq, "state and pool qubit counts differ");
     set_device(c);
     cudaStream_t s = as_stream(stream);
-    const int tiles = taylor5_pair_tiles(p->nq);
+    const int tiles = taylor5_pair_parts(p->nq, psi->prec);
     double* part = static_cast<double*>(scratch(c, S_PART, (size_t)tiles * sizeof(double)));
     launch(c, "taylor5_pair", s, [&] { return launch_taylor5_pair(p->view, 1, psi->prec, psi->data, nullptr, nullptr, k, theta, part,
-                                        tiles, taylor5_pair_grid(c->sm_count), s); });
+                                        c->sm_count, s); });
     if (renormalize) {
         launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, 1, tiles, nullptr, &c->step->norm2, s); });
         launch(c, "scale", s, [&] { return launch_scale(psi->data, psi->prec, psi->D, &c->step->norm2, s); });
@@ -721,7 +722,8 @@ size_t partials_needed(long long D, int M, int nq, int sms) {
         n = std::max(n, (size_t)M * nch);
     }
     n = std::max(n, (size_t)512 * 5);
-    n = std::max(n, (size_t)taylor5_pair_tiles(nq));
+    n = std::max(n, (size_t)taylor5_pair_parts(nq, TQ_C64));
+    n = std::max(n, (size_t)taylor5_pair_parts(nq, TQ_C128));
     return n + 8;
 }
 
@@ -819,9 +821,9 @@ extern "C" int tq_adapt_step(tq_ctx* c, const tq_ham* h, const tq_pool* p, tq_st
         launch(c, "line_dots", s, [&] { return launch_line_dots(w0, w1, w2, u1, u2, D, part, c->tickets + 2, c->step, s); });
     }
     launch(c, "line_search", s, [&] { return launch_line_search(c->step, theta, s); });
-    const int tiles = taylor5_pair_tiles(p->nq);
-    launch(c, "taylor5_pair_gated", s, [&] { return launch_taylor5_pair_gated(p->view, psi->prec, psi->data, c->step, part, tiles,
-                                              taylor5_pair_grid(c->sm_count), s); });
+    const int tiles = taylor5_pair_parts(p->nq, psi->prec);
+    launch(c, "taylor5_pair_gated", s, [&] { return launch_taylor5_pair_gated(p->view, psi->prec, psi->data, c->step, part,
+                                              c->sm_count, s); });
     launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, 1, tiles, nullptr, &c->step->norm2, s); });
     launch(c, "scale_gated", s, [&] { return launch_scale_gated(psi->data, psi->prec, D, &c->step->norm2, c->step, s); });
     DevStep hs;
@@ -849,10 +851,10 @@ extern "C" int tq_evolve_taylor5_batch(tq_ctx* c, const tq_pool* p, int n_states
     if (n_states == 0) return TQ_OK;
     set_device(c);
     cudaStream_t s = as_stream(stream);
-    const int tiles = taylor5_pair_tiles(p->nq);
+    const int tiles = taylor5_pair_parts(p->nq, prec);
     double* part = static_cast<double*>(scratch(c, S_PART, (size_t)n_states * tiles * sizeof(double)));
-    launch(c, "taylor5_pair", s, [&] { return launch_taylor5_pair(p->view, n_states, prec, psi, k, theta, 0, 0.0, part, tiles,
-                                        taylor5_pair_grid(c->sm_count), s); });
+    launch(c, "taylor5_pair", s, [&] { return launch_taylor5_pair(p->view, n_states, prec, psi, k, theta, 0, 0.0, part,
+                                        c->sm_count, s); });
     if (norm2) launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, n_states, tiles, norm2, nullptr, s); });
     API_END
 }
@@ -873,11 +875,10 @@ extern "C" int tq_evolve_taylor5_batch_host(tq_ctx* c, const tq_pool* p, int n_s
     // chunk of about 64 MiB of states per stream
     int chunk = (int)std::max<long long>(1, (64ll << 20) / (long long)sb);
     chunk = std::min(chunk, n_states);
-    const int tiles = taylor5_pair_tiles(p->nq);
+    const int tiles = taylor5_pair_parts(p->nq, prec);
     const size_t per_stream = (size_t)chunk * sb + (size_t)chunk * (sizeof(int) + 2 * sizeof(double)) +
                               (size_t)chunk * tiles * sizeof(double) + 256;
     unsigned char* stage = static_cast<unsigned char*>(scratch(c, S_STAGE, 3 * per_stream));
-    const int grid = taylor5_pair_grid(c->sm_count);
     for (int c0 = 0, it = 0; c0 < n_states; c0 += chunk, ++it) {
         const int n = std::min(chunk, n_states - c0);
         cudaStream_t s = c->aux[it % 3];
@@ -892,7 +893,7 @@ extern "C" int tq_evolve_taylor5_batch_host(tq_ctx* c, const tq_pool* p, int n_s
                                 cudaMemcpyHostToDevice, s));
         TQ_CUDA(cudaMemcpyAsync(dk, k_host + c0, (size_t)n * sizeof(int), cudaMemcpyHostToDevice, s));
         TQ_CUDA(cudaMemcpyAsync(dth, theta_host + c0, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s));
-        launch(c, "taylor5_pair", s, [&] { return launch_taylor5_pair(p->view, n, prec, dpsi, dk, dth, 0, 0.0, part, tiles, grid, s); });
+        launch(c, "taylor5_pair", s, [&] { return launch_taylor5_pair(p->view, n, prec, dpsi, dk, dth, 0, 0.0, part, c->sm_count, s); });
         TQ_CUDA(cudaMemcpyAsync(static_cast<unsigned char*>(psi_host) + (size_t)c0 * sb, dpsi, (size_t)n * sb,
                                 cudaMemcpyDeviceToHost, s));
         if (norm2_host) {

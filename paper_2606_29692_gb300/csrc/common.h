@@ -118,12 +118,12 @@ int launch_csr_fill(const HamView& h, double tol, int max_row, int* col, void* v
                     int prec, int sms, cudaStream_t s);
 
 // Taylor-5, matrix-free pair path: states back to back, op k[b] / theta[b]
-// (device arrays, or the immediates when the pointers are null).
+// (device arrays, or the immediates when the pointers are null).  Writes
+// taylor5_pair_parts(nq, prec) float64 norm partials per state.
+int taylor5_pair_parts(int nq, int prec);
 int launch_taylor5_pair(const PoolView& p, int n_states, int prec, void* psi,
                         const int* k, const double* theta, int k_imm, double theta_imm,
-                        double* partials, int tiles_per_state, int grid, cudaStream_t s);
-int taylor5_pair_tiles(int nq);
-int taylor5_pair_grid(int sms);
+                        double* partials, int sms, cudaStream_t s);
 int launch_norm_reduce(const double* partials, int n_states, int tiles_per_state,
                        double* norm2_out, double* step_norm2, cudaStream_t s);
 int launch_scale(void* psi, int prec, long long D, const double* norm2, cudaStream_t s);
@@ -157,7 +157,7 @@ int launch_line_search(DevStep* step, double theta_given, cudaStream_t s);
 
 // gated variants (skip when step->converged) and layout helpers
 int launch_taylor5_pair_gated(const PoolView& p, int prec, void* psi, const DevStep* step,
-                              double* partials, int tiles, int grid, cudaStream_t s);
+                              double* partials, int sms, cudaStream_t s);
 int launch_scale_gated(void* psi, int prec, long long D, const double* norm2,
                        const DevStep* gate, cudaStream_t s);
 int launch_spmv_c128_gated(const HamView& h, const double2* x, double2* y,

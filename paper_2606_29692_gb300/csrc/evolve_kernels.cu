@@ -26,6 +26,8 @@
 
 #include <cooperative_groups.h>
 
+#include <algorithm>
+
 namespace cg = cooperative_groups;
 
 namespace tq {
@@ -33,8 +35,6 @@ namespace tq {
 namespace {
 
 constexpr int PAIR_BS = 256;
-constexpr int PAIR_UPT = 2;
-constexpr int TILE_UNITS = PAIR_BS * PAIR_UPT;   // 4 amplitudes per unit
 
 __device__ __forceinline__ void load2(const float2* p, uint32_t i, float2& a, float2& b) {
     const float4 v = *reinterpret_cast<const float4*>(p + i);
@@ -93,80 +93,164 @@ __device__ __forceinline__ void taylor_coefs(double theta, T (&cf)[6]) {
     }
 }
 
+// One pool generator as staged in shared memory: X-mask, the factored sign
+// form (A[r][r^x] = c0 (-1)^{parity(col & z0)} if parity(col & d_i) == t_i
+// for all i, else 0, with col = r ^ x), and the parities of
+// {0, 1, x, x ^ 1} against (d0, d1, d2, z0) so that one set of popcounts at
+// r0 gives the values of all four rows of a unit.
 template <typename T>
+struct OpRec {
+    uint32_t x, z0, d0, d1, d2;
+    int t;        // target parities (bits 0..2)
+    int dcode;    // 4 x 4-bit parity codes of delta in {0, 1, x, x^1}
+    T c0;
+};
+
+template <typename T>
+__device__ __forceinline__ OpRec<T> make_rec(const PoolView& p, int k) {
+    OpRec<T> o;
+    o.x = p.x[k];
+    o.z0 = p.fz0[k];
+    o.d0 = p.fd[3 * k];
+    o.d1 = p.fd[3 * k + 1];
+    o.d2 = p.fd[3 * k + 2];
+    o.t = p.ft[k];
+    o.c0 = sizeof(T) == 4 ? (T)p.fc0f[k] : (T)p.fc0d[k];
+    const uint32_t dl[4] = {0u, 1u, o.x, o.x ^ 1u};
+    int code = 0;
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t d = dl[j];
+        const int c = parity32(d & o.d0) | (parity32(d & o.d1) << 1) | (parity32(d & o.d2) << 2) |
+                      (parity32(d & o.z0) << 3);
+        code |= c << (4 * j);
+    }
+    o.dcode = code;
+    return o;
+}
+
+// Value A[row][col] given the parity code of col.
+template <typename T>
+__device__ __forceinline__ T rec_value(const OpRec<T>& o, int code) {
+    return (code & 7) != o.t ? T(0) : ((code & 8) ? -o.c0 : o.c0);
+}
+
+template <typename T>
+__device__ __forceinline__ int base_code(const OpRec<T>& o, uint32_t r) {
+    return parity32(r & o.d0) | (parity32(r & o.d1) << 1) | (parity32(r & o.d2) << 2) |
+           (parity32(r & o.z0) << 3);
+}
+
+template <typename T, int UPT>
 __global__ void __launch_bounds__(PAIR_BS)
 k_taylor5_pair(PoolView p, int n_states, typename C2<T>::type* psi, const int* kk,
                const double* th, int k_imm, double th_imm, double* partials,
                int tiles_per_state, const DevStep* gate) {
     using V = typename C2<T>::type;
-    __shared__ double sh[PAIR_BS / 32];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    OpRec<T>* ops = reinterpret_cast<OpRec<T>*>(smem_raw);
     if (gate && gate->converged) return;
-    const int nq = p.nq;
-    const long long D = 1ll << nq;
+    // the vectorised pool layout, staged once per CTA
+    for (int i = threadIdx.x; i < p.M; i += blockDim.x) ops[i] = make_rec<T>(p, i);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = PAIR_BS / 32;
+    constexpr int TU = PAIR_BS * UPT;           // units per tile
+    const long long D = 1ll << p.nq;
     const uint32_t units = (uint32_t)(D >> 2);
     const long long total = (long long)n_states * tiles_per_state;
-    for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
-        const int b = (int)(tile / tiles_per_state);
+    long long tile = blockIdx.x;
+    int b = (int)(tile / tiles_per_state);
+    int k = tile < total ? (kk ? kk[b] : k_imm) : 0;
+    double theta = tile < total ? (th ? th[b] : th_imm) : 0.0;
+    for (; tile < total; ) {
         const int tl = (int)(tile - (long long)b * tiles_per_state);
-        const int k = kk ? kk[b] : k_imm;
-        const double theta = th ? th[b] : th_imm;
+        // prefetch the next tile's op index and angle
+        const long long ntile = tile + gridDim.x;
+        const int nb = (int)(ntile / tiles_per_state);
+        int nk = 0;
+        double nth = 0.0;
+        if (ntile < total) {
+            nk = kk ? kk[nb] : k_imm;
+            nth = th ? th[nb] : th_imm;
+        }
+        double part = 0.0;
         if (k < 0 || k >= p.M) {
             // invalid op index from device memory: leave the state untouched
             // and poison its norm so the caller sees it
-            if (threadIdx.x == 0) partials[tile] = __longlong_as_double(0x7ff8000000000000ll);
-            continue;
-        }
-        OpSign<T> op;
-        op.load(p, k);
-        const uint32_t x = op.x;
-        const int hb = 31 - __clz(x);
-        T cf[6];
-        taylor_coefs<T>(theta, cf);
-        V* base = psi + (long long)b * D;
-        T part = T(0);
+            part = __longlong_as_double(0x7ff8000000000000ll);
+        } else {
+            const OpRec<T> op = ops[k];
+            const uint32_t x = op.x;
+            const int hb = 31 - __clz(x);
+            T cf[6];
+            taylor_coefs<T>(theta, cf);
+            V* base = psi + (long long)b * D;
+            V e0[UPT], e1[UPT], f0[UPT], f1[UPT];
+            uint32_t r0s[UPT];
+            bool ok[UPT];
 #pragma unroll
-        for (int j = 0; j < PAIR_UPT; ++j) {
-            const uint32_t u = (uint32_t)tl * TILE_UNITS + j * PAIR_BS + threadIdx.x;
-            if (u >= units) continue;
-            V e0, e1, f0, f1;
-            if (hb > 0) {
-                // reps r0, r0+1 (one aligned vector), partners r0^x, r0^x^1
-                const uint32_t r0 = insert_zero(2u * u, hb);
-                const uint32_t q0 = r0 ^ x;
-                const uint32_t qa = q0 & ~1u;
-                load2(base, r0, e0, e1);
-                load2(base, qa, f0, f1);
-                // partner of r0 is q0, partner of r0+1 is q0^1
-                V a0 = e0, a1 = e1;
-                V b0 = (q0 & 1u) ? f1 : f0;   // psi[q0]
-                V b1 = (q0 & 1u) ? f0 : f1;   // psi[q0 ^ 1]
-                const T s_r0 = op.value(q0), s_q0 = op.value(r0);
-                const T s_r1 = op.value(q0 ^ 1u), s_q1 = op.value(r0 + 1u);
-                chain_pair(s_r0, s_q0, cf, a0, b0);
-                chain_pair(s_r1, s_q1, cf, a1, b1);
-                part += a0.x * a0.x + a0.y * a0.y + a1.x * a1.x + a1.y * a1.y;
-                part += b0.x * b0.x + b0.y * b0.y + b1.x * b1.x + b1.y * b1.y;
-                store2(base, r0, a0, a1);
-                if (q0 & 1u) store2(base, qa, b1, b0);
-                else store2(base, qa, b0, b1);
-            } else {
-                // x == 1: pairs (4u, 4u+1) and (4u+2, 4u+3)
-                const uint32_t r0 = 4u * u, r1 = r0 + 2u;
-                load2(base, r0, e0, f0);
-                load2(base, r1, e1, f1);
-                const T s_r0 = op.value(r0 + 1u), s_q0 = op.value(r0);
-                const T s_r1 = op.value(r1 + 1u), s_q1 = op.value(r1);
-                chain_pair(s_r0, s_q0, cf, e0, f0);
-                chain_pair(s_r1, s_q1, cf, e1, f1);
-                part += e0.x * e0.x + e0.y * e0.y + f0.x * f0.x + f0.y * f0.y;
-                part += e1.x * e1.x + e1.y * e1.y + f1.x * f1.x + f1.y * f1.y;
-                store2(base, r0, e0, f0);
-                store2(base, r1, e1, f1);
+            for (int j = 0; j < UPT; ++j) {
+                const uint32_t u = (uint32_t)tl * TU + j * PAIR_BS + threadIdx.x;
+                ok[j] = u < units;
+                if (!ok[j]) continue;
+                if (hb > 0) {
+                    const uint32_t r0 = insert_zero(2u * u, hb);
+                    r0s[j] = r0;
+                    load2(base, r0, e0[j], e1[j]);
+                    load2(base, (r0 ^ x) & ~1u, f0[j], f1[j]);
+                } else {
+                    const uint32_t r0 = 4u * u;
+                    r0s[j] = r0;
+                    load2(base, r0, e0[j], f0[j]);
+                    load2(base, r0 + 2u, e1[j], f1[j]);
+                }
             }
+            T tpart = T(0);
+#pragma unroll
+            for (int j = 0; j < UPT; ++j) {
+                if (!ok[j]) continue;
+                const uint32_t r0 = r0s[j];
+                if (hb > 0) {
+                    // rows r0, r0+1 and partners q0 = r0^x, q0^1; their columns
+                    // are r0 ^ {x, x^1, 0, 1}
+                    const uint32_t q0 = r0 ^ x;
+                    const int bc = base_code(op, r0);
+                    const T s_r0 = rec_value(op, bc ^ ((op.dcode >> 8) & 15));    // col q0
+                    const T s_r1 = rec_value(op, bc ^ ((op.dcode >> 12) & 15));   // col q0^1
+                    const T s_q0 = rec_value(op, bc ^ (op.dcode & 15));           // col r0
+                    const T s_q1 = rec_value(op, bc ^ ((op.dcode >> 4) & 15));    // col r0+1
+                    V a0 = e0[j], a1 = e1[j];
+                    V b0 = (q0 & 1u) ? f1[j] : f0[j];   // psi[q0]
+                    V b1 = (q0 & 1u) ? f0[j] : f1[j];   // psi[q0 ^ 1]
+                    chain_pair(s_r0, s_q0, cf, a0, b0);
+                    chain_pair(s_r1, s_q1, cf, a1, b1);
+                    tpart += a0.x * a0.x + a0.y * a0.y + a1.x * a1.x + a1.y * a1.y;
+                    tpart += b0.x * b0.x + b0.y * b0.y + b1.x * b1.x + b1.y * b1.y;
+                    store2(base, r0, a0, a1);
+                    if (q0 & 1u) store2(base, q0 & ~1u, b1, b0);
+                    else store2(base, q0 & ~1u, b0, b1);
+                } else {
+                    // x == 1: pairs (r0, r0+1) and (r0+2, r0+3)
+                    const int b0c = base_code(op, r0), b2c = base_code(op, r0 + 2u);
+                    const T s_r0 = rec_value(op, b0c ^ ((op.dcode >> 4) & 15));  // col r0+1
+                    const T s_q0 = rec_value(op, b0c);                           // col r0
+                    const T s_r1 = rec_value(op, b2c ^ ((op.dcode >> 4) & 15));  // col r0+3
+                    const T s_q1 = rec_value(op, b2c);                           // col r0+2
+                    chain_pair(s_r0, s_q0, cf, e0[j], f0[j]);
+                    chain_pair(s_r1, s_q1, cf, e1[j], f1[j]);
+                    tpart += e0[j].x * e0[j].x + e0[j].y * e0[j].y + f0[j].x * f0[j].x + f0[j].y * f0[j].y;
+                    tpart += e1[j].x * e1[j].x + e1[j].y * e1[j].y + f1[j].x * f1[j].x + f1[j].y * f1[j].y;
+                    store2(base, r0, e0[j], f0[j]);
+                    store2(base, r0 + 2u, e1[j], f1[j]);
+                }
+            }
+            part = warp_sum((double)tpart);
         }
-        double v[1] = {(double)part};
-        block_sum<1>(v, sh);
-        if (threadIdx.x == 0) partials[tile] = v[0];
+        if (lane == 0) partials[tile * NW + warp] = part;
+        tile = ntile;
+        b = nb;
+        k = nk;
+        theta = nth;
     }
 }
 
@@ -434,40 +518,70 @@ int run_unfused(int nq, const int* rowptr, const int* col, const VT* val, double
 
 }  // namespace
 
-int taylor5_pair_tiles(int nq) {
-    const long long units = (1ll << nq) >> 2;
-    return (int)((units + TILE_UNITS - 1) / TILE_UNITS);
+namespace {
+
+// Resident CTAs per SM for the pool table size (cached per 4 KB bucket).
+template <typename T, int UPT>
+int pair_grid(int M, int sms) {
+    static int per_sm[32] = {0};
+    const size_t smem = (size_t)M * sizeof(OpRec<T>);
+    const int bucket = (int)std::min<size_t>(31, smem / 4096);
+    if (per_sm[bucket] == 0) {
+        cudaFuncSetAttribute(k_taylor5_pair<T, UPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_taylor5_pair<T, UPT>, PAIR_BS,
+                                                      (size_t)(bucket + 1) * 4096);
+        per_sm[bucket] = n < 1 ? 1 : n;
+    }
+    return per_sm[bucket] * sms;
 }
 
-int taylor5_pair_grid(int sms) { return sms * 8; }
+template <typename T, int UPT>
+int launch_pair(const PoolView& p, int n_states, void* psi, const int* k, const double* theta,
+                int k_imm, double theta_imm, double* partials, const DevStep* gate, int sms,
+                cudaStream_t s) {
+    using V = typename C2<T>::type;
+    const long long units = (1ll << p.nq) >> 2;
+    const int tiles = (int)((units + PAIR_BS * UPT - 1) / (PAIR_BS * UPT));
+    const long long total = (long long)n_states * tiles;
+    long long grid = pair_grid<T, UPT>(p.M, sms);
+    if (grid > total) grid = total;
+    if (grid < 1) grid = 1;
+    const size_t smem = (size_t)p.M * sizeof(OpRec<T>);
+    k_taylor5_pair<T, UPT><<<(int)grid, PAIR_BS, smem, s>>>(p, n_states, static_cast<V*>(psi), k, theta,
+                                                            k_imm, theta_imm, partials, tiles, gate);
+    return 1;
+}
+
+constexpr int PAIR_UPT_C64 = 2;
+constexpr int PAIR_UPT_C128 = 2;
+
+}  // namespace
+
+int taylor5_pair_parts(int nq, int prec) {
+    const int upt = prec == TQ_C128 ? PAIR_UPT_C128 : PAIR_UPT_C64;
+    const long long units = (1ll << nq) >> 2;
+    const int tiles = (int)((units + PAIR_BS * upt - 1) / (PAIR_BS * upt));
+    return tiles * (PAIR_BS / 32);
+}
 
 int launch_taylor5_pair(const PoolView& p, int n_states, int prec, void* psi, const int* k,
-                        const double* theta, int k_imm, double theta_imm, double* partials,
-                        int tiles_per_state, int grid, cudaStream_t s) {
-    const long long total = (long long)n_states * tiles_per_state;
-    if (grid > total) grid = (int)total;
-    if (grid < 1) grid = 1;
+                        const double* theta, int k_imm, double theta_imm, double* partials, int sms,
+                        cudaStream_t s) {
     if (prec == TQ_C128)
-        k_taylor5_pair<double><<<grid, PAIR_BS, 0, s>>>(p, n_states, static_cast<double2*>(psi), k,
-                                                        theta, k_imm, theta_imm, partials,
-                                                        tiles_per_state, nullptr);
-    else
-        k_taylor5_pair<float><<<grid, PAIR_BS, 0, s>>>(p, n_states, static_cast<float2*>(psi), k,
-                                                       theta, k_imm, theta_imm, partials,
-                                                       tiles_per_state, nullptr);
-    return 1;
+        return launch_pair<double, PAIR_UPT_C128>(p, n_states, psi, k, theta, k_imm, theta_imm, partials,
+                                                  nullptr, sms, s);
+    return launch_pair<float, PAIR_UPT_C64>(p, n_states, psi, k, theta, k_imm, theta_imm, partials,
+                                            nullptr, sms, s);
 }
 
 int launch_taylor5_pair_gated(const PoolView& p, int prec, void* psi, const DevStep* step,
-                              double* partials, int tiles, int grid, cudaStream_t s) {
-    if (grid > tiles) grid = tiles;
+                              double* partials, int sms, cudaStream_t s) {
     if (prec == TQ_C128)
-        k_taylor5_pair<double><<<grid, PAIR_BS, 0, s>>>(p, 1, static_cast<double2*>(psi), &step->selected,
-                                                        &step->theta, 0, 0.0, partials, tiles, step);
-    else
-        k_taylor5_pair<float><<<grid, PAIR_BS, 0, s>>>(p, 1, static_cast<float2*>(psi), &step->selected,
-                                                       &step->theta, 0, 0.0, partials, tiles, step);
-    return 1;
+        return launch_pair<double, PAIR_UPT_C128>(p, 1, psi, &step->selected, &step->theta, 0, 0.0, partials,
+                                                  step, sms, s);
+    return launch_pair<float, PAIR_UPT_C64>(p, 1, psi, &step->selected, &step->theta, 0, 0.0, partials,
+                                            step, sms, s);
 }
 
 int launch_norm_reduce(const double* partials, int n_states, int tiles_per_state,
