@@ -93,6 +93,20 @@ int tq_ctx_launch_count(const tq_ctx* ctx, long long* launches);
 int tq_ctx_trace(tq_ctx* ctx, int enable);
 int tq_ctx_trace_report(tq_ctx* ctx, char* buf, size_t buf_size);
 
+/* Launch schedule of the Taylor-5 pair kernel per precision: pair units
+ * (4 amplitudes each) per thread per tile, one of 1, 2, 4, 8.  More units
+ * per thread put more bytes in flight per thread; fewer raise occupancy.
+ * Defaults: 2 (TQ_C128), 4 (TQ_C64). */
+int tq_ctx_set_pair_schedule(tq_ctx* ctx, int prec, int units_per_thread);
+int tq_ctx_get_pair_schedule(const tq_ctx* ctx, int prec, int* units_per_thread);
+/* Autotuner: times each schedule on n_states device scratch states of the
+ * pool's qubit count (one warm launch, then the mean of five, CUDA events
+ * on the legacy stream), sets the fastest on the context, and returns it
+ * with its time per launch.  Synchronises the device; uses context scratch
+ * (n_states * 2^N amplitudes). */
+int tq_autotune_pair(tq_ctx* ctx, const tq_pool* pool, int prec, int n_states,
+                     int* best_units_per_thread, double* best_ms);
+
 /* ------------------------------------------------- host-side construction */
 
 /* Qubit Hamiltonian as a Pauli sum (Eq. (3)) from the fermionic Hamiltonian

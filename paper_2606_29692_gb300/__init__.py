@@ -20,7 +20,7 @@ __all__ = [
     "pauli_hamiltonian", "pool_excitations", "pauli_pool", "hf_index", "build_hamiltonian",
     "build_pool", "evolve_taylor5", "evolve_taylor5_csr", "energy", "energy_matrix_free",
     "pool_gradients", "adapt_step", "evolve_taylor5_batch", "evolve_taylor5_batch_host",
-    "state_set_hf", "pool_csr", "ham_csr", "lib",
+    "state_set_hf", "pool_csr", "ham_csr", "lib", "autotune_pair",
 ]
 
 
@@ -105,6 +105,14 @@ class Context:
         n = C.c_longlong()
         call("tq_ctx_launch_count", self.handle, C.byref(n))
         return n.value
+
+    def set_pair_schedule(self, prec, units_per_thread):
+        call("tq_ctx_set_pair_schedule", self.handle, prec, int(units_per_thread))
+
+    def pair_schedule(self, prec):
+        u = C.c_int()
+        call("tq_ctx_get_pair_schedule", self.handle, prec, C.byref(u))
+        return u.value
 
     def trace(self, enable=True):
         """Bracket every kernel launch with CUDA events on its stream."""
@@ -281,6 +289,13 @@ def adapt_step(ctx, ham, pool, state, eps, theta=float("nan"), stream=None):
          float(theta), C.byref(r), _stream(stream))
     return {"energy": r.energy, "max_grad": r.max_grad, "theta": r.theta,
             "selected": r.selected, "converged": bool(r.converged)}
+
+
+def autotune_pair(ctx, pool, prec=TQ_C64, n_states=1024):
+    """Time every pair-kernel schedule; set and return (units_per_thread, ms)."""
+    u, ms = C.c_int(), C.c_double()
+    call("tq_autotune_pair", ctx.handle, pool.handle, prec, int(n_states), C.byref(u), C.byref(ms))
+    return u.value, ms.value
 
 
 def evolve_taylor5_batch(ctx, pool, psi, k, theta, norm2=None, prec=TQ_C64, stream=None):

@@ -84,7 +84,9 @@ void check_launch(tq_ctx* c, int n) {
 template <typename F>
 void launch(tq_ctx* c, const char* name, cudaStream_t s, F&& f) {
     Traced t(c, name, s);
-    check_launch(c, f());
+    const int n = f();
+    if (n < 0) throw Error(TQ_EINVAL, std::string(name) + ": problem too large for one launch");
+    check_launch(c, n);
 }
 
 void* dev_alloc(size_t bytes) {
@@ -241,6 +243,78 @@ extern "C" int tq_ctx_launch_count(const tq_ctx* c, long long* launches) {
     API_BEGIN
     TQ_REQUIRE(c && launches, "null argument");
     *launches = c->launches;
+    API_END
+}
+
+extern "C" int tq_ctx_set_pair_schedule(tq_ctx* c, int prec, int units_per_thread) {
+    API_BEGIN
+    TQ_REQUIRE(c != nullptr, "ctx is null");
+    check_prec(prec);
+    TQ_REQUIRE(pair_upt_valid(units_per_thread), "units_per_thread must be 1, 2, 4 or 8");
+    c->pair_upt[prec] = units_per_thread;
+    API_END
+}
+
+extern "C" int tq_ctx_get_pair_schedule(const tq_ctx* c, int prec, int* units_per_thread) {
+    API_BEGIN
+    TQ_REQUIRE(c && units_per_thread, "null argument");
+    check_prec(prec);
+    *units_per_thread = c->pair_upt[prec];
+    API_END
+}
+
+extern "C" int tq_autotune_pair(tq_ctx* c, const tq_pool* p, int prec, int n_states, int* best_upt,
+                                double* best_ms) {
+    API_BEGIN
+    TQ_REQUIRE(c && p, "null argument");
+    check_prec(prec);
+    TQ_REQUIRE(n_states >= 1, "n_states must be >= 1");
+    set_device(c);
+    const long long D = 1ll << p->nq;
+    const size_t sb = (size_t)D * elem_bytes(prec);
+    const size_t parts = (size_t)n_states * taylor5_pair_parts(p->nq, 1);
+    unsigned char* buf = static_cast<unsigned char*>(
+        scratch(c, S_STAGE, (size_t)n_states * sb + (size_t)n_states * (sizeof(int) + sizeof(double)) +
+                                parts * sizeof(double) + 256));
+    void* psi = buf;
+    int* dk = reinterpret_cast<int*>(buf + (size_t)n_states * sb);
+    double* dth = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(dk + n_states) + 15) & ~(uintptr_t)15);
+    double* part = dth + n_states;
+    std::vector<int> hk(n_states);
+    std::vector<double> hth(n_states);
+    for (int b = 0; b < n_states; ++b) {
+        hk[b] = (int)((b * 2654435761u) % (unsigned)p->M);
+        hth[b] = 0.05 + 1e-4 * (b % 97);
+    }
+    TQ_CUDA(cudaMemset(psi, 0, (size_t)n_states * sb));
+    TQ_CUDA(cudaMemcpy(dk, hk.data(), n_states * sizeof(int), cudaMemcpyHostToDevice));
+    TQ_CUDA(cudaMemcpy(dth, hth.data(), n_states * sizeof(double), cudaMemcpyHostToDevice));
+    cudaEvent_t e0, e1;
+    TQ_CUDA(cudaEventCreate(&e0));
+    TQ_CUDA(cudaEventCreate(&e1));
+    int best = c->pair_upt[prec];
+    float best_t = 1e30f;
+    const int cands[4] = {1, 2, 4, 8};
+    for (int u : cands) {
+        launch(c, "autotune_pair", 0, [&] { return launch_taylor5_pair(p->view, n_states, prec, u, psi, dk, dth, 0, 0.0, part, c->sm_count, 0); });
+        TQ_CUDA(cudaEventRecord(e0, 0));
+        for (int r = 0; r < 5; ++r)
+            launch(c, "autotune_pair", 0, [&] { return launch_taylor5_pair(p->view, n_states, prec, u, psi, dk, dth, 0, 0.0, part, c->sm_count, 0); });
+        TQ_CUDA(cudaEventRecord(e1, 0));
+        TQ_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        TQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        ms /= 5.f;
+        if (ms < best_t) {
+            best_t = ms;
+            best = u;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->pair_upt[prec] = best;
+    if (best_upt) *best_upt = best;
+    if (best_ms) *best_ms = best_t;
     API_END
 }
 
@@ -681,12 +755,13 @@ extern "C" int tq_evolve_taylor5(tq_ctx* c, const tq_pool* p, int k, double thet
     TQ_REQUIRE(psi->nq == p->nq, "state and pool qubit counts differ");
     set_device(c);
     cudaStream_t s = as_stream(stream);
-    const int tiles = taylor5_pair_parts(p->nq, psi->prec);
+    const int upt = c->pair_upt[psi->prec];
+    const int tiles = taylor5_pair_parts(p->nq, upt);
     double* part = static_cast<double*>(scratch(c, S_PART, (size_t)tiles * sizeof(double)));
-    launch(c, "taylor5_pair", s, [&] { return launch_taylor5_pair(p->view, 1, psi->prec, psi->data, nullptr, nullptr, k, theta, part,
+    launch(c, "taylor5_pair", s, [&] { return launch_taylor5_pair(p->view, 1, psi->prec, upt, psi->data, nullptr, nullptr, k, theta, part,
                                         c->sm_count, s); });
     if (renormalize) {
-        launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, 1, tiles, nullptr, &c->step->norm2, s); });
+        launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, psi->prec, 1, tiles, nullptr, &c->step->norm2, s); });
         launch(c, "scale", s, [&] { return launch_scale(psi->data, psi->prec, psi->D, &c->step->norm2, s); });
     }
     API_END
@@ -722,8 +797,7 @@ size_t partials_needed(long long D, int M, int nq, int sms) {
         n = std::max(n, (size_t)M * nch);
     }
     n = std::max(n, (size_t)512 * 5);
-    n = std::max(n, (size_t)taylor5_pair_parts(nq, TQ_C64));
-    n = std::max(n, (size_t)taylor5_pair_parts(nq, TQ_C128));
+    n = std::max(n, (size_t)taylor5_pair_parts(nq, 1));
     return n + 8;
 }
 
@@ -821,10 +895,11 @@ extern "C" int tq_adapt_step(tq_ctx* c, const tq_ham* h, const tq_pool* p, tq_st
         launch(c, "line_dots", s, [&] { return launch_line_dots(w0, w1, w2, u1, u2, D, part, c->tickets + 2, c->step, s); });
     }
     launch(c, "line_search", s, [&] { return launch_line_search(c->step, theta, s); });
-    const int tiles = taylor5_pair_parts(p->nq, psi->prec);
-    launch(c, "taylor5_pair_gated", s, [&] { return launch_taylor5_pair_gated(p->view, psi->prec, psi->data, c->step, part,
+    const int upt = c->pair_upt[psi->prec];
+    const int tiles = taylor5_pair_parts(p->nq, upt);
+    launch(c, "taylor5_pair_gated", s, [&] { return launch_taylor5_pair_gated(p->view, psi->prec, upt, psi->data, c->step, part,
                                               c->sm_count, s); });
-    launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, 1, tiles, nullptr, &c->step->norm2, s); });
+    launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, psi->prec, 1, tiles, nullptr, &c->step->norm2, s); });
     launch(c, "scale_gated", s, [&] { return launch_scale_gated(psi->data, psi->prec, D, &c->step->norm2, c->step, s); });
     DevStep hs;
     TQ_CUDA(cudaMemcpyAsync(&hs, c->step, sizeof(DevStep), cudaMemcpyDeviceToHost, s));
@@ -851,11 +926,12 @@ extern "C" int tq_evolve_taylor5_batch(tq_ctx* c, const tq_pool* p, int n_states
     if (n_states == 0) return TQ_OK;
     set_device(c);
     cudaStream_t s = as_stream(stream);
-    const int tiles = taylor5_pair_parts(p->nq, prec);
+    const int upt = c->pair_upt[prec];
+    const int tiles = taylor5_pair_parts(p->nq, upt);
     double* part = static_cast<double*>(scratch(c, S_PART, (size_t)n_states * tiles * sizeof(double)));
-    launch(c, "taylor5_pair", s, [&] { return launch_taylor5_pair(p->view, n_states, prec, psi, k, theta, 0, 0.0, part,
+    launch(c, "taylor5_pair", s, [&] { return launch_taylor5_pair(p->view, n_states, prec, upt, psi, k, theta, 0, 0.0, part,
                                         c->sm_count, s); });
-    if (norm2) launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, n_states, tiles, norm2, nullptr, s); });
+    if (norm2) launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, prec, n_states, tiles, norm2, nullptr, s); });
     API_END
 }
 
@@ -875,7 +951,8 @@ extern "C" int tq_evolve_taylor5_batch_host(tq_ctx* c, const tq_pool* p, int n_s
     // chunk of about 64 MiB of states per stream
     int chunk = (int)std::max<long long>(1, (64ll << 20) / (long long)sb);
     chunk = std::min(chunk, n_states);
-    const int tiles = taylor5_pair_parts(p->nq, prec);
+    const int upt = c->pair_upt[prec];
+    const int tiles = taylor5_pair_parts(p->nq, upt);
     const size_t per_stream = (size_t)chunk * sb + (size_t)chunk * (sizeof(int) + 2 * sizeof(double)) +
                               (size_t)chunk * tiles * sizeof(double) + 256;
     unsigned char* stage = static_cast<unsigned char*>(scratch(c, S_STAGE, 3 * per_stream));
@@ -893,11 +970,11 @@ extern "C" int tq_evolve_taylor5_batch_host(tq_ctx* c, const tq_pool* p, int n_s
                                 cudaMemcpyHostToDevice, s));
         TQ_CUDA(cudaMemcpyAsync(dk, k_host + c0, (size_t)n * sizeof(int), cudaMemcpyHostToDevice, s));
         TQ_CUDA(cudaMemcpyAsync(dth, theta_host + c0, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s));
-        launch(c, "taylor5_pair", s, [&] { return launch_taylor5_pair(p->view, n, prec, dpsi, dk, dth, 0, 0.0, part, c->sm_count, s); });
+        launch(c, "taylor5_pair", s, [&] { return launch_taylor5_pair(p->view, n, prec, upt, dpsi, dk, dth, 0, 0.0, part, c->sm_count, s); });
         TQ_CUDA(cudaMemcpyAsync(static_cast<unsigned char*>(psi_host) + (size_t)c0 * sb, dpsi, (size_t)n * sb,
                                 cudaMemcpyDeviceToHost, s));
         if (norm2_host) {
-            launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, n, tiles, dn, nullptr, s); });
+            launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, prec, n, tiles, dn, nullptr, s); });
             TQ_CUDA(cudaMemcpyAsync(norm2_host + c0, dn, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s));
         }
     }

@@ -119,12 +119,14 @@ int launch_csr_fill(const HamView& h, double tol, int max_row, int* col, void* v
 
 // Taylor-5, matrix-free pair path: states back to back, op k[b] / theta[b]
 // (device arrays, or the immediates when the pointers are null).  Writes
-// taylor5_pair_parts(nq, prec) float64 norm partials per state.
-int taylor5_pair_parts(int nq, int prec);
-int launch_taylor5_pair(const PoolView& p, int n_states, int prec, void* psi,
+// taylor5_pair_parts(nq, upt) norm partials per state; `upt` (1, 2, 4, 8)
+// is the schedule: pair units (4 amplitudes each) per thread per tile.
+int taylor5_pair_parts(int nq, int upt);
+bool pair_upt_valid(int upt);
+int launch_taylor5_pair(const PoolView& p, int n_states, int prec, int upt, void* psi,
                         const int* k, const double* theta, int k_imm, double theta_imm,
                         double* partials, int sms, cudaStream_t s);
-int launch_norm_reduce(const double* partials, int n_states, int tiles_per_state,
+int launch_norm_reduce(const double* partials, int prec, int n_states, int tiles_per_state,
                        double* norm2_out, double* step_norm2, cudaStream_t s);
 int launch_scale(void* psi, int prec, long long D, const double* norm2, cudaStream_t s);
 
@@ -156,7 +158,7 @@ int launch_line_dots(const double2* w0, const double2* w1, const double2* w2,
 int launch_line_search(DevStep* step, double theta_given, cudaStream_t s);
 
 // gated variants (skip when step->converged) and layout helpers
-int launch_taylor5_pair_gated(const PoolView& p, int prec, void* psi, const DevStep* step,
+int launch_taylor5_pair_gated(const PoolView& p, int prec, int upt, void* psi, const DevStep* step,
                               double* partials, int sms, cudaStream_t s);
 int launch_scale_gated(void* psi, int prec, long long D, const double* norm2,
                        const DevStep* gate, cudaStream_t s);
@@ -179,6 +181,7 @@ struct tq_ctx {
     int sm_count = 0;
     long long launches = 0;
     int tracing = 0;
+    int pair_upt[2] = {2, 4};              // schedule per precision (C128, C64)
     std::vector<tq_trace_rec> trace;      // recorded, not yet reported
     std::vector<cudaEvent_t> event_pool;  // reusable events
     // device scratch, grown on demand

@@ -27,6 +27,31 @@ __device__ __forceinline__ int warp_sum_int(int v) {
     return v;
 }
 
+// Error-free float32 sum (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Warp sum of float32 partials carried as (hi, lo) pairs with TwoSum at
+// every level; lane 0 returns hi + lo in float64.  Keeps the reduction
+// accurate to float64 level without float64 arithmetic on every lane.
+__device__ __forceinline__ double warp_sum_compensated(float v) {
+    float hi = v, lo = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_down_sync(0xffffffffu, hi, o);
+        const float ol = __shfl_down_sync(0xffffffffu, lo, o);
+        float s, e;
+        two_sum(hi, oh, s, e);
+        hi = s;
+        lo = lo + ol + e;
+    }
+    return (double)hi + (double)lo;
+}
+__device__ __forceinline__ double warp_sum_compensated(double v) { return warp_sum(v); }
+
 // Block-wide float64 sum of `n` values per thread (n <= 4); result valid in
 // thread 0.  `sh` needs blockDim/32 * n doubles.  Deterministic: fixed tree.
 template <int n>

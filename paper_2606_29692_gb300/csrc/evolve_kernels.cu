@@ -82,6 +82,25 @@ __device__ __forceinline__ void chain_pair(T s_r, T s_q, const T (&cf)[6], V& ar
     }
 }
 
+// complex64: the same chain on Blackwell's packed float32x2 pipe (one
+// instruction per complex multiply-by-real or multiply-add, rounding as the
+// scalar form).
+__device__ __forceinline__ void chain_pair(float s_r, float s_q, const float (&cf)[6], float2& ar,
+                                           float2& aq) {
+    const float2 sr = make_float2(s_r, s_r), sq = make_float2(s_q, s_q);
+    float2 vr = ar, vq = aq;
+#pragma unroll
+    for (int k = 1; k <= 5; ++k) {
+        const float2 nr = __fmul2_rn(sr, vq);
+        const float2 nq = __fmul2_rn(sq, vr);
+        vr = nr;
+        vq = nq;
+        const float2 c = make_float2(cf[k], cf[k]);
+        ar = __ffma2_rn(c, vr, ar);
+        aq = __ffma2_rn(c, vq, aq);
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void taylor_coefs(double theta, T (&cf)[6]) {
     double c = 1.0;
@@ -91,6 +110,49 @@ __device__ __forceinline__ void taylor_coefs(double theta, T (&cf)[6]) {
         c = c * theta / (double)k;
         cf[k] = (T)c;
     }
+}
+
+// theta^k / k! for k = 0..5 in the kernel's own precision: powers by
+// multiplication and constant reciprocal factorials (no division).  The
+// complex64 path stays entirely on the float32 pipes: float64 issues at
+// about 1/57 of the float32 rate on this part.
+template <typename T>
+__device__ __forceinline__ void taylor_coefs_fast(double theta, T (&cf)[6]) {
+    const T t = (T)theta;
+    const T t2 = t * t, t3 = t2 * t, t4 = t3 * t, t5 = t4 * t;
+    cf[0] = T(1);
+    cf[1] = t;
+    cf[2] = t2 * T(0.5);
+    cf[3] = t3 * T(1.0 / 6.0);
+    cf[4] = t4 * T(1.0 / 24.0);
+    cf[5] = t5 * T(1.0 / 120.0);
+}
+
+// Per-warp norm partial: float64 sum for complex128; for complex64 a
+// TwoSum-compensated float32 warp sum stored as a (hi, lo) float pair in
+// the 8-byte slot and widened to float64 by the reduction kernel.
+__device__ __forceinline__ void store_partial(double* slot, double v) {
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) *slot = v;
+}
+__device__ __forceinline__ void store_partial(double* slot, float v) {
+    float hi = v, lo = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_down_sync(0xffffffffu, hi, o);
+        const float ol = __shfl_down_sync(0xffffffffu, lo, o);
+        float sum, err;
+        two_sum(hi, oh, sum, err);
+        hi = sum;
+        lo = lo + ol + err;
+    }
+    if ((threadIdx.x & 31) == 0) *reinterpret_cast<float2*>(slot) = make_float2(hi, lo);
+}
+__device__ __forceinline__ void store_nan_partial(double* slot, double) {
+    if ((threadIdx.x & 31) == 0) *slot = __longlong_as_double(0x7ff8000000000000ll);
+}
+__device__ __forceinline__ void store_nan_partial(double* slot, float) {
+    if ((threadIdx.x & 31) == 0) *reinterpret_cast<float2*>(slot) = make_float2(__int_as_float(0x7fc00000), 0.f);
 }
 
 // One pool generator as staged in shared memory: X-mask, the factored sign
@@ -152,38 +214,39 @@ k_taylor5_pair(PoolView p, int n_states, typename C2<T>::type* psi, const int* k
     // the vectorised pool layout, staged once per CTA
     for (int i = threadIdx.x; i < p.M; i += blockDim.x) ops[i] = make_rec<T>(p, i);
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5;
     constexpr int NW = PAIR_BS / 32;
     constexpr int TU = PAIR_BS * UPT;           // units per tile
     const long long D = 1ll << p.nq;
     const uint32_t units = (uint32_t)(D >> 2);
-    const long long total = (long long)n_states * tiles_per_state;
-    long long tile = blockIdx.x;
-    int b = (int)(tile / tiles_per_state);
+    const unsigned total = (unsigned)n_states * (unsigned)tiles_per_state;
+    const unsigned tps = (unsigned)tiles_per_state;
+    unsigned tile = blockIdx.x;
+    int b = (int)(tile / tps);
     int k = tile < total ? (kk ? kk[b] : k_imm) : 0;
     double theta = tile < total ? (th ? th[b] : th_imm) : 0.0;
     for (; tile < total; ) {
-        const int tl = (int)(tile - (long long)b * tiles_per_state);
+        const int tl = (int)(tile - (unsigned)b * tps);
         // prefetch the next tile's op index and angle
-        const long long ntile = tile + gridDim.x;
-        const int nb = (int)(ntile / tiles_per_state);
+        const unsigned ntile = tile + gridDim.x;
+        const int nb = (int)(ntile / tps);
         int nk = 0;
         double nth = 0.0;
         if (ntile < total) {
             nk = kk ? kk[nb] : k_imm;
             nth = th ? th[nb] : th_imm;
         }
-        double part = 0.0;
+        double* slot = partials + (size_t)tile * NW + warp;
         if (k < 0 || k >= p.M) {
             // invalid op index from device memory: leave the state untouched
             // and poison its norm so the caller sees it
-            part = __longlong_as_double(0x7ff8000000000000ll);
+            store_nan_partial(slot, T(0));
         } else {
             const OpRec<T> op = ops[k];
             const uint32_t x = op.x;
             const int hb = 31 - __clz(x);
             T cf[6];
-            taylor_coefs<T>(theta, cf);
+            taylor_coefs_fast<T>(theta, cf);
             V* base = psi + (long long)b * D;
             V e0[UPT], e1[UPT], f0[UPT], f1[UPT];
             uint32_t r0s[UPT];
@@ -244,9 +307,8 @@ k_taylor5_pair(PoolView p, int n_states, typename C2<T>::type* psi, const int* k
                     store2(base, r0 + 2u, e1[j], f1[j]);
                 }
             }
-            part = warp_sum((double)tpart);
+            store_partial(slot, tpart);
         }
-        if (lane == 0) partials[tile * NW + warp] = part;
         tile = ntile;
         b = nb;
         k = nk;
@@ -254,14 +316,24 @@ k_taylor5_pair(PoolView p, int n_states, typename C2<T>::type* psi, const int* k
     }
 }
 
-// One warp per state: fixed-order float64 sum of the state's tile partials.
+// One warp per state: fixed-order float64 sum of the state's partials
+// (float64 values for complex128; (hi, lo) float pairs for complex64).
+template <bool PAIRS>
 __global__ void k_norm_reduce(const double* partials, int n_states, int tiles,
                               double* norm2_out, double* step_norm2) {
     const int lane = threadIdx.x & 31;
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= n_states) return;
     double s = 0.0;
-    for (int t = lane; t < tiles; t += 32) s += partials[(long long)w * tiles + t];
+    for (int t = lane; t < tiles; t += 32) {
+        const double* slot = partials + (long long)w * tiles + t;
+        if (PAIRS) {
+            const float2 hl = *reinterpret_cast<const float2*>(slot);
+            s += (double)hl.x + (double)hl.y;
+        } else {
+            s += *slot;
+        }
+    }
     s = warp_sum(s);
     if (lane == 0) {
         if (norm2_out) norm2_out[w] = s;
@@ -544,6 +616,7 @@ int launch_pair(const PoolView& p, int n_states, void* psi, const int* k, const 
     const long long units = (1ll << p.nq) >> 2;
     const int tiles = (int)((units + PAIR_BS * UPT - 1) / (PAIR_BS * UPT));
     const long long total = (long long)n_states * tiles;
+    if (total >= (1ll << 31)) return -1;   // caller splits such batches
     long long grid = pair_grid<T, UPT>(p.M, sms);
     if (grid > total) grid = total;
     if (grid < 1) grid = 1;
@@ -553,42 +626,56 @@ int launch_pair(const PoolView& p, int n_states, void* psi, const int* k, const 
     return 1;
 }
 
-constexpr int PAIR_UPT_C64 = 2;
-constexpr int PAIR_UPT_C128 = 2;
-
 }  // namespace
 
-int taylor5_pair_parts(int nq, int prec) {
-    const int upt = prec == TQ_C128 ? PAIR_UPT_C128 : PAIR_UPT_C64;
+int taylor5_pair_parts(int nq, int upt) {
     const long long units = (1ll << nq) >> 2;
     const int tiles = (int)((units + PAIR_BS * upt - 1) / (PAIR_BS * upt));
     return tiles * (PAIR_BS / 32);
 }
 
-int launch_taylor5_pair(const PoolView& p, int n_states, int prec, void* psi, const int* k,
+bool pair_upt_valid(int upt) { return upt == 1 || upt == 2 || upt == 4 || upt == 8; }
+
+namespace {
+
+template <typename T>
+int dispatch_pair(int upt, const PoolView& p, int n_states, void* psi, const int* k, const double* theta,
+                  int k_imm, double theta_imm, double* partials, const DevStep* gate, int sms,
+                  cudaStream_t s) {
+    switch (upt) {
+        case 1: return launch_pair<T, 1>(p, n_states, psi, k, theta, k_imm, theta_imm, partials, gate, sms, s);
+        case 2: return launch_pair<T, 2>(p, n_states, psi, k, theta, k_imm, theta_imm, partials, gate, sms, s);
+        case 4: return launch_pair<T, 4>(p, n_states, psi, k, theta, k_imm, theta_imm, partials, gate, sms, s);
+        case 8: return launch_pair<T, 8>(p, n_states, psi, k, theta, k_imm, theta_imm, partials, gate, sms, s);
+        default: return -1;
+    }
+}
+
+}  // namespace
+
+int launch_taylor5_pair(const PoolView& p, int n_states, int prec, int upt, void* psi, const int* k,
                         const double* theta, int k_imm, double theta_imm, double* partials, int sms,
                         cudaStream_t s) {
     if (prec == TQ_C128)
-        return launch_pair<double, PAIR_UPT_C128>(p, n_states, psi, k, theta, k_imm, theta_imm, partials,
-                                                  nullptr, sms, s);
-    return launch_pair<float, PAIR_UPT_C64>(p, n_states, psi, k, theta, k_imm, theta_imm, partials,
-                                            nullptr, sms, s);
+        return dispatch_pair<double>(upt, p, n_states, psi, k, theta, k_imm, theta_imm, partials, nullptr, sms, s);
+    return dispatch_pair<float>(upt, p, n_states, psi, k, theta, k_imm, theta_imm, partials, nullptr, sms, s);
 }
 
-int launch_taylor5_pair_gated(const PoolView& p, int prec, void* psi, const DevStep* step,
+int launch_taylor5_pair_gated(const PoolView& p, int prec, int upt, void* psi, const DevStep* step,
                               double* partials, int sms, cudaStream_t s) {
     if (prec == TQ_C128)
-        return launch_pair<double, PAIR_UPT_C128>(p, 1, psi, &step->selected, &step->theta, 0, 0.0, partials,
-                                                  step, sms, s);
-    return launch_pair<float, PAIR_UPT_C64>(p, 1, psi, &step->selected, &step->theta, 0, 0.0, partials,
-                                            step, sms, s);
+        return dispatch_pair<double>(upt, p, 1, psi, &step->selected, &step->theta, 0, 0.0, partials, step, sms, s);
+    return dispatch_pair<float>(upt, p, 1, psi, &step->selected, &step->theta, 0, 0.0, partials, step, sms, s);
 }
 
-int launch_norm_reduce(const double* partials, int n_states, int tiles_per_state,
+int launch_norm_reduce(const double* partials, int prec, int n_states, int tiles_per_state,
                        double* norm2_out, double* step_norm2, cudaStream_t s) {
     const int bs = 256;
     const int grid = (n_states * 32 + bs - 1) / bs;
-    k_norm_reduce<<<grid, bs, 0, s>>>(partials, n_states, tiles_per_state, norm2_out, step_norm2);
+    if (prec == TQ_C128)
+        k_norm_reduce<false><<<grid, bs, 0, s>>>(partials, n_states, tiles_per_state, norm2_out, step_norm2);
+    else
+        k_norm_reduce<true><<<grid, bs, 0, s>>>(partials, n_states, tiles_per_state, norm2_out, step_norm2);
     return 1;
 }
 

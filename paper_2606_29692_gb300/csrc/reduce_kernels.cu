@@ -53,7 +53,8 @@ k_energy_csr(HamView h, const typename C2<T>::type* __restrict__ psi, double2* _
             px = fma(a, v.x, px);
             py = fma(a, v.y, py);
         }
-        const double sx = warp_sum((double)px), sy = warp_sum((double)py);
+        // complex64: float32 lane sums, compensated warp sum -> float64
+        const double sx = warp_sum_compensated(px), sy = warp_sum_compensated(py);
         if (lane == 0) {
             const double2 pr = to_d2<T>(psi[r]);
             const double d = h.diag[r];

@@ -207,6 +207,49 @@ def test_full_size_batch_sampled(ctx):
         assert abs(dn[b].item() - np.vdot(ref, ref).real) <= 1e-6
 
 
+@pytest.mark.parametrize("prec", [tq.TQ_C128, tq.TQ_C64])
+def test_every_schedule_gives_identical_results(ctx, prec):
+    import torch
+    pool = tq.build_pool(ctx, 6, 8, 1)
+    S = 40
+    rng = np.random.default_rng(8)
+    psi = np.stack([synth.random_state(12, 50 + b) for b in range(S)])
+    k = torch.as_tensor(rng.integers(0, pool.M, size=S).astype(np.int32)).cuda()
+    th = torch.as_tensor(rng.normal(0, 0.2, size=S)).cuda()
+    dt = torch.complex128 if prec == tq.TQ_C128 else torch.complex64
+    outs = []
+    for upt in (1, 2, 4, 8):
+        ctx.set_pair_schedule(prec, upt)
+        d = torch.as_tensor(psi).to(dt).cuda()
+        n = torch.zeros(S, dtype=torch.float64, device="cuda")
+        tq.evolve_taylor5_batch(ctx, pool, d, k, th, n, prec=prec)
+        torch.cuda.synchronize()
+        outs.append((d.cpu().numpy(), n.cpu().numpy()))
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0])
+        # the norm partials are grouped by tile, so only rounding may differ
+        assert np.abs(o[1] - outs[0][1]).max() <= 1e-12 * outs[0][1].max()
+    best, ms = tq.autotune_pair(ctx, pool, prec, n_states=64)
+    assert best in (1, 2, 4, 8) and ms > 0 and ctx.pair_schedule(prec) == best
+    with pytest.raises(tq.TQError):
+        ctx.set_pair_schedule(prec, 3)
+
+
+def test_invalid_op_index_poisons_norm(ctx):
+    import torch
+    pool = tq.build_pool(ctx, 4, 4, 0)
+    psi = torch.zeros((3, 256), dtype=torch.complex64, device="cuda")
+    psi[:, 5] = 1.0
+    before = psi.clone()
+    k = torch.as_tensor(np.array([0, pool.M, -1], dtype=np.int32)).cuda()
+    th = torch.as_tensor(np.array([0.1, 0.1, 0.1])).cuda()
+    n = torch.zeros(3, dtype=torch.float64, device="cuda")
+    tq.evolve_taylor5_batch(ctx, pool, psi, k, th, n)
+    torch.cuda.synchronize()
+    assert np.isfinite(n[0].item()) and np.isnan(n[1].item()) and np.isnan(n[2].item())
+    assert torch.equal(psi[1:], before[1:])
+
+
 def test_evolve_rejects_bad_arguments(ctx):
     pool = tq.build_pool(ctx, 4, 4, 0)
     st = to_state(ctx, synth.random_state(8, 1), 8, tq.TQ_C128)
