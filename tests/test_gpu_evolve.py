@@ -185,6 +185,7 @@ def test_full_size_batch_sampled(ctx):
     n, ne, mp = 7, 6, 1
     N, S = 14, 8192
     pool = tq.build_pool(ctx, n, ne, mp)
+    tq.autotune_pair(ctx, pool, tq.TQ_C64, n_states=2048)     # as the benchmark does
     prep_k, prep_th, k, th = synth.t5_batch(S, pool.M)
     hf = tq.hf_index(N, ne, mp)
     psi = torch.zeros((S, 1 << N), dtype=torch.complex64, device="cuda")
