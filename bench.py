@@ -222,7 +222,11 @@ def run_ours(args, rank, world, local_rank):
     dn = torch.zeros(S, dtype=torch.float64, device="cuda")
     # the library's autotuner picks the pair kernel's schedule on scratch
     # states (untimed, before warm-up)
-    upt, tune_ms = tq.autotune_pair(ctx, pool, tq.TQ_C64, n_states=min(S, 2048))
+    if args.pair_schedule:
+        ctx.set_pair_schedule(tq.TQ_C64, args.pair_schedule)
+        upt, tune_ms = args.pair_schedule, None
+    else:
+        upt, tune_ms = tq.autotune_pair(ctx, pool, tq.TQ_C64, n_states=min(S, 2048))
 
     def step():
         tq.evolve_taylor5_batch(ctx, pool, psi, dk, dth, dn)
@@ -329,6 +333,8 @@ def main():
     ap.add_argument("--states", type=int, default=8192)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pair-schedule", type=int, default=0,
+                    help="units per thread of the pair kernel (0 = autotune)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

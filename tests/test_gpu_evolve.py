@@ -226,10 +226,13 @@ def test_every_schedule_gives_identical_results(ctx, prec):
         tq.evolve_taylor5_batch(ctx, pool, d, k, th, n, prec=prec)
         torch.cuda.synchronize()
         outs.append((d.cpu().numpy(), n.cpu().numpy()))
+    # complex64 norms: per-thread float32 partials of <= 32 squares, grouped
+    # by the schedule, so schedules agree to float32 rounding of those
+    # partials; the cross-thread sums are compensated and widened to float64
+    tol = 1e-12 if prec == tq.TQ_C128 else 2e-6
     for o in outs[1:]:
         assert np.array_equal(o[0], outs[0][0])
-        # the norm partials are grouped by tile, so only rounding may differ
-        assert np.abs(o[1] - outs[0][1]).max() <= 1e-12 * outs[0][1].max()
+        assert np.abs(o[1] - outs[0][1]).max() <= tol * outs[0][1].max()
     best, ms = tq.autotune_pair(ctx, pool, prec, n_states=64)
     assert best in (1, 2, 4, 8) and ms > 0 and ctx.pair_schedule(prec) == best
     with pytest.raises(tq.TQError):
