@@ -237,6 +237,30 @@ int tq_evolve_taylor5_csr(tq_ctx* ctx, int n_qubits, const int* rowptr,
  * host scalar *E (synchronises the stream). */
 int tq_energy(tq_ctx* ctx, const tq_ham* ham, const tq_state* psi, double* E,
               void* stream);
+/* Energy that allocates nothing (the paper has no counterpart: it serves
+ * callers that cannot call cudaMalloc or cudaFree where they need an energy,
+ * such as serving loops that reserved their memory up front and must not
+ * stall the device on an allocation, or hosts whose own allocator owns the
+ * device heap).  Same arithmetic as tq_energy (float64 warp-shuffle sums of
+ * the fused CSR SpMV), on the calling thread's current device, with inputs
+ * given as device pointers: the off-diagonal CSR (rowptr int32[D+1], col
+ * int32, val float64 for TQ_C128 / float32 for TQ_C64), the float64
+ * diagonal[D], and the state psi (D amplitudes of `prec`).  The energy is
+ * written to energy_out (one float64 in device memory), stream-ordered on
+ * `stream`; the call does not synchronise.
+ * Its scratch is one fixed 64 KiB array in device global memory that every
+ * GPU loading the library holds until the process exits; it bounds the
+ * reduction to 4032 CTA partials.  The first call on a device resolves that
+ * array's device address (cudaGetSymbolAddress) and the SM count, so make
+ * the first call before any stream capture.  Every call shares the array:
+ * calls that overlap on the GPU (other streams, other threads) race and
+ * must be ordered by the caller.  Errors: TQ_EINVAL (null pointer,
+ * precision, n_qubits outside [1, 26], or a reduction larger than the
+ * scratch holds), TQ_ECUDA. */
+int tq_energy_noalloc(int n_qubits, int prec, const int* rowptr, const int* col,
+                      const void* val, const double* diag, const void* psi,
+                      double* energy_out, void* stream);
+
 /* Same energy, computed from the X-mask-grouped Pauli layout without the
  * CSR (cross-check of the CSR build; arithmetic-bound). */
 int tq_energy_matrix_free(tq_ctx* ctx, const tq_ham* ham, const tq_state* psi,

@@ -20,7 +20,7 @@ __all__ = [
     "pauli_hamiltonian", "pool_excitations", "pauli_pool", "hf_index", "build_hamiltonian",
     "build_pool", "evolve_taylor5", "evolve_taylor5_csr", "energy", "energy_matrix_free",
     "pool_gradients", "adapt_step", "evolve_taylor5_batch", "evolve_taylor5_batch_host",
-    "state_set_hf", "pool_csr", "ham_csr", "lib", "autotune_pair",
+    "state_set_hf", "pool_csr", "ham_csr", "lib", "autotune_pair", "energy_noalloc",
 ]
 
 
@@ -263,6 +263,13 @@ def energy(ctx, ham, state, stream=None):
     e = C.c_double()
     call("tq_energy", ctx.handle, ham.handle, state.handle, C.byref(e), _stream(stream))
     return e.value
+
+
+def energy_noalloc(n_qubits, prec, rowptr, col, val, diag, psi, energy_out, stream=None):
+    """Energy without any allocation; every argument is a device pointer (int)
+    and the result lands in ``energy_out`` (one float64 on the device)."""
+    call("tq_energy_noalloc", n_qubits, prec, C.c_void_p(rowptr), C.c_void_p(col), C.c_void_p(val),
+         C.c_void_p(diag), C.c_void_p(psi), C.c_void_p(energy_out), _stream(stream))
 
 
 def energy_matrix_free(ctx, ham, state, stream=None):

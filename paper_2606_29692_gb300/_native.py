@@ -69,6 +69,7 @@ SIGNATURES = {
     "tq_evolve_taylor5_csr": [vp, i32, vp, vp, vp, f64, vp, i32, vp],
     "tq_energy": [vp, vp, vp, P(f64), vp],
     "tq_energy_matrix_free": [vp, vp, vp, P(f64), vp],
+    "tq_energy_noalloc": [i32, i32, vp, vp, vp, vp, vp, vp, vp],
     "tq_pool_gradients": [vp, vp, vp, vp, vp, i32, vp],
     "tq_adapt_step": [vp, vp, vp, vp, f64, f64, P(AdaptResult), vp],
     "tq_evolve_taylor5_batch": [vp, vp, i32, i32, vp, vp, vp, vp, vp],

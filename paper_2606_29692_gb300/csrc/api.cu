@@ -190,6 +190,10 @@ void free_all(std::vector<void*>& allocs) {
 
 // ===================================================================== misc
 
+namespace tq {
+void set_last_error(const std::string& m) { g_last_error = m; }
+}  // namespace tq
+
 extern "C" const char* tq_last_error(void) { return g_last_error.c_str(); }
 extern "C" int tq_version(void) { return 100; }
 

@@ -43,6 +43,8 @@ struct SignForm {
 };
 
 void check_mapping(int mapping);
+// Sets the thread-local reason returned by tq_last_error().
+void set_last_error(const std::string& m);
 std::vector<PauliTerm> pauli_hamiltonian(int n, const double* h1, const double* g2,
                                          double e_const, int mapping);
 std::vector<Excitation> excitations(int n, int ne);
