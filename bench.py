@@ -42,7 +42,7 @@ D = 1 << NQ
 FALLBACK_HBM_GBS = 6800.0
 PROFILE = os.path.join(ROOT, "profiles", "taylor5_pair_c64_14q.md")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2606_29692_gb300", "csrc", f)
-                  for f in ("evolve_kernels.cu", "dev.cuh")]
+                  for f in ("evolve_kernels.cu", "pair.cuh", "dev.cuh")]
 
 
 def workload_config(n_states):
@@ -298,6 +298,10 @@ def run_ours(args, rank, world, local_rank):
            "d2h_bytes_per_step": S * D * 8 + S * 8,
            "api": "tq_evolve_taylor5_batch_host (pinned host buffers, 3-stream chunked copies)"}
     finite = bool(torch.isfinite(dn).all().item()) and float(dn.min().item()) > 0.5
+    extra = {}
+    if rank == 0 and not args.headline_only:
+        extra["spmv"] = measure_spmv(tq, ctx, args.spmv_qubits)
+        extra["trajectories"] = measure_trajectories(tq, ctx, args.traj)
     out = None
     if rank == 0:
         out = {
@@ -321,7 +325,85 @@ def run_ours(args, rank, world, local_rank):
             "clocks": clk,
             "norms_finite": finite,
         }
+        out.update(extra)
     return out
+
+
+def measure_spmv(tq, ctx, nq):
+    """Energy (fused CSR SpMV + float64 dots) on a Hamiltonian larger than L2."""
+    import numpy as np
+    import torch
+
+    import synth
+    n = nq // 2
+    ne = synth.electrons_for(n)
+    ints = synth.integrals(n, synth.SEED_CATALOGUE_BASE + 12)
+    t0 = time.perf_counter()
+    ham = tq.build_hamiltonian(ctx, ints.h, ints.g, ints.e_const, 1, tq.TQ_C64)
+    build_s = time.perf_counter() - t0
+    D = 1 << nq
+    st = tq.State(ctx, nq, tq.TQ_C64)
+    tq.state_set_hf(st, ne, 1)
+    pool = tq.build_pool(ctx, n, ne, 1)
+    for k in range(0, pool.M, max(1, pool.M // 8)):
+        tq.evolve_taylor5(ctx, pool, k, 0.1, st, renormalize=True)
+    for _ in range(3):
+        tq.energy(ctx, ham, st)
+    ctx.trace(True)
+    reps = 20
+    for _ in range(reps):
+        e = tq.energy(ctx, ham, st)
+    rep = ctx.trace_report()
+    ctx.trace(False)
+    n_l, ms = rep["energy_csr"]
+    ms /= n_l
+    alg = 4 * (D + 1) + 8 * ham.nnz + 8 * D + 8 * D + 16 * D
+    peak, _ = peaks()
+    gbs = alg / (ms * 1e-3) / 1e9
+    return {"workload": f"energy of a {nq}-qubit BK Hamiltonian (synthetic, {n} orbitals, "
+                        f"{ne} electrons), complex64 state, float32 CSR + float64 diagonal",
+            "kernel": "k_energy_csr<float,float>", "nnz": ham.nnz, "hamiltonian_bytes": ham.device_bytes,
+            "build_s": build_s, "ms_per_energy": ms,
+            "algorithmic_bytes": alg, "achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak,
+            "energy": e, "l2_policy": "CSR larger than L2"}
+
+
+def measure_trajectories(tq, ctx, n_traj):
+    """Independent ADAPT trajectories of 10-16 qubits, one graph replay per run."""
+    import numpy as np
+    import torch
+
+    import synth
+    trajs = synth.trajectories(n_traj)
+    t0 = time.perf_counter()
+    hams, pools = [], []
+    for tr in trajs:
+        ints = synth.integrals(tr.n_spatial, tr.seed)
+        hams.append(tq.build_hamiltonian(ctx, ints.h, ints.g, ints.e_const, tr.mapping, tq.TQ_C64))
+        pools.append(tq.build_pool(ctx, tr.n_spatial, tr.n_electrons, tr.mapping))
+    b = tq.Batch(ctx, hams, pools, [t.n_electrons for t in trajs], [t.mapping for t in trajs],
+                 [t.thetas for t in trajs], 1e-3)
+    build_s = time.perf_counter() - t0
+    lpr, _ = b.autotune()
+    b.run(use_graph=True)          # warm: captures the graph
+    torch.cuda.synchronize()
+    runs = 3
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(runs):
+        b.run(use_graph=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / runs
+    res = b.results()
+    iters = sum(r["n_iter"] for r in res)
+    return {"workload": f"{n_traj} ADAPT trajectories, qubits uniform over 10-16, JW/BK 50/50, "
+                        "own integrals (seeds 1000+i), angle lists of 1-30 from N(0,0.1), eps 1e-3, "
+                        "complex64 with float64 reductions",
+            "build_s": build_s, "lanes_per_row": lpr, "ms_per_run": ms,
+            "iterations_per_run": iters, "iterations_per_s": iters / (ms * 1e-3),
+            "converged": int(sum(r["converged"] for r in res)), "graph_launches_per_run": 6 * max(len(t.thetas) for t in trajs)}
 
 
 def main():
@@ -333,6 +415,10 @@ def main():
     ap.add_argument("--states", type=int, default=8192)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="skip the SpMV and trajectory-batch measurements")
+    ap.add_argument("--spmv-qubits", type=int, default=18)
+    ap.add_argument("--traj", type=int, default=256)
     ap.add_argument("--pair-schedule", type=int, default=0,
                     help="units per thread of the pair kernel (0 = autotune)")
     args = ap.parse_args()

@@ -318,6 +318,45 @@ int tq_evolve_taylor5_batch_host(tq_ctx* ctx, const tq_pool* pool,
                                  const int* k_host, const double* theta_host,
                                  double* norm2_host);
 
+/* --------------------------------------------------- trajectory batches */
+
+/* Many independent ADAPT trajectories (the loop of Sec. III-D) advanced
+ * together.  Trajectory t uses Hamiltonian hams[t] and pool pools[t] (same
+ * qubit count; every Hamiltonian of one batch has the same precision, which
+ * is the states' precision), starts from the Hartree-Fock state of
+ * n_electrons[t] under mappings[t], and runs at most lengths[t] iterations,
+ * iteration i using angle thetas[off_t + i] (off_t = sum of the earlier
+ * lengths) unless max|g| < eps stops it first.  Each iteration is energy,
+ * all gradients, selection (tie rule of tq_adapt_step), the Taylor-5 update
+ * and renormalisation.  The batch owns its states and keeps the handles it
+ * was given (they must outlive it).  Every iteration of every trajectory is
+ * six persistent launches over static work tables; finished trajectories are
+ * skipped by a device-side flag, so a run needs no host round trip. */
+typedef struct tq_batch tq_batch;
+int tq_batch_create(tq_ctx* ctx, int n_traj, tq_ham* const* hams,
+                    tq_pool* const* pools, const int* n_electrons,
+                    const int* mappings, const int* lengths,
+                    const double* thetas, double eps, tq_batch** out);
+/* Lanes that share one Hamiltonian row in the energy SpMV: 4, 8, 16, 32. */
+int tq_batch_set_schedule(tq_batch* b, int lanes_per_row);
+/* Autotuner: times the energy launch at each lanes-per-row value on the
+ * batch's own states (reset to Hartree-Fock), keeps the fastest. */
+int tq_batch_autotune(tq_batch* b, int* lanes_per_row, double* best_ms);
+/* Reset every state to Hartree-Fock and run all iterations, enqueued on
+ * `stream`.  use_graph != 0 replays one CUDA graph holding every iteration
+ * (captured on the first such call and after a schedule change).  Async. */
+int tq_batch_run(tq_batch* b, int use_graph, void* stream);
+/* Per trajectory: iterations evaluated and the converged flag; per
+ * iteration (laid out like `thetas`): energy before the update, max|g|,
+ * selected op, angle used (0 on the converged iteration).  Any output may
+ * be NULL.  Synchronises the device. */
+int tq_batch_results(const tq_batch* b, int* n_iter, int* converged,
+                     double* energy, double* max_grad, int* selected,
+                     double* theta);
+/* Borrowed device pointer to trajectory t's state. */
+int tq_batch_state(const tq_batch* b, int t, void** dev_ptr, int* n_qubits);
+int tq_batch_free(tq_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

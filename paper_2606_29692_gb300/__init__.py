@@ -20,7 +20,7 @@ __all__ = [
     "pauli_hamiltonian", "pool_excitations", "pauli_pool", "hf_index", "build_hamiltonian",
     "build_pool", "evolve_taylor5", "evolve_taylor5_csr", "energy", "energy_matrix_free",
     "pool_gradients", "adapt_step", "evolve_taylor5_batch", "evolve_taylor5_batch_host",
-    "state_set_hf", "pool_csr", "ham_csr", "lib", "autotune_pair", "energy_noalloc",
+    "state_set_hf", "pool_csr", "ham_csr", "lib", "autotune_pair", "energy_noalloc", "Batch",
 ]
 
 
@@ -317,3 +317,77 @@ def evolve_taylor5_batch_host(ctx, pool, psi, k, theta, norm2=None, prec=TQ_C64)
     n_states = psi.shape[0]
     call("tq_evolve_taylor5_batch_host", ctx.handle, pool.handle, n_states, prec, _ptr(psi), _ptr(k),
          _ptr(theta), _ptr(norm2))
+
+
+# ----------------------------------------------------------- trajectory batch
+
+class Batch:
+    """Independent ADAPT trajectories advanced together (graph-replayed)."""
+
+    def __init__(self, ctx, hams, pools, n_electrons, mappings, thetas, eps=1e-3):
+        self.ctx, self.hams, self.pools = ctx, list(hams), list(pools)
+        n = len(self.hams)
+        self.lengths = np.array([len(t) for t in thetas], dtype=np.int32)
+        flat = np.concatenate([np.asarray(t, dtype=np.float64) for t in thetas]) if n else np.zeros(0)
+        self._flat = np.ascontiguousarray(flat if flat.size else np.zeros(1))
+        hh = (C.c_void_p * n)(*[h.handle.value for h in self.hams])
+        pp = (C.c_void_p * n)(*[p.handle.value for p in self.pools])
+        ne = np.ascontiguousarray(n_electrons, dtype=np.int32)
+        mp = np.ascontiguousarray(mappings, dtype=np.int32)
+        h = C.c_void_p()
+        call("tq_batch_create", ctx.handle, n, hh, pp, _ptr(ne), _ptr(mp), _ptr(self.lengths),
+             _ptr(self._flat), float(eps), C.byref(h))
+        self.handle = h
+        self.n = n
+
+    def set_schedule(self, lanes_per_row):
+        call("tq_batch_set_schedule", self.handle, int(lanes_per_row))
+
+    def autotune(self):
+        l, ms = C.c_int(), C.c_double()
+        call("tq_batch_autotune", self.handle, C.byref(l), C.byref(ms))
+        return l.value, ms.value
+
+    def run(self, use_graph=True, stream=None):
+        call("tq_batch_run", self.handle, 1 if use_graph else 0, _stream(stream))
+
+    def results(self):
+        L = int(self.lengths.sum())
+        n_iter = np.zeros(self.n, dtype=np.int32)
+        conv = np.zeros(self.n, dtype=np.int32)
+        e, g, th = (np.zeros(max(L, 1)) for _ in range(3))
+        sel = np.zeros(max(L, 1), dtype=np.int32)
+        call("tq_batch_results", self.handle, _ptr(n_iter), _ptr(conv), _ptr(e), _ptr(g), _ptr(sel), _ptr(th))
+        out, off = [], 0
+        for t in range(self.n):
+            n = int(self.lengths[t])
+            k = int(n_iter[t])
+            out.append({"n_iter": k, "converged": bool(conv[t]), "energy": e[off:off + k].copy(),
+                        "max_grad": g[off:off + k].copy(), "selected": sel[off:off + k].copy(),
+                        "theta": th[off:off + k].copy()})
+            off += n
+        return out
+
+    def state(self, t):
+        """Copy of trajectory t's state as a complex128 numpy array."""
+        import torch
+        ptr, nq = C.c_void_p(), C.c_int()
+        call("tq_batch_state", self.handle, int(t), C.byref(ptr), C.byref(nq))
+        prec = self.hams[0].prec
+        n = 1 << nq.value
+        typestr = "<c16" if prec == TQ_C128 else "<c8"
+
+        class _View:
+            __cuda_array_interface__ = {"shape": (n,), "typestr": typestr,
+                                        "data": (ptr.value, False), "version": 3}
+
+        torch.cuda.synchronize()
+        return torch.as_tensor(_View(), device="cuda").cpu().numpy().astype(np.complex128)
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().tq_batch_free(self.handle)
+                self.handle = None
+        except Exception:
+            pass

@@ -74,6 +74,13 @@ SIGNATURES = {
     "tq_adapt_step": [vp, vp, vp, vp, f64, f64, P(AdaptResult), vp],
     "tq_evolve_taylor5_batch": [vp, vp, i32, i32, vp, vp, vp, vp, vp],
     "tq_evolve_taylor5_batch_host": [vp, vp, i32, i32, vp, vp, vp, vp],
+    "tq_batch_create": [vp, i32, vp, vp, vp, vp, vp, vp, f64, P(vp)],
+    "tq_batch_set_schedule": [vp, i32],
+    "tq_batch_autotune": [vp, P(i32), P(f64)],
+    "tq_batch_run": [vp, i32, vp],
+    "tq_batch_results": [vp, vp, vp, vp, vp, vp, vp],
+    "tq_batch_state": [vp, i32, P(vp), P(i32)],
+    "tq_batch_free": [vp],
 }
 _RET = {"tq_last_error": C.c_char_p}
 

@@ -1,0 +1,666 @@
+// Many independent ADAPT trajectories (Sec. III-D loop) of uneven size,
+// advanced together.
+//
+// Every trajectory t has its own Hamiltonian, pool, state, angle list and
+// convergence test.  One iteration of all of them is six persistent
+// launches, each spanning every trajectory through a static work table:
+//   energy   items (t, row block): w_t = H_t psi_t, <psi|w>, <psi|psi>;
+//   grads    items (t, op, chunk): g_t[k] = 2 Re<w_t|A_k psi_t>/<psi|psi>;
+//   select   one warp per t: k*, max|g|, convergence, angle, record;
+//   update   items (t, tile): the fused Taylor-5 pair update with A_{k*};
+//   norm     one warp per t: ||psi'||^2, advance the iteration counter;
+//   scale    items (t, chunk): psi /= ||psi'||.
+// Items of finished trajectories are skipped by a flag read on the device,
+// so the whole run (max length x six launches) is captured once into a CUDA
+// graph and replayed without any host round trip.  The SpMV of the energy
+// item has a lanes-per-row schedule (4, 8, 16, 32) chosen by an autotuner.
+#include "dev.cuh"
+#include "host_util.h"
+#include "pair.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace tq {
+
+struct TrajDev {
+    int nq, M, len, nch, chunk;
+    int eoff, ecnt;          // energy items of this trajectory
+    int pcnt;                // pair tiles (8 norm partials each)
+    long long D;
+    long long hf;
+    long long nbase;         // first norm-partial slot
+    const double* diag;
+    const int* rowptr;
+    const int* col;
+    const void* val;
+    PoolView pool;
+    void* psi;
+    double2* w;
+    const double* thetas;
+    double* g;
+    double* gpart;
+    unsigned* gtick;
+    double* res_e;
+    double* res_g;
+    double* res_th;
+    int* res_sel;
+};
+
+struct TrajState {
+    double e_num, e_den, energy, max_grad, theta, norm2;
+    int selected, converged, iter, active, do_update;
+    unsigned etick;
+};
+
+namespace {
+
+constexpr int BT_BS = 256;
+constexpr int ROWS_PER_ITEM = 256;
+constexpr int BT_UPT = 2;
+
+template <typename T> __device__ __forceinline__ double2 d2(typename C2<T>::type v) {
+    return make_double2((double)v.x, (double)v.y);
+}
+
+// sum over a group of W lanes (W divides 32); result in the group's lane 0
+template <int W>
+__device__ __forceinline__ double group_sum(double v) {
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o, W);
+    return v;
+}
+template <int W>
+__device__ __forceinline__ double group_sum(float v) {
+    float hi = v, lo = 0.f;
+#pragma unroll
+    for (int o = W / 2; o > 0; o >>= 1) {
+        const float oh = __shfl_down_sync(0xffffffffu, hi, o, W);
+        const float ol = __shfl_down_sync(0xffffffffu, lo, o, W);
+        float s, e;
+        two_sum(hi, oh, s, e);
+        hi = s;
+        lo = lo + ol + e;
+    }
+    return (double)hi + (double)lo;
+}
+
+template <typename T>
+__global__ void kb_reset(const TrajDev* tr, TrajState* ts, const int4* items, int n_items) {
+    using V = typename C2<T>::type;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int4 w = items[it];
+        const TrajDev& d = tr[w.x];
+        V* psi = static_cast<V*>(d.psi);
+        for (int i = threadIdx.x; i < w.z; i += blockDim.x) {
+            const long long r = (long long)w.y + i;
+            V v;
+            v.x = r == d.hf ? 1 : 0;
+            v.y = 0;
+            psi[r] = v;
+        }
+        if (w.y == 0 && threadIdx.x == 0) {
+            TrajState s{};
+            s.active = d.len > 0;
+            ts[w.x] = s;
+        }
+    }
+}
+
+template <typename T, typename VT, int LPR>
+__global__ void __launch_bounds__(BT_BS)
+kb_energy(const TrajDev* tr, TrajState* ts, const int4* items, int n_items, double* part) {
+    using V = typename C2<T>::type;
+    __shared__ double sh[2 * (BT_BS / 32)];
+    __shared__ bool last;
+    const int grp = threadIdx.x / LPR, gl = threadIdx.x % LPR;
+    constexpr int NG = BT_BS / LPR;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int4 w4 = items[it];
+        const int t = w4.x;
+        if (!ts[t].active) continue;                     // uniform across the block
+        const TrajDev& d = tr[t];
+        const V* psi = static_cast<const V*>(d.psi);
+        const VT* val = static_cast<const VT*>(d.val);
+        double num = 0.0, den = 0.0;
+        for (int r = w4.y + grp; r < w4.y + w4.z; r += NG) {
+            T px = T(0), py = T(0);
+            const int e1 = d.rowptr[r + 1];
+            for (int e = d.rowptr[r] + gl; e < e1; e += LPR) {
+                const T a = (T)val[e];
+                const V v = psi[d.col[e]];
+                px = fma(a, v.x, px);
+                py = fma(a, v.y, py);
+            }
+            const double sx = group_sum<LPR>(px), sy = group_sum<LPR>(py);
+            if (gl == 0) {
+                const double2 pr = d2<T>(psi[r]);
+                const double dg = d.diag[r];
+                const double wx = fma(dg, pr.x, sx), wy = fma(dg, pr.y, sy);
+                d.w[r] = make_double2(wx, wy);
+                num += pr.x * wx + pr.y * wy;
+                den += pr.x * pr.x + pr.y * pr.y;
+            }
+        }
+        double v[2] = {num, den};
+        block_sum<2>(v, sh);
+        if (threadIdx.x == 0) {
+            part[2 * it] = v[0];
+            part[2 * it + 1] = v[1];
+            __threadfence();
+            last = atomicAdd(&ts[t].etick, 1u) == (unsigned)d.ecnt - 1;
+        }
+        __syncthreads();
+        if (last && threadIdx.x == 0) {
+            double a = 0.0, b = 0.0;
+            for (int i = d.eoff; i < d.eoff + d.ecnt; ++i) {
+                a += __ldcg(part + 2 * i);
+                b += __ldcg(part + 2 * i + 1);
+            }
+            ts[t].e_num = a;
+            ts[t].e_den = b;
+            ts[t].energy = a / b;
+            ts[t].etick = 0u;
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BT_BS)
+kb_grad(const TrajDev* tr, TrajState* ts, const int4* items, int n_items) {
+    using V = typename C2<T>::type;
+    __shared__ double sh[BT_BS / 32];
+    __shared__ bool last;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int4 w4 = items[it];
+        const int t = w4.x, k = w4.y, c = w4.z;
+        if (!ts[t].active) continue;
+        const TrajDev& d = tr[t];
+        const V* psi = static_cast<const V*>(d.psi);
+        OpSign<double> op;
+        op.load(d.pool, k);
+        double acc = 0.0;
+        const uint32_t r0 = (uint32_t)c * d.chunk;
+        for (int i = threadIdx.x; i < d.chunk; i += BT_BS) {
+            const uint32_t r = r0 + i, q = r ^ op.x;
+            const double s = op.value(q);
+            if (s != 0.0) {
+                const double2 wr = d.w[r];
+                const double2 v = d2<T>(psi[q]);
+                acc += s * (wr.x * v.x + wr.y * v.y);
+            }
+        }
+        double v[1] = {acc};
+        block_sum<1>(v, sh);
+        if (threadIdx.x == 0) {
+            d.gpart[(long long)k * d.nch + c] = v[0];
+            __threadfence();
+            last = atomicAdd(&d.gtick[k], 1u) == (unsigned)d.nch - 1;
+        }
+        __syncthreads();
+        if (last && threadIdx.x == 0) {
+            double s = 0.0;
+            for (int i = 0; i < d.nch; ++i) s += __ldcg(d.gpart + (long long)k * d.nch + i);
+            d.g[k] = 2.0 * s / ts[t].e_den;
+            d.gtick[k] = 0u;
+        }
+        __syncthreads();
+    }
+}
+
+// One warp per trajectory: choice, convergence, angle, record.
+__global__ void kb_select(const TrajDev* tr, TrajState* ts, int n, double eps, int prec) {
+    const int lane = threadIdx.x & 31;
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= n) return;
+    TrajState& s = ts[t];
+    if (!s.active) {
+        if (lane == 0) s.do_update = 0;
+        return;
+    }
+    const TrajDev& d = tr[t];
+    double m = 0.0;
+    for (int k = lane; k < d.M; k += 32) m = fmax(m, fabs(d.g[k]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const double tau = prec == TQ_C128 ? 1e-9 * fmax(1.0, m) : 1e-5;
+    int best = d.M;
+    for (int k = lane; k < d.M; k += 32)
+        if (fabs(d.g[k]) >= m - tau && k < best) best = k;
+    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if (lane == 0) {
+        const int it = s.iter;
+        s.selected = best < d.M ? best : 0;
+        s.max_grad = m;
+        s.converged = m < eps ? 1 : 0;
+        s.theta = s.converged ? 0.0 : d.thetas[it];
+        s.do_update = !s.converged;
+        d.res_e[it] = s.energy;
+        d.res_g[it] = m;
+        d.res_sel[it] = s.selected;
+        d.res_th[it] = s.theta;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PAIR_BS)
+kb_pair(const TrajDev* tr, const TrajState* ts, const int4* items, int n_items, double* npart) {
+    constexpr int NW = PAIR_BS / 32;
+    const int warp = threadIdx.x >> 5;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int4 w4 = items[it];
+        const int t = w4.x, tl = w4.y;
+        const TrajState& s = ts[t];
+        if (!s.do_update) continue;
+        const TrajDev& d = tr[t];
+        const OpRec<T> op = make_rec<T>(d.pool, s.selected);
+        const T tp = pair_tile<T, BT_UPT>(op, s.theta, static_cast<typename C2<T>::type*>(d.psi),
+                                          (uint32_t)tl, (uint32_t)(d.D >> 2));
+        store_partial(npart + d.nbase + (long long)tl * NW + warp, tp);
+    }
+}
+
+// One warp per trajectory: norm of the update, then advance the counter.
+template <bool PAIRS>
+__global__ void kb_norm(const TrajDev* tr, TrajState* ts, int n, const double* npart) {
+    const int lane = threadIdx.x & 31;
+    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (t >= n) return;
+    TrajState& s = ts[t];
+    if (!s.active) return;
+    const TrajDev& d = tr[t];
+    double acc = 0.0;
+    if (s.do_update) {
+        const int slots = d.pcnt * (PAIR_BS / 32);
+        for (int i = lane; i < slots; i += 32) {
+            const double* slot = npart + d.nbase + i;
+            if (PAIRS) {
+                const float2 hl = *reinterpret_cast<const float2*>(slot);
+                acc += (double)hl.x + (double)hl.y;
+            } else {
+                acc += *slot;
+            }
+        }
+        acc = warp_sum(acc);
+    }
+    if (lane == 0) {
+        if (s.do_update) s.norm2 = acc;
+        s.iter += 1;
+        s.active = (!s.converged && s.iter < d.len) ? 1 : 0;
+    }
+}
+
+template <typename T>
+__global__ void kb_scale(const TrajDev* tr, const TrajState* ts, const int4* items, int n_items) {
+    using V = typename C2<T>::type;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int4 w = items[it];
+        const TrajState& s = ts[w.x];
+        if (!s.do_update) continue;
+        const TrajDev& d = tr[w.x];
+        const double sc = 1.0 / sqrt(s.norm2);
+        V* psi = static_cast<V*>(d.psi);
+        for (int i = threadIdx.x; i < w.z; i += blockDim.x) {
+            V v = psi[w.y + i];
+            v.x = (T)((double)v.x * sc);
+            v.y = (T)((double)v.y * sc);
+            psi[w.y + i] = v;
+        }
+    }
+}
+
+template <typename K>
+int resident_grid(K kernel, int bs, int sms) {
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, bs, 0);
+    return std::max(1, per) * sms;
+}
+
+}  // namespace
+}  // namespace tq
+
+using namespace tq;
+
+struct tq_batch {
+    tq_ctx* ctx = nullptr;
+    int n = 0, prec = 0, max_len = 0, lpr = 32;
+    double eps = 0.0;
+    std::vector<TrajDev> td;
+    TrajDev* d_td = nullptr;
+    TrajState* d_ts = nullptr;
+    int4 *eitems = nullptr, *gitems = nullptr, *pitems = nullptr, *sitems = nullptr;
+    int n_e = 0, n_g = 0, n_p = 0, n_s = 0;
+    double* epart = nullptr;
+    double* npart = nullptr;
+    std::vector<void*> allocs;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int graph_lpr = -1;
+    int grid_e[4] = {1, 1, 1, 1};   // energy, per lanes-per-row 4, 8, 16, 32
+    int grid_g = 1, grid_p = 1;
+};
+
+namespace {
+
+template <typename T>
+T* dalloc(tq_batch* b, size_t n) {
+    T* p = static_cast<T*>(dev_alloc(std::max<size_t>(1, n) * sizeof(T)));
+    b->allocs.push_back(p);
+    return p;
+}
+
+template <typename T>
+T* dupload(tq_batch* b, const std::vector<T>& v) {
+    T* p = dalloc<T>(b, v.size());
+    if (!v.empty()) TQ_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return p;
+}
+
+template <typename T, typename VT>
+int launch_energy(tq_batch* b, cudaStream_t s) {
+    switch (b->lpr) {
+        case 4: kb_energy<T, VT, 4><<<b->grid_e[0], BT_BS, 0, s>>>(b->d_td, b->d_ts, b->eitems, b->n_e, b->epart); break;
+        case 8: kb_energy<T, VT, 8><<<b->grid_e[1], BT_BS, 0, s>>>(b->d_td, b->d_ts, b->eitems, b->n_e, b->epart); break;
+        case 16: kb_energy<T, VT, 16><<<b->grid_e[2], BT_BS, 0, s>>>(b->d_td, b->d_ts, b->eitems, b->n_e, b->epart); break;
+        default: kb_energy<T, VT, 32><<<b->grid_e[3], BT_BS, 0, s>>>(b->d_td, b->d_ts, b->eitems, b->n_e, b->epart); break;
+    }
+    return 1;
+}
+
+// Persistent grid sizes, computed once (no runtime query inside a capture).
+template <typename T, typename VT>
+void compute_grids(tq_batch* b) {
+    const int sms = b->ctx->sm_count;
+    b->grid_e[0] = std::min(b->n_e, resident_grid(kb_energy<T, VT, 4>, BT_BS, sms));
+    b->grid_e[1] = std::min(b->n_e, resident_grid(kb_energy<T, VT, 8>, BT_BS, sms));
+    b->grid_e[2] = std::min(b->n_e, resident_grid(kb_energy<T, VT, 16>, BT_BS, sms));
+    b->grid_e[3] = std::min(b->n_e, resident_grid(kb_energy<T, VT, 32>, BT_BS, sms));
+    b->grid_g = std::min(b->n_g, resident_grid(kb_grad<T>, BT_BS, sms));
+    b->grid_p = std::min(b->n_p, resident_grid(kb_pair<T>, PAIR_BS, sms));
+}
+
+template <typename T>
+int launch_reset(tq_batch* b, cudaStream_t s) {
+    const int grid = std::min(b->n_s, b->ctx->sm_count * 8);
+    kb_reset<T><<<std::max(1, grid), 256, 0, s>>>(b->d_td, b->d_ts, b->sitems, b->n_s);
+    return 1;
+}
+
+// One iteration of every trajectory: six launches.
+template <typename T, typename VT>
+void enqueue_iteration(tq_batch* b, cudaStream_t s) {
+    tq_ctx* c = b->ctx;
+    const int sms = c->sm_count;
+    launch(c, "batch_energy", s, [&] { return launch_energy<T, VT>(b, s); });
+    launch(c, "batch_gradients", s, [&] {
+        kb_grad<T><<<b->grid_g, BT_BS, 0, s>>>(b->d_td, b->d_ts, b->gitems, b->n_g);
+        return 1;
+    });
+    launch(c, "batch_select", s, [&] {
+        kb_select<<<(b->n * 32 + 255) / 256, 256, 0, s>>>(b->d_td, b->d_ts, b->n, b->eps, b->prec);
+        return 1;
+    });
+    launch(c, "batch_taylor5_pair", s, [&] {
+        kb_pair<T><<<b->grid_p, PAIR_BS, 0, s>>>(b->d_td, b->d_ts, b->pitems, b->n_p, b->npart);
+        return 1;
+    });
+    launch(c, "batch_norm", s, [&] {
+        kb_norm<sizeof(T) == 4><<<(b->n * 32 + 255) / 256, 256, 0, s>>>(b->d_td, b->d_ts, b->n, b->npart);
+        return 1;
+    });
+    launch(c, "batch_scale", s, [&] {
+        kb_scale<T><<<std::min(b->n_s, sms * 8), 256, 0, s>>>(b->d_td, b->d_ts, b->sitems, b->n_s);
+        return 1;
+    });
+}
+
+void enqueue_all(tq_batch* b, cudaStream_t s) {
+    for (int i = 0; i < b->max_len; ++i) {
+        if (b->prec == TQ_C128) enqueue_iteration<double, double>(b, s);
+        else enqueue_iteration<float, float>(b, s);
+    }
+}
+
+void reset(tq_batch* b, cudaStream_t s) {
+    launch(b->ctx, "batch_reset", s, [&] {
+        return b->prec == TQ_C128 ? launch_reset<double>(b, s) : launch_reset<float>(b, s);
+    });
+}
+
+void drop_graph(tq_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->graph_lpr = -1;
+}
+
+}  // namespace
+
+extern "C" int tq_batch_create(tq_ctx* c, int n_traj, tq_ham* const* hams, tq_pool* const* pools,
+                               const int* n_electrons, const int* mappings, const int* lengths,
+                               const double* thetas, double eps, tq_batch** out) {
+    API_BEGIN
+    TQ_REQUIRE(c && hams && pools && n_electrons && mappings && lengths && thetas && out, "null argument");
+    TQ_REQUIRE(n_traj >= 1, "n_traj must be >= 1");
+    TQ_REQUIRE(std::isfinite(eps) && eps >= 0.0, "eps must be finite and >= 0");
+    *out = nullptr;
+    TQ_CUDA(cudaSetDevice(c->device));
+    auto* b = new tq_batch();
+    try {
+        b->ctx = c;
+        b->n = n_traj;
+        b->eps = eps;
+        b->prec = hams[0]->prec;
+        std::vector<int4> ei, gi, pi, si;
+        long long nslots = 0, toff = 0;
+        for (int t = 0; t < n_traj; ++t) {
+            const tq_ham* h = hams[t];
+            const tq_pool* p = pools[t];
+            TQ_REQUIRE(h && p, "null Hamiltonian or pool handle");
+            TQ_REQUIRE(h->prec == b->prec, "all Hamiltonians must share one precision");
+            TQ_REQUIRE(h->nq == p->nq, "Hamiltonian and pool qubit counts differ");
+            TQ_REQUIRE(lengths[t] >= 0, "negative trajectory length");
+            for (int i = 0; i < lengths[t]; ++i)
+                TQ_REQUIRE(std::isfinite(thetas[toff + i]), "non-finite angle");
+            TrajDev d{};
+            d.nq = h->nq;
+            d.D = h->D;
+            d.M = p->M;
+            d.len = lengths[t];
+            d.hf = (long long)hf_index(h->nq, n_electrons[t], mappings[t]);
+            d.diag = h->view.diag;
+            d.rowptr = h->view.rowptr;
+            d.col = h->view.col;
+            d.val = h->view.val;
+            d.pool = p->view;
+            d.chunk = (int)std::min<long long>(d.D, 2048);
+            d.nch = (int)(d.D / d.chunk);
+            d.eoff = (int)ei.size();
+            for (long long r = 0; r < d.D; r += ROWS_PER_ITEM)
+                ei.push_back(make_int4(t, (int)r, (int)std::min<long long>(ROWS_PER_ITEM, d.D - r), 0));
+            d.ecnt = (int)ei.size() - d.eoff;
+            for (int k = 0; k < d.M; ++k)
+                for (int ch = 0; ch < d.nch; ++ch) gi.push_back(make_int4(t, k, ch, 0));
+            const long long units = d.D >> 2;
+            d.pcnt = (int)((units + PAIR_BS * BT_UPT - 1) / (PAIR_BS * BT_UPT));
+            for (int tl = 0; tl < d.pcnt; ++tl) pi.push_back(make_int4(t, tl, 0, 0));
+            d.nbase = nslots;
+            nslots += (long long)d.pcnt * (PAIR_BS / 32);
+            for (long long r = 0; r < d.D; r += 4096)
+                si.push_back(make_int4(t, (int)r, (int)std::min<long long>(4096, d.D - r), 0));
+            const size_t es = b->prec == TQ_C128 ? 16 : 8;
+            d.psi = dalloc<unsigned char>(b, (size_t)d.D * es);
+            d.w = dalloc<double2>(b, (size_t)d.D);
+            d.thetas = dupload(b, std::vector<double>(thetas + toff, thetas + toff + d.len));
+            toff += d.len;
+            d.g = dalloc<double>(b, d.M);
+            d.gpart = dalloc<double>(b, (size_t)d.M * d.nch);
+            d.gtick = dalloc<unsigned>(b, d.M);
+            TQ_CUDA(cudaMemset(d.gtick, 0, d.M * sizeof(unsigned)));
+            d.res_e = dalloc<double>(b, std::max(1, d.len));
+            d.res_g = dalloc<double>(b, std::max(1, d.len));
+            d.res_th = dalloc<double>(b, std::max(1, d.len));
+            d.res_sel = dalloc<int>(b, std::max(1, d.len));
+            b->max_len = std::max(b->max_len, d.len);
+            b->td.push_back(d);
+        }
+        b->eitems = dupload(b, ei);
+        b->gitems = dupload(b, gi);
+        b->pitems = dupload(b, pi);
+        b->sitems = dupload(b, si);
+        b->n_e = (int)ei.size();
+        b->n_g = (int)gi.size();
+        b->n_p = (int)pi.size();
+        b->n_s = (int)si.size();
+        b->epart = dalloc<double>(b, 2 * ei.size());
+        b->npart = dalloc<double>(b, (size_t)nslots);
+        b->d_td = dupload(b, b->td);
+        b->d_ts = dalloc<TrajState>(b, n_traj);
+        TQ_CUDA(cudaMemset(b->d_ts, 0, n_traj * sizeof(TrajState)));
+        TQ_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+        if (b->prec == TQ_C128) compute_grids<double, double>(b);
+        else compute_grids<float, float>(b);
+    } catch (...) {
+        tq_batch_free(b);
+        throw;
+    }
+    *out = b;
+    API_END
+}
+
+extern "C" int tq_batch_set_schedule(tq_batch* b, int lanes_per_row) {
+    API_BEGIN
+    TQ_REQUIRE(b != nullptr, "batch is null");
+    TQ_REQUIRE(lanes_per_row == 4 || lanes_per_row == 8 || lanes_per_row == 16 || lanes_per_row == 32,
+               "lanes_per_row must be 4, 8, 16 or 32");
+    b->lpr = lanes_per_row;
+    API_END
+}
+
+extern "C" int tq_batch_autotune(tq_batch* b, int* lanes_per_row, double* best_ms) {
+    API_BEGIN
+    TQ_REQUIRE(b != nullptr, "batch is null");
+    TQ_CUDA(cudaSetDevice(b->ctx->device));
+    cudaStream_t s = b->cap;
+    cudaEvent_t e0, e1;
+    TQ_CUDA(cudaEventCreate(&e0));
+    TQ_CUDA(cudaEventCreate(&e1));
+    int best = b->lpr;
+    float best_t = 1e30f;
+    for (int l : {4, 8, 16, 32}) {
+        b->lpr = l;
+        reset(b, s);
+        auto one = [&] {
+            launch(b->ctx, "autotune_batch_energy", s, [&] {
+                return b->prec == TQ_C128 ? launch_energy<double, double>(b, s) : launch_energy<float, float>(b, s);
+            });
+        };
+        one();
+        TQ_CUDA(cudaEventRecord(e0, s));
+        for (int r = 0; r < 3; ++r) one();
+        TQ_CUDA(cudaEventRecord(e1, s));
+        TQ_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        TQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        ms /= 3.f;
+        if (ms < best_t) {
+            best_t = ms;
+            best = l;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->lpr = best;
+    if (lanes_per_row) *lanes_per_row = best;
+    if (best_ms) *best_ms = best_t;
+    API_END
+}
+
+extern "C" int tq_batch_run(tq_batch* b, int use_graph, void* stream) {
+    API_BEGIN
+    TQ_REQUIRE(b != nullptr, "batch is null");
+    TQ_CUDA(cudaSetDevice(b->ctx->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    reset(b, s);
+    if (!use_graph) {
+        enqueue_all(b, s);
+        return TQ_OK;
+    }
+    if (!b->exec || b->graph_lpr != b->lpr) {
+        drop_graph(b);
+        // capture on the batch's own stream, after the reset so that no
+        // host-side check inside a launch sees a capturing stream
+        TQ_CUDA(cudaStreamSynchronize(s));
+        const int tracing = b->ctx->tracing;
+        b->ctx->tracing = 0;   // no event records inside the graph
+        TQ_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+        try {
+            enqueue_all(b, b->cap);
+        } catch (...) {
+            cudaGraph_t g = nullptr;
+            cudaStreamEndCapture(b->cap, &g);
+            if (g) cudaGraphDestroy(g);
+            b->ctx->tracing = tracing;
+            throw;
+        }
+        b->ctx->tracing = tracing;
+        TQ_CUDA(cudaStreamEndCapture(b->cap, &b->graph));
+        TQ_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
+        b->graph_lpr = b->lpr;
+        b->ctx->launches -= 6ll * b->max_len;   // counted again at each replay below
+    }
+    {
+        Traced t(b->ctx, "batch_graph", s);
+        TQ_CUDA(cudaGraphLaunch(b->exec, s));
+    }
+    b->ctx->launches += 6ll * b->max_len;
+    API_END
+}
+
+extern "C" int tq_batch_results(const tq_batch* b, int* n_iter, int* converged, double* energy,
+                                double* max_grad, int* selected, double* theta) {
+    API_BEGIN
+    TQ_REQUIRE(b != nullptr, "batch is null");
+    TQ_CUDA(cudaSetDevice(b->ctx->device));
+    TQ_CUDA(cudaDeviceSynchronize());
+    std::vector<TrajState> hs(b->n);
+    TQ_CUDA(cudaMemcpy(hs.data(), b->d_ts, b->n * sizeof(TrajState), cudaMemcpyDeviceToHost));
+    long long off = 0;
+    for (int t = 0; t < b->n; ++t) {
+        const TrajDev& d = b->td[t];
+        if (n_iter) n_iter[t] = hs[t].iter;
+        if (converged) converged[t] = hs[t].converged;
+        const size_t L = (size_t)d.len;
+        if (L) {
+            if (energy) TQ_CUDA(cudaMemcpy(energy + off, d.res_e, L * sizeof(double), cudaMemcpyDeviceToHost));
+            if (max_grad) TQ_CUDA(cudaMemcpy(max_grad + off, d.res_g, L * sizeof(double), cudaMemcpyDeviceToHost));
+            if (selected) TQ_CUDA(cudaMemcpy(selected + off, d.res_sel, L * sizeof(int), cudaMemcpyDeviceToHost));
+            if (theta) TQ_CUDA(cudaMemcpy(theta + off, d.res_th, L * sizeof(double), cudaMemcpyDeviceToHost));
+        }
+        off += d.len;
+    }
+    API_END
+}
+
+extern "C" int tq_batch_state(const tq_batch* b, int t, void** dev_ptr, int* n_qubits) {
+    API_BEGIN
+    TQ_REQUIRE(b != nullptr, "batch is null");
+    TQ_REQUIRE(t >= 0 && t < b->n, "trajectory index out of range");
+    if (dev_ptr) *dev_ptr = b->td[t].psi;
+    if (n_qubits) *n_qubits = b->td[t].nq;
+    API_END
+}
+
+extern "C" int tq_batch_free(tq_batch* b) {
+    if (!b) return TQ_OK;
+    if (b->ctx) cudaSetDevice(b->ctx->device);
+    cudaDeviceSynchronize();
+    drop_graph(b);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    for (void* p : b->allocs) cudaFree(p);
+    delete b;
+    return TQ_OK;
+}

@@ -1,0 +1,252 @@
+// Device code of the fused Taylor-5 pair update (Sec. III-C, Eqs. (6)-(8)),
+// shared by the single, batched and trajectory-batch kernels.
+#pragma once
+
+#include "dev.cuh"
+
+namespace tq {
+
+constexpr int PAIR_BS = 256;
+
+__device__ __forceinline__ void load2(const float2* p, uint32_t i, float2& a, float2& b) {
+    const float4 v = *reinterpret_cast<const float4*>(p + i);
+    a = make_float2(v.x, v.y);
+    b = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void store2(float2* p, uint32_t i, float2 a, float2 b) {
+    *reinterpret_cast<float4*>(p + i) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void load2(const double2* p, uint32_t i, double2& a, double2& b) {
+    a = p[i];
+    b = p[i + 1];
+}
+__device__ __forceinline__ void store2(double2* p, uint32_t i, double2 a, double2 b) {
+    p[i] = a;
+    p[i + 1] = b;
+}
+
+template <typename V, typename T>
+__device__ __forceinline__ V scal(T s, V v) {
+    V o;
+    o.x = s * v.x;
+    o.y = s * v.y;
+    return o;
+}
+template <typename V, typename T>
+__device__ __forceinline__ void axpy(V& acc, T c, V v) {
+    acc.x = fma(c, v.x, acc.x);
+    acc.y = fma(c, v.y, acc.y);
+}
+
+// Five chained products on one closed pair (r, q = r ^ x) with
+// s_r = A[r][q], s_q = A[q][r]; returns the accumulated pair in (ar, aq).
+template <typename V, typename T>
+__device__ __forceinline__ void chain_pair(T s_r, T s_q, const T (&cf)[6], V& ar, V& aq) {
+    V vr = ar, vq = aq;
+#pragma unroll
+    for (int k = 1; k <= 5; ++k) {
+        const V nr = scal(s_r, vq);   // (A v)[r] = A[r][q] v[q]
+        const V nq = scal(s_q, vr);   // (A v)[q] = A[q][r] v[r]
+        vr = nr;
+        vq = nq;
+        axpy(ar, cf[k], vr);
+        axpy(aq, cf[k], vq);
+    }
+}
+
+// complex64: the same chain on Blackwell's packed float32x2 pipe (one
+// instruction per complex multiply-by-real or multiply-add, rounding as the
+// scalar form).
+__device__ __forceinline__ void chain_pair(float s_r, float s_q, const float (&cf)[6], float2& ar,
+                                           float2& aq) {
+    const float2 sr = make_float2(s_r, s_r), sq = make_float2(s_q, s_q);
+    float2 vr = ar, vq = aq;
+#pragma unroll
+    for (int k = 1; k <= 5; ++k) {
+        const float2 nr = __fmul2_rn(sr, vq);
+        const float2 nq = __fmul2_rn(sq, vr);
+        vr = nr;
+        vq = nq;
+        const float2 c = make_float2(cf[k], cf[k]);
+        ar = __ffma2_rn(c, vr, ar);
+        aq = __ffma2_rn(c, vq, aq);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void taylor_coefs(double theta, T (&cf)[6]) {
+    double c = 1.0;
+    cf[0] = T(1);
+#pragma unroll
+    for (int k = 1; k <= 5; ++k) {
+        c = c * theta / (double)k;
+        cf[k] = (T)c;
+    }
+}
+
+// theta^k / k! for k = 0..5 in the kernel's own precision: powers by
+// multiplication and constant reciprocal factorials (no division).  The
+// complex64 path stays entirely on the float32 pipes: float64 issues at
+// about 1/57 of the float32 rate on this part.
+template <typename T>
+__device__ __forceinline__ void taylor_coefs_fast(double theta, T (&cf)[6]) {
+    const T t = (T)theta;
+    const T t2 = t * t, t3 = t2 * t, t4 = t3 * t, t5 = t4 * t;
+    cf[0] = T(1);
+    cf[1] = t;
+    cf[2] = t2 * T(0.5);
+    cf[3] = t3 * T(1.0 / 6.0);
+    cf[4] = t4 * T(1.0 / 24.0);
+    cf[5] = t5 * T(1.0 / 120.0);
+}
+
+// Per-warp norm partial: float64 sum for complex128; for complex64 a
+// TwoSum-compensated float32 warp sum stored as a (hi, lo) float pair in
+// the 8-byte slot and widened to float64 by the reduction kernel.
+__device__ __forceinline__ void store_partial(double* slot, double v) {
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) *slot = v;
+}
+__device__ __forceinline__ void store_partial(double* slot, float v) {
+    float hi = v, lo = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_down_sync(0xffffffffu, hi, o);
+        const float ol = __shfl_down_sync(0xffffffffu, lo, o);
+        float sum, err;
+        two_sum(hi, oh, sum, err);
+        hi = sum;
+        lo = lo + ol + err;
+    }
+    if ((threadIdx.x & 31) == 0) *reinterpret_cast<float2*>(slot) = make_float2(hi, lo);
+}
+__device__ __forceinline__ void store_nan_partial(double* slot, double) {
+    if ((threadIdx.x & 31) == 0) *slot = __longlong_as_double(0x7ff8000000000000ll);
+}
+__device__ __forceinline__ void store_nan_partial(double* slot, float) {
+    if ((threadIdx.x & 31) == 0) *reinterpret_cast<float2*>(slot) = make_float2(__int_as_float(0x7fc00000), 0.f);
+}
+
+// One pool generator as staged in shared memory: X-mask, the factored sign
+// form (A[r][r^x] = c0 (-1)^{parity(col & z0)} if parity(col & d_i) == t_i
+// for all i, else 0, with col = r ^ x), and the parities of
+// {0, 1, x, x ^ 1} against (d0, d1, d2, z0) so that one set of popcounts at
+// r0 gives the values of all four rows of a unit.
+template <typename T>
+struct OpRec {
+    uint32_t x, z0, d0, d1, d2;
+    int t;        // target parities (bits 0..2)
+    int dcode;    // 4 x 4-bit parity codes of delta in {0, 1, x, x^1}
+    T c0;
+};
+
+template <typename T>
+__device__ __forceinline__ OpRec<T> make_rec(const PoolView& p, int k) {
+    OpRec<T> o;
+    o.x = p.x[k];
+    o.z0 = p.fz0[k];
+    o.d0 = p.fd[3 * k];
+    o.d1 = p.fd[3 * k + 1];
+    o.d2 = p.fd[3 * k + 2];
+    o.t = p.ft[k];
+    o.c0 = sizeof(T) == 4 ? (T)p.fc0f[k] : (T)p.fc0d[k];
+    const uint32_t dl[4] = {0u, 1u, o.x, o.x ^ 1u};
+    int code = 0;
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t d = dl[j];
+        const int c = parity32(d & o.d0) | (parity32(d & o.d1) << 1) | (parity32(d & o.d2) << 2) |
+                      (parity32(d & o.z0) << 3);
+        code |= c << (4 * j);
+    }
+    o.dcode = code;
+    return o;
+}
+
+// Value A[row][col] given the parity code of col.
+template <typename T>
+__device__ __forceinline__ T rec_value(const OpRec<T>& o, int code) {
+    return (code & 7) != o.t ? T(0) : ((code & 8) ? -o.c0 : o.c0);
+}
+
+template <typename T>
+__device__ __forceinline__ int base_code(const OpRec<T>& o, uint32_t r) {
+    return parity32(r & o.d0) | (parity32(r & o.d1) << 1) | (parity32(r & o.d2) << 2) |
+           (parity32(r & o.z0) << 3);
+}
+
+// One tile of the pair update: units tl*TU .. tl*TU+TU-1 of a state at
+// `base` (4 amplitudes per unit), generator `op`, angle theta.  Loads every
+// unit of the thread first, then runs the five-product chains and stores.
+// Returns the thread's float32 (complex64) or float64 sum of |psi'|^2.
+template <typename T, int UPT>
+__device__ __forceinline__ T pair_tile(const OpRec<T>& op, double theta,
+                                       typename C2<T>::type* base, uint32_t tl, uint32_t units) {
+    using V = typename C2<T>::type;
+    constexpr int TU = PAIR_BS * UPT;
+    T cf[6];
+    taylor_coefs_fast<T>(theta, cf);
+    const uint32_t x = op.x;
+    const int hb = 31 - __clz(x);
+    V e0[UPT], e1[UPT], f0[UPT], f1[UPT];
+    uint32_t r0s[UPT];
+    bool ok[UPT];
+#pragma unroll
+    for (int j = 0; j < UPT; ++j) {
+        const uint32_t u = (uint32_t)tl * TU + j * PAIR_BS + threadIdx.x;
+        ok[j] = u < units;
+        if (!ok[j]) continue;
+        if (hb > 0) {
+            const uint32_t r0 = insert_zero(2u * u, hb);
+            r0s[j] = r0;
+            load2(base, r0, e0[j], e1[j]);
+            load2(base, (r0 ^ x) & ~1u, f0[j], f1[j]);
+        } else {
+            const uint32_t r0 = 4u * u;
+            r0s[j] = r0;
+            load2(base, r0, e0[j], f0[j]);
+            load2(base, r0 + 2u, e1[j], f1[j]);
+        }
+    }
+    T tpart = T(0);
+#pragma unroll
+    for (int j = 0; j < UPT; ++j) {
+        if (!ok[j]) continue;
+        const uint32_t r0 = r0s[j];
+        if (hb > 0) {
+            // rows r0, r0+1 and partners q0 = r0^x, q0^1; their columns
+            // are r0 ^ {x, x^1, 0, 1}
+            const uint32_t q0 = r0 ^ x;
+            const int bc = base_code(op, r0);
+            const T s_r0 = rec_value(op, bc ^ ((op.dcode >> 8) & 15));    // col q0
+            const T s_r1 = rec_value(op, bc ^ ((op.dcode >> 12) & 15));   // col q0^1
+            const T s_q0 = rec_value(op, bc ^ (op.dcode & 15));           // col r0
+            const T s_q1 = rec_value(op, bc ^ ((op.dcode >> 4) & 15));    // col r0+1
+            V a0 = e0[j], a1 = e1[j];
+            V b0 = (q0 & 1u) ? f1[j] : f0[j];   // psi[q0]
+            V b1 = (q0 & 1u) ? f0[j] : f1[j];   // psi[q0 ^ 1]
+            chain_pair(s_r0, s_q0, cf, a0, b0);
+            chain_pair(s_r1, s_q1, cf, a1, b1);
+            tpart += a0.x * a0.x + a0.y * a0.y + a1.x * a1.x + a1.y * a1.y;
+            tpart += b0.x * b0.x + b0.y * b0.y + b1.x * b1.x + b1.y * b1.y;
+            store2(base, r0, a0, a1);
+            if (q0 & 1u) store2(base, q0 & ~1u, b1, b0);
+            else store2(base, q0 & ~1u, b0, b1);
+        } else {
+            // x == 1: pairs (r0, r0+1) and (r0+2, r0+3)
+            const int b0c = base_code(op, r0), b2c = base_code(op, r0 + 2u);
+            const T s_r0 = rec_value(op, b0c ^ ((op.dcode >> 4) & 15));  // col r0+1
+            const T s_q0 = rec_value(op, b0c);                           // col r0
+            const T s_r1 = rec_value(op, b2c ^ ((op.dcode >> 4) & 15));  // col r0+3
+            const T s_q1 = rec_value(op, b2c);                           // col r0+2
+            chain_pair(s_r0, s_q0, cf, e0[j], f0[j]);
+            chain_pair(s_r1, s_q1, cf, e1[j], f1[j]);
+            tpart += e0[j].x * e0[j].x + e0[j].y * e0[j].y + f0[j].x * f0[j].x + f0[j].y * f0[j].y;
+            tpart += e1[j].x * e1[j].x + e1[j].y * e1[j].y + f1[j].x * f1[j].x + f1[j].y * f1[j].y;
+            store2(base, r0, e0[j], f0[j]);
+            store2(base, r0 + 2u, e1[j], f1[j]);
+        }
+    }
+    return tpart;
+}
+
+}  // namespace tq
