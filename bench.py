@@ -347,6 +347,7 @@ def measure_spmv(tq, ctx, nq):
     pool = tq.build_pool(ctx, n, ne, 1)
     for k in range(0, pool.M, max(1, pool.M // 8)):
         tq.evolve_taylor5(ctx, pool, k, 0.1, st, renormalize=True)
+    lanes, _ = tq.autotune_spmv(ctx, ham, st)
     for _ in range(3):
         tq.energy(ctx, ham, st)
     ctx.trace(True)
@@ -363,7 +364,7 @@ def measure_spmv(tq, ctx, nq):
     return {"workload": f"energy of a {nq}-qubit BK Hamiltonian (synthetic, {n} orbitals, "
                         f"{ne} electrons), complex64 state, float32 CSR + float64 diagonal",
             "kernel": "k_energy_csr<float,float>", "nnz": ham.nnz, "hamiltonian_bytes": ham.device_bytes,
-            "build_s": build_s, "ms_per_energy": ms,
+            "build_s": build_s, "ms_per_energy": ms, "lanes_per_row": lanes,
             "algorithmic_bytes": alg, "achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak,
             "energy": e, "l2_policy": "CSR larger than L2"}
 
@@ -398,12 +399,19 @@ def measure_trajectories(tq, ctx, n_traj):
     ms = e0.elapsed_time(e1) / runs
     res = b.results()
     iters = sum(r["n_iter"] for r in res)
+    # one more, untimed run without the graph, traced per kernel
+    ctx.trace(True)
+    b.run(use_graph=False)
+    split = ctx.trace_report()
+    ctx.trace(False)
     return {"workload": f"{n_traj} ADAPT trajectories, qubits uniform over 10-16, JW/BK 50/50, "
                         "own integrals (seeds 1000+i), angle lists of 1-30 from N(0,0.1), eps 1e-3, "
                         "complex64 with float64 reductions",
             "build_s": build_s, "lanes_per_row": lpr, "ms_per_run": ms,
             "iterations_per_run": iters, "iterations_per_s": iters / (ms * 1e-3),
-            "converged": int(sum(r["converged"] for r in res)), "graph_launches_per_run": 6 * max(len(t.thetas) for t in trajs)}
+            "converged": int(sum(r["converged"] for r in res)),
+            "graph_launches_per_run": 6 * max(len(t.thetas) for t in trajs),
+            "kernel_ms_untimed_direct_run": {k: round(v[1], 3) for k, v in split.items()}}
 
 
 def main():

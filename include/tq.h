@@ -107,6 +107,13 @@ int tq_ctx_get_pair_schedule(const tq_ctx* ctx, int prec, int* units_per_thread)
 int tq_autotune_pair(tq_ctx* ctx, const tq_pool* pool, int prec, int n_states,
                      int* best_units_per_thread, double* best_ms);
 
+/* Lanes that share one Hamiltonian row in the energy SpMV (4, 8, 16, 32;
+ * default 32), and its autotuner: times tq_energy's launch at each value on
+ * (ham, psi), keeps the fastest.  Synchronises the device. */
+int tq_ctx_set_spmv_schedule(tq_ctx* ctx, int lanes_per_row);
+int tq_autotune_spmv(tq_ctx* ctx, const tq_ham* ham, const tq_state* psi,
+                     int* best_lanes_per_row, double* best_ms);
+
 /* ------------------------------------------------- host-side construction */
 
 /* Qubit Hamiltonian as a Pauli sum (Eq. (3)) from the fermionic Hamiltonian

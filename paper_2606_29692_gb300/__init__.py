@@ -20,7 +20,7 @@ __all__ = [
     "pauli_hamiltonian", "pool_excitations", "pauli_pool", "hf_index", "build_hamiltonian",
     "build_pool", "evolve_taylor5", "evolve_taylor5_csr", "energy", "energy_matrix_free",
     "pool_gradients", "adapt_step", "evolve_taylor5_batch", "evolve_taylor5_batch_host",
-    "state_set_hf", "pool_csr", "ham_csr", "lib", "autotune_pair", "energy_noalloc", "Batch",
+    "state_set_hf", "pool_csr", "ham_csr", "lib", "autotune_pair", "energy_noalloc", "Batch", "autotune_spmv",
 ]
 
 
@@ -113,6 +113,9 @@ class Context:
         u = C.c_int()
         call("tq_ctx_get_pair_schedule", self.handle, prec, C.byref(u))
         return u.value
+
+    def set_spmv_schedule(self, lanes_per_row):
+        call("tq_ctx_set_spmv_schedule", self.handle, int(lanes_per_row))
 
     def trace(self, enable=True):
         """Bracket every kernel launch with CUDA events on its stream."""
@@ -303,6 +306,13 @@ def autotune_pair(ctx, pool, prec=TQ_C64, n_states=1024):
     u, ms = C.c_int(), C.c_double()
     call("tq_autotune_pair", ctx.handle, pool.handle, prec, int(n_states), C.byref(u), C.byref(ms))
     return u.value, ms.value
+
+
+def autotune_spmv(ctx, ham, state):
+    """Time every energy-SpMV schedule on (ham, state); set and return (lanes, ms)."""
+    l, ms = C.c_int(), C.c_double()
+    call("tq_autotune_spmv", ctx.handle, ham.handle, state.handle, C.byref(l), C.byref(ms))
+    return l.value, ms.value
 
 
 def evolve_taylor5_batch(ctx, pool, psi, k, theta, norm2=None, prec=TQ_C64, stream=None):

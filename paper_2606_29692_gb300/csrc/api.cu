@@ -2,6 +2,7 @@
 // handle lifetime, device memory, and the launch sequences of each call.
 #include "dev.cuh"
 #include "host_util.h"
+#include "grad.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -45,7 +46,10 @@ unsigned* tickets(tq_ctx* c, size_t n) {
     return c->tickets;
 }
 
-enum { S_PART = 0, S_W0, S_U1, S_U2, S_W1, S_W2, S_G, S_STAGE };
+enum { S_PART = 0, S_W0, S_U1, S_U2, S_W1, S_W2, S_G, S_STAGE, S_W32 };
+
+void run_energy(tq_ctx* c, const tq_ham* h, const tq_state* psi, double* part, cudaStream_t s);
+double* prepare(tq_ctx* c, long long D, const tq_pool* p, int nq);
 
 size_t elem_bytes(int prec) { return prec == TQ_C128 ? 16 : 8; }
 
@@ -142,7 +146,7 @@ extern "C" int tq_ctx_destroy(tq_ctx* c) {
     if (!c) return TQ_OK;
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 10; ++i)
         if (c->scratch[i]) cudaFree(c->scratch[i]);
     if (c->step) cudaFree(c->step);
     if (c->tickets) cudaFree(c->tickets);
@@ -232,6 +236,50 @@ extern "C" int tq_autotune_pair(tq_ctx* c, const tq_pool* p, int prec, int n_sta
     cudaEventDestroy(e1);
     c->pair_upt[prec] = best;
     if (best_upt) *best_upt = best;
+    if (best_ms) *best_ms = best_t;
+    API_END
+}
+
+extern "C" int tq_ctx_set_spmv_schedule(tq_ctx* c, int lanes_per_row) {
+    API_BEGIN
+    TQ_REQUIRE(c != nullptr, "ctx is null");
+    TQ_REQUIRE(lanes_per_row == 4 || lanes_per_row == 8 || lanes_per_row == 16 || lanes_per_row == 32,
+               "lanes_per_row must be 4, 8, 16 or 32");
+    c->spmv_lanes = lanes_per_row;
+    API_END
+}
+
+extern "C" int tq_autotune_spmv(tq_ctx* c, const tq_ham* h, const tq_state* psi, int* best_lanes,
+                                double* best_ms) {
+    API_BEGIN
+    TQ_REQUIRE(c && h && psi, "null argument");
+    TQ_REQUIRE(h->nq == psi->nq && h->prec == psi->prec, "state and Hamiltonian do not match");
+    set_device(c);
+    double* part = prepare(c, h->D, nullptr, h->nq);
+    cudaEvent_t e0, e1;
+    TQ_CUDA(cudaEventCreate(&e0));
+    TQ_CUDA(cudaEventCreate(&e1));
+    int best = c->spmv_lanes;
+    float best_t = 1e30f;
+    for (int l : {4, 8, 16, 32}) {
+        c->spmv_lanes = l;
+        run_energy(c, h, psi, part, 0);
+        TQ_CUDA(cudaEventRecord(e0, 0));
+        for (int r = 0; r < 3; ++r) run_energy(c, h, psi, part, 0);
+        TQ_CUDA(cudaEventRecord(e1, 0));
+        TQ_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        TQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        ms /= 3.f;
+        if (ms < best_t) {
+            best_t = ms;
+            best = l;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->spmv_lanes = best;
+    if (best_lanes) *best_lanes = best;
     if (best_ms) *best_ms = best_t;
     API_END
 }
@@ -465,6 +513,8 @@ extern "C" int tq_build_pool(tq_ctx* c, int n_spatial, int n_electrons, int mapp
         std::vector<uint32_t> x(M), z(8 * M, 0), fz0(M, 0), fd(3 * M, 0);
         std::vector<int> nterm(M), fok(M, 0), fm(M, 0), ft(M, 0);
         std::vector<float> cf(8 * M, 0.f), fc0f(M, 0.f);
+        std::vector<int4> supp(M);
+        std::vector<uint32_t> supe(3 * M, 0);
         std::vector<double> cd(8 * M, 0.0), fc0d(M, 0.0);
         p->idx4.resize(4 * M);
         p->terms.assign(8 * M, PauliTerm{0, 0, 0.0});
@@ -491,6 +541,9 @@ extern "C" int tq_build_pool(tq_ctx* c, int n_spatial, int n_electrons, int mapp
                 ft[k] = f.t;
                 fc0d[k] = f.c0;
                 fc0f[k] = (float)f.c0;
+                SupportForm sf = support_form(f, t[0].x);
+                supp[k] = make_int4(sf.m | (sf.target << 8), sf.p[0] | (sf.p[1] << 8) | (sf.p[2] << 16), 0, 0);
+                for (int i = 0; i < 3; ++i) supe[3 * k + i] = (uint32_t)sf.e[i];
             }
         }
         p->nterm = nterm;
@@ -509,6 +562,21 @@ extern "C" int tq_build_pool(tq_ctx* c, int n_spatial, int n_electrons, int mapp
         v.ft = upload(p->allocs, ft);
         v.fc0f = upload(p->allocs, fc0f);
         v.fc0d = upload(p->allocs, fc0d);
+        v.supp = upload(p->allocs, supp);
+        v.supe = upload(p->allocs, supe);
+        // gradient work items: (op, chunk of its support rows)
+        std::vector<int2> gitems;
+        std::vector<int> gfirst;
+        for (int k = 0; k < M; ++k) {
+            gfirst.push_back((int)gitems.size());
+            const int m = supp[k].x & 0xff;
+            const long long size = (1ll << p->nq) >> m;
+            for (long long u = 0, ch = 0; u < size; u += GRAD_CHUNK, ++ch) gitems.push_back(make_int2(k, (int)ch));
+        }
+        gfirst.push_back((int)gitems.size());
+        v.gitems = upload(p->allocs, gitems);
+        v.gfirst = upload(p->allocs, gfirst);
+        v.n_gitems = (int)gitems.size();
         for (int q = 0; q < 2; ++q) {
             p->csr_rowptr[q].assign(M, nullptr);
             p->csr_col[q].assign(M, nullptr);
@@ -707,13 +775,9 @@ extern "C" int tq_evolve_taylor5_csr(tq_ctx* c, int n_qubits, const int* rowptr,
 namespace {
 
 // Partials needed by energy + gradients (+ line search) on this problem.
-size_t partials_needed(long long D, int M, int nq, int sms) {
+size_t partials_needed(long long D, int n_gitems, int nq, int sms) {
     size_t n = (size_t)energy_grid(D, sms) * 2;
-    if (M > 0) {
-        int nch, chunk;
-        grad_layout(nq, &nch, &chunk);
-        n = std::max(n, (size_t)M * nch);
-    }
+    n = std::max(n, (size_t)std::max(n_gitems, 0));
     n = std::max(n, (size_t)512 * 5);
     n = std::max(n, (size_t)taylor5_pair_parts(nq, 1));
     return n + 8;
@@ -723,23 +787,30 @@ void run_energy(tq_ctx* c, const tq_ham* h, const tq_state* psi, double* part, c
     TQ_REQUIRE(h->nq == psi->nq, "state and Hamiltonian qubit counts differ");
     TQ_REQUIRE(h->prec == psi->prec, "state and Hamiltonian precisions differ");
     double2* w = static_cast<double2*>(c->scratch[S_W0]);
-    launch(c, "energy_csr", s, [&] { return launch_energy_csr(h->view, psi->data, psi->prec, w, part, c->tickets, c->step,
-                                      c->sm_count, s); });
+    float2* w32 = psi->prec == TQ_C64 ? static_cast<float2*>(c->scratch[S_W32]) : nullptr;
+    launch(c, "energy_csr", s, [&] { return launch_energy_csr2(h->view, psi->data, psi->prec, w, w32, part,
+                                                               c->tickets, c->step, c->sm_count, s,
+                                                               c->spmv_lanes); });
 }
 
 void run_gradients(tq_ctx* c, const tq_ham* h, const tq_pool* p, const tq_state* psi, double* g,
                    double* part, cudaStream_t s) {
     TQ_REQUIRE(p->nq == psi->nq, "state and pool qubit counts differ");
     run_energy(c, h, psi, part, s);
-    launch(c, "pool_gradients", s, [&] { return launch_pool_gradients(p->view, static_cast<double2*>(c->scratch[S_W0]), psi->data,
-                                          psi->prec, c->step, part, c->tickets + 16, g, c->sm_count, s); });
+    launch(c, "pool_gradients", s, [&] {
+        return launch_pool_gradients(p->view, static_cast<double2*>(c->scratch[S_W0]),
+                                     static_cast<float2*>(c->scratch[S_W32]), psi->data, psi->prec, c->step,
+                                     part, c->tickets + 16, g, c->sm_count, s);
+    });
 }
 
 // Allocate (before any launch of the call) the scratch energy/gradients use.
-double* prepare(tq_ctx* c, long long D, int M, int nq) {
+double* prepare(tq_ctx* c, long long D, const tq_pool* p, int nq) {
     scratch(c, S_W0, (size_t)D * sizeof(double2));
-    tickets(c, 16 + (size_t)std::max(M, 0) + 64);
-    return static_cast<double*>(scratch(c, S_PART, partials_needed(D, M, nq, c->sm_count) * sizeof(double)));
+    scratch(c, S_W32, (size_t)D * sizeof(float2));
+    tickets(c, 16 + (size_t)(p ? p->M : 0) + 64);
+    return static_cast<double*>(
+        scratch(c, S_PART, partials_needed(D, p ? p->view.n_gitems : 0, nq, c->sm_count) * sizeof(double)));
 }
 
 }  // namespace
@@ -749,7 +820,7 @@ extern "C" int tq_energy(tq_ctx* c, const tq_ham* h, const tq_state* psi, double
     TQ_REQUIRE(c && h && psi && E, "null argument");
     set_device(c);
     cudaStream_t s = as_stream(stream);
-    double* part = prepare(c, h->D, 0, h->nq);
+    double* part = prepare(c, h->D, nullptr, h->nq);
     run_energy(c, h, psi, part, s);
     TQ_CUDA(cudaMemcpyAsync(E, &c->step->energy, sizeof(double), cudaMemcpyDeviceToHost, s));
     TQ_CUDA(cudaStreamSynchronize(s));
@@ -763,7 +834,7 @@ extern "C" int tq_energy_matrix_free(tq_ctx* c, const tq_ham* h, const tq_state*
     TQ_REQUIRE(h->nq == psi->nq, "state and Hamiltonian qubit counts differ");
     set_device(c);
     cudaStream_t s = as_stream(stream);
-    double* part = prepare(c, h->D, 0, h->nq);
+    double* part = prepare(c, h->D, nullptr, h->nq);
     launch(c, "energy_matrix_free", s, [&] { return launch_energy_matrix_free(h->view, psi->data, psi->prec, part, c->tickets + 1,
                                               c->step, c->sm_count, s); });
     TQ_CUDA(cudaMemcpyAsync(E, &c->step->energy, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -778,7 +849,7 @@ extern "C" int tq_pool_gradients(tq_ctx* c, const tq_ham* h, const tq_pool* p, c
     set_device(c);
     cudaStream_t s = as_stream(stream);
     double* gd = g_on_device ? g : static_cast<double*>(scratch(c, S_G, (size_t)p->M * sizeof(double)));
-    double* part = prepare(c, h->D, p->M, p->nq);
+    double* part = prepare(c, h->D, p, p->nq);
     run_gradients(c, h, p, psi, gd, part, s);
     if (!g_on_device) {
         TQ_CUDA(cudaMemcpyAsync(g, gd, (size_t)p->M * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -802,7 +873,7 @@ extern "C" int tq_adapt_step(tq_ctx* c, const tq_ham* h, const tq_pool* p, tq_st
     double2* u2 = static_cast<double2*>(scratch(c, S_U2, vb));
     double2* w1 = static_cast<double2*>(scratch(c, S_W1, vb));
     double2* w2 = static_cast<double2*>(scratch(c, S_W2, vb));
-    double* part = prepare(c, D, p->M, p->nq);
+    double* part = prepare(c, D, p, p->nq);
     double2* w0 = static_cast<double2*>(c->scratch[S_W0]);
     run_gradients(c, h, p, psi, g, part, s);
     launch(c, "select", s, [&] { return launch_select(g, p->M, eps, psi->prec, c->step, s); });

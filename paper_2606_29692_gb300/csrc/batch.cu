@@ -17,6 +17,8 @@
 #include "dev.cuh"
 #include "host_util.h"
 #include "pair.cuh"
+#include "grad.cuh"
+#include "spmv.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -37,11 +39,13 @@ struct TrajDev {
     const void* val;
     PoolView pool;
     void* psi;
-    double2* w;
+    double2* w;              // H psi, float64 (complex128 states)
+    float2* w32;             // H psi, float32 (complex64 states)
     const double* thetas;
     double* g;
-    double* gpart;
+    double* gpart;           // one partial per gradient item of this trajectory
     unsigned* gtick;
+    int gbase;               // first gradient item of this trajectory
     double* res_e;
     double* res_g;
     double* res_th;
@@ -57,33 +61,11 @@ struct TrajState {
 namespace {
 
 constexpr int BT_BS = 256;
-constexpr int ROWS_PER_ITEM = 256;
+constexpr int ROWS_PER_ITEM = ENERGY_ROWS;
 constexpr int BT_UPT = 2;
 
 template <typename T> __device__ __forceinline__ double2 d2(typename C2<T>::type v) {
     return make_double2((double)v.x, (double)v.y);
-}
-
-// sum over a group of W lanes (W divides 32); result in the group's lane 0
-template <int W>
-__device__ __forceinline__ double group_sum(double v) {
-#pragma unroll
-    for (int o = W / 2; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o, W);
-    return v;
-}
-template <int W>
-__device__ __forceinline__ double group_sum(float v) {
-    float hi = v, lo = 0.f;
-#pragma unroll
-    for (int o = W / 2; o > 0; o >>= 1) {
-        const float oh = __shfl_down_sync(0xffffffffu, hi, o, W);
-        const float ol = __shfl_down_sync(0xffffffffu, lo, o, W);
-        float s, e;
-        two_sum(hi, oh, s, e);
-        hi = s;
-        lo = lo + ol + e;
-    }
-    return (double)hi + (double)lo;
 }
 
 template <typename T>
@@ -108,14 +90,17 @@ __global__ void kb_reset(const TrajDev* tr, TrajState* ts, const int4* items, in
     }
 }
 
+// Energy item: ROWS_PER_ITEM rows of one trajectory.  Groups of LPR lanes
+// take LPR consecutive rows each; per row the group strides over the
+// non-zeros and reduces with an xor butterfly in the state's precision, and
+// lane j of the group keeps row j's sum; each lane then finishes its row in
+// float64 (diagonal, w, dots).
 template <typename T, typename VT, int LPR>
 __global__ void __launch_bounds__(BT_BS)
 kb_energy(const TrajDev* tr, TrajState* ts, const int4* items, int n_items, double* part) {
     using V = typename C2<T>::type;
     __shared__ double sh[2 * (BT_BS / 32)];
     __shared__ bool last;
-    const int grp = threadIdx.x / LPR, gl = threadIdx.x % LPR;
-    constexpr int NG = BT_BS / LPR;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const int4 w4 = items[it];
         const int t = w4.x;
@@ -124,25 +109,8 @@ kb_energy(const TrajDev* tr, TrajState* ts, const int4* items, int n_items, doub
         const V* psi = static_cast<const V*>(d.psi);
         const VT* val = static_cast<const VT*>(d.val);
         double num = 0.0, den = 0.0;
-        for (int r = w4.y + grp; r < w4.y + w4.z; r += NG) {
-            T px = T(0), py = T(0);
-            const int e1 = d.rowptr[r + 1];
-            for (int e = d.rowptr[r] + gl; e < e1; e += LPR) {
-                const T a = (T)val[e];
-                const V v = psi[d.col[e]];
-                px = fma(a, v.x, px);
-                py = fma(a, v.y, py);
-            }
-            const double sx = group_sum<LPR>(px), sy = group_sum<LPR>(py);
-            if (gl == 0) {
-                const double2 pr = d2<T>(psi[r]);
-                const double dg = d.diag[r];
-                const double wx = fma(dg, pr.x, sx), wy = fma(dg, pr.y, sy);
-                d.w[r] = make_double2(wx, wy);
-                num += pr.x * wx + pr.y * wy;
-                den += pr.x * pr.x + pr.y * pr.y;
-            }
-        }
+        energy_rows<T, VT, LPR>(d.rowptr, d.col, val, d.diag, psi, d.w, d.w32, w4.y, (long long)w4.y + w4.z,
+                                num, den);
         double v[2] = {num, den};
         block_sum<2>(v, sh);
         if (threadIdx.x == 0) {
@@ -167,43 +135,39 @@ kb_energy(const TrajDev* tr, TrajState* ts, const int4* items, int n_items, doub
     }
 }
 
+// Gradient item: (t, op, chunk of the op's support rows).
 template <typename T>
-__global__ void __launch_bounds__(BT_BS)
+__global__ void __launch_bounds__(GRAD_TPB)
 kb_grad(const TrajDev* tr, TrajState* ts, const int4* items, int n_items) {
     using V = typename C2<T>::type;
-    __shared__ double sh[BT_BS / 32];
+    __shared__ double sh[GRAD_TPB / 32];
     __shared__ bool last;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const int4 w4 = items[it];
-        const int t = w4.x, k = w4.y, c = w4.z;
+        const int4 w4 = items[it];          // (t, op, chunk, chunks of this op)
+        const int t = w4.x, k = w4.y;
         if (!ts[t].active) continue;
         const TrajDev& d = tr[t];
-        const V* psi = static_cast<const V*>(d.psi);
-        OpSign<double> op;
-        op.load(d.pool, k);
-        double acc = 0.0;
-        const uint32_t r0 = (uint32_t)c * d.chunk;
-        for (int i = threadIdx.x; i < d.chunk; i += BT_BS) {
-            const uint32_t r = r0 + i, q = r ^ op.x;
-            const double s = op.value(q);
-            if (s != 0.0) {
-                const double2 wr = d.w[r];
-                const double2 v = d2<T>(psi[q]);
-                acc += s * (wr.x * v.x + wr.y * v.y);
-            }
-        }
-        double v[1] = {acc};
-        block_sum<1>(v, sh);
+        const SuppRec s = load_supp(d.pool, k);
+        const uint32_t size = (uint32_t)(d.D >> s.m);
+        const uint32_t u0 = (uint32_t)w4.z * GRAD_CHUNK;
+        const uint32_t cnt = min((uint32_t)GRAD_CHUNK, size - u0);
+        const T c0 = sizeof(T) == 4 ? (T)d.pool.fc0f[k] : (T)d.pool.fc0d[k];
+        double v;
+        if constexpr (sizeof(T) == 4)
+            v = grad_item<T>(s, c0, d.w32, static_cast<const V*>(d.psi), u0, cnt, sh);
+        else
+            v = grad_item<T>(s, c0, d.w, static_cast<const V*>(d.psi), u0, cnt, sh);
+        const int first = it - w4.z;        // the op's items are consecutive
         if (threadIdx.x == 0) {
-            d.gpart[(long long)k * d.nch + c] = v[0];
+            d.gpart[first - d.gbase + w4.z] = v;
             __threadfence();
-            last = atomicAdd(&d.gtick[k], 1u) == (unsigned)d.nch - 1;
+            last = atomicAdd(&d.gtick[k], 1u) == (unsigned)w4.w - 1;
         }
         __syncthreads();
         if (last && threadIdx.x == 0) {
-            double s = 0.0;
-            for (int i = 0; i < d.nch; ++i) s += __ldcg(d.gpart + (long long)k * d.nch + i);
-            d.g[k] = 2.0 * s / ts[t].e_den;
+            double acc = 0.0;
+            for (int i = 0; i < w4.w; ++i) acc += __ldcg(d.gpart + (first - d.gbase) + i);
+            d.g[k] = 2.0 * acc / ts[t].e_den;
             d.gtick[k] = 0u;
         }
         __syncthreads();
@@ -377,7 +341,7 @@ void compute_grids(tq_batch* b) {
     b->grid_e[1] = std::min(b->n_e, resident_grid(kb_energy<T, VT, 8>, BT_BS, sms));
     b->grid_e[2] = std::min(b->n_e, resident_grid(kb_energy<T, VT, 16>, BT_BS, sms));
     b->grid_e[3] = std::min(b->n_e, resident_grid(kb_energy<T, VT, 32>, BT_BS, sms));
-    b->grid_g = std::min(b->n_g, resident_grid(kb_grad<T>, BT_BS, sms));
+    b->grid_g = std::min(b->n_g, resident_grid(kb_grad<T>, GRAD_TPB, sms));
     b->grid_p = std::min(b->n_p, resident_grid(kb_pair<T>, PAIR_BS, sms));
 }
 
@@ -395,7 +359,7 @@ void enqueue_iteration(tq_batch* b, cudaStream_t s) {
     const int sms = c->sm_count;
     launch(c, "batch_energy", s, [&] { return launch_energy<T, VT>(b, s); });
     launch(c, "batch_gradients", s, [&] {
-        kb_grad<T><<<b->grid_g, BT_BS, 0, s>>>(b->d_td, b->d_ts, b->gitems, b->n_g);
+        kb_grad<T><<<b->grid_g, GRAD_TPB, 0, s>>>(b->d_td, b->d_ts, b->gitems, b->n_g);
         return 1;
     });
     launch(c, "batch_select", s, [&] {
@@ -476,14 +440,20 @@ extern "C" int tq_batch_create(tq_ctx* c, int n_traj, tq_ham* const* hams, tq_po
             d.col = h->view.col;
             d.val = h->view.val;
             d.pool = p->view;
-            d.chunk = (int)std::min<long long>(d.D, 2048);
-            d.nch = (int)(d.D / d.chunk);
+            d.chunk = 0;
+            d.nch = 0;
             d.eoff = (int)ei.size();
             for (long long r = 0; r < d.D; r += ROWS_PER_ITEM)
                 ei.push_back(make_int4(t, (int)r, (int)std::min<long long>(ROWS_PER_ITEM, d.D - r), 0));
             d.ecnt = (int)ei.size() - d.eoff;
-            for (int k = 0; k < d.M; ++k)
-                for (int ch = 0; ch < d.nch; ++ch) gi.push_back(make_int4(t, k, ch, 0));
+            d.gbase = (int)gi.size();
+            for (int k = 0; k < d.M; ++k) {
+                const int m = p->nterm[k] == 2 ? 1 : 3;    // conditions of a single / double
+                const long long size = d.D >> m;
+                const int nchunks = (int)((size + GRAD_CHUNK - 1) / GRAD_CHUNK);
+                for (int ch = 0; ch < nchunks; ++ch) gi.push_back(make_int4(t, k, ch, nchunks));
+            }
+            const int n_gitems_t = (int)gi.size() - d.gbase;
             const long long units = d.D >> 2;
             d.pcnt = (int)((units + PAIR_BS * BT_UPT - 1) / (PAIR_BS * BT_UPT));
             for (int tl = 0; tl < d.pcnt; ++tl) pi.push_back(make_int4(t, tl, 0, 0));
@@ -493,11 +463,12 @@ extern "C" int tq_batch_create(tq_ctx* c, int n_traj, tq_ham* const* hams, tq_po
                 si.push_back(make_int4(t, (int)r, (int)std::min<long long>(4096, d.D - r), 0));
             const size_t es = b->prec == TQ_C128 ? 16 : 8;
             d.psi = dalloc<unsigned char>(b, (size_t)d.D * es);
-            d.w = dalloc<double2>(b, (size_t)d.D);
+            if (b->prec == TQ_C128) d.w = dalloc<double2>(b, (size_t)d.D);
+            else d.w32 = dalloc<float2>(b, (size_t)d.D);
             d.thetas = dupload(b, std::vector<double>(thetas + toff, thetas + toff + d.len));
             toff += d.len;
             d.g = dalloc<double>(b, d.M);
-            d.gpart = dalloc<double>(b, (size_t)d.M * d.nch);
+            d.gpart = dalloc<double>(b, (size_t)n_gitems_t);
             d.gtick = dalloc<unsigned>(b, d.M);
             TQ_CUDA(cudaMemset(d.gtick, 0, d.M * sizeof(unsigned)));
             d.res_e = dalloc<double>(b, std::max(1, d.len));

@@ -42,6 +42,20 @@ struct SignForm {
     int t;
 };
 
+// Support of a generator, {r : A[r][r^x] != 0}, as an affine subspace in
+// reduced form: m pivot bits p[0] < p[1] < p[2]; each mask e[i] contains
+// pivot p[i] and no other pivot; row r is in the support iff
+// parity(r & e[i]) == bit i of target for every i.  Support row u
+// (0 <= u < 2^(N-m)) is u with zeros inserted at the pivots, each pivot bit
+// then set to target_i xor parity(r & e[i]).
+struct SupportForm {
+    int m;
+    int p[3];
+    uint64_t e[3];
+    int target;
+};
+SupportForm support_form(const SignForm& f, uint64_t x);
+
 void check_mapping(int mapping);
 // Sets the thread-local reason returned by tq_last_error().
 void set_last_error(const std::string& m);
@@ -70,6 +84,11 @@ struct PoolView {
     const int* ft;          // target parities, bit i for condition i
     const float* fc0f;      // leading coefficient, float32
     const double* fc0d;     // leading coefficient, float64
+    const int4* supp;       // [M] support form: (m | target << 8, p0 | p1 << 8 | p2 << 16, -, -)
+    const uint32_t* supe;   // [3 M] support masks
+    const int2* gitems;     // gradient work items (op, chunk of support rows)
+    int n_gitems;
+    const int* gfirst;      // [M + 1] first work item of each op
 };
 
 // Hamiltonian: float64 diagonal + off-diagonal CSR + X-mask-grouped terms.
@@ -145,9 +164,13 @@ int launch_energy_csr(const HamView& h, const void* psi, int psi_prec, double2* 
 int launch_energy_matrix_free(const HamView& h, const void* psi, int psi_prec,
                               double* partials, unsigned* ticket, DevStep* step,
                               int sms, cudaStream_t s);
-int launch_pool_gradients(const PoolView& p, const double2* w, const void* psi, int prec,
-                          const DevStep* step, double* partials, unsigned* tickets,
-                          double* g, int sms, cudaStream_t s);
+int launch_energy_csr2(const HamView& h, const void* psi, int psi_prec, double2* w,
+                       float2* w32, double* partials, unsigned* ticket, DevStep* step,
+                       int sms, cudaStream_t s, int lanes_per_row);
+// gradients read w in float32 (w32) for complex64 states, float64 (w) otherwise
+int launch_pool_gradients(const PoolView& p, const double2* w, const float2* w32,
+                          const void* psi, int prec, const DevStep* step, double* partials,
+                          unsigned* tickets, double* g, int sms, cudaStream_t s);
 int launch_select(const double* g, int M, double eps, int prec, DevStep* step,
                   cudaStream_t s);
 int launch_apply_twice(const PoolView& p, const DevStep* step, const void* psi, int prec,
@@ -167,7 +190,6 @@ int launch_scale_gated(void* psi, int prec, long long D, const double* norm2,
 int launch_spmv_c128_gated(const HamView& h, const double2* x, double2* y,
                            const DevStep* gate, int sms, cudaStream_t s);
 int energy_grid(long long D, int sms);
-void grad_layout(int nq, int* nch, int* chunk);
 
 }  // namespace tq
 
@@ -184,11 +206,12 @@ struct tq_ctx {
     long long launches = 0;
     int tracing = 0;
     int pair_upt[2] = {2, 4};              // schedule per precision (C128, C64)
+    int spmv_lanes = 32;                   // energy SpMV lanes per row
     std::vector<tq_trace_rec> trace;      // recorded, not yet reported
     std::vector<cudaEvent_t> event_pool;  // reusable events
     // device scratch, grown on demand
-    void* scratch[8] = {nullptr};
-    size_t scratch_bytes[8] = {0};
+    void* scratch[10] = {nullptr};
+    size_t scratch_bytes[10] = {0};
     tq::DevStep* step = nullptr;      // device
     unsigned* tickets = nullptr;      // device, zero between calls
     size_t tickets_n = 0;

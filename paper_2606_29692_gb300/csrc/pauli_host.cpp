@@ -279,4 +279,39 @@ SignForm factor_generator(const std::vector<PauliTerm>& t) {
     return f;
 }
 
+SupportForm support_form(const SignForm& f, uint64_t x) {
+    // conditions on col = r ^ x become conditions on r with flipped targets
+    SupportForm s{};
+    s.m = f.m;
+    uint64_t e[3] = {f.d[0], f.d[1], f.d[2]};
+    int t[3];
+    for (int i = 0; i < f.m; ++i)
+        t[i] = ((f.t >> i) & 1) ^ (__builtin_popcountll(x & e[i]) & 1);
+    // reduce: pivot = highest set bit, eliminated from every other row
+    int piv[3] = {0, 0, 0};
+    for (int i = 0; i < f.m; ++i) {
+        int best = i;
+        for (int j = i + 1; j < f.m; ++j)
+            if (e[j] > e[best]) best = j;
+        std::swap(e[i], e[best]);
+        std::swap(t[i], t[best]);
+        if (e[i] == 0) throw Error(TQ_ENUMERIC, "degenerate generator support");
+        piv[i] = 63 - __builtin_clzll(e[i]);
+        for (int j = 0; j < f.m; ++j)
+            if (j != i && ((e[j] >> piv[i]) & 1)) {
+                e[j] ^= e[i];
+                t[j] ^= t[i];
+            }
+    }
+    // order by ascending pivot
+    int ord[3] = {0, 1, 2};
+    std::sort(ord, ord + f.m, [&](int a, int b) { return piv[a] < piv[b]; });
+    for (int i = 0; i < f.m; ++i) {
+        s.p[i] = piv[ord[i]];
+        s.e[i] = e[ord[i]];
+        s.target |= t[ord[i]] << i;
+    }
+    return s;
+}
+
 }  // namespace tq

@@ -6,6 +6,8 @@
 // shuffle tree, CTAs write one partial each, and the last CTA to finish
 // (atomic ticket, reset by that CTA) sums the partials in index order.
 #include "dev.cuh"
+#include "grad.cuh"
+#include "spmv.cuh"
 
 #include <cmath>
 
@@ -32,37 +34,21 @@ template <typename T> __device__ __forceinline__ double2 to_d2(typename C2<T>::t
     return make_double2((double)v.x, (double)v.y);
 }
 
-// w = H psi (diagonal float64 + CSR off-diagonal), and the float64 sums
-// <psi|w> and <psi|psi>.  One warp per row.
-template <typename T, typename VT>
+// w = H psi (diagonal float64 + CSR off-diagonal) and the float64 sums
+// <psi|w>, <psi|psi>: a persistent grid over 256-row items (energy_rows),
+// one partial pair per CTA, the last CTA sums them in order.
+template <typename T, typename VT, int L>
 __global__ void __launch_bounds__(256)
 k_energy_csr(HamView h, const typename C2<T>::type* __restrict__ psi, double2* __restrict__ w,
-             double* partials, unsigned* ticket, DevStep* step) {
+             float2* __restrict__ w32, double* partials, unsigned* ticket, DevStep* step) {
     __shared__ double sh[2 * 8];
     const VT* __restrict__ val = static_cast<const VT*>(h.val);
-    const int lane = threadIdx.x & 31;
-    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     double num = 0.0, den = 0.0;
-    for (long long r = warp; r < h.D; r += nwarps) {
-        T px = T(0), py = T(0);
-        const int e1 = h.rowptr[r + 1];
-        for (int e = h.rowptr[r] + lane; e < e1; e += 32) {
-            const T a = (T)val[e];
-            const auto v = psi[h.col[e]];
-            px = fma(a, v.x, px);
-            py = fma(a, v.y, py);
-        }
-        // complex64: float32 lane sums, compensated warp sum -> float64
-        const double sx = warp_sum_compensated(px), sy = warp_sum_compensated(py);
-        if (lane == 0) {
-            const double2 pr = to_d2<T>(psi[r]);
-            const double d = h.diag[r];
-            const double wx = fma(d, pr.x, sx), wy = fma(d, pr.y, sy);
-            if (w) w[r] = make_double2(wx, wy);
-            num += pr.x * wx + pr.y * wy;
-            den += pr.x * pr.x + pr.y * pr.y;
-        }
+    const long long items = (h.D + ENERGY_ROWS - 1) / ENERGY_ROWS;
+    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
+        const long long r0 = it * ENERGY_ROWS;
+        const long long r1 = r0 + ENERGY_ROWS < h.D ? r0 + ENERGY_ROWS : h.D;
+        energy_rows<T, VT, L>(h.rowptr, h.col, val, h.diag, psi, w, w32, r0, r1, num, den);
     }
     double v[2] = {num, den};
     block_sum<2>(v, sh);
@@ -136,48 +122,36 @@ k_energy_mf(HamView h, const typename C2<T>::type* __restrict__ psi, double* par
     }
 }
 
-// g_k = 2 Re<w|A_k psi> / <psi|psi> for all k: work items (op, row chunk)
-// in one persistent launch; per-op tickets pick the CTA that finalises g_k.
-constexpr int GRAD_BS = 256;
-
-template <typename T>
-__global__ void __launch_bounds__(GRAD_BS)
-k_pool_grad(PoolView p, const double2* __restrict__ w, const typename C2<T>::type* __restrict__ psi,
-            const DevStep* step, double* partials, unsigned* tickets, double* g, int nch,
-            int chunk) {
-    __shared__ double sh[GRAD_BS / 32];
-    const long long items = (long long)p.M * nch;
-    for (long long it = blockIdx.x; it < items; it += gridDim.x) {
-        const int k = (int)(it / nch);
-        const int c = (int)(it - (long long)k * nch);
-        OpSign<double> op;
-        op.load(p, k);
-        double acc = 0.0;
-        const uint32_t r0 = (uint32_t)c * chunk;
-        for (int i = threadIdx.x; i < chunk; i += GRAD_BS) {
-            const uint32_t r = r0 + i;
-            const uint32_t q = r ^ op.x;
-            const double s = op.value(q);
-            if (s != 0.0) {
-                const double2 wr = w[r];
-                const double2 v = to_d2<T>(psi[q]);
-                acc += s * (wr.x * v.x + wr.y * v.y);
-            }
-        }
-        double v[1] = {acc};
-        block_sum<1>(v, sh);
-        __shared__ bool last;
+// g_k = 2 Re<w|A_k psi> / <psi|psi> for all k in one persistent launch:
+// work items (op, chunk of support rows); per-op tickets pick the CTA that
+// finalises g_k from the op's chunk partials in order.
+template <typename T, typename W>
+__global__ void __launch_bounds__(GRAD_TPB)
+k_pool_grad(PoolView p, const W* __restrict__ w, const typename C2<T>::type* __restrict__ psi,
+            const DevStep* step, double* partials, unsigned* tickets, double* g,
+            const int2* items, int n_items, const int* first_item) {
+    __shared__ double sh[GRAD_TPB / 32];
+    __shared__ bool last;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int2 kc = items[it];
+        const int k = kc.x;
+        const SuppRec s = load_supp(p, k);
+        const uint32_t size = (uint32_t)((1ll << p.nq) >> s.m);
+        const uint32_t u0 = (uint32_t)kc.y * GRAD_CHUNK;
+        const uint32_t cnt = min((uint32_t)GRAD_CHUNK, size - u0);
+        const T c0 = sizeof(T) == 4 ? (T)p.fc0f[k] : (T)p.fc0d[k];
+        const double v = grad_item<T>(s, c0, w, psi, u0, cnt, sh);
+        const int nch = first_item[k + 1] - first_item[k];
         if (threadIdx.x == 0) {
-            partials[it] = v[0];
+            partials[it] = v;
             __threadfence();
-            const unsigned t = atomicAdd(&tickets[k], 1u);
-            last = (t == (unsigned)nch - 1);
+            last = atomicAdd(&tickets[k], 1u) == (unsigned)nch - 1;
         }
         __syncthreads();
         if (last && threadIdx.x == 0) {
-            double s = 0.0;
-            for (int i = 0; i < nch; ++i) s += __ldcg(partials + (long long)k * nch + i);
-            g[k] = 2.0 * s / step->e_den;
+            double acc = 0.0;
+            for (int i = first_item[k]; i < first_item[k + 1]; ++i) acc += __ldcg(partials + i);
+            g[k] = 2.0 * acc / step->e_den;
             tickets[k] = 0u;
         }
         __syncthreads();
@@ -406,18 +380,56 @@ int grid_rows(long long D, int rows_per_block, int sms, int per_sm) {
 
 }  // namespace
 
-int energy_grid(long long D, int sms) { return grid_rows(D, 8, sms, 8); }
+int energy_grid(long long D, int sms) { return grid_rows(D, ENERGY_ROWS, sms, 8); }
 
 int launch_energy_csr(const HamView& h, const void* psi, int psi_prec, double2* w,
                       double* partials, unsigned* ticket, DevStep* step, int sms, cudaStream_t s) {
-    const int grid = energy_grid(h.D, sms);
+    return launch_energy_csr2(h, psi, psi_prec, w, nullptr, partials, ticket, step, sms, s, 32);
+}
+
+namespace {
+
+template <typename T, typename VT, int L>
+int resident(int sms) {
+    static int per = 0;
+    if (per == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_energy_csr<T, VT, L>, 256, 0);
+        if (per < 1) per = 1;
+    }
+    return per * sms;
+}
+
+template <typename T, typename VT, int L>
+void energy_launch(const HamView& h, const void* psi, double2* w, float2* w32, double* partials,
+                   unsigned* ticket, DevStep* step, int sms, cudaStream_t s) {
+    using V = typename C2<T>::type;
+    const long long items = (h.D + ENERGY_ROWS - 1) / ENERGY_ROWS;
+    long long grid = resident<T, VT, L>(sms);
+    if (grid > items) grid = items;
+    k_energy_csr<T, VT, L><<<(int)grid, 256, 0, s>>>(h, static_cast<const V*>(psi), w, w32, partials, ticket,
+                                                     step);
+}
+
+template <typename T, typename VT>
+int energy_dispatch(int lanes, const HamView& h, const void* psi, double2* w, float2* w32, double* partials,
+                    unsigned* ticket, DevStep* step, int sms, cudaStream_t s) {
+    switch (lanes) {
+        case 4: energy_launch<T, VT, 4>(h, psi, w, w32, partials, ticket, step, sms, s); return 1;
+        case 8: energy_launch<T, VT, 8>(h, psi, w, w32, partials, ticket, step, sms, s); return 1;
+        case 16: energy_launch<T, VT, 16>(h, psi, w, w32, partials, ticket, step, sms, s); return 1;
+        case 32: energy_launch<T, VT, 32>(h, psi, w, w32, partials, ticket, step, sms, s); return 1;
+        default: return -1;
+    }
+}
+
+}  // namespace
+
+int launch_energy_csr2(const HamView& h, const void* psi, int psi_prec, double2* w, float2* w32,
+                       double* partials, unsigned* ticket, DevStep* step, int sms, cudaStream_t s,
+                       int lanes) {
     if (psi_prec == TQ_C128)
-        k_energy_csr<double, double><<<grid, 256, 0, s>>>(h, static_cast<const double2*>(psi), w, partials,
-                                                          ticket, step);
-    else
-        k_energy_csr<float, float><<<grid, 256, 0, s>>>(h, static_cast<const float2*>(psi), w, partials,
-                                                        ticket, step);
-    return 1;
+        return energy_dispatch<double, double>(lanes, h, psi, w, w32, partials, ticket, step, sms, s);
+    return energy_dispatch<float, float>(lanes, h, psi, w, w32, partials, ticket, step, sms, s);
 }
 
 int launch_energy_matrix_free(const HamView& h, const void* psi, int psi_prec, double* partials,
@@ -430,26 +442,17 @@ int launch_energy_matrix_free(const HamView& h, const void* psi, int psi_prec, d
     return 1;
 }
 
-void grad_layout(int nq, int* nch, int* chunk) {
-    const long long D = 1ll << nq;
-    int c = (int)(D < 2048 ? D : 2048);
-    *chunk = c;
-    *nch = (int)(D / c);
-}
-
-int launch_pool_gradients(const PoolView& p, const double2* w, const void* psi, int prec,
-                          const DevStep* step, double* partials, unsigned* tickets, double* g,
+int launch_pool_gradients(const PoolView& p, const double2* w, const float2* w32, const void* psi,
+                          int prec, const DevStep* step, double* partials, unsigned* tickets, double* g,
                           int sms, cudaStream_t s) {
-    int nch, chunk;
-    grad_layout(p.nq, &nch, &chunk);
-    const long long items = (long long)p.M * nch;
-    const int grid = (int)(items < (long long)sms * 8 ? items : (long long)sms * 8);
+    const int n = p.n_gitems;
+    const int grid = n < sms * 8 ? n : sms * 8;
     if (prec == TQ_C128)
-        k_pool_grad<double><<<grid, GRAD_BS, 0, s>>>(p, w, static_cast<const double2*>(psi), step, partials,
-                                                     tickets, g, nch, chunk);
+        k_pool_grad<double, double2><<<grid, GRAD_TPB, 0, s>>>(p, w, static_cast<const double2*>(psi), step,
+                                                               partials, tickets, g, p.gitems, n, p.gfirst);
     else
-        k_pool_grad<float><<<grid, GRAD_BS, 0, s>>>(p, w, static_cast<const float2*>(psi), step, partials,
-                                                    tickets, g, nch, chunk);
+        k_pool_grad<float, float2><<<grid, GRAD_TPB, 0, s>>>(p, w32, static_cast<const float2*>(psi), step,
+                                                             partials, tickets, g, p.gitems, n, p.gfirst);
     return 1;
 }
 

@@ -86,3 +86,18 @@ def test_energy_rejects_mismatch(ctx):
     st10 = to_state(ctx, synth.random_state(10, 1), 10, tq.TQ_C128)
     with pytest.raises(tq.TQError):
         tq.energy(ctx, ham, st10)
+
+
+def test_every_spmv_schedule_agrees(ctx):
+    ints, ne, sysm = osys("c2", 1)
+    for prec in (tq.TQ_C128, tq.TQ_C64):
+        ham = tq.build_hamiltonian(ctx, ints.h, ints.g, 0.0, 1, prec)
+        psi = _states(sysm, 14, ne, 1)["corr"]
+        st = to_state(ctx, psi, 14, prec)
+        ref = oadapt.energy(sysm.H, st.numpy())[0]
+        for lanes in (4, 8, 16, 32):
+            ctx.set_spmv_schedule(lanes)
+            assert abs(tq.energy(ctx, ham, st) - ref) <= (1e-10 if prec == tq.TQ_C128 else 1e-6)
+        best, ms = tq.autotune_spmv(ctx, ham, st)
+        assert best in (4, 8, 16, 32) and ms > 0
+    ctx.set_spmv_schedule(32)
