@@ -302,6 +302,8 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.headline_only:
         extra["spmv"] = measure_spmv(tq, ctx, args.spmv_qubits)
         extra["trajectories"] = measure_trajectories(tq, ctx, args.traj)
+        if args.serve_seconds > 0:
+            extra["serving"] = measure_serving(tq, local_rank, args.serve_seconds, args.serve_rate)
     out = None
     if rank == 0:
         out = {
@@ -369,6 +371,69 @@ def measure_spmv(tq, ctx, nq):
             "energy": e, "l2_policy": "CSR larger than L2"}
 
 
+def measure_serving(tq, device, seconds, rate):
+    """Poisson request stream into the continuous-batching request loop."""
+    import numpy as np
+
+    import synth
+    ctx = tq.Context(device)                  # the server owns this context
+    srv = tq.Server(ctx, tq.TQ_C64, hbm_budget=16 << 30, max_batch=1024)
+    cat = synth.catalogue()
+    pools_m = []
+    t0 = time.perf_counter()
+    for n, ne, mp, seed in cat:
+        ints = synth.integrals(n, seed)
+        ham = tq.build_hamiltonian(ctx, ints.h, ints.g, ints.e_const, mp, tq.TQ_C64)
+        pool = tq.build_pool(ctx, n, ne, mp)
+        srv.add_hamiltonian(ham, pool)
+        pools_m.append(pool.M)
+    n_sessions = 256
+    for j in range(n_sessions):
+        n, ne, mp, _ = cat[j % len(cat)]
+        srv.add_session(j % len(cat), ne, mp)
+    build_s = time.perf_counter() - t0
+    srv.start()
+    arr = synth.arrivals(rate, seconds, n_sessions)
+    lag = []
+
+    def submitter():
+        start = time.perf_counter()
+        for i, a in enumerate(arr):
+            dt = start + a.t - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            lag.append(time.perf_counter() - start - a.t)
+            srv.submit(a.kind, a.session, a.op % pools_m[a.session % len(cat)], a.theta, i)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    got = []
+    deadline = time.perf_counter() + seconds + 60
+    while len(got) < len(arr) and time.perf_counter() < deadline:
+        got += srv.poll(5000)
+    th.join()
+    srv.stop()
+    st = srv.stats()
+    lat = np.array([c["t_done"] - c["t_submit"] for c in got]) * 1e3
+    span = max(c["t_done"] for c in got) - min(c["t_submit"] for c in got)
+    by_kind = {}
+    for name, kind in (("evolve", 0), ("energy", 1), ("gradients", 2)):
+        lk = np.array([c["t_done"] - c["t_submit"] for c in got if c["kind"] == kind]) * 1e3
+        if lk.size:
+            by_kind[name] = {"n": int(lk.size), "p50_ms": float(np.percentile(lk, 50)),
+                             "p99_ms": float(np.percentile(lk, 99))}
+    return {"workload": (f"Poisson arrivals at {rate:.0f}/s for {seconds:.0f} s, 50% evolve / 30% energy / "
+                         "20% gradients, 256 resident sessions over 16 resident Hamiltonians and pools of "
+                         "12-18 qubits (synthetic, seeds 2000+j), complex64 with float64 reductions"),
+            "requests": len(arr), "completed": len(got),
+            "failed": int(sum(c["status"] != 0 for c in got)),
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "throughput_rps": len(got) / span,
+            "ticks": st["ticks"], "mean_batch": len(got) / max(1, st["ticks"]),
+            "submit_lag_p99_ms": float(np.percentile(np.array(lag) * 1e3, 99)),
+            "by_kind": by_kind, "build_s": build_s}
+
+
 def measure_trajectories(tq, ctx, n_traj):
     """Independent ADAPT trajectories of 10-16 qubits, one graph replay per run."""
     import numpy as np
@@ -427,6 +492,9 @@ def main():
                     help="skip the SpMV and trajectory-batch measurements")
     ap.add_argument("--spmv-qubits", type=int, default=18)
     ap.add_argument("--traj", type=int, default=256)
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="length of the request-loop measurement (0 skips it)")
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--pair-schedule", type=int, default=0,
                     help="units per thread of the pair kernel (0 = autotune)")
     args = ap.parse_args()

@@ -364,6 +364,67 @@ int tq_batch_results(const tq_batch* b, int* n_iter, int* converged,
 int tq_batch_state(const tq_batch* b, int t, void** dev_ptr, int* n_qubits);
 int tq_batch_free(tq_batch* b);
 
+/* ----------------------------------------------------------- request loop */
+
+/* A request loop that batches evolve, energy and gradient requests on
+ * resident sessions continuously (the paper runs one trajectory at a time;
+ * this serves many at once).  Each session is a state of one registered
+ * Hamiltonian and its pool, created at the Hartree-Fock state.  A server
+ * thread forms ticks from the queue in arrival order -- at most one request
+ * per session per tick (a session's requests complete in submission order),
+ * at most max_batch per tick, and only while the per-request working memory
+ * (w = H psi, gradients, their partials) fits the arena: admission is by
+ * HBM footprint -- and runs each tick as one batched launch per step; the
+ * next tick is formed while the current one runs.  Evolve applies the
+ * Taylor-5 update of the given op and angle and renormalises; energy is
+ * Eq. (1); gradients returns max |g| and its op (the ADAPT selection rule)
+ * and the energy.  A request's result does not depend on the other
+ * requests of its tick.  While the server runs it owns its context: issue
+ * no other call on that context until tq_server_stop. */
+enum { TQ_REQ_EVOLVE = 0, TQ_REQ_ENERGY = 1, TQ_REQ_GRADIENTS = 2 };
+typedef struct {
+    int kind;                 /* TQ_REQ_*                                  */
+    int session;              /* session id                                */
+    int op;                   /* pool op (evolve)                          */
+    int pad;
+    double theta;             /* angle (evolve)                            */
+    unsigned long long tag;   /* caller's id, returned in the completion   */
+} tq_request;
+typedef struct {
+    unsigned long long tag;
+    int kind, session, status, argmax;   /* argmax: gradients, else -1     */
+    double energy;            /* energy and gradients requests             */
+    double max_grad;          /* gradients requests                        */
+    double norm2;             /* evolve: ||psi'||^2 before renormalising;
+                                 others: <psi|psi>                         */
+    double t_submit, t_done;  /* steady-clock seconds, for latency         */
+} tq_completion;
+typedef struct tq_server tq_server;
+/* hbm_budget covers session states (at most half of it) and the working
+ * arena (the rest, allocated at start). */
+int tq_server_create(tq_ctx* ctx, int prec, size_t hbm_budget, int max_batch,
+                     tq_server** out);
+int tq_server_add_hamiltonian(tq_server* s, const tq_ham* ham, const tq_pool* pool,
+                              int* ham_id);
+/* TQ_EBUSY when the session's state would exceed half of the budget. */
+int tq_server_add_session(tq_server* s, int ham_id, int n_electrons, int mapping,
+                          int* session_id);
+int tq_server_start(tq_server* s);
+/* Thread-safe enqueue; TQ_EBUSY when the queue is full. */
+int tq_server_submit(tq_server* s, const tq_request* req);
+/* Up to max completions; waits at most timeout_us for the first one and
+ * returns TQ_ETIMEOUT if none arrived. */
+int tq_server_poll(tq_server* s, tq_completion* out, int max, int* n_out,
+                   int timeout_us);
+int tq_server_stats(const tq_server* s, long long* ticks, long long* completed,
+                    long long* queued);
+/* Borrowed device pointer to a session's state (read it only when idle). */
+int tq_server_session_state(const tq_server* s, int session, void** dev_ptr,
+                            int* n_qubits);
+/* Stop the server thread after the ticks in flight; queued requests stay. */
+int tq_server_stop(tq_server* s);
+int tq_server_free(tq_server* s);
+
 #ifdef __cplusplus
 }
 #endif

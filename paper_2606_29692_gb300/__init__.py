@@ -13,14 +13,18 @@ import ctypes as C
 
 import numpy as np
 
-from ._native import (TQ_BK, TQ_C64, TQ_C128, TQ_JW, AdaptResult, TQError, call, lib)
+from ._native import (TQ_BK, TQ_C64, TQ_C128, TQ_JW, AdaptResult, Completion, Request, TQError, call,
+                      lib)
+
+TQ_REQ_EVOLVE, TQ_REQ_ENERGY, TQ_REQ_GRADIENTS = 0, 1, 2
 
 __all__ = [
     "TQ_JW", "TQ_BK", "TQ_C128", "TQ_C64", "TQError", "Context", "Hamiltonian", "Pool", "State",
     "pauli_hamiltonian", "pool_excitations", "pauli_pool", "hf_index", "build_hamiltonian",
     "build_pool", "evolve_taylor5", "evolve_taylor5_csr", "energy", "energy_matrix_free",
     "pool_gradients", "adapt_step", "evolve_taylor5_batch", "evolve_taylor5_batch_host",
-    "state_set_hf", "pool_csr", "ham_csr", "lib", "autotune_pair", "energy_noalloc", "Batch", "autotune_spmv",
+    "state_set_hf", "pool_csr", "ham_csr", "lib", "autotune_pair", "energy_noalloc", "Batch", "autotune_spmv", "Server",
+    "TQ_REQ_EVOLVE", "TQ_REQ_ENERGY", "TQ_REQ_GRADIENTS",
 ]
 
 
@@ -398,6 +402,79 @@ class Batch:
         try:
             if self.handle:
                 lib().tq_batch_free(self.handle)
+                self.handle = None
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------------- request loop
+
+class Server:
+    """Continuous-batching request loop over resident sessions (owns ``ctx`` while running)."""
+
+    def __init__(self, ctx, prec=TQ_C64, hbm_budget=4 << 30, max_batch=512):
+        self.ctx, self.prec = ctx, prec
+        h = C.c_void_p()
+        call("tq_server_create", ctx.handle, prec, C.c_size_t(int(hbm_budget)), int(max_batch), C.byref(h))
+        self.handle = h
+        self._keep = []
+        self._out = (Completion * 4096)()
+
+    def add_hamiltonian(self, ham, pool):
+        i = C.c_int()
+        call("tq_server_add_hamiltonian", self.handle, ham.handle, pool.handle, C.byref(i))
+        self._keep += [ham, pool]
+        return i.value
+
+    def add_session(self, ham_id, n_electrons, mapping):
+        i = C.c_int()
+        call("tq_server_add_session", self.handle, int(ham_id), int(n_electrons), int(mapping), C.byref(i))
+        return i.value
+
+    def start(self):
+        call("tq_server_start", self.handle)
+
+    def submit(self, kind, session, op=0, theta=0.0, tag=0):
+        r = Request(int(kind), int(session), int(op), 0, float(theta), int(tag))
+        call("tq_server_submit", self.handle, C.byref(r))
+
+    def poll(self, timeout_us=1000):
+        """Completions as dicts (empty list on timeout)."""
+        n = C.c_int()
+        rc = lib().tq_server_poll(self.handle, self._out, len(self._out), C.byref(n), int(timeout_us))
+        if rc == -4:
+            return []
+        if rc != 0:
+            raise TQError(rc, "tq_server_poll", lib().tq_last_error().decode())
+        return [{f: getattr(self._out[i], f) for f, _ in Completion._fields_} for i in range(n.value)]
+
+    def stats(self):
+        t, c, q = C.c_longlong(), C.c_longlong(), C.c_longlong()
+        call("tq_server_stats", self.handle, C.byref(t), C.byref(c), C.byref(q))
+        return {"ticks": t.value, "completed": c.value, "queued": q.value}
+
+    def state(self, session):
+        """Copy of a session's state (call when idle), complex128 numpy."""
+        import torch
+        ptr, nq = C.c_void_p(), C.c_int()
+        call("tq_server_session_state", self.handle, int(session), C.byref(ptr), C.byref(nq))
+        n = 1 << nq.value
+        typestr = "<c16" if self.prec == TQ_C128 else "<c8"
+
+        class _View:
+            __cuda_array_interface__ = {"shape": (n,), "typestr": typestr,
+                                        "data": (ptr.value, False), "version": 3}
+
+        torch.cuda.synchronize()
+        return torch.as_tensor(_View(), device="cuda").cpu().numpy().astype(np.complex128)
+
+    def stop(self):
+        call("tq_server_stop", self.handle)
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().tq_server_free(self.handle)
                 self.handle = None
         except Exception:
             pass

@@ -25,6 +25,17 @@ class TQError(RuntimeError):
         self.code = code
 
 
+class Request(C.Structure):
+    _fields_ = [("kind", C.c_int), ("session", C.c_int), ("op", C.c_int), ("pad", C.c_int),
+                ("theta", C.c_double), ("tag", C.c_ulonglong)]
+
+
+class Completion(C.Structure):
+    _fields_ = [("tag", C.c_ulonglong), ("kind", C.c_int), ("session", C.c_int), ("status", C.c_int),
+                ("argmax", C.c_int), ("energy", C.c_double), ("max_grad", C.c_double),
+                ("norm2", C.c_double), ("t_submit", C.c_double), ("t_done", C.c_double)]
+
+
 class AdaptResult(C.Structure):
     _fields_ = [("energy", C.c_double), ("max_grad", C.c_double), ("theta", C.c_double),
                 ("selected", C.c_int), ("converged", C.c_int)]
@@ -83,6 +94,16 @@ SIGNATURES = {
     "tq_batch_results": [vp, vp, vp, vp, vp, vp, vp],
     "tq_batch_state": [vp, i32, P(vp), P(i32)],
     "tq_batch_free": [vp],
+    "tq_server_create": [vp, i32, C.c_size_t, i32, P(vp)],
+    "tq_server_add_hamiltonian": [vp, vp, vp, P(i32)],
+    "tq_server_add_session": [vp, i32, i32, i32, P(i32)],
+    "tq_server_start": [vp],
+    "tq_server_submit": [vp, P(Request)],
+    "tq_server_poll": [vp, vp, i32, P(i32), i32],
+    "tq_server_stats": [vp, P(i64), P(i64), P(i64)],
+    "tq_server_session_state": [vp, i32, P(vp), P(i32)],
+    "tq_server_stop": [vp],
+    "tq_server_free": [vp],
 }
 _RET = {"tq_last_error": C.c_char_p}
 
