@@ -148,12 +148,14 @@ class ClockSampler:
 
 # -------------------------------------------------------- CPU oracle timing
 
-def _oracle_worker(args):
-    """Oracle Taylor-5 updates on a slice of sample states for ~`seconds`."""
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
-    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
-    idx, seconds = args
-    import numpy as np
+_ORACLE_CACHE = {}
+
+
+def _oracle_setup(idx):
+    """Oracle-side inputs of a worker's sample states (cached per process)."""
+    key = tuple(idx)
+    if key in _ORACLE_CACHE:
+        return _ORACLE_CACHE[key]
     import synth
     from oracle import adapt, evolve, pauli
     exc, pps = pauli.pool_pauli(N_SPATIAL, N_ELECTRONS, MAPPING)
@@ -170,24 +172,37 @@ def _oracle_worker(args):
         psi = adapt.hf_state(NQ, N_ELECTRONS, MAPPING)
         for j in range(prep_k.shape[1]):
             psi = evolve.taylor5(A(int(prep_k[b, j])), psi, prep_th[b, j])
-        A(int(k[b]))
-        states.append(psi)
+        states.append((psi, A(int(k[b])), float(th[b])))
+    _ORACLE_CACHE[key] = states
+    return states
+
+
+def _oracle_worker(args):
+    """Oracle Taylor-5 updates on a slice of sample states for ~`seconds`."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    idx, seconds = args
+    from oracle import evolve
+    states = _oracle_setup(idx)
     n = 0
     t0 = time.perf_counter()
     while True:
-        for b, psi in zip(idx, states):
-            evolve.taylor5(A(int(k[b])), psi, th[b])
+        for psi, A, th in states:
+            evolve.taylor5(A, psi, th)
             n += 1
         el = time.perf_counter() - t0
         if el >= seconds:
             return n, el
 
 
-def cpu_oracle_rate(seconds=12.0, states_per_core=4, cores=None):
+def cpu_oracle_rate(seconds=12.0, states_per_core=4, cores=None, pool=None):
     cores = cores or os.cpu_count() or 1
     jobs = [(list(range(c * states_per_core, (c + 1) * states_per_core)), seconds) for c in range(cores)]
-    ctx = mp.get_context("spawn")
-    with ctx.Pool(cores) as pool:
+    if pool is None:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(cores) as p:
+            res = p.map(_oracle_worker, jobs)
+    else:
         res = pool.map(_oracle_worker, jobs)
     n = sum(r[0] for r in res)
     t = max(r[1] for r in res)
@@ -203,14 +218,15 @@ def run_ours(args, rank, world, local_rank):
     import paper_2606_29692_gb300 as tq
     import synth
 
+    from paper_2606_29692_gb300 import dist as tqd
+
     torch.cuda.set_device(local_rank)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    tqd.init("nccl", torch.device("cuda", local_rank))
     S = args.states
     ctx = tq.Context(local_rank)
     pool = tq.build_pool(ctx, N_SPATIAL, N_ELECTRONS, MAPPING)
-    prep_k, prep_th, k, th = synth.t5_batch(S, pool.M)
+    # every rank updates its own batch of S states (weak scaling, no exchange)
+    prep_k, prep_th, k, th = synth.t5_batch(S, pool.M, seed=tqd.rank_seed(synth.SEED_T5_BATCH, rank))
     hf = tq.hf_index(NQ, N_ELECTRONS, MAPPING)
     psi = torch.zeros((S, D), dtype=torch.complex64, device="cuda")
     psi[:, hf] = 1.0
@@ -231,18 +247,10 @@ def run_ours(args, rank, world, local_rank):
     def step():
         tq.evolve_taylor5_batch(ctx, pool, psi, dk, dth, dn)
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
+    barrier = tqd.barrier
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return tqd.max_over_ranks(x, device="cuda")
 
     for _ in range(args.warmup):
         step()
@@ -272,7 +280,7 @@ def run_ours(args, rank, world, local_rank):
     rep = ctx.trace_report()
     ctx.trace(False)
     t = max_over_ranks(e0.elapsed_time(e1) / 1e3)
-    value = world * S * args.steps / t
+    value = tqd.weak_scaling_value(S, world, args.steps, t)
     pair_n, pair_ms = rep.get("taylor5_pair", (0, float("nan")))
     pair_s = pair_ms / max(pair_n, 1) / 1e3
     alg_bytes = S * 2 * D * 8                       # read + write each amplitude once
@@ -489,7 +497,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true",
-                    help="skip the SpMV and trajectory-batch measurements")
+                    help="skip the SpMV, trajectory-batch and request-loop measurements")
+    ap.add_argument("--section", choices=["spmv", "trajectories", "serving"], default=None,
+                    help="run one secondary measurement alone and print its JSON (profiling)")
     ap.add_argument("--spmv-qubits", type=int, default=18)
     ap.add_argument("--traj", type=int, default=256)
     ap.add_argument("--serve-seconds", type=float, default=10.0,
@@ -508,6 +518,22 @@ def main():
         if rank != 0:
             return 0
         return run_reference(args, world)
+
+    if args.section:
+        if rank != 0:
+            return 0
+        import torch
+
+        import paper_2606_29692_gb300 as tq
+        torch.cuda.set_device(local_rank)
+        ctx = tq.Context(local_rank)
+        if args.section == "spmv":
+            print(json.dumps(measure_spmv(tq, ctx, args.spmv_qubits)))
+        elif args.section == "trajectories":
+            print(json.dumps(measure_trajectories(tq, ctx, args.traj)))
+        else:
+            print(json.dumps(measure_serving(tq, local_rank, args.serve_seconds, args.serve_rate)))
+        return 0
 
     out = run_ours(args, rank, world, local_rank)
     if rank == 0:
@@ -532,10 +558,11 @@ def run_reference(args, world):
     cores = os.cpu_count() or 1
     per_step = max(1.0, min(6.0, 150.0 / max(1, args.steps + args.warmup)))
     rates = []
-    for i in range(args.warmup + args.steps):
-        rate, c, n, t = cpu_oracle_rate(per_step, states_per_core=2, cores=cores)
-        if i >= args.warmup:
-            rates.append((n, t))
+    with mp.get_context("spawn").Pool(cores) as pool:
+        for i in range(args.warmup + args.steps):
+            rate, c, n, t = cpu_oracle_rate(per_step, states_per_core=2, cores=cores, pool=pool)
+            if i >= args.warmup:
+                rates.append((n, t))
     n = sum(r[0] for r in rates)
     t = sum(r[1] for r in rates)
     value = n / t
@@ -545,8 +572,8 @@ def run_reference(args, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
         "data": "synthetic", "config": workload_config(args.states),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": (f"each step: {per_step:.1f} s of oracle updates on "
-                                    f"{2 * cores} states of the workload across {cores} spawn workers")},
+                         "sample": (f"each step: {per_step:.1f} s of oracle updates (scipy CSR complex128) "
+                                    f"on {2 * cores} states of the workload across {cores} spawn workers")},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out))
