@@ -120,16 +120,15 @@ kb_energy(const TrajDev* tr, TrajState* ts, const int4* items, int n_items, doub
             last = atomicAdd(&ts[t].etick, 1u) == (unsigned)d.ecnt - 1;
         }
         __syncthreads();
-        if (last && threadIdx.x == 0) {
-            double a = 0.0, b = 0.0;
-            for (int i = d.eoff; i < d.eoff + d.ecnt; ++i) {
-                a += __ldcg(part + 2 * i);
-                b += __ldcg(part + 2 * i + 1);
+        if (last) {
+            double a, b;
+            block_sum_pairs(part, d.eoff, d.ecnt, sh, a, b);
+            if (threadIdx.x == 0) {
+                ts[t].e_num = a;
+                ts[t].e_den = b;
+                ts[t].energy = a / b;
+                ts[t].etick = 0u;
             }
-            ts[t].e_num = a;
-            ts[t].e_den = b;
-            ts[t].energy = a / b;
-            ts[t].etick = 0u;
         }
         __syncthreads();
     }

@@ -86,6 +86,21 @@ __device__ __forceinline__ void block_sum(double (&v)[n], double* sh) {
     __syncthreads();
 }
 
+// Sums of n (num, den) partial pairs part[2i], part[2i+1], i in [first,
+// first + n), by the whole block in a fixed order (strided, then a fixed
+// tree); result in thread 0.  Reads bypass L1 (other CTAs wrote them).
+__device__ __forceinline__ void block_sum_pairs(const double* part, int first, int n, double* sh,
+                                                double& a, double& b) {
+    double v[2] = {0.0, 0.0};
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        v[0] += __ldcg(part + 2 * (first + i));
+        v[1] += __ldcg(part + 2 * (first + i) + 1);
+    }
+    block_sum<2>(v, sh);
+    a = v[0];
+    b = v[1];
+}
+
 // Value A_k[r][r ^ x] of pool generator k at column col = r ^ x.
 template <typename T>
 __device__ __forceinline__ T op_value(const PoolView& p, int k, uint32_t col);

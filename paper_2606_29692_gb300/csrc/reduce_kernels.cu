@@ -56,16 +56,15 @@ k_energy_csr(HamView h, const typename C2<T>::type* __restrict__ psi, double2* _
         partials[2 * blockIdx.x] = v[0];
         partials[2 * blockIdx.x + 1] = v[1];
     }
-    if (last_block(ticket, gridDim.x) && threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (unsigned i = 0; i < gridDim.x; ++i) {
-            a += __ldcg(partials + 2 * i);
-            b += __ldcg(partials + 2 * i + 1);
+    if (last_block(ticket, gridDim.x)) {
+        double a, b;
+        block_sum_pairs(partials, 0, (int)gridDim.x, sh, a, b);
+        if (threadIdx.x == 0) {
+            step->e_num = a;
+            step->e_den = b;
+            step->energy = a / b;
+            *ticket = 0u;
         }
-        step->e_num = a;
-        step->e_den = b;
-        step->energy = a / b;
-        *ticket = 0u;
     }
 }
 
@@ -109,16 +108,15 @@ k_energy_mf(HamView h, const typename C2<T>::type* __restrict__ psi, double* par
         partials[2 * blockIdx.x] = v[0];
         partials[2 * blockIdx.x + 1] = v[1];
     }
-    if (last_block(ticket, gridDim.x) && threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (unsigned i = 0; i < gridDim.x; ++i) {
-            a += __ldcg(partials + 2 * i);
-            b += __ldcg(partials + 2 * i + 1);
+    if (last_block(ticket, gridDim.x)) {
+        double a, b;
+        block_sum_pairs(partials, 0, (int)gridDim.x, sh, a, b);
+        if (threadIdx.x == 0) {
+            step->e_num = a;
+            step->e_den = b;
+            step->energy = a / b;
+            *ticket = 0u;
         }
-        step->e_num = a;
-        step->e_den = b;
-        step->energy = a / b;
-        *ticket = 0u;
     }
 }
 

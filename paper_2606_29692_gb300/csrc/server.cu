@@ -100,14 +100,13 @@ ks_energy(ReqDev* E, const Idx* ix, int n, double* epart) {
             last = atomicAdd(&d.etick, 1u) == (unsigned)(ix->e_off[q + 1] - ix->e_off[q]) - 1;
         }
         __syncthreads();
-        if (last && threadIdx.x == 0) {
-            double a = 0.0, b = 0.0;
-            for (int i = ix->e_off[q]; i < ix->e_off[q + 1]; ++i) {
-                a += __ldcg(epart + 2 * i);
-                b += __ldcg(epart + 2 * i + 1);
+        if (last) {
+            double a, b;
+            block_sum_pairs(epart, ix->e_off[q], ix->e_off[q + 1] - ix->e_off[q], sh, a, b);
+            if (threadIdx.x == 0) {
+                d.e_den = b;
+                d.energy = a / b;
             }
-            d.e_den = b;
-            d.energy = a / b;
         }
         __syncthreads();
     }
