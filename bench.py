@@ -308,6 +308,7 @@ def run_ours(args, rank, world, local_rank):
     finite = bool(torch.isfinite(dn).all().item()) and float(dn.min().item()) > 0.5
     extra = {}
     if rank == 0 and not args.headline_only:
+        extra["fp64_single_instance"] = measure_fp64_single(tq, ctx, pool, k, th)
         extra["spmv"] = measure_spmv(tq, ctx, args.spmv_qubits)
         extra["trajectories"] = measure_trajectories(tq, ctx, args.traj)
         if args.serve_seconds > 0:
@@ -337,6 +338,29 @@ def run_ours(args, rank, world, local_rank):
         }
         out.update(extra)
     return out
+
+
+def measure_fp64_single(tq, ctx, pool, k, th, reps=2000):
+    """The plain float64 single-instance form: one 14-qubit complex128 state
+    per call, renormalised after each update (as the ADAPT step does)."""
+    import torch
+    st = tq.State(ctx, NQ, tq.TQ_C128)
+    tq.state_set_hf(st, N_ELECTRONS, MAPPING)
+    for i in range(20):
+        tq.evolve_taylor5(ctx, pool, int(k[i]), float(th[i]), st, renormalize=True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for i in range(reps):
+        tq.evolve_taylor5(ctx, pool, int(k[i % len(k)]), float(th[i % len(th)]), st, renormalize=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"workload": "one 14-qubit complex128 state, evolve_taylor5 with renormalisation per call, "
+                        "back-to-back calls on one stream",
+            "updates_per_s": 1e3 / ms, "us_per_update": ms * 1e3,
+            "launches_per_update": 3}
 
 
 def measure_spmv(tq, ctx, nq):

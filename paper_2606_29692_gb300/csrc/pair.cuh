@@ -137,6 +137,8 @@ struct OpRec {
     uint32_t x, z0, d0, d1, d2;
     int t;        // target parities (bits 0..2)
     int dcode;    // 4 x 4-bit parity codes of delta in {0, 1, x, x^1}
+    int unit;     // |c0| == 1: every entry of A is 0 or +-1
+    int c0neg;    // c0 < 0
     T c0;
 };
 
@@ -150,6 +152,8 @@ __device__ __forceinline__ OpRec<T> make_rec(const PoolView& p, int k) {
     o.d2 = p.fd[3 * k + 2];
     o.t = p.ft[k];
     o.c0 = sizeof(T) == 4 ? (T)p.fc0f[k] : (T)p.fc0d[k];
+    o.unit = fabsf(p.fc0f[k]) == 1.0f;
+    o.c0neg = p.fc0f[k] < 0.0f;
     const uint32_t dl[4] = {0u, 1u, o.x, o.x ^ 1u};
     int code = 0;
     for (int j = 0; j < 4; ++j) {
@@ -166,6 +170,41 @@ __device__ __forceinline__ OpRec<T> make_rec(const PoolView& p, int k) {
 template <typename T>
 __device__ __forceinline__ T rec_value(const OpRec<T>& o, int code) {
     return (code & 7) != o.t ? T(0) : ((code & 8) ? -o.c0 : o.c0);
+}
+
+// Entry of A as an integer -1, 0, +1 (valid when op.unit).
+template <typename T>
+__device__ __forceinline__ int rec_sign(const OpRec<T>& o, int code) {
+    if ((code & 7) != o.t) return 0;
+    return ((code & 8) != 0) != (o.c0neg != 0) ? -1 : 1;
+}
+
+// s * v for s in {-1, 0, +1} with integer masks on the float64 bit
+// patterns: bit-identical to the float64 product, and no float64
+// instruction (this part issues float64 at about 1/57 of float32).
+__device__ __forceinline__ double2 sign_apply(int s, double2 v) {
+    const unsigned long long keep = s != 0 ? ~0ull : 0ull;
+    const unsigned long long flip = s < 0 ? 0x8000000000000000ull : 0ull;
+    return make_double2(__longlong_as_double((__double_as_longlong(v.x) & keep) ^ flip),
+                        __longlong_as_double((__double_as_longlong(v.y) & keep) ^ flip));
+}
+
+// The five-product chain of complex128 pairs with entries of A in
+// {-1, 0, +1}: only the accumulation uses the float64 pipe.
+__device__ __forceinline__ void chain_pair_sign(int s_r, int s_q, const double (&cf)[6], double2& ar,
+                                                double2& aq) {
+    double2 vr = ar, vq = aq;
+#pragma unroll
+    for (int k = 1; k <= 5; ++k) {
+        const double2 nr = sign_apply(s_r, vq);
+        const double2 nq = sign_apply(s_q, vr);
+        vr = nr;
+        vq = nq;
+        ar.x = fma(cf[k], vr.x, ar.x);
+        ar.y = fma(cf[k], vr.y, ar.y);
+        aq.x = fma(cf[k], vq.x, aq.x);
+        aq.y = fma(cf[k], vq.y, aq.y);
+    }
 }
 
 template <typename T>
@@ -217,15 +256,25 @@ __device__ __forceinline__ T pair_tile(const OpRec<T>& op, double theta,
             // are r0 ^ {x, x^1, 0, 1}
             const uint32_t q0 = r0 ^ x;
             const int bc = base_code(op, r0);
-            const T s_r0 = rec_value(op, bc ^ ((op.dcode >> 8) & 15));    // col q0
-            const T s_r1 = rec_value(op, bc ^ ((op.dcode >> 12) & 15));   // col q0^1
-            const T s_q0 = rec_value(op, bc ^ (op.dcode & 15));           // col r0
-            const T s_q1 = rec_value(op, bc ^ ((op.dcode >> 4) & 15));    // col r0+1
+            const int c_r0 = bc ^ ((op.dcode >> 8) & 15);    // col q0
+            const int c_r1 = bc ^ ((op.dcode >> 12) & 15);   // col q0^1
+            const int c_q0 = bc ^ (op.dcode & 15);           // col r0
+            const int c_q1 = bc ^ ((op.dcode >> 4) & 15);    // col r0+1
             V a0 = e0[j], a1 = e1[j];
             V b0 = (q0 & 1u) ? f1[j] : f0[j];   // psi[q0]
             V b1 = (q0 & 1u) ? f0[j] : f1[j];   // psi[q0 ^ 1]
-            chain_pair(s_r0, s_q0, cf, a0, b0);
-            chain_pair(s_r1, s_q1, cf, a1, b1);
+            if constexpr (sizeof(T) == 8) {
+                if (op.unit) {
+                    chain_pair_sign(rec_sign(op, c_r0), rec_sign(op, c_q0), cf, a0, b0);
+                    chain_pair_sign(rec_sign(op, c_r1), rec_sign(op, c_q1), cf, a1, b1);
+                } else {
+                    chain_pair(rec_value(op, c_r0), rec_value(op, c_q0), cf, a0, b0);
+                    chain_pair(rec_value(op, c_r1), rec_value(op, c_q1), cf, a1, b1);
+                }
+            } else {
+                chain_pair(rec_value(op, c_r0), rec_value(op, c_q0), cf, a0, b0);
+                chain_pair(rec_value(op, c_r1), rec_value(op, c_q1), cf, a1, b1);
+            }
             tpart += a0.x * a0.x + a0.y * a0.y + a1.x * a1.x + a1.y * a1.y;
             tpart += b0.x * b0.x + b0.y * b0.y + b1.x * b1.x + b1.y * b1.y;
             store2(base, r0, a0, a1);
