@@ -908,11 +908,12 @@ extern "C" int tq_adapt_step(tq_ctx* c, const tq_ham* h, const tq_pool* p, tq_st
 extern "C" int tq_evolve_taylor5_batch(tq_ctx* c, const tq_pool* p, int n_states, int prec, void* psi,
                                        const int* k, const double* theta, double* norm2, void* stream) {
     API_BEGIN
-    TQ_REQUIRE(c && p && psi && k && theta, "null argument");
+    TQ_REQUIRE(c && p, "null argument");
     TQ_REQUIRE(n_states >= 0, "n_states < 0");
     check_prec(prec);
+    if (n_states == 0) return TQ_OK;   // an empty batch is a no-op
+    TQ_REQUIRE(psi && k && theta, "null argument");
     TQ_REQUIRE(((uintptr_t)psi & 15u) == 0, "psi must be 16-byte aligned");
-    if (n_states == 0) return TQ_OK;
     set_device(c);
     cudaStream_t s = as_stream(stream);
     const int upt = c->pair_upt[prec];
@@ -928,10 +929,11 @@ extern "C" int tq_evolve_taylor5_batch_host(tq_ctx* c, const tq_pool* p, int n_s
                                             void* psi_host, const int* k_host, const double* theta_host,
                                             double* norm2_host) {
     API_BEGIN
-    TQ_REQUIRE(c && p && psi_host && k_host && theta_host, "null argument");
+    TQ_REQUIRE(c && p, "null argument");
     TQ_REQUIRE(n_states >= 0, "n_states < 0");
     check_prec(prec);
-    if (n_states == 0) return TQ_OK;
+    if (n_states == 0) return TQ_OK;   // an empty batch is a no-op
+    TQ_REQUIRE(psi_host && k_host && theta_host, "null argument");
     set_device(c);
     for (auto& st : c->aux)
         if (!st) TQ_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));

@@ -129,3 +129,16 @@ def test_full_size_batch_sampled(ctx):
             assert abs(g["energy"][i] - r.energy) <= 1e-6
         assert fidelity(b.state(tr.index), psi) > 0.999999
     assert all(np.isfinite(x["energy"]).all() for x in got)
+
+
+def test_zero_length_and_single_trajectory(ctx):
+    spec = [(3, 2, 0, 15, 0), (2, 2, 1, 17, 1)]
+    b, th = _build(ctx, spec, tq.TQ_C128)
+    b.run()
+    r = b.results()
+    assert r[0]["n_iter"] == 0 and r[0]["energy"].size == 0
+    assert np.array_equal(b.state(0), oadapt.hf_state(6, 2, 0))
+    ref = _oracle(spec[1:], th[1:])[0]
+    assert r[1]["n_iter"] == len(ref[0]) == 1
+    assert abs(r[1]["energy"][0] - ref[0][0].energy) <= 1e-10
+    assert rel_l2(b.state(1), ref[1]) <= 1e-12

@@ -254,6 +254,17 @@ def test_invalid_op_index_poisons_norm(ctx):
     assert torch.equal(psi[1:], before[1:])
 
 
+def test_empty_batch_is_a_noop(ctx):
+    import torch
+    pool = tq.build_pool(ctx, 4, 4, 0)
+    for prec, dt in ((tq.TQ_C64, torch.complex64), (tq.TQ_C128, torch.complex128)):
+        psi = torch.zeros((0, 256), dtype=dt, device="cuda")
+        k = torch.zeros(0, dtype=torch.int32, device="cuda")
+        th = torch.zeros(0, dtype=torch.float64, device="cuda")
+        tq.evolve_taylor5_batch(ctx, pool, psi, k, th, None, prec=prec)
+        tq.evolve_taylor5_batch_host(ctx, pool, psi.cpu(), k.cpu(), th.cpu(), None, prec=prec)
+
+
 def test_evolve_rejects_bad_arguments(ctx):
     pool = tq.build_pool(ctx, 4, 4, 0)
     st = to_state(ctx, synth.random_state(8, 1), 8, tq.TQ_C128)
