@@ -364,7 +364,7 @@ def measure_fp64_single(tq, ctx, pool, k, th, reps=2000):
 
 
 def measure_spmv(tq, ctx, nq):
-    """Energy (fused CSR SpMV + float64 dots) on a Hamiltonian larger than L2."""
+    """Energy (fused SpMV + float64 dots) on a Hamiltonian larger than L2, every schedule timed."""
     import numpy as np
     import torch
 
@@ -381,26 +381,45 @@ def measure_spmv(tq, ctx, nq):
     pool = tq.build_pool(ctx, n, ne, 1)
     for k in range(0, pool.M, max(1, pool.M // 8)):
         tq.evolve_taylor5(ctx, pool, k, 0.1, st, renormalize=True)
-    lanes, _ = tq.autotune_spmv(ctx, ham, st)
-    for _ in range(3):
-        tq.energy(ctx, ham, st)
-    ctx.trace(True)
+    best, _ = tq.autotune_spmv(ctx, ham, st)
     reps = 20
-    for _ in range(reps):
-        e = tq.energy(ctx, ham, st)
-    rep = ctx.trace_report()
-    ctx.trace(False)
-    n_l, ms = rep["energy_csr"]
-    ms /= n_l
+
+    def timed(sched):
+        ctx.set_spmv_schedule(sched)
+        for _ in range(3):
+            tq.energy(ctx, ham, st)
+        ctx.trace(True)
+        for _ in range(reps):
+            e = tq.energy(ctx, ham, st)
+        rep = ctx.trace_report()
+        ctx.trace(False)
+        n_l, t = rep["energy_xell" if sched == tq.TQ_SPMV_XELL else "energy_csr"]
+        return t / n_l, e
+
+    per_sched = {}
+    for sched in (4, 8, 16, 32, tq.TQ_SPMV_XELL):
+        per_sched["xell" if sched == tq.TQ_SPMV_XELL else f"csr_lanes_{sched}"] = timed(sched)[0]
+    ms, e = timed(best)
+    nb, npairs = tq.ham_xell(ham)[:2]
+    # what the method must move (CSR of float32 values, float64 diagonal, state in, w out)
     alg = 4 * (D + 1) + 8 * ham.nnz + 8 * D + 8 * D + 16 * D
+    # what the chosen layout moves
+    if best == tq.TQ_SPMV_XELL:
+        layout = 4 * (nb + 1) + (4 + 8 * 4) * npairs + 8 * D + 8 * D + 16 * D
+        kernel = "k_energy_xell_tma<float,float>"
+    else:
+        layout = alg
+        kernel = f"k_energy_csr<float,float,{best}>"
     peak, _ = peaks()
     gbs = alg / (ms * 1e-3) / 1e9
     return {"workload": f"energy of a {nq}-qubit BK Hamiltonian (synthetic, {n} orbitals, "
-                        f"{ne} electrons), complex64 state, float32 CSR + float64 diagonal",
-            "kernel": "k_energy_csr<float,float>", "nnz": ham.nnz, "hamiltonian_bytes": ham.device_bytes,
-            "build_s": build_s, "ms_per_energy": ms, "lanes_per_row": lanes,
-            "algorithmic_bytes": alg, "achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak,
-            "energy": e, "l2_policy": "CSR larger than L2"}
+                        f"{ne} electrons), complex64 state, float32 off-diagonal values + float64 diagonal",
+            "kernel": kernel, "schedule": "xell" if best == tq.TQ_SPMV_XELL else f"csr_lanes_{best}",
+            "nnz": ham.nnz, "xell_pairs": npairs, "hamiltonian_bytes": ham.device_bytes,
+            "build_s": build_s, "ms_per_energy": ms, "ms_per_schedule": per_sched,
+            "algorithmic_bytes": alg, "layout_bytes": layout, "achieved_gbs": gbs,
+            "layout_gbs": layout / (ms * 1e-3) / 1e9, "peak_gbs": peak, "frac": gbs / peak,
+            "energy": e, "l2_policy": "Hamiltonian larger than L2"}
 
 
 def measure_serving(tq, device, seconds, rate):

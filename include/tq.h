@@ -107,9 +107,16 @@ int tq_ctx_get_pair_schedule(const tq_ctx* ctx, int prec, int* units_per_thread)
 int tq_autotune_pair(tq_ctx* ctx, const tq_pool* pool, int prec, int n_states,
                      int* best_units_per_thread, double* best_ms);
 
-/* Lanes that share one Hamiltonian row in the energy SpMV (4, 8, 16, 32;
- * default 32), and its autotuner: times tq_energy's launch at each value on
- * (ham, psi), keeps the fastest.  Synchronises the device. */
+/* Schedule of the energy SpMV (the H pass of tq_energy, tq_pool_gradients
+ * and tq_adapt_step): 4, 8, 16 or 32 lanes sharing one row of the CSR
+ * (default 32), or TQ_SPMV_XELL for the XOR-ELL layout.  Every Hamiltonian
+ * holds both layouts of the same off-diagonal entries: the CSR, and blocks
+ * of 8 rows where each X-mask present in the block stores its 8 values
+ * H[8R+i][(8R+i)^x] (zero where the CSR has no entry), so one pair's 8
+ * gathers read one aligned run of 8 amplitudes.  The autotuner times
+ * tq_energy's launch under every schedule on (ham, psi) and keeps the
+ * fastest.  Synchronises the device. */
+enum { TQ_SPMV_XELL = 0 };
 int tq_ctx_set_spmv_schedule(tq_ctx* ctx, int lanes_per_row);
 int tq_autotune_spmv(tq_ctx* ctx, const tq_ham* ham, const tq_state* psi,
                      int* best_lanes_per_row, double* best_ms);
@@ -178,6 +185,17 @@ int tq_ham_info(const tq_ham* ham, int* n_qubits, int* prec, long long* nnz,
 /* Borrowed device pointers (valid until tq_ham_free). */
 int tq_ham_csr(const tq_ham* ham, const int** rowptr, const int** col,
                const void** val, const double** diag);
+/* Borrowed device pointers to the XOR-ELL layout of the same off-diagonal
+ * entries (no counterpart in the paper; it is a second storage order of
+ * the CSR's values).  Rows come in blocks of 8; block R's pairs are
+ * xptr[R] .. xptr[R+1]-1 (int32, n_blocks + 1 = ceil(2^N / 8) + 1 entries),
+ * pair p has X-mask xmask[p] (uint32) and values xval[8p + i] =
+ * H[8R+i][(8R+i) ^ xmask[p]] (double for TQ_C128, float for TQ_C64, zero
+ * where the CSR drops the entry); a block's pairs are the X-mask groups
+ * with a kept entry in any of its rows, in ascending group order.  Any
+ * output pointer may be NULL. */
+int tq_ham_xell(const tq_ham* ham, long long* n_blocks, long long* n_pairs,
+                const int** xptr, const unsigned** xmask, const void** xval);
 int tq_ham_free(tq_ham* ham);
 
 /* ------------------------------------------------------------------- pool */
@@ -239,9 +257,12 @@ int tq_evolve_taylor5_csr(tq_ctx* ctx, int n_qubits, const int* rowptr,
                           tq_state* psi, int renormalize, void* stream);
 
 /* Energy of Eq. (1): E = Re<psi|H|psi> / <psi|psi>, float64.  One fused
- * pass: CSR SpMV (w = H psi, kept in context scratch for
- * tq_pool_gradients) and float64 warp-shuffle dot products.  Writes the
- * host scalar *E (synchronises the stream). */
+ * pass: SpMV over the CSR or the XOR-ELL layout (the context's SpMV
+ * schedule; w = H psi, kept in context scratch for tq_pool_gradients) and
+ * float64 warp-shuffle dot products.  The XOR-ELL pass streams its pairs
+ * through shared memory with bulk copies; its waits are bounded, and a
+ * wait that runs out returns TQ_ETIMEOUT (E is then NaN).  Writes the host
+ * scalar *E (synchronises the stream). */
 int tq_energy(tq_ctx* ctx, const tq_ham* ham, const tq_state* psi, double* E,
               void* stream);
 /* Energy that allocates nothing (the paper has no counterpart: it serves

@@ -17,6 +17,7 @@ from ._native import (TQ_BK, TQ_C64, TQ_C128, TQ_JW, AdaptResult, Completion, Re
                       lib)
 
 TQ_REQ_EVOLVE, TQ_REQ_ENERGY, TQ_REQ_GRADIENTS = 0, 1, 2
+TQ_SPMV_XELL = 0      # energy-SpMV schedule: the XOR-ELL layout (else CSR lanes per row)
 
 __all__ = [
     "TQ_JW", "TQ_BK", "TQ_C128", "TQ_C64", "TQError", "Context", "Hamiltonian", "Pool", "State",
@@ -24,7 +25,7 @@ __all__ = [
     "build_pool", "evolve_taylor5", "evolve_taylor5_csr", "energy", "energy_matrix_free",
     "pool_gradients", "adapt_step", "evolve_taylor5_batch", "evolve_taylor5_batch_host",
     "state_set_hf", "pool_csr", "ham_csr", "lib", "autotune_pair", "energy_noalloc", "Batch", "autotune_spmv", "Server",
-    "TQ_REQ_EVOLVE", "TQ_REQ_ENERGY", "TQ_REQ_GRADIENTS",
+    "TQ_REQ_EVOLVE", "TQ_REQ_ENERGY", "TQ_REQ_GRADIENTS", "TQ_SPMV_XELL", "ham_xell",
 ]
 
 
@@ -119,6 +120,7 @@ class Context:
         return u.value
 
     def set_spmv_schedule(self, lanes_per_row):
+        """4, 8, 16 or 32 CSR lanes per row, or TQ_SPMV_XELL."""
         call("tq_ctx_set_spmv_schedule", self.handle, int(lanes_per_row))
 
     def trace(self, enable=True):
@@ -242,6 +244,14 @@ def ham_csr(ham):
     return rp.value, cl.value, vl.value, dg.value
 
 
+def ham_xell(ham):
+    """(n_blocks, n_pairs, xptr, xmask, xval) of the XOR-ELL layout (borrowed device pointers)."""
+    nb, npairs = C.c_longlong(), C.c_longlong()
+    xp, xm, xv = C.c_void_p(), C.c_void_p(), C.c_void_p()
+    call("tq_ham_xell", ham.handle, C.byref(nb), C.byref(npairs), C.byref(xp), C.byref(xm), C.byref(xv))
+    return nb.value, npairs.value, xp.value, xm.value, xv.value
+
+
 def pool_csr(ctx, pool, k, prec=TQ_C128):
     """(rowptr, col, val, nnz) of generator k (device pointers, built on demand)."""
     rp, cl, vl, nnz = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_longlong()
@@ -313,7 +323,9 @@ def autotune_pair(ctx, pool, prec=TQ_C64, n_states=1024):
 
 
 def autotune_spmv(ctx, ham, state):
-    """Time every energy-SpMV schedule on (ham, state); set and return (lanes, ms)."""
+    """Time every energy-SpMV schedule on (ham, state); set and return (schedule, ms).
+
+    The schedule is a CSR lanes-per-row count or TQ_SPMV_XELL."""
     l, ms = C.c_int(), C.c_double()
     call("tq_autotune_spmv", ctx.handle, ham.handle, state.handle, C.byref(l), C.byref(ms))
     return l.value, ms.value

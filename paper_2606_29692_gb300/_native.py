@@ -68,6 +68,7 @@ SIGNATURES = {
     "tq_build_hamiltonian": [vp, i32, vp, vp, f64, i32, i32, P(vp)],
     "tq_ham_info": [vp, P(i32), P(i32), P(i64), P(i64), P(i64), P(i64), P(C.c_size_t)],
     "tq_ham_csr": [vp, P(vp), P(vp), P(vp), P(vp)],
+    "tq_ham_xell": [vp, P(i64), P(i64), P(vp), P(vp), P(vp)],
     "tq_ham_free": [vp],
     "tq_build_pool": [vp, i32, i32, i32, P(vp)],
     "tq_pool_info": [vp, P(i32), P(i32), vp],

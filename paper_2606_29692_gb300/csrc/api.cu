@@ -98,6 +98,55 @@ long long build_csr(tq_ctx* c, HamView& h, double maxc, int prec, std::vector<vo
     return nnz;
 }
 
+// XOR-ELL form of the same off-diagonal entries (blocks of XELL_ROWS rows);
+// returns the number of pairs.
+long long build_xell(tq_ctx* c, HamView& h, double maxc, int prec, std::vector<void*>& allocs) {
+    h.n_blocks = (h.D + XELL_ROWS - 1) / XELL_ROWS;
+    const long long B = h.n_blocks;
+    int* counts = static_cast<int*>(scratch(c, S_G, (size_t)B * sizeof(int)));
+    int* xptr = static_cast<int*>(dev_alloc((size_t)(B + 1) * sizeof(int)));
+    allocs.push_back(xptr);
+    struct Out { long long total; int max_row; int pad; };
+    Out* dout = static_cast<Out*>(scratch(c, S_PART, sizeof(Out)));
+    TQ_CUDA(cudaMemset(dout, 0, sizeof(Out)));
+    const double tol = 1e-12 * maxc;
+    if (h.G > 0) {
+        launch(c, "xell_count", 0, [&] { return launch_xell_count(h, tol, counts, c->sm_count, 0); });
+    } else {
+        TQ_CUDA(cudaMemset(counts, 0, (size_t)B * sizeof(int)));
+    }
+    launch(c, "scan", 0, [&] { return launch_scan(counts, B, xptr, &dout->total, &dout->max_row, 0); });
+    Out hout;
+    TQ_CUDA(cudaMemcpy(&hout, dout, sizeof(Out), cudaMemcpyDeviceToHost));
+    if (hout.total >= 2147483647ll)
+        throw Error(TQ_ENOMEM, "XOR-ELL has 2^31 or more pairs; int32 offsets cannot address it");
+    const long long np = hout.total;
+    // padded to whole copy chunks: the staged energy copies chunk by chunk
+    const long long chunk = xell_chunk_pairs();
+    const long long cap = std::max(1ll, (np + chunk - 1) / chunk) * chunk;
+    const size_t vb = prec == TQ_C128 ? sizeof(double) : sizeof(float);
+    uint32_t* xmask = static_cast<uint32_t*>(dev_alloc((size_t)cap * sizeof(uint32_t)));
+    allocs.push_back(xmask);
+    void* xval = dev_alloc((size_t)cap * XELL_ROWS * vb);
+    allocs.push_back(xval);
+    TQ_CUDA(cudaMemset(xmask + np, 0, (size_t)(cap - np) * sizeof(uint32_t)));
+    TQ_CUDA(cudaMemset(static_cast<char*>(xval) + (size_t)np * XELL_ROWS * vb, 0,
+                       (size_t)(cap - np) * XELL_ROWS * vb));
+    h.xptr = xptr;
+    h.xmask = xmask;
+    h.xval = xval;
+    h.n_pairs = np;
+    if (np > 0) launch(c, "xell_fill", 0, [&] { return launch_xell_fill(h, tol, xmask, xval, prec, c->sm_count, 0); });
+    // pair-balanced block ranges for the staged energy launch
+    h.xgrid = xell_grid(B, prec, c->sm_count);
+    int* split = static_cast<int*>(dev_alloc((size_t)(h.xgrid + 1) * sizeof(int)));
+    allocs.push_back(split);
+    h.xsplit = split;
+    launch(c, "xell_split", 0, [&] { return launch_xell_split(xptr, B, h.xgrid, split, 0); });
+    TQ_CUDA(cudaDeviceSynchronize());
+    return np;
+}
+
 void free_all(std::vector<void*>& allocs) {
     for (void* p : allocs)
         if (p) cudaFree(p);
@@ -243,8 +292,9 @@ extern "C" int tq_autotune_pair(tq_ctx* c, const tq_pool* p, int prec, int n_sta
 extern "C" int tq_ctx_set_spmv_schedule(tq_ctx* c, int lanes_per_row) {
     API_BEGIN
     TQ_REQUIRE(c != nullptr, "ctx is null");
-    TQ_REQUIRE(lanes_per_row == 4 || lanes_per_row == 8 || lanes_per_row == 16 || lanes_per_row == 32,
-               "lanes_per_row must be 4, 8, 16 or 32");
+    TQ_REQUIRE(lanes_per_row == TQ_SPMV_XELL || lanes_per_row == 4 || lanes_per_row == 8 ||
+                   lanes_per_row == 16 || lanes_per_row == 32,
+               "schedule must be 4, 8, 16 or 32 CSR lanes per row, or TQ_SPMV_XELL");
     c->spmv_lanes = lanes_per_row;
     API_END
 }
@@ -261,7 +311,7 @@ extern "C" int tq_autotune_spmv(tq_ctx* c, const tq_ham* h, const tq_state* psi,
     TQ_CUDA(cudaEventCreate(&e1));
     int best = c->spmv_lanes;
     float best_t = 1e30f;
-    for (int l : {4, 8, 16, 32}) {
+    for (int l : {4, 8, 16, 32, (int)TQ_SPMV_XELL}) {
         c->spmv_lanes = l;
         run_energy(c, h, psi, part, 0);
         TQ_CUDA(cudaEventRecord(e0, 0));
@@ -447,7 +497,10 @@ extern "C" int tq_build_hamiltonian(tq_ctx* c, int n_spatial, const double* h1, 
         v.diag = diag;
         launch(c, "diag", 0, [&] { return launch_diag(v, diag, c->sm_count, 0); });
         h->nnz = build_csr(c, v, maxc, prec, h->allocs, &h->n_amb, &h->max_row);
-        h->bytes = (size_t)h->D * 8 + (size_t)(h->D + 1) * 4 + (size_t)h->nnz * (4 + (prec == TQ_C128 ? 8 : 4)) +
+        const long long np = build_xell(c, v, maxc, prec, h->allocs);
+        const size_t vb = prec == TQ_C128 ? 8 : 4;
+        h->bytes = (size_t)h->D * 8 + (size_t)(h->D + 1) * 4 + (size_t)h->nnz * (4 + vb) +
+                   (size_t)(v.n_blocks + 1) * 4 + (size_t)np * (4 + XELL_ROWS * vb) + (size_t)(v.xgrid + 1) * 4 +
                    (gx.size() + goff.size() + tz.size() + dz.size()) * 4 + (tc.size() + dc.size()) * 8;
     } catch (...) {
         tq_ham_free(h);
@@ -479,6 +532,18 @@ extern "C" int tq_ham_csr(const tq_ham* h, const int** rowptr, const int** col, 
     if (col) *col = h->view.col;
     if (val) *val = h->view.val;
     if (diag) *diag = h->view.diag;
+    API_END
+}
+
+extern "C" int tq_ham_xell(const tq_ham* h, long long* n_blocks, long long* n_pairs, const int** xptr,
+                           const unsigned** xmask, const void** xval) {
+    API_BEGIN
+    TQ_REQUIRE(h != nullptr, "ham is null");
+    if (n_blocks) *n_blocks = h->view.n_blocks;
+    if (n_pairs) *n_pairs = h->view.n_pairs;
+    if (xptr) *xptr = h->view.xptr;
+    if (xmask) *xmask = h->view.xmask;
+    if (xval) *xval = h->view.xval;
     API_END
 }
 
@@ -777,6 +842,7 @@ namespace {
 // Partials needed by energy + gradients (+ line search) on this problem.
 size_t partials_needed(long long D, int n_gitems, int nq, int sms) {
     size_t n = (size_t)energy_grid(D, sms) * 2;
+    n = std::max(n, (size_t)16 * sms);      // any persistent energy grid (at most 8 blocks per SM)
     n = std::max(n, (size_t)std::max(n_gitems, 0));
     n = std::max(n, (size_t)512 * 5);
     n = std::max(n, (size_t)taylor5_pair_parts(nq, 1));
@@ -788,9 +854,13 @@ void run_energy(tq_ctx* c, const tq_ham* h, const tq_state* psi, double* part, c
     TQ_REQUIRE(h->prec == psi->prec, "state and Hamiltonian precisions differ");
     double2* w = static_cast<double2*>(c->scratch[S_W0]);
     float2* w32 = psi->prec == TQ_C64 ? static_cast<float2*>(c->scratch[S_W32]) : nullptr;
-    launch(c, "energy_csr", s, [&] { return launch_energy_csr2(h->view, psi->data, psi->prec, w, w32, part,
-                                                               c->tickets, c->step, c->sm_count, s,
-                                                               c->spmv_lanes); });
+    if (c->spmv_lanes == TQ_SPMV_XELL)
+        launch(c, "energy_xell", s, [&] { return launch_energy_xell(h->view, psi->data, psi->prec, w, w32, part,
+                                                                    c->tickets, c->step, s); });
+    else
+        launch(c, "energy_csr", s, [&] { return launch_energy_csr2(h->view, psi->data, psi->prec, w, w32, part,
+                                                                   c->tickets, c->step, c->sm_count, s,
+                                                                   c->spmv_lanes); });
 }
 
 void run_gradients(tq_ctx* c, const tq_ham* h, const tq_pool* p, const tq_state* psi, double* g,
@@ -813,6 +883,15 @@ double* prepare(tq_ctx* c, long long D, const tq_pool* p, int nq) {
         scratch(c, S_PART, partials_needed(D, p ? p->view.n_gitems : 0, nq, c->sm_count) * sizeof(double)));
 }
 
+// A kernel that gave up on a bounded wait left TQ_ETIMEOUT in the step's
+// status word: clear it and report the failure.
+void raise_status(tq_ctx* c, int status, cudaStream_t s) {
+    if (status == TQ_OK) return;
+    TQ_CUDA(cudaMemsetAsync(&c->step->status, 0, sizeof(int), s));
+    TQ_CUDA(cudaStreamSynchronize(s));
+    throw Error(status, "a kernel wait timed out; its results are invalid");
+}
+
 }  // namespace
 
 extern "C" int tq_energy(tq_ctx* c, const tq_ham* h, const tq_state* psi, double* E, void* stream) {
@@ -822,8 +901,11 @@ extern "C" int tq_energy(tq_ctx* c, const tq_ham* h, const tq_state* psi, double
     cudaStream_t s = as_stream(stream);
     double* part = prepare(c, h->D, nullptr, h->nq);
     run_energy(c, h, psi, part, s);
+    int status = 0;
     TQ_CUDA(cudaMemcpyAsync(E, &c->step->energy, sizeof(double), cudaMemcpyDeviceToHost, s));
+    TQ_CUDA(cudaMemcpyAsync(&status, &c->step->status, sizeof(int), cudaMemcpyDeviceToHost, s));
     TQ_CUDA(cudaStreamSynchronize(s));
+    raise_status(c, status, s);
     API_END
 }
 
@@ -852,8 +934,11 @@ extern "C" int tq_pool_gradients(tq_ctx* c, const tq_ham* h, const tq_pool* p, c
     double* part = prepare(c, h->D, p, p->nq);
     run_gradients(c, h, p, psi, gd, part, s);
     if (!g_on_device) {
+        int status = 0;
         TQ_CUDA(cudaMemcpyAsync(g, gd, (size_t)p->M * sizeof(double), cudaMemcpyDeviceToHost, s));
+        TQ_CUDA(cudaMemcpyAsync(&status, &c->step->status, sizeof(int), cudaMemcpyDeviceToHost, s));
         TQ_CUDA(cudaStreamSynchronize(s));
+        raise_status(c, status, s);
     }
     API_END
 }
@@ -893,6 +978,7 @@ extern "C" int tq_adapt_step(tq_ctx* c, const tq_ham* h, const tq_pool* p, tq_st
     DevStep hs;
     TQ_CUDA(cudaMemcpyAsync(&hs, c->step, sizeof(DevStep), cudaMemcpyDeviceToHost, s));
     TQ_CUDA(cudaStreamSynchronize(s));
+    raise_status(c, hs.status, s);
     out->energy = hs.energy;
     out->max_grad = hs.max_grad;
     out->selected = hs.selected;

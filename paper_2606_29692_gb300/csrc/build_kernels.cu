@@ -163,6 +163,88 @@ __global__ void k_csr_fill(HamView h, double tol, int cap, int* col, VT* val) {
     }
 }
 
+// XOR-ELL of the off-diagonal part (a second layout of the same entries):
+// rows in blocks of XELL_ROWS = 8 (block R holds rows 8R .. 8R + 7).  For
+// every X-mask group with a kept entry in any row of the block there is one
+// pair: the mask x and the eight values H[8R + i][(8R + i) ^ x], written as
+// zero where the CSR drop rule drops that entry.  The values are the CSR's
+// (same group sums in the same order, same rounding), and the pairs of a
+// block follow the canonical group order.  One warp per block, lanes over
+// groups, as in the CSR passes.
+__device__ __forceinline__ bool xell_values(const HamView& h, int g, long long R, double tol,
+                                            double (&v)[XELL_ROWS]) {
+    bool any = false;
+#pragma unroll
+    for (int i = 0; i < XELL_ROWS; ++i) {
+        const long long r = R * XELL_ROWS + i;
+        v[i] = 0.0;
+        if (r < h.D) {
+            const double a = group_value(h, g, (uint32_t)r ^ h.gx[g]);
+            if (fabs(a) > tol) {
+                v[i] = a;
+                any = true;
+            }
+        }
+    }
+    return any;
+}
+
+__global__ void k_xell_count(HamView h, double tol, int* counts) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long R = warp; R < h.n_blocks; R += nwarps) {
+        int cnt = 0;
+        double v[XELL_ROWS];
+        for (int g = lane; g < h.G; g += 32) cnt += xell_values(h, g, R, tol, v);
+        cnt = warp_sum_int(cnt);
+        if (lane == 0) counts[R] = cnt;
+    }
+}
+
+template <typename VT>
+__global__ void k_xell_fill(HamView h, double tol, uint32_t* xmask, VT* xval) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long R = warp; R < h.n_blocks; R += nwarps) {
+        long long base = h.xptr[R];
+        for (int g0 = 0; g0 < h.G; g0 += 32) {
+            const int g = g0 + lane;
+            double v[XELL_ROWS];
+            const bool keep = g < h.G && xell_values(h, g, R, tol, v);
+            const unsigned ball = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const long long pos = base + __popc(ball & ((1u << lane) - 1u));
+                xmask[pos] = h.gx[g];
+#pragma unroll
+                for (int i = 0; i < XELL_ROWS; ++i) xval[pos * XELL_ROWS + i] = (VT)v[i];
+            }
+            base += __popc(ball);
+        }
+    }
+}
+
+// split[c] = first row block of CTA c: the smallest R with
+// xptr[R] >= c * n_pairs / grid (pair-balanced contiguous ranges);
+// split[grid] = n_blocks.
+__global__ void k_xell_split(const int* xptr, long long n_blocks, int grid, int* split) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c > grid) return;
+    if (c == grid) {
+        split[c] = (int)n_blocks;
+        return;
+    }
+    const long long target = (long long)c * xptr[n_blocks] / grid;
+    long long lo = 0, hi = n_blocks;        // first index in [0, n_blocks] with xptr >= target
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (xptr[mid] >= target) hi = mid;
+        else lo = mid + 1;
+    }
+    split[c] = (int)lo;
+}
+
 __global__ void k_set_basis_c128(double2* psi, long long D, long long index) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < D; i += stride)
@@ -220,6 +302,28 @@ int launch_csr_fill(const HamView& h, double tol, int max_row, int* col, void* v
         cudaFuncSetAttribute(k_csr_fill<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_csr_fill<float><<<grid, bs, smem, s>>>(h, tol, cap, col, static_cast<float*>(val));
     }
+    return 1;
+}
+
+int launch_xell_count(const HamView& h, double tol, int* counts, int sms, cudaStream_t s) {
+    const int bs = 256;
+    k_xell_count<<<grid_for(h.n_blocks * 32, bs, sms, 8), bs, 0, s>>>(h, tol, counts);
+    return 1;
+}
+
+int launch_xell_fill(const HamView& h, double tol, uint32_t* xmask, void* xval, int prec, int sms,
+                     cudaStream_t s) {
+    const int bs = 256;
+    const int grid = grid_for(h.n_blocks * 32, bs, sms, 8);
+    if (prec == TQ_C128)
+        k_xell_fill<double><<<grid, bs, 0, s>>>(h, tol, xmask, static_cast<double*>(xval));
+    else
+        k_xell_fill<float><<<grid, bs, 0, s>>>(h, tol, xmask, static_cast<float*>(xval));
+    return 1;
+}
+
+int launch_xell_split(const int* xptr, long long n_blocks, int grid, int* split, cudaStream_t s) {
+    k_xell_split<<<(grid + 1 + 255) / 256, 256, 0, s>>>(xptr, n_blocks, grid, split);
     return 1;
 }
 

@@ -91,7 +91,10 @@ struct PoolView {
     const int* gfirst;      // [M + 1] first work item of each op
 };
 
-// Hamiltonian: float64 diagonal + off-diagonal CSR + X-mask-grouped terms.
+constexpr int XELL_ROWS = 8;   // rows per XOR-ELL block
+
+// Hamiltonian: float64 diagonal + off-diagonal CSR + the same off-diagonal
+// entries in XOR-ELL form + X-mask-grouped terms.
 struct HamView {
     int nq;
     int prec;
@@ -101,6 +104,14 @@ struct HamView {
     const int* rowptr;
     const int* col;
     const void* val;        // double or float
+    long long n_blocks;     // XOR-ELL row blocks of XELL_ROWS rows, ceil(D / XELL_ROWS)
+    long long n_pairs;
+    const int* xptr;        // [n_blocks + 1] first pair of each block
+    const uint32_t* xmask;  // [n_pairs] X-mask of the pair
+    const void* xval;       // [XELL_ROWS n_pairs] values, double or float
+                            // (both arrays padded to whole copy chunks)
+    int xgrid;              // CTAs of the staged XOR-ELL energy launch
+    const int* xsplit;      // [xgrid + 1] first row block of each CTA
     int G;                  // off-diagonal X-mask groups
     const uint32_t* gx;     // [G] group masks
     const int* goff;        // [G + 1] term offsets
@@ -120,7 +131,8 @@ struct DevStep {
     double dots[6];                // line-search matrix elements
     int selected;
     int converged;
-    int pad[2];
+    int status;                    // TQ_OK, or TQ_ETIMEOUT from a bounded wait
+    int pad;
 };
 
 // ------------------------------------------------------------- kernel launchers
@@ -137,6 +149,9 @@ int launch_scan(const int* counts, long long D, int* rowptr, long long* total,
                 int* max_row, cudaStream_t s);
 int launch_csr_fill(const HamView& h, double tol, int max_row, int* col, void* val,
                     int prec, int sms, cudaStream_t s);
+int launch_xell_count(const HamView& h, double tol, int* counts, int sms, cudaStream_t s);
+int launch_xell_fill(const HamView& h, double tol, uint32_t* xmask, void* xval, int prec, int sms,
+                     cudaStream_t s);
 
 // Taylor-5, matrix-free pair path: states back to back, op k[b] / theta[b]
 // (device arrays, or the immediates when the pointers are null).  Writes
@@ -164,6 +179,11 @@ int launch_energy_csr(const HamView& h, const void* psi, int psi_prec, double2* 
 int launch_energy_matrix_free(const HamView& h, const void* psi, int psi_prec,
                               double* partials, unsigned* ticket, DevStep* step,
                               int sms, cudaStream_t s);
+int launch_energy_xell(const HamView& h, const void* psi, int psi_prec, double2* w, float2* w32,
+                       double* partials, unsigned* ticket, DevStep* step, cudaStream_t s);
+int xell_grid(long long n_blocks, int prec, int sms);
+int xell_chunk_pairs();
+int launch_xell_split(const int* xptr, long long n_blocks, int grid, int* split, cudaStream_t s);
 int launch_energy_csr2(const HamView& h, const void* psi, int psi_prec, double2* w,
                        float2* w32, double* partials, unsigned* ticket, DevStep* step,
                        int sms, cudaStream_t s, int lanes_per_row);
@@ -206,7 +226,7 @@ struct tq_ctx {
     long long launches = 0;
     int tracing = 0;
     int pair_upt[2] = {2, 4};              // schedule per precision (C128, C64)
-    int spmv_lanes = 32;                   // energy SpMV lanes per row
+    int spmv_lanes = 32;                   // energy SpMV: CSR lanes per row, or 0 for XOR-ELL
     std::vector<tq_trace_rec> trace;      // recorded, not yet reported
     std::vector<cudaEvent_t> event_pool;  // reusable events
     // device scratch, grown on demand

@@ -8,6 +8,7 @@
 #include "dev.cuh"
 #include "grad.cuh"
 #include "spmv.cuh"
+#include "tma.cuh"
 
 #include <cmath>
 
@@ -60,6 +61,250 @@ k_energy_csr(HamView h, const typename C2<T>::type* __restrict__ psi, double2* _
         double a, b;
         block_sum_pairs(partials, 0, (int)gridDim.x, sh, a, b);
         if (threadIdx.x == 0) {
+            step->e_num = a;
+            step->e_den = b;
+            step->energy = a / b;
+            *ticket = 0u;
+        }
+    }
+}
+
+// The XOR-ELL energy with the pair stream staged through shared memory by
+// bulk copies (TMA).  Each CTA owns a contiguous range of row blocks,
+// balanced by pair count (h.xsplit), so its pairs form one contiguous run
+// of the (mask, values) arrays.  Warp 8 is the producer: one lane copies
+// the run in chunks of XT_CHUNK pairs into a ring of xt_stages<VT>() stages,
+// each guarded by a `full` barrier (copy landed) and an `empty` barrier
+// (all eight consumer warps are past it).  Warps 0-7 consume: lane l of
+// warp w serves rows 2u, 2u+1 (u = l & 3) of pair slot 8w + (l >> 2), so
+// the two amplitudes a lane needs, (8R + 2u) ^ x and its bit-0 partner,
+// are one aligned 16-byte load for complex64; masks and values come from
+// shared memory and psi from L2, so no thread waits on DRAM for the
+// stream.  Rounds are straight-line (no per-pair branches).  Each block's
+// slot sums are reduced in the warp and parked in shared memory; every
+// XT_GROUP blocks (256 rows) the consumers finish one row each in float64,
+// with psi and the diagonal loaded at the start of the group, between two
+// named barriers.  On a wait time-out the block sets its abort flag,
+// finishes its control flow without using the stream, drains its copies
+// and reports energy NaN with status TQ_ETIMEOUT.
+constexpr int XT_CHUNK_LOG = 8;
+constexpr int XT_CHUNK = 1 << XT_CHUNK_LOG;       // pairs per copy chunk
+constexpr int XT_CONSUMERS = 256;
+constexpr int XT_THREADS = XT_CONSUMERS + 32;
+constexpr int XT_SLOTS = XT_CONSUMERS / 4;        // pairs per round of the block
+constexpr int XT_GROUP = XT_CONSUMERS / XELL_ROWS;   // row blocks finished together (one row per thread)
+// ring depth (a power of two, at least 2: a round spans at most two chunks)
+template <typename VT> constexpr int xt_stages() { return sizeof(VT) == 4 ? 4 : 2; }
+
+// The ring is S * XT_CHUNK consecutive pairs (a power of two): pair p of
+// the CTA's run sits at ring index (p - k0 * XT_CHUNK) & (S * XT_CHUNK - 1).
+template <typename T, typename VT>
+struct XtSmem {
+    static constexpr int S = xt_stages<VT>();
+    uint32_t mask[S * XT_CHUNK];
+    VT val[S * XT_CHUNK * XELL_ROWS];
+    uint64_t full[S];
+    uint64_t empty[S];
+    T red[XT_GROUP][XT_CONSUMERS / 32][XELL_ROWS][2];   // per block, warp, row: slot sums
+    double sh[2 * (XT_THREADS / 32)];
+    int abort;
+};
+
+// The amplitudes of rows 2u and 2u + 1 (2u even) at columns 2u ^ x and
+// 2u ^ x ^ 1, given the even one of the two, a0 = (2u ^ x) & ~1: for
+// complex64 one 16-byte load of the aligned pair, swapped when x is odd.
+__device__ __forceinline__ void gather_two(const float2* __restrict__ psi, uint32_t a0, uint32_t x, float2& v0,
+                                           float2& v1) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(psi + a0));
+    const bool sw = x & 1u;
+    v0 = sw ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
+    v1 = sw ? make_float2(q.x, q.y) : make_float2(q.z, q.w);
+}
+__device__ __forceinline__ void gather_two(const double2* __restrict__ psi, uint32_t a0, uint32_t x, double2& v0,
+                                           double2& v1) {
+    const double2 e = psi[a0], o = psi[a0 + 1];
+    const bool sw = x & 1u;
+    v0 = sw ? o : e;
+    v1 = sw ? e : o;
+}
+
+// K k-steps of one round for one lane: pairs lp0 + 64k (local indices) of
+// the ring, rows 2u and 2u + 1.  Straight-line: a pair at or past the
+// block's end `le` reads a stale ring entry, whose gather stays in bounds
+// (masked index) and whose coefficients are replaced by zero; rows at or
+// beyond D (D < 8 only) carry zero values from the build.
+template <typename T, typename VT, int K>
+__device__ __forceinline__ void xt_round(const uint32_t* mask, const typename C2<VT>::type* sval,
+                                         const typename C2<T>::type* __restrict__ psi, uint32_t ru, uint32_t dmask,
+                                         int lp0, int kRing, int le, int u, T& ax, T& ay, T& bx, T& by) {
+    using V = typename C2<T>::type;
+    using VT2 = typename C2<VT>::type;
+    uint32_t x[K];
+    VT2 av[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int lp = lp0 + XT_SLOTS * k;
+        const int ri = lp & kRing;
+        x[k] = mask[ri];
+        const VT2 a = sval[ri * (XELL_ROWS / 2) + u];
+        av[k] = lp < le ? a : VT2{};
+    }
+    V v0[K], v1[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) gather_two(psi, (ru ^ x[k]) & dmask, x[k], v0[k], v1[k]);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        ax = fma((T)av[k].x, v0[k].x, ax);
+        ay = fma((T)av[k].x, v0[k].y, ay);
+        bx = fma((T)av[k].y, v1[k].x, bx);
+        by = fma((T)av[k].y, v1[k].y, by);
+    }
+}
+
+template <typename T, typename VT>
+__global__ void __launch_bounds__(XT_THREADS, sizeof(VT) == 4 ? 3 : 2)
+k_energy_xell_tma(HamView h, const typename C2<T>::type* __restrict__ psi, double2* __restrict__ w,
+                  float2* __restrict__ w32, double* partials, unsigned* ticket, DevStep* step) {
+    using V = typename C2<T>::type;
+    constexpr int S = xt_stages<VT>();
+    extern __shared__ __align__(128) unsigned char xt_raw[];
+    XtSmem<T, VT>& sm = *reinterpret_cast<XtSmem<T, VT>*>(xt_raw);
+    volatile int* abort = &sm.abort;
+    const int t = threadIdx.x;
+    const VT* __restrict__ xval = static_cast<const VT*>(h.xval);
+    const long long b0 = h.xsplit[blockIdx.x], b1 = h.xsplit[blockIdx.x + 1];
+    const int P0 = h.xptr[b0], P1 = h.xptr[b1];
+    const int k0 = P0 / XT_CHUNK;
+    const int nk = P1 > P0 ? (P1 - 1) / XT_CHUNK - k0 + 1 : 0;
+    if (t == 0) {
+        for (int st = 0; st < S; ++st) {
+            mbar_init(&sm.full[st], 1);
+            mbar_init(&sm.empty[st], XT_CONSUMERS / 32);
+        }
+        sm.abort = 0;
+        mbar_init_fence();
+    }
+    __syncthreads();
+    double num = 0.0, den = 0.0;
+    if (t >= XT_CONSUMERS) {
+        if (t == XT_CONSUMERS) {
+            constexpr unsigned kBytes = XT_CHUNK * (4 + XELL_ROWS * sizeof(VT));
+            int issued = 0;
+            for (int j = 0; j < nk; ++j) {
+                const int st = j % S;
+                if (j >= S && !mbar_wait(&sm.empty[st], ((j / S) - 1) & 1, abort)) break;
+                mbar_arrive_expect_tx(&sm.full[st], kBytes);
+                const size_t c = (size_t)(k0 + j) * XT_CHUNK;
+                bulk_load(sm.mask + st * XT_CHUNK, h.xmask + c, XT_CHUNK * 4, &sm.full[st]);
+                bulk_load(sm.val + st * XT_CHUNK * XELL_ROWS, xval + c * XELL_ROWS,
+                          XT_CHUNK * XELL_ROWS * sizeof(VT), &sm.full[st]);
+                issued = j + 1;
+            }
+            // every issued copy lands before the block may exit
+            for (int j = issued > S ? issued - S : 0; j < issued; ++j)
+                mbar_wait(&sm.full[j % S], (j / S) & 1, abort, false);
+        }
+    } else {
+        using VT2 = typename C2<VT>::type;
+        const int wid = t >> 5, lane = t & 31, u = lane & 3, sub = lane >> 2;
+        const uint32_t dmask = (uint32_t)(h.D - 1) & ~1u;
+        const int base = k0 * XT_CHUNK;                   // pair index of ring position 0
+        constexpr int kRing = S * XT_CHUNK - 1;
+        const VT2* __restrict__ sval = reinterpret_cast<const VT2*>(sm.val);
+        int next_wait = 0, next_rel = 0;
+        auto wait_next = [&]() {
+            uint64_t* bar = &sm.full[next_wait % S];
+            const unsigned ph = (unsigned)(next_wait / S) & 1u;
+            if (!mbar_try_wait(bar, ph)) mbar_wait(bar, ph, abort);
+            ++next_wait;
+        };
+        // releases every chunk wholly below pair `lo` (waiting first for any
+        // chunk this warp has not seen, so arrivals stay in chunk order)
+        auto release_below = [&](int lo) {
+            const int below = min((lo - base) >> XT_CHUNK_LOG, nk);
+            while (next_rel < below) {
+                while (next_wait <= next_rel) wait_next();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.empty[next_rel % S]);
+                ++next_rel;
+            }
+        };
+        int pb = P0, pe = b0 < b1 ? h.xptr[b0 + 1] : P0;
+        for (long long G0 = b0; G0 < b1; G0 += XT_GROUP) {
+            const long long G1 = G0 + XT_GROUP < b1 ? G0 + XT_GROUP : b1;
+            // this thread's row of the group, finished after the group's blocks
+            const long long rf = G0 * XELL_ROWS + t;
+            const bool fin = rf < G1 * XELL_ROWS && rf < h.D;
+            V pr = V{};
+            double dg = 0.0;
+            if (fin) {
+                pr = psi[rf];
+                dg = h.diag[rf];
+            }
+            for (long long R = G0; R < G1; ++R) {
+                const int pn = R + 2 <= b1 ? h.xptr[R + 2] : pe;     // next block's end, one block ahead
+                const uint32_t ru = (uint32_t)(R * XELL_ROWS + 2 * u);
+                T ax = T(0), ay = T(0), bx = T(0), by = T(0);
+                const int le = pe - base;                          // block end, local
+                // warp-uniform rounds: pairs q + 64k + sub, k < 4
+                for (int q = pb + 8 * wid; q < pe; q += 4 * XT_SLOTS) {
+                    const int lq = q - base;
+                    const int need = (min(lq + 3 * XT_SLOTS + 7, le - 1)) >> XT_CHUNK_LOG;
+                    while (next_wait <= need) wait_next();
+                    xt_round<T, VT, 4>(sm.mask, sval, psi, ru, dmask, lq + sub, kRing, le, u, ax, ay, bx, by);
+                    release_below(q + 4 * XT_SLOTS < pe ? q + 4 * XT_SLOTS : pe);
+                }
+                release_below(pe);
+#pragma unroll
+                for (int o = 4; o < 32; o <<= 1) {
+                    ax += __shfl_xor_sync(0xffffffffu, ax, o);
+                    ay += __shfl_xor_sync(0xffffffffu, ay, o);
+                    bx += __shfl_xor_sync(0xffffffffu, bx, o);
+                    by += __shfl_xor_sync(0xffffffffu, by, o);
+                }
+                if (lane < 4) {
+                    T (*rb)[XELL_ROWS][2] = sm.red[R - G0];
+                    rb[wid][2 * u][0] = ax;
+                    rb[wid][2 * u][1] = ay;
+                    rb[wid][2 * u + 1][0] = bx;
+                    rb[wid][2 * u + 1][1] = by;
+                }
+                pb = pe;
+                pe = pn;
+            }
+            named_sync(XT_CONSUMERS);
+            if (fin) {
+                T mx = T(0), my = T(0);
+#pragma unroll
+                for (int k = 0; k < XT_CONSUMERS / 32; ++k) {
+                    mx += sm.red[t / XELL_ROWS][k][t % XELL_ROWS][0];
+                    my += sm.red[t / XELL_ROWS][k][t % XELL_ROWS][1];
+                }
+                const double prx = (double)pr.x, pry = (double)pr.y;
+                const double wx = fma(dg, prx, (double)mx), wy = fma(dg, pry, (double)my);
+                if (w) w[rf] = make_double2(wx, wy);
+                if (w32) w32[rf] = make_float2((float)wx, (float)wy);
+                num += prx * wx + pry * wy;
+                den += prx * prx + pry * pry;
+            }
+            named_sync(XT_CONSUMERS);
+        }
+    }
+    __syncthreads();
+    if (*abort) {
+        num = nan("");
+        if (t == 0) atomicExch(&step->status, (int)TQ_ETIMEOUT);
+    }
+    double v[2] = {num, den};
+    block_sum<2>(v, sm.sh);
+    if (t == 0) {
+        partials[2 * blockIdx.x] = v[0];
+        partials[2 * blockIdx.x + 1] = v[1];
+    }
+    if (last_block(ticket, gridDim.x)) {
+        double a, b;
+        block_sum_pairs(partials, 0, (int)gridDim.x, sm.sh, a, b);
+        if (t == 0) {
             step->e_num = a;
             step->e_den = b;
             step->energy = a / b;
@@ -421,6 +666,55 @@ int energy_dispatch(int lanes, const HamView& h, const void* psi, double2* w, fl
 }
 
 }  // namespace
+
+namespace {
+
+template <typename T, typename VT>
+void xell_launch(const HamView& h, const void* psi, double2* w, float2* w32, double* partials,
+                 unsigned* ticket, DevStep* step, cudaStream_t s) {
+    using V = typename C2<T>::type;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_energy_xell_tma<T, VT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(XtSmem<T, VT>));
+        attr = true;
+    }
+    k_energy_xell_tma<T, VT><<<h.xgrid, XT_THREADS, sizeof(XtSmem<T, VT>), s>>>(
+        h, static_cast<const V*>(psi), w, w32, partials, ticket, step);
+}
+
+}  // namespace
+
+int launch_energy_xell(const HamView& h, const void* psi, int psi_prec, double2* w, float2* w32,
+                       double* partials, unsigned* ticket, DevStep* step, cudaStream_t s) {
+    if (psi_prec == TQ_C128)
+        xell_launch<double, double>(h, psi, w, w32, partials, ticket, step, s);
+    else
+        xell_launch<float, float>(h, psi, w, w32, partials, ticket, step, s);
+    return 1;
+}
+
+// Grid of the staged XOR-ELL energy: resident blocks on `sms` SMs, at most
+// one per row block.
+int xell_grid(long long n_blocks, int prec, int sms) {
+    int per = 0;
+    if (prec == TQ_C128) {
+        cudaFuncSetAttribute(k_energy_xell_tma<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(XtSmem<double, double>));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_energy_xell_tma<double, double>, XT_THREADS,
+                                                      sizeof(XtSmem<double, double>));
+    } else {
+        cudaFuncSetAttribute(k_energy_xell_tma<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(XtSmem<float, float>));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_energy_xell_tma<float, float>, XT_THREADS,
+                                                      sizeof(XtSmem<float, float>));
+    }
+    long long g = (long long)(per < 1 ? 1 : per) * sms;
+    if (g > n_blocks) g = n_blocks;
+    return (int)(g < 1 ? 1 : g);
+}
+
+int xell_chunk_pairs() { return XT_CHUNK; }
 
 int launch_energy_csr2(const HamView& h, const void* psi, int psi_prec, double2* w, float2* w32,
                        double* partials, unsigned* ticket, DevStep* step, int sms, cudaStream_t s,

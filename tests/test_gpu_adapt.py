@@ -80,9 +80,19 @@ def test_config1_teacher_forced_c64(ctx, mp):
     _teacher_forced(ctx, mp, tq.TQ_C64, 8)
 
 
+@pytest.mark.parametrize("sched", [32, tq.TQ_SPMV_XELL])
 @pytest.mark.parametrize("prec", [tq.TQ_C128, tq.TQ_C64])
-def test_config1_free_running(ctx, prec):
-    """20 iterations on the GPU alone vs the oracle's own trajectory."""
+def test_config1_free_running(ctx, prec, sched):
+    """20 iterations on the GPU alone vs the oracle's own trajectory, with
+    the H pass on the CSR and on the XOR-ELL layout."""
+    ctx.set_spmv_schedule(sched)
+    try:
+        _free_running(ctx, prec)
+    finally:
+        ctx.set_spmv_schedule(32)
+
+
+def _free_running(ctx, prec):
     ints, ne = synth.config1()
     mp = 1
     sysm = oadapt.build_system(ints, ne, mp)

@@ -60,6 +60,51 @@ def test_hamiltonian_csr_matches_oracle(ctx, cfg, mp, prec):
     assert np.abs(diag - odiag).max() <= 1e-14 * np.abs(ps.c).sum()
 
 
+def xell_numpy(ham, prec):
+    nb, npairs, xp, xm, xv = tq.ham_xell(ham)
+    xptr = dev_to_numpy(xp, nb + 1, "<i4")
+    xmask = dev_to_numpy(xm, npairs, "<u4") if npairs else np.zeros(0, np.uint32)
+    vt = "<f8" if prec == tq.TQ_C128 else "<f4"
+    xval = dev_to_numpy(xv, 8 * npairs, vt).reshape(npairs, 8) if npairs else np.zeros((0, 8))
+    return nb, xptr, xmask, xval
+
+
+@pytest.mark.parametrize("prec", [tq.TQ_C128, tq.TQ_C64])
+@pytest.mark.parametrize("cfg,mp", [("n1", 0), ("n3", 1), ("c0", 0), ("c1", 0), ("c1", 1), ("c2", 1)])
+def test_hamiltonian_xell_matches_oracle(ctx, cfg, mp, prec):
+    """The XOR-ELL layout holds exactly the CSR's entries: per block of 8
+    rows, the X-masks r ^ c of the oracle's off-diagonal entries (ascending,
+    bit-exact), the oracle's value where the entry exists and exact zero
+    where it does not; values equal the library's own CSR bit for bit."""
+    ints, ne, ps, H = oracle_h(cfg, mp)
+    ham = tq.build_hamiltonian(ctx, ints.h, ints.g, ints.e_const, mp, prec)
+    nb, xptr, xmask, xval = xell_numpy(ham, prec)
+    rowptr, col, val, _ = ham_csr_numpy(ham)
+    orp, ocol, oval, _ = oracle_split(H)
+    D = len(orp) - 1
+    assert nb == (D + 7) // 8 and xptr[0] == 0
+    maxc = np.abs(ps.c).max()
+    for R in range(nb):
+        rows = range(8 * R, min(8 * R + 8, D))
+        expect = sorted({r ^ int(c) for r in rows for c in ocol[orp[r]:orp[r + 1]]})
+        got = xmask[xptr[R]:xptr[R + 1]]
+        assert got.tolist() == expect, f"block {R}: X-masks differ"
+        blk = xval[xptr[R]:xptr[R + 1]]
+        for i, r in enumerate(rows):
+            oc = {int(c): v for c, v in zip(ocol[orp[r]:orp[r + 1]], oval[orp[r]:orp[r + 1]])}
+            mine = {int(c): v for c, v in zip(col[rowptr[r]:rowptr[r + 1]], val[rowptr[r]:rowptr[r + 1]])}
+            for j, x in enumerate(expect):
+                c = r ^ x
+                if c in oc:
+                    assert blk[j, i] == mine[c]
+                    assert abs(float(blk[j, i]) - oc[c]) <= (1e-14 * maxc if prec == tq.TQ_C128
+                                                            else float(np.spacing(np.float32(abs(oc[c])))))
+                else:
+                    assert blk[j, i] == 0.0
+        for i in range(len(rows), 8):
+            assert np.all(blk[:, i] == 0.0)
+
+
 @pytest.mark.parametrize("prec", [tq.TQ_C128, tq.TQ_C64])
 @pytest.mark.parametrize("n,ne,mp", [(2, 2, 0), (4, 4, 0), (4, 4, 1), (6, 8, 1), (7, 6, 1)])
 def test_pool_csr_matches_oracle(ctx, n, ne, mp, prec):

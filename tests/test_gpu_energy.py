@@ -38,9 +38,18 @@ def _states(sysm, nq, ne, mp):
     return {"hf": hf, "corr": psi, "rand": synth.random_state(nq, 4) * 0.7}
 
 
+@pytest.mark.parametrize("sched", [32, tq.TQ_SPMV_XELL])
 @pytest.mark.parametrize("prec", [tq.TQ_C128, tq.TQ_C64])
 @pytest.mark.parametrize("cfg,mp", [("c0", 0), ("c0", 1), ("c1", 0), ("c1", 1), ("c2", 1)])
-def test_energy_and_gradients_match_oracle(ctx, cfg, mp, prec):
+def test_energy_and_gradients_match_oracle(ctx, cfg, mp, prec, sched):
+    ctx.set_spmv_schedule(sched)
+    try:
+        _energy_and_gradients(ctx, cfg, mp, prec)
+    finally:
+        ctx.set_spmv_schedule(32)
+
+
+def _energy_and_gradients(ctx, cfg, mp, prec):
     ints, ne, sysm = osys(cfg, mp)
     nq = 2 * ints.n_spatial
     ham = tq.build_hamiltonian(ctx, ints.h, ints.g, ints.e_const, mp, prec)
@@ -95,9 +104,9 @@ def test_every_spmv_schedule_agrees(ctx):
         psi = _states(sysm, 14, ne, 1)["corr"]
         st = to_state(ctx, psi, 14, prec)
         ref = oadapt.energy(sysm.H, st.numpy())[0]
-        for lanes in (4, 8, 16, 32):
+        for lanes in (4, 8, 16, 32, tq.TQ_SPMV_XELL):
             ctx.set_spmv_schedule(lanes)
             assert abs(tq.energy(ctx, ham, st) - ref) <= (1e-10 if prec == tq.TQ_C128 else 1e-6)
         best, ms = tq.autotune_spmv(ctx, ham, st)
-        assert best in (4, 8, 16, 32) and ms > 0
+        assert best in (4, 8, 16, 32, tq.TQ_SPMV_XELL) and ms > 0
     ctx.set_spmv_schedule(32)

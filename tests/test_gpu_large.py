@@ -75,6 +75,23 @@ def test_18_qubit_hf_energy_and_rows(ctx, mp, prec):
         groups = np.unique(ps.x[ps.x != 0])
         expect = sorted(r ^ int(g) for g in groups if abs(_element(ps, r, r ^ int(g))) > 1e-12 * maxc)
         assert list(cols) == expect
+    # XOR-ELL blocks of the same rows: masks and values from the element formula
+    nb, npairs, xp, xm, xv = tq.ham_xell(ham)
+    assert nb == 1 << 15
+    xptr = dev_to_numpy(xp, nb + 1, "<i4")
+    for R in [0, hf >> 3, nb - 1] + list(rng.integers(0, nb, size=3)):
+        R = int(R)
+        a, b = int(xptr[R]), int(xptr[R + 1])
+        masks = dev_to_numpy(xm + 4 * a, b - a, "<u4")
+        vals = dev_to_numpy(xv + 64 * a, 8 * (b - a), "<f8").reshape(b - a, 8)
+        el = {int(g): [_element(ps, 8 * R + i, (8 * R + i) ^ int(g)) for i in range(8)] for g in groups}
+        kept = [g for g in sorted(el) if max(abs(v) for v in el[g]) > 1e-12 * maxc]
+        assert masks.tolist() == kept
+        for j, g in enumerate(kept):
+            for i in range(8):
+                ref = el[g][i] if abs(el[g][i]) > 1e-12 * maxc else 0.0
+                assert abs(vals[j, i] - ref) <= 1e-14 * maxc
+                assert (vals[j, i] == 0.0) == (ref == 0.0)
 
 
 @pytest.mark.parametrize("mp", [0, 1])
