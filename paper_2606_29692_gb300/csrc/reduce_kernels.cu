@@ -110,22 +110,12 @@ struct XtSmem {
     int abort;
 };
 
-// The amplitudes of rows 2u and 2u + 1 (2u even) at columns 2u ^ x and
-// 2u ^ x ^ 1, given the even one of the two, a0 = (2u ^ x) & ~1: for
-// complex64 one 16-byte load of the aligned pair, swapped when x is odd.
-__device__ __forceinline__ void gather_two(const float2* __restrict__ psi, uint32_t a0, uint32_t x, float2& v0,
-                                           float2& v1) {
-    const float4 q = __ldg(reinterpret_cast<const float4*>(psi + a0));
-    const bool sw = x & 1u;
-    v0 = sw ? make_float2(q.z, q.w) : make_float2(q.x, q.y);
-    v1 = sw ? make_float2(q.x, q.y) : make_float2(q.z, q.w);
-}
-__device__ __forceinline__ void gather_two(const double2* __restrict__ psi, uint32_t a0, uint32_t x, double2& v0,
-                                           double2& v1) {
-    const double2 e = psi[a0], o = psi[a0 + 1];
-    const bool sw = x & 1u;
-    v0 = sw ? o : e;
-    v1 = sw ? e : o;
+// The amplitudes of rows 2u and 2u + 1 (2u even) at columns a = 2u ^ x and
+// a ^ 1.
+template <typename V>
+__device__ __forceinline__ void gather_two(const V* __restrict__ psi, uint32_t a, V& v0, V& v1) {
+    v0 = __ldg(psi + a);
+    v1 = __ldg(psi + (a ^ 1u));
 }
 
 // K k-steps of one round for one lane: pairs lp0 + 64k (local indices) of
@@ -151,13 +141,27 @@ __device__ __forceinline__ void xt_round(const uint32_t* mask, const typename C2
     }
     V v0[K], v1[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) gather_two(psi, (ru ^ x[k]) & dmask, x[k], v0[k], v1[k]);
+    for (int k = 0; k < K; ++k) gather_two(psi, (ru ^ x[k]) & dmask, v0[k], v1[k]);
+    if constexpr (sizeof(T) == 4) {
+        // packed float32x2: (re, im) of a row in one instruction
+        float2 A = make_float2(ax, ay), B = make_float2(bx, by);
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        ax = fma((T)av[k].x, v0[k].x, ax);
-        ay = fma((T)av[k].x, v0[k].y, ay);
-        bx = fma((T)av[k].y, v1[k].x, bx);
-        by = fma((T)av[k].y, v1[k].y, by);
+        for (int k = 0; k < K; ++k) {
+            A = __ffma2_rn(make_float2(av[k].x, av[k].x), v0[k], A);
+            B = __ffma2_rn(make_float2(av[k].y, av[k].y), v1[k], B);
+        }
+        ax = A.x;
+        ay = A.y;
+        bx = B.x;
+        by = B.y;
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            ax = fma((T)av[k].x, v0[k].x, ax);
+            ay = fma((T)av[k].x, v0[k].y, ay);
+            bx = fma((T)av[k].y, v1[k].x, bx);
+            by = fma((T)av[k].y, v1[k].y, by);
+        }
     }
 }
 
@@ -207,7 +211,7 @@ k_energy_xell_tma(HamView h, const typename C2<T>::type* __restrict__ psi, doubl
     } else {
         using VT2 = typename C2<VT>::type;
         const int wid = t >> 5, lane = t & 31, u = lane & 3, sub = lane >> 2;
-        const uint32_t dmask = (uint32_t)(h.D - 1) & ~1u;
+        const uint32_t dmask = (uint32_t)(h.D - 1);
         const int base = k0 * XT_CHUNK;                   // pair index of ring position 0
         constexpr int kRing = S * XT_CHUNK - 1;
         const VT2* __restrict__ sval = reinterpret_cast<const VT2*>(sm.val);
