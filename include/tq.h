@@ -229,6 +229,56 @@ int tq_state_data(const tq_state* st, void** dev_ptr, int* n_qubits, int* prec);
 int tq_state_set_hf(tq_state* st, int n_electrons, int mapping, void* stream);
 int tq_state_free(tq_state* st);
 
+/* ---------------------------------------------- sector-restricted basis */
+/* Not in the paper, which works in the full 2^N space: the same operators
+ * restricted to the occupation states with n_alpha electrons in the even
+ * spin orbitals (alpha, P = 2p) and n_beta in the odd ones (beta).  H of
+ * Eq. (2) and every spin-conserving pool generator map this subspace into
+ * itself, so energies, gradients and Taylor-5 updates of a state in it are
+ * those of the full space, with C(n, n_alpha) C(n, n_beta) amplitudes
+ * instead of 2^(2n) (14 qubits, 3 + 3 electrons: 1225 instead of 16384).
+ * Basis order: rank = rank_alpha * C(n, n_beta) + rank_beta, rank_x the
+ * colexicographic rank of the occupied x-spin spatial orbitals
+ * {c_1 < ... < c_k}: sum_j C(c_j, j).  The matrices in this order do not
+ * depend on the mapping; the mapping fixes only the qubit-space index of
+ * each basis state.  1 <= n_spatial <= 13, 0 <= n_alpha, n_beta <=
+ * n_spatial, else TQ_EINVAL. */
+int tq_sector_dim(int n_spatial, int n_alpha, int n_beta, long long* dim);
+/* Host: qubit-space index (under `mapping`) of every basis state, in rank
+ * order, into qubit_index[0 .. dim-1]; TQ_EINVAL if capacity < dim. */
+int tq_sector_basis(int n_spatial, int n_alpha, int n_beta, int mapping,
+                    long long capacity, unsigned* qubit_index);
+/* As tq_build_hamiltonian, restricted to the sector: float64 diagonal and
+ * CSR (rowptr int32[dim+1], col int32 ascending, real values) over ranks,
+ * read with tq_ham_csr; no XOR-ELL layout (tq_energy uses the CSR). */
+int tq_build_hamiltonian_sector(tq_ctx* ctx, int n_spatial, const double* h1,
+                                const double* g2, double e_const, int mapping,
+                                int prec, int n_alpha, int n_beta, tq_ham** out);
+/* As tq_build_pool, plus each generator restricted to the sector: per op k
+ * and row r, col[k*dim + r] (int32) and sgn[k*dim + r] (int8) with
+ * A_k[r][col] = sgn = +-1, or sgn = 0 where A_k annihilates row r (then
+ * col = r).  TQ_ENUMERIC if a generator leaves the sector.  The sector pool
+ * drives tq_evolve_taylor5, tq_evolve_taylor5_batch(_host) (states of dim
+ * amplitudes), tq_pool_gradients and tq_adapt_step with sector
+ * Hamiltonians and states; the trajectory batch, the request loop and the
+ * pair autotuner take full-space objects only. */
+int tq_build_pool_sector(tq_ctx* ctx, int n_spatial, int n_electrons,
+                         int mapping, int n_alpha, int n_beta, tq_pool** out);
+/* Borrowed device pointers to a sector pool's tables (dim = 0 and NULL
+ * tables for a full-space pool). */
+int tq_pool_sector_table(const tq_pool* pool, long long* dim, const int** col,
+                         const signed char** sgn);
+/* Sector states: dim amplitudes in rank order, owned (zeroed) or borrowed
+ * (16-byte aligned).  tq_state_set_hf puts the lowest determinant (spin
+ * orbitals P < n_electrons; rank 0) and fails with TQ_EINVAL unless
+ * n_alpha = ceil(n_electrons/2) and n_beta = floor(n_electrons/2).  Every
+ * hot-path call checks that Hamiltonian, pool and state describe the same
+ * space (full, or the same sector): TQ_EINVAL otherwise. */
+int tq_state_create_sector(tq_ctx* ctx, int n_spatial, int n_alpha, int n_beta,
+                           int prec, tq_state** out);
+int tq_state_wrap_sector(tq_ctx* ctx, int n_spatial, int n_alpha, int n_beta,
+                         int prec, void* dev_ptr, tq_state** out);
+
 /* ------------------------------------------------------------- hot path */
 
 /* Fifth-order Taylor update of Sec. III-C, Eqs. (6)-(8):

@@ -26,6 +26,7 @@ __all__ = [
     "pool_gradients", "adapt_step", "evolve_taylor5_batch", "evolve_taylor5_batch_host",
     "state_set_hf", "pool_csr", "ham_csr", "lib", "autotune_pair", "energy_noalloc", "Batch", "autotune_spmv", "Server",
     "TQ_REQ_EVOLVE", "TQ_REQ_ENERGY", "TQ_REQ_GRADIENTS", "TQ_SPMV_XELL", "ham_xell",
+    "sector_dim", "sector_basis", "build_hamiltonian_sector", "build_pool_sector", "pool_sector_table",
 ]
 
 
@@ -190,20 +191,29 @@ class Pool:
 
 
 class State:
-    """A state backed by a torch tensor (device memory comes from torch)."""
+    """A state backed by a torch tensor (device memory comes from torch).
 
-    def __init__(self, ctx, n_qubits, prec=TQ_C128, tensor=None):
+    With ``sector=(n_alpha, n_beta)`` it holds the sector's amplitudes in rank
+    order (``sector_dim`` of them) instead of all 2^n_qubits."""
+
+    def __init__(self, ctx, n_qubits, prec=TQ_C128, tensor=None, sector=None):
         import torch
         self.ctx = ctx
         self.n_qubits = n_qubits
         self.prec = prec
+        self.sector = tuple(sector) if sector is not None else None
+        n = sector_dim(n_qubits // 2, *self.sector) if self.sector else 1 << n_qubits
         if tensor is None:
-            tensor = torch.zeros(1 << n_qubits, dtype=_torch_dtype(prec), device=f"cuda:{ctx.device}")
-        assert tensor.is_contiguous() and tensor.numel() == (1 << n_qubits)
+            tensor = torch.zeros(n, dtype=_torch_dtype(prec), device=f"cuda:{ctx.device}")
+        assert tensor.is_contiguous() and tensor.numel() == n
         assert tensor.dtype == _torch_dtype(prec)
         self.tensor = tensor
         h = C.c_void_p()
-        call("tq_state_wrap", ctx.handle, n_qubits, prec, _ptr(tensor), C.byref(h))
+        if self.sector:
+            call("tq_state_wrap_sector", ctx.handle, n_qubits // 2, self.sector[0], self.sector[1], prec,
+                 _ptr(tensor), C.byref(h))
+        else:
+            call("tq_state_wrap", ctx.handle, n_qubits, prec, _ptr(tensor), C.byref(h))
         self.handle = h
 
     def numpy(self):
@@ -235,6 +245,51 @@ def build_pool(ctx, n_spatial, n_electrons, mapping=TQ_JW):
     h = C.c_void_p()
     call("tq_build_pool", ctx.handle, n_spatial, n_electrons, mapping, C.byref(h))
     return Pool(ctx, h)
+
+
+# ------------------------------------------------------- sector-restricted basis
+
+def sector_dim(n_spatial, n_alpha, n_beta):
+    """C(n, n_alpha) * C(n, n_beta): amplitudes of the fixed-(n_alpha, n_beta) sector."""
+    d = C.c_longlong()
+    call("tq_sector_dim", int(n_spatial), int(n_alpha), int(n_beta), C.byref(d))
+    return d.value
+
+
+def sector_basis(n_spatial, n_alpha, n_beta, mapping=TQ_JW):
+    """Qubit-space index of every sector basis state, in rank order (host)."""
+    out = np.zeros(sector_dim(n_spatial, n_alpha, n_beta), dtype=np.uint32)
+    call("tq_sector_basis", int(n_spatial), int(n_alpha), int(n_beta), mapping, out.size, _ptr(out))
+    return out
+
+
+def build_hamiltonian_sector(ctx, h1, g2, e_const=0.0, mapping=TQ_JW, prec=TQ_C128, n_alpha=0, n_beta=0):
+    h1 = np.ascontiguousarray(h1, dtype=np.float64)
+    g2 = np.ascontiguousarray(g2, dtype=np.float64)
+    h = C.c_void_p()
+    call("tq_build_hamiltonian_sector", ctx.handle, h1.shape[0], _ptr(h1), _ptr(g2), float(e_const), mapping,
+         prec, int(n_alpha), int(n_beta), C.byref(h))
+    ham = Hamiltonian(ctx, h)
+    ham.sector = (int(n_alpha), int(n_beta))
+    ham.dim = sector_dim(h1.shape[0], n_alpha, n_beta)
+    return ham
+
+
+def build_pool_sector(ctx, n_spatial, n_electrons, mapping=TQ_JW, n_alpha=0, n_beta=0):
+    h = C.c_void_p()
+    call("tq_build_pool_sector", ctx.handle, n_spatial, n_electrons, mapping, int(n_alpha), int(n_beta),
+         C.byref(h))
+    pool = Pool(ctx, h)
+    pool.sector = (int(n_alpha), int(n_beta))
+    pool.dim = sector_dim(n_spatial, n_alpha, n_beta)
+    return pool
+
+
+def pool_sector_table(pool):
+    """(dim, col, sgn) borrowed device pointers of a sector pool's tables."""
+    d, cl, sg = C.c_longlong(), C.c_void_p(), C.c_void_p()
+    call("tq_pool_sector_table", pool.handle, C.byref(d), C.byref(cl), C.byref(sg))
+    return d.value, cl.value, sg.value
 
 
 def ham_csr(ham):

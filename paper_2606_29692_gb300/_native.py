@@ -79,6 +79,13 @@ SIGNATURES = {
     "tq_state_data": [vp, P(vp), P(i32), P(i32)],
     "tq_state_set_hf": [vp, i32, i32, vp],
     "tq_state_free": [vp],
+    "tq_sector_dim": [i32, i32, i32, P(i64)],
+    "tq_sector_basis": [i32, i32, i32, i32, i64, vp],
+    "tq_build_hamiltonian_sector": [vp, i32, vp, vp, f64, i32, i32, i32, i32, P(vp)],
+    "tq_build_pool_sector": [vp, i32, i32, i32, i32, i32, P(vp)],
+    "tq_pool_sector_table": [vp, P(i64), P(vp), P(vp)],
+    "tq_state_create_sector": [vp, i32, i32, i32, i32, P(vp)],
+    "tq_state_wrap_sector": [vp, i32, i32, i32, i32, vp, P(vp)],
     "tq_evolve_taylor5": [vp, vp, i32, f64, vp, i32, vp],
     "tq_evolve_taylor5_csr": [vp, i32, vp, vp, vp, f64, vp, i32, vp],
     "tq_energy": [vp, vp, vp, P(f64), vp],

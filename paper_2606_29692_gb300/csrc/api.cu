@@ -147,6 +147,21 @@ long long build_xell(tq_ctx* c, HamView& h, double maxc, int prec, std::vector<v
     return np;
 }
 
+// A pool, Hamiltonian and state must describe the same space: the same
+// qubit count, and either all the full space or all the same sector.
+void check_space(const tq_pool* p, const tq_state* s) {
+    TQ_REQUIRE(s->nq == p->nq, "state and pool qubit counts differ");
+    TQ_REQUIRE(s->sector == p->sector, "state and pool differ in sector restriction");
+    if (p->sector)
+        TQ_REQUIRE(s->n_alpha == p->n_alpha && s->n_beta == p->n_beta, "state and pool sectors differ");
+}
+void check_space(const tq_ham* h, const tq_state* s) {
+    TQ_REQUIRE(h->nq == s->nq, "state and Hamiltonian qubit counts differ");
+    TQ_REQUIRE(h->sector == s->sector, "state and Hamiltonian differ in sector restriction");
+    if (h->sector)
+        TQ_REQUIRE(s->n_alpha == h->n_alpha && s->n_beta == h->n_beta, "state and Hamiltonian sectors differ");
+}
+
 void free_all(std::vector<void*>& allocs) {
     for (void* p : allocs)
         if (p) cudaFree(p);
@@ -238,6 +253,7 @@ extern "C" int tq_autotune_pair(tq_ctx* c, const tq_pool* p, int prec, int n_sta
                                 double* best_ms) {
     API_BEGIN
     TQ_REQUIRE(c && p, "null argument");
+    TQ_REQUIRE(!p->sector, "the pair-kernel autotuner works on full-space pools");
     check_prec(prec);
     TQ_REQUIRE(n_states >= 1, "n_states must be >= 1");
     set_device(c);
@@ -303,7 +319,8 @@ extern "C" int tq_autotune_spmv(tq_ctx* c, const tq_ham* h, const tq_state* psi,
                                 double* best_ms) {
     API_BEGIN
     TQ_REQUIRE(c && h && psi, "null argument");
-    TQ_REQUIRE(h->nq == psi->nq && h->prec == psi->prec, "state and Hamiltonian do not match");
+    check_space(h, psi);
+    TQ_REQUIRE(h->prec == psi->prec, "state and Hamiltonian precisions differ");
     set_device(c);
     double* part = prepare(c, h->D, nullptr, h->nq);
     cudaEvent_t e0, e1;
@@ -312,6 +329,7 @@ extern "C" int tq_autotune_spmv(tq_ctx* c, const tq_ham* h, const tq_state* psi,
     int best = c->spmv_lanes;
     float best_t = 1e30f;
     for (int l : {4, 8, 16, 32, (int)TQ_SPMV_XELL}) {
+        if (l == TQ_SPMV_XELL && h->sector) continue;   // a sector Hamiltonian has the CSR only
         c->spmv_lanes = l;
         run_energy(c, h, psi, part, 0);
         TQ_CUDA(cudaEventRecord(e0, 0));
@@ -441,16 +459,12 @@ extern "C" int tq_hf_index(int n_qubits, int n_electrons, int mapping, long long
 
 // ============================================================ Hamiltonian
 
-extern "C" int tq_build_hamiltonian(tq_ctx* c, int n_spatial, const double* h1, const double* g2,
-                                    double e_const, int mapping, int prec, tq_ham** out) {
-    API_BEGIN
-    TQ_REQUIRE(c && out, "null argument");
-    *out = nullptr;
-    check_prec(prec);
-    TQ_REQUIRE(std::isfinite(e_const), "e_const is not finite");
-    TQ_REQUIRE(n_spatial >= 1 && 2 * n_spatial <= TQ_MAX_STATE_QUBITS,
-               "n_spatial must give at most 26 qubits for a device Hamiltonian");
-    set_device(c);
+namespace {
+
+// Pauli sum -> device Hamiltonian (diagonal, CSR, and outside a sector the
+// XOR-ELL layout), over the full space or over a sector (`sect` non-null).
+tq_ham* make_hamiltonian(tq_ctx* c, int n_spatial, const double* h1, const double* g2, double e_const,
+                         int mapping, int prec, const SectorSpec* sect) {
     auto terms = pauli_hamiltonian(n_spatial, h1, g2, e_const, mapping);
     auto* h = new tq_ham();
     try {
@@ -459,7 +473,7 @@ extern "C" int tq_build_hamiltonian(tq_ctx* c, int n_spatial, const double* h1, 
         h->nq = 2 * n_spatial;
         h->prec = prec;
         h->mapping = mapping;
-        h->D = 1ll << h->nq;
+        h->D = sect ? sector_dim(sect->n, sect->na, sect->nb) : 1ll << h->nq;
         h->n_pauli = (long long)terms.size();
         std::vector<uint32_t> gx, tz, dz;
         std::vector<int> goff;
@@ -492,21 +506,81 @@ extern "C" int tq_build_hamiltonian(tq_ctx* c, int n_spatial, const double* h1, 
         v.Kd = (int)dz.size();
         v.dz = upload(h->allocs, dz);
         v.dc = upload(h->allocs, dc);
+        size_t extra = 0;
+        if (sect) {
+            h->sector = 1;
+            h->n_alpha = sect->na;
+            h->n_beta = sect->nb;
+            const auto basis = sector_basis(*sect);
+            v.sq = upload(h->allocs, basis);
+            v.sect = upload(h->allocs, std::vector<SectorSpec>{*sect});
+            extra = basis.size() * 4 + sizeof(SectorSpec);
+        }
         double* diag = static_cast<double*>(dev_alloc((size_t)h->D * sizeof(double)));
         h->allocs.push_back(diag);
         v.diag = diag;
         launch(c, "diag", 0, [&] { return launch_diag(v, diag, c->sm_count, 0); });
         h->nnz = build_csr(c, v, maxc, prec, h->allocs, &h->n_amb, &h->max_row);
-        const long long np = build_xell(c, v, maxc, prec, h->allocs);
+        const long long np = sect ? 0 : build_xell(c, v, maxc, prec, h->allocs);
         const size_t vb = prec == TQ_C128 ? 8 : 4;
-        h->bytes = (size_t)h->D * 8 + (size_t)(h->D + 1) * 4 + (size_t)h->nnz * (4 + vb) +
-                   (size_t)(v.n_blocks + 1) * 4 + (size_t)np * (4 + XELL_ROWS * vb) + (size_t)(v.xgrid + 1) * 4 +
+        h->bytes = (size_t)h->D * 8 + (size_t)(h->D + 1) * 4 + (size_t)h->nnz * (4 + vb) + extra +
+                   (sect ? 0 : (size_t)(v.n_blocks + 1) * 4 + (size_t)np * (4 + XELL_ROWS * vb) + (size_t)(v.xgrid + 1) * 4) +
                    (gx.size() + goff.size() + tz.size() + dz.size()) * 4 + (tc.size() + dc.size()) * 8;
     } catch (...) {
         tq_ham_free(h);
         throw;
     }
-    *out = h;
+    return h;
+}
+
+}  // namespace
+
+extern "C" int tq_build_hamiltonian(tq_ctx* c, int n_spatial, const double* h1, const double* g2,
+                                    double e_const, int mapping, int prec, tq_ham** out) {
+    API_BEGIN
+    TQ_REQUIRE(c && out, "null argument");
+    *out = nullptr;
+    check_prec(prec);
+    TQ_REQUIRE(std::isfinite(e_const), "e_const is not finite");
+    TQ_REQUIRE(n_spatial >= 1 && 2 * n_spatial <= TQ_MAX_STATE_QUBITS,
+               "n_spatial must give at most 26 qubits for a device Hamiltonian");
+    set_device(c);
+    *out = make_hamiltonian(c, n_spatial, h1, g2, e_const, mapping, prec, nullptr);
+    API_END
+}
+
+extern "C" int tq_build_hamiltonian_sector(tq_ctx* c, int n_spatial, const double* h1, const double* g2,
+                                           double e_const, int mapping, int prec, int n_alpha, int n_beta,
+                                           tq_ham** out) {
+    API_BEGIN
+    TQ_REQUIRE(c && out, "null argument");
+    *out = nullptr;
+    check_prec(prec);
+    TQ_REQUIRE(std::isfinite(e_const), "e_const is not finite");
+    TQ_REQUIRE(n_spatial >= 1 && 2 * n_spatial <= TQ_MAX_STATE_QUBITS,
+               "n_spatial must give at most 26 qubits for a device Hamiltonian");
+    const SectorSpec sp = make_sector_spec(n_spatial, n_alpha, n_beta, mapping);
+    set_device(c);
+    *out = make_hamiltonian(c, n_spatial, h1, g2, e_const, mapping, prec, &sp);
+    API_END
+}
+
+extern "C" int tq_sector_dim(int n_spatial, int n_alpha, int n_beta, long long* dim) {
+    API_BEGIN
+    TQ_REQUIRE(dim != nullptr, "null argument");
+    const SectorSpec sp = make_sector_spec(n_spatial, n_alpha, n_beta, TQ_JW);
+    *dim = sector_dim(sp.n, sp.na, sp.nb);
+    API_END
+}
+
+extern "C" int tq_sector_basis(int n_spatial, int n_alpha, int n_beta, int mapping, long long capacity,
+                               unsigned* qubit_index) {
+    API_BEGIN
+    TQ_REQUIRE(qubit_index != nullptr, "null argument");
+    const SectorSpec sp = make_sector_spec(n_spatial, n_alpha, n_beta, mapping);
+    TQ_REQUIRE(capacity >= sector_dim(sp.n, sp.na, sp.nb), "capacity is smaller than the sector dimension");
+    const auto b = sector_basis(sp);
+    std::copy(b.begin(), b.end(), qubit_index);
     API_END
 }
 
@@ -557,13 +631,9 @@ extern "C" int tq_ham_free(tq_ham* h) {
 
 // =================================================================== pool
 
-extern "C" int tq_build_pool(tq_ctx* c, int n_spatial, int n_electrons, int mapping, tq_pool** out) {
-    API_BEGIN
-    TQ_REQUIRE(c && out, "null argument");
-    *out = nullptr;
-    TQ_REQUIRE(n_spatial >= 1 && 2 * n_spatial <= TQ_MAX_STATE_QUBITS, "n_spatial out of range");
-    check_mapping(mapping);
-    set_device(c);
+namespace {
+
+tq_pool* make_pool(tq_ctx* c, int n_spatial, int n_electrons, int mapping) {
     auto ex = excitations(n_spatial, n_electrons);
     TQ_REQUIRE(!ex.empty(), "the pool is empty for this electron count");
     auto* p = new tq_pool();
@@ -652,7 +722,73 @@ extern "C" int tq_build_pool(tq_ctx* c, int n_spatial, int n_electrons, int mapp
         tq_pool_free(p);
         throw;
     }
+    return p;
+}
+
+}  // namespace
+
+extern "C" int tq_build_pool(tq_ctx* c, int n_spatial, int n_electrons, int mapping, tq_pool** out) {
+    API_BEGIN
+    TQ_REQUIRE(c && out, "null argument");
+    *out = nullptr;
+    TQ_REQUIRE(n_spatial >= 1 && 2 * n_spatial <= TQ_MAX_STATE_QUBITS, "n_spatial out of range");
+    check_mapping(mapping);
+    set_device(c);
+    *out = make_pool(c, n_spatial, n_electrons, mapping);
+    API_END
+}
+
+extern "C" int tq_build_pool_sector(tq_ctx* c, int n_spatial, int n_electrons, int mapping, int n_alpha,
+                                    int n_beta, tq_pool** out) {
+    API_BEGIN
+    TQ_REQUIRE(c && out, "null argument");
+    *out = nullptr;
+    TQ_REQUIRE(n_spatial >= 1 && 2 * n_spatial <= TQ_MAX_STATE_QUBITS, "n_spatial out of range");
+    const SectorSpec sp = make_sector_spec(n_spatial, n_alpha, n_beta, mapping);
+    set_device(c);
+    tq_pool* p = make_pool(c, n_spatial, n_electrons, mapping);
+    try {
+        const long long dim = sector_dim(sp.n, sp.na, sp.nb);
+        std::vector<void*> tmp;
+        const uint32_t* sq = upload(tmp, sector_basis(sp));
+        const SectorSpec* dsp = upload(tmp, std::vector<SectorSpec>{sp});
+        unsigned long long* bad = static_cast<unsigned long long*>(dev_alloc(sizeof(unsigned long long)));
+        tmp.push_back(bad);
+        int* scol = static_cast<int*>(dev_alloc((size_t)p->M * dim * sizeof(int)));
+        p->allocs.push_back(scol);
+        signed char* ssgn = static_cast<signed char*>(dev_alloc((size_t)p->M * dim));
+        p->allocs.push_back(ssgn);
+        unsigned long long hbad = 0;
+        try {
+            TQ_CUDA(cudaMemset(bad, 0, sizeof(unsigned long long)));
+            launch(c, "sector_pool", 0, [&] { return launch_sector_pool(p->view, sq, dsp, dim, scol, ssgn, bad, c->sm_count, 0); });
+            TQ_CUDA(cudaMemcpy(&hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost));
+        } catch (...) {
+            free_all(tmp);
+            throw;
+        }
+        free_all(tmp);
+        if (hbad) throw Error(TQ_ENUMERIC, "a pool generator leaves the sector");
+        p->sector = 1;
+        p->n_alpha = n_alpha;
+        p->n_beta = n_beta;
+        p->view.sdim = dim;
+        p->view.scol = scol;
+        p->view.ssgn = ssgn;
+    } catch (...) {
+        tq_pool_free(p);
+        throw;
+    }
     *out = p;
+    API_END
+}
+
+extern "C" int tq_pool_sector_table(const tq_pool* p, long long* dim, const int** col, const signed char** sgn) {
+    API_BEGIN
+    TQ_REQUIRE(p != nullptr, "pool is null");
+    if (dim) *dim = p->view.sdim;
+    if (col) *col = p->view.scol;
+    if (sgn) *sgn = p->view.ssgn;
     API_END
 }
 
@@ -767,6 +903,59 @@ extern "C" int tq_state_wrap(tq_ctx* c, int n_qubits, int prec, void* dev_ptr, t
     API_END
 }
 
+namespace {
+
+tq_state* new_sector_state(tq_ctx* c, int n_spatial, int n_alpha, int n_beta, int prec) {
+    const SectorSpec sp = make_sector_spec(n_spatial, n_alpha, n_beta, TQ_JW);
+    auto* s = new tq_state();
+    s->ctx = c;
+    s->nq = 2 * n_spatial;
+    s->prec = prec;
+    s->D = sector_dim(sp.n, sp.na, sp.nb);
+    s->sector = 1;
+    s->n_spatial = n_spatial;
+    s->n_alpha = n_alpha;
+    s->n_beta = n_beta;
+    return s;
+}
+
+}  // namespace
+
+extern "C" int tq_state_create_sector(tq_ctx* c, int n_spatial, int n_alpha, int n_beta, int prec,
+                                      tq_state** out) {
+    API_BEGIN
+    TQ_REQUIRE(c && out, "null argument");
+    *out = nullptr;
+    check_prec(prec);
+    TQ_REQUIRE(2 * n_spatial <= TQ_MAX_STATE_QUBITS, "n_spatial out of range");
+    set_device(c);
+    tq_state* s = new_sector_state(c, n_spatial, n_alpha, n_beta, prec);
+    s->owned = 1;
+    try {
+        s->data = dev_alloc((size_t)s->D * elem_bytes(prec));
+        TQ_CUDA(cudaMemset(s->data, 0, (size_t)s->D * elem_bytes(prec)));
+    } catch (...) {
+        delete s;
+        throw;
+    }
+    *out = s;
+    API_END
+}
+
+extern "C" int tq_state_wrap_sector(tq_ctx* c, int n_spatial, int n_alpha, int n_beta, int prec, void* dev_ptr,
+                                    tq_state** out) {
+    API_BEGIN
+    TQ_REQUIRE(c && out && dev_ptr, "null argument");
+    *out = nullptr;
+    check_prec(prec);
+    TQ_REQUIRE(2 * n_spatial <= TQ_MAX_STATE_QUBITS, "n_spatial out of range");
+    TQ_REQUIRE(((uintptr_t)dev_ptr & 15u) == 0, "state pointer must be 16-byte aligned");
+    tq_state* s = new_sector_state(c, n_spatial, n_alpha, n_beta, prec);
+    s->data = dev_ptr;
+    *out = s;
+    API_END
+}
+
 extern "C" int tq_state_data(const tq_state* s, void** dev_ptr, int* n_qubits, int* prec) {
     API_BEGIN
     TQ_REQUIRE(s != nullptr, "state is null");
@@ -780,7 +969,18 @@ extern "C" int tq_state_set_hf(tq_state* s, int n_electrons, int mapping, void* 
     API_BEGIN
     TQ_REQUIRE(s != nullptr, "state is null");
     set_device(s->ctx);
-    const long long idx = (long long)hf_index(s->nq, n_electrons, mapping);
+    long long idx;
+    if (s->sector) {
+        // the lowest determinant (spin orbitals P < n_electrons) has rank 0
+        // in its sector, and is outside any other
+        check_mapping(mapping);
+        TQ_REQUIRE(n_electrons >= 0 && n_electrons <= s->nq, "n_electrons out of range");
+        TQ_REQUIRE((n_electrons + 1) / 2 == s->n_alpha && n_electrons / 2 == s->n_beta,
+                   "the lowest determinant is not in this state's sector");
+        idx = 0;
+    } else {
+        idx = (long long)hf_index(s->nq, n_electrons, mapping);
+    }
     check_launch(s->ctx, launch_set_basis(s->data, s->prec, s->D, idx, as_stream(stream)));
     API_END
 }
@@ -797,20 +997,48 @@ extern "C" int tq_state_free(tq_state* s) {
 
 // ================================================================ hot path
 
+namespace {
+
+long long state_len(const tq_pool* p) { return p->sector ? p->view.sdim : 1ll << p->nq; }
+
+// norm partials per state of the Taylor-5 launch for this pool
+int update_tiles(const tq_pool* p, int upt) {
+    return p->sector ? sector_tiles(p->view.sdim) : taylor5_pair_parts(p->nq, upt);
+}
+
+// Taylor-5 on n states (ops and angles from k/theta arrays, or k_fixed and
+// theta_fixed, or the step record when `gate` is set)
+void launch_update(tq_ctx* c, const tq_pool* p, long long n, int prec, int upt, void* psi, const int* k,
+                   const double* theta, int k_fixed, double theta_fixed, const DevStep* gate, double* part,
+                   cudaStream_t s) {
+    if (p->sector) {
+        launch(c, gate ? "taylor5_sector_gated" : "taylor5_sector", s, [&] {
+            return launch_taylor5_sector(p->view, n, prec, psi, k, theta, k_fixed, theta_fixed, gate, part, s);
+        });
+    } else if (gate) {
+        launch(c, "taylor5_pair_gated", s, [&] { return launch_taylor5_pair_gated(p->view, prec, upt, psi, gate, part,
+                                                  c->sm_count, s); });
+    } else {
+        launch(c, "taylor5_pair", s, [&] { return launch_taylor5_pair(p->view, (int)n, prec, upt, psi, k, theta, k_fixed,
+                                                                      theta_fixed, part, c->sm_count, s); });
+    }
+}
+
+}  // namespace
+
 extern "C" int tq_evolve_taylor5(tq_ctx* c, const tq_pool* p, int k, double theta, tq_state* psi,
                                  int renormalize, void* stream) {
     API_BEGIN
     TQ_REQUIRE(c && p && psi, "null argument");
     TQ_REQUIRE(k >= 0 && k < p->M, "pool index out of range");
     TQ_REQUIRE(std::isfinite(theta), "theta is not finite");
-    TQ_REQUIRE(psi->nq == p->nq, "state and pool qubit counts differ");
+    check_space(p, psi);
     set_device(c);
     cudaStream_t s = as_stream(stream);
     const int upt = c->pair_upt[psi->prec];
-    const int tiles = taylor5_pair_parts(p->nq, upt);
+    const int tiles = update_tiles(p, upt);
     double* part = static_cast<double*>(scratch(c, S_PART, (size_t)tiles * sizeof(double)));
-    launch(c, "taylor5_pair", s, [&] { return launch_taylor5_pair(p->view, 1, psi->prec, upt, psi->data, nullptr, nullptr, k, theta, part,
-                                        c->sm_count, s); });
+    launch_update(c, p, 1, psi->prec, upt, psi->data, nullptr, nullptr, k, theta, nullptr, part, s);
     if (renormalize) {
         launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, psi->prec, 1, tiles, nullptr, &c->step->norm2, s); });
         launch(c, "scale", s, [&] { return launch_scale(psi->data, psi->prec, psi->D, &c->step->norm2, s); });
@@ -850,23 +1078,31 @@ size_t partials_needed(long long D, int n_gitems, int nq, int sms) {
 }
 
 void run_energy(tq_ctx* c, const tq_ham* h, const tq_state* psi, double* part, cudaStream_t s) {
-    TQ_REQUIRE(h->nq == psi->nq, "state and Hamiltonian qubit counts differ");
+    check_space(h, psi);
     TQ_REQUIRE(h->prec == psi->prec, "state and Hamiltonian precisions differ");
     double2* w = static_cast<double2*>(c->scratch[S_W0]);
     float2* w32 = psi->prec == TQ_C64 ? static_cast<float2*>(c->scratch[S_W32]) : nullptr;
-    if (c->spmv_lanes == TQ_SPMV_XELL)
+    // a sector Hamiltonian has the CSR only
+    const int lanes = c->spmv_lanes == TQ_SPMV_XELL && h->sector ? 8 : c->spmv_lanes;
+    if (lanes == TQ_SPMV_XELL)
         launch(c, "energy_xell", s, [&] { return launch_energy_xell(h->view, psi->data, psi->prec, w, w32, part,
                                                                     c->tickets, c->step, s); });
     else
         launch(c, "energy_csr", s, [&] { return launch_energy_csr2(h->view, psi->data, psi->prec, w, w32, part,
-                                                                   c->tickets, c->step, c->sm_count, s,
-                                                                   c->spmv_lanes); });
+                                                                   c->tickets, c->step, c->sm_count, s, lanes); });
 }
 
 void run_gradients(tq_ctx* c, const tq_ham* h, const tq_pool* p, const tq_state* psi, double* g,
                    double* part, cudaStream_t s) {
-    TQ_REQUIRE(p->nq == psi->nq, "state and pool qubit counts differ");
+    check_space(p, psi);
     run_energy(c, h, psi, part, s);
+    if (p->sector) {
+        launch(c, "sector_gradients", s, [&] {
+            return launch_sector_gradients(p->view, static_cast<double2*>(c->scratch[S_W0]), psi->data, psi->prec,
+                                           c->step, g, s);
+        });
+        return;
+    }
     launch(c, "pool_gradients", s, [&] {
         return launch_pool_gradients(p->view, static_cast<double2*>(c->scratch[S_W0]),
                                      static_cast<float2*>(c->scratch[S_W32]), psi->data, psi->prec, c->step,
@@ -913,7 +1149,8 @@ extern "C" int tq_energy_matrix_free(tq_ctx* c, const tq_ham* h, const tq_state*
                                      void* stream) {
     API_BEGIN
     TQ_REQUIRE(c && h && psi && E, "null argument");
-    TQ_REQUIRE(h->nq == psi->nq, "state and Hamiltonian qubit counts differ");
+    TQ_REQUIRE(!h->sector, "the matrix-free energy works in the full space only");
+    check_space(h, psi);
     set_device(c);
     cudaStream_t s = as_stream(stream);
     double* part = prepare(c, h->D, nullptr, h->nq);
@@ -963,16 +1200,19 @@ extern "C" int tq_adapt_step(tq_ctx* c, const tq_ham* h, const tq_pool* p, tq_st
     run_gradients(c, h, p, psi, g, part, s);
     launch(c, "select", s, [&] { return launch_select(g, p->M, eps, psi->prec, c->step, s); });
     if (std::isnan(theta)) {
-        launch(c, "apply_twice", s, [&] { return launch_apply_twice(p->view, c->step, psi->data, psi->prec, u1, u2, s); });
+        if (p->sector)
+            launch(c, "apply_twice_sector", s, [&] { return launch_apply_twice_sector(p->view, c->step, psi->data, psi->prec,
+                                                                                      u1, u2, s); });
+        else
+            launch(c, "apply_twice", s, [&] { return launch_apply_twice(p->view, c->step, psi->data, psi->prec, u1, u2, s); });
         launch(c, "spmv_c128_gated", s, [&] { return launch_spmv_c128_gated(h->view, u1, w1, c->step, c->sm_count, s); });
         launch(c, "spmv_c128_gated", s, [&] { return launch_spmv_c128_gated(h->view, u2, w2, c->step, c->sm_count, s); });
         launch(c, "line_dots", s, [&] { return launch_line_dots(w0, w1, w2, u1, u2, D, part, c->tickets + 2, c->step, s); });
     }
     launch(c, "line_search", s, [&] { return launch_line_search(c->step, theta, s); });
     const int upt = c->pair_upt[psi->prec];
-    const int tiles = taylor5_pair_parts(p->nq, upt);
-    launch(c, "taylor5_pair_gated", s, [&] { return launch_taylor5_pair_gated(p->view, psi->prec, upt, psi->data, c->step, part,
-                                              c->sm_count, s); });
+    const int tiles = update_tiles(p, upt);
+    launch_update(c, p, 1, psi->prec, upt, psi->data, nullptr, nullptr, 0, 0.0, c->step, part, s);
     launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, psi->prec, 1, tiles, nullptr, &c->step->norm2, s); });
     launch(c, "scale_gated", s, [&] { return launch_scale_gated(psi->data, psi->prec, D, &c->step->norm2, c->step, s); });
     DevStep hs;
@@ -1003,10 +1243,9 @@ extern "C" int tq_evolve_taylor5_batch(tq_ctx* c, const tq_pool* p, int n_states
     set_device(c);
     cudaStream_t s = as_stream(stream);
     const int upt = c->pair_upt[prec];
-    const int tiles = taylor5_pair_parts(p->nq, upt);
+    const int tiles = update_tiles(p, upt);
     double* part = static_cast<double*>(scratch(c, S_PART, (size_t)n_states * tiles * sizeof(double)));
-    launch(c, "taylor5_pair", s, [&] { return launch_taylor5_pair(p->view, n_states, prec, upt, psi, k, theta, 0, 0.0, part,
-                                        c->sm_count, s); });
+    launch_update(c, p, n_states, prec, upt, psi, k, theta, 0, 0.0, nullptr, part, s);
     if (norm2) launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, prec, n_states, tiles, norm2, nullptr, s); });
     API_END
 }
@@ -1023,13 +1262,13 @@ extern "C" int tq_evolve_taylor5_batch_host(tq_ctx* c, const tq_pool* p, int n_s
     set_device(c);
     for (auto& st : c->aux)
         if (!st) TQ_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-    const long long D = 1ll << p->nq;
+    const long long D = state_len(p);
     const size_t sb = (size_t)D * elem_bytes(prec);
     // chunk of about 64 MiB of states per stream
     int chunk = (int)std::max<long long>(1, (64ll << 20) / (long long)sb);
     chunk = std::min(chunk, n_states);
     const int upt = c->pair_upt[prec];
-    const int tiles = taylor5_pair_parts(p->nq, upt);
+    const int tiles = update_tiles(p, upt);
     const size_t per_stream = (size_t)chunk * sb + (size_t)chunk * (sizeof(int) + 2 * sizeof(double)) +
                               (size_t)chunk * tiles * sizeof(double) + 256;
     unsigned char* stage = static_cast<unsigned char*>(scratch(c, S_STAGE, 3 * per_stream));
@@ -1047,7 +1286,7 @@ extern "C" int tq_evolve_taylor5_batch_host(tq_ctx* c, const tq_pool* p, int n_s
                                 cudaMemcpyHostToDevice, s));
         TQ_CUDA(cudaMemcpyAsync(dk, k_host + c0, (size_t)n * sizeof(int), cudaMemcpyHostToDevice, s));
         TQ_CUDA(cudaMemcpyAsync(dth, theta_host + c0, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s));
-        launch(c, "taylor5_pair", s, [&] { return launch_taylor5_pair(p->view, n, prec, upt, dpsi, dk, dth, 0, 0.0, part, c->sm_count, s); });
+        launch_update(c, p, n, prec, upt, dpsi, dk, dth, 0, 0.0, nullptr, part, s);
         TQ_CUDA(cudaMemcpyAsync(static_cast<unsigned char*>(psi_host) + (size_t)c0 * sb, dpsi, (size_t)n * sb,
                                 cudaMemcpyDeviceToHost, s));
         if (norm2_host) {

@@ -407,6 +407,9 @@ extern "C" int tq_batch_create(tq_ctx* c, int n_traj, tq_ham* const* hams, tq_po
                                const double* thetas, double eps, tq_batch** out) {
     API_BEGIN
     TQ_REQUIRE(c && hams && pools && n_electrons && mappings && lengths && thetas && out, "null argument");
+    for (int i = 0; i < n_traj; ++i)
+        TQ_REQUIRE(hams[i] && pools[i] && !hams[i]->sector && !pools[i]->sector,
+                   "the trajectory batch works in the full space");
     TQ_REQUIRE(n_traj >= 1, "n_traj must be >= 1");
     TQ_REQUIRE(std::isfinite(eps) && eps >= 0.0, "eps must be finite and >= 0");
     *out = nullptr;

@@ -11,7 +11,12 @@
 //           shared memory with a ballot, sorts them by column (bitonic
 //           network over the next power of two) and writes them.
 // The X-mask 0 group (the diagonal) is kept apart in a float64 array.
+//
+// In a sector (h.sq, h.sect set) row r stands for qubit index h.sq[r] and
+// the column of qubit index c is its sector rank; columns outside the
+// sector (rank -1) are skipped.
 #include "dev.cuh"
+#include "sector.cuh"
 
 #include <climits>
 
@@ -29,15 +34,25 @@ __device__ __forceinline__ double group_value(const HamView& h, int g, uint32_t 
     return v;
 }
 
+__device__ __forceinline__ uint32_t row_index(const HamView& h, long long r) {
+    return h.sq ? h.sq[r] : (uint32_t)r;
+}
+__device__ __forceinline__ long long col_position(const HamView& h, uint32_t c) {
+    return h.sect ? sector_rank(c, *h.sect) : (long long)c;
+}
+
 __global__ void k_csr_count(HamView h, double tol, double amb_hi, int* counts,
                             unsigned long long* n_amb) {
     const int lane = threadIdx.x & 31;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long r = warp; r < h.D; r += nwarps) {
+        const uint32_t e = row_index(h, r);
         int cnt = 0, amb = 0;
         for (int g = lane; g < h.G; g += 32) {
-            const double a = fabs(group_value(h, g, (uint32_t)r ^ h.gx[g]));
+            const uint32_t c = e ^ h.gx[g];
+            if (col_position(h, c) < 0) continue;
+            const double a = fabs(group_value(h, g, c));
             cnt += a > tol;
             amb += (a > tol) & (a <= amb_hi);
         }
@@ -53,10 +68,11 @@ __global__ void k_csr_count(HamView h, double tol, double amb_hi, int* counts,
 __global__ void k_diag(HamView h, double* diag) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < h.D; r += stride) {
+        const uint32_t e = row_index(h, r);
         double v = 0.0;
         for (int t = 0; t < h.Kd; ++t) {
             const double c = h.dc[t];
-            v += parity32((uint32_t)r & h.dz[t]) ? -c : c;
+            v += parity32(e & h.dz[t]) ? -c : c;
         }
         diag[r] = v;
     }
@@ -113,6 +129,7 @@ __global__ void k_csr_fill(HamView h, double tol, int cap, int* col, VT* val) {
         const int start = h.rowptr[r];
         const int n = h.rowptr[r + 1] - start;
         if (n == 0) continue;
+        const uint32_t e = row_index(h, r);
         int base = 0;
         for (int g0 = 0; g0 < h.G; g0 += 32) {
             const int g = g0 + lane;
@@ -120,9 +137,13 @@ __global__ void k_csr_fill(HamView h, double tol, int cap, int* col, VT* val) {
             double v = 0.0;
             bool keep = false;
             if (g < h.G) {
-                c = (uint32_t)r ^ h.gx[g];
-                v = group_value(h, g, c);
-                keep = fabs(v) > tol;
+                const uint32_t cq = e ^ h.gx[g];
+                const long long pos = col_position(h, cq);
+                if (pos >= 0) {
+                    c = (uint32_t)pos;
+                    v = group_value(h, g, cq);
+                    keep = fabs(v) > tol;
+                }
             }
             const unsigned ball = __ballot_sync(0xffffffffu, keep);
             if (keep) {

@@ -65,6 +65,24 @@ std::vector<Excitation> excitations(int n, int ne);
 std::vector<PauliTerm> pauli_generator(const Excitation& ex, int N, int mapping);
 uint64_t hf_index(int N, int ne, int mapping);
 SignForm factor_generator(const std::vector<PauliTerm>& t);
+// rows of B^-1 (occupation bit j = parity(qubit index & rows[j])) and the
+// qubit index of an occupation index under a mapping
+std::vector<uint32_t> decode_rows(int N, int mapping);
+uint64_t encode_occupation(int N, int mapping, uint64_t occ);
+
+// Sector-restricted basis: occupation states with n_alpha electrons in the
+// even spin orbitals and n_beta in the odd ones, ranked colexicographically
+// (rank = rank_alpha * C(n, n_beta) + rank_beta).  A variant of the
+// paper's 2^N formulation, not part of it.
+struct SectorSpec {
+    int n, na, nb, nq, mapping;
+    uint32_t dec[32];        // rows of B^-1 (JW: unused)
+    int binom[16][16];       // C(i, j)
+};
+SectorSpec make_sector_spec(int n, int na, int nb, int mapping);
+long long sector_dim(int n, int na, int nb);
+// qubit indices of the sector in rank order
+std::vector<uint32_t> sector_basis(const SectorSpec& s);
 
 // --------------------------------------------------------------- device views
 
@@ -89,6 +107,11 @@ struct PoolView {
     const int2* gitems;     // gradient work items (op, chunk of support rows)
     int n_gitems;
     const int* gfirst;      // [M + 1] first work item of each op
+    // sector pools: A_k restricted to the sector, one entry per (op, row):
+    // A_k[r][scol] = ssgn (+-1), or ssgn = 0 (A_k annihilates row r)
+    long long sdim;         // sector dimension (0: full space)
+    const int* scol;        // [M sdim]
+    const signed char* ssgn;  // [M sdim]
 };
 
 constexpr int XELL_ROWS = 8;   // rows per XOR-ELL block
@@ -104,6 +127,8 @@ struct HamView {
     const int* rowptr;
     const int* col;
     const void* val;        // double or float
+    const uint32_t* sq;     // sector basis: qubit index of each row (null: full space)
+    const SectorSpec* sect; // sector spec on the device (null: full space)
     long long n_blocks;     // XOR-ELL row blocks of XELL_ROWS rows, ceil(D / XELL_ROWS)
     long long n_pairs;
     const int* xptr;        // [n_blocks + 1] first pair of each block
@@ -211,6 +236,18 @@ int launch_spmv_c128_gated(const HamView& h, const double2* x, double2* y,
                            const DevStep* gate, int sms, cudaStream_t s);
 int energy_grid(long long D, int sms);
 
+// sector-restricted basis
+int sector_tiles(long long dim);
+int launch_sector_pool(const PoolView& p, const uint32_t* sq, const SectorSpec* sect, long long dim, int* scol,
+                       signed char* ssgn, unsigned long long* bad, int sms, cudaStream_t s);
+int launch_taylor5_sector(const PoolView& p, long long n_states, int prec, void* psi, const int* k,
+                          const double* theta, int k_fixed, double theta_fixed, const DevStep* gate,
+                          double* partials, cudaStream_t s);
+int launch_sector_gradients(const PoolView& p, const double2* w, const void* psi, int prec, const DevStep* step,
+                            double* g, cudaStream_t s);
+int launch_apply_twice_sector(const PoolView& p, const DevStep* step, const void* psi, int prec, double2* u1,
+                              double2* u2, cudaStream_t s);
+
 }  // namespace tq
 
 // ------------------------------------------------------------------- handles
@@ -241,6 +278,7 @@ struct tq_ctx {
 struct tq_ham {
     tq_ctx* ctx = nullptr;
     int n_spatial = 0, nq = 0, prec = 0, mapping = 0;
+    int sector = 0, n_alpha = 0, n_beta = 0;   // sector-restricted basis
     long long D = 0, nnz = 0, n_pauli = 0, n_amb = 0;
     int max_row = 0;
     size_t bytes = 0;
@@ -251,6 +289,7 @@ struct tq_ham {
 struct tq_pool {
     tq_ctx* ctx = nullptr;
     int n_spatial = 0, n_electrons = 0, nq = 0, mapping = 0, M = 0;
+    int sector = 0, n_alpha = 0, n_beta = 0;   // sector-restricted basis
     std::vector<int> idx4;
     std::vector<tq::PauliTerm> terms;   // 8 slots per op (host copy)
     std::vector<int> nterm;
@@ -267,6 +306,7 @@ struct tq_pool {
 struct tq_state {
     tq_ctx* ctx = nullptr;
     int nq = 0, prec = 0, owned = 0;
+    int sector = 0, n_spatial = 0, n_alpha = 0, n_beta = 0;   // sector-restricted basis
     long long D = 0;
     void* data = nullptr;
 };

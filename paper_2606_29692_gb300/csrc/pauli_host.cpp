@@ -218,6 +218,79 @@ uint64_t hf_index(int N, int ne, int mapping) {
     return b;
 }
 
+std::vector<uint32_t> decode_rows(int N, int mapping) {
+    check_mapping(mapping);
+    Enc e = make_encoding(N, mapping);
+    std::vector<uint32_t> r(N);
+    for (int j = 0; j < N; ++j) r[j] = (uint32_t)e.q[j];
+    return r;
+}
+
+uint64_t encode_occupation(int N, int mapping, uint64_t occ) {
+    check_mapping(mapping);
+    Enc e = make_encoding(N, mapping);
+    uint64_t b = 0;
+    for (int P = 0; P < N; ++P)
+        if ((occ >> P) & 1) b ^= e.c[P];
+    return b;
+}
+
+namespace {
+long long choose(int n, int k) {
+    if (k < 0 || k > n) return 0;
+    long long r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;
+    return r;
+}
+
+// The k-subset of colexicographic rank `rank`: the largest element c_k is
+// the largest c with C(c, k) <= rank, and so on down.
+std::vector<int> colex_unrank(long long rank, int k) {
+    std::vector<int> out(k);
+    for (int j = k; j >= 1; --j) {
+        int c = j - 1;
+        while (choose(c + 1, j) <= rank) ++c;
+        out[j - 1] = c;
+        rank -= choose(c, j);
+    }
+    return out;
+}
+}  // namespace
+
+long long sector_dim(int n, int na, int nb) { return choose(n, na) * choose(n, nb); }
+
+SectorSpec make_sector_spec(int n, int na, int nb, int mapping) {
+    check_mapping(mapping);
+    if (n < 1 || 2 * n > TQ_MAX_STATE_QUBITS) throw Error(TQ_EINVAL, "n_spatial out of range [1, 13]");
+    if (na < 0 || na > n || nb < 0 || nb > n) throw Error(TQ_EINVAL, "n_alpha, n_beta out of range [0, n_spatial]");
+    SectorSpec s{};
+    s.n = n;
+    s.na = na;
+    s.nb = nb;
+    s.nq = 2 * n;
+    s.mapping = mapping;
+    auto rows = decode_rows(2 * n, mapping);
+    for (int j = 0; j < 2 * n; ++j) s.dec[j] = rows[j];
+    for (int i = 0; i < 16; ++i)
+        for (int j = 0; j < 16; ++j) s.binom[i][j] = (int)choose(i, j);
+    return s;
+}
+
+std::vector<uint32_t> sector_basis(const SectorSpec& s) {
+    const long long da = choose(s.n, s.na), db = choose(s.n, s.nb);
+    const Enc e = make_encoding(s.nq, s.mapping);
+    // qubit-space images of the alpha and beta halves (the encoding is linear)
+    std::vector<uint64_t> qa((size_t)da), qb((size_t)db);
+    for (long long r = 0; r < da; ++r)
+        for (int p : colex_unrank(r, s.na)) qa[(size_t)r] ^= e.c[2 * p];
+    for (long long r = 0; r < db; ++r)
+        for (int p : colex_unrank(r, s.nb)) qb[(size_t)r] ^= e.c[2 * p + 1];
+    std::vector<uint32_t> out((size_t)(da * db));
+    for (long long ra = 0; ra < da; ++ra)
+        for (long long rb = 0; rb < db; ++rb) out[(size_t)(ra * db + rb)] = (uint32_t)(qa[(size_t)ra] ^ qb[(size_t)rb]);
+    return out;
+}
+
 // Factor a generator's sign function (see common.h, SignForm).  The z masks
 // of its 2^m terms form an affine space z0 ^ span(d_1..d_m); when the
 // coefficients are c0 / 2^m * prod_i (-1)^{a_i t_i} (a = coordinates in that

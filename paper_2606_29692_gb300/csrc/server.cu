@@ -560,6 +560,7 @@ extern "C" int tq_server_create(tq_ctx* c, int prec, size_t hbm_budget, int max_
 extern "C" int tq_server_add_hamiltonian(tq_server* s, const tq_ham* h, const tq_pool* p, int* ham_id) {
     API_BEGIN
     TQ_REQUIRE(s && h && p && ham_id, "null argument");
+    TQ_REQUIRE(!h->sector && !p->sector, "the request loop works in the full space");
     TQ_REQUIRE(!s->running.load(), "add Hamiltonians before tq_server_start");
     TQ_REQUIRE(h->prec == s->prec, "Hamiltonian precision differs from the server's");
     TQ_REQUIRE(h->nq == p->nq, "Hamiltonian and pool qubit counts differ");

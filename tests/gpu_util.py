@@ -24,7 +24,7 @@ def dev_to_numpy(ptr, n, typestr):
 def ham_csr_numpy(ham):
     """(rowptr, col, val, diag) of a device Hamiltonian as numpy arrays."""
     rp, cl, vl, dg = tq.ham_csr(ham)
-    D = 1 << ham.n_qubits
+    D = getattr(ham, "dim", 1 << ham.n_qubits)
     rowptr = dev_to_numpy(rp, D + 1, "<i4")
     nnz = int(rowptr[-1])
     col = dev_to_numpy(cl, nnz, "<i4")
@@ -49,11 +49,11 @@ def oracle_split(H):
     return np.cumsum(rowptr), c, v, diag
 
 
-def to_state(ctx, psi, nq, prec):
+def to_state(ctx, psi, nq, prec, sector=None):
     import torch
     dt = torch.complex128 if prec == tq.TQ_C128 else torch.complex64
     t = torch.as_tensor(np.asarray(psi), dtype=dt).to("cuda").contiguous()
-    return tq.State(ctx, nq, prec, tensor=t)
+    return tq.State(ctx, nq, prec, tensor=t, sector=sector)
 
 
 def rel_l2(a, b):

@@ -118,3 +118,22 @@ def test_invalid_arguments_are_rejected(tq):
     ints, _ = synth.config0()
     with pytest.raises(tq.TQError):
         tq.pauli_hamiltonian(ints.h, ints.g, 0.0, 5)
+
+
+@pytest.mark.parametrize("mp", [mapping.JW, mapping.BK])
+def test_sector_basis_matches_oracle(tq, mp):
+    from oracle import sector
+    for n, na, nb in [(1, 1, 0), (3, 1, 2), (4, 2, 2), (6, 4, 4), (7, 3, 3), (7, 2, 4)]:
+        assert tq.sector_dim(n, na, nb) == sector.dimension(n, na, nb)
+        got = tq.sector_basis(n, na, nb, mp).astype(np.int64)
+        assert np.array_equal(got, sector.qubit_basis(n, na, nb, mp))
+    # the largest sector a device state can hold (26 qubits): dimension only
+    assert tq.sector_dim(13, 6, 7) == sector.dimension(13, 6, 7)
+
+
+def test_sector_arguments_are_rejected(tq):
+    for args in [(0, 0, 0), (14, 7, 7), (4, 5, 0), (4, 0, -1)]:
+        with pytest.raises(tq.TQError):
+            tq.sector_dim(*args)
+    with pytest.raises(tq.TQError):
+        tq.sector_basis(4, 2, 2, 7)
