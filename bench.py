@@ -311,6 +311,7 @@ def run_ours(args, rank, world, local_rank):
         extra["fp64_single_instance"] = measure_fp64_single(tq, ctx, pool, k, th)
         extra["spmv"] = measure_spmv(tq, ctx, args.spmv_qubits)
         extra["trajectories"] = measure_trajectories(tq, ctx, args.traj)
+        extra["sector"] = measure_sector(tq, ctx)
         if args.serve_seconds > 0:
             extra["serving"] = measure_serving(tq, local_rank, args.serve_seconds, args.serve_rate)
     out = None
@@ -420,6 +421,73 @@ def measure_spmv(tq, ctx, nq):
             "algorithmic_bytes": alg, "layout_bytes": layout, "achieved_gbs": gbs,
             "layout_gbs": layout / (ms * 1e-3) / 1e9, "peak_gbs": peak, "frac": gbs / peak,
             "energy": e, "l2_policy": "Hamiltonian larger than L2"}
+
+
+def measure_sector(tq, ctx, n_states=65536, reps=20):
+    """Batched Taylor-5 and energies in the sector-restricted basis.
+
+    The 14-qubit workload of the headline (7 orbitals, 6 electrons, BK,
+    strongly correlated) restricted to its Hartree-Fock sector (3 alpha + 3
+    beta electrons: 1225 amplitudes instead of 16384); n_states complex64
+    states, each with its own generator and angle (inputs larger than L2)."""
+    import numpy as np
+    import torch
+
+    import synth
+    ints, ne = synth.config2()
+    n = ints.n_spatial
+    na, nb = (ne + 1) // 2, ne // 2
+    mp = 1
+    pool = tq.build_pool_sector(ctx, n, ne, mp, na, nb)
+    dim = pool.dim
+    rng = np.random.default_rng(synth.SEED_T5_BATCH)
+    k = torch.as_tensor(rng.integers(0, pool.M, size=n_states).astype(np.int32)).cuda()
+    th = torch.as_tensor(rng.normal(0.0, 0.1, size=n_states)).cuda()
+    g = torch.Generator("cuda").manual_seed(5)
+    psi = torch.randn(n_states, dim, dtype=torch.complex64, device="cuda", generator=g)
+    psi /= torch.linalg.vector_norm(psi, dim=1, keepdim=True)
+    n2 = torch.zeros(n_states, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        tq.evolve_taylor5_batch(ctx, pool, psi, k, th, n2)
+    ctx.trace(True)
+    for _ in range(reps):
+        tq.evolve_taylor5_batch(ctx, pool, psi, k, th, n2)
+    rep = ctx.trace_report()
+    ctx.trace(False)
+    n_l, ms = rep["taylor5_sector"]
+    ms /= n_l
+    nr, nrms = rep.get("norm_reduce", (1, 0.0))      # the shared-memory update finishes norms itself
+    # every amplitude read and written once (the state goes through shared
+    # memory); the generator tables (int32 + int8 per row and op) stay in L2
+    alg = 2.0 * dim * 8
+    peak, _ = peaks()
+    gbs = alg * n_states / (ms * 1e-3) / 1e9
+    out = {"workload": f"{n_states} complex64 states of the 14-qubit BK Hamiltonian's ({na}, {nb}) sector "
+                       f"({dim} amplitudes), own generator and angle each",
+           "kernel": "k_taylor5_sector_smem<float>", "ms_per_launch": ms, "norm_reduce_ms": nrms / nr,
+           "updates_per_s": n_states / ((ms + nrms / nr) * 1e-3),
+           "algorithmic_bytes_per_update": alg, "achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak,
+           "norms_finite": bool(torch.isfinite(n2).all().item())}
+    # energies: 14 and 18 qubits in their Hartree-Fock sectors
+    for nq_, seed in ((14, None), (18, synth.SEED_CATALOGUE_BASE + 12)):
+        ints_ = ints if seed is None else synth.integrals(nq_ // 2, seed)
+        ne_ = ne if seed is None else synth.electrons_for(nq_ // 2)
+        a_, b_ = (ne_ + 1) // 2, ne_ // 2
+        ham = tq.build_hamiltonian_sector(ctx, ints_.h, ints_.g, ints_.e_const, mp, tq.TQ_C64, a_, b_)
+        st = tq.State(ctx, nq_, tq.TQ_C64, sector=(a_, b_))
+        tq.state_set_hf(st, ne_, mp)
+        tq.autotune_spmv(ctx, ham, st)
+        for _ in range(3):
+            tq.energy(ctx, ham, st)
+        ctx.trace(True)
+        for _ in range(reps):
+            tq.energy(ctx, ham, st)
+        r = ctx.trace_report()
+        ctx.trace(False)
+        nl, t = r["energy_csr"]
+        out[f"energy_{nq_}q"] = {"dim": ham.dim, "nnz": ham.nnz, "ms_per_energy": t / nl}
+    ctx.set_spmv_schedule(32)
+    return out
 
 
 def measure_serving(tq, device, seconds, rate):
@@ -541,7 +609,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the SpMV, trajectory-batch and request-loop measurements")
-    ap.add_argument("--section", choices=["spmv", "trajectories", "serving"], default=None,
+    ap.add_argument("--section", choices=["spmv", "trajectories", "serving", "sector"], default=None,
                     help="run one secondary measurement alone and print its JSON (profiling)")
     ap.add_argument("--spmv-qubits", type=int, default=18)
     ap.add_argument("--traj", type=int, default=256)
@@ -574,6 +642,8 @@ def main():
             print(json.dumps(measure_spmv(tq, ctx, args.spmv_qubits)))
         elif args.section == "trajectories":
             print(json.dumps(measure_trajectories(tq, ctx, args.traj)))
+        elif args.section == "sector":
+            print(json.dumps(measure_sector(tq, ctx)))
         else:
             print(json.dumps(measure_serving(tq, local_rank, args.serve_seconds, args.serve_rate)))
         return 0

@@ -1002,26 +1002,32 @@ namespace {
 long long state_len(const tq_pool* p) { return p->sector ? p->view.sdim : 1ll << p->nq; }
 
 // norm partials per state of the Taylor-5 launch for this pool
-int update_tiles(const tq_pool* p, int upt) {
-    return p->sector ? sector_tiles(p->view.sdim) : taylor5_pair_parts(p->nq, upt);
+int update_tiles(const tq_pool* p, int prec, int upt) {
+    return p->sector ? sector_tiles(p->view.sdim, prec) : taylor5_pair_parts(p->nq, upt);
 }
 
 // Taylor-5 on n states (ops and angles from k/theta arrays, or k_fixed and
-// theta_fixed, or the step record when `gate` is set)
-void launch_update(tq_ctx* c, const tq_pool* p, long long n, int prec, int upt, void* psi, const int* k,
+// theta_fixed, or the step record when `gate` is set).  Returns true when
+// the launch also wrote the float64 norms (norm2[i] and/or *step_norm2);
+// otherwise they are in `part`, for launch_norm_reduce.
+bool launch_update(tq_ctx* c, const tq_pool* p, long long n, int prec, int upt, void* psi, const int* k,
                    const double* theta, int k_fixed, double theta_fixed, const DevStep* gate, double* part,
-                   cudaStream_t s) {
+                   double* norm2, double* step_norm2, cudaStream_t s) {
     if (p->sector) {
         launch(c, gate ? "taylor5_sector_gated" : "taylor5_sector", s, [&] {
-            return launch_taylor5_sector(p->view, n, prec, psi, k, theta, k_fixed, theta_fixed, gate, part, s);
+            return launch_taylor5_sector(p->view, n, prec, psi, k, theta, k_fixed, theta_fixed, gate, part, norm2,
+                                         step_norm2, s);
         });
-    } else if (gate) {
+        return sector_in_smem(p->view.sdim, prec);
+    }
+    if (gate) {
         launch(c, "taylor5_pair_gated", s, [&] { return launch_taylor5_pair_gated(p->view, prec, upt, psi, gate, part,
                                                   c->sm_count, s); });
     } else {
         launch(c, "taylor5_pair", s, [&] { return launch_taylor5_pair(p->view, (int)n, prec, upt, psi, k, theta, k_fixed,
                                                                       theta_fixed, part, c->sm_count, s); });
     }
+    return false;
 }
 
 }  // namespace
@@ -1036,11 +1042,13 @@ extern "C" int tq_evolve_taylor5(tq_ctx* c, const tq_pool* p, int k, double thet
     set_device(c);
     cudaStream_t s = as_stream(stream);
     const int upt = c->pair_upt[psi->prec];
-    const int tiles = update_tiles(p, upt);
+    const int tiles = update_tiles(p, psi->prec, upt);
     double* part = static_cast<double*>(scratch(c, S_PART, (size_t)tiles * sizeof(double)));
-    launch_update(c, p, 1, psi->prec, upt, psi->data, nullptr, nullptr, k, theta, nullptr, part, s);
+    const bool fin = launch_update(c, p, 1, psi->prec, upt, psi->data, nullptr, nullptr, k, theta, nullptr, part,
+                                   nullptr, renormalize ? &c->step->norm2 : nullptr, s);
     if (renormalize) {
-        launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, psi->prec, 1, tiles, nullptr, &c->step->norm2, s); });
+        if (!fin)
+            launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, psi->prec, 1, tiles, nullptr, &c->step->norm2, s); });
         launch(c, "scale", s, [&] { return launch_scale(psi->data, psi->prec, psi->D, &c->step->norm2, s); });
     }
     API_END
@@ -1211,9 +1219,10 @@ extern "C" int tq_adapt_step(tq_ctx* c, const tq_ham* h, const tq_pool* p, tq_st
     }
     launch(c, "line_search", s, [&] { return launch_line_search(c->step, theta, s); });
     const int upt = c->pair_upt[psi->prec];
-    const int tiles = update_tiles(p, upt);
-    launch_update(c, p, 1, psi->prec, upt, psi->data, nullptr, nullptr, 0, 0.0, c->step, part, s);
-    launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, psi->prec, 1, tiles, nullptr, &c->step->norm2, s); });
+    const int tiles = update_tiles(p, psi->prec, upt);
+    if (!launch_update(c, p, 1, psi->prec, upt, psi->data, nullptr, nullptr, 0, 0.0, c->step, part, nullptr,
+                       &c->step->norm2, s))
+        launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, psi->prec, 1, tiles, nullptr, &c->step->norm2, s); });
     launch(c, "scale_gated", s, [&] { return launch_scale_gated(psi->data, psi->prec, D, &c->step->norm2, c->step, s); });
     DevStep hs;
     TQ_CUDA(cudaMemcpyAsync(&hs, c->step, sizeof(DevStep), cudaMemcpyDeviceToHost, s));
@@ -1243,10 +1252,11 @@ extern "C" int tq_evolve_taylor5_batch(tq_ctx* c, const tq_pool* p, int n_states
     set_device(c);
     cudaStream_t s = as_stream(stream);
     const int upt = c->pair_upt[prec];
-    const int tiles = update_tiles(p, upt);
+    const int tiles = update_tiles(p, prec, upt);
     double* part = static_cast<double*>(scratch(c, S_PART, (size_t)n_states * tiles * sizeof(double)));
-    launch_update(c, p, n_states, prec, upt, psi, k, theta, 0, 0.0, nullptr, part, s);
-    if (norm2) launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, prec, n_states, tiles, norm2, nullptr, s); });
+    const bool fin = launch_update(c, p, n_states, prec, upt, psi, k, theta, 0, 0.0, nullptr, part, norm2, nullptr, s);
+    if (norm2 && !fin)
+        launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, prec, n_states, tiles, norm2, nullptr, s); });
     API_END
 }
 
@@ -1268,7 +1278,7 @@ extern "C" int tq_evolve_taylor5_batch_host(tq_ctx* c, const tq_pool* p, int n_s
     int chunk = (int)std::max<long long>(1, (64ll << 20) / (long long)sb);
     chunk = std::min(chunk, n_states);
     const int upt = c->pair_upt[prec];
-    const int tiles = update_tiles(p, upt);
+    const int tiles = update_tiles(p, prec, upt);
     const size_t per_stream = (size_t)chunk * sb + (size_t)chunk * (sizeof(int) + 2 * sizeof(double)) +
                               (size_t)chunk * tiles * sizeof(double) + 256;
     unsigned char* stage = static_cast<unsigned char*>(scratch(c, S_STAGE, 3 * per_stream));
@@ -1286,11 +1296,12 @@ extern "C" int tq_evolve_taylor5_batch_host(tq_ctx* c, const tq_pool* p, int n_s
                                 cudaMemcpyHostToDevice, s));
         TQ_CUDA(cudaMemcpyAsync(dk, k_host + c0, (size_t)n * sizeof(int), cudaMemcpyHostToDevice, s));
         TQ_CUDA(cudaMemcpyAsync(dth, theta_host + c0, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s));
-        launch_update(c, p, n, prec, upt, dpsi, dk, dth, 0, 0.0, nullptr, part, s);
+        const bool fin = launch_update(c, p, n, prec, upt, dpsi, dk, dth, 0, 0.0, nullptr, part,
+                                       norm2_host ? dn : nullptr, nullptr, s);
         TQ_CUDA(cudaMemcpyAsync(static_cast<unsigned char*>(psi_host) + (size_t)c0 * sb, dpsi, (size_t)n * sb,
                                 cudaMemcpyDeviceToHost, s));
         if (norm2_host) {
-            launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, prec, n, tiles, dn, nullptr, s); });
+            if (!fin) launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, prec, n, tiles, dn, nullptr, s); });
             TQ_CUDA(cudaMemcpyAsync(norm2_host + c0, dn, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s));
         }
     }

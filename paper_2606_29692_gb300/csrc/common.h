@@ -237,12 +237,14 @@ int launch_spmv_c128_gated(const HamView& h, const double2* x, double2* y,
 int energy_grid(long long D, int sms);
 
 // sector-restricted basis
-int sector_tiles(long long dim);
+int sector_tiles(long long dim, int prec);
+// true when the sector update finishes the norms itself (no reduction launch)
+bool sector_in_smem(long long dim, int prec);
 int launch_sector_pool(const PoolView& p, const uint32_t* sq, const SectorSpec* sect, long long dim, int* scol,
                        signed char* ssgn, unsigned long long* bad, int sms, cudaStream_t s);
 int launch_taylor5_sector(const PoolView& p, long long n_states, int prec, void* psi, const int* k,
                           const double* theta, int k_fixed, double theta_fixed, const DevStep* gate,
-                          double* partials, cudaStream_t s);
+                          double* partials, double* norm2, double* step_norm2, cudaStream_t s);
 int launch_sector_gradients(const PoolView& p, const double2* w, const void* psi, int prec, const DevStep* step,
                             double* g, cudaStream_t s);
 int launch_apply_twice_sector(const PoolView& p, const DevStep* step, const void* psi, int prec, double2* u1,
