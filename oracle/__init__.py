@@ -18,6 +18,9 @@ Modules, in the order of the paper's pipeline (Sec. III-D, steps 1-4):
 * ``evolve``   -- the Taylor-5 chain of Eqs. (6)-(8) and exact exponentials.
 * ``adapt``    -- energy (Eq. (1)), pool gradients (Eq. (5)), operator
   selection, line search and one ADAPT iteration (Sec. III-D step 3).
+* ``families`` -- commuting-family partition of the pool (Sec. III-F,
+  Algorithm 1): non-commutativity graph (full commutator or qubit-wise)
+  and the largest-first greedy colouring.
 * ``sector``   -- the same operators restricted to a fixed (n_alpha,
   n_beta) subspace (a variant of the paper's 2^N formulation, not part of
   it): colexicographic ranking, basis, restriction, embedding.
