@@ -312,6 +312,7 @@ def run_ours(args, rank, world, local_rank):
         extra["spmv"] = measure_spmv(tq, ctx, args.spmv_qubits)
         extra["trajectories"] = measure_trajectories(tq, ctx, args.traj)
         extra["sector"] = measure_sector(tq, ctx)
+        extra["families"] = measure_families(tq)
         if args.serve_seconds > 0:
             extra["serving"] = measure_serving(tq, local_rank, args.serve_seconds, args.serve_rate)
     out = None
@@ -488,6 +489,16 @@ def measure_sector(tq, ctx, n_states=65536, reps=20):
         out[f"energy_{nq_}q"] = {"dim": ham.dim, "nnz": ham.nnz, "ms_per_energy": t / nl}
     ctx.set_spmv_schedule(32)
     return out
+
+
+def measure_families(tq):
+    """Algorithm 1 (commuting families) on the 18-qubit pool, both relations (host)."""
+    out = {}
+    for name, mode in (("full", tq.TQ_COMMUTE_FULL), ("qubit_wise", tq.TQ_COMMUTE_QWC)):
+        t0 = time.perf_counter()
+        fam, _, k = tq.pool_families_host(9, 8, tq.TQ_BK, mode)
+        out[name] = {"pool_size": int(fam.size), "families": k, "ms": 1e3 * (time.perf_counter() - t0)}
+    return {"workload": "pool of 9 orbitals, 8 electrons, BK (560 generators)", **out}
 
 
 def measure_serving(tq, device, seconds, rate):

@@ -229,6 +229,28 @@ int tq_state_data(const tq_state* st, void** dev_ptr, int* n_qubits, int* prec);
 int tq_state_set_hf(tq_state* st, int n_electrons, int mapping, void* stream);
 int tq_state_free(tq_state* st);
 
+/* ----------------------------------------------------- commuting families */
+/* Sec. III-F, Algorithm 1: partition of the pool into families of mutually
+ * commuting generators by a largest-first greedy colouring of the
+ * non-commutativity graph (vertices by descending degree, ties by pool
+ * index; each joins the lowest-indexed family holding none of its
+ * neighbours, else opens a new one).  The paper names the relation two
+ * ways; `mode` picks one:
+ *   TQ_COMMUTE_FULL: an edge where [A_i, A_j] != 0 as operators (exact:
+ *     the commutator's Pauli expansion has dyadic coefficients);
+ *   TQ_COMMUTE_QWC:  an edge unless every Pauli string of A_i commutes
+ *     qubit-wise with every string of A_j.
+ * Outputs (host arrays of M = pool size, any may be NULL): family[k] in
+ * [0, n_families); order = pool indices family by family, ascending inside
+ * a family (the family-contiguous layout of the pool).  Host only: the
+ * _host variant builds the pool's strings itself (no device, no context);
+ * TQ_EINVAL if capacity < M or mode is unknown. */
+enum { TQ_COMMUTE_FULL = 0, TQ_COMMUTE_QWC = 1 };
+int tq_pool_families(const tq_pool* pool, int mode, int* family, int* order,
+                     int* n_families);
+int tq_pool_families_host(int n_spatial, int n_electrons, int mapping, int mode,
+                          int capacity, int* family, int* order, int* n_families);
+
 /* ---------------------------------------------- sector-restricted basis */
 /* Not in the paper, which works in the full 2^N space: the same operators
  * restricted to the occupation states with n_alpha electrons in the even

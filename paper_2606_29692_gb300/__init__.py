@@ -27,6 +27,7 @@ __all__ = [
     "state_set_hf", "pool_csr", "ham_csr", "lib", "autotune_pair", "energy_noalloc", "Batch", "autotune_spmv", "Server",
     "TQ_REQ_EVOLVE", "TQ_REQ_ENERGY", "TQ_REQ_GRADIENTS", "TQ_SPMV_XELL", "ham_xell",
     "sector_dim", "sector_basis", "build_hamiltonian_sector", "build_pool_sector", "pool_sector_table",
+    "TQ_COMMUTE_FULL", "TQ_COMMUTE_QWC", "pool_families", "pool_families_host",
 ]
 
 
@@ -245,6 +246,31 @@ def build_pool(ctx, n_spatial, n_electrons, mapping=TQ_JW):
     h = C.c_void_p()
     call("tq_build_pool", ctx.handle, n_spatial, n_electrons, mapping, C.byref(h))
     return Pool(ctx, h)
+
+
+# ------------------------------------------------------------ commuting families
+
+TQ_COMMUTE_FULL, TQ_COMMUTE_QWC = 0, 1
+
+
+def pool_families(pool, mode=TQ_COMMUTE_FULL):
+    """Algorithm 1 on a built pool: (family per generator, family-major order, count)."""
+    fam = np.zeros(pool.M, dtype=np.int32)
+    order = np.zeros(pool.M, dtype=np.int32)
+    k = C.c_int()
+    call("tq_pool_families", pool.handle, int(mode), _ptr(fam), _ptr(order), C.byref(k))
+    return fam, order, k.value
+
+
+def pool_families_host(n_spatial, n_electrons, mapping=TQ_JW, mode=TQ_COMMUTE_FULL):
+    """Algorithm 1 on the host, from (n_spatial, n_electrons, mapping); no device needed."""
+    M = len(pool_excitations(n_spatial, n_electrons))
+    fam = np.zeros(M, dtype=np.int32)
+    order = np.zeros(M, dtype=np.int32)
+    k = C.c_int()
+    call("tq_pool_families_host", int(n_spatial), int(n_electrons), mapping, int(mode), M, _ptr(fam), _ptr(order),
+         C.byref(k))
+    return fam, order, k.value
 
 
 # ------------------------------------------------------- sector-restricted basis

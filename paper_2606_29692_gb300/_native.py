@@ -79,6 +79,8 @@ SIGNATURES = {
     "tq_state_data": [vp, P(vp), P(i32), P(i32)],
     "tq_state_set_hf": [vp, i32, i32, vp],
     "tq_state_free": [vp],
+    "tq_pool_families": [vp, i32, vp, vp, P(i32)],
+    "tq_pool_families_host": [i32, i32, i32, i32, i32, vp, vp, P(i32)],
     "tq_sector_dim": [i32, i32, i32, P(i64)],
     "tq_sector_basis": [i32, i32, i32, i32, i64, vp],
     "tq_build_hamiltonian_sector": [vp, i32, vp, vp, f64, i32, i32, i32, i32, P(vp)],

@@ -783,6 +783,49 @@ extern "C" int tq_build_pool_sector(tq_ctx* c, int n_spatial, int n_electrons, i
     API_END
 }
 
+namespace {
+
+void write_families(const std::vector<int>& fam, int* family, int* order, int* n_families) {
+    const int M = (int)fam.size();
+    int K = 0;
+    for (int f : fam) K = std::max(K, f + 1);
+    if (family) std::copy(fam.begin(), fam.end(), family);
+    if (order) {
+        std::vector<int> o(M);
+        for (int v = 0; v < M; ++v) o[v] = v;
+        std::stable_sort(o.begin(), o.end(), [&](int a, int b) { return fam[a] < fam[b]; });
+        std::copy(o.begin(), o.end(), order);
+    }
+    if (n_families) *n_families = K;
+}
+
+}  // namespace
+
+extern "C" int tq_pool_families(const tq_pool* p, int mode, int* family, int* order, int* n_families) {
+    API_BEGIN
+    TQ_REQUIRE(p != nullptr, "pool is null");
+    write_families(pool_families(p->terms, p->nterm, mode), family, order, n_families);
+    API_END
+}
+
+extern "C" int tq_pool_families_host(int n_spatial, int n_electrons, int mapping, int mode, int capacity,
+                                     int* family, int* order, int* n_families) {
+    API_BEGIN
+    check_mapping(mapping);
+    auto ex = excitations(n_spatial, n_electrons);
+    TQ_REQUIRE(capacity >= (int)ex.size(), "capacity is smaller than the pool");
+    std::vector<PauliTerm> terms(8 * ex.size(), PauliTerm{0, 0, 0.0});
+    std::vector<int> nterm(ex.size());
+    for (size_t k = 0; k < ex.size(); ++k) {
+        auto t = pauli_generator(ex[k], 2 * n_spatial, mapping);
+        TQ_REQUIRE(!t.empty() && t.size() <= 8, "generator term count not in 1..8");
+        nterm[k] = (int)t.size();
+        for (size_t j = 0; j < t.size(); ++j) terms[8 * k + j] = t[j];
+    }
+    write_families(pool_families(terms, nterm, mode), family, order, n_families);
+    API_END
+}
+
 extern "C" int tq_pool_sector_table(const tq_pool* p, long long* dim, const int** col, const signed char** sgn) {
     API_BEGIN
     TQ_REQUIRE(p != nullptr, "pool is null");

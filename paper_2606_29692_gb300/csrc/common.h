@@ -80,6 +80,10 @@ struct SectorSpec {
     int binom[16][16];       // C(i, j)
 };
 SectorSpec make_sector_spec(int n, int na, int nb, int mapping);
+
+// Commuting families (Sec. III-F, Algorithm 1): terms holds 8 slots per
+// generator, nterm[k] of them used; returns the family of each generator.
+std::vector<int> pool_families(const std::vector<PauliTerm>& terms, const std::vector<int>& nterm, int mode);
 long long sector_dim(int n, int na, int nb);
 // qubit indices of the sector in rank order
 std::vector<uint32_t> sector_basis(const SectorSpec& s);

@@ -291,6 +291,77 @@ std::vector<uint32_t> sector_basis(const SectorSpec& s) {
     return out;
 }
 
+// ---------------------------------------------------------------------------
+// Commuting families of the pool (Sec. III-F, Algorithm 1).
+
+bool generators_commute(const PauliTerm* a, int na, const PauliTerm* b, int nb, int mode) {
+    if (mode == TQ_COMMUTE_QWC) {
+        // every pair of strings equal or identity on each qubit they share
+        for (int i = 0; i < na; ++i)
+            for (int j = 0; j < nb; ++j) {
+                const uint64_t both = (a[i].x | a[i].z) & (b[j].x | b[j].z);
+                if (((a[i].x ^ b[j].x) | (a[i].z ^ b[j].z)) & both) return false;
+            }
+        return true;
+    }
+    // [A, B] = sum over anticommuting string pairs of
+    //   2 c_a c_b X^xa Z^za X^xb Z^zb = 2 c_a c_b (-1)^{za.xb} X^(xa^xb) Z^(za^zb),
+    // summed per product string; the coefficients are dyadic, so the sums are exact
+    std::vector<PauliTerm> acc;
+    for (int i = 0; i < na; ++i)
+        for (int j = 0; j < nb; ++j) {
+            const int s1 = parity64(a[i].z & b[j].x), s2 = parity64(b[j].z & a[i].x);
+            if (s1 == s2) continue;
+            const uint64_t x = a[i].x ^ b[j].x, z = a[i].z ^ b[j].z;
+            const double v = 2.0 * a[i].c * b[j].c * (s1 ? -1.0 : 1.0);
+            bool found = false;
+            for (auto& t : acc)
+                if (t.x == x && t.z == z) {
+                    t.c += v;
+                    found = true;
+                    break;
+                }
+            if (!found) acc.push_back({x, z, v});
+        }
+    for (const auto& t : acc)
+        if (std::fabs(t.c) > 1e-12) return false;
+    return true;
+}
+
+std::vector<int> greedy_families(int M, const std::vector<std::vector<int>>& nbr) {
+    std::vector<int> order(M);
+    for (int v = 0; v < M; ++v) order[v] = v;
+    // largest degree first; equal degrees keep pool order
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int u, int v) { return nbr[u].size() > nbr[v].size(); });
+    std::vector<int> family(M, -1);
+    int K = 0;
+    std::vector<int> taken;
+    for (int v : order) {
+        taken.assign(K + 1, 0);
+        for (int u : nbr[v])
+            if (family[u] >= 0) taken[family[u]] = 1;
+        int f = 0;
+        while (taken[f]) ++f;           // lowest family with no neighbour (K: a new one)
+        family[v] = f;
+        if (f == K) ++K;
+    }
+    return family;
+}
+
+std::vector<int> pool_families(const std::vector<PauliTerm>& terms, const std::vector<int>& nterm, int mode) {
+    if (mode != TQ_COMMUTE_FULL && mode != TQ_COMMUTE_QWC) throw Error(TQ_EINVAL, "mode must be TQ_COMMUTE_FULL or TQ_COMMUTE_QWC");
+    const int M = (int)nterm.size();
+    std::vector<std::vector<int>> nbr(M);
+    for (int i = 0; i < M; ++i)
+        for (int j = i + 1; j < M; ++j)
+            if (!generators_commute(&terms[8 * i], nterm[i], &terms[8 * j], nterm[j], mode)) {
+                nbr[i].push_back(j);
+                nbr[j].push_back(i);
+            }
+    return greedy_families(M, nbr);
+}
+
 // Factor a generator's sign function (see common.h, SignForm).  The z masks
 // of its 2^m terms form an affine space z0 ^ span(d_1..d_m); when the
 // coefficients are c0 / 2^m * prod_i (-1)^{a_i t_i} (a = coordinates in that

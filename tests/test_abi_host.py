@@ -137,3 +137,29 @@ def test_sector_arguments_are_rejected(tq):
             tq.sector_dim(*args)
     with pytest.raises(tq.TQError):
         tq.sector_basis(4, 2, 2, 7)
+
+
+@pytest.mark.parametrize("mp", [mapping.JW, mapping.BK])
+def test_pool_families_match_oracle(tq, mp):
+    """Algorithm 1 in the library (Pauli-algebra commutators) against the
+    oracle (dense commutators; qubit-wise from Pauli labels): identical
+    families, family-major order, and count."""
+    from oracle import families, pauli
+    cases = [(4, 4, tq.TQ_COMMUTE_FULL), (4, 4, tq.TQ_COMMUTE_QWC), (3, 2, tq.TQ_COMMUTE_FULL),
+             (6, 8, tq.TQ_COMMUTE_QWC), (7, 6, tq.TQ_COMMUTE_QWC)]
+    for n, ne, mode in cases:
+        exc, pool_ps = pauli.pool_pauli(n, ne, mp)
+        if mode == tq.TQ_COMMUTE_FULL:
+            edges = families.full_edges([pauli.pauli_to_csr(p) for p in pool_ps])
+        else:
+            edges = families.qwc_edges([families.labels(p) for p in pool_ps])
+        ref = families.greedy_families(len(exc), edges)
+        fam, order, k = tq.pool_families_host(n, ne, mp, mode)
+        assert fam.tolist() == ref, (n, ne, mode)
+        assert order.tolist() == families.family_order(ref)
+        assert k == max(ref) + 1
+
+
+def test_pool_families_rejects_bad_mode(tq):
+    with pytest.raises(tq.TQError):
+        tq.pool_families_host(4, 4, 0, 5)

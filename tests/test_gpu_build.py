@@ -134,3 +134,12 @@ def test_build_rejects_bad_arguments(ctx):
         tq.build_pool(ctx, 1, 1, 0)        # empty pool
     with pytest.raises(tq.TQError):
         tq.build_hamiltonian(ctx, ints.h, ints.g, float("inf"), 0, tq.TQ_C128)
+
+
+@pytest.mark.parametrize("mode", [tq.TQ_COMMUTE_FULL, tq.TQ_COMMUTE_QWC])
+def test_pool_families_of_a_device_pool_equal_the_host_ones(ctx, mode):
+    for n, ne, mp in [(4, 4, 0), (7, 6, 1)]:
+        pool = tq.build_pool(ctx, n, ne, mp)
+        fam, order, k = tq.pool_families(pool, mode)
+        hfam, horder, hk = tq.pool_families_host(n, ne, mp, mode)
+        assert np.array_equal(fam, hfam) and np.array_equal(order, horder) and k == hk
