@@ -18,6 +18,9 @@ Modules, in the order of the paper's pipeline (Sec. III-D, steps 1-4):
 * ``evolve``   -- the Taylor-5 chain of Eqs. (6)-(8) and exact exponentials.
 * ``adapt``    -- energy (Eq. (1)), pool gradients (Eq. (5)), operator
   selection, line search and one ADAPT iteration (Sec. III-D step 3).
+* ``vqe``      -- ADAPT-VQE with every angle re-optimised (not in the
+  paper): energy of the Taylor-5 product ansatz and its adjoint gradient,
+  BFGS, the outer loop.
 * ``families`` -- commuting-family partition of the pool (Sec. III-F,
   Algorithm 1): non-commutativity graph (full commutator or qubit-wise)
   and the largest-first greedy colouring.
