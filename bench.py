@@ -313,6 +313,7 @@ def run_ours(args, rank, world, local_rank):
         extra["trajectories"] = measure_trajectories(tq, ctx, args.traj)
         extra["sector"] = measure_sector(tq, ctx)
         extra["families"] = measure_families(tq)
+        extra["vqe"] = measure_vqe(tq, ctx)
         if args.serve_seconds > 0:
             extra["serving"] = measure_serving(tq, local_rank, args.serve_seconds, args.serve_rate)
     out = None
@@ -491,6 +492,52 @@ def measure_sector(tq, ctx, n_states=65536, reps=20):
     return out
 
 
+def measure_vqe(tq, ctx, reps=20):
+    """ADAPT-VQE with re-optimised angles: one energy + adjoint gradient of a
+    20-factor ansatz at 14 qubits (c64 and c128; the oracle timed beside it),
+    and a whole run on the 12-qubit workload (BK, eps 1e-3, c128)."""
+    import numpy as np
+
+    import synth
+    out = {}
+    ints, ne = synth.config2()
+    n = ints.n_spatial
+    rng = np.random.default_rng(11)
+    pool = tq.build_pool(ctx, n, ne, 1)
+    ops = rng.integers(0, pool.M, size=20).astype(np.int32)
+    th = rng.normal(0, 0.2, size=20)
+    for name, prec in (("c64", tq.TQ_C64), ("c128", tq.TQ_C128)):
+        ham = tq.build_hamiltonian(ctx, ints.h, ints.g, ints.e_const, 1, prec)
+        st = tq.State(ctx, 2 * n, prec)
+        tq.state_set_hf(st, ne, 1)
+        for _ in range(3):
+            tq.ansatz_energy_grad(ctx, ham, pool, st, ops, th)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            tq.ansatz_energy_grad(ctx, ham, pool, st, ops, th)
+        out[f"energy_grad_20_ops_14q_{name}_ms"] = 1e3 * (time.perf_counter() - t0) / reps
+    # the oracle on the same 20-factor evaluation (one host thread)
+    from oracle import adapt as oadapt, vqe as ovqe
+    sysm = oadapt.build_system(ints, ne, 1)
+    psi0 = oadapt.hf_state(2 * n, ne, 1)
+    t0 = time.perf_counter()
+    ovqe.energy_and_gradient(sysm, list(ops), th, psi0)
+    out["oracle_energy_grad_20_ops_14q_ms"] = 1e3 * (time.perf_counter() - t0)
+    # a whole run
+    ints1, ne1 = synth.config1()
+    ham = tq.build_hamiltonian(ctx, ints1.h, ints1.g, ints1.e_const, 1, tq.TQ_C128)
+    pool1 = tq.build_pool(ctx, ints1.n_spatial, ne1, 1)
+    st = tq.State(ctx, 2 * ints1.n_spatial, tq.TQ_C128)
+    tq.state_set_hf(st, ne1, 1)
+    t0 = time.perf_counter()
+    ops1, th1, en1 = tq.adapt_vqe(ctx, ham, pool1, st, 1e-3, max_ops=20, gtol=1e-6)
+    out["adapt_vqe_12q"] = {"seconds": time.perf_counter() - t0, "operators": int(ops1.size),
+                            "final_energy": float(en1[-1]) if en1.size else None}
+    out["workload"] = ("energy + adjoint gradient of a 20-factor Taylor-5 ansatz of the 14-qubit BK "
+                       "Hamiltonian from HF; ADAPT-VQE (BFGS on every angle) on the 12-qubit BK workload")
+    return out
+
+
 def measure_families(tq):
     """Algorithm 1 (commuting families) on the 18-qubit pool, both relations (host)."""
     out = {}
@@ -620,7 +667,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the SpMV, trajectory-batch and request-loop measurements")
-    ap.add_argument("--section", choices=["spmv", "trajectories", "serving", "sector"], default=None,
+    ap.add_argument("--section", choices=["spmv", "trajectories", "serving", "sector", "vqe"], default=None,
                     help="run one secondary measurement alone and print its JSON (profiling)")
     ap.add_argument("--spmv-qubits", type=int, default=18)
     ap.add_argument("--traj", type=int, default=256)
@@ -655,6 +702,8 @@ def main():
             print(json.dumps(measure_trajectories(tq, ctx, args.traj)))
         elif args.section == "sector":
             print(json.dumps(measure_sector(tq, ctx)))
+        elif args.section == "vqe":
+            print(json.dumps(measure_vqe(tq, ctx)))
         else:
             print(json.dumps(measure_serving(tq, local_rank, args.serve_seconds, args.serve_rate)))
         return 0

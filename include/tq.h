@@ -229,6 +229,39 @@ int tq_state_data(const tq_state* st, void** dev_ptr, int* n_qubits, int* prec);
 int tq_state_set_hf(tq_state* st, int n_electrons, int mapping, void* stream);
 int tq_state_free(tq_state* st);
 
+/* -------------------------------------- ADAPT-VQE with re-optimised angles */
+/* Not in the paper, whose loop (Sec. III-D) sets only the newest angle: the
+ * standard ADAPT-VQE form of that loop on the same Taylor-5 factors
+ * U_j(t) = sum_{m<=5} (t A_j)^m / m! of Eqs. (6)-(8).
+ *
+ * tq_ansatz_energy_grad: for psi(theta) = U_n(theta_n) ... U_1(theta_1) psi0
+ * (no renormalisation), E = Re<psi|H|psi>/<psi|psi> (Eq. (1)) into *E and,
+ * if grad is not NULL, dE/dtheta_j into grad[0 .. n_ops-1], exact for the
+ * product (one forward sweep that keeps the n_ops + 1 states in context
+ * scratch, one adjoint sweep: chi = (H - E) psi, grad_j =
+ * 2 Re<chi_j | U_j'(theta_j) phi_{j-1}> / <psi|psi>, chi_{j-1} =
+ * U_j(-theta_j) chi_j).  ops, thetas, E, grad: host arrays; psi0 (not
+ * modified) and psi_out (optional, receives psi(theta)) are states of the
+ * pool's space (full or sector).  Synchronises the stream.  TQ_EINVAL for
+ * an op index out of range, a non-finite angle or mismatched spaces.
+ *
+ * tq_adapt_vqe: from psi0, repeat up to max_ops times: pool gradients at
+ * psi(theta), the operator with the largest |g| (tie rule of
+ * tq_adapt_step), stop if max|g| < eps, else append it with angle 0 and
+ * re-optimise every angle by BFGS (inverse-Hessian update, backtracking
+ * line search; stop at max |dE/dtheta| < gtol or max_iter iterations).
+ * Writes n_ops and ops_out, thetas_out, energies_out (host arrays of
+ * max_ops; energies_out[i] = the optimised energy with i + 1 operators),
+ * and psi(theta) into psi_out if not NULL.  Runs on the legacy stream. */
+int tq_ansatz_energy_grad(tq_ctx* ctx, const tq_ham* ham, const tq_pool* pool,
+                          const tq_state* psi0, int n_ops, const int* ops,
+                          const double* thetas, double* E, double* grad,
+                          tq_state* psi_out, void* stream);
+int tq_adapt_vqe(tq_ctx* ctx, const tq_ham* ham, const tq_pool* pool,
+                 const tq_state* psi0, double eps, int max_ops, double gtol,
+                 int max_iter, int* n_ops, int* ops_out, double* thetas_out,
+                 double* energies_out, tq_state* psi_out);
+
 /* ----------------------------------------------------- commuting families */
 /* Sec. III-F, Algorithm 1: partition of the pool into families of mutually
  * commuting generators by a largest-first greedy colouring of the

@@ -28,6 +28,7 @@ __all__ = [
     "TQ_REQ_EVOLVE", "TQ_REQ_ENERGY", "TQ_REQ_GRADIENTS", "TQ_SPMV_XELL", "ham_xell",
     "sector_dim", "sector_basis", "build_hamiltonian_sector", "build_pool_sector", "pool_sector_table",
     "TQ_COMMUTE_FULL", "TQ_COMMUTE_QWC", "pool_families", "pool_families_host",
+    "ansatz_energy_grad", "adapt_vqe",
 ]
 
 
@@ -246,6 +247,33 @@ def build_pool(ctx, n_spatial, n_electrons, mapping=TQ_JW):
     h = C.c_void_p()
     call("tq_build_pool", ctx.handle, n_spatial, n_electrons, mapping, C.byref(h))
     return Pool(ctx, h)
+
+
+# ----------------------------------------------- ADAPT-VQE with re-optimised angles
+
+def ansatz_energy_grad(ctx, ham, pool, psi0, ops, thetas, psi_out=None, gradient=True, stream=None):
+    """E and dE/dtheta of the Taylor-5 product ansatz U_n ... U_1 psi0."""
+    ops = np.ascontiguousarray(ops, dtype=np.int32)
+    th = np.ascontiguousarray(thetas, dtype=np.float64)
+    E = C.c_double()
+    g = np.zeros(max(ops.size, 1), dtype=np.float64)
+    call("tq_ansatz_energy_grad", ctx.handle, ham.handle, pool.handle, psi0.handle, int(ops.size),
+         _ptr(ops) if ops.size else None, _ptr(th) if th.size else None, C.byref(E),
+         _ptr(g) if gradient else None, psi_out.handle if psi_out is not None else None, _stream(stream))
+    return E.value, g[: ops.size]
+
+
+def adapt_vqe(ctx, ham, pool, psi0, eps=1e-3, max_ops=20, gtol=1e-8, max_iter=200, psi_out=None):
+    """ADAPT-VQE with every angle re-optimised: (ops, thetas, energies)."""
+    n = C.c_int()
+    ops = np.zeros(max(max_ops, 1), dtype=np.int32)
+    th = np.zeros(max(max_ops, 1), dtype=np.float64)
+    en = np.zeros(max(max_ops, 1), dtype=np.float64)
+    call("tq_adapt_vqe", ctx.handle, ham.handle, pool.handle, psi0.handle, float(eps), int(max_ops), float(gtol),
+         int(max_iter), C.byref(n), _ptr(ops), _ptr(th), _ptr(en),
+         psi_out.handle if psi_out is not None else None)
+    k = n.value
+    return ops[:k].copy(), th[:k].copy(), en[:k].copy()
 
 
 # ------------------------------------------------------------ commuting families

@@ -241,6 +241,14 @@ int launch_spmv_c128_gated(const HamView& h, const double2* x, double2* y,
 int energy_grid(long long D, int sms);
 
 // sector-restricted basis
+// ADAPT-VQE adjoint sweep: grad_out = 2 Re<chi | A_k T4(theta A_k) phi> / e_den,
+// with A T4(theta A) = c4 A - s4 P on A's support (A^2 = -P there),
+// c4 = 1 - theta^2/2 + theta^4/24, s4 = theta - theta^3/6; and chi = w - E psi
+int launch_ansatz_dot(const PoolView& p, int k, double c4, double s4, const void* chi, const void* phi, int prec,
+                      long long D, double* partials, unsigned* ticket, const DevStep* step, double* grad_out,
+                      int sms, cudaStream_t s);
+int launch_residual(const double2* w, const void* psi, void* chi, int prec, long long D, const DevStep* step,
+                    cudaStream_t s);
 int sector_tiles(long long dim, int prec);
 // true when the sector update finishes the norms itself (no reduction launch)
 bool sector_in_smem(long long dim, int prec);
@@ -273,8 +281,9 @@ struct tq_ctx {
     std::vector<tq_trace_rec> trace;      // recorded, not yet reported
     std::vector<cudaEvent_t> event_pool;  // reusable events
     // device scratch, grown on demand
-    void* scratch[10] = {nullptr};
-    size_t scratch_bytes[10] = {0};
+    static constexpr int kScratch = 16;
+    void* scratch[kScratch] = {nullptr};
+    size_t scratch_bytes[kScratch] = {0};
     tq::DevStep* step = nullptr;      // device
     unsigned* tickets = nullptr;      // device, zero between calls
     size_t tickets_n = 0;
