@@ -24,6 +24,8 @@ Modules, in the order of the paper's pipeline (Sec. III-D, steps 1-4):
 * ``families`` -- commuting-family partition of the pool (Sec. III-F,
   Algorithm 1): non-commutativity graph (full commutator or qubit-wise)
   and the largest-first greedy colouring.
+* ``fcidump``  -- the FCIDUMP integral file format (reader and writer),
+  for integrals supplied from outside (the paper's are not available).
 * ``sector``   -- the same operators restricted to a fixed (n_alpha,
   n_beta) subspace (a variant of the paper's 2^N formulation, not part of
   it): colexicographic ranking, basis, restriction, embedding.
