@@ -314,6 +314,7 @@ def run_ours(args, rank, world, local_rank):
         extra["sector"] = measure_sector(tq, ctx)
         extra["families"] = measure_families(tq)
         extra["vqe"] = measure_vqe(tq, ctx)
+        extra["io"] = measure_io(tq, ctx)
         if args.serve_seconds > 0:
             extra["serving"] = measure_serving(tq, local_rank, args.serve_seconds, args.serve_rate)
     out = None
@@ -535,6 +536,33 @@ def measure_vqe(tq, ctx, reps=20):
                             "final_energy": float(en1[-1]) if en1.size else None}
     out["workload"] = ("energy + adjoint gradient of a 20-factor Taylor-5 ansatz of the 14-qubit BK "
                        "Hamiltonian from HF; ADAPT-VQE (BFGS on every angle) on the 12-qubit BK workload")
+    return out
+
+
+def measure_io(tq, ctx):
+    """FCIDUMP read of 13 orbitals and a checkpoint of a 24-qubit complex64 state."""
+    import os
+    import tempfile
+
+    import synth
+    out = {}
+    with tempfile.TemporaryDirectory() as d:
+        ints = synth.integrals(13, 7)
+        path = os.path.join(d, "FCIDUMP")
+        tq.write_fcidump(path, ints.h, ints.g, 0.0, 12)
+        t0 = time.perf_counter()
+        tq.read_fcidump(path)
+        out["fcidump_13_orbitals_read_ms"] = 1e3 * (time.perf_counter() - t0)
+        st = tq.State(ctx, 24, tq.TQ_C64)
+        tq.state_set_hf(st, 12, tq.TQ_BK)
+        sp = os.path.join(d, "state.bin")
+        t0 = time.perf_counter()
+        tq.state_save(st, sp)
+        t1 = time.perf_counter()
+        tq.state_load(st, sp)
+        t2 = time.perf_counter()
+        mb = (1 << 24) * 8 / 1e6
+        out["checkpoint_24q_c64"] = {"mbytes": mb, "save_gbs": mb / 1e3 / (t1 - t0), "load_gbs": mb / 1e3 / (t2 - t1)}
     return out
 
 

@@ -229,6 +229,35 @@ int tq_state_data(const tq_state* st, void** dev_ptr, int* n_qubits, int* prec);
 int tq_state_set_hf(tq_state* st, int n_electrons, int mapping, void* stream);
 int tq_state_free(tq_state* st);
 
+/* ------------------------------------------------- integrals and checkpoints */
+/* FCIDUMP integral files (host only; the paper's molecular integrals are
+ * not available, so real ones are supplied this way).  Format: a namelist
+ * header "&FCI NORB=n, NELEC=ne, MS2=m, ... &END" (or "/"), then lines
+ * "value i j k l" with 1-based orbitals: all non-zero -> chemist (ij|kl),
+ * k = l = 0 -> h_ij, all zero -> core energy, other patterns skipped; each
+ * (ij|kl) line fills its 8 real-orbital symmetry partners and each h_ij
+ * line also h_ji; a Fortran D exponent is accepted.
+ * tq_read_fcidump: header values into n_spatial, n_electrons, ms2 (any may
+ * be NULL); with h1 (n*n, row-major) and/or g2 (n^4, [((p*n+q)*n+r)*n+s] =
+ * (pq|rs), the layout tq_build_hamiltonian takes) and/or e_core non-NULL,
+ * also the integrals (entries not in the file are 0; capacity_n >= n).
+ * TQ_EINVAL: unreadable file, missing header key, NORB outside [1, 15],
+ * an orbital index above NORB, a malformed line.
+ * tq_write_fcidump: the symmetry-unique entries with |v| > tol (i >= j,
+ * k >= l, pair(ij) >= pair(kl); then h_ij with i >= j; then the core
+ * energy), %.16E: a read-back is exact. */
+int tq_read_fcidump(const char* path, int* n_spatial, int* n_electrons, int* ms2,
+                    double* e_core, double* h1, double* g2, int capacity_n);
+int tq_write_fcidump(const char* path, int n_spatial, int n_electrons, int ms2,
+                     const double* h1, const double* g2, double e_core, double tol);
+/* State checkpoints: a 40-byte header (magic "TQSTATE1", int32 precision,
+ * qubits, sector flag, n_alpha, n_beta, 0, int64 amplitude count) and the
+ * amplitudes as stored on the device.  tq_state_load requires the header
+ * to match the target state (TQ_EINVAL otherwise).  Both synchronise the
+ * device. */
+int tq_state_save(const tq_state* st, const char* path);
+int tq_state_load(tq_state* st, const char* path);
+
 /* -------------------------------------- ADAPT-VQE with re-optimised angles */
 /* Not in the paper, whose loop (Sec. III-D) sets only the newest angle: the
  * standard ADAPT-VQE form of that loop on the same Taylor-5 factors

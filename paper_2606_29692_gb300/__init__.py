@@ -28,7 +28,7 @@ __all__ = [
     "TQ_REQ_EVOLVE", "TQ_REQ_ENERGY", "TQ_REQ_GRADIENTS", "TQ_SPMV_XELL", "ham_xell",
     "sector_dim", "sector_basis", "build_hamiltonian_sector", "build_pool_sector", "pool_sector_table",
     "TQ_COMMUTE_FULL", "TQ_COMMUTE_QWC", "pool_families", "pool_families_host",
-    "ansatz_energy_grad", "adapt_vqe",
+    "ansatz_energy_grad", "adapt_vqe", "read_fcidump", "write_fcidump", "state_save", "state_load", "replay",
 ]
 
 
@@ -247,6 +247,50 @@ def build_pool(ctx, n_spatial, n_electrons, mapping=TQ_JW):
     h = C.c_void_p()
     call("tq_build_pool", ctx.handle, n_spatial, n_electrons, mapping, C.byref(h))
     return Pool(ctx, h)
+
+
+# ------------------------------------------------- integrals and checkpoints
+
+class FcidumpIntegrals:
+    """Integrals read from a FCIDUMP file: h (n, n), g (n, n, n, n) chemist
+    (pq|rs), e_const (core energy), n_spatial, n_electrons, ms2."""
+
+    def __init__(self, h, g, e_const, n_electrons, ms2):
+        self.h, self.g, self.e_const = h, g, e_const
+        self.n_spatial = h.shape[0]
+        self.n_electrons, self.ms2 = n_electrons, ms2
+
+
+def read_fcidump(path):
+    n, ne, ms2 = C.c_int(), C.c_int(), C.c_int()
+    call("tq_read_fcidump", str(path).encode(), C.byref(n), C.byref(ne), C.byref(ms2), None, None, None, 0)
+    h = np.zeros((n.value, n.value))
+    g = np.zeros((n.value,) * 4)
+    e = C.c_double()
+    call("tq_read_fcidump", str(path).encode(), None, None, None, C.byref(e), _ptr(h), _ptr(g), n.value)
+    return FcidumpIntegrals(h, g, e.value, ne.value, ms2.value)
+
+
+def write_fcidump(path, h, g, e_const, n_electrons, ms2=0, tol=0.0):
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    call("tq_write_fcidump", str(path).encode(), h.shape[0], int(n_electrons), int(ms2), _ptr(h), _ptr(g),
+         float(e_const), float(tol))
+
+
+def state_save(state, path):
+    call("tq_state_save", state.handle, str(path).encode())
+
+
+def state_load(state, path):
+    call("tq_state_load", state.handle, str(path).encode())
+
+
+def replay(ctx, pool, state, ops, thetas, renormalize=True, stream=None):
+    """Re-apply a recorded sequence of (operator, angle) updates to ``state``
+    (e.g. from Hartree-Fock), as the ADAPT step applied them."""
+    for k, th in zip(ops, thetas):
+        evolve_taylor5(ctx, pool, int(k), float(th), state, renormalize=renormalize, stream=stream)
 
 
 # ----------------------------------------------- ADAPT-VQE with re-optimised angles

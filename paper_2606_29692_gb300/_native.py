@@ -79,6 +79,10 @@ SIGNATURES = {
     "tq_state_data": [vp, P(vp), P(i32), P(i32)],
     "tq_state_set_hf": [vp, i32, i32, vp],
     "tq_state_free": [vp],
+    "tq_read_fcidump": [C.c_char_p, P(i32), P(i32), P(i32), P(f64), vp, vp, i32],
+    "tq_write_fcidump": [C.c_char_p, i32, i32, i32, vp, vp, f64, f64],
+    "tq_state_save": [vp, C.c_char_p],
+    "tq_state_load": [vp, C.c_char_p],
     "tq_ansatz_energy_grad": [vp, vp, vp, vp, i32, vp, vp, P(f64), vp, vp, vp],
     "tq_adapt_vqe": [vp, vp, vp, vp, f64, i32, f64, i32, P(i32), vp, vp, vp, vp],
     "tq_pool_families": [vp, i32, vp, vp, P(i32)],

@@ -163,3 +163,36 @@ def test_pool_families_match_oracle(tq, mp):
 def test_pool_families_rejects_bad_mode(tq):
     with pytest.raises(tq.TQError):
         tq.pool_families_host(4, 4, 0, 5)
+
+
+def test_fcidump_reader_matches_the_golden_expansion(tq):
+    from test_oracle_fcidump import GOLD, expected_2orb
+    h, g, meta = expected_2orb()
+    ints = tq.read_fcidump(os.path.join(GOLD, "fcidump_2orb.txt"))
+    assert np.array_equal(ints.h, h) and np.array_equal(ints.g, g)
+    assert ints.e_const == meta["e"] and ints.n_electrons == meta["nelec"] and ints.ms2 == meta["ms2"]
+
+
+def test_fcidump_round_trips_with_the_oracle(tq, tmp_path):
+    from oracle import fcidump
+    for n, seed in [(3, 6), (6, 1), (9, 2012)]:
+        ints = synth.integrals(n, seed)
+        a = str(tmp_path / "oracle.txt")
+        fcidump.write(a, ints.h, ints.g, 0.375, 2 * (n // 2), ms2=0)
+        r = tq.read_fcidump(a)                                   # library reads the oracle's file
+        assert np.array_equal(r.h, ints.h) and np.array_equal(r.g, ints.g) and r.e_const == 0.375
+        b = str(tmp_path / "lib.txt")
+        tq.write_fcidump(b, ints.h, ints.g, -1.5, 2 * (n // 2))
+        h, g, e, nn, ne, ms2 = fcidump.read(b)                   # oracle reads the library's file
+        assert np.array_equal(h, ints.h) and np.array_equal(g, ints.g) and e == -1.5 and nn == n
+
+
+def test_fcidump_errors(tq, tmp_path):
+    bad = tmp_path / "bad.txt"
+    for text in ["no header at all\n", " &FCI NELEC=2, &END\n 1.0 1 1 1 1\n",
+                 " &FCI NORB=2,NELEC=2 &END\n 1.0 3 1 1 1\n", " &FCI NORB=2,NELEC=2 &END\n 1.0 1 x 1 1\n"]:
+        bad.write_text(text)
+        with pytest.raises(tq.TQError):
+            tq.read_fcidump(str(bad))
+    with pytest.raises(tq.TQError):
+        tq.read_fcidump(str(tmp_path / "missing.txt"))
