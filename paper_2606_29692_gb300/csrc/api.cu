@@ -469,6 +469,7 @@ tq_ham* make_hamiltonian(tq_ctx* c, int n_spatial, const double* h1, const doubl
     auto* h = new tq_ham();
     try {
         h->ctx = c;
+        h->device = c->device;
         h->n_spatial = n_spatial;
         h->nq = 2 * n_spatial;
         h->prec = prec;
@@ -623,9 +624,10 @@ extern "C" int tq_ham_xell(const tq_ham* h, long long* n_blocks, long long* n_pa
 
 extern "C" int tq_ham_free(tq_ham* h) {
     if (!h) return TQ_OK;
-    if (h->ctx) cudaSetDevice(h->ctx->device);
+    cudaSetDevice(h->device);
     free_all(h->allocs);
     delete h;
+    (void)cudaGetLastError();   // a failure while freeing is not reported to later calls
     return TQ_OK;
 }
 
@@ -639,6 +641,7 @@ tq_pool* make_pool(tq_ctx* c, int n_spatial, int n_electrons, int mapping) {
     auto* p = new tq_pool();
     try {
         p->ctx = c;
+        p->device = c->device;
         p->n_spatial = n_spatial;
         p->n_electrons = n_electrons;
         p->nq = 2 * n_spatial;
@@ -896,9 +899,10 @@ extern "C" int tq_pool_csr(tq_ctx* c, tq_pool* p, int k, int prec, const int** r
 
 extern "C" int tq_pool_free(tq_pool* p) {
     if (!p) return TQ_OK;
-    if (p->ctx) cudaSetDevice(p->ctx->device);
+    cudaSetDevice(p->device);
     free_all(p->allocs);
     delete p;
+    (void)cudaGetLastError();   // a failure while freeing is not reported to later calls
     return TQ_OK;
 }
 
@@ -913,6 +917,7 @@ extern "C" int tq_state_create(tq_ctx* c, int n_qubits, int prec, tq_state** out
     set_device(c);
     auto* s = new tq_state();
     s->ctx = c;
+    s->device = c->device;
     s->nq = n_qubits;
     s->prec = prec;
     s->D = 1ll << n_qubits;
@@ -937,6 +942,7 @@ extern "C" int tq_state_wrap(tq_ctx* c, int n_qubits, int prec, void* dev_ptr, t
     TQ_REQUIRE(((uintptr_t)dev_ptr & 15u) == 0, "state pointer must be 16-byte aligned");
     auto* s = new tq_state();
     s->ctx = c;
+    s->device = c->device;
     s->nq = n_qubits;
     s->prec = prec;
     s->D = 1ll << n_qubits;
@@ -952,6 +958,7 @@ tq_state* new_sector_state(tq_ctx* c, int n_spatial, int n_alpha, int n_beta, in
     const SectorSpec sp = make_sector_spec(n_spatial, n_alpha, n_beta, TQ_JW);
     auto* s = new tq_state();
     s->ctx = c;
+    s->device = c->device;
     s->nq = 2 * n_spatial;
     s->prec = prec;
     s->D = sector_dim(sp.n, sp.na, sp.nb);
@@ -1031,10 +1038,11 @@ extern "C" int tq_state_set_hf(tq_state* s, int n_electrons, int mapping, void* 
 extern "C" int tq_state_free(tq_state* s) {
     if (!s) return TQ_OK;
     if (s->owned && s->data) {
-        cudaSetDevice(s->ctx->device);
+        cudaSetDevice(s->device);
         cudaFree(s->data);
     }
     delete s;
+    (void)cudaGetLastError();   // a failure while freeing is not reported to later calls
     return TQ_OK;
 }
 

@@ -286,6 +286,7 @@ int resident_grid(K kernel, int bs, int sms) {
 using namespace tq;
 
 struct tq_batch {
+    int device = 0;     // the context's device, kept for freeing after the context
     tq_ctx* ctx = nullptr;
     int n = 0, prec = 0, max_len = 0, lpr = 32;
     double eps = 0.0;
@@ -417,6 +418,7 @@ extern "C" int tq_batch_create(tq_ctx* c, int n_traj, tq_ham* const* hams, tq_po
     auto* b = new tq_batch();
     try {
         b->ctx = c;
+        b->device = c->device;
         b->n = n_traj;
         b->eps = eps;
         b->prec = hams[0]->prec;
@@ -629,11 +631,12 @@ extern "C" int tq_batch_state(const tq_batch* b, int t, void** dev_ptr, int* n_q
 
 extern "C" int tq_batch_free(tq_batch* b) {
     if (!b) return TQ_OK;
-    if (b->ctx) cudaSetDevice(b->ctx->device);
+    cudaSetDevice(b->device);
     cudaDeviceSynchronize();
     drop_graph(b);
     if (b->cap) cudaStreamDestroy(b->cap);
     for (void* p : b->allocs) cudaFree(p);
     delete b;
+    (void)cudaGetLastError();   // a failure while freeing is not reported to later calls
     return TQ_OK;
 }

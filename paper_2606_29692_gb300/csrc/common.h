@@ -292,6 +292,7 @@ struct tq_ctx {
 
 struct tq_ham {
     tq_ctx* ctx = nullptr;
+    int device = 0;            // the context's device, kept for freeing after the context
     int n_spatial = 0, nq = 0, prec = 0, mapping = 0;
     int sector = 0, n_alpha = 0, n_beta = 0;   // sector-restricted basis
     long long D = 0, nnz = 0, n_pauli = 0, n_amb = 0;
@@ -303,6 +304,7 @@ struct tq_ham {
 
 struct tq_pool {
     tq_ctx* ctx = nullptr;
+    int device = 0;            // the context's device, kept for freeing after the context
     int n_spatial = 0, n_electrons = 0, nq = 0, mapping = 0, M = 0;
     int sector = 0, n_alpha = 0, n_beta = 0;   // sector-restricted basis
     std::vector<int> idx4;
@@ -320,6 +322,7 @@ struct tq_pool {
 
 struct tq_state {
     tq_ctx* ctx = nullptr;
+    int device = 0;            // the context's device, kept for freeing after the context
     int nq = 0, prec = 0, owned = 0;
     int sector = 0, n_spatial = 0, n_alpha = 0, n_beta = 0;   // sector-restricted basis
     long long D = 0;

@@ -60,8 +60,11 @@ inline void check_launch(tq_ctx* c, int n) {
 }
 
 // Launch through `f` (which returns its launch count), traced under `name`.
+// A launch error left pending by an unrelated earlier call (ours or another
+// library's) is cleared first, so the check below reports this launch only.
 template <typename F>
 void launch(tq_ctx* c, const char* name, cudaStream_t s, F&& f) {
+    (void)cudaGetLastError();
     Traced t(c, name, s);
     const int n = f();
     if (n < 0) throw Error(TQ_EINVAL, std::string(name) + ": problem too large for one launch");

@@ -176,7 +176,7 @@ static_assert(sizeof(StateHeader) == 40, "state header layout");
 extern "C" int tq_state_save(const tq_state* s, const char* path) {
     API_BEGIN
     TQ_REQUIRE(s && path, "null argument");
-    cudaSetDevice(s->ctx->device);
+    TQ_CUDA(cudaSetDevice(s->device));
     const size_t bytes = (size_t)s->D * (s->prec == TQ_C128 ? 16 : 8);
     std::vector<unsigned char> buf(bytes);
     TQ_CUDA(cudaDeviceSynchronize());
@@ -214,7 +214,7 @@ extern "C" int tq_state_load(tq_state* s, const char* path) {
     const bool ok = std::fread(buf.data(), 1, bytes, f) == bytes;
     std::fclose(f);
     TQ_REQUIRE(ok, "checkpoint is truncated");
-    cudaSetDevice(s->ctx->device);
+    TQ_CUDA(cudaSetDevice(s->device));
     TQ_CUDA(cudaDeviceSynchronize());
     TQ_CUDA(cudaMemcpy(s->data, buf.data(), bytes, cudaMemcpyHostToDevice));
     API_END

@@ -243,6 +243,7 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 using namespace tq;
 
 struct tq_server {
+    int device = 0;     // the context's device, kept for freeing after the context
     tq_ctx* ctx = nullptr;
     int prec = TQ_C64;
     size_t budget = 0, states_bytes = 0;
@@ -530,6 +531,7 @@ extern "C" int tq_server_create(tq_ctx* c, int prec, size_t hbm_budget, int max_
     auto* s = new tq_server();
     try {
         s->ctx = c;
+        s->device = c->device;
         s->prec = prec;
         s->budget = hbm_budget;
         s->max_batch = max_batch;
@@ -687,7 +689,7 @@ extern "C" int tq_server_stop(tq_server* s) {
 extern "C" int tq_server_free(tq_server* s) {
     if (!s) return TQ_OK;
     tq_server_stop(s);
-    cudaSetDevice(s->ctx->device);
+    cudaSetDevice(s->device);
     cudaDeviceSynchronize();
     for (auto& tk : s->tick) {
         if (tk.h) cudaFreeHost(tk.h);
@@ -696,5 +698,6 @@ extern "C" int tq_server_free(tq_server* s) {
     if (s->stream) cudaStreamDestroy(s->stream);
     for (void* p : s->allocs) cudaFree(p);
     delete s;
+    (void)cudaGetLastError();   // a failure while freeing is not reported to later calls
     return TQ_OK;
 }
