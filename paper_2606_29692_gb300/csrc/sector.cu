@@ -46,7 +46,7 @@ __global__ void k_sector_pool(PoolView p, const uint32_t* sq, const SectorSpec* 
 
 constexpr int SECT_ROWS_PER_LANE = 4;
 constexpr int SECT_WARP_ROWS = 32 * SECT_ROWS_PER_LANE;
-constexpr int SECT_SMEM_THREADS = 256;
+constexpr int SECT_SMEM_THREADS = 128;
 constexpr size_t SECT_SMEM_MAX = 48 * 1024;    // states up to this size go through shared memory
 
 struct SectOp {
@@ -89,7 +89,7 @@ __device__ __forceinline__ void sector_pair(V& vr, V& vc, T c5, T s5, int sg) {
 // finishes the state's float64 norm (warp partials in a fixed order) into
 // norm2[b] and/or *step_norm2, so no reduction launch follows.
 template <typename T>
-__global__ void __launch_bounds__(SECT_SMEM_THREADS, 6)
+__global__ void __launch_bounds__(SECT_SMEM_THREADS, 10)
 k_taylor5_sector_smem(PoolView p, typename C2<T>::type* psi, const int* ks, const double* thetas, int k_fixed,
                       double theta_fixed, const DevStep* gate, double* norm2, double* step_norm2) {
     using V = typename C2<T>::type;
@@ -115,7 +115,7 @@ k_taylor5_sector_smem(PoolView p, typename C2<T>::type* psi, const int* ks, cons
     const int* __restrict__ col = p.scol + (long long)(kok ? k : 0) * dim;
     const signed char* __restrict__ sgn = p.ssgn + (long long)(kok ? k : 0) * dim;
     // the state and this thread's table entries load together
-    constexpr int J = 6;
+    constexpr int J = 10;
     int cj[J], sj[J];
 #pragma unroll
     for (int j = 0; j < J; ++j) {
