@@ -309,6 +309,7 @@ def run_ours(args, rank, world, local_rank):
     extra = {}
     if rank == 0 and not args.headline_only:
         extra["fp64_single_instance"] = measure_fp64_single(tq, ctx, pool, k, th)
+        extra["c128_batched"] = measure_c128_batched(tq, ctx, pool)
         extra["spmv"] = measure_spmv(tq, ctx, args.spmv_qubits)
         extra["trajectories"] = measure_trajectories(tq, ctx, args.traj)
         extra["sector"] = measure_sector(tq, ctx)
@@ -342,6 +343,39 @@ def run_ours(args, rank, world, local_rank):
         }
         out.update(extra)
     return out
+
+
+def measure_c128_batched(tq, ctx, pool, n_states=4096, reps=20):
+    """The complex128 form of the headline update, batched: n_states 14-qubit
+    states (1 GiB, larger than L2), each its own generator and angle."""
+    import numpy as np
+    import torch
+
+    import synth
+    D = 1 << NQ
+    rng = np.random.default_rng(synth.SEED_T5_BATCH)
+    k = torch.as_tensor(rng.integers(0, pool.M, size=n_states).astype(np.int32)).cuda()
+    th = torch.as_tensor(rng.normal(0.0, 0.1, size=n_states)).cuda()
+    g = torch.Generator("cuda").manual_seed(6)
+    psi = torch.randn(n_states, D, dtype=torch.complex128, device="cuda", generator=g)
+    psi /= torch.linalg.vector_norm(psi, dim=1, keepdim=True)
+    n2 = torch.zeros(n_states, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        tq.evolve_taylor5_batch(ctx, pool, psi, k, th, n2, prec=tq.TQ_C128)
+    ctx.trace(True)
+    for _ in range(reps):
+        tq.evolve_taylor5_batch(ctx, pool, psi, k, th, n2, prec=tq.TQ_C128)
+    rep = ctx.trace_report()
+    ctx.trace(False)
+    n_l, ms = rep["taylor5_pair"]
+    ms /= n_l
+    nr, nrms = rep.get("norm_reduce", (1, 0.0))
+    peak, _ = peaks()
+    alg = 2.0 * D * 16
+    return {"workload": f"{n_states} complex128 states, 14 qubits, own generator and angle each",
+            "kernel": "k_taylor5_pair<double>", "ms_per_launch": ms, "norm_reduce_ms": nrms / nr,
+            "updates_per_s": n_states / ((ms + nrms / nr) * 1e-3),
+            "achieved_gbs": alg * n_states / (ms * 1e-3) / 1e9, "hbm_frac": alg * n_states / (ms * 1e-3) / 1e9 / peak}
 
 
 def measure_fp64_single(tq, ctx, pool, k, th, reps=2000):
@@ -695,7 +729,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the SpMV, trajectory-batch and request-loop measurements")
-    ap.add_argument("--section", choices=["spmv", "trajectories", "serving", "sector", "vqe"], default=None,
+    ap.add_argument("--section", choices=["spmv", "trajectories", "serving", "sector", "vqe", "c128"], default=None,
                     help="run one secondary measurement alone and print its JSON (profiling)")
     ap.add_argument("--spmv-qubits", type=int, default=18)
     ap.add_argument("--traj", type=int, default=256)
@@ -732,6 +766,10 @@ def main():
             print(json.dumps(measure_sector(tq, ctx)))
         elif args.section == "vqe":
             print(json.dumps(measure_vqe(tq, ctx)))
+        elif args.section == "c128":
+            import synth
+            ints, ne = synth.config2()
+            print(json.dumps(measure_c128_batched(tq, ctx, tq.build_pool(ctx, ints.n_spatial, ne, MAPPING))))
         else:
             print(json.dumps(measure_serving(tq, local_rank, args.serve_seconds, args.serve_rate)))
         return 0

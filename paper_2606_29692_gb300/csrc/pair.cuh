@@ -217,6 +217,24 @@ __device__ __forceinline__ int base_code(const OpRec<T>& o, uint32_t r) {
 // `base` (4 amplitudes per unit), generator `op`, angle theta.  Loads every
 // unit of the thread first, then runs the five-product chains and stores.
 // Returns the thread's float32 (complex64) or float64 sum of |psi'|^2.
+// The same five products and sum in closed form for complex128 pairs whose
+// 2x2 block of A is [[0, s], [-s, 0]], s = +-1 (every pool generator's, on
+// its support): there A^2 = -I, so sum_k (theta A)^k / k! = c5 I + s5 A
+// with c5 = cf0 - cf2 + cf4 and s5 = cf1 - cf3 + cf5; a pair A annihilates
+// keeps psi.  Half the float64 work of the explicit chain, which still runs
+// for any other sign pattern.
+__device__ __forceinline__ void closed_pair_sign(int s_r, int s_q, const double (&cf)[6], double c5, double s5,
+                                                 double2& ar, double2& aq) {
+    if (s_r != 0 && s_q == -s_r) {
+        const double2 tq = sign_apply(s_r, aq), tr = sign_apply(s_q, ar);
+        const double2 vr = ar, vq = aq;
+        ar = make_double2(fma(s5, tq.x, c5 * vr.x), fma(s5, tq.y, c5 * vr.y));
+        aq = make_double2(fma(s5, tr.x, c5 * vq.x), fma(s5, tr.y, c5 * vq.y));
+    } else if (s_r != 0 || s_q != 0) {
+        chain_pair_sign(s_r, s_q, cf, ar, aq);
+    }
+}
+
 template <typename T, int UPT>
 __device__ __forceinline__ T pair_tile(const OpRec<T>& op, double theta,
                                        typename C2<T>::type* base, uint32_t tl, uint32_t units) {
@@ -265,8 +283,9 @@ __device__ __forceinline__ T pair_tile(const OpRec<T>& op, double theta,
             V b1 = (q0 & 1u) ? f0[j] : f1[j];   // psi[q0 ^ 1]
             if constexpr (sizeof(T) == 8) {
                 if (op.unit) {
-                    chain_pair_sign(rec_sign(op, c_r0), rec_sign(op, c_q0), cf, a0, b0);
-                    chain_pair_sign(rec_sign(op, c_r1), rec_sign(op, c_q1), cf, a1, b1);
+                    const double c5 = cf[0] - cf[2] + cf[4], s5 = cf[1] - cf[3] + cf[5];
+                    closed_pair_sign(rec_sign(op, c_r0), rec_sign(op, c_q0), cf, c5, s5, a0, b0);
+                    closed_pair_sign(rec_sign(op, c_r1), rec_sign(op, c_q1), cf, c5, s5, a1, b1);
                 } else {
                     chain_pair(rec_value(op, c_r0), rec_value(op, c_q0), cf, a0, b0);
                     chain_pair(rec_value(op, c_r1), rec_value(op, c_q1), cf, a1, b1);
