@@ -117,6 +117,13 @@ int tq_autotune_pair(tq_ctx* ctx, const tq_pool* pool, int prec, int n_states,
  * tq_energy's launch under every schedule on (ham, psi) and keeps the
  * fastest.  Synchronises the device. */
 enum { TQ_SPMV_XELL = 0 };
+/* Failure-path tests only (no counterpart in the paper).  With
+ * TQ_TEST_WITHHOLD_CHUNK set, the XOR-ELL energy pass never copies its
+ * first pair chunk into shared memory, so every consumer wait on it runs
+ * out after its bound (about 2 s): the call returns TQ_ETIMEOUT with E NaN,
+ * nothing faults, and the context stays usable once the flag is cleared. */
+enum { TQ_TEST_WITHHOLD_CHUNK = 1 };
+int tq_ctx_set_test_flags(tq_ctx* ctx, int flags);
 int tq_ctx_set_spmv_schedule(tq_ctx* ctx, int lanes_per_row);
 int tq_autotune_spmv(tq_ctx* ctx, const tq_ham* ham, const tq_state* psi,
                      int* best_lanes_per_row, double* best_ms);

@@ -18,6 +18,7 @@ from ._native import (TQ_BK, TQ_C64, TQ_C128, TQ_JW, AdaptResult, Completion, Re
 
 TQ_REQ_EVOLVE, TQ_REQ_ENERGY, TQ_REQ_GRADIENTS = 0, 1, 2
 TQ_SPMV_XELL = 0      # energy-SpMV schedule: the XOR-ELL layout (else CSR lanes per row)
+TQ_TEST_WITHHOLD_CHUNK = 1
 
 __all__ = [
     "TQ_JW", "TQ_BK", "TQ_C128", "TQ_C64", "TQError", "Context", "Hamiltonian", "Pool", "State",
@@ -121,6 +122,11 @@ class Context:
         u = C.c_int()
         call("tq_ctx_get_pair_schedule", self.handle, prec, C.byref(u))
         return u.value
+
+    def set_test_flags(self, flags):
+        """Failure-path tests only: TQ_TEST_WITHHOLD_CHUNK makes the XOR-ELL
+        energy's bounded waits run out (TQ_ETIMEOUT)."""
+        call("tq_ctx_set_test_flags", self.handle, int(flags))
 
     def set_spmv_schedule(self, lanes_per_row):
         """4, 8, 16 or 32 CSR lanes per row, or TQ_SPMV_XELL."""

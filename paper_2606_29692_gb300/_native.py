@@ -59,6 +59,7 @@ SIGNATURES = {
     "tq_ctx_get_pair_schedule": [vp, i32, P(i32)],
     "tq_autotune_pair": [vp, vp, i32, i32, P(i32), P(f64)],
     "tq_ctx_set_spmv_schedule": [vp, i32],
+    "tq_ctx_set_test_flags": [vp, i32],
     "tq_autotune_spmv": [vp, vp, vp, P(i32), P(f64)],
     "tq_ctx_trace_report": [vp, vp, C.c_size_t],
     "tq_pauli_hamiltonian": [i32, vp, vp, f64, i32, P(i64), vp, vp, vp, i64],

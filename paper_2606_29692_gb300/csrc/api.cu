@@ -352,6 +352,14 @@ extern "C" int tq_autotune_spmv(tq_ctx* c, const tq_ham* h, const tq_state* psi,
     API_END
 }
 
+extern "C" int tq_ctx_set_test_flags(tq_ctx* c, int flags) {
+    API_BEGIN
+    TQ_REQUIRE(c != nullptr, "ctx is null");
+    TQ_REQUIRE((flags & ~TQ_TEST_WITHHOLD_CHUNK) == 0, "unknown test flag");
+    c->test_flags = flags;
+    API_END
+}
+
 extern "C" int tq_ctx_trace(tq_ctx* c, int enable) {
     API_BEGIN
     TQ_REQUIRE(c != nullptr, "ctx is null");
@@ -1144,8 +1152,10 @@ void run_energy(tq_ctx* c, const tq_ham* h, const tq_state* psi, double* part, c
     // a sector Hamiltonian has the CSR only
     const int lanes = c->spmv_lanes == TQ_SPMV_XELL && h->sector ? 8 : c->spmv_lanes;
     if (lanes == TQ_SPMV_XELL)
-        launch(c, "energy_xell", s, [&] { return launch_energy_xell(h->view, psi->data, psi->prec, w, w32, part,
-                                                                    c->tickets, c->step, s); });
+        launch(c, "energy_xell", s, [&] {
+            return launch_energy_xell(h->view, psi->data, psi->prec, w, w32, part, c->tickets, c->step, s,
+                                      (c->test_flags & TQ_TEST_WITHHOLD_CHUNK) ? 0 : -1);
+        });
     else
         launch(c, "energy_csr", s, [&] { return launch_energy_csr2(h->view, psi->data, psi->prec, w, w32, part,
                                                                    c->tickets, c->step, c->sm_count, s, lanes); });

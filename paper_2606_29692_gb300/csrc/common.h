@@ -209,7 +209,7 @@ int launch_energy_matrix_free(const HamView& h, const void* psi, int psi_prec,
                               double* partials, unsigned* ticket, DevStep* step,
                               int sms, cudaStream_t s);
 int launch_energy_xell(const HamView& h, const void* psi, int psi_prec, double2* w, float2* w32,
-                       double* partials, unsigned* ticket, DevStep* step, cudaStream_t s);
+                       double* partials, unsigned* ticket, DevStep* step, cudaStream_t s, int withhold_chunk = -1);
 int xell_grid(long long n_blocks, int prec, int sms);
 int xell_chunk_pairs();
 int launch_xell_split(const int* xptr, long long n_blocks, int grid, int* split, cudaStream_t s);
@@ -278,6 +278,7 @@ struct tq_ctx {
     int tracing = 0;
     int pair_upt[2] = {2, 4};              // schedule per precision (C128, C64)
     int spmv_lanes = 32;                   // energy SpMV: CSR lanes per row, or 0 for XOR-ELL
+    int test_flags = 0;                    // TQ_TEST_* (tests of the failure paths only)
     std::vector<tq_trace_rec> trace;      // recorded, not yet reported
     std::vector<cudaEvent_t> event_pool;  // reusable events
     // device scratch, grown on demand

@@ -168,7 +168,7 @@ __device__ __forceinline__ void xt_round(const uint32_t* mask, const typename C2
 template <typename T, typename VT>
 __global__ void __launch_bounds__(XT_THREADS, sizeof(VT) == 4 ? 3 : 2)
 k_energy_xell_tma(HamView h, const typename C2<T>::type* __restrict__ psi, double2* __restrict__ w,
-                  float2* __restrict__ w32, double* partials, unsigned* ticket, DevStep* step) {
+                  float2* __restrict__ w32, double* partials, unsigned* ticket, DevStep* step, int withhold) {
     using V = typename C2<T>::type;
     constexpr int S = xt_stages<VT>();
     extern __shared__ __align__(128) unsigned char xt_raw[];
@@ -193,20 +193,23 @@ k_energy_xell_tma(HamView h, const typename C2<T>::type* __restrict__ psi, doubl
     if (t >= XT_CONSUMERS) {
         if (t == XT_CONSUMERS) {
             constexpr unsigned kBytes = XT_CHUNK * (4 + XELL_ROWS * sizeof(VT));
-            int issued = 0;
+            int fills[S];
+            for (int st = 0; st < S; ++st) fills[st] = 0;
             for (int j = 0; j < nk; ++j) {
                 const int st = j % S;
                 if (j >= S && !mbar_wait(&sm.empty[st], ((j / S) - 1) & 1, abort)) break;
+                if (j == withhold) continue;       // failure-path test: this chunk never arrives
+                ++fills[st];
                 mbar_arrive_expect_tx(&sm.full[st], kBytes);
                 const size_t c = (size_t)(k0 + j) * XT_CHUNK;
                 bulk_load(sm.mask + st * XT_CHUNK, h.xmask + c, XT_CHUNK * 4, &sm.full[st]);
                 bulk_load(sm.val + st * XT_CHUNK * XELL_ROWS, xval + c * XELL_ROWS,
                           XT_CHUNK * XELL_ROWS * sizeof(VT), &sm.full[st]);
-                issued = j + 1;
             }
-            // every issued copy lands before the block may exit
-            for (int j = issued > S ? issued - S : 0; j < issued; ++j)
-                mbar_wait(&sm.full[j % S], (j / S) & 1, abort, false);
+            // every issued copy lands before the block may exit: wait for the
+            // last phase of each stage that was filled (phases complete in order)
+            for (int st = 0; st < S; ++st)
+                if (fills[st] > 0) mbar_wait(&sm.full[st], (fills[st] - 1) & 1, abort, false);
         }
     } else {
         using VT2 = typename C2<VT>::type;
@@ -675,7 +678,7 @@ namespace {
 
 template <typename T, typename VT>
 void xell_launch(const HamView& h, const void* psi, double2* w, float2* w32, double* partials,
-                 unsigned* ticket, DevStep* step, cudaStream_t s) {
+                 unsigned* ticket, DevStep* step, cudaStream_t s, int withhold) {
     using V = typename C2<T>::type;
     static bool attr = false;
     if (!attr) {
@@ -684,17 +687,17 @@ void xell_launch(const HamView& h, const void* psi, double2* w, float2* w32, dou
         attr = true;
     }
     k_energy_xell_tma<T, VT><<<h.xgrid, XT_THREADS, sizeof(XtSmem<T, VT>), s>>>(
-        h, static_cast<const V*>(psi), w, w32, partials, ticket, step);
+        h, static_cast<const V*>(psi), w, w32, partials, ticket, step, withhold);
 }
 
 }  // namespace
 
 int launch_energy_xell(const HamView& h, const void* psi, int psi_prec, double2* w, float2* w32,
-                       double* partials, unsigned* ticket, DevStep* step, cudaStream_t s) {
+                       double* partials, unsigned* ticket, DevStep* step, cudaStream_t s, int withhold_chunk) {
     if (psi_prec == TQ_C128)
-        xell_launch<double, double>(h, psi, w, w32, partials, ticket, step, s);
+        xell_launch<double, double>(h, psi, w, w32, partials, ticket, step, s, withhold_chunk);
     else
-        xell_launch<float, float>(h, psi, w, w32, partials, ticket, step, s);
+        xell_launch<float, float>(h, psi, w, w32, partials, ticket, step, s, withhold_chunk);
     return 1;
 }
 
