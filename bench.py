@@ -523,7 +523,7 @@ def measure_sector(tq, ctx, n_states=65536, reps=20):
         ctx.trace(False)
         nl, t = r["energy_csr"]
         out[f"energy_{nq_}q"] = {"dim": ham.dim, "nnz": ham.nnz, "ms_per_energy": t / nl}
-    ctx.set_spmv_schedule(32)
+    ctx.set_spmv_schedule(tq.TQ_SPMV_XELL)
     return out
 
 

@@ -108,8 +108,9 @@ int tq_autotune_pair(tq_ctx* ctx, const tq_pool* pool, int prec, int n_states,
                      int* best_units_per_thread, double* best_ms);
 
 /* Schedule of the energy SpMV (the H pass of tq_energy, tq_pool_gradients
- * and tq_adapt_step): 4, 8, 16 or 32 lanes sharing one row of the CSR
- * (default 32), or TQ_SPMV_XELL for the XOR-ELL layout.  Every Hamiltonian
+ * and tq_adapt_step): 4, 8, 16 or 32 lanes sharing one row of the CSR,
+ * or TQ_SPMV_XELL for the XOR-ELL layout (the default; a sector
+ * Hamiltonian, which has only the CSR, then uses 8 lanes).  Every Hamiltonian
  * holds both layouts of the same off-diagonal entries: the CSR, and blocks
  * of 8 rows where each X-mask present in the block stores its 8 values
  * H[8R+i][(8R+i)^x] (zero where the CSR has no entry), so one pair's 8

@@ -129,7 +129,7 @@ class Context:
         call("tq_ctx_set_test_flags", self.handle, int(flags))
 
     def set_spmv_schedule(self, lanes_per_row):
-        """4, 8, 16 or 32 CSR lanes per row, or TQ_SPMV_XELL."""
+        """4, 8, 16 or 32 CSR lanes per row, or TQ_SPMV_XELL (the default)."""
         call("tq_ctx_set_spmv_schedule", self.handle, int(lanes_per_row))
 
     def trace(self, enable=True):

@@ -277,7 +277,7 @@ struct tq_ctx {
     long long launches = 0;
     int tracing = 0;
     int pair_upt[2] = {2, 4};              // schedule per precision (C128, C64)
-    int spmv_lanes = 32;                   // energy SpMV: CSR lanes per row, or 0 for XOR-ELL
+    int spmv_lanes = 0;                    // energy SpMV: CSR lanes per row, or 0 for XOR-ELL (default)
     int test_flags = 0;                    // TQ_TEST_* (tests of the failure paths only)
     std::vector<tq_trace_rec> trace;      // recorded, not yet reported
     std::vector<cudaEvent_t> event_pool;  // reusable events

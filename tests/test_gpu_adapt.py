@@ -89,7 +89,7 @@ def test_config1_free_running(ctx, prec, sched):
     try:
         _free_running(ctx, prec)
     finally:
-        ctx.set_spmv_schedule(32)
+        ctx.set_spmv_schedule(tq.TQ_SPMV_XELL)
 
 
 def _free_running(ctx, prec):

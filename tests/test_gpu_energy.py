@@ -46,7 +46,7 @@ def test_energy_and_gradients_match_oracle(ctx, cfg, mp, prec, sched):
     try:
         _energy_and_gradients(ctx, cfg, mp, prec)
     finally:
-        ctx.set_spmv_schedule(32)
+        ctx.set_spmv_schedule(tq.TQ_SPMV_XELL)
 
 
 def _energy_and_gradients(ctx, cfg, mp, prec):
@@ -109,4 +109,4 @@ def test_every_spmv_schedule_agrees(ctx):
             assert abs(tq.energy(ctx, ham, st) - ref) <= (1e-10 if prec == tq.TQ_C128 else 1e-6)
         best, ms = tq.autotune_spmv(ctx, ham, st)
         assert best in (4, 8, 16, 32, tq.TQ_SPMV_XELL) and ms > 0
-    ctx.set_spmv_schedule(32)
+    ctx.set_spmv_schedule(tq.TQ_SPMV_XELL)

@@ -35,6 +35,6 @@ def test_withheld_chunk_times_out_and_the_context_recovers():
         assert 1.0 < dt < 30.0                            # the bound, not a hang
         ctx.set_test_flags(0)
         assert tq.energy(ctx, ham, st) == E0              # the context is still usable
-        ctx.set_spmv_schedule(32)
+        ctx.set_spmv_schedule(tq.TQ_SPMV_XELL)
     with pytest.raises(tq.TQError):
         ctx.set_test_flags(8)
