@@ -6,9 +6,13 @@ Workload (the 14-qubit configuration the headline metric is quoted on):
 Bravyi-Kitaev, strongly correlated synthetic integrals), each prepared from
 the Hartree-Fock state by three Taylor updates and then updated in place,
 once per step, with its own pool generator (204 spin-conserving singles and
-doubles) and angle.  One step = one launch of the pair kernel over all 8192
-states (1 GiB read + 1 GiB written, larger than L2) plus the float64
-per-state norm reduction.
+doubles) and angle.  One step = one launch of the support-only update over
+all 8192 states: each state's generator support (D/2 rows for a single,
+D/8 for a double) is read and written in place, rows off the support are
+left as they are (every term of the series past the first vanishes there),
+and each state's float64 squared norm is carried (about 0.83 GB of DRAM
+traffic per step, larger than L2).  The full-state kernel, which streams
+all 2 GiB, is reported beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -40,9 +44,12 @@ N_SPATIAL, N_ELECTRONS, MAPPING = 7, 6, 1      # 14 qubits, BK
 NQ = 2 * N_SPATIAL
 D = 1 << NQ
 FALLBACK_HBM_GBS = 6800.0
-PROFILE = os.path.join(ROOT, "profiles", "taylor5_pair_c64_14q.md")
-KERNEL_SOURCES = [os.path.join(ROOT, "paper_2606_29692_gb300", "csrc", f)
-                  for f in ("evolve_kernels.cu", "pair.cuh", "dev.cuh")]
+CSRC = os.path.join(ROOT, "paper_2606_29692_gb300", "csrc")
+# committed ncu summaries: (file, sources whose hash the summary records)
+PROFILE_SUPPORT = (os.path.join(ROOT, "profiles", "taylor5_support_c64_14q.md"),
+                   [os.path.join(CSRC, f) for f in ("support.cu", "pair.cuh", "grad.cuh", "dev.cuh")])
+PROFILE_PAIR = (os.path.join(ROOT, "profiles", "taylor5_pair_c64_14q.md"),
+                [os.path.join(CSRC, f) for f in ("evolve_kernels.cu", "pair.cuh", "dev.cuh")])
 
 
 def workload_config(n_states):
@@ -56,7 +63,9 @@ def workload_config(n_states):
         "pool_size": 204,
         "mapping": "BK",
         "state_precision": "complex64 (float32 products), float64 norm reduction",
-        "l2_policy": "inputs larger than L2 (1 GiB per sweep, in place)",
+        "l2_policy": "inputs larger than L2 (1 GiB of states; each step moves about 0.83 GB of support "
+                     "lines and sectors, in place)",
+        "norm": "float64 squared norm per state, carried across steps",
     }
 
 
@@ -71,22 +80,24 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash():
+def kernel_source_hash(sources):
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources:
         with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(n_states):
-    """DRAM bytes per launch from the committed ncu summary, if still valid."""
-    if not os.path.exists(PROFILE):
+def profiled_traffic(profile, n_states):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel's
+    sources still hash to the value the summary records."""
+    path, sources = profile
+    if not os.path.exists(path):
         return None
-    txt = open(PROFILE).read()
+    txt = open(path).read()
     m = re.search(r"traffic_bytes_per_state:\s*([0-9.eE+]+)", txt)
     h = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", txt)
-    if not m or not h or h.group(1) != kernel_source_hash():
+    if not m or not h or h.group(1) != kernel_source_hash(sources):
         return None
     return float(m.group(1)) * n_states
 
@@ -230,22 +241,25 @@ def run_ours(args, rank, world, local_rank):
     hf = tq.hf_index(NQ, N_ELECTRONS, MAPPING)
     psi = torch.zeros((S, D), dtype=torch.complex64, device="cuda")
     psi[:, hf] = 1.0
+    dn = torch.ones(S, dtype=torch.float64, device="cuda")       # ||HF||^2, carried from here on
     for j in range(prep_k.shape[1]):
-        tq.evolve_taylor5_batch(ctx, pool, psi, torch.as_tensor(prep_k[:, j].copy()).cuda(),
-                                torch.as_tensor(prep_th[:, j].copy()).cuda())
+        tq.evolve_taylor5_batch_support(ctx, pool, psi, torch.as_tensor(prep_k[:, j].copy()).cuda(),
+                                        torch.as_tensor(prep_th[:, j].copy()).cuda(), dn)
     dk = torch.as_tensor(k).cuda()
     dth = torch.as_tensor(th).cuda()
-    dn = torch.zeros(S, dtype=torch.float64, device="cuda")
-    # the library's autotuner picks the pair kernel's schedule on scratch
-    # states (untimed, before warm-up)
+    # the library's autotuner picks the schedule on scratch states (untimed,
+    # before warm-up); the CUDA context fetches 32-byte sectors on L2 misses
+    # (the update's reads are scattered over each generator's support)
     if args.pair_schedule:
-        ctx.set_pair_schedule(tq.TQ_C64, args.pair_schedule)
+        ctx.set_support_schedule(tq.TQ_C64, args.pair_schedule)
         upt, tune_ms = args.pair_schedule, None
     else:
-        upt, tune_ms = tq.autotune_pair(ctx, pool, tq.TQ_C64, n_states=min(S, 2048))
+        upt, tune_ms = tq.autotune_support(ctx, pool, tq.TQ_C64, n_states=min(S, 2048))
+    fetch_default = ctx.l2_fetch()
+    ctx.set_l2_fetch(32)
 
     def step():
-        tq.evolve_taylor5_batch(ctx, pool, psi, dk, dth, dn)
+        tq.evolve_taylor5_batch_support(ctx, pool, psi, dk, dth, dn)
 
     barrier = tqd.barrier
 
@@ -281,12 +295,22 @@ def run_ours(args, rank, world, local_rank):
     ctx.trace(False)
     t = max_over_ranks(e0.elapsed_time(e1) / 1e3)
     value = tqd.weak_scaling_value(S, world, args.steps, t)
-    pair_n, pair_ms = rep.get("taylor5_pair", (0, float("nan")))
-    pair_s = pair_ms / max(pair_n, 1) / 1e3
-    alg_bytes = S * 2 * D * 8                       # read + write each amplitude once
+    ctx.set_l2_fetch(0)
+    sup_n, sup_ms = rep.get("taylor5_support", (0, float("nan")))
+    sup_s = sup_ms / max(sup_n, 1) / 1e3
+    # algorithmic bytes: each support amplitude read and written once, the
+    # carried norm read and written once; the touched 32-byte sectors and
+    # 128-byte lines are the floors the memory system can reach
+    rows = support_rows(tq, N_SPATIAL, N_ELECTRONS, MAPPING)
+    n_rows = np.array([r.size for r in rows], dtype=np.float64)[k]
+    n_sect = np.array([np.unique(r >> 2).size for r in rows], dtype=np.float64)[k]
+    n_line = np.array([np.unique(r >> 4).size for r in rows], dtype=np.float64)[k]
+    alg_bytes = float((16 * n_rows).sum() + 16 * S)
+    sector_bytes = float((64 * n_sect).sum() + 16 * S)
+    line_bytes = float((128 * n_line + 32 * n_sect).sum())      # reads by line, writes by sector
     peak, peak_src = peaks()
-    achieved = alg_bytes / pair_s / 1e9
-    traffic = profiled_traffic(S)
+    achieved = alg_bytes / sup_s / 1e9
+    traffic = profiled_traffic(PROFILE_SUPPORT, S)
 
     # end to end: the same update through the host-buffer entry point
     psi_h = torch.empty((S, D), dtype=torch.complex64).pin_memory()
@@ -309,6 +333,7 @@ def run_ours(args, rank, world, local_rank):
     extra = {}
     if rank == 0 and not args.headline_only:
         extra["fp64_single_instance"] = measure_fp64_single(tq, ctx, pool, k, th)
+        extra["full_state"] = measure_full_state(tq, ctx, pool, S)
         extra["c128_batched"] = measure_c128_batched(tq, ctx, pool)
         extra["spmv"] = measure_spmv(tq, ctx, args.spmv_qubits)
         extra["trajectories"] = measure_trajectories(tq, ctx, args.traj)
@@ -326,13 +351,19 @@ def run_ours(args, rank, world, local_rank):
             "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64",
             "data": "synthetic",
-            "config": dict(workload_config(S), schedule={"pair_units_per_thread": upt,
-                                                         "autotune_ms_per_2048_states": tune_ms}),
+            "config": dict(workload_config(S), schedule={"support_pairs_per_thread": upt,
+                                                         "autotune_ms_per_2048_states": tune_ms,
+                                                         "l2_fetch_bytes": 32,
+                                                         "l2_fetch_default": fetch_default}),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_taylor5_pair<float>",
+                         "kernel": "k_taylor5_support<float>",
                          "algorithmic_bytes_per_launch": alg_bytes,
-                         "kernel_ms_per_launch": pair_s * 1e3,
+                         "sector_bytes_per_launch": sector_bytes,
+                         "sector_frac": sector_bytes / sup_s / 1e9 / peak,
+                         "line_read_sector_write_bytes_per_launch": line_bytes,
+                         "line_frac": line_bytes / sup_s / 1e9 / peak,
+                         "kernel_ms_per_launch": sup_s * 1e3,
                          "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
                          else "fallback"},
             "e2e": e2e,
@@ -343,6 +374,44 @@ def run_ours(args, rank, world, local_rank):
         }
         out.update(extra)
     return out
+
+
+def measure_full_state(tq, ctx, pool, n_states, reps=50):
+    """The same batch with the full-state pair kernel, which streams every
+    amplitude of every state (2 D 8 bytes per update) and recomputes each
+    norm from scratch."""
+    import torch
+
+    import synth
+    prep_k, prep_th, k, th = synth.t5_batch(n_states, pool.M, seed=synth.SEED_T5_BATCH)
+    hf = tq.hf_index(NQ, N_ELECTRONS, MAPPING)
+    psi = torch.zeros((n_states, D), dtype=torch.complex64, device="cuda")
+    psi[:, hf] = 1.0
+    for j in range(prep_k.shape[1]):
+        tq.evolve_taylor5_batch(ctx, pool, psi, torch.as_tensor(prep_k[:, j].copy()).cuda(),
+                                torch.as_tensor(prep_th[:, j].copy()).cuda())
+    dk = torch.as_tensor(k).cuda()
+    dth = torch.as_tensor(th).cuda()
+    dn = torch.zeros(n_states, dtype=torch.float64, device="cuda")
+    upt, _ = tq.autotune_pair(ctx, pool, tq.TQ_C64, n_states=min(n_states, 2048))
+    for _ in range(3):
+        tq.evolve_taylor5_batch(ctx, pool, psi, dk, dth, dn)
+    ctx.trace(True)
+    for _ in range(reps):
+        tq.evolve_taylor5_batch(ctx, pool, psi, dk, dth, dn)
+    rep = ctx.trace_report()
+    ctx.trace(False)
+    n_l, ms = rep["taylor5_pair"]
+    nr, nrms = rep.get("norm_reduce", (1, 0.0))
+    ms /= n_l
+    peak, _ = peaks()
+    alg = 2.0 * D * 8 * n_states
+    gbs = alg / (ms * 1e-3) / 1e9
+    return {"workload": f"the headline batch ({n_states} complex64 14-qubit states) with the full-state kernel",
+            "kernel": "k_taylor5_pair<float>", "units_per_thread": upt, "ms_per_launch": ms,
+            "norm_reduce_ms": nrms / nr, "updates_per_s": n_states / ((ms + nrms / nr) * 1e-3),
+            "algorithmic_bytes_per_launch": alg, "achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak,
+            "traffic": profiled_traffic(PROFILE_PAIR, n_states)}
 
 
 def measure_c128_batched(tq, ctx, pool, n_states=4096, reps=20):
@@ -376,6 +445,96 @@ def measure_c128_batched(tq, ctx, pool, n_states=4096, reps=20):
             "kernel": "k_taylor5_pair<double>", "ms_per_launch": ms, "norm_reduce_ms": nrms / nr,
             "updates_per_s": n_states / ((ms + nrms / nr) * 1e-3),
             "achieved_gbs": alg * n_states / (ms * 1e-3) / 1e9, "hbm_frac": alg * n_states / (ms * 1e-3) / 1e9 / peak}
+
+
+def _parity(v):
+    import numpy as np
+    v = v.astype(np.uint64)
+    for sh in (32, 16, 8, 4, 2, 1):
+        v = v ^ (v >> np.uint64(sh))
+    return (v & np.uint64(1)).astype(np.int64)
+
+
+def support_rows(tq, n_spatial, n_electrons, mapping):
+    """Per generator, the rows its support-only update reads and writes
+    (pair representatives and partners), from the library's support form."""
+    import numpy as np
+
+    def insert_zero(v, b):
+        return ((v >> b) << (b + 1)) | (v & ((1 << b) - 1))
+
+    N = 2 * n_spatial
+    f = tq.pool_support_forms(n_spatial, n_electrons, mapping)
+    x = tq.pauli_pool(n_spatial, n_electrons, mapping)[0]
+    out = []
+    for k in range(x.size):
+        m = int(f["m"][k])
+        r = insert_zero(np.arange(1 << (N - m - 1), dtype=np.int64), int(f["rep_pos"][k]))
+        for p in f["pivots"][k, :m]:
+            r = insert_zero(r, int(p))
+        for i, p in enumerate(f["pivots"][k, :m]):
+            r = r | ((((int(f["target"][k]) >> i) & 1) ^ _parity(r & int(f["masks"][k, i]))) << int(p))
+        out.append(np.concatenate([r, r ^ int(x[k])]))
+    return out
+
+
+def measure_support(tq, ctx, pool, n_states, reps=50):
+    """The headline update with the support-only kernel: the same 8192
+    complex64 14-qubit states, generators and angles; only each generator's
+    support rows are read and written (in place), the norm carried."""
+    import numpy as np
+    import torch
+
+    import synth
+    D = 1 << NQ
+    prep_k, prep_th, k, th = synth.t5_batch(n_states, pool.M, seed=synth.SEED_T5_BATCH)
+    hf = tq.hf_index(NQ, N_ELECTRONS, MAPPING)
+    psi = torch.zeros((n_states, D), dtype=torch.complex64, device="cuda")
+    psi[:, hf] = 1.0
+    dn = torch.ones(n_states, dtype=torch.float64, device="cuda")
+    for j in range(prep_k.shape[1]):
+        tq.evolve_taylor5_batch_support(ctx, pool, psi, torch.as_tensor(prep_k[:, j].copy()).cuda(),
+                                        torch.as_tensor(prep_th[:, j].copy()).cuda(), dn)
+    dk = torch.as_tensor(k).cuda()
+    dth = torch.as_tensor(th).cuda()
+    fetch0 = ctx.l2_fetch()
+    per = {}
+    for fetch in (0, 32, 64, 128):
+        ctx.set_l2_fetch(fetch)
+        for ppt in (1, 2, 4, 8):
+            ctx.set_support_schedule(tq.TQ_C64, ppt)
+            for _ in range(3):
+                tq.evolve_taylor5_batch_support(ctx, pool, psi, dk, dth, dn)
+            ctx.trace(True)
+            for _ in range(reps):
+                tq.evolve_taylor5_batch_support(ctx, pool, psi, dk, dth, dn)
+            rep = ctx.trace_report()
+            ctx.trace(False)
+            n_l, ms = rep["taylor5_support"]
+            nc, ncms = rep.get("norm_carry", (1, 0.0))
+            per[(fetch, ppt)] = (ms / n_l, ncms / nc)
+    best_f, best = min(per, key=lambda fp: per[fp][0] + per[fp][1])
+    ctx.set_support_schedule(tq.TQ_C64, best)
+    ctx.set_l2_fetch(0)
+    ms, ncms = per[(best_f, best)]
+    rows = support_rows(tq, N_SPATIAL, N_ELECTRONS, MAPPING)
+    n_rows = np.array([r.size for r in rows], dtype=np.float64)
+    n_sect = np.array([np.unique(r >> 2).size for r in rows], dtype=np.float64)   # 32-byte sectors
+    alg = float((2 * 8 * n_rows[k]).sum() + 16 * n_states)          # amplitudes in + out, norm in + out
+    sect = float((2 * 32 * n_sect[k]).sum() + 16 * n_states)
+    peak, _ = peaks()
+    gbs = alg / (ms * 1e-3) / 1e9
+    return {"workload": f"{n_states} complex64 states of 14 qubits (the headline batch), own generator and angle "
+                        "each, support rows only, norm carried",
+            "kernel": "k_taylor5_support<float>", "pairs_per_thread": best,
+            "l2_fetch_bytes": best_f or fetch0, "l2_fetch_default": fetch0,
+            "ms_by_fetch_and_schedule": {f"{f or fetch0}B/{p}": v[0] + v[1] for (f, p), v in per.items()},
+            "ms_per_launch": ms, "norm_carry_ms": ncms, "updates_per_s": n_states / ((ms + ncms) * 1e-3),
+            "algorithmic_bytes_per_launch": alg, "sector_bytes_per_launch": sect,
+            "mean_support_rows": float(n_rows[k].mean()), "achieved_gbs": gbs, "peak_gbs": peak,
+            "frac": gbs / peak, "sector_gbs": sect / (ms * 1e-3) / 1e9,
+            "sector_frac": sect / (ms * 1e-3) / 1e9 / peak,
+            "norms_finite": bool(torch.isfinite(dn).all().item())}
 
 
 def measure_fp64_single(tq, ctx, pool, k, th, reps=2000):
@@ -729,7 +888,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the SpMV, trajectory-batch and request-loop measurements")
-    ap.add_argument("--section", choices=["spmv", "trajectories", "serving", "sector", "vqe", "c128"], default=None,
+    ap.add_argument("--section", choices=["spmv", "trajectories", "serving", "sector", "vqe", "c128", "support"], default=None,
                     help="run one secondary measurement alone and print its JSON (profiling)")
     ap.add_argument("--spmv-qubits", type=int, default=18)
     ap.add_argument("--traj", type=int, default=256)
@@ -737,7 +896,7 @@ def main():
                     help="length of the request-loop measurement (0 skips it)")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--pair-schedule", type=int, default=0,
-                    help="units per thread of the pair kernel (0 = autotune)")
+                    help="support pairs per thread of the update (0 = autotune)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -766,6 +925,8 @@ def main():
             print(json.dumps(measure_sector(tq, ctx)))
         elif args.section == "vqe":
             print(json.dumps(measure_vqe(tq, ctx)))
+        elif args.section == "support":
+            print(json.dumps(measure_support(tq, ctx, tq.build_pool(ctx, N_SPATIAL, N_ELECTRONS, MAPPING), 8192)))
         elif args.section == "c128":
             import synth
             ints, ne = synth.config2()

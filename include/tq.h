@@ -107,6 +107,17 @@ int tq_ctx_get_pair_schedule(const tq_ctx* ctx, int prec, int* units_per_thread)
 int tq_autotune_pair(tq_ctx* ctx, const tq_pool* pool, int prec, int n_states,
                      int* best_units_per_thread, double* best_ms);
 
+/* L2 fetch granularity of the device's CUDA context (the process's primary
+ * context, shared by every tq_ctx on that device): 32, 64 or 128 bytes
+ * fetched from HBM per L2 miss, or 0 for the value found when the context
+ * was created.  Scattered accesses (the support-only update reads 8-byte
+ * amplitudes spread over a generator's support) move fewer bytes with 32;
+ * streaming kernels read whole lines either way.  It is a hint to the
+ * driver, lasts as long as the CUDA context, and changes no setting of the
+ * GPU itself. */
+int tq_ctx_set_l2_fetch(tq_ctx* ctx, int bytes);
+int tq_ctx_get_l2_fetch(tq_ctx* ctx, int* bytes);
+
 /* Schedule of the energy SpMV (the H pass of tq_energy, tq_pool_gradients
  * and tq_adapt_step): 4, 8, 16 or 32 lanes sharing one row of the CSR,
  * or TQ_SPMV_XELL for the XOR-ELL layout (the default; a sector
@@ -160,6 +171,19 @@ int tq_pool_excitations(int n_spatial, int n_electrons, int* n_ops,
  * (unused slots zero).  Host only. */
 int tq_pauli_pool(int n_spatial, int n_electrons, int mapping, int capacity,
                   uint64_t* x, int* nterm, uint64_t* z, double* c);
+
+/* Support of each pool generator, S_k = {r : A_k[r][r ^ x_k] != 0}, in the
+ * reduced form the support-only update and the gradients enumerate: m[k]
+ * conditions (1 for a single, 3 for a double), pivot bits pivots[3k + i]
+ * ascending (-1 past m[k]) with masks masks[3k + i], each holding its own
+ * pivot and no other; r is in S_k iff parity(r & masks[3k + i]) equals bit
+ * i of target[k] for every i.  Pair u (0 <= u < 2^(N - m - 1)) of the
+ * update is u with a zero inserted at bit rep_pos[k] and at each pivot
+ * (ascending), each pivot then set by its condition: the member of the
+ * pair {r, r ^ x_k} whose bit rep_bit[k] is 0.  Host only. */
+int tq_pool_support_forms(int n_spatial, int n_electrons, int mapping,
+                          int capacity, int* m, int* pivots, uint64_t* masks,
+                          int* target, int* rep_bit, int* rep_pos);
 
 /* Qubit-basis index of the Hartree-Fock determinant (spin orbitals
  * P < n_electrons occupied) under `mapping`.  Host only. */
@@ -478,6 +502,33 @@ int tq_adapt_step(tq_ctx* ctx, const tq_ham* ham, const tq_pool* pool,
 int tq_evolve_taylor5_batch(tq_ctx* ctx, const tq_pool* pool, int n_states,
                             int prec, void* psi, const int* k,
                             const double* theta, double* norm2, void* stream);
+
+/* Support-only batched Taylor-5 (Sec. III-C: each product of Eq. (7) is
+ * O(nnz(A))).  Same states, generators and angles as
+ * tq_evolve_taylor5_batch, and the same amplitudes out, but only the rows
+ * on the support of A_k[b] (D/2 for a single excitation, D/8 for a double)
+ * are read and written: A annihilates every other row, so all terms of
+ * Eq. (6) past the first leave it unchanged.  norm2 (device, optional) is
+ * IN/OUT: on entry ||psi_b||^2, on exit ||psi_b'||^2, carried as the entry
+ * value plus the change over the support (a state whose norm is not known
+ * can take it from tq_evolve_taylor5_batch or a dot product first).  A
+ * state whose k[b] is outside [0, M) is left unchanged and its norm2 set to
+ * NaN.  Full-space pools only (TQ_EINVAL for a sector pool).  One
+ * streaming launch plus a per-state reduction.  Async. */
+int tq_evolve_taylor5_batch_support(tq_ctx* ctx, const tq_pool* pool,
+                                    int n_states, int prec, void* psi,
+                                    const int* k, const double* theta,
+                                    double* norm2, void* stream);
+
+/* Schedule of the support-only update: support pairs per thread per pass
+ * (1, 2, 4 or 8; defaults 2 for TQ_C128, 4 for TQ_C64). */
+int tq_ctx_set_support_schedule(tq_ctx* ctx, int prec, int pairs_per_thread);
+/* Autotuner of that schedule, as tq_autotune_pair: times each on n_states
+ * device scratch states (the update and its norm), keeps the fastest on
+ * the context and returns it with its time per launch.  Synchronises. */
+int tq_autotune_support(tq_ctx* ctx, const tq_pool* pool, int prec,
+                        int n_states, int* best_pairs_per_thread,
+                        double* best_ms);
 
 /* The same batch with HOST buffers (psi, k, theta, norm2 in host memory;
  * pinned memory gives full copy speed): the batch is cut into chunks whose

@@ -93,6 +93,18 @@ def pauli_pool(n_spatial, n_electrons, mapping):
     return x, nt, z, c
 
 
+def pool_support_forms(n_spatial, n_electrons, mapping):
+    """Support of each generator in reduced form: dict of m[M], pivots[M, 3],
+    masks[M, 3], target[M], rep_bit[M], rep_pos[M]."""
+    M = pool_excitations(n_spatial, n_electrons).shape[0]
+    out = {"m": np.zeros(M, np.int32), "pivots": np.zeros((M, 3), np.int32),
+           "masks": np.zeros((M, 3), np.uint64), "target": np.zeros(M, np.int32),
+           "rep_bit": np.zeros(M, np.int32), "rep_pos": np.zeros(M, np.int32)}
+    call("tq_pool_support_forms", n_spatial, n_electrons, mapping, M, _ptr(out["m"]), _ptr(out["pivots"]),
+         _ptr(out["masks"]), _ptr(out["target"]), _ptr(out["rep_bit"]), _ptr(out["rep_pos"]))
+    return out
+
+
 def hf_index(n_qubits, n_electrons, mapping):
     out = C.c_longlong()
     call("tq_hf_index", n_qubits, n_electrons, mapping, C.byref(out))
@@ -131,6 +143,19 @@ class Context:
     def set_spmv_schedule(self, lanes_per_row):
         """4, 8, 16 or 32 CSR lanes per row, or TQ_SPMV_XELL (the default)."""
         call("tq_ctx_set_spmv_schedule", self.handle, int(lanes_per_row))
+
+    def set_support_schedule(self, prec, pairs_per_thread):
+        """Support-only update: 1, 2, 4 or 8 support pairs per thread per pass."""
+        call("tq_ctx_set_support_schedule", self.handle, prec, int(pairs_per_thread))
+
+    def set_l2_fetch(self, nbytes):
+        """L2 fetch granularity of the CUDA context: 32, 64, 128, or 0 (initial)."""
+        call("tq_ctx_set_l2_fetch", self.handle, int(nbytes))
+
+    def l2_fetch(self):
+        out = C.c_int()
+        call("tq_ctx_get_l2_fetch", self.handle, C.byref(out))
+        return out.value
 
     def trace(self, enable=True):
         """Bracket every kernel launch with CUDA events on its stream."""
@@ -474,6 +499,13 @@ def adapt_step(ctx, ham, pool, state, eps, theta=float("nan"), stream=None):
             "selected": r.selected, "converged": bool(r.converged)}
 
 
+def autotune_support(ctx, pool, prec=TQ_C64, n_states=1024):
+    """Time every support-update schedule; set and return (pairs_per_thread, ms)."""
+    u, ms = C.c_int(), C.c_double()
+    call("tq_autotune_support", ctx.handle, pool.handle, prec, int(n_states), C.byref(u), C.byref(ms))
+    return u.value, ms.value
+
+
 def autotune_pair(ctx, pool, prec=TQ_C64, n_states=1024):
     """Time every pair-kernel schedule; set and return (units_per_thread, ms)."""
     u, ms = C.c_int(), C.c_double()
@@ -494,6 +526,14 @@ def evolve_taylor5_batch(ctx, pool, psi, k, theta, norm2=None, prec=TQ_C64, stre
     """In-place batched update of ``psi`` (CUDA tensor, n_states x 2^N)."""
     n_states = psi.shape[0]
     call("tq_evolve_taylor5_batch", ctx.handle, pool.handle, n_states, prec, _ptr(psi), _ptr(k),
+         _ptr(theta), _ptr(norm2), _stream(stream))
+
+
+def evolve_taylor5_batch_support(ctx, pool, psi, k, theta, norm2=None, prec=TQ_C64, stream=None):
+    """In-place batched update touching only each generator's support rows;
+    ``norm2`` (float64 CUDA tensor) is in/out: ||psi_b||^2 in, ||psi_b'||^2 out."""
+    n_states = psi.shape[0]
+    call("tq_evolve_taylor5_batch_support", ctx.handle, pool.handle, n_states, prec, _ptr(psi), _ptr(k),
          _ptr(theta), _ptr(norm2), _stream(stream))
 
 

@@ -65,6 +65,7 @@ SIGNATURES = {
     "tq_pauli_hamiltonian": [i32, vp, vp, f64, i32, P(i64), vp, vp, vp, i64],
     "tq_pool_excitations": [i32, i32, P(i32), vp, i32],
     "tq_pauli_pool": [i32, i32, i32, i32, vp, vp, vp, vp],
+    "tq_pool_support_forms": [i32, i32, i32, i32, vp, vp, vp, vp, vp, vp],
     "tq_hf_index": [i32, i32, i32, P(i64)],
     "tq_build_hamiltonian": [vp, i32, vp, vp, f64, i32, i32, P(vp)],
     "tq_ham_info": [vp, P(i32), P(i32), P(i64), P(i64), P(i64), P(i64), P(C.c_size_t)],
@@ -103,6 +104,11 @@ SIGNATURES = {
     "tq_pool_gradients": [vp, vp, vp, vp, vp, i32, vp],
     "tq_adapt_step": [vp, vp, vp, vp, f64, f64, P(AdaptResult), vp],
     "tq_evolve_taylor5_batch": [vp, vp, i32, i32, vp, vp, vp, vp, vp],
+    "tq_evolve_taylor5_batch_support": [vp, vp, i32, i32, vp, vp, vp, vp, vp],
+    "tq_ctx_set_support_schedule": [vp, i32, i32],
+    "tq_autotune_support": [vp, vp, i32, i32, P(i32), P(f64)],
+    "tq_ctx_set_l2_fetch": [vp, i32],
+    "tq_ctx_get_l2_fetch": [vp, P(i32)],
     "tq_evolve_taylor5_batch_host": [vp, vp, i32, i32, vp, vp, vp, vp],
     "tq_batch_create": [vp, i32, vp, vp, vp, vp, vp, vp, f64, P(vp)],
     "tq_batch_set_schedule": [vp, i32],

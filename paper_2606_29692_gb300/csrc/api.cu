@@ -198,6 +198,9 @@ extern "C" int tq_ctx_create(int device, tq_ctx** out) {
         c->step = static_cast<DevStep*>(dev_alloc(sizeof(DevStep)));
         TQ_CUDA(cudaMemset(c->step, 0, sizeof(DevStep)));
         tickets(c, 4096);
+        size_t fetch = 0;
+        TQ_CUDA(cudaDeviceGetLimit(&fetch, cudaLimitMaxL2FetchGranularity));
+        c->l2_fetch_default = (int)fetch;
     } catch (...) {
         tq_ctx_destroy(c);
         throw;
@@ -238,6 +241,26 @@ extern "C" int tq_ctx_set_pair_schedule(tq_ctx* c, int prec, int units_per_threa
     check_prec(prec);
     TQ_REQUIRE(pair_upt_valid(units_per_thread), "units_per_thread must be 1, 2, 4 or 8");
     c->pair_upt[prec] = units_per_thread;
+    API_END
+}
+
+extern "C" int tq_ctx_set_l2_fetch(tq_ctx* c, int bytes) {
+    API_BEGIN
+    TQ_REQUIRE(c != nullptr, "ctx is null");
+    TQ_REQUIRE(bytes == 0 || bytes == 32 || bytes == 64 || bytes == 128, "bytes must be 0, 32, 64 or 128");
+    set_device(c);
+    if (bytes == 0) bytes = c->l2_fetch_default;
+    TQ_CUDA(cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, (size_t)bytes));
+    API_END
+}
+
+extern "C" int tq_ctx_get_l2_fetch(tq_ctx* c, int* bytes) {
+    API_BEGIN
+    TQ_REQUIRE(c && bytes, "null argument");
+    set_device(c);
+    size_t v = 0;
+    TQ_CUDA(cudaDeviceGetLimit(&v, cudaLimitMaxL2FetchGranularity));
+    *bytes = (int)v;
     API_END
 }
 
@@ -301,6 +324,74 @@ extern "C" int tq_autotune_pair(tq_ctx* c, const tq_pool* p, int prec, int n_sta
     cudaEventDestroy(e1);
     c->pair_upt[prec] = best;
     if (best_upt) *best_upt = best;
+    if (best_ms) *best_ms = best_t;
+    API_END
+}
+
+extern "C" int tq_autotune_support(tq_ctx* c, const tq_pool* p, int prec, int n_states, int* best_ppt,
+                                   double* best_ms) {
+    API_BEGIN
+    TQ_REQUIRE(c && p, "null argument");
+    TQ_REQUIRE(!p->sector, "the support-only update takes full-space pools");
+    check_prec(prec);
+    TQ_REQUIRE(n_states >= 1, "n_states must be >= 1");
+    set_device(c);
+    const long long D = 1ll << p->nq;
+    const size_t sb = (size_t)D * elem_bytes(prec);
+    size_t parts = 0;
+    for (int u : {1, 2, 4, 8})
+        parts = std::max(parts, (size_t)n_states * support_parts(support_tiles(p->nq, n_states, u, c->sm_count)));
+    unsigned char* buf = static_cast<unsigned char*>(
+        scratch(c, S_STAGE, (size_t)n_states * sb + (size_t)n_states * (sizeof(int) + 2 * sizeof(double)) +
+                                parts * sizeof(double) + 256));
+    void* psi = buf;
+    int* dk = reinterpret_cast<int*>(buf + (size_t)n_states * sb);
+    double* dth = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(dk + n_states) + 15) & ~(uintptr_t)15);
+    double* dn = dth + n_states;
+    double* part = dn + n_states;
+    std::vector<int> hk(n_states);
+    std::vector<double> hth(n_states);
+    for (int b = 0; b < n_states; ++b) {
+        hk[b] = (int)((b * 2654435761u) % (unsigned)p->M);
+        hth[b] = 0.05 + 1e-4 * (b % 97);
+    }
+    TQ_CUDA(cudaMemset(psi, 0, (size_t)n_states * sb));
+    TQ_CUDA(cudaMemset(dn, 0, (size_t)n_states * sizeof(double)));
+    TQ_CUDA(cudaMemcpy(dk, hk.data(), n_states * sizeof(int), cudaMemcpyHostToDevice));
+    TQ_CUDA(cudaMemcpy(dth, hth.data(), n_states * sizeof(double), cudaMemcpyHostToDevice));
+    cudaEvent_t e0, e1;
+    TQ_CUDA(cudaEventCreate(&e0));
+    TQ_CUDA(cudaEventCreate(&e1));
+    int best = c->supp_ppt[prec];
+    float best_t = 1e30f;
+    for (int u : {1, 2, 4, 8}) {
+        const int tps = support_tiles(p->nq, n_states, u, c->sm_count);
+        auto once = [&] {
+            launch(c, "autotune_support", 0, [&] {
+                return launch_taylor5_support(p->view, n_states, prec, u, psi, dk, dth, part, tps, dn, c->sm_count, 0);
+            });
+            if (tps > 1)
+                launch(c, "autotune_support", 0, [&] {
+                    return launch_norm_carry(part, prec, n_states, support_parts(tps), dn, dn, nullptr, 0);
+                });
+        };
+        once();
+        TQ_CUDA(cudaEventRecord(e0, 0));
+        for (int r = 0; r < 5; ++r) once();
+        TQ_CUDA(cudaEventRecord(e1, 0));
+        TQ_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        TQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        ms /= 5.f;
+        if (ms < best_t) {
+            best_t = ms;
+            best = u;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->supp_ppt[prec] = best;
+    if (best_ppt) *best_ppt = best;
     if (best_ms) *best_ms = best_t;
     API_END
 }
@@ -453,6 +544,31 @@ extern "C" int tq_pauli_pool(int n_spatial, int n_electrons, int mapping, int ca
             z[8 * k + j] = j < (int)t.size() ? t[j].z : 0;
             c[8 * k + j] = j < (int)t.size() ? t[j].c : 0.0;
         }
+    }
+    API_END
+}
+
+extern "C" int tq_pool_support_forms(int n_spatial, int n_electrons, int mapping, int capacity, int* m,
+                                     int* pivots, uint64_t* masks, int* target, int* rep_bit, int* rep_pos) {
+    API_BEGIN
+    TQ_REQUIRE(m && pivots && masks && target && rep_bit && rep_pos, "null output array");
+    auto ex = excitations(n_spatial, n_electrons);
+    TQ_REQUIRE(capacity >= (int)ex.size(), "capacity too small");
+    const int N = 2 * n_spatial;
+    for (size_t k = 0; k < ex.size(); ++k) {
+        auto t = pauli_generator(ex[k], N, mapping);
+        TQ_REQUIRE(!t.empty(), "empty generator");
+        SignForm f = factor_generator(t);
+        if (!f.ok) throw Error(TQ_ENUMERIC, "generator sign function does not factor");
+        SupportForm sf = support_form(f, t[0].x);
+        m[k] = sf.m;
+        for (int i = 0; i < 3; ++i) {
+            pivots[3 * k + i] = i < sf.m ? sf.p[i] : -1;
+            masks[3 * k + i] = i < sf.m ? sf.e[i] : 0;
+        }
+        target[k] = sf.target;
+        rep_bit[k] = sf.h;
+        rep_pos[k] = sf.hp;
     }
     API_END
 }
@@ -688,7 +804,7 @@ tq_pool* make_pool(tq_ctx* c, int n_spatial, int n_electrons, int mapping) {
                 fc0d[k] = f.c0;
                 fc0f[k] = (float)f.c0;
                 SupportForm sf = support_form(f, t[0].x);
-                supp[k] = make_int4(sf.m | (sf.target << 8), sf.p[0] | (sf.p[1] << 8) | (sf.p[2] << 16), 0, 0);
+                supp[k] = make_int4(sf.m | (sf.target << 8), sf.p[0] | (sf.p[1] << 8) | (sf.p[2] << 16), sf.hp, sf.h);
                 for (int i = 0; i < 3; ++i) supe[3 * k + i] = (uint32_t)sf.e[i];
             }
         }
@@ -1540,6 +1656,39 @@ extern "C" int tq_evolve_taylor5_batch(tq_ctx* c, const tq_pool* p, int n_states
     const bool fin = launch_update(c, p, n_states, prec, upt, psi, k, theta, 0, 0.0, nullptr, part, norm2, nullptr, s);
     if (norm2 && !fin)
         launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, prec, n_states, tiles, norm2, nullptr, s); });
+    API_END
+}
+
+extern "C" int tq_evolve_taylor5_batch_support(tq_ctx* c, const tq_pool* p, int n_states, int prec, void* psi,
+                                               const int* k, const double* theta, double* norm2, void* stream) {
+    API_BEGIN
+    TQ_REQUIRE(c && p, "null argument");
+    TQ_REQUIRE(!p->sector, "the support-only update takes full-space pools (sector states: tq_evolve_taylor5_batch)");
+    TQ_REQUIRE(n_states >= 0, "n_states < 0");
+    check_prec(prec);
+    if (n_states == 0) return TQ_OK;   // an empty batch is a no-op
+    TQ_REQUIRE(psi && k && theta, "null argument");
+    TQ_REQUIRE(((uintptr_t)psi & 15u) == 0, "psi must be 16-byte aligned");
+    set_device(c);
+    cudaStream_t s = as_stream(stream);
+    const int ppt = c->supp_ppt[prec];
+    const int tps = support_tiles(p->nq, n_states, ppt, c->sm_count);
+    const int parts = support_parts(tps);
+    double* part = static_cast<double*>(scratch(c, S_PART, (size_t)n_states * parts * sizeof(double)));
+    launch(c, "taylor5_support", s, [&] {
+        return launch_taylor5_support(p->view, n_states, prec, ppt, psi, k, theta, part, tps, norm2, c->sm_count, s);
+    });
+    if (norm2 && tps > 1)
+        launch(c, "norm_carry", s, [&] { return launch_norm_carry(part, prec, n_states, parts, norm2, norm2, nullptr, s); });
+    API_END
+}
+
+extern "C" int tq_ctx_set_support_schedule(tq_ctx* c, int prec, int pairs_per_thread) {
+    API_BEGIN
+    TQ_REQUIRE(c, "null argument");
+    check_prec(prec);
+    TQ_REQUIRE(pair_upt_valid(pairs_per_thread), "pairs_per_thread must be 1, 2, 4 or 8");
+    c->supp_ppt[prec] = pairs_per_thread;
     API_END
 }
 

@@ -47,12 +47,17 @@ struct SignForm {
 // pivot p[i] and no other pivot; row r is in the support iff
 // parity(r & e[i]) == bit i of target for every i.  Support row u
 // (0 <= u < 2^(N-m)) is u with zeros inserted at the pivots, each pivot bit
-// then set to target_i xor parity(r & e[i]).
+// then set to target_i xor parity(r & e[i]).  The support is closed under
+// r -> r ^ x; h is the highest set bit of x that is not a pivot (one always
+// exists) and hp its position among the free bits: pair u (0 <= u <
+// 2^(N-m-1)) is support row insert_zero(u, hp), the member of its pair
+// {r, r ^ x} whose bit h is 0.
 struct SupportForm {
     int m;
     int p[3];
     uint64_t e[3];
     int target;
+    int h, hp;
 };
 SupportForm support_form(const SignForm& f, uint64_t x);
 
@@ -193,6 +198,18 @@ int launch_taylor5_pair(const PoolView& p, int n_states, int prec, int upt, void
                         double* partials, int sms, cudaStream_t s);
 int launch_norm_reduce(const double* partials, int prec, int n_states, int tiles_per_state,
                        double* norm2_out, double* step_norm2, cudaStream_t s);
+// The same sum added to base[i] (in/out allowed: norm2_out == base).
+int launch_norm_carry(const double* partials, int prec, int n_states, int tiles_per_state, const double* base,
+                      double* norm2_out, double* step_norm2, cudaStream_t s);
+// Support-only batched Taylor-5 (in place; rows outside each generator's
+// support are not touched); partials hold the change of |psi|^2 per tile.
+// With one tile per state and norm2 set, the launch adds the change to
+// norm2 itself (nothing is left for launch_norm_carry).
+int support_tiles(int nq, int n_states, int ppt, int sms);
+int support_parts(int tiles);
+int launch_taylor5_support(const PoolView& p, int n_states, int prec, int ppt, void* psi, const int* k,
+                           const double* theta, double* partials, int tps, double* norm2, int sms,
+                           cudaStream_t s);
 int launch_scale(void* psi, int prec, long long D, const double* norm2, cudaStream_t s);
 
 // Taylor-5 for a general CSR operator.
@@ -277,6 +294,8 @@ struct tq_ctx {
     long long launches = 0;
     int tracing = 0;
     int pair_upt[2] = {2, 4};              // schedule per precision (C128, C64)
+    int supp_ppt[2] = {2, 4};              // support-only update: pairs per thread per pass (C128, C64)
+    int l2_fetch_default = 0;              // the CUDA context's L2 fetch granularity at creation (bytes)
     int spmv_lanes = 0;                    // energy SpMV: CSR lanes per row, or 0 for XOR-ELL (default)
     int test_flags = 0;                    // TQ_TEST_* (tests of the failure paths only)
     std::vector<tq_trace_rec> trace;      // recorded, not yet reported

@@ -88,7 +88,7 @@ k_taylor5_pair(PoolView p, int n_states, typename C2<T>::type* psi, const int* k
 // One warp per state: fixed-order float64 sum of the state's partials
 // (float64 values for complex128; (hi, lo) float pairs for complex64).
 template <bool PAIRS>
-__global__ void k_norm_reduce(const double* partials, int n_states, int tiles,
+__global__ void k_norm_reduce(const double* partials, int n_states, int tiles, const double* base,
                               double* norm2_out, double* step_norm2) {
     const int lane = threadIdx.x & 31;
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -105,6 +105,7 @@ __global__ void k_norm_reduce(const double* partials, int n_states, int tiles,
     }
     s = warp_sum(s);
     if (lane == 0) {
+        if (base) s = base[w] + s;   // a carried norm: base + the change
         if (norm2_out) norm2_out[w] = s;
         if (step_norm2 && w == 0) *step_norm2 = s;
     }
@@ -439,12 +440,17 @@ int launch_taylor5_pair_gated(const PoolView& p, int prec, int upt, void* psi, c
 
 int launch_norm_reduce(const double* partials, int prec, int n_states, int tiles_per_state,
                        double* norm2_out, double* step_norm2, cudaStream_t s) {
+    return launch_norm_carry(partials, prec, n_states, tiles_per_state, nullptr, norm2_out, step_norm2, s);
+}
+
+int launch_norm_carry(const double* partials, int prec, int n_states, int tiles_per_state, const double* base,
+                      double* norm2_out, double* step_norm2, cudaStream_t s) {
     const int bs = 256;
     const int grid = (n_states * 32 + bs - 1) / bs;
     if (prec == TQ_C128)
-        k_norm_reduce<false><<<grid, bs, 0, s>>>(partials, n_states, tiles_per_state, norm2_out, step_norm2);
+        k_norm_reduce<false><<<grid, bs, 0, s>>>(partials, n_states, tiles_per_state, base, norm2_out, step_norm2);
     else
-        k_norm_reduce<true><<<grid, bs, 0, s>>>(partials, n_states, tiles_per_state, norm2_out, step_norm2);
+        k_norm_reduce<true><<<grid, bs, 0, s>>>(partials, n_states, tiles_per_state, base, norm2_out, step_norm2);
     return 1;
 }
 

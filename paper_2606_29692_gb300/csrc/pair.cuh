@@ -100,6 +100,14 @@ __device__ __forceinline__ void taylor_coefs_fast(double theta, T (&cf)[6]) {
     cf[5] = t5 * T(1.0 / 120.0);
 }
 
+// c5 = cf0 - cf2 + cf4 and s5 = cf1 - cf3 + cf5 (the closed form below) with
+// additions the compiler may not fuse with the products inside cf, so every
+// kernel that uses them gets the same bits.
+__device__ __forceinline__ void closed_coefs(const double (&cf)[6], double& c5, double& s5) {
+    c5 = __dadd_rn(__dsub_rn(cf[0], cf[2]), cf[4]);
+    s5 = __dadd_rn(__dsub_rn(cf[1], cf[3]), cf[5]);
+}
+
 // Per-warp norm partial: float64 sum for complex128; for complex64 a
 // TwoSum-compensated float32 warp sum stored as a (hi, lo) float pair in
 // the 8-byte slot and widened to float64 by the reduction kernel.
@@ -283,7 +291,8 @@ __device__ __forceinline__ T pair_tile(const OpRec<T>& op, double theta,
             V b1 = (q0 & 1u) ? f0[j] : f1[j];   // psi[q0 ^ 1]
             if constexpr (sizeof(T) == 8) {
                 if (op.unit) {
-                    const double c5 = cf[0] - cf[2] + cf[4], s5 = cf[1] - cf[3] + cf[5];
+                    double c5, s5;
+                    closed_coefs(cf, c5, s5);
                     closed_pair_sign(rec_sign(op, c_r0), rec_sign(op, c_q0), cf, c5, s5, a0, b0);
                     closed_pair_sign(rec_sign(op, c_r1), rec_sign(op, c_q1), cf, c5, s5, a1, b1);
                 } else {

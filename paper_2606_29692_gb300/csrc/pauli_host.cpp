@@ -455,6 +455,18 @@ SupportForm support_form(const SignForm& f, uint64_t x) {
         s.e[i] = e[ord[i]];
         s.target |= t[ord[i]] << i;
     }
+    // pair representative bit: if every set bit of x were a pivot, the
+    // conditions parity(x & e[i]) == 0 (x maps the support to itself) would
+    // force x = 0
+    s.h = -1;
+    for (int bit = 63; bit >= 0 && s.h < 0; --bit) {
+        bool pivot = false;
+        for (int i = 0; i < f.m; ++i) pivot = pivot || s.p[i] == bit;
+        if (((x >> bit) & 1) && !pivot) s.h = bit;
+    }
+    if (s.h < 0) throw Error(TQ_ENUMERIC, "generator X-mask has no free bit");
+    s.hp = s.h;
+    for (int i = 0; i < f.m; ++i) s.hp -= s.p[i] < s.h;
     return s;
 }
 

@@ -1,0 +1,229 @@
+// Support-only batched Taylor-5 update (Sec. III-C, Eqs. (6)-(8)).
+//
+// Each product v_k = A v_{k-1} of Eq. (7) costs O(nnz(A)), and a pool
+// generator's non-zeros sit on its support S = {r : A[r][r ^ x] != 0}: a
+// single excitation has |S| = D/2, a double D/8.  A row outside S is
+// annihilated by A, so every term k >= 1 of Eq. (6) leaves it at zero and
+// psi'[r] = psi[r] there.  An in-place update therefore reads and writes
+// the amplitudes of S only, where the full-state pair kernel streams all D.
+//
+// S is an affine subspace of codimension m (the generator's conditions on
+// the column, rewritten on the row: pivots p_i and masks e_i, as the
+// gradient kernel uses them) and is closed under r -> r ^ x.  One member
+// of each pair {r, r ^ x} is taken: the one whose bit h is 0, h a free
+// (non-pivot) bit of x (one always exists: if every set bit of x were a
+// pivot, the conditions A x = 0 on S would force x = 0).  Pair u of a
+// generator is then u with a zero inserted at h's position among the free
+// bits, expanded by the pivots.  Consecutive u give consecutive rows
+// wherever the low bits are free, so a warp's loads stay coalesced.
+//
+// The squared norm is carried, not recomputed: on exit
+// ||psi'||^2 = ||psi||^2 + sum_S (|psi'_r|^2 - |psi_r|^2), each difference
+// formed as (a' - a)(a' + a) per component, so the small change keeps its
+// relative accuracy.  The five products run exactly as in the full-state
+// kernel (complex64: packed float32 chain; complex128 with entries +-1:
+// the closed form c5 psi + s5 A psi), so the two kernels give equal
+// amplitudes.
+#include "dev.cuh"
+#include "grad.cuh"
+#include "pair.cuh"
+
+#include <algorithm>
+
+namespace tq {
+
+namespace {
+
+constexpr int SUPP_BS = 256;
+
+template <typename T>
+struct SupOp {
+    SuppRec s;
+    int hp;      // insert position of the pair representative's zero bit
+    int unit;    // every entry of A is 0 or +-1
+    int c0neg;
+    T c0;
+};
+
+template <typename T>
+__device__ __forceinline__ SupOp<T> load_supop(const PoolView& p, int k) {
+    SupOp<T> o;
+    o.s = load_supp(p, k);
+    o.hp = p.supp[k].z;
+    o.c0 = sizeof(T) == 4 ? (T)p.fc0f[k] : (T)p.fc0d[k];
+    o.unit = fabsf(p.fc0f[k]) == 1.0f;
+    o.c0neg = p.fc0f[k] < 0.0f;
+    return o;
+}
+
+// Updates the support pairs [i0, i1) of one state; returns the thread's
+// sum of |psi'|^2 - |psi|^2.
+template <typename T, int PPT>
+__device__ __forceinline__ T support_tile(const SupOp<T>& op, double theta, typename C2<T>::type* __restrict__ base,
+                                          uint32_t i0, uint32_t i1) {
+    using V = typename C2<T>::type;
+    T cf[6];
+    taylor_coefs_fast<T>(theta, cf);
+    double c5 = 0.0, s5 = 0.0;
+    if constexpr (sizeof(T) == 8) closed_coefs(cf, c5, s5);
+    T delta = T(0);
+    for (uint32_t i = i0 + threadIdx.x; i < i1; i += SUPP_BS * PPT) {
+        uint32_t rr[PPT];
+        V a[PPT], b[PPT];
+        bool ok[PPT];
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+            const uint32_t u = i + j * SUPP_BS;
+            ok[j] = u < i1;
+            if (!ok[j]) continue;
+            const uint32_t r = supp_row(op.s, insert_zero(u, op.hp));
+            rr[j] = r;
+            a[j] = base[r];
+            b[j] = base[r ^ op.s.x];
+        }
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+            if (!ok[j]) continue;
+            const uint32_t r = rr[j], q = r ^ op.s.x;
+            const int nr = parity32(q & op.s.z0), nq = parity32(r & op.s.z0);   // signs of A[r][q], A[q][r]
+            V ar = a[j], aq = b[j];
+            if constexpr (sizeof(T) == 8) {
+                if (op.unit) {
+                    const int sr = (nr != op.c0neg) ? -1 : 1, sq = (nq != op.c0neg) ? -1 : 1;
+                    closed_pair_sign(sr, sq, cf, c5, s5, ar, aq);
+                } else {
+                    chain_pair(nr ? -op.c0 : op.c0, nq ? -op.c0 : op.c0, cf, ar, aq);
+                }
+            } else {
+                chain_pair(nr ? -op.c0 : op.c0, nq ? -op.c0 : op.c0, cf, ar, aq);
+            }
+            delta += (ar.x - a[j].x) * (ar.x + a[j].x) + (ar.y - a[j].y) * (ar.y + a[j].y);
+            delta += (aq.x - b[j].x) * (aq.x + b[j].x) + (aq.y - b[j].y) * (aq.y + b[j].y);
+            base[r] = ar;
+            base[q] = aq;
+        }
+    }
+    return delta;
+}
+
+// Persistent grid over (state, tile) items; tile tl of a state whose
+// generator has P support pairs covers pairs [tl P / tps, (tl + 1) P / tps).
+// With one tile per state and `norm2` set, the CTA finishes the state's
+// norm itself (norm2[b] += the fixed-order sum of its warps' partials);
+// otherwise every warp leaves its partial for the reduction kernel.
+template <typename T, int PPT>
+__global__ void __launch_bounds__(SUPP_BS)
+k_taylor5_support(PoolView p, int n_states, typename C2<T>::type* psi, const int* kk, const double* th,
+                  double* partials, int tiles_per_state, double* norm2) {
+    const int warp = threadIdx.x >> 5;
+    constexpr int NW = SUPP_BS / 32;
+    __shared__ double red[NW];
+    const bool fold = tiles_per_state == 1 && norm2 != nullptr;
+    const long long D = 1ll << p.nq;
+    const unsigned tps = (unsigned)tiles_per_state;
+    const unsigned total = (unsigned)n_states * tps;
+    unsigned tile = blockIdx.x;
+    int b = (int)(tile / tps);
+    int k = tile < total ? kk[b] : 0;
+    double theta = tile < total ? th[b] : 0.0;
+    while (tile < total) {
+        const unsigned tl = tile - (unsigned)b * tps;
+        const unsigned ntile = tile + gridDim.x;
+        const int nb = (int)(ntile / tps);
+        int nk = 0;
+        double nth = 0.0;
+        if (ntile < total) {
+            nk = kk[nb];
+            nth = th[nb];
+        }
+        double* slot = fold ? &red[warp] : partials + (size_t)tile * NW + warp;
+        if (k < 0 || k >= p.M) {
+            store_nan_partial(slot, T(0));   // the state is left untouched, its norm poisoned
+        } else {
+            const SupOp<T> op = load_supop<T>(p, k);
+            const unsigned long long P = 1ull << (p.nq - op.s.m - 1);
+            const uint32_t i0 = (uint32_t)(P * tl / tps), i1 = (uint32_t)(P * (tl + 1) / tps);
+            const T d = support_tile<T, PPT>(op, theta, psi + (long long)b * D, i0, i1);
+            store_partial(slot, d);
+        }
+        if (fold) {
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double sum = 0.0;
+                for (int w = 0; w < NW; ++w) {
+                    if constexpr (sizeof(T) == 4) {
+                        const float2 hl = *reinterpret_cast<const float2*>(&red[w]);
+                        sum += (double)hl.x + (double)hl.y;
+                    } else {
+                        sum += red[w];
+                    }
+                }
+                norm2[b] = norm2[b] + sum;
+            }
+            __syncthreads();
+        }
+        tile = ntile;
+        b = nb;
+        k = nk;
+        theta = nth;
+    }
+}
+
+template <typename T, int PPT>
+int launch_support(const PoolView& p, int n_states, void* psi, const int* k, const double* theta,
+                   double* partials, int tps, double* norm2, int sms, cudaStream_t s) {
+    using V = typename C2<T>::type;
+    const long long total = (long long)n_states * tps;
+    if (total >= (1ll << 31)) return -1;
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_taylor5_support<T, PPT>, SUPP_BS, 0);
+        per_sm = n < 1 ? 1 : n;
+    }
+    long long grid = (long long)per_sm * sms;
+    if (grid > total) grid = total;
+    if (grid < 1) grid = 1;
+    k_taylor5_support<T, PPT><<<(int)grid, SUPP_BS, 0, s>>>(p, n_states, static_cast<V*>(psi), k, theta,
+                                                             partials, tps, norm2);
+    return 1;
+}
+
+template <typename T>
+int dispatch_support(int ppt, const PoolView& p, int n_states, void* psi, const int* k, const double* theta,
+                     double* partials, int tps, double* norm2, int sms, cudaStream_t s) {
+    switch (ppt) {
+        case 1: return launch_support<T, 1>(p, n_states, psi, k, theta, partials, tps, norm2, sms, s);
+        case 2: return launch_support<T, 2>(p, n_states, psi, k, theta, partials, tps, norm2, sms, s);
+        case 4: return launch_support<T, 4>(p, n_states, psi, k, theta, partials, tps, norm2, sms, s);
+        case 8: return launch_support<T, 8>(p, n_states, psi, k, theta, partials, tps, norm2, sms, s);
+        default: return -1;
+    }
+}
+
+}  // namespace
+
+// Tiles per state: a double excitation (the smallest support, 2^(nq-4)
+// pairs) fills one tile of SUPP_BS * ppt pairs; small batches split states
+// further (down to 32 pairs of a double per tile) to fill the GPU.
+int support_tiles(int nq, int n_states, int ppt, int sms) {
+    const long long dpairs = nq >= 4 ? 1ll << (nq - 4) : 1;
+    long long t = dpairs / ((long long)SUPP_BS * ppt);
+    if (t < 1) t = 1;
+    const long long want = (4ll * sms + n_states - 1) / std::max(n_states, 1);
+    const long long cap = std::max(1ll, dpairs / 32);
+    while (t < want && t * 2 <= cap) t *= 2;
+    return (int)t;
+}
+
+int support_parts(int tiles) { return tiles * (SUPP_BS / 32); }
+
+int launch_taylor5_support(const PoolView& p, int n_states, int prec, int ppt, void* psi, const int* k,
+                           const double* theta, double* partials, int tps, double* norm2, int sms,
+                           cudaStream_t s) {
+    if (prec == TQ_C128)
+        return dispatch_support<double>(ppt, p, n_states, psi, k, theta, partials, tps, norm2, sms, s);
+    return dispatch_support<float>(ppt, p, n_states, psi, k, theta, partials, tps, norm2, sms, s);
+}
+
+}  // namespace tq

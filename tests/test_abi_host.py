@@ -196,3 +196,37 @@ def test_fcidump_errors(tq, tmp_path):
             tq.read_fcidump(str(bad))
     with pytest.raises(tq.TQError):
         tq.read_fcidump(str(tmp_path / "missing.txt"))
+
+
+def _insert_zero(v, b):
+    return ((v >> b) << (b + 1)) | (v & ((1 << b) - 1))
+
+
+@pytest.mark.parametrize("n,ne,mp", [(2, 2, mapping.JW), (2, 2, mapping.BK), (4, 4, mapping.JW),
+                                     (4, 4, mapping.BK), (6, 8, mapping.BK), (7, 6, mapping.JW),
+                                     (7, 6, mapping.BK)])
+def test_support_pair_enumeration_covers_the_oracle_support(tq, n, ne, mp):
+    """Pairs enumerated from the exported support form (the formula the
+    support-only update and the gradients run) are exactly the oracle
+    generator's non-zero rows, each pair once, every row in range."""
+    N = 2 * n
+    f = tq.pool_support_forms(n, ne, mp)
+    x, _, _, _ = tq.pauli_pool(n, ne, mp)
+    _, pps = pauli.pool_pauli(n, ne, mp)
+    for k, ps in enumerate(pps):
+        m = int(f["m"][k])
+        piv = [int(p) for p in f["pivots"][k, :m]]
+        assert piv == sorted(piv) and all(0 <= p < N for p in piv)
+        u = np.arange(1 << (N - m - 1), dtype=np.int64)
+        r = _insert_zero(u, int(f["rep_pos"][k]))
+        for p in piv:
+            r = _insert_zero(r, p)
+        for i, p in enumerate(piv):
+            par = np.array([bin(int(v) & int(f["masks"][k, i])).count("1") & 1 for v in r], dtype=np.int64)
+            r = r | (((int(f["target"][k]) >> i) & 1) ^ par) << p
+        q = r ^ int(x[k])
+        assert r.max() < (1 << N) and np.all((r >> int(f["rep_bit"][k])) & 1 == 0)
+        rows = np.concatenate([r, q])
+        assert np.unique(rows).size == rows.size                     # each pair once
+        A = pauli.pauli_to_csr(ps).tocoo()
+        assert np.array_equal(np.sort(rows), np.unique(A.row))

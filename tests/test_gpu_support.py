@@ -1,0 +1,190 @@
+"""GPU parity: the support-only batched Taylor-5 update (Sec. III-C).
+
+Only the rows on each generator's support are read and written; the tests
+check the amplitudes against the oracle's five-product chain, the equality
+with the full-state kernel, that rows off the support keep their bits, and
+the carried squared norm."""
+
+import numpy as np
+import pytest
+
+import paper_2606_29692_gb300 as tq
+import synth
+from gpu_util import fidelity, rel_l2
+from oracle import adapt as oadapt
+from oracle import evolve, pauli
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return tq.Context(0)
+
+
+_A = {}
+
+
+def oracle_A(n, ne, mp, k):
+    key = (n, ne, mp)
+    if key not in _A:
+        _A[key] = (pauli.pool_pauli(n, ne, mp)[1], {})
+    pps, cache = _A[key]
+    if k not in cache:
+        cache[k] = pauli.pauli_to_csr(pps[k])
+    return cache[k]
+
+
+def _inputs(n_q, S, M, seed, prec):
+    import torch
+    rng = np.random.default_rng(seed)
+    psi = np.stack([synth.random_state(n_q, seed * 1000 + b) for b in range(S)])
+    k = (np.arange(S) % M).astype(np.int32)          # every generator at least once when S >= M
+    rng.shuffle(k)
+    th = rng.normal(0, 0.3, size=S)
+    th[0] = 0.0
+    dt = torch.complex128 if prec == tq.TQ_C128 else torch.complex64
+    return psi, k, th, dt
+
+
+@pytest.mark.parametrize("prec", [tq.TQ_C128, tq.TQ_C64])
+@pytest.mark.parametrize("n,ne,mp", [(2, 2, 0), (2, 2, 1), (4, 4, 0), (4, 4, 1), (6, 8, 0), (7, 6, 1)])
+def test_support_update_matches_oracle(ctx, n, ne, mp, prec):
+    import torch
+    N = 2 * n
+    pool = tq.build_pool(ctx, n, ne, mp)
+    S = max(pool.M, 24) if N <= 12 else 64
+    psi, k, th, dt = _inputs(N, S, pool.M, 3 + n + mp, prec)
+    dpsi = torch.as_tensor(psi).to(dt).cuda()
+    n_in = (dpsi.abs().double() ** 2).sum(dim=1)
+    dn = n_in.clone()
+    tq.evolve_taylor5_batch_support(ctx, pool, dpsi, torch.as_tensor(k).cuda(), torch.as_tensor(th).cuda(), dn,
+                                    prec=prec)
+    torch.cuda.synchronize()
+    out = dpsi.cpu().numpy().astype(np.complex128)
+    nrm = dn.cpu().numpy()
+    for b in range(S):
+        ref = evolve.taylor5(oracle_A(n, ne, mp, int(k[b])), psi[b], th[b])
+        tol = 1e-12 if prec == tq.TQ_C128 else 2e-6
+        assert rel_l2(out[b], ref) <= tol, b
+        if prec == tq.TQ_C128:
+            assert abs(nrm[b] - np.vdot(ref, ref).real) <= 1e-12, b
+        else:
+            assert abs(nrm[b] - np.vdot(out[b], out[b]).real) <= 1e-6, b
+
+
+@pytest.mark.parametrize("prec", [tq.TQ_C128, tq.TQ_C64])
+@pytest.mark.parametrize("n,ne,mp", [(6, 8, 0), (6, 8, 1), (7, 6, 1)])
+def test_support_update_equals_full_state_kernel(ctx, n, ne, mp, prec):
+    """Same amplitudes as the full-state pair kernel, rows off the support
+    bit-for-bit untouched, every schedule identical."""
+    import torch
+    N = 2 * n
+    pool = tq.build_pool(ctx, n, ne, mp)
+    S = 96
+    psi, k, th, dt = _inputs(N, S, pool.M, 40 + n + mp, prec)
+    dk = torch.as_tensor(k).cuda()
+    dth = torch.as_tensor(th).cuda()
+    full = torch.as_tensor(psi).to(dt).cuda()
+    n_full = torch.zeros(S, dtype=torch.float64, device="cuda")
+    tq.evolve_taylor5_batch(ctx, pool, full, dk, dth, n_full, prec=prec)
+    before = torch.as_tensor(psi).to(dt).cuda()
+    n_in = (before.abs().double() ** 2).sum(dim=1)
+    outs = []
+    for ppt in (1, 2, 4, 8):
+        ctx.set_support_schedule(prec, ppt)
+        d = before.clone()
+        dn = n_in.clone()
+        tq.evolve_taylor5_batch_support(ctx, pool, d, dk, dth, dn, prec=prec)
+        torch.cuda.synchronize()
+        outs.append((d, dn))
+    ctx.set_support_schedule(prec, 2 if prec == tq.TQ_C128 else 4)
+    fv = torch.view_as_real(full)
+    bv = torch.view_as_real(before)
+    for d, dn in outs:
+        assert torch.equal(torch.view_as_real(d), fv)       # values (a -0.0 equals +0.0)
+        assert torch.equal(torch.view_as_real(d), torch.view_as_real(outs[0][0]))
+        tol = 1e-12 if prec == tq.TQ_C128 else 2e-6
+        assert (dn - n_full).abs().max().item() <= tol * n_full.max().item()
+    # rows off the support: identical bits
+    d = outs[-1][0]
+    ib = bv.view(torch.int64) if prec == tq.TQ_C128 else bv.view(torch.int32)
+    io = torch.view_as_real(d).view(torch.int64) if prec == tq.TQ_C128 else torch.view_as_real(d).view(torch.int32)
+    for b in range(0, S, 7):
+        A = oracle_A(n, ne, mp, int(k[b]))
+        on = np.zeros(1 << N, dtype=bool)
+        on[np.unique(A.tocoo().row)] = True
+        off = torch.as_tensor(~on).cuda()
+        assert torch.equal(io[b][off], ib[b][off])
+
+
+def test_full_size_batch_sampled(ctx):
+    """8192 complex64 states of 14 qubits (the batched benchmark's launch),
+    norms carried over two updates, sampled against the oracle."""
+    import torch
+    n, ne, mp = 7, 6, 1
+    N, S = 14, 8192
+    pool = tq.build_pool(ctx, n, ne, mp)
+    prep_k, prep_th, k, th = synth.t5_batch(S, pool.M)
+    hf = tq.hf_index(N, ne, mp)
+    psi = torch.zeros((S, 1 << N), dtype=torch.complex64, device="cuda")
+    psi[:, hf] = 1.0
+    dn = torch.ones(S, dtype=torch.float64, device="cuda")
+    for j in range(prep_k.shape[1]):
+        tq.evolve_taylor5_batch_support(ctx, pool, psi, torch.as_tensor(prep_k[:, j].copy()).cuda(),
+                                        torch.as_tensor(prep_th[:, j].copy()).cuda(), dn)
+    tq.evolve_taylor5_batch_support(ctx, pool, psi, torch.as_tensor(k).cuda(), torch.as_tensor(th).cuda(), dn)
+    torch.cuda.synchronize()
+    sample = [0, 1, 777, 4095, 4096, 8190, 8191] + list(np.random.default_rng(0).integers(0, S, 9))
+    for b in sample:
+        ref = oadapt.hf_state(N, ne, mp)
+        for j in range(prep_k.shape[1]):
+            ref = evolve.taylor5(oracle_A(n, ne, mp, int(prep_k[b, j])), ref, prep_th[b, j])
+        ref = evolve.taylor5(oracle_A(n, ne, mp, int(k[b])), ref, th[b])
+        out = psi[b].cpu().numpy().astype(np.complex128)
+        assert rel_l2(out, ref) <= 2e-6
+        assert fidelity(out, ref) > 0.999999
+        assert abs(dn[b].item() - np.vdot(ref, ref).real) <= 1e-6
+
+
+@pytest.mark.parametrize("prec", [tq.TQ_C128, tq.TQ_C64])
+def test_single_large_state_splits_tiles(ctx, prec):
+    """One 18-qubit state: the state is split over many tiles."""
+    import torch
+    n, ne, mp = 9, 8, 1
+    N = 18
+    pool = tq.build_pool(ctx, n, ne, mp)
+    for kk in (0, pool.M // 3, pool.M - 1):
+        psi = synth.random_state(N, 77 + kk)
+        dt = torch.complex128 if prec == tq.TQ_C128 else torch.complex64
+        d = torch.as_tensor(psi[None, :]).to(dt).cuda()
+        dn = torch.ones(1, dtype=torch.float64, device="cuda")
+        tq.evolve_taylor5_batch_support(ctx, pool, d, torch.as_tensor(np.array([kk], np.int32)).cuda(),
+                                        torch.as_tensor(np.array([0.37])).cuda(), dn, prec=prec)
+        torch.cuda.synchronize()
+        ref = evolve.taylor5(oracle_A(n, ne, mp, kk), psi, 0.37)
+        out = d[0].cpu().numpy().astype(np.complex128)
+        assert rel_l2(out, ref) <= (1e-12 if prec == tq.TQ_C128 else 2e-6)
+        assert abs(dn[0].item() - np.vdot(ref, ref).real) <= (1e-12 if prec == tq.TQ_C128 else 1e-6)
+
+
+def test_invalid_index_empty_batch_and_sector_pool(ctx):
+    import torch
+    pool = tq.build_pool(ctx, 4, 4, 0)
+    psi = torch.zeros((3, 256), dtype=torch.complex64, device="cuda")
+    psi[:, 5] = 1.0
+    before = psi.clone()
+    k = torch.as_tensor(np.array([0, pool.M, -1], dtype=np.int32)).cuda()
+    th = torch.as_tensor(np.array([0.1, 0.1, 0.1])).cuda()
+    n = torch.ones(3, dtype=torch.float64, device="cuda")
+    tq.evolve_taylor5_batch_support(ctx, pool, psi, k, th, n)
+    torch.cuda.synchronize()
+    assert np.isfinite(n[0].item()) and np.isnan(n[1].item()) and np.isnan(n[2].item())
+    assert torch.equal(psi[1:], before[1:])
+    empty = torch.zeros((0, 256), dtype=torch.complex64, device="cuda")
+    tq.evolve_taylor5_batch_support(ctx, pool, empty, k[:0], th[:0], None)
+    spool = tq.build_pool_sector(ctx, 4, 4, 0, 2, 2)
+    with pytest.raises(tq.TQError):
+        tq.evolve_taylor5_batch_support(ctx, spool, psi, k, th, n)
+    with pytest.raises(tq.TQError):
+        ctx.set_support_schedule(tq.TQ_C64, 3)
