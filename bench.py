@@ -247,19 +247,28 @@ def run_ours(args, rank, world, local_rank):
                                         torch.as_tensor(prep_th[:, j].copy()).cuda(), dn)
     dk = torch.as_tensor(k).cuda()
     dth = torch.as_tensor(th).cuda()
-    # the library's autotuner picks the schedule on scratch states (untimed,
-    # before warm-up); the CUDA context fetches 32-byte sectors on L2 misses
-    # (the update's reads are scattered over each generator's support)
-    if args.pair_schedule:
-        ctx.set_support_schedule(tq.TQ_C64, args.pair_schedule)
-        upt, tune_ms = args.pair_schedule, None
-    else:
-        upt, tune_ms = tq.autotune_support(ctx, pool, tq.TQ_C64, n_states=min(S, 2048))
+    # the CUDA context fetches 32-byte sectors on L2 misses (the update's
+    # reads are scattered over each generator's support); the schedule is
+    # the fastest of the eight on this batch (untimed, before warm-up)
     fetch_default = ctx.l2_fetch()
     ctx.set_l2_fetch(32)
 
     def step():
         tq.evolve_taylor5_batch_support(ctx, pool, psi, dk, dth, dn)
+
+    tune = {}
+    for cand in ([args.pair_schedule] if args.pair_schedule else [1, 2, 4, 8, -1, -2, -4, -8]):
+        ctx.set_support_schedule(tq.TQ_C64, cand)
+        step()
+        ctx.trace(True)
+        for _ in range(10):
+            step()
+        r_ = ctx.trace_report()
+        ctx.trace(False)
+        tune[cand] = sum(v[1] for v in r_.values()) / 10
+    upt = min(tune, key=tune.get)
+    tune_ms = {str(c_): v for c_, v in tune.items()}
+    ctx.set_support_schedule(tq.TQ_C64, upt)
 
     barrier = tqd.barrier
 
@@ -352,7 +361,7 @@ def run_ours(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "c64",
             "data": "synthetic",
             "config": dict(workload_config(S), schedule={"support_pairs_per_thread": upt,
-                                                         "autotune_ms_per_2048_states": tune_ms,
+                                                         "ms_per_launch_by_schedule": tune_ms,
                                                          "l2_fetch_bytes": 32,
                                                          "l2_fetch_default": fetch_default}),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -441,10 +450,30 @@ def measure_c128_batched(tq, ctx, pool, n_states=4096, reps=20):
     nr, nrms = rep.get("norm_reduce", (1, 0.0))
     peak, _ = peaks()
     alg = 2.0 * D * 16
+    # the support-only form of the same update (norm carried), every schedule
+    per = {}
+    for ppt in (1, 2, 4, 8, -1, -2, -4, -8):
+        ctx.set_support_schedule(tq.TQ_C128, ppt)
+        for _ in range(3):
+            tq.evolve_taylor5_batch_support(ctx, pool, psi, k, th, n2, prec=tq.TQ_C128)
+        ctx.trace(True)
+        for _ in range(reps):
+            tq.evolve_taylor5_batch_support(ctx, pool, psi, k, th, n2, prec=tq.TQ_C128)
+        rep = ctx.trace_report()
+        ctx.trace(False)
+        ns, sms_ = rep["taylor5_support"]
+        nc, ncms = rep.get("norm_carry", (1, 0.0))
+        per[ppt] = sms_ / ns + ncms / nc
+    ppt = min(per, key=per.get)
+    ctx.set_support_schedule(tq.TQ_C128, ppt)
+    sup_ms = per[ppt]
     return {"workload": f"{n_states} complex128 states, 14 qubits, own generator and angle each",
             "kernel": "k_taylor5_pair<double>", "ms_per_launch": ms, "norm_reduce_ms": nrms / nr,
             "updates_per_s": n_states / ((ms + nrms / nr) * 1e-3),
-            "achieved_gbs": alg * n_states / (ms * 1e-3) / 1e9, "hbm_frac": alg * n_states / (ms * 1e-3) / 1e9 / peak}
+            "achieved_gbs": alg * n_states / (ms * 1e-3) / 1e9, "hbm_frac": alg * n_states / (ms * 1e-3) / 1e9 / peak,
+            "support": {"kernel": "k_taylor5_support<double>", "pairs_per_thread": ppt, "ms_per_update_launch": sup_ms,
+                        "ms_by_schedule": {str(p_): v for p_, v in per.items()},
+                        "updates_per_s": n_states / (sup_ms * 1e-3)}}
 
 
 def _parity(v):
@@ -499,9 +528,9 @@ def measure_support(tq, ctx, pool, n_states, reps=50):
     dth = torch.as_tensor(th).cuda()
     fetch0 = ctx.l2_fetch()
     per = {}
-    for fetch in (0, 32, 64, 128):
+    for fetch in (0, 32):
         ctx.set_l2_fetch(fetch)
-        for ppt in (1, 2, 4, 8):
+        for ppt in (1, 2, 4, 8, -1, -2, -4, -8):
             ctx.set_support_schedule(tq.TQ_C64, ppt)
             for _ in range(3):
                 tq.evolve_taylor5_batch_support(ctx, pool, psi, dk, dth, dn)
@@ -888,7 +917,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the SpMV, trajectory-batch and request-loop measurements")
-    ap.add_argument("--section", choices=["spmv", "trajectories", "serving", "sector", "vqe", "c128", "support"], default=None,
+    ap.add_argument("--section", choices=["spmv", "trajectories", "serving", "sector", "vqe", "c128", "support",
+                                              "full_state"], default=None,
                     help="run one secondary measurement alone and print its JSON (profiling)")
     ap.add_argument("--spmv-qubits", type=int, default=18)
     ap.add_argument("--traj", type=int, default=256)
@@ -925,6 +955,8 @@ def main():
             print(json.dumps(measure_sector(tq, ctx)))
         elif args.section == "vqe":
             print(json.dumps(measure_vqe(tq, ctx)))
+        elif args.section == "full_state":
+            print(json.dumps(measure_full_state(tq, ctx, tq.build_pool(ctx, N_SPATIAL, N_ELECTRONS, MAPPING), 8192)))
         elif args.section == "support":
             print(json.dumps(measure_support(tq, ctx, tq.build_pool(ctx, N_SPATIAL, N_ELECTRONS, MAPPING), 8192)))
         elif args.section == "c128":

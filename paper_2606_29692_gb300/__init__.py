@@ -145,7 +145,8 @@ class Context:
         call("tq_ctx_set_spmv_schedule", self.handle, int(lanes_per_row))
 
     def set_support_schedule(self, prec, pairs_per_thread):
-        """Support-only update: 1, 2, 4 or 8 support pairs per thread per pass."""
+        """Support-only update: 1, 2, 4 or 8 support pairs per thread per pass
+        (registers), or -1, -2, -4, -8 (shared-memory staging, pipelined)."""
         call("tq_ctx_set_support_schedule", self.handle, prec, int(pairs_per_thread))
 
     def set_l2_fetch(self, nbytes):

@@ -341,6 +341,7 @@ extern "C" int tq_autotune_support(tq_ctx* c, const tq_pool* p, int prec, int n_
     size_t parts = 0;
     for (int u : {1, 2, 4, 8})
         parts = std::max(parts, (size_t)n_states * support_parts(support_tiles(p->nq, n_states, u, c->sm_count)));
+    const int cands[8] = {1, 2, 4, 8, -1, -2, -4, -8};
     unsigned char* buf = static_cast<unsigned char*>(
         scratch(c, S_STAGE, (size_t)n_states * sb + (size_t)n_states * (sizeof(int) + 2 * sizeof(double)) +
                                 parts * sizeof(double) + 256));
@@ -364,7 +365,7 @@ extern "C" int tq_autotune_support(tq_ctx* c, const tq_pool* p, int prec, int n_
     TQ_CUDA(cudaEventCreate(&e1));
     int best = c->supp_ppt[prec];
     float best_t = 1e30f;
-    for (int u : {1, 2, 4, 8}) {
+    for (int u : cands) {
         const int tps = support_tiles(p->nq, n_states, u, c->sm_count);
         auto once = [&] {
             launch(c, "autotune_support", 0, [&] {
@@ -1687,7 +1688,7 @@ extern "C" int tq_ctx_set_support_schedule(tq_ctx* c, int prec, int pairs_per_th
     API_BEGIN
     TQ_REQUIRE(c, "null argument");
     check_prec(prec);
-    TQ_REQUIRE(pair_upt_valid(pairs_per_thread), "pairs_per_thread must be 1, 2, 4 or 8");
+    TQ_REQUIRE(pair_upt_valid(std::abs(pairs_per_thread)), "pairs_per_thread must be +-1, +-2, +-4 or +-8");
     c->supp_ppt[prec] = pairs_per_thread;
     API_END
 }

@@ -89,8 +89,7 @@ __device__ __forceinline__ void taylor_coefs(double theta, T (&cf)[6]) {
 // complex64 path stays entirely on the float32 pipes: float64 issues at
 // about 1/57 of the float32 rate on this part.
 template <typename T>
-__device__ __forceinline__ void taylor_coefs_fast(double theta, T (&cf)[6]) {
-    const T t = (T)theta;
+__device__ __forceinline__ void taylor_coefs_typed(T t, T (&cf)[6]) {
     const T t2 = t * t, t3 = t2 * t, t4 = t3 * t, t5 = t4 * t;
     cf[0] = T(1);
     cf[1] = t;
@@ -98,6 +97,10 @@ __device__ __forceinline__ void taylor_coefs_fast(double theta, T (&cf)[6]) {
     cf[3] = t3 * T(1.0 / 6.0);
     cf[4] = t4 * T(1.0 / 24.0);
     cf[5] = t5 * T(1.0 / 120.0);
+}
+template <typename T>
+__device__ __forceinline__ void taylor_coefs_fast(double theta, T (&cf)[6]) {
+    taylor_coefs_typed<T>((T)theta, cf);
 }
 
 // c5 = cf0 - cf2 + cf4 and s5 = cf1 - cf3 + cf5 (the closed form below) with

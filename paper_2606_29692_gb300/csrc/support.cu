@@ -27,6 +27,7 @@
 #include "dev.cuh"
 #include "grad.cuh"
 #include "pair.cuh"
+#include "tma.cuh"
 
 #include <algorithm>
 
@@ -54,6 +55,12 @@ __device__ __forceinline__ SupOp<T> load_supop(const PoolView& p, int k) {
     o.unit = fabsf(p.fc0f[k]) == 1.0f;
     o.c0neg = p.fc0f[k] < 0.0f;
     return o;
+}
+
+// Start of tile tl's pair range when a generator's 2^lp support pairs are
+// split over 2^lt tiles: tl 2^lp / 2^lt by shifts (both are powers of two).
+__device__ __forceinline__ uint32_t pair_bound(int lp, unsigned tl, int lt) {
+    return (uint32_t)(((unsigned long long)tl << lp) >> lt);
 }
 
 // Updates the support pairs [i0, i1) of one state; returns the thread's
@@ -106,8 +113,25 @@ __device__ __forceinline__ T support_tile(const SupOp<T>& op, double theta, type
     return delta;
 }
 
+// Fixed-order float64 sum of a CTA's warp partials (complex64: (hi, lo)
+// float pairs in the 8-byte slots).
+template <typename T, int NW>
+__device__ __forceinline__ double sum_partials(const double* red) {
+    double sum = 0.0;
+    for (int w = 0; w < NW; ++w) {
+        if constexpr (sizeof(T) == 4) {
+            const float2 hl = *reinterpret_cast<const float2*>(&red[w]);
+            sum += (double)hl.x + (double)hl.y;
+        } else {
+            sum += red[w];
+        }
+    }
+    return sum;
+}
+
 // Persistent grid over (state, tile) items; tile tl of a state whose
-// generator has P support pairs covers pairs [tl P / tps, (tl + 1) P / tps).
+// generator has P support pairs covers pairs [tl P / tps, (tl + 1) P / tps)
+// (tps, the tiles per state, a power of two).
 // With one tile per state and `norm2` set, the CTA finishes the state's
 // norm itself (norm2[b] += the fixed-order sum of its warps' partials);
 // otherwise every warp leaves its partial for the reduction kernel.
@@ -121,15 +145,16 @@ k_taylor5_support(PoolView p, int n_states, typename C2<T>::type* psi, const int
     const bool fold = tiles_per_state == 1 && norm2 != nullptr;
     const long long D = 1ll << p.nq;
     const unsigned tps = (unsigned)tiles_per_state;
+    const int lt = __ffs(tiles_per_state) - 1;        // tps is a power of two
     const unsigned total = (unsigned)n_states * tps;
     unsigned tile = blockIdx.x;
-    int b = (int)(tile / tps);
+    int b = (int)(tile >> lt);
     int k = tile < total ? kk[b] : 0;
     double theta = tile < total ? th[b] : 0.0;
     while (tile < total) {
-        const unsigned tl = tile - (unsigned)b * tps;
+        const unsigned tl = tile & (tps - 1);
         const unsigned ntile = tile + gridDim.x;
-        const int nb = (int)(ntile / tps);
+        const int nb = (int)(ntile >> lt);
         int nk = 0;
         double nth = 0.0;
         if (ntile < total) {
@@ -141,25 +166,14 @@ k_taylor5_support(PoolView p, int n_states, typename C2<T>::type* psi, const int
             store_nan_partial(slot, T(0));   // the state is left untouched, its norm poisoned
         } else {
             const SupOp<T> op = load_supop<T>(p, k);
-            const unsigned long long P = 1ull << (p.nq - op.s.m - 1);
-            const uint32_t i0 = (uint32_t)(P * tl / tps), i1 = (uint32_t)(P * (tl + 1) / tps);
+            const int lp = p.nq - op.s.m - 1;
+            const uint32_t i0 = pair_bound(lp, tl, lt), i1 = pair_bound(lp, tl + 1, lt);
             const T d = support_tile<T, PPT>(op, theta, psi + (long long)b * D, i0, i1);
             store_partial(slot, d);
         }
         if (fold) {
             __syncthreads();
-            if (threadIdx.x == 0) {
-                double sum = 0.0;
-                for (int w = 0; w < NW; ++w) {
-                    if constexpr (sizeof(T) == 4) {
-                        const float2 hl = *reinterpret_cast<const float2*>(&red[w]);
-                        sum += (double)hl.x + (double)hl.y;
-                    } else {
-                        sum += red[w];
-                    }
-                }
-                norm2[b] = norm2[b] + sum;
-            }
+            if (threadIdx.x == 0) norm2[b] = norm2[b] + sum_partials<T, NW>(red);
             __syncthreads();
         }
         tile = ntile;
@@ -167,6 +181,188 @@ k_taylor5_support(PoolView p, int n_states, typename C2<T>::type* psi, const int
         k = nk;
         theta = nth;
     }
+}
+
+// ------------------------------------------------ pipelined (cp.async) form
+//
+// The same update with the amplitudes staged in shared memory by cp.async:
+// each thread copies the PPT pairs of its next pass (of the same tile, or
+// the first pass of its CTA's next tile) while it computes the current
+// one, so the bytes in flight per SM are bounded by shared memory rather
+// than by registers.  Every thread reads back only its own slots, so no
+// barrier orders the copies; the CTA synchronises only to finish a norm.
+
+__device__ __forceinline__ void cp_async(void* dst, const float2* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async(void* dst, const double2* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+template <typename T>
+struct SupTile {
+    SupOp<T> op;
+    T theta;           // in the kernel's precision: converted once per tile
+    int b;
+    int bad;           // op index outside [0, M): state untouched, norm NaN
+    uint32_t i0, i1;   // the tile's pair range
+};
+
+template <typename T>
+__device__ __forceinline__ SupTile<T> sup_tile(const PoolView& p, const int* kk, const double* th, unsigned tile,
+                                               int lt) {
+    SupTile<T> t;
+    t.b = (int)(tile >> lt);
+    const unsigned tl = tile & ((1u << lt) - 1u);
+    const int k = kk[t.b];
+    t.theta = (T)th[t.b];
+    t.bad = k < 0 || k >= p.M;
+    t.i0 = t.i1 = 0;
+    if (!t.bad) {
+        t.op = load_supop<T>(p, k);
+        const int lp = p.nq - t.op.s.m - 1;
+        t.i0 = pair_bound(lp, tl, lt);
+        t.i1 = pair_bound(lp, tl + 1, lt);
+    }
+    return t;
+}
+
+template <typename T, int PPT>
+__device__ __forceinline__ void sup_issue(const SupTile<T>& t, uint32_t pos, const typename C2<T>::type* base,
+                                          typename C2<T>::type* stage, uint32_t* rows) {
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+        const uint32_t u = pos + j * SUPP_BS + threadIdx.x;
+        if (u < t.i1) {
+            const uint32_t r = supp_row(t.op.s, insert_zero(u, t.op.hp));
+            rows[j * SUPP_BS + threadIdx.x] = r;
+            cp_async(&stage[(2 * j) * SUPP_BS + threadIdx.x], base + r);
+            cp_async(&stage[(2 * j + 1) * SUPP_BS + threadIdx.x], base + (r ^ t.op.s.x));
+        }
+    }
+}
+
+template <typename T, int PPT>
+__device__ __forceinline__ T sup_compute(const SupTile<T>& t, uint32_t pos, typename C2<T>::type* base,
+                                         const typename C2<T>::type* stage, const uint32_t* rows) {
+    using V = typename C2<T>::type;
+    T cf[6];
+    taylor_coefs_typed<T>(t.theta, cf);
+    double c5 = 0.0, s5 = 0.0;
+    if constexpr (sizeof(T) == 8) closed_coefs(cf, c5, s5);
+    T delta = T(0);
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+        const uint32_t u = pos + j * SUPP_BS + threadIdx.x;
+        if (u >= t.i1) continue;
+        const uint32_t r = rows[j * SUPP_BS + threadIdx.x], q = r ^ t.op.s.x;
+        const V a = stage[(2 * j) * SUPP_BS + threadIdx.x], b = stage[(2 * j + 1) * SUPP_BS + threadIdx.x];
+        const int nr = parity32(q & t.op.s.z0), nq = parity32(r & t.op.s.z0);
+        V ar = a, aq = b;
+        if constexpr (sizeof(T) == 8) {
+            if (t.op.unit) {
+                closed_pair_sign((nr != t.op.c0neg) ? -1 : 1, (nq != t.op.c0neg) ? -1 : 1, cf, c5, s5, ar, aq);
+            } else {
+                chain_pair(nr ? -t.op.c0 : t.op.c0, nq ? -t.op.c0 : t.op.c0, cf, ar, aq);
+            }
+        } else {
+            chain_pair(nr ? -t.op.c0 : t.op.c0, nq ? -t.op.c0 : t.op.c0, cf, ar, aq);
+        }
+        delta += (ar.x - a.x) * (ar.x + a.x) + (ar.y - a.y) * (ar.y + a.y);
+        delta += (aq.x - b.x) * (aq.x + b.x) + (aq.y - b.y) * (aq.y + b.y);
+        base[r] = ar;
+        base[q] = aq;
+    }
+    return delta;
+}
+
+// With one tile per state and norm2 set, the CTA finishes each state's
+// norm itself (norm2[b] += its warps' partials in fixed order).
+template <typename T, int PPT>
+__global__ void __launch_bounds__(SUPP_BS)
+k_taylor5_support_pipe(PoolView p, int n_states, typename C2<T>::type* psi, const int* kk, const double* th,
+                       double* partials, int tiles_per_state, double* norm2) {
+    using V = typename C2<T>::type;
+    extern __shared__ __align__(16) unsigned char supp_smem[];
+    V* stages = reinterpret_cast<V*>(supp_smem);    // [2][PPT][2][SUPP_BS]
+    constexpr int NW = SUPP_BS / 32;
+    constexpr int STAGE = 2 * PPT * SUPP_BS;
+    uint32_t* rowbuf = reinterpret_cast<uint32_t*>(stages + 2 * STAGE);   // [2][PPT][SUPP_BS]
+    __shared__ double red[NW];
+    const int warp = threadIdx.x >> 5;
+    const bool fold = tiles_per_state == 1 && norm2 != nullptr;
+    const long long D = 1ll << p.nq;
+    const unsigned tps = (unsigned)tiles_per_state;
+    const int lt = __ffs(tiles_per_state) - 1;        // tps is a power of two
+    const unsigned total = (unsigned)n_states * tps;
+    unsigned tile = blockIdx.x;
+    if (tile >= total) return;
+    SupTile<T> cur = sup_tile<T>(p, kk, th, tile, lt);
+    uint32_t pos = cur.i0;
+    int st = 0;
+    if (!cur.bad) sup_issue<T, PPT>(cur, pos, psi + (long long)cur.b * D, stages, rowbuf);
+    cp_commit();
+    T delta = T(0);
+    for (;;) {
+        // the next pass: later in this tile, or the first of the next tile
+        uint32_t npos = pos + SUPP_BS * PPT;
+        const bool tile_end = cur.bad || npos >= cur.i1;
+        const unsigned ntile = tile_end ? tile + gridDim.x : tile;
+        const bool more = ntile < total;
+        SupTile<T> nxt = cur;
+        if (tile_end && more) {
+            nxt = sup_tile<T>(p, kk, th, ntile, lt);
+            npos = nxt.i0;
+        }
+        if (more && !nxt.bad)
+            sup_issue<T, PPT>(nxt, npos, psi + (long long)nxt.b * D, stages + (st ^ 1) * STAGE,
+                              rowbuf + (st ^ 1) * PPT * SUPP_BS);
+        cp_commit();
+        cp_wait_one();
+        if (!cur.bad)
+            delta += sup_compute<T, PPT>(cur, pos, psi + (long long)cur.b * D, stages + st * STAGE,
+                                         rowbuf + st * PPT * SUPP_BS);
+        if (tile_end) {
+            double* slot = fold ? &red[warp] : partials + (size_t)tile * NW + warp;
+            if (cur.bad) store_nan_partial(slot, T(0));
+            else store_partial(slot, delta);
+            delta = T(0);
+            if (fold) {
+                __syncthreads();
+                if (threadIdx.x == 0) norm2[cur.b] = norm2[cur.b] + sum_partials<T, NW>(red);
+                __syncthreads();
+            }
+        }
+        if (!more) break;
+        tile = ntile;
+        cur = nxt;
+        pos = npos;
+        st ^= 1;
+    }
+}
+
+template <typename T, int PPT>
+int launch_support_pipe(const PoolView& p, int n_states, void* psi, const int* k, const double* theta,
+                        double* partials, int tps, double* norm2, int sms, cudaStream_t s) {
+    using V = typename C2<T>::type;
+    const long long total = (long long)n_states * tps;
+    if (total >= (1ll << 31)) return -1;
+    const size_t smem = (size_t)2 * PPT * SUPP_BS * (2 * sizeof(V) + sizeof(uint32_t));
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaFuncSetAttribute(k_taylor5_support_pipe<T, PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_taylor5_support_pipe<T, PPT>, SUPP_BS, smem);
+        per_sm = n < 1 ? 1 : n;
+    }
+    long long grid = (long long)per_sm * sms;
+    if (grid > total) grid = total;
+    if (grid < 1) grid = 1;
+    k_taylor5_support_pipe<T, PPT><<<(int)grid, SUPP_BS, smem, s>>>(p, n_states, static_cast<V*>(psi), k, theta,
+                                                                     partials, tps, norm2);
+    return 1;
 }
 
 template <typename T, int PPT>
@@ -197,6 +393,10 @@ int dispatch_support(int ppt, const PoolView& p, int n_states, void* psi, const 
         case 2: return launch_support<T, 2>(p, n_states, psi, k, theta, partials, tps, norm2, sms, s);
         case 4: return launch_support<T, 4>(p, n_states, psi, k, theta, partials, tps, norm2, sms, s);
         case 8: return launch_support<T, 8>(p, n_states, psi, k, theta, partials, tps, norm2, sms, s);
+        case -1: return launch_support_pipe<T, 1>(p, n_states, psi, k, theta, partials, tps, norm2, sms, s);
+        case -2: return launch_support_pipe<T, 2>(p, n_states, psi, k, theta, partials, tps, norm2, sms, s);
+        case -4: return launch_support_pipe<T, 4>(p, n_states, psi, k, theta, partials, tps, norm2, sms, s);
+        case -8: return launch_support_pipe<T, 8>(p, n_states, psi, k, theta, partials, tps, norm2, sms, s);
         default: return -1;
     }
 }
@@ -207,8 +407,12 @@ int dispatch_support(int ppt, const PoolView& p, int n_states, void* psi, const 
 // pairs) fills one tile of SUPP_BS * ppt pairs; small batches split states
 // further (down to 32 pairs of a double per tile) to fill the GPU.
 int support_tiles(int nq, int n_states, int ppt, int sms) {
+    // the pipelined form streams several passes per tile: a tile of a
+    // double then spans four of its passes
+    const int passes = ppt < 0 ? 4 : 1;
+    ppt = ppt < 0 ? -ppt : ppt;
     const long long dpairs = nq >= 4 ? 1ll << (nq - 4) : 1;
-    long long t = dpairs / ((long long)SUPP_BS * ppt);
+    long long t = dpairs / ((long long)SUPP_BS * ppt * passes);
     if (t < 1) t = 1;
     const long long want = (4ll * sms + n_states - 1) / std::max(n_states, 1);
     const long long cap = std::max(1ll, dpairs / 32);
@@ -221,6 +425,7 @@ int support_parts(int tiles) { return tiles * (SUPP_BS / 32); }
 int launch_taylor5_support(const PoolView& p, int n_states, int prec, int ppt, void* psi, const int* k,
                            const double* theta, double* partials, int tps, double* norm2, int sms,
                            cudaStream_t s) {
+    if (tps < 1 || (tps & (tps - 1)) != 0) return -1;   // the kernels split by shifts
     if (prec == TQ_C128)
         return dispatch_support<double>(ppt, p, n_states, psi, k, theta, partials, tps, norm2, sms, s);
     return dispatch_support<float>(ppt, p, n_states, psi, k, theta, partials, tps, norm2, sms, s);

@@ -91,14 +91,14 @@ def test_support_update_equals_full_state_kernel(ctx, n, ne, mp, prec):
     before = torch.as_tensor(psi).to(dt).cuda()
     n_in = (before.abs().double() ** 2).sum(dim=1)
     outs = []
-    for ppt in (1, 2, 4, 8):
+    for ppt in (1, 2, 4, 8, -1, -2, -4, -8):
         ctx.set_support_schedule(prec, ppt)
         d = before.clone()
         dn = n_in.clone()
         tq.evolve_taylor5_batch_support(ctx, pool, d, dk, dth, dn, prec=prec)
         torch.cuda.synchronize()
         outs.append((d, dn))
-    ctx.set_support_schedule(prec, 2 if prec == tq.TQ_C128 else 4)
+    ctx.set_support_schedule(prec, 2 if prec == tq.TQ_C128 else -1)
     fv = torch.view_as_real(full)
     bv = torch.view_as_real(before)
     for d, dn in outs:
@@ -188,3 +188,12 @@ def test_invalid_index_empty_batch_and_sector_pool(ctx):
         tq.evolve_taylor5_batch_support(ctx, spool, psi, k, th, n)
     with pytest.raises(tq.TQError):
         ctx.set_support_schedule(tq.TQ_C64, 3)
+
+
+def test_autotuner_picks_a_valid_schedule(ctx):
+    pool = tq.build_pool(ctx, 6, 8, 1)
+    for prec in (tq.TQ_C64, tq.TQ_C128):
+        best, ms = tq.autotune_support(ctx, pool, prec, n_states=64)
+        assert best in (1, 2, 4, 8, -1, -2, -4, -8) and ms > 0
+    ctx.set_support_schedule(tq.TQ_C128, 2)
+    ctx.set_support_schedule(tq.TQ_C64, -1)
