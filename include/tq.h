@@ -520,6 +520,19 @@ int tq_evolve_taylor5_batch_support(tq_ctx* ctx, const tq_pool* pool,
                                     const int* k, const double* theta,
                                     double* norm2, void* stream);
 
+/* The support-only update on states in HOST memory, read and written in
+ * place by the kernel over the host link (NVLink-C2C on Grace-Blackwell):
+ * only the support sectors cross it.  psi_host must be page-locked and
+ * mapped for the device (cudaHostAlloc, or cudaHostRegister with the
+ * mapped flag), else TQ_EINVAL before any launch.  k_host, theta_host and
+ * norm2_host (in/out as above, optional) are ordinary host arrays, copied.
+ * Synchronises. */
+int tq_evolve_taylor5_batch_support_host(tq_ctx* ctx, const tq_pool* pool,
+                                         int n_states, int prec,
+                                         void* psi_host, const int* k_host,
+                                         const double* theta_host,
+                                         double* norm2_host);
+
 /* Schedule of the support-only update: support pairs per thread per pass,
  * 1, 2, 4 or 8 with the amplitudes held in registers, or -1, -2, -4, -8
  * with them staged in shared memory by asynchronous copies that run one

@@ -538,6 +538,15 @@ def evolve_taylor5_batch_support(ctx, pool, psi, k, theta, norm2=None, prec=TQ_C
          _ptr(theta), _ptr(norm2), _stream(stream))
 
 
+def evolve_taylor5_batch_support_host(ctx, pool, psi, k, theta, norm2=None, prec=TQ_C64):
+    """Support-only update of states in page-locked HOST memory (a pinned
+    torch CPU tensor), read and written in place by the kernel; k, theta and
+    norm2 (in/out) are host arrays."""
+    n_states = psi.shape[0]
+    call("tq_evolve_taylor5_batch_support_host", ctx.handle, pool.handle, n_states, prec, _ptr(psi), _ptr(k),
+         _ptr(theta), _ptr(norm2))
+
+
 def evolve_taylor5_batch_host(ctx, pool, psi, k, theta, norm2=None, prec=TQ_C64):
     """Batched update of HOST arrays (numpy or pinned torch CPU tensors)."""
     n_states = psi.shape[0]

@@ -105,6 +105,7 @@ SIGNATURES = {
     "tq_adapt_step": [vp, vp, vp, vp, f64, f64, P(AdaptResult), vp],
     "tq_evolve_taylor5_batch": [vp, vp, i32, i32, vp, vp, vp, vp, vp],
     "tq_evolve_taylor5_batch_support": [vp, vp, i32, i32, vp, vp, vp, vp, vp],
+    "tq_evolve_taylor5_batch_support_host": [vp, vp, i32, i32, vp, vp, vp, vp],
     "tq_ctx_set_support_schedule": [vp, i32, i32],
     "tq_autotune_support": [vp, vp, i32, i32, P(i32), P(f64)],
     "tq_ctx_set_l2_fetch": [vp, i32],

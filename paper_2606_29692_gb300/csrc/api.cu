@@ -46,7 +46,7 @@ unsigned* tickets(tq_ctx* c, size_t n) {
     return c->tickets;
 }
 
-enum { S_PART = 0, S_W0, S_U1, S_U2, S_W1, S_W2, S_G, S_STAGE, S_W32, S_PHI, S_CHI, S_AG };
+enum { S_PART = 0, S_W0, S_U1, S_U2, S_W1, S_W2, S_G, S_STAGE, S_W32, S_PHI, S_CHI, S_AG, S_HOSTB };
 
 void run_energy(tq_ctx* c, const tq_ham* h, const tq_state* psi, double* part, cudaStream_t s);
 double* prepare(tq_ctx* c, long long D, const tq_pool* p, int nq);
@@ -1681,6 +1681,54 @@ extern "C" int tq_evolve_taylor5_batch_support(tq_ctx* c, const tq_pool* p, int 
     });
     if (norm2 && tps > 1)
         launch(c, "norm_carry", s, [&] { return launch_norm_carry(part, prec, n_states, parts, norm2, norm2, nullptr, s); });
+    API_END
+}
+
+extern "C" int tq_evolve_taylor5_batch_support_host(tq_ctx* c, const tq_pool* p, int n_states, int prec,
+                                                    void* psi_host, const int* k_host, const double* theta_host,
+                                                    double* norm2_host) {
+    API_BEGIN
+    TQ_REQUIRE(c && p, "null argument");
+    TQ_REQUIRE(!p->sector, "the support-only update takes full-space pools (sector states: tq_evolve_taylor5_batch)");
+    TQ_REQUIRE(n_states >= 0, "n_states < 0");
+    check_prec(prec);
+    if (n_states == 0) return TQ_OK;   // an empty batch is a no-op
+    TQ_REQUIRE(psi_host && k_host && theta_host, "null argument");
+    TQ_REQUIRE(((uintptr_t)psi_host & 15u) == 0, "psi must be 16-byte aligned");
+    set_device(c);
+    // the kernel reads and writes the states where they are, over the
+    // host link: they must be page-locked and mapped for this device
+    cudaPointerAttributes attr{};
+    const cudaError_t ae = cudaPointerGetAttributes(&attr, psi_host);
+    if (ae != cudaSuccess) (void)cudaGetLastError();
+    TQ_REQUIRE(ae == cudaSuccess && attr.type == cudaMemoryTypeHost && attr.devicePointer != nullptr,
+               "psi_host must be page-locked host memory mapped for the device (cudaHostAlloc / cudaHostRegister)");
+    void* psi = attr.devicePointer;
+    cudaStream_t s = c->aux[0];
+    if (!s) TQ_CUDA(cudaStreamCreateWithFlags(&c->aux[0], cudaStreamNonBlocking));
+    s = c->aux[0];
+    const int ppt = c->supp_ppt[prec];
+    const int tps = support_tiles(p->nq, n_states, ppt, c->sm_count);
+    const int parts = support_parts(tps);
+    unsigned char* buf = static_cast<unsigned char*>(
+        scratch(c, S_HOSTB, (size_t)n_states * (sizeof(int) + 2 * sizeof(double)) + 64));
+    int* dk = reinterpret_cast<int*>(buf);
+    double* dth = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(dk + n_states) + 15) & ~(uintptr_t)15);
+    double* dn = dth + n_states;
+    double* part = static_cast<double*>(scratch(c, S_PART, (size_t)n_states * parts * sizeof(double)));
+    TQ_CUDA(cudaMemcpyAsync(dk, k_host, (size_t)n_states * sizeof(int), cudaMemcpyHostToDevice, s));
+    TQ_CUDA(cudaMemcpyAsync(dth, theta_host, (size_t)n_states * sizeof(double), cudaMemcpyHostToDevice, s));
+    if (norm2_host)
+        TQ_CUDA(cudaMemcpyAsync(dn, norm2_host, (size_t)n_states * sizeof(double), cudaMemcpyHostToDevice, s));
+    double* n2 = norm2_host ? dn : nullptr;
+    launch(c, "taylor5_support_host", s, [&] {
+        return launch_taylor5_support(p->view, n_states, prec, ppt, psi, dk, dth, part, tps, n2, c->sm_count, s);
+    });
+    if (n2 && tps > 1)
+        launch(c, "norm_carry", s, [&] { return launch_norm_carry(part, prec, n_states, parts, n2, n2, nullptr, s); });
+    if (norm2_host)
+        TQ_CUDA(cudaMemcpyAsync(norm2_host, dn, (size_t)n_states * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TQ_CUDA(cudaStreamSynchronize(s));
     API_END
 }
 

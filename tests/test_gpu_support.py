@@ -197,3 +197,29 @@ def test_autotuner_picks_a_valid_schedule(ctx):
         assert best in (1, 2, 4, 8, -1, -2, -4, -8) and ms > 0
     ctx.set_support_schedule(tq.TQ_C128, 2)
     ctx.set_support_schedule(tq.TQ_C64, -1)
+
+
+@pytest.mark.parametrize("prec", [tq.TQ_C128, tq.TQ_C64])
+def test_states_in_host_memory(ctx, prec):
+    """The same update on page-locked host states, read and written in
+    place by the kernel: bit-identical to the device-memory path."""
+    import torch
+    n, ne, mp = 7, 6, 1
+    pool = tq.build_pool(ctx, n, ne, mp)
+    S = 40
+    psi, k, th, dt = _inputs(14, S, pool.M, 91, prec)
+    dev = torch.as_tensor(psi).to(dt).cuda()
+    n_in = (dev.abs().double() ** 2).sum(dim=1)
+    dn = n_in.clone()
+    tq.evolve_taylor5_batch_support(ctx, pool, dev, torch.as_tensor(k).cuda(), torch.as_tensor(th).cuda(), dn,
+                                    prec=prec)
+    host = torch.as_tensor(psi).to(dt).pin_memory()
+    hn = n_in.cpu().clone()
+    tq.evolve_taylor5_batch_support_host(ctx, pool, host, k, th, hn.numpy(), prec=prec)
+    torch.cuda.synchronize()
+    assert torch.equal(torch.view_as_real(host), torch.view_as_real(dev.cpu()))
+    assert torch.equal(hn, dn.cpu())
+    # memory the device cannot reach is refused before any launch
+    with pytest.raises(tq.TQError):
+        tq.evolve_taylor5_batch_support_host(ctx, pool, torch.as_tensor(psi).to(dt).numpy(), k, th, None,
+                                             prec=prec)
