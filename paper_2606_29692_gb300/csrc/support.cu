@@ -63,6 +63,38 @@ __device__ __forceinline__ uint32_t pair_bound(int lp, unsigned tl, int lt) {
     return (uint32_t)(((unsigned long long)tl << lp) >> lt);
 }
 
+// The update of one support pair (r, q = r ^ x) with nr, nq the sign bits of
+// A[r][q] and A[q][r].  Returns true when the pair took the complex128
+// closed form (entries +-1, A[q][r] = -A[r][q], so A^2 = -I on the pair):
+// there |psi'_r|^2 + |psi'_q|^2 = (c5^2 + s5^2)(|psi_r|^2 + |psi_q|^2)
+// exactly, and the caller adds the norm change in closed form.
+template <typename T>
+__device__ __forceinline__ bool sup_pair(const SupOp<T>& op, int nr, int nq, const T (&cf)[6], double c5,
+                                         double s5, typename C2<T>::type& ar, typename C2<T>::type& aq) {
+    if constexpr (sizeof(T) == 8) {
+        if (op.unit && nr != nq) {
+            const int sr = (nr != op.c0neg) ? -1 : 1;
+            closed_pair_sign(sr, -sr, cf, c5, s5, ar, aq);
+            return true;
+        }
+    }
+    chain_pair(nr ? -op.c0 : op.c0, nq ? -op.c0 : op.c0, cf, ar, aq);
+    return false;
+}
+
+__device__ __forceinline__ double pair_norm2(double2 a, double2 b, double acc) {
+    return fma(a.x, a.x, fma(a.y, a.y, fma(b.x, b.x, fma(b.y, b.y, acc))));
+}
+__device__ __forceinline__ double pair_norm2(float2, float2, double acc) { return acc; }
+
+// c5^2 + s5^2 - 1 for the fifth-order series of a generator with A^2 = -I:
+// theta^6/360 - theta^8/960 + theta^10/14400, without the cancellation of
+// forming c5^2 + s5^2 first.
+__device__ __forceinline__ double norm_growth(double theta) {
+    const double t2 = theta * theta, t6 = t2 * t2 * t2;
+    return t6 * fma(t2, fma(t2, 1.0 / 14400.0, -1.0 / 960.0), 1.0 / 360.0);
+}
+
 // Updates the support pairs [i0, i1) of one state; returns the thread's
 // sum of |psi'|^2 - |psi|^2.
 template <typename T, int PPT>
@@ -74,6 +106,7 @@ __device__ __forceinline__ T support_tile(const SupOp<T>& op, double theta, type
     double c5 = 0.0, s5 = 0.0;
     if constexpr (sizeof(T) == 8) closed_coefs(cf, c5, s5);
     T delta = T(0);
+    double nsq = 0.0;   // complex128 closed-form pairs: sum of |psi|^2 before the update
     for (uint32_t i = i0 + threadIdx.x; i < i1; i += SUPP_BS * PPT) {
         uint32_t rr[PPT];
         V a[PPT], b[PPT];
@@ -94,22 +127,17 @@ __device__ __forceinline__ T support_tile(const SupOp<T>& op, double theta, type
             const uint32_t r = rr[j], q = r ^ op.s.x;
             const int nr = parity32(q & op.s.z0), nq = parity32(r & op.s.z0);   // signs of A[r][q], A[q][r]
             V ar = a[j], aq = b[j];
-            if constexpr (sizeof(T) == 8) {
-                if (op.unit) {
-                    const int sr = (nr != op.c0neg) ? -1 : 1, sq = (nq != op.c0neg) ? -1 : 1;
-                    closed_pair_sign(sr, sq, cf, c5, s5, ar, aq);
-                } else {
-                    chain_pair(nr ? -op.c0 : op.c0, nq ? -op.c0 : op.c0, cf, ar, aq);
-                }
+            if (sup_pair<T>(op, nr, nq, cf, c5, s5, ar, aq)) {
+                nsq = pair_norm2(a[j], b[j], nsq);
             } else {
-                chain_pair(nr ? -op.c0 : op.c0, nq ? -op.c0 : op.c0, cf, ar, aq);
+                delta += (ar.x - a[j].x) * (ar.x + a[j].x) + (ar.y - a[j].y) * (ar.y + a[j].y);
+                delta += (aq.x - b[j].x) * (aq.x + b[j].x) + (aq.y - b[j].y) * (aq.y + b[j].y);
             }
-            delta += (ar.x - a[j].x) * (ar.x + a[j].x) + (ar.y - a[j].y) * (ar.y + a[j].y);
-            delta += (aq.x - b[j].x) * (aq.x + b[j].x) + (aq.y - b[j].y) * (aq.y + b[j].y);
             base[r] = ar;
             base[q] = aq;
         }
     }
+    if constexpr (sizeof(T) == 8) delta += norm_growth(theta) * nsq;
     return delta;
 }
 
@@ -253,6 +281,7 @@ __device__ __forceinline__ T sup_compute(const SupTile<T>& t, uint32_t pos, type
     double c5 = 0.0, s5 = 0.0;
     if constexpr (sizeof(T) == 8) closed_coefs(cf, c5, s5);
     T delta = T(0);
+    double nsq = 0.0;
 #pragma unroll
     for (int j = 0; j < PPT; ++j) {
         const uint32_t u = pos + j * SUPP_BS + threadIdx.x;
@@ -261,20 +290,16 @@ __device__ __forceinline__ T sup_compute(const SupTile<T>& t, uint32_t pos, type
         const V a = stage[(2 * j) * SUPP_BS + threadIdx.x], b = stage[(2 * j + 1) * SUPP_BS + threadIdx.x];
         const int nr = parity32(q & t.op.s.z0), nq = parity32(r & t.op.s.z0);
         V ar = a, aq = b;
-        if constexpr (sizeof(T) == 8) {
-            if (t.op.unit) {
-                closed_pair_sign((nr != t.op.c0neg) ? -1 : 1, (nq != t.op.c0neg) ? -1 : 1, cf, c5, s5, ar, aq);
-            } else {
-                chain_pair(nr ? -t.op.c0 : t.op.c0, nq ? -t.op.c0 : t.op.c0, cf, ar, aq);
-            }
+        if (sup_pair<T>(t.op, nr, nq, cf, c5, s5, ar, aq)) {
+            nsq = pair_norm2(a, b, nsq);
         } else {
-            chain_pair(nr ? -t.op.c0 : t.op.c0, nq ? -t.op.c0 : t.op.c0, cf, ar, aq);
+            delta += (ar.x - a.x) * (ar.x + a.x) + (ar.y - a.y) * (ar.y + a.y);
+            delta += (aq.x - b.x) * (aq.x + b.x) + (aq.y - b.y) * (aq.y + b.y);
         }
-        delta += (ar.x - a.x) * (ar.x + a.x) + (ar.y - a.y) * (ar.y + a.y);
-        delta += (aq.x - b.x) * (aq.x + b.x) + (aq.y - b.y) * (aq.y + b.y);
         base[r] = ar;
         base[q] = aq;
     }
+    if constexpr (sizeof(T) == 8) delta += norm_growth((double)t.theta) * nsq;
     return delta;
 }
 
