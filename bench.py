@@ -569,6 +569,15 @@ def measure_support(tq, ctx, pool, n_states, reps=50):
             per[(fetch, ppt)] = (ms / n_l, ncms / nc)
     best_f, best = min(per, key=lambda fp: per[fp][0] + per[fp][1])
     ctx.set_support_schedule(tq.TQ_C64, best)
+    # the same launch without the norm (the finish's share of the time)
+    ctx.set_l2_fetch(best_f)
+    ctx.trace(True)
+    for _ in range(reps):
+        tq.evolve_taylor5_batch_support(ctx, pool, psi, dk, dth, None)
+    rep = ctx.trace_report()
+    ctx.trace(False)
+    n_l, ms_nn = rep["taylor5_support"]
+    ms_no_norm = ms_nn / n_l
     ctx.set_l2_fetch(0)
     ms, ncms = per[(best_f, best)]
     rows = support_rows(tq, N_SPATIAL, N_ELECTRONS, MAPPING)
@@ -583,7 +592,8 @@ def measure_support(tq, ctx, pool, n_states, reps=50):
             "kernel": "k_taylor5_support<float>", "pairs_per_thread": best,
             "l2_fetch_bytes": best_f or fetch0, "l2_fetch_default": fetch0,
             "ms_by_fetch_and_schedule": {f"{f or fetch0}B/{p}": v[0] + v[1] for (f, p), v in per.items()},
-            "ms_per_launch": ms, "norm_carry_ms": ncms, "updates_per_s": n_states / ((ms + ncms) * 1e-3),
+            "ms_per_launch": ms, "norm_carry_ms": ncms, "ms_per_launch_without_norm": ms_no_norm,
+            "updates_per_s": n_states / ((ms + ncms) * 1e-3),
             "algorithmic_bytes_per_launch": alg, "sector_bytes_per_launch": sect,
             "mean_support_rows": float(n_rows[k].mean()), "achieved_gbs": gbs, "peak_gbs": peak,
             "frac": gbs / peak, "sector_gbs": sect / (ms * 1e-3) / 1e9,

@@ -18,12 +18,13 @@
 // wherever the low bits are free, so a warp's loads stay coalesced.
 //
 // The squared norm is carried, not recomputed: on exit
-// ||psi'||^2 = ||psi||^2 + sum_S (|psi'_r|^2 - |psi_r|^2), each difference
-// formed as (a' - a)(a' + a) per component, so the small change keeps its
-// relative accuracy.  The five products run exactly as in the full-state
-// kernel (complex64: packed float32 chain; complex128 with entries +-1:
-// the closed form c5 psi + s5 A psi), so the two kernels give equal
-// amplitudes.
+// ||psi'||^2 = ||psi||^2 + sum_S (|psi'_r|^2 - |psi_r|^2).  In complex64
+// each difference is formed as (a' - a)(a' + a) per component, so the small
+// change keeps its relative accuracy; complex128 pairs in closed form add
+// (c5^2 + s5^2 - 1) (|psi_r|^2 + |psi_q|^2), exact for A^2 = -I.  The five
+// products run exactly as in the full-state kernel (complex64: packed
+// float32 chain; complex128 with entries +-1: the closed form
+// c5 psi + s5 A psi), so the two kernels give equal amplitudes.
 #include "dev.cuh"
 #include "grad.cuh"
 #include "pair.cuh"
