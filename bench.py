@@ -206,6 +206,83 @@ def _oracle_worker(args):
             return n, el
 
 
+RATE_OPS = ((0, 0.1), (101, -0.07), (203, 0.05))    # (pool index, angle) applied to HF
+
+
+def _oracle_rate_worker(args):
+    """Oracle energies or gradient sweeps of one 14-qubit state for ~`seconds`."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    kind, seconds = args
+    import synth
+    from oracle import adapt, evolve
+    if "rates" not in _ORACLE_CACHE:
+        ints, ne = synth.config2()
+        sysm = adapt.build_system(ints, ne, MAPPING)
+        psi = adapt.hf_state(NQ, ne, MAPPING)
+        for k, th in RATE_OPS:
+            psi = evolve.taylor5(sysm.pool[k], psi, th)
+        _ORACLE_CACHE["rates"] = (sysm, psi)
+    sysm, psi = _ORACLE_CACHE["rates"]
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        if kind == "energy":
+            adapt.energy(sysm.H, psi)
+        elif kind == "gradients":
+            adapt.gradients(sysm.H, sysm.pool, psi)
+        else:
+            evolve.taylor5(sysm.pool[RATE_OPS[0][0]], psi, 0.1)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            return n, el
+
+
+def oracle_rates(seconds=3.0):
+    """The oracle's energies/s, gradient sweeps/s and updates/s at 14 qubits:
+    one core, and all cores (one spawn worker per core, each on its own copy)."""
+    cores = os.cpu_count() or 1
+    out = {"cores": cores, "workload": "one 14-qubit BK state (Hartree-Fock after three updates), "
+                                       "config-2 integrals, complex128 SciPy CSR"}
+    with mp.get_context("spawn").Pool(cores) as p:
+        for kind in ("energy", "gradients", "update"):
+            n1, t1 = p.map(_oracle_rate_worker, [(kind, seconds)])[0]
+            res = p.map(_oracle_rate_worker, [(kind, seconds)] * cores)
+            out[kind] = {"one_core_per_s": n1 / t1,
+                         "all_cores_per_s": sum(r[0] for r in res) / max(r[1] for r in res)}
+    return out
+
+
+def measure_rates(tq, ctx, reps=200):
+    """Energies/s and gradient sweeps/s through the public API (one state per
+    call, result read back on the host) at 14 qubits, beside the oracle's."""
+    import synth
+    ints, ne = synth.config2()
+    out = {"workload": "one 14-qubit BK state (Hartree-Fock after three updates), config-2 integrals; "
+                       "tq_energy / tq_pool_gradients with host results (each call synchronises)"}
+    pool = tq.build_pool(ctx, ints.n_spatial, ne, MAPPING)
+    for prec, name in ((tq.TQ_C64, "c64"), (tq.TQ_C128, "c128")):
+        ham = tq.build_hamiltonian(ctx, ints.h, ints.g, ints.e_const, MAPPING, prec)
+        st = tq.State(ctx, NQ, prec)
+        tq.state_set_hf(st, ne, MAPPING)
+        for k, th in RATE_OPS:
+            tq.evolve_taylor5(ctx, pool, k, th, st)
+        for _ in range(5):
+            tq.energy(ctx, ham, st)
+            tq.pool_gradients(ctx, ham, pool, st)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            tq.energy(ctx, ham, st)
+        te = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            tq.pool_gradients(ctx, ham, pool, st)
+        tg = time.perf_counter() - t0
+        out[name] = {"energies_per_s": reps / te, "gradient_sweeps_per_s": reps / tg}
+    return out
+
+
 def cpu_oracle_rate(seconds=12.0, states_per_core=4, cores=None, pool=None):
     cores = cores or os.cpu_count() or 1
     jobs = [(list(range(c * states_per_core, (c + 1) * states_per_core)), seconds) for c in range(cores)]
@@ -368,6 +445,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.headline_only:
         extra["fp64_single_instance"] = measure_fp64_single(tq, ctx, pool, k, th)
         extra["full_state"] = measure_full_state(tq, ctx, pool, S)
+        extra["rates_14q"] = measure_rates(tq, ctx)
         extra["c128_batched"] = measure_c128_batched(tq, ctx, pool)
         extra["spmv"] = measure_spmv(tq, ctx, args.spmv_qubits)
         extra["trajectories"] = measure_trajectories(tq, ctx, args.traj)
@@ -376,7 +454,7 @@ def run_ours(args, rank, world, local_rank):
         extra["vqe"] = measure_vqe(tq, ctx)
         extra["io"] = measure_io(tq, ctx)
         if args.serve_seconds > 0:
-            extra["serving"] = measure_serving(tq, local_rank, args.serve_seconds, args.serve_rate)
+            extra["serving"] = measure_serving_process(local_rank, args.serve_seconds, args.serve_rate)
     out = None
     if rank == 0:
         out = {
@@ -833,6 +911,20 @@ def measure_families(tq):
     return {"workload": "pool of 9 orbitals, 8 electrons, BK (560 generators)", **out}
 
 
+def measure_serving_process(device, seconds, rate):
+    """The request loop measured in a process of its own (as a server runs):
+    `bench.py --section serving` on the same device, its JSON line parsed."""
+    env = dict(os.environ, LOCAL_RANK=str(device), RANK="0", WORLD_SIZE="1")
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--section", "serving",
+           "--serve-seconds", str(seconds), "--serve-rate", str(rate)]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=seconds + 600)
+    if r.returncode != 0:
+        return {"error": f"serving process exited {r.returncode}: {r.stderr.strip()[-300:]}"}
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    out["process"] = "own process (bench.py --section serving)"
+    return out
+
+
 def measure_serving(tq, device, seconds, rate):
     """Poisson request stream into the continuous-batching request loop."""
     import numpy as np
@@ -1011,6 +1103,8 @@ def main():
                 "sample": (f"{n} oracle updates (scipy CSR complex128, 5 SpMV + Eq. (8) sum) of "
                            f"{4 * cores} states of the same workload, {cores} spawn workers, "
                            f"{t:.1f} s")}
+            if "rates_14q" in out:
+                out["rates_14q"]["oracle"] = oracle_rates(seconds=2.0)
         else:
             out["cpu_baseline"] = None
         print(json.dumps(out))
