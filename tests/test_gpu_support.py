@@ -223,3 +223,15 @@ def test_states_in_host_memory(ctx, prec):
     with pytest.raises(tq.TQError):
         tq.evolve_taylor5_batch_support_host(ctx, pool, torch.as_tensor(psi).to(dt).numpy(), k, th, None,
                                              prec=prec)
+
+
+def test_l2_fetch_granularity_round_trip(ctx):
+    default = ctx.l2_fetch()
+    assert default in (32, 64, 128)
+    for b in (32, 64, 128):
+        ctx.set_l2_fetch(b)
+        assert ctx.l2_fetch() == b
+    ctx.set_l2_fetch(0)
+    assert ctx.l2_fetch() == default
+    with pytest.raises(tq.TQError):
+        ctx.set_l2_fetch(48)
