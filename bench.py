@@ -254,6 +254,35 @@ def oracle_rates(seconds=3.0):
     return out
 
 
+def measure_adapt_step(tq, ctx, steps=10):
+    """tq_adapt_step with the exact line search (theta = NaN), one state, ten
+    consecutive iterations from Hartree-Fock, at 14 and 18 qubits: wall
+    time per call (each call synchronises) and the kernels' split."""
+    import synth
+    out = {"workload": "ADAPT iterations with the line search from Hartree-Fock, complex64 state, BK, "
+                       "14 q (config-2 integrals) and 18 q (9 orbitals, 8 electrons, seed 2012)"}
+    for nq_, ints, ne in ((14,) + synth.config2(),
+                          (18, synth.integrals(9, synth.SEED_CATALOGUE_BASE + 12), synth.electrons_for(9))):
+        ham = tq.build_hamiltonian(ctx, ints.h, ints.g, ints.e_const, MAPPING, tq.TQ_C64)
+        pool = tq.build_pool(ctx, ints.n_spatial, ne, MAPPING)
+        st = tq.State(ctx, nq_, tq.TQ_C64)
+        tq.state_set_hf(st, ne, MAPPING)
+        tq.adapt_step(ctx, ham, pool, st, 0.0, float("nan"))          # warm
+        tq.state_set_hf(st, ne, MAPPING)
+        ctx.trace(True)
+        t0 = time.perf_counter()
+        energies = []
+        for _ in range(steps):
+            energies.append(tq.adapt_step(ctx, ham, pool, st, 0.0, float("nan"))["energy"])
+        t = (time.perf_counter() - t0) / steps
+        rep = ctx.trace_report()
+        ctx.trace(False)
+        out[f"{nq_}q"] = {"ms_per_step": 1e3 * t, "nnz": ham.nnz, "pool": pool.M,
+                          "kernel_ms_per_step": {k_: v[1] / steps for k_, v in rep.items()},
+                          "energy_first_last": [energies[0], energies[-1]]}
+    return out
+
+
 def measure_rates(tq, ctx, reps=200):
     """Energies/s and gradient sweeps/s through the public API (one state per
     call, result read back on the host) at 14 qubits, beside the oracle's."""
@@ -446,6 +475,7 @@ def run_ours(args, rank, world, local_rank):
         extra["fp64_single_instance"] = measure_fp64_single(tq, ctx, pool, k, th)
         extra["full_state"] = measure_full_state(tq, ctx, pool, S)
         extra["rates_14q"] = measure_rates(tq, ctx)
+        extra["adapt_step"] = measure_adapt_step(tq, ctx)
         extra["c128_batched"] = measure_c128_batched(tq, ctx, pool)
         extra["spmv"] = measure_spmv(tq, ctx, args.spmv_qubits)
         extra["trajectories"] = measure_trajectories(tq, ctx, args.traj)
@@ -1045,7 +1075,7 @@ def main():
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the SpMV, trajectory-batch and request-loop measurements")
     ap.add_argument("--section", choices=["spmv", "trajectories", "serving", "sector", "vqe", "c128", "support",
-                                              "full_state"], default=None,
+                                              "full_state", "adapt"], default=None,
                     help="run one secondary measurement alone and print its JSON (profiling)")
     ap.add_argument("--spmv-qubits", type=int, default=18)
     ap.add_argument("--traj", type=int, default=256)
@@ -1082,6 +1112,8 @@ def main():
             print(json.dumps(measure_sector(tq, ctx)))
         elif args.section == "vqe":
             print(json.dumps(measure_vqe(tq, ctx)))
+        elif args.section == "adapt":
+            print(json.dumps(measure_adapt_step(tq, ctx)))
         elif args.section == "full_state":
             print(json.dumps(measure_full_state(tq, ctx, tq.build_pool(ctx, N_SPATIAL, N_ELECTRONS, MAPPING), 8192)))
         elif args.section == "support":

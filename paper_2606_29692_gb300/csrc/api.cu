@@ -1256,7 +1256,7 @@ size_t partials_needed(long long D, int n_gitems, int nq, int sms) {
     size_t n = (size_t)energy_grid(D, sms) * 2;
     n = std::max(n, (size_t)16 * sms);      // any persistent energy grid (at most 8 blocks per SM)
     n = std::max(n, (size_t)std::max(n_gitems, 0));
-    n = std::max(n, (size_t)512 * 5);
+    n = std::max(n, (size_t)512 * 6);            // the line search's six dots per block
     n = std::max(n, (size_t)taylor5_pair_parts(nq, 1));
     return n + 8;
 }
@@ -1391,9 +1391,12 @@ extern "C" int tq_adapt_step(tq_ctx* c, const tq_ham* h, const tq_pool* p, tq_st
                                                                                       u1, u2, s); });
         else
             launch(c, "apply_twice", s, [&] { return launch_apply_twice(p->view, c->step, psi->data, psi->prec, u1, u2, s); });
-        launch(c, "spmv_c128_gated", s, [&] { return launch_spmv_c128_gated(h->view, u1, w1, c->step, c->sm_count, s); });
-        launch(c, "spmv_c128_gated", s, [&] { return launch_spmv_c128_gated(h->view, u2, w2, c->step, c->sm_count, s); });
-        launch(c, "line_dots", s, [&] { return launch_line_dots(w0, w1, w2, u1, u2, D, part, c->tickets + 2, c->step, s); });
+        // H psi, H u1 and H u2 from one pass with one arithmetic (w0 is
+        // rewritten: the gradients that read it have run)
+        launch(c, "line_spmv_gated", s, [&] { return launch_line_spmv_gated(h->view, psi->data, u1, u2, w0, w1, w2,
+                                                                             c->step, c->sm_count, s); });
+        launch(c, "line_dots", s, [&] { return launch_line_dots(psi->data, w0, w1, w2, u1, u2, psi->prec, D, part,
+                                                                c->tickets + 2, c->step, s); });
     }
     launch(c, "line_search", s, [&] { return launch_line_search(c->step, theta, s); });
     const int upt = c->pair_upt[psi->prec];

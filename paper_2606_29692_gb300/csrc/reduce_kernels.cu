@@ -441,84 +441,180 @@ __global__ void k_select(const double* g, int M, double eps, int prec, DevStep* 
     }
 }
 
-// u1 = A psi, u2 = A u1 for the selected op (float64 outputs).
+// u1 = A psi, u2 = A u1 for the selected op, in the state's precision
+// (entries of A are +-c0, so complex64 vectors hold them exactly when
+// c0 = +-1).
 template <typename T>
 __global__ void k_apply_twice(PoolView p, const DevStep* step, const typename C2<T>::type* psi,
-                              double2* u1, double2* u2, long long D) {
+                              typename C2<T>::type* u1, typename C2<T>::type* u2, long long D) {
+    using V = typename C2<T>::type;
     if (step->converged) return;
-    OpSign<double> op;
+    OpSign<T> op;
     op.load(p, step->selected);
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < D; i += stride) {
         const uint32_t r = (uint32_t)i, q = r ^ op.x;
-        const double s_r = op.value(q);   // A[r][q]
-        const double s_q = op.value(r);   // A[q][r]
-        const double2 pq = to_d2<T>(psi[q]);
-        const double2 pr = to_d2<T>(psi[r]);
-        u1[r] = make_double2(s_r * pq.x, s_r * pq.y);
-        const double s2 = s_r * s_q;
-        u2[r] = make_double2(s2 * pr.x, s2 * pr.y);
+        const T s_r = op.value(q);   // A[r][q]
+        const T s_q = op.value(r);   // A[q][r]
+        const V pq = psi[q], pr = psi[r];
+        u1[r] = V{s_r * pq.x, s_r * pq.y};
+        const T s2 = s_r * s_q;
+        u2[r] = V{s2 * pr.x, s2 * pr.y};
     }
 }
 
-// y = H x for float64 complex x (line search products).
-template <typename VT>
+// Error-free float32 accumulation of products: (hi, lo) carries the sum of
+// a*v with the rounding of each product (an FMA gives it exactly) and of
+// each addition (TwoSum), about 48 significant bits in float32 arithmetic.
+struct F32x2 {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add_product(float a, float v) {
+        const float p = __fmul_rn(a, v);   // not contracted into the sum below
+        const float e = fmaf(a, v, -p);
+        float s, r;
+        two_sum(hi, p, s, r);
+        hi = s;
+        lo += r + e;
+    }
+    __device__ __forceinline__ void add(float h2, float l2) {
+        float s, r;
+        two_sum(hi, h2, s, r);
+        hi = s;
+        lo += r + l2;
+    }
+    __device__ __forceinline__ void shfl_xor(int o) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o), l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        add(h2, l2);
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+// y_i = H x_i for the line search's three vectors (psi, A psi, A^2 psi) in
+// one pass over H: L lanes per row, 32/L rows per warp, each entry's value
+// and column read once and applied to all three.  The diagonal term and
+// the results are float64.  Complex64 products run on the float32 pipe
+// with compensated sums (F32x2), about 48 bits: the line search decides a
+// tie between the two minima of a pi-periodic energy curve at 1e-10, and
+// that curve is pi-periodic only through exact relations between its
+// coefficients (<H psi|A^2 psi> = -<psi|H psi> when A^2 psi = -psi), which
+// hold when all three products share one arithmetic and are accurate well
+// below 1e-10; float64 instructions would cost several times more here.
+template <typename T, int L>
 __global__ void __launch_bounds__(256)
-k_spmv_c128(HamView h, const double2* __restrict__ x, double2* __restrict__ y, const DevStep* gate) {
+k_line_spmv(HamView h, const typename C2<T>::type* __restrict__ x0, const typename C2<T>::type* __restrict__ x1,
+            const typename C2<T>::type* __restrict__ x2, double2* __restrict__ y0, double2* __restrict__ y1,
+            double2* __restrict__ y2, const DevStep* gate) {
+    using V = typename C2<T>::type;
     if (gate && gate->converged) return;
-    const VT* __restrict__ val = static_cast<const VT*>(h.val);
-    const int lane = threadIdx.x & 31;
+    const T* __restrict__ val = static_cast<const T*>(h.val);
+    const int lane = threadIdx.x & 31, sub = lane & (L - 1);
+    constexpr int RPW = 32 / L;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long r = warp; r < h.D; r += nwarps) {
-        double sx = 0.0, sy = 0.0;
-        for (int e = h.rowptr[r] + lane; e < h.rowptr[r + 1]; e += 32) {
-            const double a = (double)val[e];
-            const double2 v = x[h.col[e]];
-            sx = fma(a, v.x, sx);
-            sy = fma(a, v.y, sy);
+    const V* xs[3] = {x0, x1, x2};
+    double2* ys[3] = {y0, y1, y2};
+    for (long long r0 = warp * RPW; r0 < h.D; r0 += nwarps * RPW) {
+        const long long r = r0 + (lane / L);
+        double sx[3], sy[3];
+        if constexpr (sizeof(T) == 4) {
+            F32x2 ax[3], ay[3];
+            if (r < h.D) {
+                for (int e = h.rowptr[r] + sub; e < h.rowptr[r + 1]; e += L) {
+                    const float a = val[e];
+                    const int c = h.col[e];
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        const V v = xs[i][c];
+                        ax[i].add_product(a, v.x);
+                        ay[i].add_product(a, v.y);
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+#pragma unroll
+                for (int o = L / 2; o > 0; o >>= 1) {
+                    ax[i].shfl_xor(o);
+                    ay[i].shfl_xor(o);
+                }
+                sx[i] = ax[i].value();
+                sy[i] = ay[i].value();
+            }
+        } else {
+            double ax[3] = {0.0, 0.0, 0.0}, ay[3] = {0.0, 0.0, 0.0};
+            if (r < h.D) {
+                for (int e = h.rowptr[r] + sub; e < h.rowptr[r + 1]; e += L) {
+                    const double a = val[e];
+                    const int c = h.col[e];
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        const V v = xs[i][c];
+                        ax[i] = fma(a, v.x, ax[i]);
+                        ay[i] = fma(a, v.y, ay[i]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+#pragma unroll
+                for (int o = L / 2; o > 0; o >>= 1) {
+                    ax[i] += __shfl_xor_sync(0xffffffffu, ax[i], o);
+                    ay[i] += __shfl_xor_sync(0xffffffffu, ay[i], o);
+                }
+                sx[i] = ax[i];
+                sy[i] = ay[i];
+            }
         }
-        sx = warp_sum(sx);
-        sy = warp_sum(sy);
-        if (lane == 0) {
+        if (sub == 0 && r < h.D) {
             const double d = h.diag[r];
-            const double2 xr = x[r];
-            y[r] = make_double2(fma(d, xr.x, sx), fma(d, xr.y, sy));
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const V p = xs[i][r];
+                ys[i][r] = make_double2(fma(d, (double)p.x, sx[i]), fma(d, (double)p.y, sy[i]));
+            }
         }
     }
 }
 
-// Five Re-dots of the line search, divided by <psi|psi>:
-// dots = {<w0|u1>, <w0|u2>, <u1|w1>, <w1|u2>, <u2|w2>}.
+// The six Re-dots of the line search, divided by <psi|psi>, with
+// w0 = H psi, w1 = H u1, w2 = H u2 from one pass:
+// dots = {<psi|w0>, <w0|u1>, <w0|u2>, <u1|w1>, <w1|u2>, <u2|w2>}.  <psi|w0>
+// and <w0|u2> are written in the same shape so that u2 = -psi gives
+// exactly opposite values (and <u2|w2> exactly <psi|w0>).
+template <typename T>
 __global__ void __launch_bounds__(256)
-k_line_dots(const double2* w0, const double2* w1, const double2* w2, const double2* u1,
-            const double2* u2, long long D, double* partials, unsigned* ticket, DevStep* step) {
-    __shared__ double sh[5 * 8];
+k_line_dots(const typename C2<T>::type* psi, const double2* w0, const double2* w1, const double2* w2,
+            const typename C2<T>::type* u1, const typename C2<T>::type* u2, long long D, double* partials,
+            unsigned* ticket, DevStep* step) {
+    __shared__ double sh[6 * 8];
     if (step->converged) return;
-    double a[5] = {0, 0, 0, 0, 0};
+    double a[6] = {0, 0, 0, 0, 0, 0};
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < D; i += stride) {
-        const double2 x0 = w0[i], x1 = w1[i], x2 = w2[i], v1 = u1[i], v2 = u2[i];
-        a[0] += x0.x * v1.x + x0.y * v1.y;
-        a[1] += x0.x * v2.x + x0.y * v2.y;
-        a[2] += v1.x * x1.x + v1.y * x1.y;
-        a[3] += x1.x * v2.x + x1.y * v2.y;
-        a[4] += v2.x * x2.x + v2.y * x2.y;
+        const double2 x0 = w0[i], x1 = w1[i], x2 = w2[i], v1 = to_d2<T>(u1[i]), v2 = to_d2<T>(u2[i]);
+        const double2 p = to_d2<T>(psi[i]);
+        a[0] += x0.x * p.x + x0.y * p.y;
+        a[1] += x0.x * v1.x + x0.y * v1.y;
+        a[2] += x0.x * v2.x + x0.y * v2.y;
+        a[3] += v1.x * x1.x + v1.y * x1.y;
+        a[4] += x1.x * v2.x + x1.y * v2.y;
+        a[5] += x2.x * v2.x + x2.y * v2.y;
     }
     // two-stage block sum (block_sum handles up to 4 values)
     double lo[4] = {a[0], a[1], a[2], a[3]};
-    double hi[1] = {a[4]};
+    double hi[2] = {a[4], a[5]};
     block_sum<4>(lo, sh);
-    block_sum<1>(hi, sh + 32);
+    block_sum<2>(hi, sh + 32);
     if (threadIdx.x == 0) {
-        for (int j = 0; j < 4; ++j) partials[5 * blockIdx.x + j] = lo[j];
-        partials[5 * blockIdx.x + 4] = hi[0];
+        for (int j = 0; j < 4; ++j) partials[6 * blockIdx.x + j] = lo[j];
+        partials[6 * blockIdx.x + 4] = hi[0];
+        partials[6 * blockIdx.x + 5] = hi[1];
     }
     if (last_block(ticket, gridDim.x) && threadIdx.x == 0) {
-        double s[5] = {0, 0, 0, 0, 0};
+        double s[6] = {0, 0, 0, 0, 0, 0};
         for (unsigned b = 0; b < gridDim.x; ++b)
-            for (int j = 0; j < 5; ++j) s[j] += __ldcg(partials + 5 * b + j);
-        for (int j = 0; j < 5; ++j) step->dots[1 + j] = s[j] / step->e_den;
+            for (int j = 0; j < 6; ++j) s[j] += __ldcg(partials + 6 * b + j);
+        for (int j = 0; j < 6; ++j) step->dots[j] = s[j] / step->e_den;
         *ticket = 0u;
     }
 }
@@ -553,7 +649,7 @@ __global__ void k_line_search(DevStep* step, double theta_given) {
         return;
     }
     double c[6];
-    c[0] = step->energy;
+    c[0] = step->dots[0];   // H00, from the same products as the others
     c[1] = step->dots[1];   // H01
     c[2] = step->dots[2];   // H02
     c[3] = step->dots[3];   // H11
@@ -760,38 +856,53 @@ int launch_select(const double* g, int M, double eps, int prec, DevStep* step, c
     return 1;
 }
 
-int launch_apply_twice(const PoolView& p, const DevStep* step, const void* psi, int prec, double2* u1,
-                       double2* u2, cudaStream_t s) {
+int launch_apply_twice(const PoolView& p, const DevStep* step, const void* psi, int prec, void* u1, void* u2,
+                       cudaStream_t s) {
     const long long D = 1ll << p.nq;
     const int bs = 256;
     const int grid = (int)((D + bs - 1) / bs < 2048 ? (D + bs - 1) / bs : 2048);
     if (prec == TQ_C128)
-        k_apply_twice<double><<<grid, bs, 0, s>>>(p, step, static_cast<const double2*>(psi), u1, u2, D);
+        k_apply_twice<double><<<grid, bs, 0, s>>>(p, step, static_cast<const double2*>(psi),
+                                                   static_cast<double2*>(u1), static_cast<double2*>(u2), D);
     else
-        k_apply_twice<float><<<grid, bs, 0, s>>>(p, step, static_cast<const float2*>(psi), u1, u2, D);
+        k_apply_twice<float><<<grid, bs, 0, s>>>(p, step, static_cast<const float2*>(psi), static_cast<float2*>(u1),
+                                                  static_cast<float2*>(u2), D);
     return 1;
 }
 
-int launch_spmv_c128_gated(const HamView& h, const double2* x, double2* y, const DevStep* gate, int sms,
-                           cudaStream_t s) {
-    const int grid = energy_grid(h.D, sms);
+int launch_line_spmv_gated(const HamView& h, const void* x0, const void* x1, const void* x2, double2* y0,
+                           double2* y1, double2* y2, const DevStep* gate, int sms, cudaStream_t s) {
+    constexpr int L = 8;
+    const long long warps = (h.D + 32 / L - 1) / (32 / L);
+    long long grid = (warps * 32 + 255) / 256;
+    const long long cap = (long long)energy_grid(h.D, sms);
+    if (grid > cap) grid = cap;
+    if (grid < 1) grid = 1;
     if (h.prec == TQ_C128)
-        k_spmv_c128<double><<<grid, 256, 0, s>>>(h, x, y, gate);
+        k_line_spmv<double, L><<<(int)grid, 256, 0, s>>>(h, static_cast<const double2*>(x0),
+                                                          static_cast<const double2*>(x1),
+                                                          static_cast<const double2*>(x2), y0, y1, y2, gate);
     else
-        k_spmv_c128<float><<<grid, 256, 0, s>>>(h, x, y, gate);
+        k_line_spmv<float, L><<<(int)grid, 256, 0, s>>>(h, static_cast<const float2*>(x0),
+                                                         static_cast<const float2*>(x1),
+                                                         static_cast<const float2*>(x2), y0, y1, y2, gate);
     return 1;
 }
 
-int launch_spmv_c128(const HamView& h, const double2* x, double2* y, int sms, cudaStream_t s) {
-    return launch_spmv_c128_gated(h, x, y, nullptr, sms, s);
-}
 
-int launch_line_dots(const double2* w0, const double2* w1, const double2* w2, const double2* u1,
-                     const double2* u2, long long D, double* partials, unsigned* ticket, DevStep* step,
+int launch_line_dots(const void* psi, const double2* w0, const double2* w1, const double2* w2, const void* u1,
+                     const void* u2, int prec, long long D, double* partials, unsigned* ticket, DevStep* step,
                      cudaStream_t s) {
     const int bs = 256;
     const int grid = (int)((D + bs - 1) / bs < 512 ? (D + bs - 1) / bs : 512);
-    k_line_dots<<<grid, bs, 0, s>>>(w0, w1, w2, u1, u2, D, partials, ticket, step);
+    if (prec == TQ_C128)
+        k_line_dots<double><<<grid, bs, 0, s>>>(static_cast<const double2*>(psi), w0, w1, w2,
+                                                 static_cast<const double2*>(u1), static_cast<const double2*>(u2), D,
+                                                 partials, ticket, step);
+    else
+        k_line_dots<float><<<grid, bs, 0, s>>>(static_cast<const float2*>(psi), w0, w1, w2,
+                                                static_cast<const float2*>(u1), static_cast<const float2*>(u2), D,
+                                                partials, ticket, step);
     return 1;
 }
 

@@ -279,10 +279,12 @@ k_sector_grad(PoolView p, const double2* __restrict__ w, const typename C2<T>::t
 }
 
 // u1 = A psi, u2 = A u1 = -psi on the rows A does not annihilate (A^2 = -I
-// on a pair), for the selected op; float64 outputs.
+// on a pair), for the selected op; in the state's precision (exact: the
+// entries are +-1).
 template <typename T>
-__global__ void k_apply_twice_sector(PoolView p, const DevStep* step, const typename C2<T>::type* psi, double2* u1,
-                                     double2* u2) {
+__global__ void k_apply_twice_sector(PoolView p, const DevStep* step, const typename C2<T>::type* psi,
+                                     typename C2<T>::type* u1, typename C2<T>::type* u2) {
+    using V = typename C2<T>::type;
     if (step->converged) return;
     const long long dim = p.sdim;
     const int k = step->selected;
@@ -291,9 +293,9 @@ __global__ void k_apply_twice_sector(PoolView p, const DevStep* step, const type
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < dim; r += stride) {
         const int sg = sgn[r];
-        const typename C2<T>::type vc = psi[col[r]], vr = psi[r];
-        u1[r] = make_double2(sg * (double)vc.x, sg * (double)vc.y);
-        u2[r] = sg ? make_double2(-(double)vr.x, -(double)vr.y) : make_double2(0.0, 0.0);
+        const V vc = psi[col[r]], vr = psi[r];
+        u1[r] = sg > 0 ? vc : (sg < 0 ? V{-vc.x, -vc.y} : V{T(0), T(0)});
+        u2[r] = sg ? V{-vr.x, -vr.y} : V{T(0), T(0)};
     }
 }
 
@@ -351,14 +353,16 @@ int launch_sector_gradients(const PoolView& p, const double2* w, const void* psi
     return 1;
 }
 
-int launch_apply_twice_sector(const PoolView& p, const DevStep* step, const void* psi, int prec, double2* u1,
-                              double2* u2, cudaStream_t s) {
+int launch_apply_twice_sector(const PoolView& p, const DevStep* step, const void* psi, int prec, void* u1, void* u2,
+                              cudaStream_t s) {
     const long long dim = p.sdim;
     const int grid = (int)((dim + 255) / 256 < 1024 ? (dim + 255) / 256 : 1024);
     if (prec == TQ_C128)
-        k_apply_twice_sector<double><<<grid, 256, 0, s>>>(p, step, static_cast<const double2*>(psi), u1, u2);
+        k_apply_twice_sector<double><<<grid, 256, 0, s>>>(p, step, static_cast<const double2*>(psi),
+                                                          static_cast<double2*>(u1), static_cast<double2*>(u2));
     else
-        k_apply_twice_sector<float><<<grid, 256, 0, s>>>(p, step, static_cast<const float2*>(psi), u1, u2);
+        k_apply_twice_sector<float><<<grid, 256, 0, s>>>(p, step, static_cast<const float2*>(psi),
+                                                         static_cast<float2*>(u1), static_cast<float2*>(u2));
     return 1;
 }
 

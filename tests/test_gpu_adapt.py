@@ -145,3 +145,31 @@ def test_converged_step_leaves_state(ctx):
     r = tq.adapt_step(ctx, ham, pool, st, 1e3)     # eps above every gradient
     assert r["converged"]
     assert np.array_equal(st.numpy(), before)
+
+
+@pytest.mark.parametrize("mp", [0, 1])
+def test_line_search_16q_c64_follows_c128(ctx, mp):
+    """Ten line-search steps at 16 qubits (rows of up to ~280 non-zeros):
+    complex64 takes the same operators and the same angles as complex128.
+    When psi lies in a generator's support the energy curve has two tied
+    minima half a period apart; the line-search products must resolve that
+    tie (to 1e-10) in complex64 too, else the update takes the far minimum,
+    where Taylor-5 is no longer accurate, and the energy rises."""
+    n = 8
+    ne = synth.electrons_for(n)
+    ints = synth.integrals(n, 4242)
+    runs = {}
+    for prec in (tq.TQ_C128, tq.TQ_C64):
+        ham = tq.build_hamiltonian(ctx, ints.h, ints.g, ints.e_const, mp, prec)
+        pool = tq.build_pool(ctx, n, ne, mp)
+        st = tq.State(ctx, 2 * n, prec)
+        tq.state_set_hf(st, ne, mp)
+        runs[prec] = [tq.adapt_step(ctx, ham, pool, st, 0.0, float("nan")) for _ in range(10)]
+    a, b = runs[tq.TQ_C128], runs[tq.TQ_C64]
+    for i, (ra, rb) in enumerate(zip(a, b)):
+        assert ra["selected"] == rb["selected"], i
+        assert abs(ra["theta"] - rb["theta"]) <= 1e-4, (i, ra["theta"], rb["theta"])
+        assert abs(ra["energy"] - rb["energy"]) <= 1e-5, i
+        assert abs(rb["theta"]) <= np.pi / 2 + 1e-9, i
+    e = [r["energy"] for r in b]
+    assert all(e[i + 1] <= e[i] + 1e-6 for i in range(len(e) - 1)), e
