@@ -437,15 +437,17 @@ def run_ours(args, rank, world, local_rank):
     n_h = dn.cpu().pin_memory()
     e2e_steps = max(1, min(args.steps, 20))
     e2e_tune = {}
-    ctx.set_l2_fetch(32)
-    for cand in (-1, -2, -4, -8, 1, 2, 4):
-        ctx.set_support_schedule(tq.TQ_C64, cand)
-        tq.evolve_taylor5_batch_support_host(ctx, pool, psi_h, k_h, th_h, n_h)
-        t0 = time.perf_counter()
-        for _ in range(3):
+    for fetch in (32, 64, 128):
+        ctx.set_l2_fetch(fetch)
+        for cand in (-1, -2, -4, -8, 1, 2, 4):
+            ctx.set_support_schedule(tq.TQ_C64, cand)
             tq.evolve_taylor5_batch_support_host(ctx, pool, psi_h, k_h, th_h, n_h)
-        e2e_tune[cand] = (time.perf_counter() - t0) / 3
-    e2e_sched = min(e2e_tune, key=e2e_tune.get)
+            t0 = time.perf_counter()
+            for _ in range(3):
+                tq.evolve_taylor5_batch_support_host(ctx, pool, psi_h, k_h, th_h, n_h)
+            e2e_tune[(fetch, cand)] = (time.perf_counter() - t0) / 3
+    e2e_fetch, e2e_sched = min(e2e_tune, key=e2e_tune.get)
+    ctx.set_l2_fetch(e2e_fetch)
     ctx.set_support_schedule(tq.TQ_C64, e2e_sched)
     barrier()
     t0 = time.perf_counter()
@@ -458,7 +460,8 @@ def run_ours(args, rank, world, local_rank):
            "d2h_bytes_per_step": float(32 * n_sect.sum()) + S * 8,
            "bytes_note": "support sectors read and written in place by the kernel over the host link "
                          "(32-byte sectors), plus k, theta and the norms copied",
-           "schedule": e2e_sched, "ms_per_step_by_schedule": {str(c_): 1e3 * v for c_, v in e2e_tune.items()},
+           "schedule": e2e_sched, "l2_fetch_bytes": e2e_fetch,
+           "ms_per_step_by_fetch_and_schedule": {f"{f_}B/{c_}": 1e3 * v for (f_, c_), v in e2e_tune.items()},
            "api": "tq_evolve_taylor5_batch_support_host (states in pinned host memory)"}
     # the full-state host path for comparison: whole states copied in and out
     tq.evolve_taylor5_batch_host(ctx, pool, psi_h, k_h, th_h, n_h)     # warm
