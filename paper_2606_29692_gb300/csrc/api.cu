@@ -201,6 +201,10 @@ extern "C" int tq_ctx_create(int device, tq_ctx** out) {
         size_t fetch = 0;
         TQ_CUDA(cudaDeviceGetLimit(&fetch, cudaLimitMaxL2FetchGranularity));
         c->l2_fetch_default = (int)fetch;
+        // the line search's sample table, filled before any call can read it
+        c->line_sc = static_cast<double2*>(dev_alloc(4096 * sizeof(double2)));
+        launch(c, "line_table", 0, [&] { return launch_line_table(c->line_sc, 0); });
+        TQ_CUDA(cudaDeviceSynchronize());
     } catch (...) {
         tq_ctx_destroy(c);
         throw;
@@ -217,6 +221,7 @@ extern "C" int tq_ctx_destroy(tq_ctx* c) {
         if (c->scratch[i]) cudaFree(c->scratch[i]);
     if (c->step) cudaFree(c->step);
     if (c->tickets) cudaFree(c->tickets);
+    if (c->line_sc) cudaFree(c->line_sc);
     for (auto& s : c->aux)
         if (s) cudaStreamDestroy(s);
     for (auto& r : c->trace) {
@@ -1377,8 +1382,7 @@ extern "C" int tq_adapt_step(tq_ctx* c, const tq_ham* h, const tq_pool* p, tq_st
     const long long D = h->D;
     double* g = static_cast<double*>(scratch(c, S_G, (size_t)p->M * sizeof(double)));
     const size_t vb = (size_t)D * sizeof(double2);
-    double2* u1 = static_cast<double2*>(scratch(c, S_U1, vb));
-    double2* u2 = static_cast<double2*>(scratch(c, S_U2, vb));
+    void* z = scratch(c, S_U1, 4 * (size_t)D * elem_bytes(psi->prec));   // {psi, A psi, A^2 psi, 0} per row
     double2* w1 = static_cast<double2*>(scratch(c, S_W1, vb));
     double2* w2 = static_cast<double2*>(scratch(c, S_W2, vb));
     double* part = prepare(c, D, p, p->nq);
@@ -1387,18 +1391,18 @@ extern "C" int tq_adapt_step(tq_ctx* c, const tq_ham* h, const tq_pool* p, tq_st
     launch(c, "select", s, [&] { return launch_select(g, p->M, eps, psi->prec, c->step, s); });
     if (std::isnan(theta)) {
         if (p->sector)
-            launch(c, "apply_twice_sector", s, [&] { return launch_apply_twice_sector(p->view, c->step, psi->data, psi->prec,
-                                                                                      u1, u2, s); });
+            launch(c, "apply_twice_sector", s, [&] { return launch_apply_twice_sector(p->view, c->step, psi->data,
+                                                                                      psi->prec, z, s); });
         else
-            launch(c, "apply_twice", s, [&] { return launch_apply_twice(p->view, c->step, psi->data, psi->prec, u1, u2, s); });
-        // H psi, H u1 and H u2 from one pass with one arithmetic (w0 is
-        // rewritten: the gradients that read it have run)
-        launch(c, "line_spmv_gated", s, [&] { return launch_line_spmv_gated(h->view, psi->data, u1, u2, w0, w1, w2,
-                                                                             c->step, c->sm_count, s); });
-        launch(c, "line_dots", s, [&] { return launch_line_dots(psi->data, w0, w1, w2, u1, u2, psi->prec, D, part,
-                                                                c->tickets + 2, c->step, s); });
+            launch(c, "apply_twice", s, [&] { return launch_apply_twice(p->view, c->step, psi->data, psi->prec, z, s); });
+        // H psi, H A psi and H A^2 psi from one pass with one arithmetic (w0
+        // is rewritten: the gradients that read it have run)
+        launch(c, "line_spmv_gated", s, [&] { return launch_line_spmv_gated(h->view, z, w0, w1, w2, c->step,
+                                                                             c->sm_count, s); });
+        launch(c, "line_dots", s, [&] { return launch_line_dots(z, w0, w1, w2, psi->prec, D, part, c->tickets + 2,
+                                                                c->step, s); });
     }
-    launch(c, "line_search", s, [&] { return launch_line_search(c->step, theta, s); });
+    launch(c, "line_search", s, [&] { return launch_line_search(c->step, theta, c->line_sc, s); });
     const int upt = c->pair_upt[psi->prec];
     const int tiles = update_tiles(p, psi->prec, upt);
     if (!launch_update(c, p, 1, psi->prec, upt, psi->data, nullptr, nullptr, 0, 0.0, c->step, part, nullptr,

@@ -239,23 +239,24 @@ int launch_pool_gradients(const PoolView& p, const double2* w, const float2* w32
                           unsigned* tickets, double* g, int sms, cudaStream_t s);
 int launch_select(const double* g, int M, double eps, int prec, DevStep* step,
                   cudaStream_t s);
-// Line search (u1, u2 in the state's precision: float2 or double2).
-int launch_apply_twice(const PoolView& p, const DevStep* step, const void* psi, int prec, void* u1, void* u2,
-                       cudaStream_t s);
-int launch_line_dots(const void* psi, const double2* w0, const double2* w1, const double2* w2, const void* u1,
-                     const void* u2, int prec, long long D, double* partials, unsigned* ticket, DevStep* step,
-                     cudaStream_t s);
-int launch_line_search(DevStep* step, double theta_given, cudaStream_t s);
+// Line search: z holds per row the record {psi, A psi, A^2 psi, 0} in the
+// state's precision (4 float2 or 4 double2).
+int launch_apply_twice(const PoolView& p, const DevStep* step, const void* psi, int prec, void* z, cudaStream_t s);
+int launch_line_dots(const void* z, const double2* w0, const double2* w1, const double2* w2, int prec, long long D,
+                     double* partials, unsigned* ticket, DevStep* step, cudaStream_t s);
+// sc: sin and cos of the 4096 sample angles (launch_line_table fills it).
+int launch_line_table(double2* sc, cudaStream_t s);
+int launch_line_search(DevStep* step, double theta_given, const double2* sc, cudaStream_t s);
 
 // gated variants (skip when step->converged) and layout helpers
 int launch_taylor5_pair_gated(const PoolView& p, int prec, int upt, void* psi, const DevStep* step,
                               double* partials, int sms, cudaStream_t s);
 int launch_scale_gated(void* psi, int prec, long long D, const double* norm2,
                        const DevStep* gate, cudaStream_t s);
-// The line search's three products in one pass over H: y_i = H x_i (x in
-// the Hamiltonian's precision, y float64).
-int launch_line_spmv_gated(const HamView& h, const void* x0, const void* x1, const void* x2, double2* y0,
-                           double2* y1, double2* y2, const DevStep* gate, int sms, cudaStream_t s);
+// The line search's three products in one pass over H: y_i = H x_i, x_i
+// the three vectors of the records z, y float64.
+int launch_line_spmv_gated(const HamView& h, const void* z, double2* y0, double2* y1, double2* y2,
+                           const DevStep* gate, int sms, cudaStream_t s);
 int energy_grid(long long D, int sms);
 
 // sector-restricted basis
@@ -277,7 +278,7 @@ int launch_taylor5_sector(const PoolView& p, long long n_states, int prec, void*
                           double* partials, double* norm2, double* step_norm2, cudaStream_t s);
 int launch_sector_gradients(const PoolView& p, const double2* w, const void* psi, int prec, const DevStep* step,
                             double* g, cudaStream_t s);
-int launch_apply_twice_sector(const PoolView& p, const DevStep* step, const void* psi, int prec, void* u1, void* u2,
+int launch_apply_twice_sector(const PoolView& p, const DevStep* step, const void* psi, int prec, void* z,
                               cudaStream_t s);
 
 }  // namespace tq
@@ -307,6 +308,7 @@ struct tq_ctx {
     size_t scratch_bytes[kScratch] = {0};
     tq::DevStep* step = nullptr;      // device
     unsigned* tickets = nullptr;      // device, zero between calls
+    double2* line_sc = nullptr;       // device, sin/cos of the line search's sample angles (filled once)
     size_t tickets_n = 0;
     cudaStream_t aux[3] = {nullptr, nullptr, nullptr};
 };

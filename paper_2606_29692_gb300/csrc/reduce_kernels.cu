@@ -441,12 +441,14 @@ __global__ void k_select(const double* g, int M, double eps, int prec, DevStep* 
     }
 }
 
-// u1 = A psi, u2 = A u1 for the selected op, in the state's precision
-// (entries of A are +-c0, so complex64 vectors hold them exactly when
-// c0 = +-1).
+// The line search's vectors psi, u1 = A psi and u2 = A u1 for the selected
+// op, interleaved per row as one record {psi, u1, u2, 0} of four complex
+// values (32 bytes in complex64, 64 in complex128), so that the pass over H
+// gathers all three at a column with one sector (complex64).  In the
+// state's precision: the entries of A are +-c0, exact for c0 = +-1.
 template <typename T>
 __global__ void k_apply_twice(PoolView p, const DevStep* step, const typename C2<T>::type* psi,
-                              typename C2<T>::type* u1, typename C2<T>::type* u2, long long D) {
+                              typename C2<T>::type* z, long long D) {
     using V = typename C2<T>::type;
     if (step->converged) return;
     OpSign<T> op;
@@ -457,9 +459,12 @@ __global__ void k_apply_twice(PoolView p, const DevStep* step, const typename C2
         const T s_r = op.value(q);   // A[r][q]
         const T s_q = op.value(r);   // A[q][r]
         const V pq = psi[q], pr = psi[r];
-        u1[r] = V{s_r * pq.x, s_r * pq.y};
         const T s2 = s_r * s_q;
-        u2[r] = V{s2 * pr.x, s2 * pr.y};
+        V* rec = z + 4 * i;
+        rec[0] = pr;
+        rec[1] = V{s_r * pq.x, s_r * pq.y};
+        rec[2] = V{s2 * pr.x, s2 * pr.y};
+        rec[3] = V{T(0), T(0)};
     }
 }
 
@@ -499,11 +504,24 @@ struct F32x2 {
 // coefficients (<H psi|A^2 psi> = -<psi|H psi> when A^2 psi = -psi), which
 // hold when all three products share one arithmetic and are accurate well
 // below 1e-10; float64 instructions would cost several times more here.
+// The record {x0, x1, x2, pad} of row c, as three complex values.
+__device__ __forceinline__ void line_rec(const float2* __restrict__ z, long long c, float2 (&v)[3]) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(z + 4 * c));
+    const float4 b = __ldg(reinterpret_cast<const float4*>(z + 4 * c + 2));
+    v[0] = make_float2(a.x, a.y);
+    v[1] = make_float2(a.z, a.w);
+    v[2] = make_float2(b.x, b.y);
+}
+__device__ __forceinline__ void line_rec(const double2* __restrict__ z, long long c, double2 (&v)[3]) {
+    v[0] = __ldg(z + 4 * c);
+    v[1] = __ldg(z + 4 * c + 1);
+    v[2] = __ldg(z + 4 * c + 2);
+}
+
 template <typename T, int L>
 __global__ void __launch_bounds__(256)
-k_line_spmv(HamView h, const typename C2<T>::type* __restrict__ x0, const typename C2<T>::type* __restrict__ x1,
-            const typename C2<T>::type* __restrict__ x2, double2* __restrict__ y0, double2* __restrict__ y1,
-            double2* __restrict__ y2, const DevStep* gate) {
+k_line_spmv(HamView h, const typename C2<T>::type* __restrict__ z, double2* __restrict__ y0,
+            double2* __restrict__ y1, double2* __restrict__ y2, const DevStep* gate) {
     using V = typename C2<T>::type;
     if (gate && gate->converged) return;
     const T* __restrict__ val = static_cast<const T*>(h.val);
@@ -511,7 +529,6 @@ k_line_spmv(HamView h, const typename C2<T>::type* __restrict__ x0, const typena
     constexpr int RPW = 32 / L;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    const V* xs[3] = {x0, x1, x2};
     double2* ys[3] = {y0, y1, y2};
     for (long long r0 = warp * RPW; r0 < h.D; r0 += nwarps * RPW) {
         const long long r = r0 + (lane / L);
@@ -519,14 +536,31 @@ k_line_spmv(HamView h, const typename C2<T>::type* __restrict__ x0, const typena
         if constexpr (sizeof(T) == 4) {
             F32x2 ax[3], ay[3];
             if (r < h.D) {
-                for (int e = h.rowptr[r] + sub; e < h.rowptr[r + 1]; e += L) {
-                    const float a = val[e];
-                    const int c = h.col[e];
+                // four entries in flight per lane: values and columns first,
+                // then the four records, then the products in entry order
+                constexpr int U = 4;
+                const int e1 = h.rowptr[r + 1];
+                for (int e0 = h.rowptr[r] + sub; e0 < e1; e0 += U * L) {
+                    float a[U];
+                    int c[U];
 #pragma unroll
-                    for (int i = 0; i < 3; ++i) {
-                        const V v = xs[i][c];
-                        ax[i].add_product(a, v.x);
-                        ay[i].add_product(a, v.y);
+                    for (int j = 0; j < U; ++j) {
+                        const int e = e0 + j * L;
+                        a[j] = e < e1 ? val[e] : 0.f;
+                        c[j] = e < e1 ? h.col[e] : -1;
+                    }
+                    V v[U][3];
+#pragma unroll
+                    for (int j = 0; j < U; ++j)
+                        if (c[j] >= 0) line_rec(z, c[j], v[j]);
+#pragma unroll
+                    for (int j = 0; j < U; ++j) {
+                        if (c[j] < 0) continue;
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) {
+                            ax[i].add_product(a[j], v[j][i].x);
+                            ay[i].add_product(a[j], v[j][i].y);
+                        }
                     }
                 }
             }
@@ -545,12 +579,12 @@ k_line_spmv(HamView h, const typename C2<T>::type* __restrict__ x0, const typena
             if (r < h.D) {
                 for (int e = h.rowptr[r] + sub; e < h.rowptr[r + 1]; e += L) {
                     const double a = val[e];
-                    const int c = h.col[e];
+                    V v[3];
+                    line_rec(z, h.col[e], v);
 #pragma unroll
                     for (int i = 0; i < 3; ++i) {
-                        const V v = xs[i][c];
-                        ax[i] = fma(a, v.x, ax[i]);
-                        ay[i] = fma(a, v.y, ay[i]);
+                        ax[i] = fma(a, v[i].x, ax[i]);
+                        ay[i] = fma(a, v[i].y, ay[i]);
                     }
                 }
             }
@@ -567,11 +601,11 @@ k_line_spmv(HamView h, const typename C2<T>::type* __restrict__ x0, const typena
         }
         if (sub == 0 && r < h.D) {
             const double d = h.diag[r];
+            V p[3];
+            line_rec(z, r, p);
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const V p = xs[i][r];
-                ys[i][r] = make_double2(fma(d, (double)p.x, sx[i]), fma(d, (double)p.y, sy[i]));
-            }
+            for (int i = 0; i < 3; ++i)
+                ys[i][r] = make_double2(fma(d, (double)p[i].x, sx[i]), fma(d, (double)p[i].y, sy[i]));
         }
     }
 }
@@ -583,16 +617,15 @@ k_line_spmv(HamView h, const typename C2<T>::type* __restrict__ x0, const typena
 // exactly opposite values (and <u2|w2> exactly <psi|w0>).
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_line_dots(const typename C2<T>::type* psi, const double2* w0, const double2* w1, const double2* w2,
-            const typename C2<T>::type* u1, const typename C2<T>::type* u2, long long D, double* partials,
-            unsigned* ticket, DevStep* step) {
+k_line_dots(const typename C2<T>::type* z, const double2* w0, const double2* w1, const double2* w2, long long D,
+            double* partials, unsigned* ticket, DevStep* step) {
     __shared__ double sh[6 * 8];
     if (step->converged) return;
     double a[6] = {0, 0, 0, 0, 0, 0};
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < D; i += stride) {
-        const double2 x0 = w0[i], x1 = w1[i], x2 = w2[i], v1 = to_d2<T>(u1[i]), v2 = to_d2<T>(u2[i]);
-        const double2 p = to_d2<T>(psi[i]);
+        const double2 x0 = w0[i], x1 = w1[i], x2 = w2[i];
+        const double2 p = to_d2<T>(z[4 * i]), v1 = to_d2<T>(z[4 * i + 1]), v2 = to_d2<T>(z[4 * i + 2]);
         a[0] += x0.x * p.x + x0.y * p.y;
         a[1] += x0.x * v1.x + x0.y * v1.y;
         a[2] += x0.x * v2.x + x0.y * v2.y;
@@ -610,25 +643,36 @@ k_line_dots(const typename C2<T>::type* psi, const double2* w0, const double2* w
         partials[6 * blockIdx.x + 4] = hi[0];
         partials[6 * blockIdx.x + 5] = hi[1];
     }
-    if (last_block(ticket, gridDim.x) && threadIdx.x == 0) {
-        double s[6] = {0, 0, 0, 0, 0, 0};
-        for (unsigned b = 0; b < gridDim.x; ++b)
-            for (int j = 0; j < 6; ++j) s[j] += __ldcg(partials + 6 * b + j);
-        for (int j = 0; j < 6; ++j) step->dots[j] = s[j] / step->e_den;
-        *ticket = 0u;
+    if (last_block(ticket, gridDim.x)) {
+        // every thread sums a fixed stride of the blocks, then a fixed tree
+        double f[6] = {0, 0, 0, 0, 0, 0};
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+            for (int j = 0; j < 6; ++j) f[j] += __ldcg(partials + 6 * b + j);
+        double lo2[4] = {f[0], f[1], f[2], f[3]};
+        double hi2[2] = {f[4], f[5]};
+        block_sum<4>(lo2, sh);
+        block_sum<2>(hi2, sh + 32);
+        if (threadIdx.x == 0) {
+            const double tot[6] = {lo2[0], lo2[1], lo2[2], lo2[3], hi2[0], hi2[1]};
+            for (int j = 0; j < 6; ++j) step->dots[j] = tot[j] / step->e_den;
+            *ticket = 0u;
+        }
     }
 }
 
-__device__ __forceinline__ double line_e(const double* c, double th) {
-    const double s = sin(th), u = 1.0 - cos(th);
+// E(theta) from sin(theta) and cos(theta).
+__device__ __forceinline__ double line_e_sc(const double* c, double s, double co) {
+    const double u = 1.0 - co;
     return c[0] + 2 * s * c[1] + 2 * u * c[2] + s * s * c[3] + 2 * s * u * c[4] + u * u * c[5];
 }
-__device__ __forceinline__ double line_d1(const double* c, double th) {
-    const double s = sin(th), cc = cos(th), u = 1.0 - cc;
+__device__ __forceinline__ double line_e(const double* c, double th) { return line_e_sc(c, sin(th), cos(th)); }
+// dE/dtheta and d2E/dtheta2 from sin(theta) = s and cos(theta) = cc.
+__device__ __forceinline__ double line_d1(const double* c, double s, double cc) {
+    const double u = 1.0 - cc;
     return 2 * cc * c[1] + 2 * s * c[2] + 2 * s * cc * c[3] + 2 * (cc * u + s * s) * c[4] + 2 * u * s * c[5];
 }
-__device__ __forceinline__ double line_d2(const double* c, double th) {
-    const double s = sin(th), cc = cos(th), u = 1.0 - cc;
+__device__ __forceinline__ double line_d2(const double* c, double s, double cc) {
+    const double u = 1.0 - cc;
     return -2 * s * c[1] + 2 * cc * c[2] + 2 * (cc * cc - s * s) * c[3] +
            2 * (3 * s * cc - s * u) * c[4] + 2 * (s * s + u * cc) * c[5];
 }
@@ -639,7 +683,18 @@ __device__ __forceinline__ double sample_theta(int m) {
 // Angle for the update: the given one, or the line-search minimiser
 // (4096 samples over (-pi, pi], ties within 1e-10 max(1,|E_min|) to the
 // smallest |theta| then lowest index, Newton polish within one spacing).
-__global__ void k_line_search(DevStep* step, double theta_given) {
+// sin and cos of the 4096 sample angles, computed once per context (float64
+// transcendentals are slow on this part; one block would otherwise spend
+// most of the search on them).
+__global__ void k_line_table(double2* sc) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < 4096) {
+        const double th = sample_theta(m);
+        sc[m] = make_double2(sin(th), cos(th));
+    }
+}
+
+__global__ void k_line_search(DevStep* step, double theta_given, const double2* __restrict__ sc) {
     __shared__ double se[4096];
     __shared__ double red[32];
     __shared__ int redi[32];
@@ -658,7 +713,8 @@ __global__ void k_line_search(DevStep* step, double theta_given) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     double mn = INFINITY;
     for (int m = threadIdx.x; m < 4096; m += blockDim.x) {
-        const double e = line_e(c, sample_theta(m));
+        const double2 t = sc[m];
+        const double e = line_e_sc(c, t.x, t.y);
         se[m] = e;
         mn = fmin(mn, e);
     }
@@ -704,9 +760,11 @@ __global__ void k_line_search(DevStep* step, double theta_given) {
         const double h = 2.0 * kPi / 4096.0;
         double th = th0;
         for (int it = 0; it < 8; ++it) {
-            const double d2 = line_d2(c, th);
+            double sn, cs;
+            sincos(th, &sn, &cs);
+            const double d2 = line_d2(c, sn, cs);
             if (!(d2 > 0.0)) break;
-            const double stp = line_d1(c, th) / d2;
+            const double stp = line_d1(c, sn, cs) / d2;
             const double nt = th - stp;
             if (fabs(nt - th0) > h) break;
             th = nt;
@@ -856,58 +914,65 @@ int launch_select(const double* g, int M, double eps, int prec, DevStep* step, c
     return 1;
 }
 
-int launch_apply_twice(const PoolView& p, const DevStep* step, const void* psi, int prec, void* u1, void* u2,
-                       cudaStream_t s) {
+int launch_apply_twice(const PoolView& p, const DevStep* step, const void* psi, int prec, void* z, cudaStream_t s) {
     const long long D = 1ll << p.nq;
     const int bs = 256;
     const int grid = (int)((D + bs - 1) / bs < 2048 ? (D + bs - 1) / bs : 2048);
     if (prec == TQ_C128)
-        k_apply_twice<double><<<grid, bs, 0, s>>>(p, step, static_cast<const double2*>(psi),
-                                                   static_cast<double2*>(u1), static_cast<double2*>(u2), D);
+        k_apply_twice<double><<<grid, bs, 0, s>>>(p, step, static_cast<const double2*>(psi), static_cast<double2*>(z), D);
     else
-        k_apply_twice<float><<<grid, bs, 0, s>>>(p, step, static_cast<const float2*>(psi), static_cast<float2*>(u1),
-                                                  static_cast<float2*>(u2), D);
+        k_apply_twice<float><<<grid, bs, 0, s>>>(p, step, static_cast<const float2*>(psi), static_cast<float2*>(z), D);
     return 1;
 }
 
-int launch_line_spmv_gated(const HamView& h, const void* x0, const void* x1, const void* x2, double2* y0,
-                           double2* y1, double2* y2, const DevStep* gate, int sms, cudaStream_t s) {
-    constexpr int L = 8;
+namespace {
+
+template <int L>
+int launch_line_spmv_l(const HamView& h, const void* z, double2* y0, double2* y1, double2* y2, const DevStep* gate,
+                       int sms, cudaStream_t s) {
     const long long warps = (h.D + 32 / L - 1) / (32 / L);
     long long grid = (warps * 32 + 255) / 256;
-    const long long cap = (long long)energy_grid(h.D, sms);
+    const long long cap = (long long)sms * 16;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
     if (h.prec == TQ_C128)
-        k_line_spmv<double, L><<<(int)grid, 256, 0, s>>>(h, static_cast<const double2*>(x0),
-                                                          static_cast<const double2*>(x1),
-                                                          static_cast<const double2*>(x2), y0, y1, y2, gate);
+        k_line_spmv<double, L><<<(int)grid, 256, 0, s>>>(h, static_cast<const double2*>(z), y0, y1, y2, gate);
     else
-        k_line_spmv<float, L><<<(int)grid, 256, 0, s>>>(h, static_cast<const float2*>(x0),
-                                                         static_cast<const float2*>(x1),
-                                                         static_cast<const float2*>(x2), y0, y1, y2, gate);
+        k_line_spmv<float, L><<<(int)grid, 256, 0, s>>>(h, static_cast<const float2*>(z), y0, y1, y2, gate);
     return 1;
 }
 
+}  // namespace
 
-int launch_line_dots(const void* psi, const double2* w0, const double2* w1, const double2* w2, const void* u1,
-                     const void* u2, int prec, long long D, double* partials, unsigned* ticket, DevStep* step,
-                     cudaStream_t s) {
+// Lanes per row by the mean row length: the compensated sums are dependent
+// chains, so long rows get more lanes (shorter chains).
+int launch_line_spmv_gated(const HamView& h, const void* z, double2* y0, double2* y1, double2* y2,
+                           const DevStep* gate, int sms, cudaStream_t s) {
+    const long long per_row = h.D > 0 ? h.nnz / h.D : 0;
+    if (per_row >= 192) return launch_line_spmv_l<32>(h, z, y0, y1, y2, gate, sms, s);
+    if (per_row >= 48) return launch_line_spmv_l<16>(h, z, y0, y1, y2, gate, sms, s);
+    return launch_line_spmv_l<8>(h, z, y0, y1, y2, gate, sms, s);
+}
+
+
+int launch_line_dots(const void* z, const double2* w0, const double2* w1, const double2* w2, int prec, long long D,
+                     double* partials, unsigned* ticket, DevStep* step, cudaStream_t s) {
     const int bs = 256;
     const int grid = (int)((D + bs - 1) / bs < 512 ? (D + bs - 1) / bs : 512);
     if (prec == TQ_C128)
-        k_line_dots<double><<<grid, bs, 0, s>>>(static_cast<const double2*>(psi), w0, w1, w2,
-                                                 static_cast<const double2*>(u1), static_cast<const double2*>(u2), D,
-                                                 partials, ticket, step);
+        k_line_dots<double><<<grid, bs, 0, s>>>(static_cast<const double2*>(z), w0, w1, w2, D, partials, ticket, step);
     else
-        k_line_dots<float><<<grid, bs, 0, s>>>(static_cast<const float2*>(psi), w0, w1, w2,
-                                                static_cast<const float2*>(u1), static_cast<const float2*>(u2), D,
-                                                partials, ticket, step);
+        k_line_dots<float><<<grid, bs, 0, s>>>(static_cast<const float2*>(z), w0, w1, w2, D, partials, ticket, step);
     return 1;
 }
 
-int launch_line_search(DevStep* step, double theta_given, cudaStream_t s) {
-    k_line_search<<<1, 1024, 0, s>>>(step, theta_given);
+int launch_line_table(double2* sc, cudaStream_t s) {
+    k_line_table<<<16, 256, 0, s>>>(sc);
+    return 1;
+}
+
+int launch_line_search(DevStep* step, double theta_given, const double2* sc, cudaStream_t s) {
+    k_line_search<<<1, 1024, 0, s>>>(step, theta_given, sc);
     return 1;
 }
 

@@ -278,12 +278,12 @@ k_sector_grad(PoolView p, const double2* __restrict__ w, const typename C2<T>::t
     if (threadIdx.x == 0) g[k] = 2.0 * v[0] / step->e_den;
 }
 
-// u1 = A psi, u2 = A u1 = -psi on the rows A does not annihilate (A^2 = -I
-// on a pair), for the selected op; in the state's precision (exact: the
-// entries are +-1).
+// The line search's records {psi, u1 = A psi, u2 = A u1, 0} per sector row
+// (u2 = -psi on the rows A does not annihilate: A^2 = -I on a pair), for
+// the selected op, in the state's precision (exact: the entries are +-1).
 template <typename T>
 __global__ void k_apply_twice_sector(PoolView p, const DevStep* step, const typename C2<T>::type* psi,
-                                     typename C2<T>::type* u1, typename C2<T>::type* u2) {
+                                     typename C2<T>::type* z) {
     using V = typename C2<T>::type;
     if (step->converged) return;
     const long long dim = p.sdim;
@@ -294,8 +294,11 @@ __global__ void k_apply_twice_sector(PoolView p, const DevStep* step, const type
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < dim; r += stride) {
         const int sg = sgn[r];
         const V vc = psi[col[r]], vr = psi[r];
-        u1[r] = sg > 0 ? vc : (sg < 0 ? V{-vc.x, -vc.y} : V{T(0), T(0)});
-        u2[r] = sg ? V{-vr.x, -vr.y} : V{T(0), T(0)};
+        V* rec = z + 4 * r;
+        rec[0] = vr;
+        rec[1] = sg > 0 ? vc : (sg < 0 ? V{-vc.x, -vc.y} : V{T(0), T(0)});
+        rec[2] = sg ? V{-vr.x, -vr.y} : V{T(0), T(0)};
+        rec[3] = V{T(0), T(0)};
     }
 }
 
@@ -353,16 +356,16 @@ int launch_sector_gradients(const PoolView& p, const double2* w, const void* psi
     return 1;
 }
 
-int launch_apply_twice_sector(const PoolView& p, const DevStep* step, const void* psi, int prec, void* u1, void* u2,
+int launch_apply_twice_sector(const PoolView& p, const DevStep* step, const void* psi, int prec, void* z,
                               cudaStream_t s) {
     const long long dim = p.sdim;
     const int grid = (int)((dim + 255) / 256 < 1024 ? (dim + 255) / 256 : 1024);
     if (prec == TQ_C128)
         k_apply_twice_sector<double><<<grid, 256, 0, s>>>(p, step, static_cast<const double2*>(psi),
-                                                          static_cast<double2*>(u1), static_cast<double2*>(u2));
+                                                          static_cast<double2*>(z));
     else
         k_apply_twice_sector<float><<<grid, 256, 0, s>>>(p, step, static_cast<const float2*>(psi),
-                                                         static_cast<float2*>(u1), static_cast<float2*>(u2));
+                                                         static_cast<float2*>(z));
     return 1;
 }
 
