@@ -203,6 +203,7 @@ extern "C" int tq_ctx_create(int device, tq_ctx** out) {
         c->l2_fetch_default = (int)fetch;
         // the line search's sample table, filled before any call can read it
         c->line_sc = static_cast<double2*>(dev_alloc(4096 * sizeof(double2)));
+        c->line_se = static_cast<double*>(dev_alloc((4096 + 64) * sizeof(double)));
         launch(c, "line_table", 0, [&] { return launch_line_table(c->line_sc, 0); });
         TQ_CUDA(cudaDeviceSynchronize());
     } catch (...) {
@@ -222,6 +223,7 @@ extern "C" int tq_ctx_destroy(tq_ctx* c) {
     if (c->step) cudaFree(c->step);
     if (c->tickets) cudaFree(c->tickets);
     if (c->line_sc) cudaFree(c->line_sc);
+    if (c->line_se) cudaFree(c->line_se);
     for (auto& s : c->aux)
         if (s) cudaStreamDestroy(s);
     for (auto& r : c->trace) {
@@ -1402,7 +1404,8 @@ extern "C" int tq_adapt_step(tq_ctx* c, const tq_ham* h, const tq_pool* p, tq_st
         launch(c, "line_dots", s, [&] { return launch_line_dots(z, w0, w1, w2, psi->prec, D, part, c->tickets + 2,
                                                                 c->step, s); });
     }
-    launch(c, "line_search", s, [&] { return launch_line_search(c->step, theta, c->line_sc, s); });
+    launch(c, "line_search", s, [&] { return launch_line_search(c->step, theta, c->line_sc, c->line_se, c->tickets + 3,
+                                                                s); });
     const int upt = c->pair_upt[psi->prec];
     const int tiles = update_tiles(p, psi->prec, upt);
     if (!launch_update(c, p, 1, psi->prec, upt, psi->data, nullptr, nullptr, 0, 0.0, c->step, part, nullptr,

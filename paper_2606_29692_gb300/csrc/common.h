@@ -244,9 +244,11 @@ int launch_select(const double* g, int M, double eps, int prec, DevStep* step,
 int launch_apply_twice(const PoolView& p, const DevStep* step, const void* psi, int prec, void* z, cudaStream_t s);
 int launch_line_dots(const void* z, const double2* w0, const double2* w1, const double2* w2, int prec, long long D,
                      double* partials, unsigned* ticket, DevStep* step, cudaStream_t s);
-// sc: sin and cos of the 4096 sample angles (launch_line_table fills it).
+// sc: sin and cos of the 4096 sample angles (launch_line_table fills it);
+// se: 4096 + 16 doubles of scratch; ticket: zero between calls.
 int launch_line_table(double2* sc, cudaStream_t s);
-int launch_line_search(DevStep* step, double theta_given, const double2* sc, cudaStream_t s);
+int launch_line_search(DevStep* step, double theta_given, const double2* sc, double* se, unsigned* ticket,
+                       cudaStream_t s);
 
 // gated variants (skip when step->converged) and layout helpers
 int launch_taylor5_pair_gated(const PoolView& p, int prec, int upt, void* psi, const DevStep* step,
@@ -309,6 +311,7 @@ struct tq_ctx {
     tq::DevStep* step = nullptr;      // device
     unsigned* tickets = nullptr;      // device, zero between calls
     double2* line_sc = nullptr;       // device, sin/cos of the line search's sample angles (filled once)
+    double* line_se = nullptr;        // device, the samples' energies and per-block minima (4096 + 16)
     size_t tickets_n = 0;
     cudaStream_t aux[3] = {nullptr, nullptr, nullptr};
 };

@@ -680,12 +680,9 @@ __device__ __forceinline__ double sample_theta(int m) {
     return -kPi + 2.0 * kPi * (double)(m + 1) / 4096.0;
 }
 
-// Angle for the update: the given one, or the line-search minimiser
-// (4096 samples over (-pi, pi], ties within 1e-10 max(1,|E_min|) to the
-// smallest |theta| then lowest index, Newton polish within one spacing).
 // sin and cos of the 4096 sample angles, computed once per context (float64
-// transcendentals are slow on this part; one block would otherwise spend
-// most of the search on them).
+// transcendentals are slow on this part; the search would otherwise spend
+// most of its time on them).
 __global__ void k_line_table(double2* sc) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m < 4096) {
@@ -694,13 +691,30 @@ __global__ void k_line_table(double2* sc) {
     }
 }
 
-__global__ void k_line_search(DevStep* step, double theta_given, const double2* __restrict__ sc) {
-    __shared__ double se[4096];
-    __shared__ double red[32];
-    __shared__ int redi[32];
-    if (step->converged) return;
+// Angle for the update: the given one, or the line-search minimiser
+// (4096 samples over (-pi, pi], ties within 1e-10 max(1,|E_min|) to the
+// smallest |theta| then lowest index, Newton polish within one spacing).
+// The samples are spread over LS_BLOCKS blocks, one per thread, from the
+// context's sin/cos table; the last block to finish (a ticket) takes the
+// minimum, applies the tie rule and polishes.
+constexpr int LS_BS = 256;
+constexpr int LS_BLOCKS = 4096 / LS_BS;
+
+// Of two sample indices (-1: none), the one the tie rule prefers.
+__device__ __forceinline__ int line_pick(int a, int b) {
+    if (a < 0) return b;
+    if (b < 0) return a;
+    const double ta = fabs(sample_theta(a)), tb = fabs(sample_theta(b));
+    return (tb < ta || (tb == ta && b < a)) ? b : a;
+}
+
+__global__ void __launch_bounds__(LS_BS)
+k_line_search(DevStep* step, double theta_given, const double2* __restrict__ sc, double* se, unsigned* ticket) {
+    __shared__ double red[LS_BS / 32];
+    __shared__ int redi[LS_BS / 32];
+    if (step->converged) return;                 // uniform over the grid
     if (!isnan(theta_given)) {
-        if (threadIdx.x == 0) step->theta = theta_given;
+        if (blockIdx.x == 0 && threadIdx.x == 0) step->theta = theta_given;
         return;
     }
     double c[6];
@@ -710,53 +724,42 @@ __global__ void k_line_search(DevStep* step, double theta_given, const double2* 
     c[3] = step->dots[3];   // H11
     c[4] = step->dots[4];   // H12
     c[5] = step->dots[5];   // H22
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    double mn = INFINITY;
-    for (int m = threadIdx.x; m < 4096; m += blockDim.x) {
-        const double2 t = sc[m];
-        const double e = line_e_sc(c, t.x, t.y);
-        se[m] = e;
-        mn = fmin(mn, e);
-    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int NW = LS_BS / 32;
+    const int m0 = blockIdx.x * LS_BS + threadIdx.x;
+    const double2 t0 = sc[m0];
+    double mn = line_e_sc(c, t0.x, t0.y);
+    se[m0] = mn;
     for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));
     if (lane == 0) red[wid] = mn;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double m = INFINITY;
-        for (int i = 0; i < nw; ++i) m = fmin(m, red[i]);
-        red[0] = m;
+        double b = INFINITY;
+        for (int i = 0; i < NW; ++i) b = fmin(b, red[i]);
+        se[4096 + blockIdx.x] = b;
+    }
+    __threadfence();                              // every sample visible before the ticket
+    if (!last_block(ticket, gridDim.x)) return;
+    // the last block: global minimum, tie rule, polish
+    if (threadIdx.x == 0) {
+        double b = INFINITY;
+        for (int i = 0; i < LS_BLOCKS; ++i) b = fmin(b, __ldcg(se + 4096 + i));
+        red[0] = b;
     }
     __syncthreads();
     const double emin = red[0];
     const double tol = 1e-10 * fmax(1.0, fabs(emin));
-    // candidates within tol: key = (|theta| rank, index) -> pick smallest |theta|, then m
     int best = -1;
-    for (int m = threadIdx.x; m < 4096; m += blockDim.x) {
-        if (se[m] <= emin + tol) {
-            if (best < 0 || fabs(sample_theta(m)) < fabs(sample_theta(best)) ||
-                (fabs(sample_theta(m)) == fabs(sample_theta(best)) && m < best))
-                best = m;
-        }
-    }
-    __syncthreads();
-    for (int o = 16; o > 0; o >>= 1) {
-        const int other = __shfl_down_sync(0xffffffffu, best, o);
-        if (other >= 0 && (best < 0 || fabs(sample_theta(other)) < fabs(sample_theta(best)) ||
-                           (fabs(sample_theta(other)) == fabs(sample_theta(best)) && other < best)))
-            best = other;
-    }
+    for (int m = threadIdx.x; m < 4096; m += LS_BS)
+        if (__ldcg(se + m) <= emin + tol) best = line_pick(best, m);
+    for (int o = 16; o > 0; o >>= 1) best = line_pick(best, __shfl_down_sync(0xffffffffu, best, o));
     if (lane == 0) redi[wid] = best;
     __syncthreads();
     if (threadIdx.x == 0) {
         int b = -1;
-        for (int i = 0; i < nw; ++i) {
-            const int o = redi[i];
-            if (o >= 0 && (b < 0 || fabs(sample_theta(o)) < fabs(sample_theta(b)) ||
-                           (fabs(sample_theta(o)) == fabs(sample_theta(b)) && o < b)))
-                b = o;
-        }
+        for (int i = 0; i < NW; ++i) b = line_pick(b, redi[i]);
         const double th0 = sample_theta(b);
-        const double e0 = se[b];
+        const double e0 = __ldcg(se + b);
         const double h = 2.0 * kPi / 4096.0;
         double th = th0;
         for (int it = 0; it < 8; ++it) {
@@ -772,6 +775,7 @@ __global__ void k_line_search(DevStep* step, double theta_given, const double2* 
         }
         if (line_e(c, th) > e0) th = th0;
         step->theta = th;
+        *ticket = 0u;
     }
 }
 
@@ -971,8 +975,9 @@ int launch_line_table(double2* sc, cudaStream_t s) {
     return 1;
 }
 
-int launch_line_search(DevStep* step, double theta_given, const double2* sc, cudaStream_t s) {
-    k_line_search<<<1, 1024, 0, s>>>(step, theta_given, sc);
+int launch_line_search(DevStep* step, double theta_given, const double2* sc, double* se, unsigned* ticket,
+                       cudaStream_t s) {
+    k_line_search<<<LS_BLOCKS, LS_BS, 0, s>>>(step, theta_given, sc, se, ticket);
     return 1;
 }
 
