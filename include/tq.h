@@ -489,6 +489,22 @@ int tq_adapt_step(tq_ctx* ctx, const tq_ham* ham, const tq_pool* pool,
                   tq_state* psi, double eps, double theta,
                   tq_adapt_result* out, void* stream);
 
+/* n_iter ADAPT steps in a row (the loop of Sec. III-D) without a host round
+ * trip between them: the first step is launched directly, the next ones
+ * replay one captured CUDA graph of a step.  thetas (host, n_iter finite
+ * angles, copied) gives step i its angle; NULL runs the line search at every
+ * step (as tq_adapt_step with theta = NaN).  results[i] receives step i's
+ * result as tq_adapt_step reports it; *n_done is the number of steps up to
+ * and including the first converged one (n_iter if none converged).  Steps
+ * after convergence leave the state as it is (their records repeat the
+ * converged result).  TQ_ENUMERIC with *n_done = i + 1 if the update of
+ * step i left a non-finite or zero norm.  Runs on a stream of the context
+ * after the caller's stream is idle; synchronises.  Bit-identical to n_iter
+ * calls of tq_adapt_step. */
+int tq_adapt_run(tq_ctx* ctx, const tq_ham* ham, const tq_pool* pool,
+                 tq_state* psi, double eps, const double* thetas, int n_iter,
+                 tq_adapt_result* results, int* n_done, void* stream);
+
 /* ------------------------------------------------------------ batched */
 
 /* Batched Taylor-5: n_states states of the pool's qubit count, stored

@@ -500,6 +500,19 @@ def adapt_step(ctx, ham, pool, state, eps, theta=float("nan"), stream=None):
             "selected": r.selected, "converged": bool(r.converged)}
 
 
+def adapt_run(ctx, ham, pool, state, eps, n_iter, thetas=None, stream=None):
+    """n_iter ADAPT steps replayed from one CUDA graph; thetas (length
+    n_iter) or None for the line search.  Returns (results, n_done)."""
+    res = (AdaptResult * max(int(n_iter), 1))()
+    th = None if thetas is None else np.ascontiguousarray(thetas, dtype=np.float64)
+    done = C.c_int()
+    call("tq_adapt_run", ctx.handle, ham.handle, pool.handle, state.handle, float(eps), _ptr(th), int(n_iter),
+         C.cast(res, C.c_void_p), C.byref(done), _stream(stream))
+    out = [{"energy": r.energy, "max_grad": r.max_grad, "theta": r.theta, "selected": r.selected,
+            "converged": bool(r.converged)} for r in res[:int(n_iter)]]
+    return out, done.value
+
+
 def autotune_support(ctx, pool, prec=TQ_C64, n_states=1024):
     """Time every support-update schedule; set and return (pairs_per_thread, ms)."""
     u, ms = C.c_int(), C.c_double()

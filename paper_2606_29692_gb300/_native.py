@@ -103,6 +103,7 @@ SIGNATURES = {
     "tq_energy_noalloc": [i32, i32, vp, vp, vp, vp, vp, vp, vp],
     "tq_pool_gradients": [vp, vp, vp, vp, vp, i32, vp],
     "tq_adapt_step": [vp, vp, vp, vp, f64, f64, P(AdaptResult), vp],
+    "tq_adapt_run": [vp, vp, vp, vp, f64, vp, i32, vp, P(i32), vp],
     "tq_evolve_taylor5_batch": [vp, vp, i32, i32, vp, vp, vp, vp, vp],
     "tq_evolve_taylor5_batch_support": [vp, vp, i32, i32, vp, vp, vp, vp, vp],
     "tq_evolve_taylor5_batch_support_host": [vp, vp, i32, i32, vp, vp, vp, vp],

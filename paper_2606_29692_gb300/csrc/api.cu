@@ -46,7 +46,8 @@ unsigned* tickets(tq_ctx* c, size_t n) {
     return c->tickets;
 }
 
-enum { S_PART = 0, S_W0, S_U1, S_U2, S_W1, S_W2, S_G, S_STAGE, S_W32, S_PHI, S_CHI, S_AG, S_HOSTB };
+enum { S_PART = 0, S_W0, S_U1, S_U2, S_W1, S_W2, S_G, S_STAGE, S_W32, S_PHI, S_CHI, S_AG, S_HOSTB, S_REC,
+       S_THETAS };
 
 void run_energy(tq_ctx* c, const tq_ham* h, const tq_state* psi, double* part, cudaStream_t s);
 double* prepare(tq_ctx* c, long long D, const tq_pool* p, int nq);
@@ -1373,45 +1374,82 @@ extern "C" int tq_pool_gradients(tq_ctx* c, const tq_ham* h, const tq_pool* p, c
     API_END
 }
 
+namespace {
+
+// The device buffers of an ADAPT step, allocated before any of its launches
+// (and before a graph capture of them).
+struct AdaptBufs {
+    double* g;
+    void* z;           // {psi, A psi, A^2 psi, 0} per row
+    double2 *w0, *w1, *w2;
+    double* part;
+};
+
+AdaptBufs adapt_buffers(tq_ctx* c, const tq_ham* h, const tq_pool* p, const tq_state* psi) {
+    const long long D = h->D;
+    AdaptBufs b;
+    b.g = static_cast<double*>(scratch(c, S_G, (size_t)p->M * sizeof(double)));
+    const size_t vb = (size_t)D * sizeof(double2);
+    b.z = scratch(c, S_U1, 4 * (size_t)D * elem_bytes(psi->prec));
+    b.w1 = static_cast<double2*>(scratch(c, S_W1, vb));
+    b.w2 = static_cast<double2*>(scratch(c, S_W2, vb));
+    b.part = prepare(c, D, p, p->nq);
+    b.w0 = static_cast<double2*>(c->scratch[S_W0]);
+    return b;
+}
+
+// The launches of one ADAPT step on s (no host synchronisation): energy and
+// gradients, selection, the line search when the angle is not given (theta
+// NaN and no theta_list), the update and the renormalisation.  theta_list
+// (device, optional) gives step step->iter its angle.
+void enqueue_adapt_step(tq_ctx* c, const AdaptBufs& b, const tq_ham* h, const tq_pool* p, tq_state* psi, double eps,
+                        double theta, const double* theta_list, cudaStream_t s) {
+    const long long D = h->D;
+    run_gradients(c, h, p, psi, b.g, b.part, s);
+    launch(c, "select", s, [&] { return launch_select(b.g, p->M, eps, psi->prec, c->step, s); });
+    if (std::isnan(theta) && !theta_list) {
+        if (p->sector)
+            launch(c, "apply_twice_sector", s, [&] { return launch_apply_twice_sector(p->view, c->step, psi->data,
+                                                                                      psi->prec, b.z, s); });
+        else
+            launch(c, "apply_twice", s, [&] { return launch_apply_twice(p->view, c->step, psi->data, psi->prec, b.z, s); });
+        // H psi, H A psi and H A^2 psi from one pass with one arithmetic (w0
+        // is rewritten: the gradients that read it have run)
+        launch(c, "line_spmv_gated", s, [&] { return launch_line_spmv_gated(h->view, b.z, b.w0, b.w1, b.w2, c->step,
+                                                                             c->sm_count, s); });
+        launch(c, "line_dots", s, [&] { return launch_line_dots(b.z, b.w0, b.w1, b.w2, psi->prec, D, b.part,
+                                                                c->tickets + 2, c->step, s); });
+    }
+    launch(c, "line_search", s, [&] { return launch_line_search(c->step, theta, theta_list, c->line_sc, c->line_se,
+                                                                c->tickets + 3, s); });
+    const int upt = c->pair_upt[psi->prec];
+    const int tiles = update_tiles(p, psi->prec, upt);
+    if (!launch_update(c, p, 1, psi->prec, upt, psi->data, nullptr, nullptr, 0, 0.0, c->step, b.part, nullptr,
+                       &c->step->norm2, s))
+        launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(b.part, psi->prec, 1, tiles, nullptr,
+                                                                    &c->step->norm2, s); });
+    launch(c, "scale_gated", s, [&] { return launch_scale_gated(psi->data, psi->prec, D, &c->step->norm2, c->step, s); });
+}
+
+void check_adapt_args(const tq_ham* h, const tq_pool* p, const tq_state* psi, double eps) {
+    TQ_REQUIRE(std::isfinite(eps) && eps >= 0.0, "eps must be finite and >= 0");
+    check_space(h, psi);
+    check_space(p, psi);
+    TQ_REQUIRE(h->prec == psi->prec, "state and Hamiltonian precisions differ");
+}
+
+}  // namespace
+
 extern "C" int tq_adapt_step(tq_ctx* c, const tq_ham* h, const tq_pool* p, tq_state* psi, double eps,
                              double theta, tq_adapt_result* out, void* stream) {
     API_BEGIN
     TQ_REQUIRE(c && h && p && psi && out, "null argument");
-    TQ_REQUIRE(std::isfinite(eps) && eps >= 0.0, "eps must be finite and >= 0");
+    check_adapt_args(h, p, psi, eps);
     TQ_REQUIRE(std::isnan(theta) || std::isfinite(theta), "theta must be finite or NaN");
     set_device(c);
     cudaStream_t s = as_stream(stream);
-    const long long D = h->D;
-    double* g = static_cast<double*>(scratch(c, S_G, (size_t)p->M * sizeof(double)));
-    const size_t vb = (size_t)D * sizeof(double2);
-    void* z = scratch(c, S_U1, 4 * (size_t)D * elem_bytes(psi->prec));   // {psi, A psi, A^2 psi, 0} per row
-    double2* w1 = static_cast<double2*>(scratch(c, S_W1, vb));
-    double2* w2 = static_cast<double2*>(scratch(c, S_W2, vb));
-    double* part = prepare(c, D, p, p->nq);
-    double2* w0 = static_cast<double2*>(c->scratch[S_W0]);
-    run_gradients(c, h, p, psi, g, part, s);
-    launch(c, "select", s, [&] { return launch_select(g, p->M, eps, psi->prec, c->step, s); });
-    if (std::isnan(theta)) {
-        if (p->sector)
-            launch(c, "apply_twice_sector", s, [&] { return launch_apply_twice_sector(p->view, c->step, psi->data,
-                                                                                      psi->prec, z, s); });
-        else
-            launch(c, "apply_twice", s, [&] { return launch_apply_twice(p->view, c->step, psi->data, psi->prec, z, s); });
-        // H psi, H A psi and H A^2 psi from one pass with one arithmetic (w0
-        // is rewritten: the gradients that read it have run)
-        launch(c, "line_spmv_gated", s, [&] { return launch_line_spmv_gated(h->view, z, w0, w1, w2, c->step,
-                                                                             c->sm_count, s); });
-        launch(c, "line_dots", s, [&] { return launch_line_dots(z, w0, w1, w2, psi->prec, D, part, c->tickets + 2,
-                                                                c->step, s); });
-    }
-    launch(c, "line_search", s, [&] { return launch_line_search(c->step, theta, c->line_sc, c->line_se, c->tickets + 3,
-                                                                s); });
-    const int upt = c->pair_upt[psi->prec];
-    const int tiles = update_tiles(p, psi->prec, upt);
-    if (!launch_update(c, p, 1, psi->prec, upt, psi->data, nullptr, nullptr, 0, 0.0, c->step, part, nullptr,
-                       &c->step->norm2, s))
-        launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, psi->prec, 1, tiles, nullptr, &c->step->norm2, s); });
-    launch(c, "scale_gated", s, [&] { return launch_scale_gated(psi->data, psi->prec, D, &c->step->norm2, c->step, s); });
+    const AdaptBufs b = adapt_buffers(c, h, p, psi);
+    enqueue_adapt_step(c, b, h, p, psi, eps, theta, nullptr, s);
     DevStep hs;
     TQ_CUDA(cudaMemcpyAsync(&hs, c->step, sizeof(DevStep), cudaMemcpyDeviceToHost, s));
     TQ_CUDA(cudaStreamSynchronize(s));
@@ -1423,6 +1461,87 @@ extern "C" int tq_adapt_step(tq_ctx* c, const tq_ham* h, const tq_pool* p, tq_st
     out->theta = hs.converged ? 0.0 : hs.theta;
     if (!hs.converged && !(std::isfinite(hs.norm2) && hs.norm2 > 0.0))
         throw Error(TQ_ENUMERIC, "non-finite or zero norm after the update");
+    API_END
+}
+
+extern "C" int tq_adapt_run(tq_ctx* c, const tq_ham* h, const tq_pool* p, tq_state* psi, double eps,
+                            const double* thetas, int n_iter, tq_adapt_result* results, int* n_done, void* stream) {
+    API_BEGIN
+    TQ_REQUIRE(c && h && p && psi && results && n_done, "null argument");
+    check_adapt_args(h, p, psi, eps);
+    TQ_REQUIRE(n_iter >= 0, "n_iter < 0");
+    *n_done = 0;
+    if (n_iter == 0) return TQ_OK;
+    if (thetas)
+        for (int i = 0; i < n_iter; ++i) TQ_REQUIRE(std::isfinite(thetas[i]), "thetas must be finite");
+    set_device(c);
+    // the run goes on a stream of the context, after the caller's work
+    TQ_CUDA(cudaStreamSynchronize(as_stream(stream)));
+    if (!c->aux[1]) TQ_CUDA(cudaStreamCreateWithFlags(&c->aux[1], cudaStreamNonBlocking));
+    cudaStream_t s = c->aux[1];
+    const AdaptBufs b = adapt_buffers(c, h, p, psi);
+    double* rec = static_cast<double*>(scratch(c, S_REC, (size_t)n_iter * 6 * sizeof(double)));
+    double* dth = nullptr;
+    if (thetas) {
+        dth = static_cast<double*>(scratch(c, S_THETAS, (size_t)n_iter * sizeof(double)));
+        TQ_CUDA(cudaMemcpyAsync(dth, thetas, (size_t)n_iter * sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    TQ_CUDA(cudaMemsetAsync(&c->step->iter, 0, sizeof(int), s));
+    const double nan = std::nan("");
+    // step 0 directly (it also settles every lazily set launch attribute),
+    // then one step captured as a graph and replayed: no host round trip
+    // between steps
+    enqueue_adapt_step(c, b, h, p, psi, eps, nan, dth, s);
+    launch(c, "step_record", s, [&] { return launch_step_record(c->step, rec, n_iter, s); });
+    if (n_iter > 1) {
+        if (c->tracing) {
+            for (int i = 1; i < n_iter; ++i) {
+                enqueue_adapt_step(c, b, h, p, psi, eps, nan, dth, s);
+                launch(c, "step_record", s, [&] { return launch_step_record(c->step, rec, n_iter, s); });
+            }
+        } else {
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            TQ_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            try {
+                enqueue_adapt_step(c, b, h, p, psi, eps, nan, dth, s);
+                launch(c, "step_record", s, [&] { return launch_step_record(c->step, rec, n_iter, s); });
+            } catch (...) {
+                cudaStreamEndCapture(s, &graph);
+                if (graph) cudaGraphDestroy(graph);
+                throw;
+            }
+            TQ_CUDA(cudaStreamEndCapture(s, &graph));
+            const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            TQ_CUDA(ie);
+            cudaError_t le = cudaSuccess;
+            for (int i = 1; i < n_iter && le == cudaSuccess; ++i) le = cudaGraphLaunch(exec, s);
+            cudaGraphExecDestroy(exec);
+            TQ_CUDA(le);
+        }
+    }
+    std::vector<double> hr((size_t)n_iter * 6);
+    int status = 0;
+    TQ_CUDA(cudaMemcpyAsync(hr.data(), rec, hr.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TQ_CUDA(cudaMemcpyAsync(&status, &c->step->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TQ_CUDA(cudaStreamSynchronize(s));
+    raise_status(c, status, s);
+    int done = n_iter;
+    for (int i = 0; i < n_iter; ++i) {
+        const double* r = &hr[6 * (size_t)i];
+        results[i].energy = r[0];
+        results[i].max_grad = r[1];
+        results[i].theta = r[2];
+        results[i].selected = (int)r[3];
+        results[i].converged = (int)r[4];
+        if (r[5] != 0.0) {
+            *n_done = i + 1;
+            throw Error(TQ_ENUMERIC, "non-finite or zero norm after the update of step " + std::to_string(i));
+        }
+        if (results[i].converged && done == n_iter) done = i + 1;
+    }
+    *n_done = done;
     API_END
 }
 

@@ -166,7 +166,7 @@ struct DevStep {
     int selected;
     int converged;
     int status;                    // TQ_OK, or TQ_ETIMEOUT from a bounded wait
-    int pad;
+    int iter;                      // steps recorded by a graph-replayed ADAPT run
 };
 
 // ------------------------------------------------------------- kernel launchers
@@ -247,8 +247,13 @@ int launch_line_dots(const void* z, const double2* w0, const double2* w1, const 
 // sc: sin and cos of the 4096 sample angles (launch_line_table fills it);
 // se: 4096 + 16 doubles of scratch; ticket: zero between calls.
 int launch_line_table(double2* sc, cudaStream_t s);
-int launch_line_search(DevStep* step, double theta_given, const double2* sc, double* se, unsigned* ticket,
-                       cudaStream_t s);
+// theta_list (device, optional): the angle of step step->iter (overrides
+// theta_given).
+int launch_line_search(DevStep* step, double theta_given, const double* theta_list, const double2* sc, double* se,
+                       unsigned* ticket, cudaStream_t s);
+// Appends the step's result to rec (6 doubles per step: energy, max|g|,
+// theta, selected, converged, bad norm) at step->iter, then advances it.
+int launch_step_record(DevStep* step, double* rec, int n, cudaStream_t s);
 
 // gated variants (skip when step->converged) and layout helpers
 int launch_taylor5_pair_gated(const PoolView& p, int prec, int upt, void* psi, const DevStep* step,

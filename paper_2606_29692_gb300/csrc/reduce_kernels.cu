@@ -709,10 +709,12 @@ __device__ __forceinline__ int line_pick(int a, int b) {
 }
 
 __global__ void __launch_bounds__(LS_BS)
-k_line_search(DevStep* step, double theta_given, const double2* __restrict__ sc, double* se, unsigned* ticket) {
+k_line_search(DevStep* step, double theta_given, const double* theta_list, const double2* __restrict__ sc,
+              double* se, unsigned* ticket) {
     __shared__ double red[LS_BS / 32];
     __shared__ int redi[LS_BS / 32];
     if (step->converged) return;                 // uniform over the grid
+    if (theta_list) theta_given = theta_list[step->iter];
     if (!isnan(theta_given)) {
         if (blockIdx.x == 0 && threadIdx.x == 0) step->theta = theta_given;
         return;
@@ -975,9 +977,30 @@ int launch_line_table(double2* sc, cudaStream_t s) {
     return 1;
 }
 
-int launch_line_search(DevStep* step, double theta_given, const double2* sc, double* se, unsigned* ticket,
-                       cudaStream_t s) {
-    k_line_search<<<LS_BLOCKS, LS_BS, 0, s>>>(step, theta_given, sc, se, ticket);
+int launch_line_search(DevStep* step, double theta_given, const double* theta_list, const double2* sc, double* se,
+                       unsigned* ticket, cudaStream_t s) {
+    k_line_search<<<LS_BLOCKS, LS_BS, 0, s>>>(step, theta_given, theta_list, sc, se, ticket);
+    return 1;
+}
+
+__global__ void k_step_record(DevStep* step, double* rec, int n) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int i = step->iter;
+    if (i < n) {
+        const bool bad = !step->converged && !(isfinite(step->norm2) && step->norm2 > 0.0);
+        double* r = rec + 6 * (size_t)i;
+        r[0] = step->energy;
+        r[1] = step->max_grad;
+        r[2] = step->converged ? 0.0 : step->theta;
+        r[3] = (double)step->selected;
+        r[4] = (double)step->converged;
+        r[5] = bad ? 1.0 : 0.0;
+    }
+    step->iter = i + 1;
+}
+
+int launch_step_record(DevStep* step, double* rec, int n, cudaStream_t s) {
+    k_step_record<<<1, 32, 0, s>>>(step, rec, n);
     return 1;
 }
 

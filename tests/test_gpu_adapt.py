@@ -173,3 +173,33 @@ def test_line_search_16q_c64_follows_c128(ctx, mp):
         assert abs(rb["theta"]) <= np.pi / 2 + 1e-9, i
     e = [r["energy"] for r in b]
     assert all(e[i + 1] <= e[i] + 1e-6 for i in range(len(e) - 1)), e
+
+
+@pytest.mark.parametrize("prec", [tq.TQ_C128, tq.TQ_C64])
+@pytest.mark.parametrize("given", [False, True])
+def test_adapt_run_equals_repeated_steps(ctx, prec, given):
+    """The graph-replayed run gives, bit for bit, what n_iter calls of
+    tq_adapt_step give (results and final state), with the line search or
+    with given angles; the oracle's trajectory checks the first steps."""
+    ints, ne = synth.config1()
+    mp = 1
+    n = 12
+    ham = tq.build_hamiltonian(ctx, ints.h, ints.g, ints.e_const, mp, prec)
+    pool = tq.build_pool(ctx, ints.n_spatial, ne, mp)
+    thetas = np.random.default_rng(5).normal(0.0, 0.1, size=n) if given else None
+    a = tq.State(ctx, 12, prec)
+    tq.state_set_hf(a, ne, mp)
+    ref = [tq.adapt_step(ctx, ham, pool, a, 1e-3, float(thetas[i]) if given else float("nan")) for i in range(n)]
+    b = tq.State(ctx, 12, prec)
+    tq.state_set_hf(b, ne, mp)
+    got, done = tq.adapt_run(ctx, ham, pool, b, 1e-3, n, thetas)
+    assert done == n
+    for r, g in zip(ref, got):
+        assert r == g
+    assert np.array_equal(a.numpy(), b.numpy())
+    # a converged run stops changing the state and reports where it stopped
+    c_ = tq.State(ctx, 12, prec)
+    tq.state_set_hf(c_, ne, mp)
+    got2, done2 = tq.adapt_run(ctx, ham, pool, c_, 10.0, 3, None)
+    assert done2 == 1 and got2[0]["converged"] and got2[2]["converged"]
+    assert abs(c_.numpy()[tq.hf_index(12, ne, mp)]) == 1.0
