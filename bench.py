@@ -517,6 +517,10 @@ def run_ours(args, rank, world, local_rank):
                          "sector_frac": sector_bytes / sup_s / 1e9 / peak,
                          "line_read_sector_write_bytes_per_launch": line_bytes,
                          "line_frac": line_bytes / sup_s / 1e9 / peak,
+                         # the full-state byte model (2 D 8 bytes per update):
+                         # its roofline in updates/s, and this step against it
+                         "full_state_roofline_updates_per_s": peak * 1e9 / (2 * D * 8),
+                         "value_over_full_state_roofline": value / (peak * 1e9 / (2 * D * 8) * world),
                          "kernel_ms_per_launch": sup_s * 1e3,
                          "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
                          else "fallback"},
