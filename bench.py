@@ -1095,7 +1095,7 @@ def main():
                     help="run one secondary measurement alone and print its JSON (profiling)")
     ap.add_argument("--spmv-qubits", type=int, default=18)
     ap.add_argument("--traj", type=int, default=256)
-    ap.add_argument("--serve-seconds", type=float, default=10.0,
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the request-loop measurement (0 skips it)")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--pair-schedule", type=int, default=0,
