@@ -61,7 +61,9 @@ struct TrajState {
 namespace {
 
 constexpr int BT_BS = 256;
-constexpr int ROWS_PER_ITEM = ENERGY_ROWS;
+// An energy item is four 64-row blocks: each item pays a descriptor fetch,
+// a block sum and a ticket, so longer items spend less on them.
+constexpr int ROWS_PER_ITEM = 4 * ENERGY_ROWS;
 constexpr int BT_UPT = 2;
 
 template <typename T> __device__ __forceinline__ double2 d2(typename C2<T>::type v) {
@@ -109,8 +111,10 @@ kb_energy(const TrajDev* tr, TrajState* ts, const int4* items, int n_items, doub
         const V* psi = static_cast<const V*>(d.psi);
         const VT* val = static_cast<const VT*>(d.val);
         double num = 0.0, den = 0.0;
-        energy_rows<T, VT, LPR>(d.rowptr, d.col, val, d.diag, psi, d.w, d.w32, w4.y, (long long)w4.y + w4.z,
-                                num, den);
+        const long long end = (long long)w4.y + w4.z;
+        for (long long r0 = w4.y; r0 < end; r0 += ENERGY_ROWS)
+            energy_rows<T, VT, LPR>(d.rowptr, d.col, val, d.diag, psi, d.w, d.w32, r0,
+                                    r0 + ENERGY_ROWS < end ? r0 + ENERGY_ROWS : end, num, den);
         double v[2] = {num, den};
         block_sum<2>(v, sh);
         if (threadIdx.x == 0) {

@@ -182,35 +182,6 @@ __device__ __forceinline__ void OpSign<double>::load(const PoolView& p, int k) {
     for (int i = 0; i < 8; ++i) { z[i] = p.z[8 * k + i]; c[i] = p.cd[8 * k + i]; }
 }
 
-// Sum over one CSR row of val[e] * x[col[e]] for the entries e = e0 + lane,
-// e0 + lane + L, ... (L lanes per row), four independent gathers in flight
-// per lane.  Products and sums in T (the state's precision).
-template <typename T, typename VT, typename V, int L>
-__device__ __forceinline__ void row_dot(const int* __restrict__ col, const VT* __restrict__ val,
-                                        const V* __restrict__ x, int e0, int e1, int lane, T& px,
-                                        T& py) {
-    int e = e0 + lane;
-    for (; e + 3 * L < e1; e += 4 * L) {
-        const int c0 = col[e], c1 = col[e + L], c2 = col[e + 2 * L], c3 = col[e + 3 * L];
-        const T a0 = (T)val[e], a1 = (T)val[e + L], a2 = (T)val[e + 2 * L], a3 = (T)val[e + 3 * L];
-        const V v0 = x[c0], v1 = x[c1], v2 = x[c2], v3 = x[c3];
-        px = fma(a0, v0.x, px);
-        py = fma(a0, v0.y, py);
-        px = fma(a1, v1.x, px);
-        py = fma(a1, v1.y, py);
-        px = fma(a2, v2.x, px);
-        py = fma(a2, v2.y, py);
-        px = fma(a3, v3.x, px);
-        py = fma(a3, v3.y, py);
-    }
-    for (; e < e1; e += L) {
-        const T a = (T)val[e];
-        const V v = x[col[e]];
-        px = fma(a, v.x, px);
-        py = fma(a, v.y, py);
-    }
-}
-
 // Insert a zero bit at position b of v.
 __device__ __forceinline__ uint32_t insert_zero(uint32_t v, int b) {
     const uint32_t lo = v & ((1u << b) - 1u);
