@@ -1,7 +1,9 @@
-// C ABI of the library (declared in include/tq.h).  Argument checking,
-// handle lifetime, device memory, and the launch sequences of each call.
+// C ABI of the library (declared in include/tq.h): the context (schedules,
+// autotuners, tracing), host-only algebra, and the Hamiltonian, pool and
+// state objects.  The hot path is in api_path.cu, ADAPT-VQE in api_vqe.cu,
+// the helpers they share in api_common.cu.
+#include "api_internal.h"
 #include "dev.cuh"
-#include "host_util.h"
 #include "grad.cuh"
 
 #include <algorithm>
@@ -10,164 +12,11 @@
 #include <new>
 
 using namespace tq;
+using namespace tq::api;
 
 namespace {
 
 thread_local std::string g_last_error;
-
-template <typename T>
-T* upload(std::vector<void*>& allocs, const std::vector<T>& v) {
-    T* p = static_cast<T*>(dev_alloc(v.size() * sizeof(T)));
-    allocs.push_back(p);
-    if (!v.empty()) TQ_CUDA(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
-    return p;
-}
-
-void* scratch(tq_ctx* c, int slot, size_t bytes) {
-    if (c->scratch_bytes[slot] < bytes) {
-        if (c->scratch[slot]) TQ_CUDA(cudaFree(c->scratch[slot]));
-        c->scratch[slot] = nullptr;
-        c->scratch_bytes[slot] = 0;
-        c->scratch[slot] = dev_alloc(bytes);
-        c->scratch_bytes[slot] = bytes;
-    }
-    return c->scratch[slot];
-}
-
-unsigned* tickets(tq_ctx* c, size_t n) {
-    if (c->tickets_n < n) {
-        if (c->tickets) TQ_CUDA(cudaFree(c->tickets));
-        c->tickets = nullptr;
-        c->tickets_n = 0;
-        c->tickets = static_cast<unsigned*>(dev_alloc(n * sizeof(unsigned)));
-        TQ_CUDA(cudaMemset(c->tickets, 0, n * sizeof(unsigned)));
-        c->tickets_n = n;
-    }
-    return c->tickets;
-}
-
-enum { S_PART = 0, S_W0, S_U1, S_U2, S_W1, S_W2, S_G, S_STAGE, S_W32, S_PHI, S_CHI, S_AG, S_HOSTB, S_REC,
-       S_THETAS };
-
-void run_energy(tq_ctx* c, const tq_ham* h, const tq_state* psi, double* part, cudaStream_t s);
-double* prepare(tq_ctx* c, long long D, const tq_pool* p, int nq);
-
-size_t elem_bytes(int prec) { return prec == TQ_C128 ? 16 : 8; }
-
-void check_prec(int prec) {
-    TQ_REQUIRE(prec == TQ_C128 || prec == TQ_C64, "prec must be TQ_C128 or TQ_C64");
-}
-
-cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
-
-void set_device(const tq_ctx* c) { TQ_CUDA(cudaSetDevice(c->device)); }
-
-// Build the CSR of a grouped Pauli sum into (rowptr, col, val); returns nnz.
-long long build_csr(tq_ctx* c, HamView& h, double maxc, int prec, std::vector<void*>& allocs,
-                    long long* n_amb, int* max_row) {
-    const long long D = h.D;
-    int* counts = static_cast<int*>(scratch(c, S_G, (size_t)D * sizeof(int)));
-    int* rowptr = static_cast<int*>(dev_alloc((size_t)(D + 1) * sizeof(int)));
-    allocs.push_back(rowptr);
-    struct Out { long long total; int max_row; int pad; unsigned long long amb; };
-    Out* dout = static_cast<Out*>(scratch(c, S_PART, sizeof(Out)));
-    TQ_CUDA(cudaMemset(dout, 0, sizeof(Out)));
-    const double tol = 1e-12 * maxc, amb_hi = 1e-9 * maxc;
-    if (h.G > 0) {
-        launch(c, "csr_count", 0, [&] { return launch_csr_count(h, tol, amb_hi, counts, &dout->amb, c->sm_count, 0); });
-    } else {
-        TQ_CUDA(cudaMemset(counts, 0, (size_t)D * sizeof(int)));
-    }
-    launch(c, "scan", 0, [&] { return launch_scan(counts, D, rowptr, &dout->total, &dout->max_row, 0); });
-    Out hout;
-    TQ_CUDA(cudaMemcpy(&hout, dout, sizeof(Out), cudaMemcpyDeviceToHost));
-    if (hout.total >= 2147483647ll)
-        throw Error(TQ_ENOMEM, "CSR has 2^31 or more non-zeros; int32 indices cannot address it");
-    const long long nnz = hout.total;
-    int* col = static_cast<int*>(dev_alloc((size_t)nnz * sizeof(int)));
-    allocs.push_back(col);
-    void* val = dev_alloc((size_t)nnz * (prec == TQ_C128 ? sizeof(double) : sizeof(float)));
-    allocs.push_back(val);
-    h.rowptr = rowptr;
-    h.col = col;
-    h.val = val;
-    h.nnz = nnz;
-    if (nnz > 0) launch(c, "csr_fill", 0, [&] { return launch_csr_fill(h, tol, hout.max_row, col, val, prec, c->sm_count, 0); });
-    TQ_CUDA(cudaDeviceSynchronize());
-    if (n_amb) *n_amb = (long long)hout.amb;
-    if (max_row) *max_row = hout.max_row;
-    return nnz;
-}
-
-// XOR-ELL form of the same off-diagonal entries (blocks of XELL_ROWS rows);
-// returns the number of pairs.
-long long build_xell(tq_ctx* c, HamView& h, double maxc, int prec, std::vector<void*>& allocs) {
-    h.n_blocks = (h.D + XELL_ROWS - 1) / XELL_ROWS;
-    const long long B = h.n_blocks;
-    int* counts = static_cast<int*>(scratch(c, S_G, (size_t)B * sizeof(int)));
-    int* xptr = static_cast<int*>(dev_alloc((size_t)(B + 1) * sizeof(int)));
-    allocs.push_back(xptr);
-    struct Out { long long total; int max_row; int pad; };
-    Out* dout = static_cast<Out*>(scratch(c, S_PART, sizeof(Out)));
-    TQ_CUDA(cudaMemset(dout, 0, sizeof(Out)));
-    const double tol = 1e-12 * maxc;
-    if (h.G > 0) {
-        launch(c, "xell_count", 0, [&] { return launch_xell_count(h, tol, counts, c->sm_count, 0); });
-    } else {
-        TQ_CUDA(cudaMemset(counts, 0, (size_t)B * sizeof(int)));
-    }
-    launch(c, "scan", 0, [&] { return launch_scan(counts, B, xptr, &dout->total, &dout->max_row, 0); });
-    Out hout;
-    TQ_CUDA(cudaMemcpy(&hout, dout, sizeof(Out), cudaMemcpyDeviceToHost));
-    if (hout.total >= 2147483647ll)
-        throw Error(TQ_ENOMEM, "XOR-ELL has 2^31 or more pairs; int32 offsets cannot address it");
-    const long long np = hout.total;
-    // padded to whole copy chunks: the staged energy copies chunk by chunk
-    const long long chunk = xell_chunk_pairs();
-    const long long cap = std::max(1ll, (np + chunk - 1) / chunk) * chunk;
-    const size_t vb = prec == TQ_C128 ? sizeof(double) : sizeof(float);
-    uint32_t* xmask = static_cast<uint32_t*>(dev_alloc((size_t)cap * sizeof(uint32_t)));
-    allocs.push_back(xmask);
-    void* xval = dev_alloc((size_t)cap * XELL_ROWS * vb);
-    allocs.push_back(xval);
-    TQ_CUDA(cudaMemset(xmask + np, 0, (size_t)(cap - np) * sizeof(uint32_t)));
-    TQ_CUDA(cudaMemset(static_cast<char*>(xval) + (size_t)np * XELL_ROWS * vb, 0,
-                       (size_t)(cap - np) * XELL_ROWS * vb));
-    h.xptr = xptr;
-    h.xmask = xmask;
-    h.xval = xval;
-    h.n_pairs = np;
-    if (np > 0) launch(c, "xell_fill", 0, [&] { return launch_xell_fill(h, tol, xmask, xval, prec, c->sm_count, 0); });
-    // pair-balanced block ranges for the staged energy launch
-    h.xgrid = xell_grid(B, prec, c->sm_count);
-    int* split = static_cast<int*>(dev_alloc((size_t)(h.xgrid + 1) * sizeof(int)));
-    allocs.push_back(split);
-    h.xsplit = split;
-    launch(c, "xell_split", 0, [&] { return launch_xell_split(xptr, B, h.xgrid, split, 0); });
-    TQ_CUDA(cudaDeviceSynchronize());
-    return np;
-}
-
-// A pool, Hamiltonian and state must describe the same space: the same
-// qubit count, and either all the full space or all the same sector.
-void check_space(const tq_pool* p, const tq_state* s) {
-    TQ_REQUIRE(s->nq == p->nq, "state and pool qubit counts differ");
-    TQ_REQUIRE(s->sector == p->sector, "state and pool differ in sector restriction");
-    if (p->sector)
-        TQ_REQUIRE(s->n_alpha == p->n_alpha && s->n_beta == p->n_beta, "state and pool sectors differ");
-}
-void check_space(const tq_ham* h, const tq_state* s) {
-    TQ_REQUIRE(h->nq == s->nq, "state and Hamiltonian qubit counts differ");
-    TQ_REQUIRE(h->sector == s->sector, "state and Hamiltonian differ in sector restriction");
-    if (h->sector)
-        TQ_REQUIRE(s->n_alpha == h->n_alpha && s->n_beta == h->n_beta, "state and Hamiltonian sectors differ");
-}
-
-void free_all(std::vector<void*>& allocs) {
-    for (void* p : allocs)
-        if (p) cudaFree(p);
-    allocs.clear();
-}
 
 }  // namespace
 
@@ -1177,744 +1026,4 @@ extern "C" int tq_state_free(tq_state* s) {
     delete s;
     (void)cudaGetLastError();   // a failure while freeing is not reported to later calls
     return TQ_OK;
-}
-
-// ================================================================ hot path
-
-namespace {
-
-long long state_len(const tq_pool* p) { return p->sector ? p->view.sdim : 1ll << p->nq; }
-
-// norm partials per state of the Taylor-5 launch for this pool
-int update_tiles(const tq_pool* p, int prec, int upt) {
-    return p->sector ? sector_tiles(p->view.sdim, prec) : taylor5_pair_parts(p->nq, upt);
-}
-
-// Taylor-5 on n states (ops and angles from k/theta arrays, or k_fixed and
-// theta_fixed, or the step record when `gate` is set).  Returns true when
-// the launch also wrote the float64 norms (norm2[i] and/or *step_norm2);
-// otherwise they are in `part`, for launch_norm_reduce.
-bool launch_update(tq_ctx* c, const tq_pool* p, long long n, int prec, int upt, void* psi, const int* k,
-                   const double* theta, int k_fixed, double theta_fixed, const DevStep* gate, double* part,
-                   double* norm2, double* step_norm2, cudaStream_t s) {
-    if (p->sector) {
-        launch(c, gate ? "taylor5_sector_gated" : "taylor5_sector", s, [&] {
-            return launch_taylor5_sector(p->view, n, prec, psi, k, theta, k_fixed, theta_fixed, gate, part, norm2,
-                                         step_norm2, s);
-        });
-        return sector_in_smem(p->view.sdim, prec);
-    }
-    if (gate) {
-        launch(c, "taylor5_pair_gated", s, [&] { return launch_taylor5_pair_gated(p->view, prec, upt, psi, gate, part,
-                                                  c->sm_count, s); });
-    } else {
-        launch(c, "taylor5_pair", s, [&] { return launch_taylor5_pair(p->view, (int)n, prec, upt, psi, k, theta, k_fixed,
-                                                                      theta_fixed, part, c->sm_count, s); });
-    }
-    return false;
-}
-
-}  // namespace
-
-extern "C" int tq_evolve_taylor5(tq_ctx* c, const tq_pool* p, int k, double theta, tq_state* psi,
-                                 int renormalize, void* stream) {
-    API_BEGIN
-    TQ_REQUIRE(c && p && psi, "null argument");
-    TQ_REQUIRE(k >= 0 && k < p->M, "pool index out of range");
-    TQ_REQUIRE(std::isfinite(theta), "theta is not finite");
-    check_space(p, psi);
-    set_device(c);
-    cudaStream_t s = as_stream(stream);
-    const int upt = c->pair_upt[psi->prec];
-    const int tiles = update_tiles(p, psi->prec, upt);
-    double* part = static_cast<double*>(scratch(c, S_PART, (size_t)tiles * sizeof(double)));
-    const bool fin = launch_update(c, p, 1, psi->prec, upt, psi->data, nullptr, nullptr, k, theta, nullptr, part,
-                                   nullptr, renormalize ? &c->step->norm2 : nullptr, s);
-    if (renormalize) {
-        if (!fin)
-            launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, psi->prec, 1, tiles, nullptr, &c->step->norm2, s); });
-        launch(c, "scale", s, [&] { return launch_scale(psi->data, psi->prec, psi->D, &c->step->norm2, s); });
-    }
-    API_END
-}
-
-extern "C" int tq_evolve_taylor5_csr(tq_ctx* c, int n_qubits, const int* rowptr, const int* col,
-                                     const void* val, double theta, tq_state* psi, int renormalize,
-                                     void* stream) {
-    API_BEGIN
-    TQ_REQUIRE(c && rowptr && col && val && psi, "null argument");
-    TQ_REQUIRE(std::isfinite(theta), "theta is not finite");
-    TQ_REQUIRE(psi->nq == n_qubits, "state and operator qubit counts differ");
-    set_device(c);
-    const long long D = psi->D;
-    const size_t vb = (size_t)D * elem_bytes(psi->prec);
-    double* acc = static_cast<double*>(scratch(c, S_U1, vb));
-    double* v0 = static_cast<double*>(scratch(c, S_U2, vb));
-    double* v1 = static_cast<double*>(scratch(c, S_W1, vb));
-    double* part = static_cast<double*>(scratch(c, S_PART, (size_t)c->sm_count * 4 * sizeof(double)));
-    launch(c, "taylor5_csr", as_stream(stream), [&] { return launch_taylor5_csr(n_qubits, psi->prec, rowptr, col, val, theta, psi->data, renormalize,
-                                       acc, v0, v1, part, &c->step->norm2, c->sm_count, as_stream(stream)); });
-    API_END
-}
-
-namespace {
-
-// Partials needed by energy + gradients (+ line search) on this problem.
-size_t partials_needed(long long D, int n_gitems, int nq, int sms) {
-    size_t n = (size_t)energy_grid(D, sms) * 2;
-    n = std::max(n, (size_t)16 * sms);      // any persistent energy grid (at most 8 blocks per SM)
-    n = std::max(n, (size_t)std::max(n_gitems, 0));
-    n = std::max(n, (size_t)512 * 6);            // the line search's six dots per block
-    n = std::max(n, (size_t)taylor5_pair_parts(nq, 1));
-    return n + 8;
-}
-
-void run_energy(tq_ctx* c, const tq_ham* h, const tq_state* psi, double* part, cudaStream_t s) {
-    check_space(h, psi);
-    TQ_REQUIRE(h->prec == psi->prec, "state and Hamiltonian precisions differ");
-    double2* w = static_cast<double2*>(c->scratch[S_W0]);
-    float2* w32 = psi->prec == TQ_C64 ? static_cast<float2*>(c->scratch[S_W32]) : nullptr;
-    // a sector Hamiltonian has the CSR only
-    const int lanes = c->spmv_lanes == TQ_SPMV_XELL && h->sector ? 8 : c->spmv_lanes;
-    if (lanes == TQ_SPMV_XELL)
-        launch(c, "energy_xell", s, [&] {
-            return launch_energy_xell(h->view, psi->data, psi->prec, w, w32, part, c->tickets, c->step, s,
-                                      (c->test_flags & TQ_TEST_WITHHOLD_CHUNK) ? 0 : -1);
-        });
-    else
-        launch(c, "energy_csr", s, [&] { return launch_energy_csr2(h->view, psi->data, psi->prec, w, w32, part,
-                                                                   c->tickets, c->step, c->sm_count, s, lanes); });
-}
-
-void run_gradients(tq_ctx* c, const tq_ham* h, const tq_pool* p, const tq_state* psi, double* g,
-                   double* part, cudaStream_t s) {
-    check_space(p, psi);
-    run_energy(c, h, psi, part, s);
-    if (p->sector) {
-        launch(c, "sector_gradients", s, [&] {
-            return launch_sector_gradients(p->view, static_cast<double2*>(c->scratch[S_W0]), psi->data, psi->prec,
-                                           c->step, g, s);
-        });
-        return;
-    }
-    launch(c, "pool_gradients", s, [&] {
-        return launch_pool_gradients(p->view, static_cast<double2*>(c->scratch[S_W0]),
-                                     static_cast<float2*>(c->scratch[S_W32]), psi->data, psi->prec, c->step,
-                                     part, c->tickets + 16, g, c->sm_count, s);
-    });
-}
-
-// Allocate (before any launch of the call) the scratch energy/gradients use.
-double* prepare(tq_ctx* c, long long D, const tq_pool* p, int nq) {
-    scratch(c, S_W0, (size_t)D * sizeof(double2));
-    scratch(c, S_W32, (size_t)D * sizeof(float2));
-    tickets(c, 16 + (size_t)(p ? p->M : 0) + 64);
-    return static_cast<double*>(
-        scratch(c, S_PART, partials_needed(D, p ? p->view.n_gitems : 0, nq, c->sm_count) * sizeof(double)));
-}
-
-// A kernel that gave up on a bounded wait left TQ_ETIMEOUT in the step's
-// status word: clear it and report the failure.
-void raise_status(tq_ctx* c, int status, cudaStream_t s) {
-    if (status == TQ_OK) return;
-    TQ_CUDA(cudaMemsetAsync(&c->step->status, 0, sizeof(int), s));
-    TQ_CUDA(cudaStreamSynchronize(s));
-    throw Error(status, "a kernel wait timed out; its results are invalid");
-}
-
-}  // namespace
-
-extern "C" int tq_energy(tq_ctx* c, const tq_ham* h, const tq_state* psi, double* E, void* stream) {
-    API_BEGIN
-    TQ_REQUIRE(c && h && psi && E, "null argument");
-    set_device(c);
-    cudaStream_t s = as_stream(stream);
-    double* part = prepare(c, h->D, nullptr, h->nq);
-    run_energy(c, h, psi, part, s);
-    int status = 0;
-    TQ_CUDA(cudaMemcpyAsync(E, &c->step->energy, sizeof(double), cudaMemcpyDeviceToHost, s));
-    TQ_CUDA(cudaMemcpyAsync(&status, &c->step->status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    TQ_CUDA(cudaStreamSynchronize(s));
-    raise_status(c, status, s);
-    API_END
-}
-
-extern "C" int tq_energy_matrix_free(tq_ctx* c, const tq_ham* h, const tq_state* psi, double* E,
-                                     void* stream) {
-    API_BEGIN
-    TQ_REQUIRE(c && h && psi && E, "null argument");
-    TQ_REQUIRE(!h->sector, "the matrix-free energy works in the full space only");
-    check_space(h, psi);
-    set_device(c);
-    cudaStream_t s = as_stream(stream);
-    double* part = prepare(c, h->D, nullptr, h->nq);
-    launch(c, "energy_matrix_free", s, [&] { return launch_energy_matrix_free(h->view, psi->data, psi->prec, part, c->tickets + 1,
-                                              c->step, c->sm_count, s); });
-    TQ_CUDA(cudaMemcpyAsync(E, &c->step->energy, sizeof(double), cudaMemcpyDeviceToHost, s));
-    TQ_CUDA(cudaStreamSynchronize(s));
-    API_END
-}
-
-extern "C" int tq_pool_gradients(tq_ctx* c, const tq_ham* h, const tq_pool* p, const tq_state* psi, double* g,
-                                 int g_on_device, void* stream) {
-    API_BEGIN
-    TQ_REQUIRE(c && h && p && psi && g, "null argument");
-    set_device(c);
-    cudaStream_t s = as_stream(stream);
-    double* gd = g_on_device ? g : static_cast<double*>(scratch(c, S_G, (size_t)p->M * sizeof(double)));
-    double* part = prepare(c, h->D, p, p->nq);
-    run_gradients(c, h, p, psi, gd, part, s);
-    if (!g_on_device) {
-        int status = 0;
-        TQ_CUDA(cudaMemcpyAsync(g, gd, (size_t)p->M * sizeof(double), cudaMemcpyDeviceToHost, s));
-        TQ_CUDA(cudaMemcpyAsync(&status, &c->step->status, sizeof(int), cudaMemcpyDeviceToHost, s));
-        TQ_CUDA(cudaStreamSynchronize(s));
-        raise_status(c, status, s);
-    }
-    API_END
-}
-
-namespace {
-
-// The device buffers of an ADAPT step, allocated before any of its launches
-// (and before a graph capture of them).
-struct AdaptBufs {
-    double* g;
-    void* z;           // {psi, A psi, A^2 psi, 0} per row
-    double2 *w0, *w1, *w2;
-    double* part;
-};
-
-AdaptBufs adapt_buffers(tq_ctx* c, const tq_ham* h, const tq_pool* p, const tq_state* psi) {
-    const long long D = h->D;
-    AdaptBufs b;
-    b.g = static_cast<double*>(scratch(c, S_G, (size_t)p->M * sizeof(double)));
-    const size_t vb = (size_t)D * sizeof(double2);
-    b.z = scratch(c, S_U1, 4 * (size_t)D * elem_bytes(psi->prec));
-    b.w1 = static_cast<double2*>(scratch(c, S_W1, vb));
-    b.w2 = static_cast<double2*>(scratch(c, S_W2, vb));
-    b.part = prepare(c, D, p, p->nq);
-    b.w0 = static_cast<double2*>(c->scratch[S_W0]);
-    return b;
-}
-
-// The launches of one ADAPT step on s (no host synchronisation): energy and
-// gradients, selection, the line search when the angle is not given (theta
-// NaN and no theta_list), the update and the renormalisation.  theta_list
-// (device, optional) gives step step->iter its angle.
-void enqueue_adapt_step(tq_ctx* c, const AdaptBufs& b, const tq_ham* h, const tq_pool* p, tq_state* psi, double eps,
-                        double theta, const double* theta_list, cudaStream_t s) {
-    const long long D = h->D;
-    run_gradients(c, h, p, psi, b.g, b.part, s);
-    launch(c, "select", s, [&] { return launch_select(b.g, p->M, eps, psi->prec, c->step, s); });
-    if (std::isnan(theta) && !theta_list) {
-        if (p->sector)
-            launch(c, "apply_twice_sector", s, [&] { return launch_apply_twice_sector(p->view, c->step, psi->data,
-                                                                                      psi->prec, b.z, s); });
-        else
-            launch(c, "apply_twice", s, [&] { return launch_apply_twice(p->view, c->step, psi->data, psi->prec, b.z, s); });
-        // H psi, H A psi and H A^2 psi from one pass with one arithmetic (w0
-        // is rewritten: the gradients that read it have run)
-        launch(c, "line_spmv_gated", s, [&] { return launch_line_spmv_gated(h->view, b.z, b.w0, b.w1, b.w2, c->step,
-                                                                             c->sm_count, s); });
-        launch(c, "line_dots", s, [&] { return launch_line_dots(b.z, b.w0, b.w1, b.w2, psi->prec, D, b.part,
-                                                                c->tickets + 2, c->step, s); });
-    }
-    launch(c, "line_search", s, [&] { return launch_line_search(c->step, theta, theta_list, c->line_sc, c->line_se,
-                                                                c->tickets + 3, s); });
-    const int upt = c->pair_upt[psi->prec];
-    const int tiles = update_tiles(p, psi->prec, upt);
-    if (!launch_update(c, p, 1, psi->prec, upt, psi->data, nullptr, nullptr, 0, 0.0, c->step, b.part, nullptr,
-                       &c->step->norm2, s))
-        launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(b.part, psi->prec, 1, tiles, nullptr,
-                                                                    &c->step->norm2, s); });
-    launch(c, "scale_gated", s, [&] { return launch_scale_gated(psi->data, psi->prec, D, &c->step->norm2, c->step, s); });
-}
-
-void check_adapt_args(const tq_ham* h, const tq_pool* p, const tq_state* psi, double eps) {
-    TQ_REQUIRE(std::isfinite(eps) && eps >= 0.0, "eps must be finite and >= 0");
-    check_space(h, psi);
-    check_space(p, psi);
-    TQ_REQUIRE(h->prec == psi->prec, "state and Hamiltonian precisions differ");
-}
-
-}  // namespace
-
-extern "C" int tq_adapt_step(tq_ctx* c, const tq_ham* h, const tq_pool* p, tq_state* psi, double eps,
-                             double theta, tq_adapt_result* out, void* stream) {
-    API_BEGIN
-    TQ_REQUIRE(c && h && p && psi && out, "null argument");
-    check_adapt_args(h, p, psi, eps);
-    TQ_REQUIRE(std::isnan(theta) || std::isfinite(theta), "theta must be finite or NaN");
-    set_device(c);
-    cudaStream_t s = as_stream(stream);
-    const AdaptBufs b = adapt_buffers(c, h, p, psi);
-    enqueue_adapt_step(c, b, h, p, psi, eps, theta, nullptr, s);
-    DevStep hs;
-    TQ_CUDA(cudaMemcpyAsync(&hs, c->step, sizeof(DevStep), cudaMemcpyDeviceToHost, s));
-    TQ_CUDA(cudaStreamSynchronize(s));
-    raise_status(c, hs.status, s);
-    out->energy = hs.energy;
-    out->max_grad = hs.max_grad;
-    out->selected = hs.selected;
-    out->converged = hs.converged;
-    out->theta = hs.converged ? 0.0 : hs.theta;
-    if (!hs.converged && !(std::isfinite(hs.norm2) && hs.norm2 > 0.0))
-        throw Error(TQ_ENUMERIC, "non-finite or zero norm after the update");
-    API_END
-}
-
-extern "C" int tq_adapt_run(tq_ctx* c, const tq_ham* h, const tq_pool* p, tq_state* psi, double eps,
-                            const double* thetas, int n_iter, tq_adapt_result* results, int* n_done, void* stream) {
-    API_BEGIN
-    TQ_REQUIRE(c && h && p && psi && results && n_done, "null argument");
-    check_adapt_args(h, p, psi, eps);
-    TQ_REQUIRE(n_iter >= 0, "n_iter < 0");
-    *n_done = 0;
-    if (n_iter == 0) return TQ_OK;
-    if (thetas)
-        for (int i = 0; i < n_iter; ++i) TQ_REQUIRE(std::isfinite(thetas[i]), "thetas must be finite");
-    set_device(c);
-    // the run goes on a stream of the context, after the caller's work
-    TQ_CUDA(cudaStreamSynchronize(as_stream(stream)));
-    if (!c->aux[1]) TQ_CUDA(cudaStreamCreateWithFlags(&c->aux[1], cudaStreamNonBlocking));
-    cudaStream_t s = c->aux[1];
-    const AdaptBufs b = adapt_buffers(c, h, p, psi);
-    double* rec = static_cast<double*>(scratch(c, S_REC, (size_t)n_iter * 6 * sizeof(double)));
-    double* dth = nullptr;
-    if (thetas) {
-        dth = static_cast<double*>(scratch(c, S_THETAS, (size_t)n_iter * sizeof(double)));
-        TQ_CUDA(cudaMemcpyAsync(dth, thetas, (size_t)n_iter * sizeof(double), cudaMemcpyHostToDevice, s));
-    }
-    TQ_CUDA(cudaMemsetAsync(&c->step->iter, 0, sizeof(int), s));
-    const double nan = std::nan("");
-    // step 0 directly (it also settles every lazily set launch attribute),
-    // then one step captured as a graph and replayed: no host round trip
-    // between steps
-    enqueue_adapt_step(c, b, h, p, psi, eps, nan, dth, s);
-    launch(c, "step_record", s, [&] { return launch_step_record(c->step, rec, n_iter, s); });
-    if (n_iter > 1) {
-        if (c->tracing) {
-            for (int i = 1; i < n_iter; ++i) {
-                enqueue_adapt_step(c, b, h, p, psi, eps, nan, dth, s);
-                launch(c, "step_record", s, [&] { return launch_step_record(c->step, rec, n_iter, s); });
-            }
-        } else {
-            cudaGraph_t graph = nullptr;
-            cudaGraphExec_t exec = nullptr;
-            TQ_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            try {
-                enqueue_adapt_step(c, b, h, p, psi, eps, nan, dth, s);
-                launch(c, "step_record", s, [&] { return launch_step_record(c->step, rec, n_iter, s); });
-            } catch (...) {
-                cudaStreamEndCapture(s, &graph);
-                if (graph) cudaGraphDestroy(graph);
-                throw;
-            }
-            TQ_CUDA(cudaStreamEndCapture(s, &graph));
-            const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
-            cudaGraphDestroy(graph);
-            TQ_CUDA(ie);
-            cudaError_t le = cudaSuccess;
-            for (int i = 1; i < n_iter && le == cudaSuccess; ++i) le = cudaGraphLaunch(exec, s);
-            cudaGraphExecDestroy(exec);
-            TQ_CUDA(le);
-        }
-    }
-    std::vector<double> hr((size_t)n_iter * 6);
-    int status = 0;
-    TQ_CUDA(cudaMemcpyAsync(hr.data(), rec, hr.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-    TQ_CUDA(cudaMemcpyAsync(&status, &c->step->status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    TQ_CUDA(cudaStreamSynchronize(s));
-    raise_status(c, status, s);
-    int done = n_iter;
-    for (int i = 0; i < n_iter; ++i) {
-        const double* r = &hr[6 * (size_t)i];
-        results[i].energy = r[0];
-        results[i].max_grad = r[1];
-        results[i].theta = r[2];
-        results[i].selected = (int)r[3];
-        results[i].converged = (int)r[4];
-        if (r[5] != 0.0) {
-            *n_done = i + 1;
-            throw Error(TQ_ENUMERIC, "non-finite or zero norm after the update of step " + std::to_string(i));
-        }
-        if (results[i].converged && done == n_iter) done = i + 1;
-    }
-    *n_done = done;
-    API_END
-}
-
-// ===================================================== ADAPT-VQE (re-optimised)
-
-namespace {
-
-// E(theta) and dE/dtheta of psi(theta) = U_n ... U_1 psi0 (Taylor-5 factors,
-// no renormalisation): forward states phi_0 .. phi_n kept in scratch, the
-// energy pass over phi_n (w = H psi), chi = w - E psi, then per factor from
-// the last: the gradient dot, and chi <- U_j(-theta_j) chi.  `grad` (host)
-// may be null; `psi_out` (device, D amplitudes) receives phi_n if not null.
-double ansatz_energy_grad(tq_ctx* c, const tq_ham* h, const tq_pool* p, const tq_state* psi0, int n, const int* ops,
-                          const double* th, double* grad, void* psi_out, cudaStream_t s) {
-    check_space(p, psi0);
-    check_space(h, psi0);
-    TQ_REQUIRE(h->prec == psi0->prec, "state and Hamiltonian precisions differ");
-    TQ_REQUIRE(n >= 0, "n_ops < 0");
-    for (int j = 0; j < n; ++j) {
-        TQ_REQUIRE(ops[j] >= 0 && ops[j] < p->M, "pool index out of range");
-        TQ_REQUIRE(std::isfinite(th[j]), "theta is not finite");
-    }
-    const int prec = psi0->prec;
-    const long long D = psi0->D;
-    const size_t vb = (size_t)D * elem_bytes(prec);
-    double* part = prepare(c, D, p, p->nq);
-    unsigned char* phis = static_cast<unsigned char*>(scratch(c, S_PHI, (size_t)(n + 1) * vb));
-    void* chi = scratch(c, S_CHI, vb);
-    double* gdev = static_cast<double*>(scratch(c, S_AG, (size_t)std::max(n, 1) * sizeof(double)));
-    const int upt = c->pair_upt[prec];
-    TQ_CUDA(cudaMemcpyAsync(phis, psi0->data, vb, cudaMemcpyDeviceToDevice, s));
-    for (int j = 0; j < n; ++j) {
-        unsigned char* dst = phis + (size_t)(j + 1) * vb;
-        TQ_CUDA(cudaMemcpyAsync(dst, phis + (size_t)j * vb, vb, cudaMemcpyDeviceToDevice, s));
-        launch_update(c, p, 1, prec, upt, dst, nullptr, nullptr, ops[j], th[j], nullptr, part, nullptr, nullptr, s);
-    }
-    tq_state last = *psi0;
-    last.owned = 0;
-    last.data = phis + (size_t)n * vb;
-    run_energy(c, h, &last, part, s);
-    if (grad) {
-        launch(c, "residual", s, [&] { return launch_residual(static_cast<double2*>(c->scratch[S_W0]), last.data, chi, prec,
-                                                              D, c->step, s); });
-        for (int j = n - 1; j >= 0; --j) {
-            const double t = th[j], t2 = t * t;
-            const double c4 = 1.0 - t2 / 2.0 + t2 * t2 / 24.0, s4 = t * (1.0 - t2 / 6.0);
-            launch(c, "ansatz_dot", s, [&] {
-                return launch_ansatz_dot(p->view, ops[j], c4, s4, chi, phis + (size_t)j * vb, prec, D, part,
-                                         c->tickets + 4, c->step, gdev + j, c->sm_count, s);
-            });
-            launch_update(c, p, 1, prec, upt, chi, nullptr, nullptr, ops[j], -t, nullptr, part, nullptr, nullptr, s);
-        }
-    }
-    double E = 0.0;
-    int status = 0;
-    TQ_CUDA(cudaMemcpyAsync(&E, &c->step->energy, sizeof(double), cudaMemcpyDeviceToHost, s));
-    TQ_CUDA(cudaMemcpyAsync(&status, &c->step->status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    if (grad && n > 0) TQ_CUDA(cudaMemcpyAsync(grad, gdev, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s));
-    if (psi_out) TQ_CUDA(cudaMemcpyAsync(psi_out, last.data, vb, cudaMemcpyDeviceToDevice, s));
-    TQ_CUDA(cudaStreamSynchronize(s));
-    raise_status(c, status, s);
-    return E;
-}
-
-// BFGS on f with gradient g: inverse-Hessian update, backtracking line
-// search (Armijo, halving), restart along -g when the direction does not
-// descend; stops when max |g_i| < gtol or after max_iter iterations.
-// Returns f at the result; x is updated in place.
-template <typename FG>
-double bfgs(FG fg, std::vector<double>& x, double gtol, int max_iter, int* n_eval) {
-    const size_t n = x.size();
-    std::vector<double> g(n), gn(n), xn(n), d(n), sv(n), yv(n), Hy(n);
-    std::vector<double> H(n * n, 0.0);
-    for (size_t i = 0; i < n; ++i) H[i * n + i] = 1.0;
-    double f = fg(x, g);
-    int evals = 1;
-    auto gmax = [](const std::vector<double>& v) {
-        double m = 0.0;
-        for (double e : v) m = std::max(m, std::fabs(e));
-        return m;
-    };
-    for (int it = 0; it < max_iter && gmax(g) >= gtol; ++it) {
-        double gd = 0.0;
-        for (size_t i = 0; i < n; ++i) {
-            double v = 0.0;
-            for (size_t j = 0; j < n; ++j) v -= H[i * n + j] * g[j];
-            d[i] = v;
-            gd += v * g[i];
-        }
-        if (!(gd < 0.0)) {                         // not a descent direction: restart
-            std::fill(H.begin(), H.end(), 0.0);
-            for (size_t i = 0; i < n; ++i) H[i * n + i] = 1.0, d[i] = -g[i];
-            gd = 0.0;
-            for (size_t i = 0; i < n; ++i) gd -= g[i] * g[i];
-        }
-        double a = 1.0, fn = f;
-        bool ok = false;
-        for (int ls = 0; ls < 40; ++ls) {
-            for (size_t i = 0; i < n; ++i) xn[i] = x[i] + a * d[i];
-            fn = fg(xn, gn);
-            ++evals;
-            if (fn <= f + 1e-4 * a * gd) {
-                ok = true;
-                break;
-            }
-            a *= 0.5;
-        }
-        if (!ok) break;                            // no decrease along d: converged to rounding
-        double sy = 0.0, yy = 0.0;
-        for (size_t i = 0; i < n; ++i) {
-            sv[i] = xn[i] - x[i];
-            yv[i] = gn[i] - g[i];
-            sy += sv[i] * yv[i];
-            yy += yv[i] * yv[i];
-        }
-        if (sy > 1e-300) {
-            if (it == 0) {                         // scale the first inverse Hessian
-                std::fill(H.begin(), H.end(), 0.0);
-                for (size_t i = 0; i < n; ++i) H[i * n + i] = sy / yy;
-            }
-            double yHy = 0.0;
-            for (size_t i = 0; i < n; ++i) {
-                double v = 0.0;
-                for (size_t j = 0; j < n; ++j) v += H[i * n + j] * yv[j];
-                Hy[i] = v;
-                yHy += yv[i] * v;
-            }
-            const double rho = 1.0 / sy;
-            for (size_t i = 0; i < n; ++i)
-                for (size_t j = 0; j < n; ++j)
-                    H[i * n + j] += -rho * (Hy[i] * sv[j] + sv[i] * Hy[j]) + (rho * rho * yHy + rho) * sv[i] * sv[j];
-        }
-        x = xn;
-        g = gn;
-        f = fn;
-    }
-    if (n_eval) *n_eval = evals;
-    return f;
-}
-
-// The operator choice of the ADAPT step on host gradients (the tie rule of
-// k_select): the lowest index within tau of max |g|.
-int select_host(const std::vector<double>& g, int prec, double* gmax_out) {
-    double gm = 0.0;
-    for (double v : g) gm = std::max(gm, std::fabs(v));
-    const double tau = prec == TQ_C128 ? 1e-9 * std::max(1.0, gm) : 1e-5;
-    int k = 0;
-    for (size_t i = 0; i < g.size(); ++i)
-        if (std::fabs(g[i]) >= gm - tau) {
-            k = (int)i;
-            break;
-        }
-    *gmax_out = gm;
-    return k;
-}
-
-}  // namespace
-
-extern "C" int tq_ansatz_energy_grad(tq_ctx* c, const tq_ham* h, const tq_pool* p, const tq_state* psi0, int n_ops,
-                                     const int* ops, const double* thetas, double* E, double* grad, tq_state* psi_out,
-                                     void* stream) {
-    API_BEGIN
-    TQ_REQUIRE(c && h && p && psi0 && E, "null argument");
-    TQ_REQUIRE(n_ops == 0 || (ops && thetas), "null argument");
-    if (psi_out) {
-        check_space(p, psi_out);
-        TQ_REQUIRE(psi_out->prec == psi0->prec, "output state precision differs");
-    }
-    set_device(c);
-    *E = ansatz_energy_grad(c, h, p, psi0, n_ops, ops, thetas, grad, psi_out ? psi_out->data : nullptr,
-                            as_stream(stream));
-    API_END
-}
-
-extern "C" int tq_adapt_vqe(tq_ctx* c, const tq_ham* h, const tq_pool* p, const tq_state* psi0, double eps,
-                            int max_ops, double gtol, int max_iter, int* n_ops, int* ops_out, double* thetas_out,
-                            double* energies_out, tq_state* psi_out) {
-    API_BEGIN
-    TQ_REQUIRE(c && h && p && psi0 && n_ops && ops_out && thetas_out && energies_out, "null argument");
-    TQ_REQUIRE(max_ops >= 0 && max_iter >= 0, "max_ops and max_iter must be >= 0");
-    TQ_REQUIRE(std::isfinite(eps) && eps >= 0.0 && std::isfinite(gtol) && gtol > 0.0, "eps >= 0 and gtol > 0 required");
-    check_space(p, psi0);
-    check_space(h, psi0);
-    set_device(c);
-    cudaStream_t s = 0;
-    const long long D = psi0->D;
-    std::vector<int> ops;
-    std::vector<double> th;
-    std::vector<double> g(p->M);
-    int count = 0;
-    for (int it = 0; it < max_ops; ++it) {
-        // psi(theta) and every pool gradient there
-        void* work = scratch(c, S_STAGE, (size_t)D * elem_bytes(psi0->prec));
-        ansatz_energy_grad(c, h, p, psi0, (int)ops.size(), ops.data(), th.data(), nullptr, work, s);
-        tq_state cur = *psi0;
-        cur.owned = 0;
-        cur.data = work;
-        double* gd = static_cast<double*>(scratch(c, S_G, (size_t)p->M * sizeof(double)));
-        double* part = prepare(c, D, p, p->nq);
-        run_gradients(c, h, p, &cur, gd, part, s);
-        TQ_CUDA(cudaMemcpyAsync(g.data(), gd, (size_t)p->M * sizeof(double), cudaMemcpyDeviceToHost, s));
-        TQ_CUDA(cudaStreamSynchronize(s));
-        double gmax = 0.0;
-        const int k = select_host(g, psi0->prec, &gmax);
-        if (gmax < eps) break;
-        ops.push_back(k);
-        th.push_back(0.0);
-        const double E = bfgs(
-            [&](const std::vector<double>& x, std::vector<double>& gr) {
-                return ansatz_energy_grad(c, h, p, psi0, (int)ops.size(), ops.data(), x.data(), gr.data(), nullptr, s);
-            },
-            th, gtol, max_iter, nullptr);
-        ops_out[count] = k;
-        energies_out[count] = E;
-        ++count;
-    }
-    for (int j = 0; j < count; ++j) thetas_out[j] = th[j];
-    *n_ops = count;
-    if (psi_out) {
-        check_space(p, psi_out);
-        ansatz_energy_grad(c, h, p, psi0, count, ops.data(), th.data(), nullptr, psi_out->data, s);
-    }
-    API_END
-}
-
-// ================================================================ batched
-
-extern "C" int tq_evolve_taylor5_batch(tq_ctx* c, const tq_pool* p, int n_states, int prec, void* psi,
-                                       const int* k, const double* theta, double* norm2, void* stream) {
-    API_BEGIN
-    TQ_REQUIRE(c && p, "null argument");
-    TQ_REQUIRE(n_states >= 0, "n_states < 0");
-    check_prec(prec);
-    if (n_states == 0) return TQ_OK;   // an empty batch is a no-op
-    TQ_REQUIRE(psi && k && theta, "null argument");
-    TQ_REQUIRE(((uintptr_t)psi & 15u) == 0, "psi must be 16-byte aligned");
-    set_device(c);
-    cudaStream_t s = as_stream(stream);
-    const int upt = c->pair_upt[prec];
-    const int tiles = update_tiles(p, prec, upt);
-    double* part = static_cast<double*>(scratch(c, S_PART, (size_t)n_states * tiles * sizeof(double)));
-    const bool fin = launch_update(c, p, n_states, prec, upt, psi, k, theta, 0, 0.0, nullptr, part, norm2, nullptr, s);
-    if (norm2 && !fin)
-        launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, prec, n_states, tiles, norm2, nullptr, s); });
-    API_END
-}
-
-extern "C" int tq_evolve_taylor5_batch_support(tq_ctx* c, const tq_pool* p, int n_states, int prec, void* psi,
-                                               const int* k, const double* theta, double* norm2, void* stream) {
-    API_BEGIN
-    TQ_REQUIRE(c && p, "null argument");
-    TQ_REQUIRE(!p->sector, "the support-only update takes full-space pools (sector states: tq_evolve_taylor5_batch)");
-    TQ_REQUIRE(n_states >= 0, "n_states < 0");
-    check_prec(prec);
-    if (n_states == 0) return TQ_OK;   // an empty batch is a no-op
-    TQ_REQUIRE(psi && k && theta, "null argument");
-    TQ_REQUIRE(((uintptr_t)psi & 15u) == 0, "psi must be 16-byte aligned");
-    set_device(c);
-    cudaStream_t s = as_stream(stream);
-    const int ppt = c->supp_ppt[prec];
-    const int tps = support_tiles(p->nq, n_states, ppt, c->sm_count);
-    const int parts = support_parts(tps);
-    double* part = static_cast<double*>(scratch(c, S_PART, (size_t)n_states * parts * sizeof(double)));
-    launch(c, "taylor5_support", s, [&] {
-        return launch_taylor5_support(p->view, n_states, prec, ppt, psi, k, theta, part, tps, norm2, c->sm_count, s);
-    });
-    if (norm2 && tps > 1)
-        launch(c, "norm_carry", s, [&] { return launch_norm_carry(part, prec, n_states, parts, norm2, norm2, nullptr, s); });
-    API_END
-}
-
-extern "C" int tq_evolve_taylor5_batch_support_host(tq_ctx* c, const tq_pool* p, int n_states, int prec,
-                                                    void* psi_host, const int* k_host, const double* theta_host,
-                                                    double* norm2_host) {
-    API_BEGIN
-    TQ_REQUIRE(c && p, "null argument");
-    TQ_REQUIRE(!p->sector, "the support-only update takes full-space pools (sector states: tq_evolve_taylor5_batch)");
-    TQ_REQUIRE(n_states >= 0, "n_states < 0");
-    check_prec(prec);
-    if (n_states == 0) return TQ_OK;   // an empty batch is a no-op
-    TQ_REQUIRE(psi_host && k_host && theta_host, "null argument");
-    TQ_REQUIRE(((uintptr_t)psi_host & 15u) == 0, "psi must be 16-byte aligned");
-    set_device(c);
-    // the kernel reads and writes the states where they are, over the
-    // host link: they must be page-locked and mapped for this device
-    cudaPointerAttributes attr{};
-    const cudaError_t ae = cudaPointerGetAttributes(&attr, psi_host);
-    if (ae != cudaSuccess) (void)cudaGetLastError();
-    TQ_REQUIRE(ae == cudaSuccess && attr.type == cudaMemoryTypeHost && attr.devicePointer != nullptr,
-               "psi_host must be page-locked host memory mapped for the device (cudaHostAlloc / cudaHostRegister)");
-    void* psi = attr.devicePointer;
-    cudaStream_t s = c->aux[0];
-    if (!s) TQ_CUDA(cudaStreamCreateWithFlags(&c->aux[0], cudaStreamNonBlocking));
-    s = c->aux[0];
-    const int ppt = c->supp_ppt[prec];
-    const int tps = support_tiles(p->nq, n_states, ppt, c->sm_count);
-    const int parts = support_parts(tps);
-    unsigned char* buf = static_cast<unsigned char*>(
-        scratch(c, S_HOSTB, (size_t)n_states * (sizeof(int) + 2 * sizeof(double)) + 64));
-    int* dk = reinterpret_cast<int*>(buf);
-    double* dth = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(dk + n_states) + 15) & ~(uintptr_t)15);
-    double* dn = dth + n_states;
-    double* part = static_cast<double*>(scratch(c, S_PART, (size_t)n_states * parts * sizeof(double)));
-    TQ_CUDA(cudaMemcpyAsync(dk, k_host, (size_t)n_states * sizeof(int), cudaMemcpyHostToDevice, s));
-    TQ_CUDA(cudaMemcpyAsync(dth, theta_host, (size_t)n_states * sizeof(double), cudaMemcpyHostToDevice, s));
-    if (norm2_host)
-        TQ_CUDA(cudaMemcpyAsync(dn, norm2_host, (size_t)n_states * sizeof(double), cudaMemcpyHostToDevice, s));
-    double* n2 = norm2_host ? dn : nullptr;
-    launch(c, "taylor5_support_host", s, [&] {
-        return launch_taylor5_support(p->view, n_states, prec, ppt, psi, dk, dth, part, tps, n2, c->sm_count, s);
-    });
-    if (n2 && tps > 1)
-        launch(c, "norm_carry", s, [&] { return launch_norm_carry(part, prec, n_states, parts, n2, n2, nullptr, s); });
-    if (norm2_host)
-        TQ_CUDA(cudaMemcpyAsync(norm2_host, dn, (size_t)n_states * sizeof(double), cudaMemcpyDeviceToHost, s));
-    TQ_CUDA(cudaStreamSynchronize(s));
-    API_END
-}
-
-extern "C" int tq_ctx_set_support_schedule(tq_ctx* c, int prec, int pairs_per_thread) {
-    API_BEGIN
-    TQ_REQUIRE(c, "null argument");
-    check_prec(prec);
-    TQ_REQUIRE(pair_upt_valid(std::abs(pairs_per_thread)), "pairs_per_thread must be +-1, +-2, +-4 or +-8");
-    c->supp_ppt[prec] = pairs_per_thread;
-    API_END
-}
-
-extern "C" int tq_evolve_taylor5_batch_host(tq_ctx* c, const tq_pool* p, int n_states, int prec,
-                                            void* psi_host, const int* k_host, const double* theta_host,
-                                            double* norm2_host) {
-    API_BEGIN
-    TQ_REQUIRE(c && p, "null argument");
-    TQ_REQUIRE(n_states >= 0, "n_states < 0");
-    check_prec(prec);
-    if (n_states == 0) return TQ_OK;   // an empty batch is a no-op
-    TQ_REQUIRE(psi_host && k_host && theta_host, "null argument");
-    set_device(c);
-    for (auto& st : c->aux)
-        if (!st) TQ_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-    const long long D = state_len(p);
-    const size_t sb = (size_t)D * elem_bytes(prec);
-    // chunk of about 64 MiB of states per stream
-    int chunk = (int)std::max<long long>(1, (64ll << 20) / (long long)sb);
-    chunk = std::min(chunk, n_states);
-    const int upt = c->pair_upt[prec];
-    const int tiles = update_tiles(p, prec, upt);
-    const size_t per_stream = (size_t)chunk * sb + (size_t)chunk * (sizeof(int) + 2 * sizeof(double)) +
-                              (size_t)chunk * tiles * sizeof(double) + 256;
-    unsigned char* stage = static_cast<unsigned char*>(scratch(c, S_STAGE, 3 * per_stream));
-    for (int c0 = 0, it = 0; c0 < n_states; c0 += chunk, ++it) {
-        const int n = std::min(chunk, n_states - c0);
-        cudaStream_t s = c->aux[it % 3];
-        unsigned char* base = stage + (size_t)(it % 3) * per_stream;
-        void* dpsi = base;
-        int* dk = reinterpret_cast<int*>(base + (size_t)chunk * sb);
-        double* dth = reinterpret_cast<double*>(
-            (reinterpret_cast<uintptr_t>(dk + chunk) + 15) & ~(uintptr_t)15);
-        double* dn = dth + chunk;
-        double* part = dn + chunk;
-        TQ_CUDA(cudaMemcpyAsync(dpsi, static_cast<unsigned char*>(psi_host) + (size_t)c0 * sb, (size_t)n * sb,
-                                cudaMemcpyHostToDevice, s));
-        TQ_CUDA(cudaMemcpyAsync(dk, k_host + c0, (size_t)n * sizeof(int), cudaMemcpyHostToDevice, s));
-        TQ_CUDA(cudaMemcpyAsync(dth, theta_host + c0, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, s));
-        const bool fin = launch_update(c, p, n, prec, upt, dpsi, dk, dth, 0, 0.0, nullptr, part,
-                                       norm2_host ? dn : nullptr, nullptr, s);
-        TQ_CUDA(cudaMemcpyAsync(static_cast<unsigned char*>(psi_host) + (size_t)c0 * sb, dpsi, (size_t)n * sb,
-                                cudaMemcpyDeviceToHost, s));
-        if (norm2_host) {
-            if (!fin) launch(c, "norm_reduce", s, [&] { return launch_norm_reduce(part, prec, n, tiles, dn, nullptr, s); });
-            TQ_CUDA(cudaMemcpyAsync(norm2_host + c0, dn, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s));
-        }
-    }
-    for (auto& st : c->aux) TQ_CUDA(cudaStreamSynchronize(st));
-    API_END
 }
