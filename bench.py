@@ -285,6 +285,18 @@ def measure_adapt_step(tq, ctx, steps=10):
         t0 = time.perf_counter()
         res, _ = tq.adapt_run(ctx, ham, pool, st, 0.0, steps)
         tr = (time.perf_counter() - t0) / steps
+        # the same iterations with the H passes over the CSR (8 lanes per row)
+        ctx.set_spmv_schedule(8)
+        tq.state_set_hf(st, ne, MAPPING)
+        ctx.trace(True)
+        t0 = time.perf_counter()
+        csr_e = [tq.adapt_step(ctx, ham, pool, st, 0.0, float("nan"))["energy"] for _ in range(steps)]
+        tc = (time.perf_counter() - t0) / steps
+        rep_c = ctx.trace_report()
+        ctx.trace(False)
+        ctx.set_spmv_schedule(tq.TQ_SPMV_XELL)
+        out[f"{nq_}q_csr"] = {"ms_per_step": 1e3 * tc, "kernel_ms_per_step": {k_: v[1] / steps for k_, v in rep_c.items()},
+                              "same_trajectory": [abs(a_ - b_) < 1e-6 for a_, b_ in zip(csr_e, energies)].count(True)}
         out[f"{nq_}q"] = {"ms_per_step": 1e3 * t, "ms_per_step_graph_run": 1e3 * tr, "nnz": ham.nnz, "pool": pool.M,
                           "kernel_ms_per_step": {k_: v[1] / steps for k_, v in rep.items()},
                           "energy_first_last": [energies[0], energies[-1]],
