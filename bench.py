@@ -102,6 +102,45 @@ def profiled_traffic(profile, n_states):
     return float(m.group(1)) * n_states
 
 
+def measure_link(src_h, src_d, nbytes=512 << 20, reps=3):
+    """Copy rates of the host link: pinned host -> device, device -> pinned
+    host, and both at once on two streams (the ceiling for a step whose
+    reads and writes cross the link together).  Reads src_h and src_d only."""
+    import torch
+    hs = src_h.view(torch.uint8).reshape(-1)[:nbytes]
+    ds = src_d.view(torch.uint8).reshape(-1)[:nbytes]
+    nbytes = min(hs.numel(), ds.numel())
+    hs, ds = hs[:nbytes], ds[:nbytes]
+    hb = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    db = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    cur = torch.cuda.current_stream()
+
+    def run(h2d, d2h):
+        best = float("inf")
+        for i in range(reps + 1):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(cur)
+            for s, on in ((s1, h2d), (s2, d2h)):
+                s.wait_stream(cur)
+                if on:
+                    with torch.cuda.stream(s):
+                        (db.copy_(hs, non_blocking=True) if s is s1 else hb.copy_(ds, non_blocking=True))
+            cur.wait_stream(s1)
+            cur.wait_stream(s2)
+            e1.record(cur)
+            torch.cuda.synchronize()
+            if i:
+                best = min(best, e0.elapsed_time(e1) / 1e3)
+        return best
+
+    t_in, t_out, t_both = run(True, False), run(False, True), run(True, True)
+    return {"bytes": nbytes, "h2d_gbs": nbytes / t_in / 1e9, "d2h_gbs": nbytes / t_out / 1e9,
+            "bidir_gbs": 2 * nbytes / t_both / 1e9, "note": "cudaMemcpyAsync from and to pinned host memory"}
+
+
 class ClockSampler:
     """nvidia-smi samples every 200 ms while the timed region runs."""
 
@@ -493,6 +532,15 @@ def run_ours(args, rank, world, local_rank):
     e2e["full_copy_path"] = {"value": world * S * 3 / t_full, "api": "tq_evolve_taylor5_batch_host "
                              "(whole states copied in and out on 3 streams, full-state kernel)",
                              "h2d_bytes_per_step": S * D * 8 + S * 12, "d2h_bytes_per_step": S * D * 8 + S * 8}
+    # the host link's own copy rates: the roofline of both host paths
+    link = measure_link(psi_h, psi)
+    e2e_bytes = e2e["h2d_bytes_per_step"] + e2e["d2h_bytes_per_step"]
+    full_bytes = e2e["full_copy_path"]["h2d_bytes_per_step"] + e2e["full_copy_path"]["d2h_bytes_per_step"]
+    link["frac"] = e2e_bytes / (t_e2e / e2e_steps) / 1e9 / link["bidir_gbs"]
+    link["full_copy_frac"] = full_bytes / (t_full / 3) / 1e9 / link["bidir_gbs"]
+    link["frac_note"] = ("the step's bytes over the link at the two-way copy rate, over the measured step "
+                         "time; the support path moves sectors by kernel loads and stores, not by copies")
+    e2e["link"] = link
     finite = bool(torch.isfinite(dn).all().item()) and float(dn.min().item()) > 0.5
     extra = {}
     if rank == 0 and not args.headline_only:
