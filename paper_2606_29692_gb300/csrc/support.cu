@@ -96,16 +96,27 @@ __device__ __forceinline__ double norm_growth(double theta) {
     return t6 * fma(t2, fma(t2, 1.0 / 14400.0, -1.0 / 960.0), 1.0 / 360.0);
 }
 
-// Updates the support pairs [i0, i1) of one state; returns the thread's
-// sum of |psi'|^2 - |psi|^2.
+// The float64 coefficients of one tile: theta^k / k! (k = 0..5), the
+// closed-form c5 and s5, and the norm growth, in that order.
+constexpr int N_COEF = 9;
+__device__ __forceinline__ void tile_coefs(double theta, double* sc) {
+    double cf[6], c5, s5;
+    taylor_coefs_fast<double>(theta, cf);
+    closed_coefs(cf, c5, s5);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) sc[k] = cf[k];
+    sc[6] = c5;
+    sc[7] = s5;
+    sc[8] = norm_growth(theta);
+}
+
+// Updates the support pairs [i0, i1) of one state with the tile's
+// coefficients (c5, s5 and growth are used by complex128 only); returns the
+// thread's sum of |psi'|^2 - |psi|^2.
 template <typename T, int PPT>
-__device__ __forceinline__ T support_tile(const SupOp<T>& op, double theta, typename C2<T>::type* __restrict__ base,
-                                          uint32_t i0, uint32_t i1) {
+__device__ __forceinline__ T support_tile(const SupOp<T>& op, const T (&cf)[6], double c5, double s5, double growth,
+                                          typename C2<T>::type* __restrict__ base, uint32_t i0, uint32_t i1) {
     using V = typename C2<T>::type;
-    T cf[6];
-    taylor_coefs_fast<T>(theta, cf);
-    double c5 = 0.0, s5 = 0.0;
-    if constexpr (sizeof(T) == 8) closed_coefs(cf, c5, s5);
     T delta = T(0);
     double nsq = 0.0;   // complex128 closed-form pairs: sum of |psi|^2 before the update
     for (uint32_t i = i0 + threadIdx.x; i < i1; i += SUPP_BS * PPT) {
@@ -138,7 +149,7 @@ __device__ __forceinline__ T support_tile(const SupOp<T>& op, double theta, type
             base[q] = aq;
         }
     }
-    if constexpr (sizeof(T) == 8) delta += norm_growth(theta) * nsq;
+    if constexpr (sizeof(T) == 8) delta += growth * nsq;
     return delta;
 }
 
@@ -163,7 +174,11 @@ __device__ __forceinline__ double sum_partials(const double* red) {
 // (tps, the tiles per state, a power of two).
 // With one tile per state and `norm2` set, the CTA finishes the state's
 // norm itself (norm2[b] += the fixed-order sum of its warps' partials);
-// otherwise every warp leaves its partial for the reduction kernel.
+// otherwise every warp leaves its partial for the reduction kernel.  In
+// complex128 with one tile per state, thread 0 also works out the next
+// tile's coefficients between the norm's two barriers, once per CTA: the
+// float64 pipe is this kernel's limit, and every warp would otherwise
+// repeat them.
 template <typename T, int PPT>
 __global__ void __launch_bounds__(SUPP_BS)
 k_taylor5_support(PoolView p, int n_states, typename C2<T>::type* psi, const int* kk, const double* th,
@@ -171,7 +186,9 @@ k_taylor5_support(PoolView p, int n_states, typename C2<T>::type* psi, const int
     const int warp = threadIdx.x >> 5;
     constexpr int NW = SUPP_BS / 32;
     __shared__ double red[NW];
+    __shared__ double sc[N_COEF];
     const bool fold = tiles_per_state == 1 && norm2 != nullptr;
+    constexpr bool wide = sizeof(T) == 8;
     const long long D = 1ll << p.nq;
     const unsigned tps = (unsigned)tiles_per_state;
     const int lt = __ffs(tiles_per_state) - 1;        // tps is a power of two
@@ -180,6 +197,10 @@ k_taylor5_support(PoolView p, int n_states, typename C2<T>::type* psi, const int
     int b = (int)(tile >> lt);
     int k = tile < total ? kk[b] : 0;
     double theta = tile < total ? th[b] : 0.0;
+    if (wide && fold) {
+        if (threadIdx.x == 0 && tile < total) tile_coefs(theta, sc);
+        __syncthreads();
+    }
     while (tile < total) {
         const unsigned tl = tile & (tps - 1);
         const unsigned ntile = tile + gridDim.x;
@@ -197,12 +218,34 @@ k_taylor5_support(PoolView p, int n_states, typename C2<T>::type* psi, const int
             const SupOp<T> op = load_supop<T>(p, k);
             const int lp = p.nq - op.s.m - 1;
             const uint32_t i0 = pair_bound(lp, tl, lt), i1 = pair_bound(lp, tl + 1, lt);
-            const T d = support_tile<T, PPT>(op, theta, psi + (long long)b * D, i0, i1);
+            T cf[6];
+            double c5 = 0.0, s5 = 0.0, growth = 0.0;
+            if (wide && fold) {
+#pragma unroll
+                for (int j = 0; j < 6; ++j) cf[j] = (T)sc[j];
+                c5 = sc[6];
+                s5 = sc[7];
+                growth = sc[8];
+            } else if constexpr (wide) {
+                double w[N_COEF];
+                tile_coefs(theta, w);
+#pragma unroll
+                for (int j = 0; j < 6; ++j) cf[j] = (T)w[j];
+                c5 = w[6];
+                s5 = w[7];
+                growth = w[8];
+            } else {
+                taylor_coefs_fast<T>(theta, cf);
+            }
+            const T d = support_tile<T, PPT>(op, cf, c5, s5, growth, psi + (long long)b * D, i0, i1);
             store_partial(slot, d);
         }
         if (fold) {
-            __syncthreads();
-            if (threadIdx.x == 0) norm2[b] = norm2[b] + sum_partials<T, NW>(red);
+            __syncthreads();   // the partials are in red, and every thread has read sc
+            if (threadIdx.x == 0) {
+                norm2[b] = norm2[b] + sum_partials<T, NW>(red);
+                if (wide && ntile < total) tile_coefs(nth, sc);
+            }
             __syncthreads();
         }
         tile = ntile;
