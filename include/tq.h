@@ -552,7 +552,7 @@ int tq_evolve_taylor5_batch_support_host(tq_ctx* ctx, const tq_pool* pool,
 /* Schedule of the support-only update: support pairs per thread per pass,
  * 1, 2, 4 or 8 with the amplitudes held in registers, or -1, -2, -4, -8
  * with them staged in shared memory by asynchronous copies that run one
- * pass ahead (across states).  Defaults: 2 for TQ_C128, -1 for TQ_C64. */
+ * pass ahead (across states).  Defaults: 4 for TQ_C128, -1 for TQ_C64. */
 int tq_ctx_set_support_schedule(tq_ctx* ctx, int prec, int pairs_per_thread);
 /* Autotuner of that schedule, as tq_autotune_pair: times each on n_states
  * device scratch states (the update and its norm), keeps the fastest on

@@ -303,7 +303,7 @@ struct tq_ctx {
     long long launches = 0;
     int tracing = 0;
     int pair_upt[2] = {2, 4};              // schedule per precision (C128, C64)
-    int supp_ppt[2] = {2, -1};             // support-only update: pairs per thread per pass, < 0 pipelined (C128, C64)
+    int supp_ppt[2] = {4, -1};             // support-only update: pairs per thread per pass, < 0 pipelined (C128, C64)
     int l2_fetch_default = 0;              // the CUDA context's L2 fetch granularity at creation (bytes)
     int spmv_lanes = 0;                    // energy SpMV: CSR lanes per row, or 0 for XOR-ELL (default)
     int test_flags = 0;                    // TQ_TEST_* (tests of the failure paths only)

@@ -98,7 +98,7 @@ def test_support_update_equals_full_state_kernel(ctx, n, ne, mp, prec):
         tq.evolve_taylor5_batch_support(ctx, pool, d, dk, dth, dn, prec=prec)
         torch.cuda.synchronize()
         outs.append((d, dn))
-    ctx.set_support_schedule(prec, 2 if prec == tq.TQ_C128 else -1)
+    ctx.set_support_schedule(prec, 4 if prec == tq.TQ_C128 else -1)
     fv = torch.view_as_real(full)
     bv = torch.view_as_real(before)
     for d, dn in outs:
@@ -195,7 +195,7 @@ def test_autotuner_picks_a_valid_schedule(ctx):
     for prec in (tq.TQ_C64, tq.TQ_C128):
         best, ms = tq.autotune_support(ctx, pool, prec, n_states=64)
         assert best in (1, 2, 4, 8, -1, -2, -4, -8) and ms > 0
-    ctx.set_support_schedule(tq.TQ_C128, 2)
+    ctx.set_support_schedule(tq.TQ_C128, 4)
     ctx.set_support_schedule(tq.TQ_C64, -1)
 
 
