@@ -676,13 +676,29 @@ def measure_c128_batched(tq, ctx, pool, n_states=4096, reps=20):
     ppt = min(per, key=per.get)
     ctx.set_support_schedule(tq.TQ_C128, ppt)
     sup_ms = per[ppt]
+    # both kernels are bound by the float64 pipe: 12 float64 operations per
+    # pair (c5 psi + s5 A psi: 4 multiplies and 4 FMAs; |psi|^2: 4 FMAs),
+    # against the device's measured float64 FMA rate
+    fma_rate = tq.fp64_fma_rate(ctx)
+    rows = support_rows(tq, N_SPATIAL, N_ELECTRONS, MAPPING)
+    n_pairs = np.array([r.size // 2 for r in rows], dtype=np.float64)[k.cpu().numpy()]
+    ops_sup = 12.0 * float(n_pairs.sum())
+    ops_full = 12.0 * n_states * (D // 2)
+    fp64 = {"peak_lane_ops_per_s": fma_rate, "peak_tflops": 2 * fma_rate / 1e12,
+            "peak_source": "tq_fp64_fma_rate (independent float64 FMA chains, this run)",
+            "ops_per_pair": 12,
+            "support": {"lane_ops_per_launch": ops_sup, "achieved_lane_ops_per_s": ops_sup / (sup_ms * 1e-3),
+                        "frac": ops_sup / (sup_ms * 1e-3) / fma_rate},
+            "full_state": {"lane_ops_per_launch": ops_full, "achieved_lane_ops_per_s": ops_full / (ms * 1e-3),
+                           "frac": ops_full / (ms * 1e-3) / fma_rate}}
     return {"workload": f"{n_states} complex128 states, 14 qubits, own generator and angle each",
             "kernel": "k_taylor5_pair<double>", "ms_per_launch": ms, "norm_reduce_ms": nrms / nr,
             "updates_per_s": n_states / ((ms + nrms / nr) * 1e-3),
             "achieved_gbs": alg * n_states / (ms * 1e-3) / 1e9, "hbm_frac": alg * n_states / (ms * 1e-3) / 1e9 / peak,
             "support": {"kernel": "k_taylor5_support<double>", "pairs_per_thread": ppt, "ms_per_update_launch": sup_ms,
                         "ms_by_schedule": {str(p_): v for p_, v in per.items()},
-                        "updates_per_s": n_states / (sup_ms * 1e-3)}}
+                        "updates_per_s": n_states / (sup_ms * 1e-3)},
+            "fp64_roofline": fp64}
 
 
 def _parity(v):

@@ -561,6 +561,17 @@ int tq_autotune_support(tq_ctx* ctx, const tq_pool* pool, int prec,
                         int n_states, int* best_pairs_per_thread,
                         double* best_ms);
 
+/* Measured float64 FMA rate of the context's device, in float64 lane
+ * operations per second (one fused multiply-add, two flops, on one lane
+ * each): the roofline of the complex128 updates, which the float64 pipe
+ * bounds on this part rather than HBM.  Launches a microbenchmark of
+ * independent FMA chains (iters steps of 8 chains per thread, 8 CTAs of
+ * 256 threads per SM; 1 <= iters <= 2^20, about 4096 for a 20 ms launch)
+ * on the legacy default stream and keeps the fastest of three timed
+ * launches.  Synchronises.  TQ_EINVAL for a null argument or iters out of
+ * range. */
+int tq_fp64_fma_rate(tq_ctx* ctx, int iters, double* lane_ops_per_s);
+
 /* The same batch with HOST buffers (psi, k, theta, norm2 in host memory;
  * pinned memory gives full copy speed): the batch is cut into chunks whose
  * host-to-device copy, update and device-to-host copy overlap on three

@@ -25,7 +25,7 @@ __all__ = [
     "pauli_hamiltonian", "pool_excitations", "pauli_pool", "hf_index", "build_hamiltonian",
     "build_pool", "evolve_taylor5", "evolve_taylor5_csr", "energy", "energy_matrix_free",
     "pool_gradients", "adapt_step", "evolve_taylor5_batch", "evolve_taylor5_batch_host",
-    "state_set_hf", "pool_csr", "ham_csr", "lib", "autotune_pair", "energy_noalloc", "Batch", "autotune_spmv", "Server",
+    "state_set_hf", "pool_csr", "ham_csr", "lib", "autotune_pair", "fp64_fma_rate", "energy_noalloc", "Batch", "autotune_spmv", "Server",
     "TQ_REQ_EVOLVE", "TQ_REQ_ENERGY", "TQ_REQ_GRADIENTS", "TQ_SPMV_XELL", "ham_xell",
     "sector_dim", "sector_basis", "build_hamiltonian_sector", "build_pool_sector", "pool_sector_table",
     "TQ_COMMUTE_FULL", "TQ_COMMUTE_QWC", "pool_families", "pool_families_host",
@@ -518,6 +518,14 @@ def autotune_support(ctx, pool, prec=TQ_C64, n_states=1024):
     u, ms = C.c_int(), C.c_double()
     call("tq_autotune_support", ctx.handle, pool.handle, prec, int(n_states), C.byref(u), C.byref(ms))
     return u.value, ms.value
+
+
+def fp64_fma_rate(ctx, iters=4096):
+    """Measured float64 FMA rate of the device, float64 lane operations per
+    second (one FMA per lane each; twice that in flops)."""
+    r = C.c_double()
+    call("tq_fp64_fma_rate", ctx.handle, int(iters), C.byref(r))
+    return r.value
 
 
 def autotune_pair(ctx, pool, prec=TQ_C64, n_states=1024):

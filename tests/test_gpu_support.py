@@ -235,3 +235,18 @@ def test_l2_fetch_granularity_round_trip(ctx):
     assert ctx.l2_fetch() == default
     with pytest.raises(tq.TQError):
         ctx.set_l2_fetch(48)
+
+
+def test_fp64_fma_rate(ctx):
+    """The float64 roofline of the complex128 updates: a positive, finite
+    rate within the range any float64 pipe of one GPU can have (10^9 to
+    10^14 FMA lane operations per second), repeatable within a factor of 2,
+    and arguments out of range rejected."""
+    r1 = tq.fp64_fma_rate(ctx, 1024)
+    r2 = tq.fp64_fma_rate(ctx, 4096)
+    for r in (r1, r2):
+        assert np.isfinite(r) and 1e9 < r < 1e14
+    assert 0.5 < r1 / r2 < 2.0
+    for bad in (0, -1, (1 << 20) + 1):
+        with pytest.raises(tq.TQError):
+            tq.fp64_fma_rate(ctx, bad)
