@@ -873,6 +873,27 @@ def measure_spmv(tq, ctx, nq):
         kernel = f"k_energy_csr<float,float,{best}>"
     peak, _ = peaks()
     gbs = alg / (ms * 1e-3) / 1e9
+    # the matrix-free energy (each row's terms evaluated from the X-mask
+    # groups, no matrix stored): one float64 add per term and row and two
+    # FMAs per off-diagonal group and row, against the measured FMA rate
+    tq.energy_matrix_free(ctx, ham, st)
+    ctx.trace(True)
+    for _ in range(3):
+        e_mf = tq.energy_matrix_free(ctx, ham, st)
+    rep = ctx.trace_report()
+    ctx.trace(False)
+    n_mf, t_mf = rep["energy_matrix_free"]
+    ms_mf = t_mf / n_mf
+    terms = float(D) * ham.n_pauli
+    g_off = ham.n_xgroups - 1                     # the groups less the diagonal (x = 0) one
+    fp64_ops = terms + 2.0 * D * g_off
+    fma_rate = tq.fp64_fma_rate(ctx)
+    mf = {"kernel": "k_energy_mf<float>", "ms_per_energy": ms_mf, "pauli_terms": ham.n_pauli,
+          "x_mask_groups": ham.n_xgroups, "term_evaluations": terms,
+          "term_evaluations_per_s": terms / (ms_mf * 1e-3), "fp64_lane_ops": fp64_ops,
+          "bound": "fp64 (an add per term and row, two FMAs per group and row)",
+          "fp64_peak_lane_ops_per_s": fma_rate, "fp64_frac": fp64_ops / (ms_mf * 1e-3) / fma_rate,
+          "energy_abs_diff_vs_stored_layout": abs(e_mf - e)}
     return {"workload": f"energy of a {nq}-qubit BK Hamiltonian (synthetic, {n} orbitals, "
                         f"{ne} electrons), complex64 state, float32 off-diagonal values + float64 diagonal",
             "kernel": kernel, "schedule": "xell" if best == tq.TQ_SPMV_XELL else f"csr_lanes_{best}",
@@ -880,7 +901,7 @@ def measure_spmv(tq, ctx, nq):
             "build_s": build_s, "ms_per_energy": ms, "ms_per_schedule": per_sched,
             "algorithmic_bytes": alg, "layout_bytes": layout, "achieved_gbs": gbs,
             "layout_gbs": layout / (ms * 1e-3) / 1e9, "peak_gbs": peak, "frac": gbs / peak,
-            "energy": e, "l2_policy": "Hamiltonian larger than L2"}
+            "energy": e, "l2_policy": "Hamiltonian larger than L2", "matrix_free": mf}
 
 
 def measure_sector(tq, ctx, n_states=65536, reps=20):

@@ -320,21 +320,27 @@ k_energy_xell_tma(HamView h, const typename C2<T>::type* __restrict__ psi, doubl
     }
 }
 
-// Same energy from the X-mask-grouped terms (no CSR): one warp per row,
-// lanes over groups and over diagonal terms.
+// Same energy from the X-mask-grouped terms (no CSR), one row per lane:
+// the warp walks the groups together, so every lane reads the same term
+// (a broadcast) and the 32 gathers psi[r ^ x] of its consecutive rows fall
+// in aligned runs.  Each lane sums its row's signed terms in float64, group
+// by group in term order, then the diagonal terms.  A lane past D (D < 32)
+// repeats the warp's first row and adds nothing, so every index stays
+// below D.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_energy_mf(HamView h, const typename C2<T>::type* __restrict__ psi, double* partials,
             unsigned* ticket, DevStep* step) {
     __shared__ double sh[2 * 8];
     const int lane = threadIdx.x & 31;
-    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long stride = (long long)gridDim.x * blockDim.x;
     double num = 0.0, den = 0.0;
-    for (long long r = warp; r < h.D; r += nwarps) {
-        const uint32_t ru = (uint32_t)r;
+    for (long long rb = (long long)blockIdx.x * blockDim.x + (threadIdx.x - lane); rb < h.D; rb += stride) {
+        const long long r = rb + lane;
+        const bool active = r < h.D;
+        const uint32_t ru = (uint32_t)(active ? r : rb);
         double sx = 0.0, sy = 0.0, dg = 0.0;
-        for (int g = lane; g < h.G; g += 32) {
+        for (int g = 0; g < h.G; ++g) {
             const uint32_t c = ru ^ h.gx[g];
             double a = 0.0;
             for (int t = h.goff[g]; t < h.goff[g + 1]; ++t)
@@ -343,12 +349,9 @@ k_energy_mf(HamView h, const typename C2<T>::type* __restrict__ psi, double* par
             sx = fma(a, v.x, sx);
             sy = fma(a, v.y, sy);
         }
-        for (int t = lane; t < h.Kd; t += 32) dg += parity32(ru & h.dz[t]) ? -h.dc[t] : h.dc[t];
-        sx = warp_sum(sx);
-        sy = warp_sum(sy);
-        dg = warp_sum(dg);
-        if (lane == 0) {
-            const double2 pr = to_d2<T>(psi[r]);
+        for (int t = 0; t < h.Kd; ++t) dg += parity32(ru & h.dz[t]) ? -h.dc[t] : h.dc[t];
+        if (active) {
+            const double2 pr = to_d2<T>(psi[ru]);
             const double wx = fma(dg, pr.x, sx), wy = fma(dg, pr.y, sy);
             num += pr.x * wx + pr.y * wy;
             den += pr.x * pr.x + pr.y * pr.y;
@@ -893,7 +896,8 @@ int launch_energy_csr2(const HamView& h, const void* psi, int psi_prec, double2*
 
 int launch_energy_matrix_free(const HamView& h, const void* psi, int psi_prec, double* partials,
                               unsigned* ticket, DevStep* step, int sms, cudaStream_t s) {
-    const int grid = energy_grid(h.D, sms);
+    const long long blocks = (h.D + 255) / 256;                 // one row per thread
+    const int grid = (int)(blocks < (long long)sms * 8 ? blocks : (long long)sms * 8);
     if (psi_prec == TQ_C128)
         k_energy_mf<double><<<grid, 256, 0, s>>>(h, static_cast<const double2*>(psi), partials, ticket, step);
     else
