@@ -577,6 +577,9 @@ def run_ours(args, rank, world, local_rank):
                          "sector_frac": sector_bytes / sup_s / 1e9 / peak,
                          "line_read_sector_write_bytes_per_launch": line_bytes,
                          "line_frac": line_bytes / sup_s / 1e9 / peak,
+                         # the ncu DRAM bytes of the committed capture over this run's launch time
+                         "traffic_gbs": traffic / sup_s / 1e9 if traffic is not None else None,
+                         "traffic_frac": traffic / sup_s / 1e9 / peak if traffic is not None else None,
                          # the full-state byte model (2 D 8 bytes per update):
                          # its roofline in updates/s, and this step against it
                          "full_state_roofline_updates_per_s": peak * 1e9 / (2 * D * 8),
