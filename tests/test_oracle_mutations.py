@@ -11,10 +11,14 @@ import pytest
 import synth
 import test_oracle_adapt as ta
 import test_oracle_evolve as te
+import test_oracle_families as tfam
+import test_oracle_fcidump as tf
 import test_oracle_hamiltonian as th
 import test_oracle_mapping as tm
 import test_oracle_pool as tp
-from oracle import adapt, evolve, fermion, mapping
+import test_oracle_sector as ts
+import test_oracle_vqe as tv
+from oracle import adapt, evolve, families, fcidump, fermion, mapping, sector, vqe
 
 
 def test_wrong_taylor_coefficient_is_caught(monkeypatch):
@@ -100,3 +104,130 @@ def test_wrong_line_search_term_is_caught(monkeypatch):
     sysm = adapt.build_system(ints, ne, mapping.JW)
     with pytest.raises(AssertionError):
         ta.test_line_search_energy_curve((ints, ne, sysm))
+
+
+# ---------------------------------------------------------------- more slips
+
+
+def test_ladder_parity_mask_off_by_one_is_caught(monkeypatch):
+    # route A's parity counted over the modes at or below j instead of below
+    # j: every annihilator picks up an extra sign.  (The string on the modes
+    # above j instead, Eq. (4) as printed, is no slip: for the
+    # number-conserving strings of H and the pool it gives the same matrix.)
+    def bad(states, amps, j, create):
+        occ = (states >> j) & 1
+        valid = (occ == 0) if create else (occ == 1)
+        upto = states & ((1 << (j + 1)) - 1)
+        sign = np.where(np.bitwise_count(upto) & 1, -1.0, 1.0)
+        return states ^ (1 << j), amps * sign * valid
+
+    monkeypatch.setattr(fermion, "apply_ladder", bad)
+    with pytest.raises(AssertionError):
+        th.test_route_b_equals_route_a(mapping.JW, 2, 5)
+
+
+def test_pool_without_mixed_spin_doubles_is_caught(monkeypatch):
+    good = fermion.excitations
+
+    def bad(n_spatial, n_electrons):
+        return [e for e in good(n_spatial, n_electrons) if not (len(e) == 4 and e[0] % 2 != e[1] % 2)]
+
+    monkeypatch.setattr(fermion, "excitations", bad)
+    with pytest.raises(AssertionError):
+        tp.test_pool_sizes_of_workloads()
+
+
+def test_fenwick_range_off_by_one_is_caught(monkeypatch):
+    def bad(k):
+        return range(k + 1 - mapping.lowbit(k), k + 1)      # lowbit(k) for lowbit(k + 1)
+
+    monkeypatch.setattr(mapping, "fenwick_range", bad)
+    with pytest.raises(AssertionError):
+        tm.test_bk_matrix_power_of_two_blocks()
+
+
+def test_hf_state_not_encoded_is_caught(monkeypatch):
+    good = adapt.hf_state
+    monkeypatch.setattr(adapt, "hf_state", lambda nq, ne, mp: good(nq, ne, mapping.JW))
+    with pytest.raises(AssertionError):
+        th.test_hf_energy_closed_form(mapping.BK, "c0")
+
+
+def test_energy_without_normalisation_is_caught(monkeypatch):
+    def bad(H, psi):
+        w = H @ psi
+        return float(np.vdot(psi, w).real), w
+
+    ints, ne = synth.config0()
+    c0 = (ints, ne, adapt.build_system(ints, ne, mapping.JW))
+    monkeypatch.setattr(adapt, "energy", bad)
+    with pytest.raises(AssertionError):
+        ta.test_rayleigh_quotient_scale_invariant(c0)
+
+
+def test_tie_to_the_highest_index_is_caught(monkeypatch):
+    def bad(g, precision=adapt.FP64):
+        ag = np.abs(np.asarray(g))
+        gmax = float(ag.max())
+        tau = adapt.TIE_REL_FP64 * max(1.0, gmax) if precision == adapt.FP64 else adapt.TIE_ABS_C64
+        return int(np.nonzero(ag >= gmax - tau)[0][-1]), gmax
+
+    monkeypatch.setattr(adapt, "select", bad)
+    with pytest.raises(AssertionError):
+        ta.test_tie_rule()
+
+
+def test_adjoint_derivative_missing_a_term_is_caught(monkeypatch):
+    def bad(A, phi, theta):
+        v, acc, coef = phi, np.zeros_like(phi), 1.0
+        for m in range(4):                                 # stops one term short
+            acc = acc + coef * v
+            v = A @ v
+            coef = coef * theta / (m + 1)
+        return A @ acc
+
+    monkeypatch.setattr(vqe, "taylor4_derivative", bad)
+    with pytest.raises(AssertionError):
+        tv.test_taylor4_derivative_is_the_series_derivative()
+
+
+def test_colex_rank_off_by_one_is_caught(monkeypatch):
+    from math import comb
+    monkeypatch.setattr(sector, "subset_rank", lambda cs: sum(comb(c, j) for j, c in enumerate(sorted(cs))))
+    with pytest.raises(AssertionError):
+        ts.test_colex_rank_textbook()
+
+
+def test_fcidump_read_in_physicist_order_is_caught(monkeypatch):
+    good = fcidump.read
+
+    def bad(path):
+        h, g, e, n, ne, ms2 = good(path)
+        return h, g.transpose(0, 2, 1, 3).copy(), e, n, ne, ms2   # (ij|kl) taken as <ij|kl>
+
+    monkeypatch.setattr(fcidump, "read", bad)
+    with pytest.raises(AssertionError):
+        tf.test_hand_written_file()
+
+
+def test_smallest_first_colouring_is_caught(monkeypatch):
+    def bad(n, edges):
+        nbr = [set() for _ in range(n)]
+        for i, j in edges:
+            nbr[i].add(j)
+            nbr[j].add(i)
+        family, members = [-1] * n, []
+        for v in sorted(range(n), key=lambda v: len(nbr[v])):   # Algorithm 1 takes the largest first
+            for f, mem in enumerate(members):
+                if not (nbr[v] & mem):
+                    family[v] = f
+                    mem.add(v)
+                    break
+            else:
+                family[v] = len(members)
+                members.append({v})
+        return family
+
+    monkeypatch.setattr(families, "greedy_families", bad)
+    with pytest.raises(AssertionError):
+        tfam.test_hand_traced_example()
