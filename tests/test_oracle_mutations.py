@@ -231,3 +231,21 @@ def test_smallest_first_colouring_is_caught(monkeypatch):
     monkeypatch.setattr(families, "greedy_families", bad)
     with pytest.raises(AssertionError):
         tfam.test_hand_traced_example()
+
+
+def test_conjugated_y_phase_in_csr_is_caught(monkeypatch):
+    # the element formula with i^(-ny) for i^(ny): the same as scaling each
+    # coefficient by (-1)^ny before the correct formula.  H is real
+    # symmetric, so its strings all have an even number of Y and it cannot
+    # show this slip; the real antisymmetric generators (odd ny) do.
+    from oracle import pauli
+    good = pauli.pauli_to_csr
+
+    def bad(ps, drop_rel=1e-12):
+        ny = np.bitwise_count(ps.x & ps.z).astype(np.int64)
+        flipped = pauli.PauliSum(ps.n_qubits, ps.x, ps.z, ps.c * (1 - 2 * (ny & 1)))
+        return good(flipped, drop_rel)
+
+    monkeypatch.setattr(pauli, "pauli_to_csr", bad)
+    with pytest.raises(AssertionError):
+        tp.test_generators_route_a_equals_route_b(mapping.BK)
