@@ -249,3 +249,11 @@ def test_conjugated_y_phase_in_csr_is_caught(monkeypatch):
     monkeypatch.setattr(pauli, "pauli_to_csr", bad)
     with pytest.raises(AssertionError):
         tp.test_generators_route_a_equals_route_b(mapping.BK)
+
+
+def test_sector_basis_not_encoded_is_caught(monkeypatch):
+    # the sector's qubit indices taken as occupation indices under BK too
+    good = sector.qubit_basis
+    monkeypatch.setattr(sector, "qubit_basis", lambda n, na, nb, mp: good(n, na, nb, mapping.JW))
+    with pytest.raises(AssertionError):
+        ts.test_jw_and_bk_restrictions_are_the_same_matrix("c0")
