@@ -257,3 +257,38 @@ def test_sector_basis_not_encoded_is_caught(monkeypatch):
     monkeypatch.setattr(sector, "qubit_basis", lambda n, na, nb, mp: good(n, na, nb, mapping.JW))
     with pytest.raises(AssertionError):
         ts.test_jw_and_bk_restrictions_are_the_same_matrix("c0")
+
+
+def test_adjoint_sweep_with_the_forward_angle_is_caught(monkeypatch):
+    # the adjoint state carried back through a factor with +theta instead of
+    # its inverse (-theta)
+    def bad(system, ops, thetas, psi0):
+        phis = [psi0]
+        for k, th in zip(ops, thetas):
+            phis.append(evolve.taylor5(system.pool[k], phis[-1], th))
+        psi = phis[-1]
+        nrm = float(np.vdot(psi, psi).real)
+        E, w = adapt.energy(system.H, psi)
+        chi = w - E * psi
+        grad = np.zeros(len(ops))
+        for j in range(len(ops) - 1, -1, -1):
+            A = system.pool[ops[j]]
+            grad[j] = 2.0 * np.vdot(chi, vqe.taylor4_derivative(A, phis[j], thetas[j])).real / nrm
+            chi = evolve.taylor5(A, chi, thetas[j])
+        return E, grad
+
+    monkeypatch.setattr(vqe, "energy_and_gradient", bad)
+    with pytest.raises(AssertionError):
+        tv.test_adjoint_gradient_matches_finite_differences(0)
+
+
+def test_commuting_pairs_taken_as_edges_is_caught(monkeypatch):
+    # the commutation test on the anticommutator AB + BA instead of AB - BA
+    def bad(pool_matrices):
+        mats = [A.toarray() if hasattr(A, "toarray") else np.asarray(A) for A in pool_matrices]
+        return {(i, j) for i in range(len(mats)) for j in range(i + 1, len(mats))
+                if np.abs(mats[i] @ mats[j] + mats[j] @ mats[i]).max() > 1e-12}
+
+    monkeypatch.setattr(families, "full_edges", bad)
+    with pytest.raises(AssertionError):
+        tfam.test_full_edges_match_the_commutator_definition_on_a_tiny_pool()
