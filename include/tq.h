@@ -456,7 +456,10 @@ int tq_energy_noalloc(int n_qubits, int prec, const int* rowptr, const int* col,
                       double* energy_out, void* stream);
 
 /* Same energy, computed from the X-mask-grouped Pauli layout without the
- * CSR (cross-check of the CSR build; arithmetic-bound). */
+ * CSR (cross-check of the CSR build).  Each row's terms are evaluated and
+ * summed in float64, an add per term and row, so the float64 pipe bounds
+ * it (see tq_fp64_fma_rate).  Full space only (TQ_EINVAL for a sector
+ * Hamiltonian or a state of another space).  Synchronises the stream. */
 int tq_energy_matrix_free(tq_ctx* ctx, const tq_ham* ham, const tq_state* psi,
                           double* E, void* stream);
 
