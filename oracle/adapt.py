@@ -138,6 +138,20 @@ def _sample_theta(m, samples):
     return -math.pi + 2.0 * math.pi * (m + 1) / samples
 
 
+def _pick_sample(e, samples):
+    """The tie rule of the line search: among the samples within
+    ``1e-10 * max(1, |E_min|)`` of the lowest energy, the one with the
+    smallest |theta|, then the lowest index."""
+    emin = min(e)
+    tol = LINE_SEARCH_TIE * max(1.0, abs(emin))
+    best_m = None
+    for m in range(samples):
+        if e[m] <= emin + tol:
+            if best_m is None or abs(_sample_theta(m, samples)) < abs(_sample_theta(best_m, samples)):
+                best_m = m
+    return best_m
+
+
 def line_search(coef, samples=LINE_SEARCH_SAMPLES):
     """Global minimiser of the energy along ``exp(theta A) psi`` on (-pi, pi].
 
@@ -151,13 +165,7 @@ def line_search(coef, samples=LINE_SEARCH_SAMPLES):
     chosen sample and are kept only if they do not raise the energy.
     """
     e = [line_energy(coef, _sample_theta(m, samples)) for m in range(samples)]
-    emin = min(e)
-    tol = LINE_SEARCH_TIE * max(1.0, abs(emin))
-    best_m = None
-    for m in range(samples):
-        if e[m] <= emin + tol:
-            if best_m is None or abs(_sample_theta(m, samples)) < abs(_sample_theta(best_m, samples)):
-                best_m = m
+    best_m = _pick_sample(e, samples)
     th0 = _sample_theta(best_m, samples)
     e0 = e[best_m]
     h = 2.0 * math.pi / samples

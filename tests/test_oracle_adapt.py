@@ -127,3 +127,51 @@ def test_adapt_trajectory_invariants():
             assert min(e) >= lam - 1e-10
     assert energies[mapping.JW][1] == energies[mapping.BK][1]
     assert np.abs(np.array(energies[mapping.JW][0]) - np.array(energies[mapping.BK][0])).max() <= 1e-10
+
+
+@pytest.mark.parametrize("mp", [mapping.JW, mapping.BK])
+def test_line_search_tie_takes_the_near_minimum(mp):
+    """The line search's tie reading, pinned by a closed form.
+
+    From psi = |HF>, every pool generator gives A|HF> = +-|Phi_k> and
+    A^2|HF> = -|HF>, so exp(theta A)|HF> = cos(theta)|HF> + sin(theta)A|HF>
+    and the energy along the curve is
+
+        E(theta) = a + b cos(2 theta) + c sin(2 theta),
+        a = (E_HF + E_k)/2,  b = (E_HF - E_k)/2,  c = <HF|H A|HF>,
+
+    with E_HF and E_k the Slater-Condon determinant energies and |c| half
+    the Slater-Condon gradient magnitude.  The curve is pi-periodic: its two
+    minima, theta_1 = atan2(-c, -b)/2 in (-pi/2, pi/2] and theta_1 -+ pi,
+    tie exactly.  The reading (smallest |theta| among tied samples) must
+    return theta_1.  The sign of c is read off the dense exponential's
+    energy at theta = pi/4 (E = a + c there), not off the oracle's
+    line-search coefficients.
+    """
+    ints, ne = synth.config0()
+    sysm = adapt.build_system(ints, ne, mp)
+    psi = adapt.hf_state(8, ne, mp)
+    e_hf = hf_energy_closed_form(ints.h, ints.g, ne)
+    partner_below = 0
+    checked = 0
+    for k, exc in enumerate(sysm.excitations):
+        half = len(exc) // 2
+        occ = (set(range(ne)) - set(exc[:half])) | set(exc[half:])
+        e_k = det_energy(ints.h, ints.g, sorted(occ))
+        a, b = 0.5 * (e_hf + e_k), 0.5 * (e_hf - e_k)
+        cmag = 0.5 * slater_condon_gradient_magnitude(ints.h, ints.g, ne, exc)
+        if cmag < 1e-6:
+            continue                    # no unique pair of minima to tell apart
+        e_quarter = adapt.energy(sysm.H, evolve.expm_dense(sysm.pool[k], math.pi / 4) @ psi)[0]
+        c = math.copysign(cmag, e_quarter - a)
+        assert abs(abs(e_quarter - a) - cmag) <= 1e-10
+        th_ref = 0.5 * math.atan2(-c, -b)
+        partner = th_ref - math.pi if th_ref > 0 else th_ref + math.pi
+        coef = adapt.line_search_coefficients(sysm.H, sysm.pool[k], psi)
+        assert abs(adapt.line_energy(coef, partner) - adapt.line_energy(coef, th_ref)) <= 1e-12
+        th = adapt.line_search(coef)
+        assert abs(th - th_ref) <= 1e-9, (k, th, th_ref)
+        checked += 1
+        partner_below += partner < -math.pi / 2
+    assert checked >= 20
+    assert partner_below >= 1          # a case where the far minimum comes first in sample order

@@ -292,3 +292,19 @@ def test_commuting_pairs_taken_as_edges_is_caught(monkeypatch):
     monkeypatch.setattr(families, "full_edges", bad)
     with pytest.raises(AssertionError):
         tfam.test_full_edges_match_the_commutator_definition_on_a_tiny_pool()
+
+
+def test_first_tied_sample_is_caught(monkeypatch):
+    """The line search's tie reading: "first sample within tolerance" in
+    place of "smallest |theta|" picks the far minimum, about pi away."""
+
+    def bad(e, samples):
+        emin = min(e)
+        tol = adapt.LINE_SEARCH_TIE * max(1.0, abs(emin))
+        return next(m for m in range(samples) if e[m] <= emin + tol)
+
+    monkeypatch.setattr(adapt, "_pick_sample", bad)
+    with pytest.raises(AssertionError):
+        ta.test_line_search_tie_takes_the_near_minimum(mapping.BK)
+    with pytest.raises(AssertionError):
+        ta.test_line_search_tie_takes_the_near_minimum(mapping.JW)
