@@ -310,12 +310,15 @@ def measure_adapt_step(tq, ctx, steps=10):
         tq.state_set_hf(st, ne, MAPPING)
         ctx.trace(True)
         t0 = time.perf_counter()
-        energies = []
+        energies, chosen = [], []
         for _ in range(steps):
-            energies.append(tq.adapt_step(ctx, ham, pool, st, 0.0, float("nan"))["energy"])
+            r_ = tq.adapt_step(ctx, ham, pool, st, 0.0, float("nan"))
+            energies.append(r_["energy"])
+            chosen.append(r_["selected"])
         t = (time.perf_counter() - t0) / steps
         rep = ctx.trace_report()
         ctx.trace(False)
+        roof = adapt_kernel_rooflines(tq, ctx, ham, pool, ints.n_spatial, ne, chosen, rep, steps)
         # the same iterations as one call: the first step launched, the rest
         # replayed from a captured graph (no host round trip between steps)
         tq.state_set_hf(st, ne, MAPPING)
@@ -337,9 +340,63 @@ def measure_adapt_step(tq, ctx, steps=10):
         out[f"{nq_}q_csr"] = {"ms_per_step": 1e3 * tc, "kernel_ms_per_step": {k_: v[1] / steps for k_, v in rep_c.items()},
                               "same_trajectory": [abs(a_ - b_) < 1e-6 for a_, b_ in zip(csr_e, energies)].count(True)}
         out[f"{nq_}q"] = {"ms_per_step": 1e3 * t, "ms_per_step_graph_run": 1e3 * tr, "nnz": ham.nnz, "pool": pool.M,
+                          "rooflines": roof,
                           "kernel_ms_per_step": {k_: v[1] / steps for k_, v in rep.items()},
                           "energy_first_last": [energies[0], energies[-1]],
                           "graph_run_same_energies": [r_["energy"] for r_ in res] == energies}
+    return out
+
+
+_L2_RATE = {}
+
+
+def l2_rate(tq, ctx):
+    """The device's measured L2 read rate (bytes/s), once per process."""
+    if "v" not in _L2_RATE:
+        _L2_RATE["v"] = tq.l2_read_rate(ctx, 32 << 20, 64)
+    return _L2_RATE["v"]
+
+
+def adapt_kernel_rooflines(tq, ctx, ham, pool, n_spatial, ne, chosen, rep, steps):
+    """Achieved bytes over time for the ADAPT step's gradient and line-search
+    kernels, against the HBM copy peak and the measured L2 read rate.
+
+    Gradients (k_pool_grad): every generator's support rows, each reading
+    H psi at the row (float32 pairs for complex64) and psi at its partner:
+    sum_k |S_k| (8 + 8) bytes in complex64; both vectors stay in L2.
+    Line search (k_line_support): the CSR rows of the chosen generator's
+    support (8 bytes per row of offsets and diagonal, 8 per entry of column
+    and value in complex64) and psi (8 bytes per amplitude, read once at
+    best); the gathers land in L2."""
+    import numpy as np
+    peak, _ = peaks()
+    l2 = l2_rate(tq, ctx) / 1e9
+    nq_ = 2 * n_spatial
+    D_ = 1 << nq_
+    f = tq.pool_support_forms(n_spatial, ne, MAPPING)
+    supp = float(sum(D_ >> int(m) for m in f["m"]))
+    out = {"peak_hbm_gbs": peak, "l2_read_gbs": l2}
+    n_g, ms_g = rep.get("pool_gradients", (0, float("nan")))
+    if n_g:
+        b = supp * 16
+        s_ = ms_g / n_g * 1e-3
+        out["pool_gradients"] = {"kernel": "k_pool_grad", "bytes_per_sweep": b, "ms": 1e3 * s_,
+                                 "achieved_gbs": b / s_ / 1e9, "frac_hbm": b / s_ / 1e9 / peak,
+                                 "frac_l2": b / s_ / 1e9 / l2}
+    n_l, ms_l = rep.get("line_support", (0, float("nan")))
+    if n_l:
+        rp, _, _, _ = tq.ham_csr(ham)
+        rowptr = _dev_to_host(rp, D_ + 1, "<i4").astype(np.int64)
+        rows = support_rows(tq, n_spatial, ne, MAPPING, ks=sorted(set(chosen)))
+        per_k = {}
+        for k_, r_ in rows.items():
+            nnz_s = int((rowptr[r_ + 1] - rowptr[r_]).sum())
+            per_k[k_] = 16.0 * r_.size + 8.0 * nnz_s + 8.0 * D_
+        b = float(np.mean([per_k[k_] for k_ in chosen]))
+        s_ = ms_l / n_l * 1e-3
+        out["line_search"] = {"kernel": "k_line_support", "mean_bytes_per_step": b, "ms": 1e3 * s_,
+                              "achieved_gbs": b / s_ / 1e9, "frac_hbm": b / s_ / 1e9 / peak,
+                              "frac_l2": b / s_ / 1e9 / l2}
     return out
 
 
@@ -401,10 +458,21 @@ def run_ours(args, rank, world, local_rank):
     tqd.init("nccl", torch.device("cuda", local_rank))
     S = args.states
     ctx = tq.Context(local_rank)
-    pool = tq.build_pool(ctx, N_SPATIAL, N_ELECTRONS, MAPPING)
+    pool_nat = tq.build_pool(ctx, N_SPATIAL, N_ELECTRONS, MAPPING)
+    # the states' memory layout: BK with its qubits relabelled so that the
+    # pool's supports fill the lowest index bits (32-byte sectors), or BK's
+    # own qubit order; every result is the same up to the index relabelling
+    if args.layout == "sector":
+        order = tq.pool_sector_order(N_SPATIAL, N_ELECTRONS, MAPPING, 4)
+        mp_run = tq.mapping_relabelled(MAPPING, order)
+        pool = tq.build_pool(ctx, N_SPATIAL, N_ELECTRONS, mp_run)
+    else:
+        order = np.arange(NQ)
+        mp_run = MAPPING
+        pool = pool_nat
     # every rank updates its own batch of S states (weak scaling, no exchange)
     prep_k, prep_th, k, th = synth.t5_batch(S, pool.M, seed=tqd.rank_seed(synth.SEED_T5_BATCH, rank))
-    hf = tq.hf_index(NQ, N_ELECTRONS, MAPPING)
+    hf = tq.hf_index(NQ, N_ELECTRONS, mp_run)
     psi = torch.zeros((S, D), dtype=torch.complex64, device="cuda")
     psi[:, hf] = 1.0
     dn = torch.ones(S, dtype=torch.float64, device="cuda")       # ||HF||^2, carried from here on
@@ -419,8 +487,11 @@ def run_ours(args, rank, world, local_rank):
     fetch_default = ctx.l2_fetch()
     ctx.set_l2_fetch(32)
 
+    applied = [0]   # launches of the timed update on the batch (the fidelity check replays them)
+
     def step():
         tq.evolve_taylor5_batch_support(ctx, pool, psi, dk, dth, dn)
+        applied[0] += 1
 
     tune = {}
     for cand in ([args.pair_schedule] if args.pair_schedule else [1, 2, 4, 8, -1, -2, -4, -8]):
@@ -476,7 +547,7 @@ def run_ours(args, rank, world, local_rank):
     # algorithmic bytes: each support amplitude read and written once, the
     # carried norm read and written once; the touched 32-byte sectors and
     # 128-byte lines are the floors the memory system can reach
-    rows = support_rows(tq, N_SPATIAL, N_ELECTRONS, MAPPING)
+    rows = support_rows(tq, N_SPATIAL, N_ELECTRONS, mp_run)
     n_rows = np.array([r.size for r in rows], dtype=np.float64)[k]
     n_sect = np.array([np.unique(r >> 2).size for r in rows], dtype=np.float64)[k]
     n_line = np.array([np.unique(r >> 4).size for r in rows], dtype=np.float64)[k]
@@ -543,7 +614,19 @@ def run_ours(args, rank, world, local_rank):
     e2e["link"] = link
     finite = bool(torch.isfinite(dn).all().item()) and float(dn.min().item()) > 0.5
     extra = {}
+    if rank == 0 and world == 1 and args.fidelity_samples > 0:
+        idx = np.linspace(0, S - 1, args.fidelity_samples).astype(np.int64).tolist()
+        # the oracle's BK order: amplitude b of the oracle is at relabel[b]
+        extra["headline_vs_oracle"] = headline_fidelity(psi, dn, idx, S, tqd.rank_seed(synth.SEED_T5_BATCH, rank),
+                                                        applied[0], tq.relabel_index(order))
+    if rank == 0 and args.layout == "sector":
+        extra["natural_layout"] = measure_natural_layout(tq, ctx, pool_nat, S, k, th, prep_k, prep_th, sup_s)
+    pool = pool_nat   # the other sections use BK's own qubit order
     if rank == 0 and not args.headline_only:
+        extra["precision_vs_oracle"] = measure_precision(tq, ctx)
+        extra["m0_8q_step"] = measure_m0(tq, ctx)
+        extra["m1_12q_trajectories"] = measure_m1(tq, ctx)
+        extra["general_update"] = measure_general_update(tq, ctx)
         extra["fp64_single_instance"] = measure_fp64_single(tq, ctx, pool, k, th)
         extra["full_state"] = measure_full_state(tq, ctx, pool, S)
         extra["rates_14q"] = measure_rates(tq, ctx)
@@ -556,7 +639,8 @@ def run_ours(args, rank, world, local_rank):
         extra["vqe"] = measure_vqe(tq, ctx)
         extra["io"] = measure_io(tq, ctx)
         if args.serve_seconds > 0:
-            extra["serving"] = measure_serving_process(local_rank, args.serve_seconds, args.serve_rate)
+            extra["serving"] = measure_serving_process(local_rank, args.serve_seconds, args.serve_rate,
+                                                       args.serve_sweep)
     out = None
     if rank == 0:
         out = {
@@ -565,7 +649,14 @@ def run_ours(args, rank, world, local_rank):
             "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64",
             "data": "synthetic",
-            "config": dict(workload_config(S), schedule={"support_pairs_per_thread": upt,
+            "config": dict(workload_config(S),
+                           qubit_layout={"kind": args.layout,
+                                         "bit_of_qubit": [int(o) for o in order],
+                                         "note": "Bravyi-Kitaev with qubit k stored at index bit bit_of_qubit[k] "
+                                                 "(tq_mapping_relabelled, order from tq_pool_sector_order): "
+                                                 "the same encoding and results, the pool's supports packed "
+                                                 "into 32-byte sectors"},
+                           schedule={"support_pairs_per_thread": upt,
                                                          "ms_per_launch_by_schedule": tune_ms,
                                                          "l2_fetch_bytes": 32,
                                                          "l2_fetch_default": fetch_default}),
@@ -595,6 +686,51 @@ def run_ours(args, rank, world, local_rank):
         }
         out.update(extra)
     return out
+
+
+def measure_natural_layout(tq, ctx, pool, n_states, k, th, prep_k, prep_th, ms_relabelled, reps=50):
+    """The headline batch in BK's own qubit order (no relabelling): the same
+    states, generators and angles, the same support-only kernel, every
+    schedule timed at 32-byte L2 fetches and the fastest kept."""
+    import numpy as np
+    import torch
+    hf = tq.hf_index(NQ, N_ELECTRONS, MAPPING)
+    psi = torch.zeros((n_states, D), dtype=torch.complex64, device="cuda")
+    psi[:, hf] = 1.0
+    dn = torch.ones(n_states, dtype=torch.float64, device="cuda")
+    for j in range(prep_k.shape[1]):
+        tq.evolve_taylor5_batch_support(ctx, pool, psi, torch.as_tensor(prep_k[:, j].copy()).cuda(),
+                                        torch.as_tensor(prep_th[:, j].copy()).cuda(), dn)
+    dk = torch.as_tensor(k).cuda()
+    dth = torch.as_tensor(th).cuda()
+    ctx.set_l2_fetch(32)
+    per = {}
+    for ppt in (1, 2, 4, -1, -2):
+        ctx.set_support_schedule(tq.TQ_C64, ppt)
+        for _ in range(3):
+            tq.evolve_taylor5_batch_support(ctx, pool, psi, dk, dth, dn)
+        ctx.trace(True)
+        for _ in range(reps):
+            tq.evolve_taylor5_batch_support(ctx, pool, psi, dk, dth, dn)
+        rep = ctx.trace_report()
+        ctx.trace(False)
+        n_l, ms = rep["taylor5_support"]
+        per[ppt] = ms / n_l
+    ctx.set_l2_fetch(0)
+    best = min(per, key=per.get)
+    ms = per[best]
+    rows = support_rows(tq, N_SPATIAL, N_ELECTRONS, MAPPING)
+    n_rows = np.array([r.size for r in rows], dtype=np.float64)[k]
+    n_sect = np.array([np.unique(r >> 2).size for r in rows], dtype=np.float64)[k]
+    alg = float((16 * n_rows).sum() + 16 * n_states)
+    sect = float((64 * n_sect).sum() + 16 * n_states)
+    peak, _ = peaks()
+    return {"workload": "the headline batch in BK's own qubit order", "pairs_per_thread": best,
+            "ms_per_launch": ms, "ms_by_schedule": {str(p_): v for p_, v in per.items()},
+            "updates_per_s": n_states / (ms * 1e-3),
+            "algorithmic_bytes_per_launch": alg, "sector_bytes_per_launch": sect,
+            "frac": alg / (ms * 1e-3) / 1e9 / peak, "sector_frac": sect / (ms * 1e-3) / 1e9 / peak,
+            "relabelled_speedup": ms / (ms_relabelled * 1e3)}
 
 
 def measure_full_state(tq, ctx, pool, n_states, reps=50):
@@ -712,9 +848,10 @@ def _parity(v):
     return (v & np.uint64(1)).astype(np.int64)
 
 
-def support_rows(tq, n_spatial, n_electrons, mapping):
+def support_rows(tq, n_spatial, n_electrons, mapping, ks=None):
     """Per generator, the rows its support-only update reads and writes
-    (pair representatives and partners), from the library's support form."""
+    (pair representatives and partners), from the library's support form;
+    a list over the pool, or a dict over `ks` when given."""
     import numpy as np
 
     def insert_zero(v, b):
@@ -723,15 +860,19 @@ def support_rows(tq, n_spatial, n_electrons, mapping):
     N = 2 * n_spatial
     f = tq.pool_support_forms(n_spatial, n_electrons, mapping)
     x = tq.pauli_pool(n_spatial, n_electrons, mapping)[0]
-    out = []
-    for k in range(x.size):
+    out = [] if ks is None else {}
+    for k in (range(x.size) if ks is None else ks):
         m = int(f["m"][k])
         r = insert_zero(np.arange(1 << (N - m - 1), dtype=np.int64), int(f["rep_pos"][k]))
         for p in f["pivots"][k, :m]:
             r = insert_zero(r, int(p))
         for i, p in enumerate(f["pivots"][k, :m]):
             r = r | ((((int(f["target"][k]) >> i) & 1) ^ _parity(r & int(f["masks"][k, i]))) << int(p))
-        out.append(np.concatenate([r, r ^ int(x[k])]))
+        rows = np.concatenate([r, r ^ int(x[k])])
+        if ks is None:
+            out.append(rows)
+        else:
+            out[k] = rows
     return out
 
 
@@ -814,17 +955,30 @@ def measure_fp64_single(tq, ctx, pool, k, th, reps=2000):
         tq.evolve_taylor5(ctx, pool, int(k[i]), float(th[i]), st, renormalize=True)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    kl = [int(x) for x in k[:reps]]
+    tl = [float(x) for x in th[:reps]]
+    n = len(kl)
     torch.cuda.synchronize()
+    l0 = ctx.launches()
     e0.record()
     for i in range(reps):
-        tq.evolve_taylor5(ctx, pool, int(k[i % len(k)]), float(th[i % len(th)]), st, renormalize=True)
+        tq.evolve_taylor5(ctx, pool, kl[i % n], tl[i % n], st, renormalize=True)
     e1.record()
     torch.cuda.synchronize()
+    launches = (ctx.launches() - l0) / reps
     ms = e0.elapsed_time(e1) / reps
+    # the kernel alone (CUDA events around each launch)
+    ctx.trace(True)
+    for i in range(200):
+        tq.evolve_taylor5(ctx, pool, kl[i % n], tl[i % n], st, renormalize=True)
+    rep = ctx.trace_report()
+    ctx.trace(False)
+    kn = "taylor5_single" if "taylor5_single" in rep else "taylor5_pair"
     return {"workload": "one 14-qubit complex128 state, evolve_taylor5 with renormalisation per call, "
-                        "back-to-back calls on one stream",
+                        "back-to-back calls on one stream from Python",
             "updates_per_s": 1e3 / ms, "us_per_update": ms * 1e3,
-            "launches_per_update": 3}
+            "launches_per_update": launches, "kernel": kn,
+            "kernel_us_per_update": 1e3 * sum(v[1] for v in rep.values()) / 200}
 
 
 def measure_spmv(tq, ctx, nq):
@@ -1057,13 +1211,13 @@ def measure_families(tq):
     return {"workload": "pool of 9 orbitals, 8 electrons, BK (560 generators)", **out}
 
 
-def measure_serving_process(device, seconds, rate):
+def measure_serving_process(device, seconds, rate, sweep=""):
     """The request loop measured in a process of its own (as a server runs):
     `bench.py --section serving` on the same device, its JSON line parsed."""
     env = dict(os.environ, LOCAL_RANK=str(device), RANK="0", WORLD_SIZE="1")
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--section", "serving",
-           "--serve-seconds", str(seconds), "--serve-rate", str(rate)]
-    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=seconds + 600)
+           "--serve-seconds", str(seconds), "--serve-rate", str(rate), "--serve-sweep", sweep]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=seconds + 900)
     if r.returncode != 0:
         return {"error": f"serving process exited {r.returncode}: {r.stderr.strip()[-300:]}"}
     out = json.loads(r.stdout.strip().splitlines()[-1])
@@ -1071,30 +1225,12 @@ def measure_serving_process(device, seconds, rate):
     return out
 
 
-def measure_serving(tq, device, seconds, rate):
-    """Poisson request stream into the continuous-batching request loop."""
+def _serve_stream(tq, srv, arr, pools_m, n_cat, timeout_s):
+    """Submits a timed arrival list from a thread while polling completions;
+    returns latency and throughput figures."""
     import numpy as np
-
-    import synth
-    ctx = tq.Context(device)                  # the server owns this context
-    srv = tq.Server(ctx, tq.TQ_C64, hbm_budget=16 << 30, max_batch=1024)
-    cat = synth.catalogue()
-    pools_m = []
-    t0 = time.perf_counter()
-    for n, ne, mp, seed in cat:
-        ints = synth.integrals(n, seed)
-        ham = tq.build_hamiltonian(ctx, ints.h, ints.g, ints.e_const, mp, tq.TQ_C64)
-        pool = tq.build_pool(ctx, n, ne, mp)
-        srv.add_hamiltonian(ham, pool)
-        pools_m.append(pool.M)
-    n_sessions = 256
-    for j in range(n_sessions):
-        n, ne, mp, _ = cat[j % len(cat)]
-        srv.add_session(j % len(cat), ne, mp)
-    build_s = time.perf_counter() - t0
-    srv.start()
-    arr = synth.arrivals(rate, seconds, n_sessions)
     lag = []
+    ticks0 = srv.stats()["ticks"]
 
     def submitter():
         start = time.perf_counter()
@@ -1103,17 +1239,18 @@ def measure_serving(tq, device, seconds, rate):
             if dt > 0:
                 time.sleep(dt)
             lag.append(time.perf_counter() - start - a.t)
-            srv.submit(a.kind, a.session, a.op % pools_m[a.session % len(cat)], a.theta, i)
+            srv.submit(a.kind, a.session, a.op % pools_m[a.session % n_cat], a.theta, i)
 
     th = threading.Thread(target=submitter)
     th.start()
     got = []
-    deadline = time.perf_counter() + seconds + 60
+    deadline = time.perf_counter() + timeout_s
     while len(got) < len(arr) and time.perf_counter() < deadline:
         got += srv.poll(5000)
     th.join()
-    srv.stop()
-    st = srv.stats()
+    ticks = srv.stats()["ticks"] - ticks0
+    if not got:
+        return {"requests": len(arr), "completed": 0}
     lat = np.array([c["t_done"] - c["t_submit"] for c in got]) * 1e3
     span = max(c["t_done"] for c in got) - min(c["t_submit"] for c in got)
     by_kind = {}
@@ -1122,16 +1259,60 @@ def measure_serving(tq, device, seconds, rate):
         if lk.size:
             by_kind[name] = {"n": int(lk.size), "p50_ms": float(np.percentile(lk, 50)),
                              "p99_ms": float(np.percentile(lk, 99))}
-    return {"workload": (f"Poisson arrivals at {rate:.0f}/s for {seconds:.0f} s, 50% evolve / 30% energy / "
-                         "20% gradients, 256 resident sessions over 16 resident Hamiltonians and pools of "
-                         "12-18 qubits (synthetic, seeds 2000+j), complex64 with float64 reductions"),
-            "requests": len(arr), "completed": len(got),
+    return {"requests": len(arr), "completed": len(got),
             "failed": int(sum(c["status"] != 0 for c in got)),
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "throughput_rps": len(got) / span,
-            "ticks": st["ticks"], "mean_batch": len(got) / max(1, st["ticks"]),
+            "ticks": ticks, "mean_batch": len(got) / max(1, ticks),
             "submit_lag_p99_ms": float(np.percentile(np.array(lag) * 1e3, 99)),
-            "by_kind": by_kind, "build_s": build_s}
+            "by_kind": by_kind}
+
+
+def measure_serving(tq, device, seconds, rate, sweep=(), sweep_seconds=5.0):
+    """Poisson request stream into the continuous-batching request loop, then
+    (same server, same resident sessions) a sweep of offered rates up to
+    saturation: it stops once p99 passes 10 ms, a request fails or the
+    achieved rate falls below 80 % of the offered one."""
+    import synth
+    ctx = tq.Context(device)                  # the server owns this context
+    srv = tq.Server(ctx, tq.TQ_C64, hbm_budget=16 << 30, max_batch=1024)
+    cat = synth.catalogue()
+    pools_m = []
+    t0 = time.perf_counter()
+    for n, ne, mp_, seed in cat:
+        ints = synth.integrals(n, seed)
+        ham = tq.build_hamiltonian(ctx, ints.h, ints.g, ints.e_const, mp_, tq.TQ_C64)
+        pool = tq.build_pool(ctx, n, ne, mp_)
+        srv.add_hamiltonian(ham, pool)
+        pools_m.append(pool.M)
+    n_sessions = 256
+    for j in range(n_sessions):
+        n, ne, mp_, _ = cat[j % len(cat)]
+        srv.add_session(j % len(cat), ne, mp_)
+    build_s = time.perf_counter() - t0
+    srv.start()
+    out = {"workload": (f"Poisson arrivals at {rate:.0f}/s for {seconds:.0f} s, 50% evolve / 30% energy / "
+                        "20% gradients, 256 resident sessions over 16 resident Hamiltonians and pools of "
+                        "12-18 qubits (synthetic, seeds 2000+j), complex64 with float64 reductions")}
+    if seconds > 0:
+        out.update(_serve_stream(tq, srv, synth.arrivals(rate, seconds, n_sessions), pools_m, len(cat),
+                                 seconds + 60))
+    sw = []
+    for r_ in sweep:
+        res = _serve_stream(tq, srv, synth.arrivals(r_, sweep_seconds, n_sessions), pools_m, len(cat),
+                            sweep_seconds + 30)
+        res = {"offered_rps": r_, "seconds": sweep_seconds, **res}
+        sw.append(res)
+        if (res.get("completed", 0) < res["requests"] or res.get("failed", 0) > 0 or res["p99_ms"] > 10.0
+                or res["throughput_rps"] < 0.8 * r_):
+            break
+    if sw:
+        out["sweep"] = sw
+        out["sweep_note"] = ("the same server and sessions, one Poisson stream per offered rate; mean_batch is "
+                             "requests per tick of the loop")
+    srv.stop()
+    out["build_s"] = build_s
+    return out
 
 
 def measure_trajectories(tq, ctx, n_traj):
@@ -1179,6 +1360,285 @@ def measure_trajectories(tq, ctx, n_traj):
             "kernel_ms_untimed_direct_run": {k: round(v[1], 3) for k, v in split.items()}}
 
 
+# ------------------------------------------- precision against the oracle
+
+def _dev_to_host(ptr, n, typestr):
+    """Copy n elements at a device pointer into a numpy array."""
+    import numpy as np
+    import torch
+
+    class _A:
+        __cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr), False),
+                                    "version": 3}
+    if n == 0:
+        return np.zeros(0, dtype=np.dtype(typestr))
+    t = torch.as_tensor(_A(), device="cuda")
+    torch.cuda.synchronize()
+    return t.cpu().numpy().copy()
+
+
+def _fid(a, b):
+    import numpy as np
+    return float(abs(np.vdot(a, b)) ** 2 / (np.vdot(a, a).real * np.vdot(b, b).real))
+
+
+def _oracle_headline_worker(args):
+    """The oracle's states for sampled members of the headline batch: each
+    prepared from HF by its three rotations, then its own update applied
+    n_apply times (the number of launches the bench ran on the batch)."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    idx, n_states, seed, n_apply = args
+    import synth
+    from oracle import adapt, evolve, pauli
+    exc, pps = pauli.pool_pauli(N_SPATIAL, N_ELECTRONS, MAPPING)
+    prep_k, prep_th, k, th = synth.t5_batch(n_states, len(exc), seed=seed)
+    out = []
+    for b in idx:
+        psi = adapt.hf_state(NQ, N_ELECTRONS, MAPPING)
+        for j in range(prep_k.shape[1]):
+            psi = evolve.taylor5(pauli.pauli_to_csr(pps[int(prep_k[b, j])]), psi, prep_th[b, j])
+        A = pauli.pauli_to_csr(pps[int(k[b])])
+        for _ in range(n_apply):
+            psi = evolve.taylor5(A, psi, th[b])
+        out.append(psi)
+    return out
+
+
+def headline_fidelity(psi, dn, idx, n_states, seed, n_apply, relabel):
+    """The headline batch's sampled states against the oracle after the
+    same updates: fidelity, relative L2 error and the carried norm's error.
+    relabel[b] is the index of the oracle's basis state b in the GPU layout."""
+    import numpy as np
+    cores = min(len(idx), os.cpu_count() or 1)
+    chunks = [list(idx[i::cores]) for i in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as p:
+        res = p.map(_oracle_headline_worker, [(c, n_states, seed, n_apply) for c in chunks])
+    ref = {}
+    for c, r in zip(chunks, res):
+        for b, v in zip(c, r):
+            ref[b] = v
+    fids, rels, nerr = [], [], []
+    got = psi[list(idx)].cpu().numpy()[:, relabel]
+    norms = dn[list(idx)].cpu().numpy()
+    for i, b in enumerate(idx):
+        o = ref[b]
+        fids.append(_fid(got[i], o))
+        rels.append(float(np.linalg.norm(got[i] - o) / np.linalg.norm(o)))
+        nerr.append(abs(float(norms[i]) - float(np.vdot(o, o).real)) / float(np.vdot(o, o).real))
+    return {"sampled_states": len(idx), "updates_per_state": n_apply + 3,
+            "min_fidelity": min(fids), "max_one_minus_fidelity": max(1.0 - f for f in fids),
+            "max_rel_l2": max(rels), "max_carried_norm_rel_err": max(nerr),
+            "reference": "oracle (complex128 SciPy CSR chain of Eqs. (7)-(8)) after the same 3 preparation "
+                         "and n_apply timed updates of each sampled state, no renormalisation"}
+
+
+def measure_precision(tq, ctx, steps=12):
+    """Each result of the complex64 form against the float64 oracle, on the
+    14-qubit BK workload (strongly correlated integrals, pool of 204): ADAPT
+    steps with the line search from HF run on the GPU in complex64 and in
+    complex128.  After every step the oracle takes the GPU's operator and
+    angle (teacher forcing) from its own complex128 state; the step's
+    energy, gradient maximum and angle are compared with the oracle's at that
+    state, and the GPU state after the update with the oracle's."""
+    import numpy as np
+
+    import synth
+    from oracle import adapt as oadapt
+    from oracle import evolve as oevolve
+    ints, ne = synth.config2()
+    sysm = oadapt.build_system(ints, ne, MAPPING)
+    out = {"workload": "ADAPT with the line search from HF, 14 q BK, config-2 integrals (seed 2), pool of 204; "
+                       "oracle teacher-forced with the GPU's operator and angle",
+           "steps": steps}
+    pool = tq.build_pool(ctx, ints.n_spatial, ne, MAPPING)
+    for prec, name in ((tq.TQ_C64, "c64"), (tq.TQ_C128, "c128")):
+        ham = tq.build_hamiltonian(ctx, ints.h, ints.g, ints.e_const, MAPPING, prec)
+        st = tq.State(ctx, NQ, prec)
+        tq.state_set_hf(st, ne, MAPPING)
+        psi_o = oadapt.hf_state(NQ, ne, MAPPING)
+        rows = []
+        for it in range(steps):
+            e_o, _ = oadapt.energy(sysm.H, psi_o)
+            g_o = oadapt.gradients(sysm.H, sysm.pool, psi_o)
+            k_o, gmax_o = oadapt.select(g_o, oadapt.FP64 if prec == tq.TQ_C128 else oadapt.C64)
+            r = tq.adapt_step(ctx, ham, pool, st, 0.0, float("nan"))
+            k = r["selected"]
+            th_o = oadapt.line_search(oadapt.line_search_coefficients(sysm.H, sysm.pool[k], psi_o))
+            psi_o = oevolve.normalise(oevolve.taylor5(sysm.pool[k], psi_o, r["theta"]))
+            got = st.numpy().astype(np.complex128)
+            e_after = tq.energy(ctx, ham, st)
+            rows.append({"step": it, "selected": k, "oracle_selected": k_o,
+                         "selection_tie": bool(abs(abs(g_o[k]) - gmax_o) <= 1e-5),
+                         "energy_err_ha": r["energy"] - e_o, "max_grad_err": r["max_grad"] - gmax_o,
+                         "theta_err": r["theta"] - th_o,
+                         "state_fidelity": _fid(got, psi_o),
+                         "state_rel_l2": float(np.linalg.norm(got - psi_o) / np.linalg.norm(psi_o)),
+                         "energy_after_err_ha": e_after - oadapt.energy(sysm.H, psi_o)[0]})
+        out[name] = {"per_step": rows,
+                     "max_abs_energy_err_ha": max(abs(x["energy_err_ha"]) for x in rows),
+                     "max_abs_energy_after_err_ha": max(abs(x["energy_after_err_ha"]) for x in rows),
+                     "min_state_fidelity": min(x["state_fidelity"] for x in rows),
+                     "max_abs_theta_err": max(abs(x["theta_err"]) for x in rows),
+                     "selections_equal_or_tied": sum(x["selected"] == x["oracle_selected"] or x["selection_tie"]
+                                                     for x in rows),
+                     "final_energy": rows[-1]["energy_after_err_ha"] + oadapt.energy(sysm.H, psi_o)[0]}
+    out["c64_minus_c128_final_energy_ha"] = out["c64"]["final_energy"] - out["c128"]["final_energy"]
+    out["bounds"] = {"c64_energy_ha": 1e-6, "c64_fidelity": 0.999999, "c128_energy_ha": 1e-10}
+    return out
+
+
+def measure_m0(tq, ctx, reps=200):
+    """The plain method at 8 qubits (JW, complex128, one ADAPT step from HF at
+    theta = 0.05): the GPU step and the oracle's, timed, and the result
+    against the dense exponential (eigendecomposition of the 256 x 256
+    generator)."""
+    import numpy as np
+
+    import synth
+    from oracle import adapt as oadapt
+    from oracle import evolve as oevolve
+    ints, ne = synth.config0()
+    mp_ = 0
+    th = 0.05
+    sysm = oadapt.build_system(ints, ne, mp_)
+    psi0 = oadapt.hf_state(8, ne, mp_)
+    ham = tq.build_hamiltonian(ctx, ints.h, ints.g, ints.e_const, mp_, tq.TQ_C128)
+    pool = tq.build_pool(ctx, ints.n_spatial, ne, mp_)
+    st = tq.State(ctx, 8, tq.TQ_C128)
+    for _ in range(10):
+        tq.state_set_hf(st, ne, mp_)
+        r = tq.adapt_step(ctx, ham, pool, st, 1e-3, th)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        tq.state_set_hf(st, ne, mp_)
+        r = tq.adapt_step(ctx, ham, pool, st, 1e-3, th)
+    t_gpu = (time.perf_counter() - t0) / reps
+    got = st.numpy()
+    n_o = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < 1.0:
+        ref, psi_ref = oadapt.adapt_step(sysm, psi0, 1e-3, theta=th)
+        n_o += 1
+    t_o = (time.perf_counter() - t0) / n_o
+    ex = oevolve.expm_dense(sysm.pool[r["selected"]], th) @ psi0
+    ex = ex / np.linalg.norm(ex)
+    return {"workload": "config 0: 8 qubits (4 orbitals, 4 electrons, seed 0), JW, complex128, one ADAPT step "
+                        "from HF at theta = 0.05 (energy, 26 gradients, selection, Taylor-5, renormalisation)",
+            "gpu_ms_per_step": 1e3 * t_gpu, "gpu_api": "tq_state_set_hf + tq_adapt_step (host result, synchronous)",
+            "oracle_ms_per_step": 1e3 * t_o, "oracle_cores": 1,
+            "selected": r["selected"], "oracle_selected": ref.selected,
+            "energy_err_vs_oracle_ha": r["energy"] - ref.energy,
+            "state_rel_l2_vs_oracle": float(np.linalg.norm(got - psi_ref) / np.linalg.norm(psi_ref)),
+            "state_err_vs_dense_expm": float(np.linalg.norm(got - ex)),
+            "truncation_bound": th ** 6 / 720,
+            "fidelity_vs_dense_expm": _fid(got, ex),
+            "energy_after_vs_dense_expm_ha": tq.energy(ctx, ham, st) - oadapt.energy(sysm.H, ex)[0]}
+
+
+def measure_m1(tq, ctx, n_iter=20):
+    """The plain method at 12 qubits: 20 ADAPT iterations (eps = 1e-3, line
+    search) from HF under JW and BK, on the GPU in complex128 and in
+    complex64 with float64 reductions (one tq_adapt_run call each), and the
+    oracle's float64 trajectory, all timed."""
+    import numpy as np
+
+    import synth
+    from oracle import adapt as oadapt
+    ints, ne = synth.config1()
+    out = {"workload": "config 1: 12 qubits (6 orbitals, 8 electrons, seed 1), pool of 92, 20 ADAPT iterations "
+                       "from HF, eps 1e-3, line-search angles"}
+    for mp_, mname in ((0, "JW"), (1, "BK")):
+        sysm = oadapt.build_system(ints, ne, mp_)
+        t0 = time.perf_counter()
+        res_o, psi_o = oadapt.trajectory(sysm, oadapt.hf_state(12, ne, mp_), 1e-3, n_iter=n_iter)
+        t_o = time.perf_counter() - t0
+        e_o = [r.energy for r in res_o]
+        row = {"oracle": {"seconds": t_o, "cores": 1, "iterations": len(res_o),
+                          "final_energy": oadapt.energy(sysm.H, psi_o)[0]}}
+        pool = tq.build_pool(ctx, ints.n_spatial, ne, mp_)
+        for prec, pname in ((tq.TQ_C128, "fp64"), (tq.TQ_C64, "c64")):
+            ham = tq.build_hamiltonian(ctx, ints.h, ints.g, ints.e_const, mp_, prec)
+            st = tq.State(ctx, 12, prec)
+            tq.state_set_hf(st, ne, mp_)
+            tq.adapt_run(ctx, ham, pool, st, 1e-3, n_iter)       # warm (captures its graph)
+            tq.state_set_hf(st, ne, mp_)
+            t0 = time.perf_counter()
+            res, done = tq.adapt_run(ctx, ham, pool, st, 1e-3, n_iter)
+            t = time.perf_counter() - t0
+            e = [x["energy"] for x in res[:done]]
+            m = min(len(e), len(e_o))
+            row[pname] = {"seconds": t, "ms_per_iteration": 1e3 * t / max(done, 1), "iterations": done,
+                          "final_energy": tq.energy(ctx, ham, st),
+                          "same_selections_as_oracle": sum(res[i]["selected"] == res_o[i].selected
+                                                           for i in range(m)),
+                          "max_abs_energy_diff_vs_oracle_ha": float(np.max(np.abs(np.array(e[:m]) -
+                                                                                   np.array(e_o[:m])))),
+                          "speedup_vs_oracle": t_o / t}
+        row["c64_minus_fp64_final_energy_ha"] = row["c64"]["final_energy"] - row["fp64"]["final_energy"]
+        out[mname] = row
+    return out
+
+
+def measure_general_update(tq, ctx, reps=100):
+    """The general-operator fused Taylor-5 (tq_evolve_taylor5_csr: any CSR
+    operator, the state held in a thread-block cluster's shared memory, each
+    of the five products behind a cluster barrier) and the one-launch
+    single-state update of a pool generator (tq_evolve_taylor5), 14 qubits."""
+    import synth
+    ints, ne = synth.config2()
+    peak, _ = peaks()
+    pool = tq.build_pool(ctx, ints.n_spatial, ne, MAPPING)
+    D_ = 1 << NQ
+    out = {"workload": "one 14-qubit state (HF after three updates), config-2 BK operators"}
+    for prec, name, vb in ((tq.TQ_C64, "c64", 4), (tq.TQ_C128, "c128", 8)):
+        ham = tq.build_hamiltonian(ctx, ints.h, ints.g, ints.e_const, MAPPING, prec)
+        st = tq.State(ctx, NQ, prec)
+        tq.state_set_hf(st, ne, MAPPING)
+        for k, th in RATE_OPS:
+            tq.evolve_taylor5(ctx, pool, k, th, st)
+        sb = 8 if prec == tq.TQ_C64 else 16
+        res = {}
+        rp, cl, vl, nnz = tq.pool_csr(ctx, pool, 101, prec)
+        hrp, hcl, hvl, _ = tq.ham_csr(ham)
+        for oname, (orp, ocl, ovl, onnz, th) in (("pool_generator_101", (rp, cl, vl, nnz, 0.07)),
+                                                 ("hamiltonian_offdiagonal", (hrp, hcl, hvl, ham.nnz, 0.01))):
+            for _ in range(5):
+                tq.evolve_taylor5_csr(ctx, NQ, orp, ocl, ovl, th, st, renormalize=True)
+            ctx.trace(True)
+            for _ in range(reps):
+                tq.evolve_taylor5_csr(ctx, NQ, orp, ocl, ovl, th, st, renormalize=True)
+            rep = ctx.trace_report()
+            ctx.trace(False)
+            n_l, ms = rep.get("taylor5_csr", (1, float("nan")))
+            ms /= n_l
+            csr_b = 4 * (D_ + 1) + (4 + vb) * onnz
+            alg = 2 * D_ * sb + csr_b
+            res[oname] = {"nnz": int(onnz), "ms_per_update": ms, "algorithmic_bytes": alg,
+                          "bytes_note": "state in and out once + the CSR once from HBM (it is re-read 4 more "
+                                        "times from L2, not counted)",
+                          "achieved_gbs": alg / (ms * 1e-3) / 1e9, "frac": alg / (ms * 1e-3) / 1e9 / peak,
+                          "csr_l2_gbs": 5 * csr_b / (ms * 1e-3) / 1e9}
+        # the one-launch single-state update (pool generator, renormalised)
+        l0 = ctx.launches()
+        ctx.trace(True)
+        for i in range(reps):
+            tq.evolve_taylor5(ctx, pool, RATE_OPS[i % 3][0], 0.01, st, renormalize=True)
+        rep = ctx.trace_report()
+        ctx.trace(False)
+        launches = (ctx.launches() - l0) / reps
+        kname = "taylor5_single" if "taylor5_single" in rep else "taylor5_pair"
+        n_l, ms = rep[kname]
+        ms /= n_l
+        res["single_state_pool_update"] = {"kernel": kname, "launches_per_update": launches,
+                                           "ms_per_update": ms, "algorithmic_bytes": 2 * D_ * sb,
+                                           "achieved_gbs": 2 * D_ * sb / (ms * 1e-3) / 1e9,
+                                           "frac": 2 * D_ * sb / (ms * 1e-3) / 1e9 / peak}
+        out[name] = res
+    out["peak_gbs"] = peak
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1191,13 +1651,20 @@ def main():
     ap.add_argument("--headline-only", action="store_true",
                     help="skip the SpMV, trajectory-batch and request-loop measurements")
     ap.add_argument("--section", choices=["spmv", "trajectories", "serving", "sector", "vqe", "c128", "support",
-                                              "full_state", "adapt"], default=None,
+                                              "full_state", "adapt", "precision", "m0", "m1", "general",
+                                              "fp64_single"], default=None,
                     help="run one secondary measurement alone and print its JSON (profiling)")
     ap.add_argument("--spmv-qubits", type=int, default=18)
     ap.add_argument("--traj", type=int, default=256)
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the request-loop measurement (0 skips it)")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-sweep", type=str, default="2000,8000,16000,32000,64000,128000",
+                    help="offered rates (requests/s) of the saturation sweep, comma-separated ('' skips)")
+    ap.add_argument("--layout", choices=["sector", "natural"], default="sector",
+                    help="states in BK's qubit order relabelled for sector fill, or in BK's own order")
+    ap.add_argument("--fidelity-samples", type=int, default=64,
+                    help="headline states checked against the oracle after the run (0 skips)")
     ap.add_argument("--pair-schedule", type=int, default=0,
                     help="support pairs per thread of the update (0 = autotune)")
     args = ap.parse_args()
@@ -1234,12 +1701,26 @@ def main():
             print(json.dumps(measure_full_state(tq, ctx, tq.build_pool(ctx, N_SPATIAL, N_ELECTRONS, MAPPING), 8192)))
         elif args.section == "support":
             print(json.dumps(measure_support(tq, ctx, tq.build_pool(ctx, N_SPATIAL, N_ELECTRONS, MAPPING), 8192)))
+        elif args.section == "precision":
+            print(json.dumps(measure_precision(tq, ctx)))
+        elif args.section == "m0":
+            print(json.dumps(measure_m0(tq, ctx)))
+        elif args.section == "m1":
+            print(json.dumps(measure_m1(tq, ctx)))
+        elif args.section == "general":
+            print(json.dumps(measure_general_update(tq, ctx)))
+        elif args.section == "fp64_single":
+            import synth
+            pool = tq.build_pool(ctx, N_SPATIAL, N_ELECTRONS, MAPPING)
+            _, _, k_, th_ = synth.t5_batch(8192, pool.M)
+            print(json.dumps(measure_fp64_single(tq, ctx, pool, k_, th_)))
         elif args.section == "c128":
             import synth
             ints, ne = synth.config2()
             print(json.dumps(measure_c128_batched(tq, ctx, tq.build_pool(ctx, ints.n_spatial, ne, MAPPING))))
         else:
-            print(json.dumps(measure_serving(tq, local_rank, args.serve_seconds, args.serve_rate)))
+            sweep = [float(x) for x in args.serve_sweep.split(",") if x.strip()]
+            print(json.dumps(measure_serving(tq, local_rank, args.serve_seconds, args.serve_rate, sweep)))
         return 0
 
     out = run_ours(args, rank, world, local_rank)

@@ -45,6 +45,9 @@ extern "C" {
  * parity of modes k+1-lowbit(k+1) .. k). */
 enum { TQ_JW = 0, TQ_BK = 1 };
 
+/* Ids of relabelled mappings (tq_mapping_relabelled) start here. */
+#define TQ_MAPPING_FIRST_RELABELLED 16
+
 /* Precisions: TQ_C128 runs every product and sum in float64.  TQ_C64 keeps
  * states and sparse products in complex64 (float32) while Hamiltonian
  * diagonals, energy and gradient dot reductions, norms and the convergence
@@ -184,6 +187,33 @@ int tq_pauli_pool(int n_spatial, int n_electrons, int mapping, int capacity,
 int tq_pool_support_forms(int n_spatial, int n_electrons, int mapping,
                           int capacity, int* m, int* pivots, uint64_t* masks,
                           int* target, int* rep_bit, int* rep_pos);
+
+/* A relabelled mapping: the JW or BK encoding (base_mapping) with its
+ * qubit k stored at bit order[k] of the basis index (order: a permutation
+ * of 0 .. n_qubits-1).  Relabelling the qubits of an encoding gives another
+ * linear encoding of the same occupations (Sec. II-A), so energies,
+ * gradients, norms and fidelities are those of the base mapping, and every
+ * amplitude sits at the relabelled index.  It changes only how the
+ * amplitudes are laid out in memory.  The returned id is accepted wherever
+ * a mapping is, for this qubit count only (TQ_EINVAL otherwise);
+ * registering the same relabelling again returns the same id.  Ids live
+ * until the process exits (at most 4096).  Host only; thread-safe.
+ * TQ_EINVAL for a base other than JW/BK, n_qubits outside [1, 30], or an
+ * order that is not a permutation. */
+int tq_mapping_relabelled(int base_mapping, int n_qubits, const int* order, int* mapping_out);
+
+/* A qubit order for tq_mapping_relabelled that makes the pool's supports
+ * (tq_pool_support_forms) dense in the lowest index bits.  An in-place
+ * update that touches only a generator's support (the support-only batched
+ * update) moves whole memory sectors, 32 bytes = the 2 lowest bits for
+ * complex64 amplitudes, and a support whose conditions have rank r on the
+ * lowest bits fills 2^-r of every sector it touches.  The lowest low_bits
+ * bits (0 .. 2 n_spatial) are filled one at a time, each with the qubit
+ * that minimises sum_k |S_k| 2^rank_k over the pool of singles and doubles
+ * (ties: the lowest qubit); the other qubits follow in their base order.
+ * order_out receives 2 n_spatial entries.  Host only.  TQ_EINVAL for bad
+ * sizes or base mapping. */
+int tq_pool_sector_order(int n_spatial, int n_electrons, int base_mapping, int low_bits, int* order_out);
 
 /* Qubit-basis index of the Hartree-Fock determinant (spin orbitals
  * P < n_electrons occupied) under `mapping`.  Host only. */
@@ -444,7 +474,7 @@ int tq_energy(tq_ctx* ctx, const tq_ham* ham, const tq_state* psi, double* E,
  * `stream`; the call does not synchronise.
  * Its scratch is one fixed 64 KiB array in device global memory that every
  * GPU loading the library holds until the process exits; it bounds the
- * reduction to 4032 CTA partials.  The first call on a device resolves that
+ * reduction to 4064 CTA partials.  The first call on a device resolves that
  * array's device address (cudaGetSymbolAddress) and the SM count, so make
  * the first call before any stream capture.  Every call shares the array:
  * calls that overlap on the GPU (other streams, other threads) race and
@@ -574,6 +604,17 @@ int tq_autotune_support(tq_ctx* ctx, const tq_pool* pool, int prec,
  * launches.  Synchronises.  TQ_EINVAL for a null argument or iters out of
  * range. */
 int tq_fp64_fma_rate(tq_ctx* ctx, int iters, double* lane_ops_per_s);
+
+/* The device's L2 read rate (no passage of the paper; the roofline of the
+ * kernels whose working set stays in L2, such as the pool gradients, which
+ * read H psi and psi at every support row of every generator).  A buffer
+ * of `bytes` (1 MiB to 256 MiB, a multiple of 16; keep it well inside
+ * the L2) from the context's scratch is zeroed, read once to bring it into
+ * L2, then read `reps` times (1 to 4096) by 4 CTAs of 512 threads per SM
+ * with 16-byte loads that bypass L1; the fastest of three launches gives
+ * *bytes_per_s.  Runs on the legacy default stream and synchronises.
+ * TQ_EINVAL for a null argument or a size out of range. */
+int tq_l2_read_rate(tq_ctx* ctx, long long bytes, int reps, double* bytes_per_s);
 
 /* The same batch with HOST buffers (psi, k, theta, norm2 in host memory;
  * pinned memory gives full copy speed): the batch is cut into chunks whose

@@ -105,6 +105,34 @@ def pool_support_forms(n_spatial, n_electrons, mapping):
     return out
 
 
+def mapping_relabelled(base_mapping, order):
+    """Id of the JW/BK encoding with qubit k stored at bit order[k] of the
+    basis index (a memory layout; every result is the base mapping's)."""
+    o = np.ascontiguousarray(order, dtype=np.int32)
+    out = C.c_int()
+    call("tq_mapping_relabelled", int(base_mapping), int(o.size), _ptr(o), C.byref(out))
+    return out.value
+
+
+def pool_sector_order(n_spatial, n_electrons, base_mapping, low_bits=4):
+    """Qubit order (for mapping_relabelled) that packs the pool's supports
+    into the lowest index bits."""
+    o = np.zeros(2 * n_spatial, dtype=np.int32)
+    call("tq_pool_sector_order", int(n_spatial), int(n_electrons), int(base_mapping), int(low_bits), _ptr(o))
+    return o
+
+
+def relabel_index(order):
+    """Relabelled index of every base-mapping basis index: out[b] has bit
+    order[k] set where b has bit k (a state moves by psi_new[out] = psi)."""
+    order = np.asarray(order, dtype=np.int64)
+    b = np.arange(1 << order.size, dtype=np.int64)
+    out = np.zeros_like(b)
+    for k, o in enumerate(order):
+        out |= ((b >> k) & 1) << o
+    return out
+
+
 def hf_index(n_qubits, n_electrons, mapping):
     out = C.c_longlong()
     call("tq_hf_index", n_qubits, n_electrons, mapping, C.byref(out))
@@ -525,6 +553,14 @@ def fp64_fma_rate(ctx, iters=4096):
     second (one FMA per lane each; twice that in flops)."""
     r = C.c_double()
     call("tq_fp64_fma_rate", ctx.handle, int(iters), C.byref(r))
+    return r.value
+
+
+def l2_read_rate(ctx, nbytes=32 << 20, reps=64):
+    """Measured L2 read rate of the device in bytes per second (a buffer of
+    ``nbytes`` read ``reps`` times with loads that bypass L1)."""
+    r = C.c_double()
+    call("tq_l2_read_rate", ctx.handle, int(nbytes), int(reps), C.byref(r))
     return r.value
 
 

@@ -431,6 +431,23 @@ extern "C" int tq_pool_support_forms(int n_spatial, int n_electrons, int mapping
     API_END
 }
 
+extern "C" int tq_mapping_relabelled(int base_mapping, int n_qubits, const int* order, int* mapping_out) {
+    API_BEGIN
+    TQ_REQUIRE(order && mapping_out, "null argument");
+    *mapping_out = register_relabelled(base_mapping, n_qubits, order);
+    API_END
+}
+
+extern "C" int tq_pool_sector_order(int n_spatial, int n_electrons, int base_mapping, int low_bits,
+                                    int* order_out) {
+    API_BEGIN
+    TQ_REQUIRE(order_out, "null argument");
+    TQ_REQUIRE(n_spatial >= 1 && n_spatial <= TQ_MAX_SPATIAL, "n_spatial out of range [1, 15]");
+    const auto o = pool_sector_order(n_spatial, n_electrons, base_mapping, low_bits);
+    std::copy(o.begin(), o.end(), order_out);
+    API_END
+}
+
 extern "C" int tq_hf_index(int n_qubits, int n_electrons, int mapping, long long* index) {
     API_BEGIN
     TQ_REQUIRE(index != nullptr, "index is null");

@@ -195,6 +195,7 @@ size_t partials_needed(long long D, int n_gitems, int nq, int sms) {
     n = std::max(n, (size_t)16 * sms);      // any persistent energy grid (at most 8 blocks per SM)
     n = std::max(n, (size_t)std::max(n_gitems, 0));
     n = std::max(n, (size_t)512 * 6);            // the line search's six dots per block
+    n = std::max(n, (size_t)line_support_partials(sms));   // its support pass: five per block
     n = std::max(n, (size_t)taylor5_pair_parts(nq, 1));
     return n + 8;
 }

@@ -25,6 +25,14 @@ extern "C" int tq_evolve_taylor5(tq_ctx* c, const tq_pool* p, int k, double thet
     check_space(p, psi);
     set_device(c);
     cudaStream_t s = as_stream(stream);
+    if (!p->sector && taylor5_single_ready(p->nq, psi->prec)) {
+        // one launch: update, norm and rescale in one thread-block cluster
+        launch(c, "taylor5_single", s, [&] {
+            return launch_taylor5_single(p->view, psi->prec, k, theta, nullptr, psi->data, renormalize,
+                                         renormalize ? &c->step->norm2 : nullptr, s);
+        });
+        return TQ_OK;
+    }
     const int upt = c->pair_upt[psi->prec];
     const int tiles = update_tiles(p, psi->prec, upt);
     double* part = static_cast<double*>(scratch(c, S_PART, (size_t)tiles * sizeof(double)));
@@ -124,9 +132,13 @@ AdaptBufs adapt_buffers(tq_ctx* c, const tq_ham* h, const tq_pool* p, const tq_s
     AdaptBufs b;
     b.g = static_cast<double*>(scratch(c, S_G, (size_t)p->M * sizeof(double)));
     const size_t vb = (size_t)D * sizeof(double2);
-    b.z = scratch(c, S_U1, 4 * (size_t)D * elem_bytes(psi->prec));
-    b.w1 = static_cast<double2*>(scratch(c, S_W1, vb));
-    b.w2 = static_cast<double2*>(scratch(c, S_W2, vb));
+    b.z = nullptr;
+    b.w1 = b.w2 = nullptr;
+    if (p->sector) {   // the record pass of a sector pool's line search
+        b.z = scratch(c, S_U1, 4 * (size_t)D * elem_bytes(psi->prec));
+        b.w1 = static_cast<double2*>(scratch(c, S_W1, vb));
+        b.w2 = static_cast<double2*>(scratch(c, S_W2, vb));
+    }
     b.part = prepare(c, D, p, p->nq);
     b.w0 = static_cast<double2*>(c->scratch[S_W0]);
     return b;
@@ -142,20 +154,30 @@ void enqueue_adapt_step(tq_ctx* c, const AdaptBufs& b, const tq_ham* h, const tq
     run_gradients(c, h, p, psi, b.g, b.part, s);
     launch(c, "select", s, [&] { return launch_select(b.g, p->M, eps, psi->prec, c->step, s); });
     if (std::isnan(theta) && !theta_list) {
-        if (p->sector)
+        if (p->sector) {
             launch(c, "apply_twice_sector", s, [&] { return launch_apply_twice_sector(p->view, c->step, psi->data,
                                                                                       psi->prec, b.z, s); });
-        else
-            launch(c, "apply_twice", s, [&] { return launch_apply_twice(p->view, c->step, psi->data, psi->prec, b.z, s); });
-        // H psi, H A psi and H A^2 psi from one pass with one arithmetic (w0
-        // is rewritten: the gradients that read it have run)
-        launch(c, "line_spmv_gated", s, [&] { return launch_line_spmv_gated(h->view, b.z, b.w0, b.w1, b.w2, c->step,
-                                                                             c->sm_count, s); });
-        launch(c, "line_dots", s, [&] { return launch_line_dots(b.z, b.w0, b.w1, b.w2, psi->prec, D, b.part,
-                                                                c->tickets + 2, c->step, s); });
+            // H psi, H A psi and H A^2 psi from one pass with one arithmetic
+            // (w0 is rewritten: the gradients that read it have run)
+            launch(c, "line_spmv_gated", s, [&] { return launch_line_spmv_gated(h->view, b.z, b.w0, b.w1, b.w2,
+                                                                                 c->step, c->sm_count, s); });
+            launch(c, "line_dots", s, [&] { return launch_line_dots(b.z, b.w0, b.w1, b.w2, psi->prec, D, b.part,
+                                                                    c->tickets + 2, c->step, s); });
+        } else {
+            // the rows of the chosen generator's support only
+            launch(c, "line_support", s, [&] { return launch_line_support(h->view, p->view, psi->data, c->step,
+                                                                          b.part, c->tickets + 2, c->sm_count, s); });
+        }
     }
     launch(c, "line_search", s, [&] { return launch_line_search(c->step, theta, theta_list, c->line_sc, c->line_se,
                                                                 c->tickets + 3, s); });
+    if (!p->sector && taylor5_single_ready(p->nq, psi->prec)) {
+        // the update, its norm and the rescale in one launch
+        launch(c, "taylor5_single_gated", s, [&] {
+            return launch_taylor5_single(p->view, psi->prec, 0, 0.0, c->step, psi->data, 1, &c->step->norm2, s);
+        });
+        return;
+    }
     const int upt = c->pair_upt[psi->prec];
     const int tiles = update_tiles(p, psi->prec, upt);
     if (!launch_update(c, p, 1, psi->prec, upt, psi->data, nullptr, nullptr, 0, 0.0, c->step, b.part, nullptr,

@@ -62,6 +62,11 @@ struct SupportForm {
 SupportForm support_form(const SignForm& f, uint64_t x);
 
 void check_mapping(int mapping);
+// Registers (or finds) the relabelled encoding base + order; returns its id.
+int register_relabelled(int base, int N, const int* order);
+// Qubit order whose lowest low_bits index bits are the qubits, picked one at
+// a time, that leave the fewest touched segments over the pool's supports.
+std::vector<int> pool_sector_order(int n, int ne, int base, int low_bits);
 // Sets the thread-local reason returned by tq_last_error().
 void set_last_error(const std::string& m);
 std::vector<PauliTerm> pauli_hamiltonian(int n, const double* h1, const double* g2,
@@ -219,6 +224,8 @@ int launch_taylor5_csr(int nq, int prec, const int* rowptr, const int* col, cons
                        double* norm2, int sms, cudaStream_t s);
 
 // Energy, gradients, ADAPT glue
+// CTAs (one partial pair each) of the launch launch_energy_csr makes.
+int energy_csr_grid(const HamView& h, int psi_prec, int sms);
 int launch_energy_csr(const HamView& h, const void* psi, int psi_prec, double2* w,
                       double* partials, unsigned* ticket, DevStep* step, int sms,
                       cudaStream_t s);
@@ -242,6 +249,13 @@ int launch_select(const double* g, int M, double eps, int prec, DevStep* step,
 // Line search: z holds per row the record {psi, A psi, A^2 psi, 0} in the
 // state's precision (4 float2 or 4 double2).
 int launch_apply_twice(const PoolView& p, const DevStep* step, const void* psi, int prec, void* z, cudaStream_t s);
+// The line search's matrix elements from the rows of the selected
+// generator's support only (full-space pools; the state itself, no
+// records): dots[1..5] divided by <psi|psi>, dots[0] the step's energy.
+// Needs line_support_partials(sms) partial slots.
+int launch_line_support(const HamView& h, const PoolView& p, const void* psi, DevStep* step, double* partials,
+                        unsigned* ticket, int sms, cudaStream_t s);
+int line_support_partials(int sms);
 int launch_line_dots(const void* z, const double2* w0, const double2* w1, const double2* w2, int prec, long long D,
                      double* partials, unsigned* ticket, DevStep* step, cudaStream_t s);
 // sc: sin and cos of the 4096 sample angles (launch_line_table fills it);
@@ -256,6 +270,13 @@ int launch_line_search(DevStep* step, double theta_given, const double* theta_li
 int launch_step_record(DevStep* step, double* rec, int n, cudaStream_t s);
 
 // gated variants (skip when step->converged) and layout helpers
+// Single-state update with the norm (and, if renorm, the rescale) in the
+// same launch: one thread-block cluster holds the state in registers.
+// k/theta from the arguments, or from the step record when gate is set.
+// ready: some cluster shape launches for 2^nq amplitudes in this precision.
+bool taylor5_single_ready(int nq, int prec);
+int launch_taylor5_single(const PoolView& p, int prec, int k, double theta, const DevStep* gate, void* psi,
+                          int renorm, double* norm2, cudaStream_t s);
 int launch_taylor5_pair_gated(const PoolView& p, int prec, int upt, void* psi, const DevStep* step,
                               double* partials, int sms, cudaStream_t s);
 int launch_scale_gated(void* psi, int prec, long long D, const double* norm2,

@@ -17,12 +17,15 @@
 
 namespace {
 
-// 64 KiB: the result record, the ticket, and up to 4032 CTA partial pairs.
+// 64 KiB: the result record, the ticket, and up to 4064 CTA partial pairs.
 constexpr size_t kScratchBytes = 64 * 1024;
 constexpr size_t kStepOffset = 0;
 constexpr size_t kTicketOffset = 256;
 constexpr size_t kPartialsOffset = 512;
 constexpr size_t kMaxPartialPairs = (kScratchBytes - kPartialsOffset) / (2 * sizeof(double));
+static_assert(kMaxPartialPairs == 4064, "the documented limit of CTA partials");
+static_assert(kStepOffset + sizeof(tq::DevStep) <= kTicketOffset, "the result record overlaps the ticket");
+static_assert(kTicketOffset + sizeof(unsigned) <= kPartialsOffset, "the ticket overlaps the partials");
 
 static __device__ __align__(256) unsigned char tq_energy_scratch[kScratchBytes];
 
@@ -103,7 +106,7 @@ extern "C" int tq_energy_noalloc(int n_qubits, int prec, const int* rowptr, cons
     h.col = col;
     h.val = val;
     h.diag = diag;
-    if ((size_t)energy_grid(h.D, d->sms) > kMaxPartialPairs) {
+    if ((size_t)energy_csr_grid(h, prec, d->sms) > kMaxPartialPairs) {
         tq::set_last_error("the reduction needs more CTA partials than the fixed scratch holds "
                           "(" + std::to_string(kMaxPartialPairs) + ")");
         return TQ_EINVAL;

@@ -138,6 +138,22 @@ __device__ __forceinline__ void store_nan_partial(double* slot, float) {
     if ((threadIdx.x & 31) == 0) *reinterpret_cast<float2*>(slot) = make_float2(__int_as_float(0x7fc00000), 0.f);
 }
 
+// Fixed-order float64 sum of a CTA's warp partials (complex64: (hi, lo)
+// float pairs in the 8-byte slots).
+template <typename T, int NW>
+__device__ __forceinline__ double sum_partials(const double* red) {
+    double sum = 0.0;
+    for (int w = 0; w < NW; ++w) {
+        if constexpr (sizeof(T) == 4) {
+            const float2 hl = *reinterpret_cast<const float2*>(&red[w]);
+            sum += (double)hl.x + (double)hl.y;
+        } else {
+            sum += red[w];
+        }
+    }
+    return sum;
+}
+
 // One pool generator as staged in shared memory: X-mask, the factored sign
 // form (A[r][r^x] = c0 (-1)^{parity(col & z0)} if parity(col & d_i) == t_i
 // for all i, else 0, with col = r ^ x), and the parities of
@@ -246,6 +262,93 @@ __device__ __forceinline__ void closed_pair_sign(int s_r, int s_q, const double 
     }
 }
 
+// Four amplitudes of one unit of the pair enumeration: rows r0, r0 + 1 and
+// their partners q0 = r0 ^ x, q0 ^ 1 (x > 1), or pairs (r0, r0 + 1) and
+// (r0 + 2, r0 + 3) (x == 1).  After unit_update, a0/a1 hold rows r0/r0 + 1
+// and b0/b1 rows q0/q0 ^ 1 (x > 1), or a0, b0, a1, b1 rows r0..r0 + 3.
+template <typename V>
+struct PairUnit {
+    uint32_t r0;
+    V a0, a1, b0, b1;
+};
+
+// Loads unit u (two aligned 2-element vectors).  hb: highest set bit of x.
+template <typename V>
+__device__ __forceinline__ void unit_load(const V* base, uint32_t x, int hb, uint32_t u, PairUnit<V>& w) {
+    if (hb > 0) {
+        const uint32_t r0 = insert_zero(2u * u, hb);
+        w.r0 = r0;
+        V f0, f1;
+        load2(base, r0, w.a0, w.a1);
+        load2(base, (r0 ^ x) & ~1u, f0, f1);
+        const uint32_t q0 = r0 ^ x;
+        w.b0 = (q0 & 1u) ? f1 : f0;   // psi[q0]
+        w.b1 = (q0 & 1u) ? f0 : f1;   // psi[q0 ^ 1]
+    } else {
+        const uint32_t r0 = 4u * u;
+        w.r0 = r0;
+        load2(base, r0, w.a0, w.b0);
+        load2(base, r0 + 2u, w.a1, w.b1);
+    }
+}
+
+template <typename V>
+__device__ __forceinline__ void unit_store(V* base, uint32_t x, int hb, const PairUnit<V>& w) {
+    if (hb > 0) {
+        const uint32_t q0 = w.r0 ^ x;
+        store2(base, w.r0, w.a0, w.a1);
+        if (q0 & 1u) store2(base, q0 & ~1u, w.b1, w.b0);
+        else store2(base, q0 & ~1u, w.b0, w.b1);
+    } else {
+        store2(base, w.r0, w.a0, w.b0);
+        store2(base, w.r0 + 2u, w.a1, w.b1);
+    }
+}
+
+// The five products and the running sum (Eqs. (7)-(8)) on the unit's two
+// pairs, in place; adds |psi'|^2 of its four amplitudes to tpart.
+template <typename T>
+__device__ __forceinline__ void unit_update(const OpRec<T>& op, int hb, const T (&cf)[6],
+                                            PairUnit<typename C2<T>::type>& w, T& tpart) {
+    const uint32_t r0 = w.r0;
+    if (hb > 0) {
+        // rows r0, r0+1 and partners q0 = r0^x, q0^1; their columns are
+        // r0 ^ {x, x^1, 0, 1}
+        const int bc = base_code(op, r0);
+        const int c_r0 = bc ^ ((op.dcode >> 8) & 15);    // col q0
+        const int c_r1 = bc ^ ((op.dcode >> 12) & 15);   // col q0^1
+        const int c_q0 = bc ^ (op.dcode & 15);           // col r0
+        const int c_q1 = bc ^ ((op.dcode >> 4) & 15);    // col r0+1
+        if constexpr (sizeof(T) == 8) {
+            if (op.unit) {
+                double c5, s5;
+                closed_coefs(cf, c5, s5);
+                closed_pair_sign(rec_sign(op, c_r0), rec_sign(op, c_q0), cf, c5, s5, w.a0, w.b0);
+                closed_pair_sign(rec_sign(op, c_r1), rec_sign(op, c_q1), cf, c5, s5, w.a1, w.b1);
+            } else {
+                chain_pair(rec_value(op, c_r0), rec_value(op, c_q0), cf, w.a0, w.b0);
+                chain_pair(rec_value(op, c_r1), rec_value(op, c_q1), cf, w.a1, w.b1);
+            }
+        } else {
+            chain_pair(rec_value(op, c_r0), rec_value(op, c_q0), cf, w.a0, w.b0);
+            chain_pair(rec_value(op, c_r1), rec_value(op, c_q1), cf, w.a1, w.b1);
+        }
+        tpart += w.a0.x * w.a0.x + w.a0.y * w.a0.y + w.a1.x * w.a1.x + w.a1.y * w.a1.y;
+        tpart += w.b0.x * w.b0.x + w.b0.y * w.b0.y + w.b1.x * w.b1.x + w.b1.y * w.b1.y;
+    } else {
+        // x == 1: pairs (r0, r0+1) and (r0+2, r0+3)
+        const int b0c = base_code(op, r0), b2c = base_code(op, r0 + 2u);
+        const T s_r0 = rec_value(op, b0c ^ ((op.dcode >> 4) & 15));  // col r0+1
+        const T s_q0 = rec_value(op, b0c);                           // col r0
+        const T s_r1 = rec_value(op, b2c ^ ((op.dcode >> 4) & 15));  // col r0+3
+        const T s_q1 = rec_value(op, b2c);                           // col r0+2
+        chain_pair(s_r0, s_q0, cf, w.a0, w.b0);
+        chain_pair(s_r1, s_q1, cf, w.a1, w.b1);
+        tpart += w.a0.x * w.a0.x + w.a0.y * w.a0.y + w.b0.x * w.b0.x + w.b0.y * w.b0.y;
+        tpart += w.a1.x * w.a1.x + w.a1.y * w.a1.y + w.b1.x * w.b1.x + w.b1.y * w.b1.y;
+    }
+}
+
 template <typename T, int UPT>
 __device__ __forceinline__ T pair_tile(const OpRec<T>& op, double theta,
                                        typename C2<T>::type* base, uint32_t tl, uint32_t units) {
@@ -255,76 +358,20 @@ __device__ __forceinline__ T pair_tile(const OpRec<T>& op, double theta,
     taylor_coefs_fast<T>(theta, cf);
     const uint32_t x = op.x;
     const int hb = 31 - __clz(x);
-    V e0[UPT], e1[UPT], f0[UPT], f1[UPT];
-    uint32_t r0s[UPT];
+    PairUnit<V> w[UPT];
     bool ok[UPT];
 #pragma unroll
     for (int j = 0; j < UPT; ++j) {
         const uint32_t u = (uint32_t)tl * TU + j * PAIR_BS + threadIdx.x;
         ok[j] = u < units;
-        if (!ok[j]) continue;
-        if (hb > 0) {
-            const uint32_t r0 = insert_zero(2u * u, hb);
-            r0s[j] = r0;
-            load2(base, r0, e0[j], e1[j]);
-            load2(base, (r0 ^ x) & ~1u, f0[j], f1[j]);
-        } else {
-            const uint32_t r0 = 4u * u;
-            r0s[j] = r0;
-            load2(base, r0, e0[j], f0[j]);
-            load2(base, r0 + 2u, e1[j], f1[j]);
-        }
+        if (ok[j]) unit_load(base, x, hb, u, w[j]);
     }
     T tpart = T(0);
 #pragma unroll
     for (int j = 0; j < UPT; ++j) {
         if (!ok[j]) continue;
-        const uint32_t r0 = r0s[j];
-        if (hb > 0) {
-            // rows r0, r0+1 and partners q0 = r0^x, q0^1; their columns
-            // are r0 ^ {x, x^1, 0, 1}
-            const uint32_t q0 = r0 ^ x;
-            const int bc = base_code(op, r0);
-            const int c_r0 = bc ^ ((op.dcode >> 8) & 15);    // col q0
-            const int c_r1 = bc ^ ((op.dcode >> 12) & 15);   // col q0^1
-            const int c_q0 = bc ^ (op.dcode & 15);           // col r0
-            const int c_q1 = bc ^ ((op.dcode >> 4) & 15);    // col r0+1
-            V a0 = e0[j], a1 = e1[j];
-            V b0 = (q0 & 1u) ? f1[j] : f0[j];   // psi[q0]
-            V b1 = (q0 & 1u) ? f0[j] : f1[j];   // psi[q0 ^ 1]
-            if constexpr (sizeof(T) == 8) {
-                if (op.unit) {
-                    double c5, s5;
-                    closed_coefs(cf, c5, s5);
-                    closed_pair_sign(rec_sign(op, c_r0), rec_sign(op, c_q0), cf, c5, s5, a0, b0);
-                    closed_pair_sign(rec_sign(op, c_r1), rec_sign(op, c_q1), cf, c5, s5, a1, b1);
-                } else {
-                    chain_pair(rec_value(op, c_r0), rec_value(op, c_q0), cf, a0, b0);
-                    chain_pair(rec_value(op, c_r1), rec_value(op, c_q1), cf, a1, b1);
-                }
-            } else {
-                chain_pair(rec_value(op, c_r0), rec_value(op, c_q0), cf, a0, b0);
-                chain_pair(rec_value(op, c_r1), rec_value(op, c_q1), cf, a1, b1);
-            }
-            tpart += a0.x * a0.x + a0.y * a0.y + a1.x * a1.x + a1.y * a1.y;
-            tpart += b0.x * b0.x + b0.y * b0.y + b1.x * b1.x + b1.y * b1.y;
-            store2(base, r0, a0, a1);
-            if (q0 & 1u) store2(base, q0 & ~1u, b1, b0);
-            else store2(base, q0 & ~1u, b0, b1);
-        } else {
-            // x == 1: pairs (r0, r0+1) and (r0+2, r0+3)
-            const int b0c = base_code(op, r0), b2c = base_code(op, r0 + 2u);
-            const T s_r0 = rec_value(op, b0c ^ ((op.dcode >> 4) & 15));  // col r0+1
-            const T s_q0 = rec_value(op, b0c);                           // col r0
-            const T s_r1 = rec_value(op, b2c ^ ((op.dcode >> 4) & 15));  // col r0+3
-            const T s_q1 = rec_value(op, b2c);                           // col r0+2
-            chain_pair(s_r0, s_q0, cf, e0[j], f0[j]);
-            chain_pair(s_r1, s_q1, cf, e1[j], f1[j]);
-            tpart += e0[j].x * e0[j].x + e0[j].y * e0[j].y + f0[j].x * f0[j].x + f0[j].y * f0[j].y;
-            tpart += e1[j].x * e1[j].x + e1[j].y * e1[j].y + f1[j].x * f1[j].x + f1[j].y * f1[j].y;
-            store2(base, r0, e0[j], f0[j]);
-            store2(base, r0 + 2u, e1[j], f1[j]);
-        }
+        unit_update<T>(op, hb, cf, w[j], tpart);
+        unit_store(base, x, hb, w[j]);
     }
     return tpart;
 }

@@ -23,10 +23,31 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 namespace tq {
 
 namespace {
+
+// Relabelled encodings: a base mapping (JW or BK) whose qubit k is stored at
+// bit order[k] of the basis index.  Registered once per process, never
+// removed; ids from TQ_MAPPING_FIRST_RELABELLED on.
+struct Relabelled {
+    int base;
+    int N;
+    std::vector<int> order;
+};
+std::mutex g_relabel_mutex;
+std::vector<Relabelled> g_relabelled;
+
+bool find_relabelled(int mapping, Relabelled* out) {
+    if (mapping < TQ_MAPPING_FIRST_RELABELLED) return false;
+    std::lock_guard<std::mutex> lock(g_relabel_mutex);
+    const size_t i = (size_t)(mapping - TQ_MAPPING_FIRST_RELABELLED);
+    if (i >= g_relabelled.size()) return false;
+    if (out) *out = g_relabelled[i];
+    return true;
+}
 
 struct Enc {
     int N;
@@ -40,16 +61,25 @@ int lowbit(int i) { return i & (-i); }
 Enc make_encoding(int N, int mapping) {
     Enc e;
     e.N = N;
+    Relabelled rl;
+    const bool relabel = find_relabelled(mapping, &rl);
+    if (relabel && rl.N != N)
+        throw Error(TQ_EINVAL, "relabelled mapping registered for " + std::to_string(rl.N) + " qubits, used with " +
+                                   std::to_string(N));
+    const int base = relabel ? rl.base : mapping;
     // rows of B as masks over modes
-    std::vector<uint64_t> rows(N, 0);
+    std::vector<uint64_t> base_rows(N, 0);
     for (int k = 0; k < N; ++k) {
-        if (mapping == TQ_JW) {
-            rows[k] = 1ull << k;
+        if (base == TQ_JW) {
+            base_rows[k] = 1ull << k;
         } else {
             int lo = k + 1 - lowbit(k + 1);
-            for (int i = lo; i <= k; ++i) rows[k] |= 1ull << i;
+            for (int i = lo; i <= k; ++i) base_rows[k] |= 1ull << i;
         }
     }
+    // a relabelling moves qubit k's row to bit order[k]: B' = P B
+    std::vector<uint64_t> rows(N, 0);
+    for (int k = 0; k < N; ++k) rows[relabel ? rl.order[k] : k] = base_rows[k];
     e.c.assign(N, 0);
     for (int k = 0; k < N; ++k)
         for (int j = 0; j < N; ++j)
@@ -128,7 +158,94 @@ std::vector<PauliTerm> canonicalise(std::vector<Term>& t, double rel) {
 }  // namespace
 
 void check_mapping(int mapping) {
-    if (mapping != TQ_JW && mapping != TQ_BK) throw Error(TQ_EINVAL, "mapping must be TQ_JW or TQ_BK");
+    if (mapping != TQ_JW && mapping != TQ_BK && !find_relabelled(mapping, nullptr))
+        throw Error(TQ_EINVAL, "mapping must be TQ_JW, TQ_BK or an id from tq_mapping_relabelled");
+}
+
+int register_relabelled(int base, int N, const int* order) {
+    if (base != TQ_JW && base != TQ_BK) throw Error(TQ_EINVAL, "base mapping must be TQ_JW or TQ_BK");
+    if (N < 1 || N > 2 * TQ_MAX_SPATIAL) throw Error(TQ_EINVAL, "n_qubits out of range [1, 30]");
+    if (!order) throw Error(TQ_EINVAL, "null order");
+    std::vector<int> seen(N, 0);
+    for (int k = 0; k < N; ++k) {
+        if (order[k] < 0 || order[k] >= N || seen[order[k]]) throw Error(TQ_EINVAL, "order is not a permutation of 0..n_qubits-1");
+        seen[order[k]] = 1;
+    }
+    std::lock_guard<std::mutex> lock(g_relabel_mutex);
+    for (size_t i = 0; i < g_relabelled.size(); ++i) {
+        const Relabelled& r = g_relabelled[i];
+        if (r.base == base && r.N == N && std::equal(r.order.begin(), r.order.end(), order))
+            return TQ_MAPPING_FIRST_RELABELLED + (int)i;
+    }
+    if (g_relabelled.size() >= 4096) throw Error(TQ_EINVAL, "too many relabelled mappings (4096)");
+    g_relabelled.push_back({base, N, std::vector<int>(order, order + N)});
+    return TQ_MAPPING_FIRST_RELABELLED + (int)g_relabelled.size() - 1;
+}
+
+namespace {
+// rank over GF(2) of up to three masks
+int gf2_rank(uint64_t a[3], int m) {
+    int rank = 0;
+    for (int bit = 0; bit < 64 && rank < m; ++bit) {
+        int piv = -1;
+        for (int i = rank; i < m; ++i)
+            if ((a[i] >> bit) & 1) { piv = i; break; }
+        if (piv < 0) continue;
+        std::swap(a[piv], a[rank]);
+        for (int i = 0; i < m; ++i)
+            if (i != rank && ((a[i] >> bit) & 1)) a[i] ^= a[rank];
+        ++rank;
+    }
+    return rank;
+}
+}  // namespace
+
+std::vector<int> pool_sector_order(int n, int ne, int base, int low_bits) {
+    if (base != TQ_JW && base != TQ_BK) throw Error(TQ_EINVAL, "base mapping must be TQ_JW or TQ_BK");
+    const int N = 2 * n;
+    if (low_bits < 0 || low_bits > N) throw Error(TQ_EINVAL, "low_bits out of range [0, 2 n_spatial]");
+    const auto ex = excitations(n, ne);
+    // every generator's support conditions (masks over the base qubits)
+    struct Supp { int m; uint64_t e[3]; };
+    std::vector<Supp> sup;
+    for (const auto& x : ex) {
+        const auto t = pauli_generator(x, N, base);
+        const SignForm f = factor_generator(t);
+        if (!f.ok) throw Error(TQ_ENUMERIC, "generator without a factored sign form");
+        const SupportForm sf = support_form(f, t.front().x);
+        Supp s{sf.m, {sf.e[0], sf.e[1], sf.e[2]}};
+        sup.push_back(s);
+    }
+    // greedy: the next lowest index bit takes the qubit that keeps the most
+    // support rows per touched segment of 2^(bits so far) amplitudes; a
+    // support with conditions of rank r on those bits fills 2^-r of them
+    std::vector<int> chosen;
+    uint64_t mask = 0;
+    for (int l = 0; l < low_bits; ++l) {
+        int best = -1;
+        double best_cost = 0.0;
+        for (int q = 0; q < N; ++q) {
+            if ((mask >> q) & 1) continue;
+            const uint64_t mq = mask | (1ull << q);
+            double cost = 0.0;
+            for (const auto& s : sup) {
+                uint64_t a[3] = {s.e[0] & mq, s.e[1] & mq, s.e[2] & mq};
+                cost += std::ldexp(1.0, N - s.m + gf2_rank(a, s.m));
+            }
+            if (best < 0 || cost < best_cost) {
+                best = q;
+                best_cost = cost;
+            }
+        }
+        chosen.push_back(best);
+        mask |= 1ull << best;
+    }
+    std::vector<int> order(N, -1);
+    int next = 0;
+    for (int q : chosen) order[q] = next++;
+    for (int q = 0; q < N; ++q)
+        if (order[q] < 0) order[q] = next++;
+    return order;
 }
 
 std::vector<PauliTerm> pauli_hamiltonian(int n, const double* h1, const double* g2,

@@ -663,6 +663,205 @@ k_line_dots(const typename C2<T>::type* z, const double2* w0, const double2* w1,
     }
 }
 
+// The line search's matrix elements from the chosen generator's support S
+// only.  u1 = A psi and u2 = A^2 psi vanish off S, so every element but
+// <psi|H psi> is a sum over rows of S:
+//   H01 = Re<H psi|u1>, H02 = Re<H psi|u2>, H11 = Re<u1|H u1>,
+//   H12 = Re<H u1|u2>,  H22 = Re<u2|H u2>,
+// and (H psi)_r, (H u1)_r, (H u2)_r for r in S need only those rows of H.
+// u1 and u2 are not stored: on S, u1_r = A[r][r^x] psi_{r^x} and
+// u2_r = -psi_r (A^2 = -I there), so a row's entries gather psi at the
+// column c and, when c is in S, at c ^ x.  H00 is the Rayleigh quotient the
+// energy pass of the same step computed: it only shifts the curve.
+//
+// The pi-periodic tie (psi inside S) depends on H22 = -H02 and
+// H12 = -H01.  The first holds bit for bit: (H psi)_r sums the entries with
+// columns in S and those outside in separate accumulators, (H u2)_r is the
+// first of them negated, and the second is exactly zero when psi lies in
+// S; both dots are then the same products with opposite signs, in the same
+// order, with no contraction.  The second holds through the compensated
+// float32 sums (about 48 bits) of complex64, or float64.
+//
+// One row per L lanes, rows of S in the support form's order (pivot bits
+// inserted), a grid-stride loop over them; float64 dots per row, fixed
+// block trees, the last block (ticket) sums the block partials in order.
+template <typename T>
+__device__ __forceinline__ T sup_sign(const SuppRec& s, T c0, uint32_t col) {
+    return parity32(col & s.z0) ? -c0 : c0;   // A[r][col], r = col ^ x in S
+}
+
+__device__ __forceinline__ bool in_support(const SuppRec& s, uint32_t r) {
+    int ok = 1;
+    if (s.m > 0) ok &= (parity32(r & s.e0) == (s.target & 1));
+    if (s.m > 1) ok &= (parity32(r & s.e1) == ((s.target >> 1) & 1));
+    if (s.m > 2) ok &= (parity32(r & s.e2) == ((s.target >> 2) & 1));
+    return ok != 0;
+}
+
+// Re(conj(a) b) with no contraction: the same bits for (a, b) and (-a, b)
+// up to sign.
+__device__ __forceinline__ double re_dot(double2 a, double2 b) {
+    return __dadd_rn(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y));
+}
+
+template <typename T, int L>
+__global__ void __launch_bounds__(256)
+k_line_support(HamView h, PoolView p, const typename C2<T>::type* __restrict__ psi, DevStep* step,
+               double* partials, unsigned* ticket) {
+    using V = typename C2<T>::type;
+    __shared__ double sh[4 * 8];
+    if (step->converged) return;
+    const T* __restrict__ val = static_cast<const T*>(h.val);
+    const int k = step->selected;
+    const SuppRec s = load_supp(p, k);
+    const T c0 = sizeof(T) == 4 ? (T)p.fc0f[k] : (T)p.fc0d[k];
+    const long long nrows = 1ll << (p.nq - s.m);
+    const int lane = threadIdx.x & 31, sub = lane & (L - 1);
+    constexpr int RPW = 32 / L;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    double a[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // H01, H02, H11, H12, H22 (before / <psi|psi>)
+    for (long long i0 = warp * RPW; i0 < nrows; i0 += nwarps * RPW) {
+        const long long i = i0 + lane / L;
+        const bool live = i < nrows;
+        const uint32_t r = live ? supp_row(s, (uint32_t)i) : 0u;
+        // y_S: columns in S, y_O: the others, y_1: (H u1) over columns in S
+        double sx[3], sy[3];
+        if constexpr (sizeof(T) == 4) {
+            // the two sums the tie relations rest on are compensated; the
+            // off-support part of H psi needs no exact relation (it is zero
+            // when psi lies in S) and takes plain float32 sums
+            F32x2 ax[2], ay[2];   // [0] y_S, [1] y_1
+            float ox = 0.f, oy = 0.f;
+            if (live) {
+                constexpr int U = 4;
+                const int e1 = h.rowptr[r + 1];
+                for (int e0 = h.rowptr[r] + sub; e0 < e1; e0 += U * L) {
+                    float av[U];
+                    int c[U];
+#pragma unroll
+                    for (int j = 0; j < U; ++j) {
+                        const int e = e0 + j * L;
+                        av[j] = e < e1 ? val[e] : 0.f;
+                        c[j] = e < e1 ? h.col[e] : -1;
+                    }
+                    V v[U], w[U];
+                    bool ins[U];
+#pragma unroll
+                    for (int j = 0; j < U; ++j) {
+                        ins[j] = c[j] >= 0 && in_support(s, (uint32_t)c[j]);
+                        if (c[j] >= 0) v[j] = __ldg(psi + c[j]);
+                        if (ins[j]) w[j] = __ldg(psi + ((uint32_t)c[j] ^ s.x));
+                    }
+#pragma unroll
+                    for (int j = 0; j < U; ++j) {
+                        if (c[j] < 0) continue;
+                        if (ins[j]) {
+                            ax[0].add_product(av[j], v[j].x);
+                            ay[0].add_product(av[j], v[j].y);
+                            // u1_c = A[c][c ^ x] psi_{c ^ x}; exact: |c0| = 1
+                            const float sg = sup_sign<float>(s, c0, (uint32_t)c[j] ^ s.x) * av[j];
+                            ax[1].add_product(sg, w[j].x);
+                            ay[1].add_product(sg, w[j].y);
+                        } else {
+                            ox = fmaf(av[j], v[j].x, ox);
+                            oy = fmaf(av[j], v[j].y, oy);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+#pragma unroll
+                for (int o = L / 2; o > 0; o >>= 1) {
+                    ax[q].shfl_xor(o);
+                    ay[q].shfl_xor(o);
+                }
+            }
+#pragma unroll
+            for (int o = L / 2; o > 0; o >>= 1) {
+                ox += __shfl_xor_sync(0xffffffffu, ox, o);
+                oy += __shfl_xor_sync(0xffffffffu, oy, o);
+            }
+            sx[0] = ax[0].value();
+            sy[0] = ay[0].value();
+            sx[2] = ax[1].value();
+            sy[2] = ay[1].value();
+            sx[1] = (double)ox;
+            sy[1] = (double)oy;
+        } else {
+            double ax[3] = {0.0, 0.0, 0.0}, ay[3] = {0.0, 0.0, 0.0};
+            if (live) {
+                for (int e = h.rowptr[r] + sub; e < h.rowptr[r + 1]; e += L) {
+                    const double av = val[e];
+                    const uint32_t c = (uint32_t)h.col[e];
+                    const V v = __ldg(psi + c);
+                    if (in_support(s, c)) {
+                        ax[0] = fma(av, v.x, ax[0]);
+                        ay[0] = fma(av, v.y, ay[0]);
+                        const V w = __ldg(psi + (c ^ s.x));
+                        const double sg = sup_sign<double>(s, c0, c ^ s.x) * av;
+                        ax[2] = fma(sg, w.x, ax[2]);
+                        ay[2] = fma(sg, w.y, ay[2]);
+                    } else {
+                        ax[1] = fma(av, v.x, ax[1]);
+                        ay[1] = fma(av, v.y, ay[1]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+#pragma unroll
+                for (int o = L / 2; o > 0; o >>= 1) {
+                    ax[q] += __shfl_xor_sync(0xffffffffu, ax[q], o);
+                    ay[q] += __shfl_xor_sync(0xffffffffu, ay[q], o);
+                }
+                sx[q] = ax[q];
+                sy[q] = ay[q];
+            }
+        }
+        if (sub == 0 && live) {
+            const double d = h.diag[r];
+            const V pr = psi[r], pq = psi[r ^ s.x];
+            const double sg = (double)sup_sign<T>(s, c0, r ^ s.x);
+            const double2 p0 = make_double2((double)pr.x, (double)pr.y);
+            const double2 u1 = make_double2(sg * (double)pq.x, sg * (double)pq.y);
+            const double2 u2 = make_double2(-p0.x, -p0.y);
+            const double2 x0 = make_double2(fma(d, p0.x, sx[0] + sx[1]), fma(d, p0.y, sy[0] + sy[1]));
+            const double2 x1 = make_double2(fma(d, u1.x, sx[2]), fma(d, u1.y, sy[2]));
+            const double2 x2 = make_double2(fma(d, u2.x, -sx[0]), fma(d, u2.y, -sy[0]));
+            a[0] += re_dot(x0, u1);
+            a[1] = __dadd_rn(a[1], re_dot(x0, u2));
+            a[2] += re_dot(u1, x1);
+            a[3] += re_dot(x1, u2);
+            a[4] = __dadd_rn(a[4], re_dot(x2, u2));
+        }
+    }
+    double lo[4] = {a[0], a[1], a[2], a[3]};
+    double hi[1] = {a[4]};
+    block_sum<4>(lo, sh);
+    block_sum<1>(hi, sh + 24);
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < 4; ++j) partials[5 * blockIdx.x + j] = lo[j];
+        partials[5 * blockIdx.x + 4] = hi[0];
+    }
+    if (last_block(ticket, gridDim.x)) {
+        double f[5] = {0, 0, 0, 0, 0};
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+            for (int j = 0; j < 5; ++j) f[j] = __dadd_rn(f[j], __ldcg(partials + 5 * b + j));
+        double lo2[4] = {f[0], f[1], f[2], f[3]};
+        double hi2[1] = {f[4]};
+        block_sum<4>(lo2, sh);
+        block_sum<1>(hi2, sh + 24);
+        if (threadIdx.x == 0) {
+            const double tot[5] = {lo2[0], lo2[1], lo2[2], lo2[3], hi2[0]};
+            step->dots[0] = step->energy;
+            for (int j = 0; j < 5; ++j) step->dots[j + 1] = tot[j] / step->e_den;
+            *ticket = 0u;
+        }
+    }
+}
+
 // E(theta) from sin(theta) and cos(theta).
 __device__ __forceinline__ double line_e_sc(const double* c, double s, double co) {
     const double u = 1.0 - co;
@@ -823,6 +1022,14 @@ void energy_launch(const HamView& h, const void* psi, double2* w, float2* w32, d
                                                      step);
 }
 
+// The grid energy_launch uses: resident CTAs, at most one per row item.
+template <typename T, typename VT, int L>
+int energy_csr_grid_t(const HamView& h, int sms) {
+    const long long items = (h.D + ENERGY_ROWS - 1) / ENERGY_ROWS;
+    long long grid = resident<T, VT, L>(sms);
+    return (int)(grid > items ? items : grid);
+}
+
 template <typename T, typename VT>
 int energy_dispatch(int lanes, const HamView& h, const void* psi, double2* w, float2* w32, double* partials,
                     unsigned* ticket, DevStep* step, int sms, cudaStream_t s) {
@@ -854,6 +1061,13 @@ void xell_launch(const HamView& h, const void* psi, double2* w, float2* w32, dou
 }
 
 }  // namespace
+
+int energy_csr_grid(const HamView& h, int psi_prec, int sms) {
+    // the schedule launch_energy_csr takes: 32 lanes per row, values in
+    // the state's precision
+    return psi_prec == TQ_C128 ? energy_csr_grid_t<double, double, 32>(h, sms)
+                               : energy_csr_grid_t<float, float, 32>(h, sms);
+}
 
 int launch_energy_xell(const HamView& h, const void* psi, int psi_prec, double2* w, float2* w32,
                        double* partials, unsigned* ticket, DevStep* step, cudaStream_t s, int withhold_chunk) {
@@ -964,6 +1178,49 @@ int launch_line_spmv_gated(const HamView& h, const void* z, double2* y0, double2
     return launch_line_spmv_l<8>(h, z, y0, y1, y2, gate, sms, s);
 }
 
+
+namespace {
+
+// Blocks of the support line pass: enough for the largest support (D/2
+// rows, a single excitation) at 32/L rows per warp, at most the resident
+// blocks (so that the grid-stride loop runs in one wave) and at most 4 per
+// SM (the partial slots).
+template <typename T, int L>
+int line_support_grid(long long D, int sms) {
+    static int per = 0;
+    if (per == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_line_support<T, L>, 256, 0);
+        per = per < 1 ? 1 : (per > 4 ? 4 : per);
+    }
+    const long long rows = D / 2 > 0 ? D / 2 : 1;
+    const long long warps = (rows + 32 / L - 1) / (32 / L);
+    long long grid = (warps * 32 + 255) / 256;
+    if (grid > (long long)sms * per) grid = (long long)sms * per;
+    return grid < 1 ? 1 : (int)grid;
+}
+
+template <int L>
+int launch_line_support_l(const HamView& h, const PoolView& p, const void* psi, DevStep* step, double* partials,
+                          unsigned* ticket, int sms, cudaStream_t s) {
+    const int grid = h.prec == TQ_C128 ? line_support_grid<double, L>(h.D, sms) : line_support_grid<float, L>(h.D, sms);
+    if (h.prec == TQ_C128)
+        k_line_support<double, L><<<grid, 256, 0, s>>>(h, p, static_cast<const double2*>(psi), step, partials, ticket);
+    else
+        k_line_support<float, L><<<grid, 256, 0, s>>>(h, p, static_cast<const float2*>(psi), step, partials, ticket);
+    return 1;
+}
+
+}  // namespace
+
+int line_support_partials(int sms) { return 5 * sms * 4; }
+
+int launch_line_support(const HamView& h, const PoolView& p, const void* psi, DevStep* step, double* partials,
+                        unsigned* ticket, int sms, cudaStream_t s) {
+    const long long per_row = h.D > 0 ? h.nnz / h.D : 0;
+    if (per_row >= 192) return launch_line_support_l<32>(h, p, psi, step, partials, ticket, sms, s);
+    if (per_row >= 48) return launch_line_support_l<16>(h, p, psi, step, partials, ticket, sms, s);
+    return launch_line_support_l<8>(h, p, psi, step, partials, ticket, sms, s);
+}
 
 int launch_line_dots(const void* z, const double2* w0, const double2* w1, const double2* w2, int prec, long long D,
                      double* partials, unsigned* ticket, DevStep* step, cudaStream_t s) {

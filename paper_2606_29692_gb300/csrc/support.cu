@@ -153,22 +153,6 @@ __device__ __forceinline__ T support_tile(const SupOp<T>& op, const T (&cf)[6], 
     return delta;
 }
 
-// Fixed-order float64 sum of a CTA's warp partials (complex64: (hi, lo)
-// float pairs in the 8-byte slots).
-template <typename T, int NW>
-__device__ __forceinline__ double sum_partials(const double* red) {
-    double sum = 0.0;
-    for (int w = 0; w < NW; ++w) {
-        if constexpr (sizeof(T) == 4) {
-            const float2 hl = *reinterpret_cast<const float2*>(&red[w]);
-            sum += (double)hl.x + (double)hl.y;
-        } else {
-            sum += red[w];
-        }
-    }
-    return sum;
-}
-
 // Persistent grid over (state, tile) items; tile tl of a state whose
 // generator has P support pairs covers pairs [tl P / tps, (tl + 1) P / tps)
 // (tps, the tiles per state, a power of two).

@@ -230,3 +230,96 @@ def test_support_pair_enumeration_covers_the_oracle_support(tq, n, ne, mp):
         assert np.unique(rows).size == rows.size                     # each pair once
         A = pauli.pauli_to_csr(ps).tocoo()
         assert np.array_equal(np.sort(rows), np.unique(A.row))
+
+
+def _permute_bits(v, order):
+    v = np.asarray(v, dtype=np.int64)
+    out = np.zeros_like(v)
+    for k, o in enumerate(order):
+        out |= ((v >> k) & 1) << int(o)
+    return out
+
+
+def _relabel_sum(x, z, c, order):
+    """A Pauli sum with its qubits relabelled, in the canonical (x, z) order."""
+    xp, zp = _permute_bits(x, order), _permute_bits(z, order)
+    i = np.lexsort((zp, xp))
+    return xp[i], zp[i], np.asarray(c)[i]
+
+
+@pytest.mark.parametrize("mp", [mapping.JW, mapping.BK])
+def test_relabelled_mapping_is_the_oracle_mapping_with_permuted_qubits(tq, mp):
+    """A relabelled encoding (qubit k stored at bit order[k]) gives the
+    oracle's JW/BK Pauli strings with every mask's bits moved by the order:
+    same coefficients, same pool, Hartree-Fock index moved the same way."""
+    ints, ne = synth.config1()
+    n, N = ints.n_spatial, 2 * ints.n_spatial
+    order = np.random.default_rng(11 + mp).permutation(N)
+    rl = tq.mapping_relabelled(mp, order)
+    assert rl >= 16 and tq.mapping_relabelled(mp, order) == rl        # registered once
+    x, z, c = tq.pauli_hamiltonian(ints.h, ints.g, 0.25, rl)
+    ps = pauli.qubit_hamiltonian(ints.h, ints.g, 0.25, mp)
+    rx, rz, rc = _relabel_sum(ps.x, ps.z, _oracle_matrix_coefs(ps).real, order)
+    assert np.array_equal(x.astype(np.int64), rx) and np.array_equal(z.astype(np.int64), rz)
+    assert np.abs(c - rc).max() <= 1e-14 * np.abs(c).max()
+    px, nt, pz, pc = tq.pauli_pool(n, ne, rl)
+    _, pref = pauli.pool_pauli(n, ne, mp)
+    for k, p in enumerate(pref):
+        assert int(px[k]) == int(_permute_bits(p.x[:1], order)[0])
+        rx, rz, rc = _relabel_sum(p.x, p.z, _oracle_matrix_coefs(p).real, order)
+        assert np.array_equal(pz[k, : nt[k]].astype(np.int64), rz)
+        assert np.array_equal(pc[k, : nt[k]], rc)                     # dyadic: exact
+    B = mapping.encoding_matrix(N, mp)
+    hf = mapping.encode_index(fermion.hf_occupation_index(ne), B)
+    assert tq.hf_index(N, ne, rl) == int(_permute_bits([hf], order)[0])
+    ix = tq.relabel_index(order)
+    assert np.array_equal(np.sort(ix), np.arange(1 << N))
+    # a mapping registered for 12 qubits is refused at another size
+    with pytest.raises(tq.TQError):
+        tq.hf_index(14, 6, rl)
+
+
+def test_relabelled_mapping_rejects_bad_orders(tq):
+    for base, order in [(2, list(range(8))), (0, [0, 1, 2, 2]), (1, [0, 1, 4, 2]), (0, [])]:
+        with pytest.raises(tq.TQError) as e:
+            tq.mapping_relabelled(base, order)
+        assert e.value.code == -1
+
+
+def _support_masks(f, k):
+    return [int(f["masks"][k, i]) for i in range(int(f["m"][k]))]
+
+
+def test_sector_order_first_pair_is_the_brute_force_best(tq):
+    """The greedy qubit order's two lowest bits are the pair that minimises
+    the touched 32-byte sectors of the pool's supports, counted row by row
+    from the exported support form (brute force over all pairs)."""
+    import itertools
+    n, ne, mp = 7, 6, mapping.BK
+    N = 2 * n
+    f = tq.pool_support_forms(n, ne, mp)
+    x, _, _, _ = tq.pauli_pool(n, ne, mp)
+    rows = []
+    for k in range(x.size):
+        m = int(f["m"][k])
+        r = np.arange(1 << N, dtype=np.int64)
+        keep = np.ones(r.size, dtype=bool)
+        for i, e in enumerate(_support_masks(f, k)):
+            keep &= (np.bitwise_count(r & e) & 1) == ((int(f["target"][k]) >> i) & 1)
+        rows.append(r[keep])
+        assert rows[-1].size == 1 << (N - m)
+
+    def touched(pair):
+        msk = (1 << pair[0]) | (1 << pair[1])
+        return sum(np.unique(r & ~msk).size for r in rows)
+
+    cost = {p: touched(p) for p in itertools.combinations(range(N), 2)}
+    best = min(cost.values())
+    order = tq.pool_sector_order(n, ne, mp, 2)
+    low = tuple(sorted(int(np.nonzero(order == b)[0][0]) for b in (0, 1)))
+    assert cost[low] == best
+    assert cost[low] < cost[(0, 1)]                      # better than the natural order
+    assert np.array_equal(np.sort(order), np.arange(N))
+    # the rest keep their base order
+    rest = [q for q in range(N) if q not in low]
+    assert [int(order[q]) for q in rest] == list(range(2, N))

@@ -38,6 +38,30 @@ def test_noalloc_energy_equals_energy_on_two_calls(prec):
         assert abs(out.item() - ref) <= tol, (seed, out.item(), ref)
 
 
+@pytest.mark.parametrize("prec", [tq.TQ_C128, tq.TQ_C64])
+def test_noalloc_smaller_call_after_larger_on_a_side_stream(prec):
+    """A 12-qubit call (more CTAs) then an 8-qubit one (fewer), both on a
+    non-default stream: the second call's reduction must not pick up the
+    partials the first left past its own grid in the shared array."""
+    import torch
+    ctx = tq.Context(0)
+    side = torch.cuda.Stream()
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    tol = 1e-10 if prec == tq.TQ_C128 else 1e-6
+    for (ints, ne), nq, seed in ((synth.config1(), 12, 5), (synth.config0(), 8, 6)):
+        ham = tq.build_hamiltonian(ctx, ints.h, ints.g, ints.e_const, tq.TQ_JW, prec)
+        rp, cl, vl, dg = tq.ham_csr(ham)
+        st = to_state(ctx, synth.random_state(nq, seed), nq, prec)
+        ref = tq.energy(ctx, ham, st)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(side):
+            out.fill_(float("nan"))
+            tq.energy_noalloc(nq, prec, rp, cl, vl, dg, st.tensor.data_ptr(), out.data_ptr(),
+                              stream=side.cuda_stream)
+        side.synchronize()
+        assert abs(out.item() - ref) <= tol, (nq, out.item(), ref)
+
+
 def test_noalloc_energy_rejects_bad_sizes():
     import torch
     out = torch.zeros(1, dtype=torch.float64, device="cuda")
