@@ -463,7 +463,7 @@ def run_ours(args, rank, world, local_rank):
     # pool's supports fill the lowest index bits (32-byte sectors), or BK's
     # own qubit order; every result is the same up to the index relabelling
     if args.layout == "sector":
-        order = tq.pool_sector_order(N_SPATIAL, N_ELECTRONS, MAPPING, 4)
+        order = tq.pool_sector_order(N_SPATIAL, N_ELECTRONS, MAPPING, args.layout_bits)
         mp_run = tq.mapping_relabelled(MAPPING, order)
         pool = tq.build_pool(ctx, N_SPATIAL, N_ELECTRONS, mp_run)
     else:
@@ -481,11 +481,10 @@ def run_ours(args, rank, world, local_rank):
                                         torch.as_tensor(prep_th[:, j].copy()).cuda(), dn)
     dk = torch.as_tensor(k).cuda()
     dth = torch.as_tensor(th).cuda()
-    # the CUDA context fetches 32-byte sectors on L2 misses (the update's
-    # reads are scattered over each generator's support); the schedule is
-    # the fastest of the eight on this batch (untimed, before warm-up)
+    # the CUDA context's L2 fetch granularity (32 or 64 bytes: the update's
+    # reads are runs of support rows) and the schedule are the fastest pair
+    # of the sixteen on this batch (untimed, before warm-up)
     fetch_default = ctx.l2_fetch()
-    ctx.set_l2_fetch(32)
 
     applied = [0]   # launches of the timed update on the batch (the fidelity check replays them)
 
@@ -494,18 +493,21 @@ def run_ours(args, rank, world, local_rank):
         applied[0] += 1
 
     tune = {}
-    for cand in ([args.pair_schedule] if args.pair_schedule else [1, 2, 4, 8, -1, -2, -4, -8]):
-        ctx.set_support_schedule(tq.TQ_C64, cand)
-        step()
-        ctx.trace(True)
-        for _ in range(10):
+    for fetch in (32, 64):
+        ctx.set_l2_fetch(fetch)
+        for cand in ([args.pair_schedule] if args.pair_schedule else [1, 2, 4, 8, -1, -2, -4, -8]):
+            ctx.set_support_schedule(tq.TQ_C64, cand)
             step()
-        r_ = ctx.trace_report()
-        ctx.trace(False)
-        tune[cand] = sum(v[1] for v in r_.values()) / 10
-    upt = min(tune, key=tune.get)
-    tune_ms = {str(c_): v for c_, v in tune.items()}
+            ctx.trace(True)
+            for _ in range(10):
+                step()
+            r_ = ctx.trace_report()
+            ctx.trace(False)
+            tune[(fetch, cand)] = sum(v[1] for v in r_.values()) / 10
+    best_fetch, upt = min(tune, key=tune.get)
+    tune_ms = {f"{f_}B/{c_}": v for (f_, c_), v in tune.items()}
     ctx.set_support_schedule(tq.TQ_C64, upt)
+    ctx.set_l2_fetch(best_fetch)
 
     barrier = tqd.barrier
 
@@ -658,7 +660,7 @@ def run_ours(args, rank, world, local_rank):
                                                  "into 32-byte sectors"},
                            schedule={"support_pairs_per_thread": upt,
                                                          "ms_per_launch_by_schedule": tune_ms,
-                                                         "l2_fetch_bytes": 32,
+                                                         "l2_fetch_bytes": best_fetch,
                                                          "l2_fetch_default": fetch_default}),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -958,11 +960,14 @@ def measure_fp64_single(tq, ctx, pool, k, th, reps=2000):
     kl = [int(x) for x in k[:reps]]
     tl = [float(x) for x in th[:reps]]
     n = len(kl)
+    stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
     l0 = ctx.launches()
     e0.record()
+    t0 = time.perf_counter()
     for i in range(reps):
-        tq.evolve_taylor5(ctx, pool, kl[i % n], tl[i % n], st, renormalize=True)
+        tq.evolve_taylor5(ctx, pool, kl[i % n], tl[i % n], st, renormalize=True, stream=stream)
+    host_s = time.perf_counter() - t0     # the host's issue time (the GPU runs behind it)
     e1.record()
     torch.cuda.synchronize()
     launches = (ctx.launches() - l0) / reps
@@ -977,6 +982,7 @@ def measure_fp64_single(tq, ctx, pool, k, th, reps=2000):
     return {"workload": "one 14-qubit complex128 state, evolve_taylor5 with renormalisation per call, "
                         "back-to-back calls on one stream from Python",
             "updates_per_s": 1e3 / ms, "us_per_update": ms * 1e3,
+            "host_issue_us_per_call": 1e6 * host_s / reps,
             "launches_per_update": launches, "kernel": kn,
             "kernel_us_per_update": 1e3 * sum(v[1] for v in rep.values()) / 200}
 
@@ -1419,16 +1425,20 @@ def headline_fidelity(psi, dn, idx, n_states, seed, n_apply, relabel):
         for b, v in zip(c, r):
             ref[b] = v
     fids, rels, nerr = [], [], []
-    got = psi[list(idx)].cpu().numpy()[:, relabel]
+    got = psi[list(idx)].cpu().numpy()[:, relabel].astype(np.complex128)
     norms = dn[list(idx)].cpu().numpy()
+    carry = []
     for i, b in enumerate(idx):
         o = ref[b]
         fids.append(_fid(got[i], o))
         rels.append(float(np.linalg.norm(got[i] - o) / np.linalg.norm(o)))
         nerr.append(abs(float(norms[i]) - float(np.vdot(o, o).real)) / float(np.vdot(o, o).real))
+        own = float(np.vdot(got[i], got[i]).real)
+        carry.append(abs(float(norms[i]) - own) / own)
     return {"sampled_states": len(idx), "updates_per_state": n_apply + 3,
             "min_fidelity": min(fids), "max_one_minus_fidelity": max(1.0 - f for f in fids),
-            "max_rel_l2": max(rels), "max_carried_norm_rel_err": max(nerr),
+            "max_rel_l2": max(rels), "max_norm2_rel_err_vs_oracle": max(nerr),
+            "max_carried_norm2_rel_err_vs_own_state": max(carry),
             "reference": "oracle (complex128 SciPy CSR chain of Eqs. (7)-(8)) after the same 3 preparation "
                          "and n_apply timed updates of each sampled state, no renormalisation"}
 
@@ -1659,10 +1669,12 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the request-loop measurement (0 skips it)")
     ap.add_argument("--serve-rate", type=float, default=2000.0)
-    ap.add_argument("--serve-sweep", type=str, default="2000,8000,16000,32000,64000,128000",
+    ap.add_argument("--serve-sweep", type=str, default="2000,4000,8000,12000,16000,24000,32000",
                     help="offered rates (requests/s) of the saturation sweep, comma-separated ('' skips)")
     ap.add_argument("--layout", choices=["sector", "natural"], default="sector",
                     help="states in BK's qubit order relabelled for sector fill, or in BK's own order")
+    ap.add_argument("--layout-bits", type=int, default=14,
+                    help="index bits the sector-packing qubit order fills (tq_pool_sector_order)")
     ap.add_argument("--fidelity-samples", type=int, default=64,
                     help="headline states checked against the oracle after the run (0 skips)")
     ap.add_argument("--pair-schedule", type=int, default=0,

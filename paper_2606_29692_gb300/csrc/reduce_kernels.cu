@@ -683,8 +683,12 @@ k_line_dots(const typename C2<T>::type* z, const double2* w0, const double2* w1,
 // float32 sums (about 48 bits) of complex64, or float64.
 //
 // One row per L lanes, rows of S in the support form's order (pivot bits
-// inserted), a grid-stride loop over them; float64 dots per row, fixed
-// block trees, the last block (ticket) sums the block partials in order.
+// inserted), G rows per warp at a time (32 when the support is large
+// enough to give every warp 32 rows): their sums go to shared memory and
+// each lane then finishes one row in float64, so a float64 instruction
+// serves G rows (this part issues float64 warp instructions at a small
+// fraction of the float32 rate).  Fixed block trees; the last block
+// (ticket) sums the block partials in order.
 template <typename T>
 __device__ __forceinline__ T sup_sign(const SuppRec& s, T c0, uint32_t col) {
     return parity32(col & s.z0) ? -c0 : c0;   // A[r][col], r = col ^ x in S
@@ -704,39 +708,63 @@ __device__ __forceinline__ double re_dot(double2 a, double2 b) {
     return __dadd_rn(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y));
 }
 
+// Row sums of one support row before its float64 finish: y_S (columns in
+// S) and y_1 (H u1 over columns in S) as compensated (hi, lo) pairs per
+// component, y_O (columns outside S) plain.  complex128: float64 sums.
+template <typename T> struct LineSums;
+template <> struct LineSums<float> {
+    float4 s, u;   // (S.x hi, S.x lo, S.y hi, S.y lo), the same for y_1
+    float2 o;
+};
+template <> struct LineSums<double> {
+    double2 s, u, o;
+};
+
 template <typename T, int L>
 __global__ void __launch_bounds__(256)
 k_line_support(HamView h, PoolView p, const typename C2<T>::type* __restrict__ psi, DevStep* step,
                double* partials, unsigned* ticket) {
     using V = typename C2<T>::type;
     __shared__ double sh[4 * 8];
+    // the sums of a warp's 32 rows, finished in float64 by one lane each
+    __shared__ LineSums<T> stash[8][32];
     if (step->converged) return;
     const T* __restrict__ val = static_cast<const T*>(h.val);
     const int k = step->selected;
     const SuppRec s = load_supp(p, k);
     const T c0 = sizeof(T) == 4 ? (T)p.fc0f[k] : (T)p.fc0d[k];
     const long long nrows = 1ll << (p.nq - s.m);
-    const int lane = threadIdx.x & 31, sub = lane & (L - 1);
+    const int lane = threadIdx.x & 31, sub = lane & (L - 1), wid = threadIdx.x >> 5;
     constexpr int RPW = 32 / L;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     double a[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // H01, H02, H11, H12, H22 (before / <psi|psi>)
-    for (long long i0 = warp * RPW; i0 < nrows; i0 += nwarps * RPW) {
-        const long long i = i0 + lane / L;
-        const bool live = i < nrows;
-        const uint32_t r = live ? supp_row(s, (uint32_t)i) : 0u;
-        // y_S: columns in S, y_O: the others, y_1: (H u1) over columns in S
-        double sx[3], sy[3];
-        if constexpr (sizeof(T) == 4) {
-            // the two sums the tie relations rest on are compensated; the
-            // off-support part of H psi needs no exact relation (it is zero
-            // when psi lies in S) and takes plain float32 sums
-            F32x2 ax[2], ay[2];   // [0] y_S, [1] y_1
-            float ox = 0.f, oy = 0.f;
-            if (live) {
-                constexpr int U = 4;
-                const int e1 = h.rowptr[r + 1];
-                for (int e0 = h.rowptr[r] + sub; e0 < e1; e0 += U * L) {
+    // rows per warp group: 32 (one float64 finish per lane) when the support
+    // has rows enough for every warp, fewer for small supports so that all
+    // warps get work (a power of two, at least the RPW rows of one round)
+    int G = 32;
+    while (G > RPW && (long long)G * nwarps > nrows) G >>= 1;
+    const int rounds = G / RPW;
+    for (long long g0 = warp * G; g0 < nrows; g0 += nwarps * G) {
+        // `rounds` rounds of RPW rows fill the warp's G slots
+        for (int rd = 0; rd < rounds; ++rd) {
+            const int slot = rd * RPW + lane / L;
+            const long long i = g0 + slot;
+            const bool live = i < nrows;
+            const uint32_t r = live ? supp_row(s, (uint32_t)i) : 0u;
+            LineSums<T> out;
+            if constexpr (sizeof(T) == 4) {
+                // the two sums the tie relations rest on are compensated; the
+                // off-support part of H psi needs no exact relation (it is
+                // zero when psi lies in S) and takes plain float32 sums
+                F32x2 ax[2], ay[2];   // [0] y_S, [1] y_1
+                float ox = 0.f, oy = 0.f;
+                if (live) {
+                    // U entries per lane in flight; the next U columns and
+                    // values load while this group's gathers are out
+                    constexpr int U = 4;
+                    const int e1 = h.rowptr[r + 1];
+                    int e0 = h.rowptr[r] + sub;
                     float av[U];
                     int c[U];
 #pragma unroll
@@ -745,82 +773,119 @@ k_line_support(HamView h, PoolView p, const typename C2<T>::type* __restrict__ p
                         av[j] = e < e1 ? val[e] : 0.f;
                         c[j] = e < e1 ? h.col[e] : -1;
                     }
-                    V v[U], w[U];
-                    bool ins[U];
+                    while (e0 < e1) {
+                        V v[U], w[U];
+                        bool ins[U];
 #pragma unroll
-                    for (int j = 0; j < U; ++j) {
-                        ins[j] = c[j] >= 0 && in_support(s, (uint32_t)c[j]);
-                        if (c[j] >= 0) v[j] = __ldg(psi + c[j]);
-                        if (ins[j]) w[j] = __ldg(psi + ((uint32_t)c[j] ^ s.x));
-                    }
+                        for (int j = 0; j < U; ++j) {
+                            ins[j] = c[j] >= 0 && in_support(s, (uint32_t)c[j]);
+                            if (c[j] >= 0) v[j] = __ldg(psi + c[j]);
+                            if (ins[j]) w[j] = __ldg(psi + ((uint32_t)c[j] ^ s.x));
+                        }
+                        const int en = e0 + U * L;
+                        float nav[U];
+                        int nc[U];
 #pragma unroll
-                    for (int j = 0; j < U; ++j) {
-                        if (c[j] < 0) continue;
-                        if (ins[j]) {
-                            ax[0].add_product(av[j], v[j].x);
-                            ay[0].add_product(av[j], v[j].y);
-                            // u1_c = A[c][c ^ x] psi_{c ^ x}; exact: |c0| = 1
-                            const float sg = sup_sign<float>(s, c0, (uint32_t)c[j] ^ s.x) * av[j];
-                            ax[1].add_product(sg, w[j].x);
-                            ay[1].add_product(sg, w[j].y);
-                        } else {
-                            ox = fmaf(av[j], v[j].x, ox);
-                            oy = fmaf(av[j], v[j].y, oy);
+                        for (int j = 0; j < U; ++j) {
+                            const int e = en + j * L;
+                            nav[j] = e < e1 ? val[e] : 0.f;
+                            nc[j] = e < e1 ? h.col[e] : -1;
+                        }
+#pragma unroll
+                        for (int j = 0; j < U; ++j) {
+                            if (c[j] < 0) continue;
+                            if (ins[j]) {
+                                ax[0].add_product(av[j], v[j].x);
+                                ay[0].add_product(av[j], v[j].y);
+                                // u1_c = A[c][c ^ x] psi_{c ^ x}; exact: |c0| = 1
+                                const float sg = sup_sign<float>(s, c0, (uint32_t)c[j] ^ s.x) * av[j];
+                                ax[1].add_product(sg, w[j].x);
+                                ay[1].add_product(sg, w[j].y);
+                            } else {
+                                ox = fmaf(av[j], v[j].x, ox);
+                                oy = fmaf(av[j], v[j].y, oy);
+                            }
+                        }
+                        e0 = en;
+#pragma unroll
+                        for (int j = 0; j < U; ++j) {
+                            av[j] = nav[j];
+                            c[j] = nc[j];
                         }
                     }
                 }
-            }
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
+                for (int q = 0; q < 2; ++q) {
 #pragma unroll
-                for (int o = L / 2; o > 0; o >>= 1) {
-                    ax[q].shfl_xor(o);
-                    ay[q].shfl_xor(o);
-                }
-            }
-#pragma unroll
-            for (int o = L / 2; o > 0; o >>= 1) {
-                ox += __shfl_xor_sync(0xffffffffu, ox, o);
-                oy += __shfl_xor_sync(0xffffffffu, oy, o);
-            }
-            sx[0] = ax[0].value();
-            sy[0] = ay[0].value();
-            sx[2] = ax[1].value();
-            sy[2] = ay[1].value();
-            sx[1] = (double)ox;
-            sy[1] = (double)oy;
-        } else {
-            double ax[3] = {0.0, 0.0, 0.0}, ay[3] = {0.0, 0.0, 0.0};
-            if (live) {
-                for (int e = h.rowptr[r] + sub; e < h.rowptr[r + 1]; e += L) {
-                    const double av = val[e];
-                    const uint32_t c = (uint32_t)h.col[e];
-                    const V v = __ldg(psi + c);
-                    if (in_support(s, c)) {
-                        ax[0] = fma(av, v.x, ax[0]);
-                        ay[0] = fma(av, v.y, ay[0]);
-                        const V w = __ldg(psi + (c ^ s.x));
-                        const double sg = sup_sign<double>(s, c0, c ^ s.x) * av;
-                        ax[2] = fma(sg, w.x, ax[2]);
-                        ay[2] = fma(sg, w.y, ay[2]);
-                    } else {
-                        ax[1] = fma(av, v.x, ax[1]);
-                        ay[1] = fma(av, v.y, ay[1]);
+                    for (int o = L / 2; o > 0; o >>= 1) {
+                        ax[q].shfl_xor(o);
+                        ay[q].shfl_xor(o);
                     }
                 }
-            }
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
 #pragma unroll
                 for (int o = L / 2; o > 0; o >>= 1) {
-                    ax[q] += __shfl_xor_sync(0xffffffffu, ax[q], o);
-                    ay[q] += __shfl_xor_sync(0xffffffffu, ay[q], o);
+                    ox += __shfl_xor_sync(0xffffffffu, ox, o);
+                    oy += __shfl_xor_sync(0xffffffffu, oy, o);
                 }
-                sx[q] = ax[q];
-                sy[q] = ay[q];
+                out.s = make_float4(ax[0].hi, ax[0].lo, ay[0].hi, ay[0].lo);
+                out.u = make_float4(ax[1].hi, ax[1].lo, ay[1].hi, ay[1].lo);
+                out.o = make_float2(ox, oy);
+            } else {
+                double ax[3] = {0.0, 0.0, 0.0}, ay[3] = {0.0, 0.0, 0.0};   // y_S, y_O, y_1
+                if (live) {
+                    for (int e = h.rowptr[r] + sub; e < h.rowptr[r + 1]; e += L) {
+                        const double av = val[e];
+                        const uint32_t c = (uint32_t)h.col[e];
+                        const V v = __ldg(psi + c);
+                        if (in_support(s, c)) {
+                            ax[0] = fma(av, v.x, ax[0]);
+                            ay[0] = fma(av, v.y, ay[0]);
+                            const V w = __ldg(psi + (c ^ s.x));
+                            const double sg = sup_sign<double>(s, c0, c ^ s.x) * av;
+                            ax[2] = fma(sg, w.x, ax[2]);
+                            ay[2] = fma(sg, w.y, ay[2]);
+                        } else {
+                            ax[1] = fma(av, v.x, ax[1]);
+                            ay[1] = fma(av, v.y, ay[1]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+#pragma unroll
+                    for (int o = L / 2; o > 0; o >>= 1) {
+                        ax[q] += __shfl_xor_sync(0xffffffffu, ax[q], o);
+                        ay[q] += __shfl_xor_sync(0xffffffffu, ay[q], o);
+                    }
+                }
+                out.s = make_double2(ax[0], ay[0]);
+                out.o = make_double2(ax[1], ay[1]);
+                out.u = make_double2(ax[2], ay[2]);
             }
+            if (sub == 0) stash[wid][slot] = out;
         }
-        if (sub == 0 && live) {
+        __syncwarp();
+        // lane g < G finishes row g0 + g in float64
+        const long long i = g0 + lane;
+        if (lane < G && i < nrows) {
+            const uint32_t r = supp_row(s, (uint32_t)i);
+            const LineSums<T> in = stash[wid][lane];
+            double sx[3], sy[3];   // y_S, y_O, y_1
+            if constexpr (sizeof(T) == 4) {
+                sx[0] = (double)in.s.x + (double)in.s.y;
+                sy[0] = (double)in.s.z + (double)in.s.w;
+                sx[2] = (double)in.u.x + (double)in.u.y;
+                sy[2] = (double)in.u.z + (double)in.u.w;
+                sx[1] = (double)in.o.x;
+                sy[1] = (double)in.o.y;
+            } else {
+                sx[0] = in.s.x;
+                sy[0] = in.s.y;
+                sx[1] = in.o.x;
+                sy[1] = in.o.y;
+                sx[2] = in.u.x;
+                sy[2] = in.u.y;
+            }
             const double d = h.diag[r];
             const V pr = psi[r], pq = psi[r ^ s.x];
             const double sg = (double)sup_sign<T>(s, c0, r ^ s.x);
@@ -836,6 +901,7 @@ k_line_support(HamView h, PoolView p, const typename C2<T>::type* __restrict__ p
             a[3] += re_dot(x1, u2);
             a[4] = __dadd_rn(a[4], re_dot(x2, u2));
         }
+        __syncwarp();   // the stash is refilled by the next group
     }
     double lo[4] = {a[0], a[1], a[2], a[3]};
     double hi[1] = {a[4]};

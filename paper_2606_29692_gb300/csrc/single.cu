@@ -37,10 +37,11 @@ k_taylor5_single(PoolView p, int k_imm, double th_imm, const DevStep* gate, type
                  int renorm, double* norm2_out) {
     using V = typename C2<T>::type;
     constexpr int NW = SINGLE_BS / 32;
+    static_assert(NW == 8, "the partials' shuffle tree spans eight warps");
     __shared__ double red[NW];
     __shared__ double cta_part;
     __shared__ double slots[SINGLE_MAX_CLUSTER];   // every CTA's sum, pushed here by its owner
-    __shared__ double total_sh;
+    __shared__ double scale_sh;
     cg::cluster_group cl = cg::this_cluster();
     // the same decision in every CTA of the cluster, before any barrier
     if (gate && gate->converged) return;
@@ -76,7 +77,22 @@ k_taylor5_single(PoolView p, int k_imm, double th_imm, const DevStep* gate, type
         if (ok[j]) unit_update<T>(op, hb, cf, w[j], tpart);
     store_partial(&red[threadIdx.x >> 5], tpart);
     __syncthreads();
-    if (threadIdx.x == 0) cta_part = sum_partials<T, NW>(red);
+    if (threadIdx.x < 32) {
+        // the warps' partials by a fixed shuffle tree (complex64: the
+        // (hi, lo) float pairs widened first)
+        double v = 0.0;
+        if (threadIdx.x < NW) {
+            if constexpr (sizeof(T) == 4) {
+                const float2 hl = *reinterpret_cast<const float2*>(&red[threadIdx.x]);
+                v = (double)hl.x + (double)hl.y;
+            } else {
+                v = red[threadIdx.x];
+            }
+        }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) cta_part = v;
+    }
     __syncthreads();
     // each CTA writes its sum into slot `rank` of every CTA (one thread per
     // peer); after the barrier every CTA adds its own slots in rank order,
@@ -85,23 +101,31 @@ k_taylor5_single(PoolView p, int k_imm, double th_imm, const DevStep* gate, type
     asm volatile("barrier.cluster.wait;\n" ::: "memory");
     if (threadIdx.x < nb) *cl.map_shared_rank(&slots[rank], threadIdx.x) = cta_part;
     cl.sync();   // the pushes are visible; nothing reads a peer after this
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (unsigned q = 0; q < nb; ++q) t += slots[q];
-        total_sh = t;
-        if (rank == 0 && norm2_out) *norm2_out = t;
+    if (threadIdx.x < 32) {
+        // warp 0: the slots by a fixed shuffle tree (rank order pairs up
+        // the same way in every CTA), then one thread takes the reciprocal
+        // square root (the float64 pipe issues a warp instruction every 64
+        // cycles on this part: no serial chains, no division)
+        double t = threadIdx.x < nb ? slots[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) {
+            scale_sh = renorm ? rsqrt(t) : 1.0;
+            if (rank == 0 && norm2_out) *norm2_out = t;
+        }
     }
     __syncthreads();
     if (renorm) {
-        const double sc = 1.0 / sqrt(total_sh);
+        // complex64 scales in float32 (the amplitudes' own precision)
+        const T sc = (T)scale_sh;
 #pragma unroll
         for (int j = 0; j < UPT; ++j) {
             if (!ok[j]) continue;
             V* v[4] = {&w[j].a0, &w[j].a1, &w[j].b0, &w[j].b1};
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                v[i]->x = (T)((double)v[i]->x * sc);
-                v[i]->y = (T)((double)v[i]->y * sc);
+                v[i]->x *= sc;
+                v[i]->y *= sc;
             }
         }
     }

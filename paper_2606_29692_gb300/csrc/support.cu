@@ -38,10 +38,60 @@ namespace {
 
 constexpr int SUPP_BS = 256;
 
+// Pair u -> support row r, with the generator's masks worked out once per
+// tile: a zero inserted at the representative's bit (position hp among the
+// free bits) and at each pivot (ascending), as (v & lo) | ((v & ~lo) << 1)
+// with lo the bits below the insertion (one less than the inserted bit);
+// then each pivot set to its target xor the parity of r over its condition
+// mask (every mask holds its own pivot and no other, so the parities read
+// only free bits).  An absent condition has pivot bit 0.
+struct RowExp {
+    uint32_t hb;                   // 1 << hp
+    uint32_t pb0, pb1, pb2;        // pivot bits (0: no such condition)
+    uint32_t e0, e1, e2;           // condition masks
+    uint32_t tb;                   // target bits at the pivots
+};
+
+__device__ __forceinline__ RowExp make_rowexp(const SuppRec& s, int hp) {
+    RowExp x;
+    x.hb = 1u << hp;
+    x.pb0 = s.m > 0 ? 1u << s.p0 : 0u;
+    x.pb1 = s.m > 1 ? 1u << s.p1 : 0u;
+    x.pb2 = s.m > 2 ? 1u << s.p2 : 0u;
+    x.e0 = s.e0;
+    x.e1 = s.e1;
+    x.e2 = s.e2;
+    x.tb = ((s.target & 1) ? x.pb0 : 0u) | ((s.target & 2) ? x.pb1 : 0u) | ((s.target & 4) ? x.pb2 : 0u);
+    return x;
+}
+
+__device__ __forceinline__ uint32_t ins0(uint32_t v, uint32_t bit) {
+    const uint32_t lo = bit - 1u;
+    return (v & lo) | ((v & ~lo) << 1);
+}
+
+// supp_row(s, insert_zero(u, hp)), the same row.
+__device__ __forceinline__ uint32_t expand_row(const RowExp& x, uint32_t u) {
+    uint32_t r = ins0(u, x.hb);
+    if (x.pb0) r = ins0(r, x.pb0);
+    if (x.pb1) r = ins0(r, x.pb1);
+    if (x.pb2) r = ins0(r, x.pb2);
+    uint32_t piv = 0u;
+    if (x.pb0) piv |= x.pb0 & (0u - (__popc(r & x.e0) & 1u));
+    if (x.pb1) piv |= x.pb1 & (0u - (__popc(r & x.e1) & 1u));
+    if (x.pb2) piv |= x.pb2 & (0u - (__popc(r & x.e2) & 1u));
+    return r | (piv ^ x.tb);
+}
+
+// Conditions of the support (codimension m): the pivot bits present.
+__device__ __forceinline__ int rowexp_m(const RowExp& x) { return (x.pb0 != 0u) + (x.pb1 != 0u) + (x.pb2 != 0u); }
+
+// What the update loops read of a generator: its X-mask, sign mask, row
+// expansion and leading coefficient.
 template <typename T>
 struct SupOp {
-    SuppRec s;
-    int hp;      // insert position of the pair representative's zero bit
+    uint32_t x, z0;
+    RowExp rx;
     int unit;    // every entry of A is 0 or +-1
     int c0neg;
     T c0;
@@ -50,8 +100,10 @@ struct SupOp {
 template <typename T>
 __device__ __forceinline__ SupOp<T> load_supop(const PoolView& p, int k) {
     SupOp<T> o;
-    o.s = load_supp(p, k);
-    o.hp = p.supp[k].z;
+    const SuppRec s = load_supp(p, k);
+    o.x = s.x;
+    o.z0 = s.z0;
+    o.rx = make_rowexp(s, p.supp[k].z);
     o.c0 = sizeof(T) == 4 ? (T)p.fc0f[k] : (T)p.fc0d[k];
     o.unit = fabsf(p.fc0f[k]) == 1.0f;
     o.c0neg = p.fc0f[k] < 0.0f;
@@ -128,16 +180,16 @@ __device__ __forceinline__ T support_tile(const SupOp<T>& op, const T (&cf)[6], 
             const uint32_t u = i + j * SUPP_BS;
             ok[j] = u < i1;
             if (!ok[j]) continue;
-            const uint32_t r = supp_row(op.s, insert_zero(u, op.hp));
+            const uint32_t r = expand_row(op.rx, u);
             rr[j] = r;
             a[j] = base[r];
-            b[j] = base[r ^ op.s.x];
+            b[j] = base[r ^ op.x];
         }
 #pragma unroll
         for (int j = 0; j < PPT; ++j) {
             if (!ok[j]) continue;
-            const uint32_t r = rr[j], q = r ^ op.s.x;
-            const int nr = parity32(q & op.s.z0), nq = parity32(r & op.s.z0);   // signs of A[r][q], A[q][r]
+            const uint32_t r = rr[j], q = r ^ op.x;
+            const int nr = parity32(q & op.z0), nq = parity32(r & op.z0);   // signs of A[r][q], A[q][r]
             V ar = a[j], aq = b[j];
             if (sup_pair<T>(op, nr, nq, cf, c5, s5, ar, aq)) {
                 nsq = pair_norm2(a[j], b[j], nsq);
@@ -200,7 +252,7 @@ k_taylor5_support(PoolView p, int n_states, typename C2<T>::type* psi, const int
             store_nan_partial(slot, T(0));   // the state is left untouched, its norm poisoned
         } else {
             const SupOp<T> op = load_supop<T>(p, k);
-            const int lp = p.nq - op.s.m - 1;
+            const int lp = p.nq - rowexp_m(op.rx) - 1;
             const uint32_t i0 = pair_bound(lp, tl, lt), i1 = pair_bound(lp, tl + 1, lt);
             T cf[6];
             double c5 = 0.0, s5 = 0.0, growth = 0.0;
@@ -278,7 +330,7 @@ __device__ __forceinline__ SupTile<T> sup_tile(const PoolView& p, const int* kk,
     t.i0 = t.i1 = 0;
     if (!t.bad) {
         t.op = load_supop<T>(p, k);
-        const int lp = p.nq - t.op.s.m - 1;
+        const int lp = p.nq - rowexp_m(t.op.rx) - 1;
         t.i0 = pair_bound(lp, tl, lt);
         t.i1 = pair_bound(lp, tl + 1, lt);
     }
@@ -292,10 +344,10 @@ __device__ __forceinline__ void sup_issue(const SupTile<T>& t, uint32_t pos, con
     for (int j = 0; j < PPT; ++j) {
         const uint32_t u = pos + j * SUPP_BS + threadIdx.x;
         if (u < t.i1) {
-            const uint32_t r = supp_row(t.op.s, insert_zero(u, t.op.hp));
+            const uint32_t r = expand_row(t.op.rx, u);
             rows[j * SUPP_BS + threadIdx.x] = r;
             cp_async(&stage[(2 * j) * SUPP_BS + threadIdx.x], base + r);
-            cp_async(&stage[(2 * j + 1) * SUPP_BS + threadIdx.x], base + (r ^ t.op.s.x));
+            cp_async(&stage[(2 * j + 1) * SUPP_BS + threadIdx.x], base + (r ^ t.op.x));
         }
     }
 }
@@ -314,9 +366,9 @@ __device__ __forceinline__ T sup_compute(const SupTile<T>& t, uint32_t pos, type
     for (int j = 0; j < PPT; ++j) {
         const uint32_t u = pos + j * SUPP_BS + threadIdx.x;
         if (u >= t.i1) continue;
-        const uint32_t r = rows[j * SUPP_BS + threadIdx.x], q = r ^ t.op.s.x;
+        const uint32_t r = rows[j * SUPP_BS + threadIdx.x], q = r ^ t.op.x;
         const V a = stage[(2 * j) * SUPP_BS + threadIdx.x], b = stage[(2 * j + 1) * SUPP_BS + threadIdx.x];
-        const int nr = parity32(q & t.op.s.z0), nq = parity32(r & t.op.s.z0);
+        const int nr = parity32(q & t.op.z0), nq = parity32(r & t.op.z0);
         V ar = a, aq = b;
         if (sup_pair<T>(t.op, nr, nq, cf, c5, s5, ar, aq)) {
             nsq = pair_norm2(a, b, nsq);
@@ -331,10 +383,48 @@ __device__ __forceinline__ T sup_compute(const SupTile<T>& t, uint32_t pos, type
     return delta;
 }
 
+// norm2 += the CTA's warp partials, by warp 0: a fixed-order shuffle tree
+// (complex64: TwoSum-compensated float32 over the (hi, lo) slots; complex128:
+// float64), then one float64 addition.  Keeps the float64 pipe, which
+// issues a warp instruction every 64 cycles on this part, out of the
+// per-state finish.
+template <typename T, int NW>
+__device__ __forceinline__ void warp0_finish(const double* red, double* norm2) {
+    const int lane = threadIdx.x & 31;
+    if constexpr (sizeof(T) == 4) {
+        float hi = 0.f, lo = 0.f;
+        if (lane < NW) {
+            const float2 hl = *reinterpret_cast<const float2*>(&red[lane]);
+            hi = hl.x;
+            lo = hl.y;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_down_sync(0xffffffffu, hi, o);
+            const float ol = __shfl_down_sync(0xffffffffu, lo, o);
+            float sum, err;
+            two_sum(hi, oh, sum, err);
+            hi = sum;
+            lo = lo + ol + err;
+        }
+        if (lane == 0) *norm2 = *norm2 + ((double)hi + (double)lo);
+    } else {
+        double v = lane < NW ? red[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) *norm2 = *norm2 + v;
+    }
+}
+
 // With one tile per state and norm2 set, the CTA finishes each state's
-// norm itself (norm2[b] += its warps' partials in fixed order).
+// norm itself: its warps' partials go to one of two shared buffers, one
+// barrier, then warp 0 adds them to norm2[b] (warp0_finish) while the
+// other warps start the next tile, whose partials go to the other buffer;
+// warp 0 reaches that tile's barrier only after reading this one.
+// Complex64 with one or two pairs per thread keeps five CTAs per SM (48
+// registers, no spills); the other forms take what they need.
 template <typename T, int PPT>
-__global__ void __launch_bounds__(SUPP_BS)
+__global__ void __launch_bounds__(SUPP_BS, (sizeof(T) == 4 && PPT <= 2) ? 5 : 1)
 k_taylor5_support_pipe(PoolView p, int n_states, typename C2<T>::type* psi, const int* kk, const double* th,
                        double* partials, int tiles_per_state, double* norm2) {
     using V = typename C2<T>::type;
@@ -343,7 +433,8 @@ k_taylor5_support_pipe(PoolView p, int n_states, typename C2<T>::type* psi, cons
     constexpr int NW = SUPP_BS / 32;
     constexpr int STAGE = 2 * PPT * SUPP_BS;
     uint32_t* rowbuf = reinterpret_cast<uint32_t*>(stages + 2 * STAGE);   // [2][PPT][SUPP_BS]
-    __shared__ double red[NW];
+    __shared__ double red[2][NW];
+    int rp = 0;
     const int warp = threadIdx.x >> 5;
     const bool fold = tiles_per_state == 1 && norm2 != nullptr;
     const long long D = 1ll << p.nq;
@@ -378,14 +469,14 @@ k_taylor5_support_pipe(PoolView p, int n_states, typename C2<T>::type* psi, cons
             delta += sup_compute<T, PPT>(cur, pos, psi + (long long)cur.b * D, stages + st * STAGE,
                                          rowbuf + st * PPT * SUPP_BS);
         if (tile_end) {
-            double* slot = fold ? &red[warp] : partials + (size_t)tile * NW + warp;
+            double* slot = fold ? &red[rp][warp] : partials + (size_t)tile * NW + warp;
             if (cur.bad) store_nan_partial(slot, T(0));
             else store_partial(slot, delta);
             delta = T(0);
             if (fold) {
                 __syncthreads();
-                if (threadIdx.x == 0) norm2[cur.b] = norm2[cur.b] + sum_partials<T, NW>(red);
-                __syncthreads();
+                if (warp == 0) warp0_finish<T, NW>(red[rp], norm2 + cur.b);
+                rp ^= 1;
             }
         }
         if (!more) break;
