@@ -495,18 +495,21 @@ def run_ours(args, rank, world, local_rank):
     tune = {}
     for fetch in (32, 64):
         ctx.set_l2_fetch(fetch)
-        for cand in ([args.pair_schedule] if args.pair_schedule else [1, 2, 4, 8, -1, -2, -4, -8]):
-            ctx.set_support_schedule(tq.TQ_C64, cand)
-            step()
-            ctx.trace(True)
-            for _ in range(10):
+        for occ in (0, 3, 2):
+            ctx.set_support_occupancy(tq.TQ_C64, occ)
+            for cand in ([args.pair_schedule] if args.pair_schedule else [4, -1, -2, -4, -8]):
+                ctx.set_support_schedule(tq.TQ_C64, cand)
                 step()
-            r_ = ctx.trace_report()
-            ctx.trace(False)
-            tune[(fetch, cand)] = sum(v[1] for v in r_.values()) / 10
-    best_fetch, upt = min(tune, key=tune.get)
-    tune_ms = {f"{f_}B/{c_}": v for (f_, c_), v in tune.items()}
+                ctx.trace(True)
+                for _ in range(10):
+                    step()
+                r_ = ctx.trace_report()
+                ctx.trace(False)
+                tune[(fetch, occ, cand)] = sum(v[1] for v in r_.values()) / 10
+    best_fetch, best_occ, upt = min(tune, key=tune.get)
+    tune_ms = {f"{f_}B/{o_ or 'max'}cta/{c_}": v for (f_, o_, c_), v in tune.items()}
     ctx.set_support_schedule(tq.TQ_C64, upt)
+    ctx.set_support_occupancy(tq.TQ_C64, best_occ)
     ctx.set_l2_fetch(best_fetch)
 
     barrier = tqd.barrier
@@ -661,6 +664,7 @@ def run_ours(args, rank, world, local_rank):
                            schedule={"support_pairs_per_thread": upt,
                                                          "ms_per_launch_by_schedule": tune_ms,
                                                          "l2_fetch_bytes": best_fetch,
+                                                         "ctas_per_sm": best_occ or "as many as fit",
                                                          "l2_fetch_default": fetch_default}),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
@@ -707,18 +711,21 @@ def measure_natural_layout(tq, ctx, pool, n_states, k, th, prep_k, prep_th, ms_r
     dth = torch.as_tensor(th).cuda()
     ctx.set_l2_fetch(32)
     per = {}
-    for ppt in (1, 2, 4, -1, -2):
-        ctx.set_support_schedule(tq.TQ_C64, ppt)
-        for _ in range(3):
-            tq.evolve_taylor5_batch_support(ctx, pool, psi, dk, dth, dn)
-        ctx.trace(True)
-        for _ in range(reps):
-            tq.evolve_taylor5_batch_support(ctx, pool, psi, dk, dth, dn)
-        rep = ctx.trace_report()
-        ctx.trace(False)
-        n_l, ms = rep["taylor5_support"]
-        per[ppt] = ms / n_l
+    for occ in (0, 3, 2):
+        ctx.set_support_occupancy(tq.TQ_C64, occ)
+        for ppt in (4, -1, -2, -4):
+            ctx.set_support_schedule(tq.TQ_C64, ppt)
+            for _ in range(3):
+                tq.evolve_taylor5_batch_support(ctx, pool, psi, dk, dth, dn)
+            ctx.trace(True)
+            for _ in range(reps):
+                tq.evolve_taylor5_batch_support(ctx, pool, psi, dk, dth, dn)
+            rep = ctx.trace_report()
+            ctx.trace(False)
+            n_l, ms = rep["taylor5_support"]
+            per[(occ, ppt)] = ms / n_l
     ctx.set_l2_fetch(0)
+    ctx.set_support_occupancy(tq.TQ_C64, 0)
     best = min(per, key=per.get)
     ms = per[best]
     rows = support_rows(tq, N_SPATIAL, N_ELECTRONS, MAPPING)
@@ -727,8 +734,9 @@ def measure_natural_layout(tq, ctx, pool, n_states, k, th, prep_k, prep_th, ms_r
     alg = float((16 * n_rows).sum() + 16 * n_states)
     sect = float((64 * n_sect).sum() + 16 * n_states)
     peak, _ = peaks()
-    return {"workload": "the headline batch in BK's own qubit order", "pairs_per_thread": best,
-            "ms_per_launch": ms, "ms_by_schedule": {str(p_): v for p_, v in per.items()},
+    return {"workload": "the headline batch in BK's own qubit order",
+            "ctas_per_sm": best[0] or "as many as fit", "pairs_per_thread": best[1],
+            "ms_per_launch": ms, "ms_by_schedule": {f"{o_ or 'max'}cta/{p_}": v for (o_, p_), v in per.items()},
             "updates_per_s": n_states / (ms * 1e-3),
             "algorithmic_bytes_per_launch": alg, "sector_bytes_per_launch": sect,
             "frac": alg / (ms * 1e-3) / 1e9 / peak, "sector_frac": sect / (ms * 1e-3) / 1e9 / peak,
@@ -1356,6 +1364,21 @@ def measure_trajectories(tq, ctx, n_traj):
     b.run(use_graph=False)
     split = ctx.trace_report()
     ctx.trace(False)
+    # the energy passes' algorithmic bytes: per pass the Hamiltonian in the
+    # chosen layout (XOR-ELL: block offsets, 4-byte masks, 8 float32 values
+    # per pair; CSR: offsets, columns, values) plus the float64 diagonal,
+    # psi read and w = H psi written (float32 pairs)
+    e_bytes = 0.0
+    for r_, h_ in zip(res, hams):
+        D_ = 1 << h_.n_qubits
+        if lpr == tq.TQ_SPMV_XELL:
+            nb_, np_, _, _, _ = tq.ham_xell(h_)
+            hb = 4.0 * (nb_ + 1) + np_ * (4 + 8 * 4)
+        else:
+            hb = 4.0 * (D_ + 1) + 8.0 * h_.nnz
+        e_bytes += r_["n_iter"] * (hb + D_ * (8 + 8 + 8))
+    peak, _ = peaks()
+    e_ms = split.get("batch_energy", (1, float("nan")))[1]
     return {"workload": f"{n_traj} ADAPT trajectories, qubits uniform over 10-16, JW/BK 50/50, "
                         "own integrals (seeds 1000+i), angle lists of 1-30 from N(0,0.1), eps 1e-3, "
                         "complex64 with float64 reductions",
@@ -1363,7 +1386,11 @@ def measure_trajectories(tq, ctx, n_traj):
             "iterations_per_run": iters, "iterations_per_s": iters / (ms * 1e-3),
             "converged": int(sum(r["converged"] for r in res)),
             "graph_launches_per_run": 6 * max(len(t.thetas) for t in trajs),
-            "kernel_ms_untimed_direct_run": {k: round(v[1], 3) for k, v in split.items()}}
+            "kernel_ms_untimed_direct_run": {k: round(v[1], 3) for k, v in split.items()},
+            "energy_roofline": {"layout": "XOR-ELL" if lpr == tq.TQ_SPMV_XELL else f"CSR, {lpr} lanes per row",
+                                "bytes_per_run": e_bytes, "ms": e_ms,
+                                "achieved_gbs": e_bytes / (e_ms * 1e-3) / 1e9,
+                                "frac": e_bytes / (e_ms * 1e-3) / 1e9 / peak}}
 
 
 # ------------------------------------------- precision against the oracle

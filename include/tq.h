@@ -587,6 +587,12 @@ int tq_evolve_taylor5_batch_support_host(tq_ctx* ctx, const tq_pool* pool,
  * with them staged in shared memory by asynchronous copies that run one
  * pass ahead (across states).  Defaults: 4 for TQ_C128, -1 for TQ_C64. */
 int tq_ctx_set_support_schedule(tq_ctx* ctx, int prec, int pairs_per_thread);
+/* Resident CTAs per SM of the support-only update (its persistent grid is
+ * that many CTAs per SM): 0 (the default) takes as many as fit, 1..32
+ * fewer.  Fewer concurrent states per SM can raise DRAM locality for the
+ * scattered support runs; a tuning knob with no counterpart in the paper.
+ * TQ_EINVAL for a bad precision or count. */
+int tq_ctx_set_support_occupancy(tq_ctx* ctx, int prec, int ctas_per_sm);
 /* Autotuner of that schedule, as tq_autotune_pair: times each on n_states
  * device scratch states (the update and its norm), keeps the fastest on
  * the context and returns it with its time per launch.  Synchronises. */
@@ -644,10 +650,13 @@ int tq_batch_create(tq_ctx* ctx, int n_traj, tq_ham* const* hams,
                     tq_pool* const* pools, const int* n_electrons,
                     const int* mappings, const int* lengths,
                     const double* thetas, double eps, tq_batch** out);
-/* Lanes that share one Hamiltonian row in the energy SpMV: 4, 8, 16, 32. */
+/* The energy SpMV's schedule: lanes that share one CSR row (4, 8, 16,
+ * 32), or TQ_SPMV_XELL for the XOR-ELL layout (8-row blocks, each X-mask's
+ * 8 values stored together, so a pair's gathers read one aligned run). */
 int tq_batch_set_schedule(tq_batch* b, int lanes_per_row);
-/* Autotuner: times the energy launch at each lanes-per-row value on the
- * batch's own states (reset to Hartree-Fock), keeps the fastest. */
+/* Autotuner: times the energy launch under each schedule (TQ_SPMV_XELL, 4,
+ * 8, 16, 32) on the batch's own states (reset to Hartree-Fock), keeps the
+ * fastest. */
 int tq_batch_autotune(tq_batch* b, int* lanes_per_row, double* best_ms);
 /* Reset every state to Hartree-Fock and run all iterations, enqueued on
  * `stream`.  use_graph != 0 replays one CUDA graph holding every iteration

@@ -177,6 +177,10 @@ class Context:
         (registers), or -1, -2, -4, -8 (shared-memory staging, pipelined)."""
         call("tq_ctx_set_support_schedule", self.handle, prec, int(pairs_per_thread))
 
+    def set_support_occupancy(self, prec, ctas_per_sm):
+        """Resident CTAs per SM of the support-only update (0: as many as fit)."""
+        call("tq_ctx_set_support_occupancy", self.handle, prec, int(ctas_per_sm))
+
     def set_l2_fetch(self, nbytes):
         """L2 fetch granularity of the CUDA context: 32, 64, 128, or 0 (initial)."""
         call("tq_ctx_set_l2_fetch", self.handle, int(nbytes))

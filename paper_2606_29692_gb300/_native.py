@@ -110,6 +110,7 @@ SIGNATURES = {
     "tq_ctx_set_support_schedule": [vp, i32, i32],
     "tq_autotune_support": [vp, vp, i32, i32, P(i32), P(f64)],
     "tq_fp64_fma_rate": [vp, i32, P(f64)],
+    "tq_ctx_set_support_occupancy": [vp, i32, i32],
     "tq_mapping_relabelled": [i32, i32, vp, P(i32)],
     "tq_pool_sector_order": [i32, i32, i32, i32, vp],
     "tq_l2_read_rate": [vp, i64, i32, P(f64)],

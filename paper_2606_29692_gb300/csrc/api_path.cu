@@ -340,7 +340,8 @@ extern "C" int tq_evolve_taylor5_batch_support(tq_ctx* c, const tq_pool* p, int 
     const int parts = support_parts(tps);
     double* part = static_cast<double*>(scratch(c, S_PART, (size_t)n_states * parts * sizeof(double)));
     launch(c, "taylor5_support", s, [&] {
-        return launch_taylor5_support(p->view, n_states, prec, ppt, psi, k, theta, part, tps, norm2, c->sm_count, s);
+        return launch_taylor5_support(p->view, n_states, prec, ppt, psi, k, theta, part, tps, norm2, c->sm_count, s,
+                                      c->supp_ctas[prec]);
     });
     if (norm2 && tps > 1)
         launch(c, "norm_carry", s, [&] { return launch_norm_carry(part, prec, n_states, parts, norm2, norm2, nullptr, s); });
@@ -385,7 +386,8 @@ extern "C" int tq_evolve_taylor5_batch_support_host(tq_ctx* c, const tq_pool* p,
         TQ_CUDA(cudaMemcpyAsync(dn, norm2_host, (size_t)n_states * sizeof(double), cudaMemcpyHostToDevice, s));
     double* n2 = norm2_host ? dn : nullptr;
     launch(c, "taylor5_support_host", s, [&] {
-        return launch_taylor5_support(p->view, n_states, prec, ppt, psi, dk, dth, part, tps, n2, c->sm_count, s);
+        return launch_taylor5_support(p->view, n_states, prec, ppt, psi, dk, dth, part, tps, n2, c->sm_count, s,
+                                      c->supp_ctas[prec]);
     });
     if (n2 && tps > 1)
         launch(c, "norm_carry", s, [&] { return launch_norm_carry(part, prec, n_states, parts, n2, n2, nullptr, s); });
@@ -401,6 +403,15 @@ extern "C" int tq_ctx_set_support_schedule(tq_ctx* c, int prec, int pairs_per_th
     check_prec(prec);
     TQ_REQUIRE(pair_upt_valid(std::abs(pairs_per_thread)), "pairs_per_thread must be +-1, +-2, +-4 or +-8");
     c->supp_ppt[prec] = pairs_per_thread;
+    API_END
+}
+
+extern "C" int tq_ctx_set_support_occupancy(tq_ctx* c, int prec, int ctas_per_sm) {
+    API_BEGIN
+    TQ_REQUIRE(c, "null argument");
+    check_prec(prec);
+    TQ_REQUIRE(ctas_per_sm >= 0 && ctas_per_sm <= 32, "ctas_per_sm must be in [0, 32]");
+    c->supp_ctas[prec] = ctas_per_sm;
     API_END
 }
 

@@ -13,7 +13,8 @@
 // Items of finished trajectories are skipped by a flag read on the device,
 // so the whole run (max length x six launches) is captured once into a CUDA
 // graph and replayed without any host round trip.  The SpMV of the energy
-// item has a lanes-per-row schedule (4, 8, 16, 32) chosen by an autotuner.
+// item runs over the CSR with a lanes-per-row schedule (4, 8, 16, 32) or
+// over the XOR-ELL layout, chosen by an autotuner.
 #include "dev.cuh"
 #include "host_util.h"
 #include "pair.cuh"
@@ -37,6 +38,9 @@ struct TrajDev {
     const int* rowptr;
     const int* col;
     const void* val;
+    const int* xptr;         // XOR-ELL: first pair of each 8-row block
+    const uint32_t* xmask;
+    const void* xval;        // 8 values per pair
     PoolView pool;
     void* psi;
     double2* w;              // H psi, float64 (complex128 states)
@@ -115,6 +119,136 @@ kb_energy(const TrajDev* tr, TrajState* ts, const int4* items, int n_items, doub
         for (long long r0 = w4.y; r0 < end; r0 += ENERGY_ROWS)
             energy_rows<T, VT, LPR>(d.rowptr, d.col, val, d.diag, psi, d.w, d.w32, r0,
                                     r0 + ENERGY_ROWS < end ? r0 + ENERGY_ROWS : end, num, den);
+        double v[2] = {num, den};
+        block_sum<2>(v, sh);
+        if (threadIdx.x == 0) {
+            part[2 * it] = v[0];
+            part[2 * it + 1] = v[1];
+            __threadfence();
+            last = atomicAdd(&ts[t].etick, 1u) == (unsigned)d.ecnt - 1;
+        }
+        __syncthreads();
+        if (last) {
+            double a, b;
+            block_sum_pairs(part, d.eoff, d.ecnt, sh, a, b);
+            if (threadIdx.x == 0) {
+                ts[t].e_num = a;
+                ts[t].e_den = b;
+                ts[t].energy = a / b;
+                ts[t].etick = 0u;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// The same energy item over the XOR-ELL layout: blocks of 8 rows, each
+// X-mask present in a block stored once with its 8 values, so one pair's
+// gathers read one aligned run of 8 amplitudes.  Warp w of the block takes
+// 4 consecutive row blocks (32 rows); per block, lane l serves pair slot
+// l >> 2 (of 8 pairs per round) and rows 2u, 2u + 1 (u = l & 3), whose two
+// amplitudes (8R + 2u) ^ x and its bit-0 partner are one aligned 16-byte
+// run for complex64.  Four rounds (32 pairs) are in flight per warp, and
+// the next four rounds' masks and values load behind their gathers.  The
+// slot sums are reduced in the warp and parked in shared memory; each lane
+// then finishes one of the warp's 32 rows in float64.
+template <typename T, typename VT>
+__global__ void __launch_bounds__(BT_BS)
+kbx_energy(const TrajDev* tr, TrajState* ts, const int4* items, int n_items, double* part) {
+    using V = typename C2<T>::type;
+    using VT2 = typename C2<VT>::type;
+    constexpr int K = 4;                       // rounds of 8 pairs in flight
+    __shared__ double sh[2 * (BT_BS / 32)];
+    __shared__ bool last;
+    __shared__ T stash[BT_BS / 32][32][2];      // per warp, row: (re, im) of the off-diagonal sum
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, slot = lane >> 2, u = lane & 3;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int4 w4 = items[it];
+        const int t = w4.x;
+        if (!ts[t].active) continue;                     // uniform across the block
+        const TrajDev& d = tr[t];
+        const V* __restrict__ psi = static_cast<const V*>(d.psi);
+        const VT2* __restrict__ xv = static_cast<const VT2*>(d.xval);
+        const uint32_t dmask = (uint32_t)(d.D - 1);
+        const long long r0 = w4.y, r1 = (long long)w4.y + w4.z;
+        const long long B0 = r0 / XELL_ROWS + 4 * wid;   // the warp's first block
+        double num = 0.0, den = 0.0;
+        for (int j = 0; j < 4; ++j) {
+            const long long R = B0 + j;
+            T ax = T(0), ay = T(0), bx = T(0), by = T(0);
+            if (R * XELL_ROWS < r1) {                    // warp-uniform
+                const int pb = d.xptr[R], pe = d.xptr[R + 1];
+                const uint32_t ru = (uint32_t)(R * XELL_ROWS + 2 * u);
+                uint32_t x[K];
+                VT2 a[K];
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const int p = pb + slot + 8 * k;
+                    x[k] = p < pe ? d.xmask[p] : 0u;
+                    a[k] = p < pe ? xv[(size_t)p * (XELL_ROWS / 2) + u] : VT2{};
+                }
+                for (int q = pb; q < pe; q += 8 * K) {
+                    V v0[K], v1[K];
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        const uint32_t c = (ru ^ x[k]) & dmask;
+                        v0[k] = __ldg(psi + c);
+                        v1[k] = __ldg(psi + (c ^ 1u));
+                    }
+                    const int qn = q + 8 * K;
+                    uint32_t nx[K];
+                    VT2 na[K];
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        const int p = qn + slot + 8 * k;
+                        nx[k] = p < pe ? d.xmask[p] : 0u;
+                        na[k] = p < pe ? xv[(size_t)p * (XELL_ROWS / 2) + u] : VT2{};
+                    }
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        ax = fma((T)a[k].x, v0[k].x, ax);
+                        ay = fma((T)a[k].x, v0[k].y, ay);
+                        bx = fma((T)a[k].y, v1[k].x, bx);
+                        by = fma((T)a[k].y, v1[k].y, by);
+                    }
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        x[k] = nx[k];
+                        a[k] = na[k];
+                    }
+                }
+            }
+            // the 8 slots' sums, fixed butterfly over lane bits 2..4
+#pragma unroll
+            for (int o = 4; o < 32; o <<= 1) {
+                ax += __shfl_xor_sync(0xffffffffu, ax, o);
+                ay += __shfl_xor_sync(0xffffffffu, ay, o);
+                bx += __shfl_xor_sync(0xffffffffu, bx, o);
+                by += __shfl_xor_sync(0xffffffffu, by, o);
+            }
+            if (slot == 0) {
+                stash[wid][8 * j + 2 * u][0] = ax;
+                stash[wid][8 * j + 2 * u][1] = ay;
+                stash[wid][8 * j + 2 * u + 1][0] = bx;
+                stash[wid][8 * j + 2 * u + 1][1] = by;
+            }
+        }
+        __syncwarp();
+        {
+            const long long r = B0 * XELL_ROWS + lane;
+            if (r < r1 && r < d.D) {
+                const V pv = psi[r];
+                const double prx = (double)pv.x, pry = (double)pv.y;
+                const double dg = d.diag[r];
+                const double wx = fma(dg, prx, (double)stash[wid][lane][0]);
+                const double wy = fma(dg, pry, (double)stash[wid][lane][1]);
+                if (d.w) d.w[r] = make_double2(wx, wy);
+                if (d.w32) d.w32[r] = make_float2((float)wx, (float)wy);
+                num += prx * wx + pry * wy;
+                den += prx * prx + pry * pry;
+            }
+        }
+        __syncwarp();
         double v[2] = {num, den};
         block_sum<2>(v, sh);
         if (threadIdx.x == 0) {
@@ -307,6 +441,7 @@ struct tq_batch {
     cudaGraphExec_t exec = nullptr;
     int graph_lpr = -1;
     int grid_e[4] = {1, 1, 1, 1};   // energy, per lanes-per-row 4, 8, 16, 32
+    int grid_x = 1;                 // energy over the XOR-ELL layout
     int grid_g = 1, grid_p = 1;
 };
 
@@ -329,6 +464,9 @@ T* dupload(tq_batch* b, const std::vector<T>& v) {
 template <typename T, typename VT>
 int launch_energy(tq_batch* b, cudaStream_t s) {
     switch (b->lpr) {
+        case TQ_SPMV_XELL:
+            kbx_energy<T, VT><<<b->grid_x, BT_BS, 0, s>>>(b->d_td, b->d_ts, b->eitems, b->n_e, b->epart);
+            break;
         case 4: kb_energy<T, VT, 4><<<b->grid_e[0], BT_BS, 0, s>>>(b->d_td, b->d_ts, b->eitems, b->n_e, b->epart); break;
         case 8: kb_energy<T, VT, 8><<<b->grid_e[1], BT_BS, 0, s>>>(b->d_td, b->d_ts, b->eitems, b->n_e, b->epart); break;
         case 16: kb_energy<T, VT, 16><<<b->grid_e[2], BT_BS, 0, s>>>(b->d_td, b->d_ts, b->eitems, b->n_e, b->epart); break;
@@ -345,6 +483,7 @@ void compute_grids(tq_batch* b) {
     b->grid_e[1] = std::min(b->n_e, resident_grid(kb_energy<T, VT, 8>, BT_BS, sms));
     b->grid_e[2] = std::min(b->n_e, resident_grid(kb_energy<T, VT, 16>, BT_BS, sms));
     b->grid_e[3] = std::min(b->n_e, resident_grid(kb_energy<T, VT, 32>, BT_BS, sms));
+    b->grid_x = std::min(b->n_e, resident_grid(kbx_energy<T, VT>, BT_BS, sms));
     b->grid_g = std::min(b->n_g, resident_grid(kb_grad<T>, GRAD_TPB, sms));
     b->grid_p = std::min(b->n_p, resident_grid(kb_pair<T>, PAIR_BS, sms));
 }
@@ -447,6 +586,9 @@ extern "C" int tq_batch_create(tq_ctx* c, int n_traj, tq_ham* const* hams, tq_po
             d.rowptr = h->view.rowptr;
             d.col = h->view.col;
             d.val = h->view.val;
+            d.xptr = h->view.xptr;
+            d.xmask = h->view.xmask;
+            d.xval = h->view.xval;
             d.pool = p->view;
             d.chunk = 0;
             d.nch = 0;
@@ -513,8 +655,9 @@ extern "C" int tq_batch_create(tq_ctx* c, int n_traj, tq_ham* const* hams, tq_po
 extern "C" int tq_batch_set_schedule(tq_batch* b, int lanes_per_row) {
     API_BEGIN
     TQ_REQUIRE(b != nullptr, "batch is null");
-    TQ_REQUIRE(lanes_per_row == 4 || lanes_per_row == 8 || lanes_per_row == 16 || lanes_per_row == 32,
-               "lanes_per_row must be 4, 8, 16 or 32");
+    TQ_REQUIRE(lanes_per_row == TQ_SPMV_XELL || lanes_per_row == 4 || lanes_per_row == 8 || lanes_per_row == 16 ||
+                   lanes_per_row == 32,
+               "lanes_per_row must be TQ_SPMV_XELL, 4, 8, 16 or 32");
     b->lpr = lanes_per_row;
     API_END
 }
@@ -529,7 +672,7 @@ extern "C" int tq_batch_autotune(tq_batch* b, int* lanes_per_row, double* best_m
     TQ_CUDA(cudaEventCreate(&e1));
     int best = b->lpr;
     float best_t = 1e30f;
-    for (int l : {4, 8, 16, 32}) {
+    for (int l : {(int)TQ_SPMV_XELL, 4, 8, 16, 32}) {
         b->lpr = l;
         reset(b, s);
         auto one = [&] {

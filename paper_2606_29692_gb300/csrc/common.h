@@ -214,7 +214,7 @@ int support_tiles(int nq, int n_states, int ppt, int sms);
 int support_parts(int tiles);
 int launch_taylor5_support(const PoolView& p, int n_states, int prec, int ppt, void* psi, const int* k,
                            const double* theta, double* partials, int tps, double* norm2, int sms,
-                           cudaStream_t s);
+                           cudaStream_t s, int ctas_per_sm = 0);
 int launch_scale(void* psi, int prec, long long D, const double* norm2, cudaStream_t s);
 
 // Taylor-5 for a general CSR operator.
@@ -325,6 +325,7 @@ struct tq_ctx {
     int tracing = 0;
     int pair_upt[2] = {2, 4};              // schedule per precision (C128, C64)
     int supp_ppt[2] = {4, -1};             // support-only update: pairs per thread per pass, < 0 pipelined (C128, C64)
+    int supp_ctas[2] = {0, 0};             // its resident CTAs per SM (0: as many as fit)
     int l2_fetch_default = 0;              // the CUDA context's L2 fetch granularity at creation (bytes)
     int spmv_lanes = 0;                    // energy SpMV: CSR lanes per row, or 0 for XOR-ELL (default)
     int test_flags = 0;                    // TQ_TEST_* (tests of the failure paths only)

@@ -308,7 +308,20 @@ __device__ __forceinline__ void unit_store(V* base, uint32_t x, int hb, const Pa
 // The five products and the running sum (Eqs. (7)-(8)) on the unit's two
 // pairs, in place; adds |psi'|^2 of its four amplitudes to tpart.
 template <typename T>
+__device__ __forceinline__ void unit_update(const OpRec<T>& op, int hb, const T (&cf)[6], double c5, double s5,
+                                            PairUnit<typename C2<T>::type>& w, T& tpart);
+
+template <typename T>
 __device__ __forceinline__ void unit_update(const OpRec<T>& op, int hb, const T (&cf)[6],
+                                            PairUnit<typename C2<T>::type>& w, T& tpart) {
+    double c5 = 0.0, s5 = 0.0;
+    if constexpr (sizeof(T) == 8) closed_coefs(cf, c5, s5);
+    unit_update<T>(op, hb, cf, c5, s5, w, tpart);
+}
+
+// The same with the closed-form coefficients c5, s5 given (complex128).
+template <typename T>
+__device__ __forceinline__ void unit_update(const OpRec<T>& op, int hb, const T (&cf)[6], double c5, double s5,
                                             PairUnit<typename C2<T>::type>& w, T& tpart) {
     const uint32_t r0 = w.r0;
     if (hb > 0) {
@@ -321,8 +334,6 @@ __device__ __forceinline__ void unit_update(const OpRec<T>& op, int hb, const T 
         const int c_q1 = bc ^ ((op.dcode >> 4) & 15);    // col r0+1
         if constexpr (sizeof(T) == 8) {
             if (op.unit) {
-                double c5, s5;
-                closed_coefs(cf, c5, s5);
                 closed_pair_sign(rec_sign(op, c_r0), rec_sign(op, c_q0), cf, c5, s5, w.a0, w.b0);
                 closed_pair_sign(rec_sign(op, c_r1), rec_sign(op, c_q1), cf, c5, s5, w.a1, w.b1);
             } else {

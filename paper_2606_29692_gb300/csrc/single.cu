@@ -61,8 +61,6 @@ k_taylor5_single(PoolView p, int k_imm, double th_imm, const DevStep* gate, type
     const uint32_t units = (uint32_t)((1ll << p.nq) >> 2);
     const uint32_t per = units / (uint32_t)cl.num_blocks();
     const uint32_t u0 = (uint32_t)cl.block_rank() * per;
-    T cf[6];
-    taylor_coefs_fast<T>(theta, cf);
     PairUnit<V> w[UPT];
     bool ok[UPT];
 #pragma unroll
@@ -71,10 +69,31 @@ k_taylor5_single(PoolView p, int k_imm, double th_imm, const DevStep* gate, type
         ok[j] = i < per;
         if (ok[j]) unit_load(psi, x, hb, u0 + i, w[j]);
     }
+    // the coefficients: complex64 per thread on the float32 pipe; complex128
+    // once per CTA, by thread 0 while the loads are in flight
+    T cf[6];
+    double c5 = 0.0, s5 = 0.0;
+    if constexpr (sizeof(T) == 8) {
+        __shared__ double coef_sh[8];
+        if (threadIdx.x == 0) {
+            double c[6];
+            taylor_coefs_fast<double>(theta, c);
+            closed_coefs(c, coef_sh[6], coef_sh[7]);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) coef_sh[i] = c[i];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 6; ++i) cf[i] = coef_sh[i];
+        c5 = coef_sh[6];
+        s5 = coef_sh[7];
+    } else {
+        taylor_coefs_fast<T>(theta, cf);
+    }
     T tpart = T(0);
 #pragma unroll
     for (int j = 0; j < UPT; ++j)
-        if (ok[j]) unit_update<T>(op, hb, cf, w[j], tpart);
+        if (ok[j]) unit_update<T>(op, hb, cf, c5, s5, w[j], tpart);
     store_partial(&red[threadIdx.x >> 5], tpart);
     __syncthreads();
     if (threadIdx.x < 32) {

@@ -489,7 +489,7 @@ k_taylor5_support_pipe(PoolView p, int n_states, typename C2<T>::type* psi, cons
 
 template <typename T, int PPT>
 int launch_support_pipe(const PoolView& p, int n_states, void* psi, const int* k, const double* theta,
-                        double* partials, int tps, double* norm2, int sms, cudaStream_t s) {
+                        double* partials, int tps, double* norm2, int sms, int ctas, cudaStream_t s) {
     using V = typename C2<T>::type;
     const long long total = (long long)n_states * tps;
     if (total >= (1ll << 31)) return -1;
@@ -501,7 +501,7 @@ int launch_support_pipe(const PoolView& p, int n_states, void* psi, const int* k
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_taylor5_support_pipe<T, PPT>, SUPP_BS, smem);
         per_sm = n < 1 ? 1 : n;
     }
-    long long grid = (long long)per_sm * sms;
+    long long grid = (long long)(ctas > 0 && ctas < per_sm ? ctas : per_sm) * sms;
     if (grid > total) grid = total;
     if (grid < 1) grid = 1;
     k_taylor5_support_pipe<T, PPT><<<(int)grid, SUPP_BS, smem, s>>>(p, n_states, static_cast<V*>(psi), k, theta,
@@ -511,7 +511,7 @@ int launch_support_pipe(const PoolView& p, int n_states, void* psi, const int* k
 
 template <typename T, int PPT>
 int launch_support(const PoolView& p, int n_states, void* psi, const int* k, const double* theta,
-                   double* partials, int tps, double* norm2, int sms, cudaStream_t s) {
+                   double* partials, int tps, double* norm2, int sms, int ctas, cudaStream_t s) {
     using V = typename C2<T>::type;
     const long long total = (long long)n_states * tps;
     if (total >= (1ll << 31)) return -1;
@@ -521,7 +521,7 @@ int launch_support(const PoolView& p, int n_states, void* psi, const int* k, con
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_taylor5_support<T, PPT>, SUPP_BS, 0);
         per_sm = n < 1 ? 1 : n;
     }
-    long long grid = (long long)per_sm * sms;
+    long long grid = (long long)(ctas > 0 && ctas < per_sm ? ctas : per_sm) * sms;
     if (grid > total) grid = total;
     if (grid < 1) grid = 1;
     k_taylor5_support<T, PPT><<<(int)grid, SUPP_BS, 0, s>>>(p, n_states, static_cast<V*>(psi), k, theta,
@@ -531,16 +531,16 @@ int launch_support(const PoolView& p, int n_states, void* psi, const int* k, con
 
 template <typename T>
 int dispatch_support(int ppt, const PoolView& p, int n_states, void* psi, const int* k, const double* theta,
-                     double* partials, int tps, double* norm2, int sms, cudaStream_t s) {
+                     double* partials, int tps, double* norm2, int sms, int ctas, cudaStream_t s) {
     switch (ppt) {
-        case 1: return launch_support<T, 1>(p, n_states, psi, k, theta, partials, tps, norm2, sms, s);
-        case 2: return launch_support<T, 2>(p, n_states, psi, k, theta, partials, tps, norm2, sms, s);
-        case 4: return launch_support<T, 4>(p, n_states, psi, k, theta, partials, tps, norm2, sms, s);
-        case 8: return launch_support<T, 8>(p, n_states, psi, k, theta, partials, tps, norm2, sms, s);
-        case -1: return launch_support_pipe<T, 1>(p, n_states, psi, k, theta, partials, tps, norm2, sms, s);
-        case -2: return launch_support_pipe<T, 2>(p, n_states, psi, k, theta, partials, tps, norm2, sms, s);
-        case -4: return launch_support_pipe<T, 4>(p, n_states, psi, k, theta, partials, tps, norm2, sms, s);
-        case -8: return launch_support_pipe<T, 8>(p, n_states, psi, k, theta, partials, tps, norm2, sms, s);
+        case 1: return launch_support<T, 1>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s);
+        case 2: return launch_support<T, 2>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s);
+        case 4: return launch_support<T, 4>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s);
+        case 8: return launch_support<T, 8>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s);
+        case -1: return launch_support_pipe<T, 1>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s);
+        case -2: return launch_support_pipe<T, 2>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s);
+        case -4: return launch_support_pipe<T, 4>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s);
+        case -8: return launch_support_pipe<T, 8>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s);
         default: return -1;
     }
 }
@@ -568,11 +568,11 @@ int support_parts(int tiles) { return tiles * (SUPP_BS / 32); }
 
 int launch_taylor5_support(const PoolView& p, int n_states, int prec, int ppt, void* psi, const int* k,
                            const double* theta, double* partials, int tps, double* norm2, int sms,
-                           cudaStream_t s) {
+                           cudaStream_t s, int ctas_per_sm) {
     if (tps < 1 || (tps & (tps - 1)) != 0) return -1;   // the kernels split by shifts
     if (prec == TQ_C128)
-        return dispatch_support<double>(ppt, p, n_states, psi, k, theta, partials, tps, norm2, sms, s);
-    return dispatch_support<float>(ppt, p, n_states, psi, k, theta, partials, tps, norm2, sms, s);
+        return dispatch_support<double>(ppt, p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas_per_sm, s);
+    return dispatch_support<float>(ppt, p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas_per_sm, s);
 }
 
 }  // namespace tq

@@ -73,7 +73,7 @@ def test_graph_direct_and_schedules_agree(ctx):
     b.run(use_graph=False)
     base = b.results()
     states = [b.state(t) for t in range(len(SMALL))]
-    for lpr in (4, 8, 16, 32):
+    for lpr in (tq.TQ_SPMV_XELL, 4, 8, 16, 32):
         b.set_schedule(lpr)
         b.run(use_graph=True)
         r = b.results()
@@ -82,7 +82,7 @@ def test_graph_direct_and_schedules_agree(ctx):
             assert np.abs(r[t]["energy"] - base[t]["energy"]).max(initial=0) <= 1e-12
             assert rel_l2(b.state(t), states[t]) <= 1e-13
     best, ms = b.autotune()
-    assert best in (4, 8, 16, 32) and ms > 0
+    assert best in (tq.TQ_SPMV_XELL, 4, 8, 16, 32) and ms > 0
     b.run()
     assert [x["n_iter"] for x in b.results()] == [x["n_iter"] for x in base]
 
