@@ -500,12 +500,7 @@ def run_ours(args, rank, world, local_rank):
             for cand in ([args.pair_schedule] if args.pair_schedule else [4, -1, -2, -4, -8]):
                 ctx.set_support_schedule(tq.TQ_C64, cand)
                 step()
-                ctx.trace(True)
-                for _ in range(10):
-                    step()
-                r_ = ctx.trace_report()
-                ctx.trace(False)
-                tune[(fetch, occ, cand)] = sum(v[1] for v in r_.values()) / 10
+                tune[(fetch, occ, cand)] = time_launches(step, 10)
     best_fetch, best_occ, upt = min(tune, key=tune.get)
     tune_ms = {f"{f_}B/{o_ or 'max'}cta/{c_}": v for (f_, o_, c_), v in tune.items()}
     ctx.set_support_schedule(tq.TQ_C64, upt)
@@ -529,8 +524,9 @@ def run_ours(args, rank, world, local_rank):
     clocks = ClockSampler(gpu_id)
     clocks.start()
     time.sleep(0.3)
+    # the timed region: K steps, one launch each, no per-launch events (a
+    # recorded event between launches adds a few microseconds of gap)
     launches0 = ctx.launches()
-    ctx.trace(True)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -542,13 +538,22 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = ctx.launches() - launches0
+    t_local = e0.elapsed_time(e1) / 1e3
+    t = max_over_ranks(t_local)
+    value = tqd.weak_scaling_value(S, world, args.steps, t)
+    # every step is one launch of the update kernel, so its average duration
+    # over the timed region is the region's time over K (gaps included)
+    assert launches == args.steps, (launches, args.steps)
+    sup_s = t_local / args.steps
+    # beside it, untimed: the same launches bracketed one by one by events
+    ctx.trace(True)
+    for _ in range(min(args.steps, 20)):
+        step()
     rep = ctx.trace_report()
     ctx.trace(False)
-    t = max_over_ranks(e0.elapsed_time(e1) / 1e3)
-    value = tqd.weak_scaling_value(S, world, args.steps, t)
-    ctx.set_l2_fetch(0)
     sup_n, sup_ms = rep.get("taylor5_support", (0, float("nan")))
-    sup_s = sup_ms / max(sup_n, 1) / 1e3
+    sup_traced_s = sup_ms / max(sup_n, 1) / 1e3
+    ctx.set_l2_fetch(0)
     # algorithmic bytes: each support amplitude read and written once, the
     # carried norm read and written once; the touched 32-byte sectors and
     # 128-byte lines are the floors the memory system can reach
@@ -682,16 +687,33 @@ def run_ours(args, rank, world, local_rank):
                          "full_state_roofline_updates_per_s": peak * 1e9 / (2 * D * 8),
                          "value_over_full_state_roofline": value / (peak * 1e9 / (2 * D * 8) * world),
                          "kernel_ms_per_launch": sup_s * 1e3,
+                         "kernel_ms_per_launch_note": "the timed region's CUDA-event time over its K launches "
+                                                      "(one launch per step, gaps included)",
+                         "kernel_ms_per_launch_event_bracketed": sup_traced_s * 1e3,
                          "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
                          else "fallback"},
             "e2e": e2e,
             "gpu_launches": launches,
-            "kernels": {k_: {"launches": v[0], "ms": v[1]} for k_, v in rep.items()},
+            "kernels": {"taylor5_support": {"launches": launches, "ms": t_local * 1e3}},
             "clocks": clk,
             "norms_finite": finite,
         }
         out.update(extra)
     return out
+
+
+def time_launches(fn, reps):
+    """Milliseconds per call of fn (one kernel launch each) on the current
+    stream: one CUDA-event pair around reps calls, no per-launch events."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
 
 
 def measure_natural_layout(tq, ctx, pool, n_states, k, th, prep_k, prep_th, ms_relabelled, reps=50):
@@ -717,13 +739,8 @@ def measure_natural_layout(tq, ctx, pool, n_states, k, th, prep_k, prep_th, ms_r
             ctx.set_support_schedule(tq.TQ_C64, ppt)
             for _ in range(3):
                 tq.evolve_taylor5_batch_support(ctx, pool, psi, dk, dth, dn)
-            ctx.trace(True)
-            for _ in range(reps):
-                tq.evolve_taylor5_batch_support(ctx, pool, psi, dk, dth, dn)
-            rep = ctx.trace_report()
-            ctx.trace(False)
-            n_l, ms = rep["taylor5_support"]
-            per[(occ, ppt)] = ms / n_l
+            per[(occ, ppt)] = time_launches(lambda: tq.evolve_taylor5_batch_support(ctx, pool, psi, dk, dth, dn),
+                                            reps)
     ctx.set_l2_fetch(0)
     ctx.set_support_occupancy(tq.TQ_C64, 0)
     best = min(per, key=per.get)

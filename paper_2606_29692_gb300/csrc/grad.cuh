@@ -50,6 +50,65 @@ __device__ __forceinline__ uint32_t supp_row(const SuppRec& s, uint32_t u) {
     return r;
 }
 
+// Pair u -> support row r, with the generator's masks worked out once per
+// tile: a zero inserted at the representative's bit (position hp among the
+// free bits) and at each pivot (ascending), as (v & lo) | ((v & ~lo) << 1)
+// with lo the bits below the insertion (one less than the inserted bit);
+// then each pivot set to its target xor the parity of r over its condition
+// mask (every mask holds its own pivot and no other, so the parities read
+// only free bits).  An absent condition has pivot bit 0.
+struct RowExp {
+    uint32_t hb;                   // 1 << hp
+    uint32_t pb0, pb1, pb2;        // pivot bits (0: no such condition)
+    uint32_t e0, e1, e2;           // condition masks
+    uint32_t tb;                   // target bits at the pivots
+};
+
+__device__ __forceinline__ RowExp make_rowexp(const SuppRec& s, int hp) {
+    RowExp x;
+    x.hb = 1u << hp;
+    x.pb0 = s.m > 0 ? 1u << s.p0 : 0u;
+    x.pb1 = s.m > 1 ? 1u << s.p1 : 0u;
+    x.pb2 = s.m > 2 ? 1u << s.p2 : 0u;
+    x.e0 = s.e0;
+    x.e1 = s.e1;
+    x.e2 = s.e2;
+    x.tb = ((s.target & 1) ? x.pb0 : 0u) | ((s.target & 2) ? x.pb1 : 0u) | ((s.target & 4) ? x.pb2 : 0u);
+    return x;
+}
+
+__device__ __forceinline__ uint32_t ins0(uint32_t v, uint32_t bit) {
+    const uint32_t lo = bit - 1u;
+    return (v & lo) | ((v & ~lo) << 1);
+}
+
+// supp_row(s, insert_zero(u, hp)), the same row.
+__device__ __forceinline__ uint32_t expand_row(const RowExp& x, uint32_t u) {
+    uint32_t r = ins0(u, x.hb);
+    if (x.pb0) r = ins0(r, x.pb0);
+    if (x.pb1) r = ins0(r, x.pb1);
+    if (x.pb2) r = ins0(r, x.pb2);
+    uint32_t piv = 0u;
+    if (x.pb0) piv |= x.pb0 & (0u - (__popc(r & x.e0) & 1u));
+    if (x.pb1) piv |= x.pb1 & (0u - (__popc(r & x.e1) & 1u));
+    if (x.pb2) piv |= x.pb2 & (0u - (__popc(r & x.e2) & 1u));
+    return r | (piv ^ x.tb);
+}
+
+// Support row u itself (no representative bit): u with zeros at the
+// pivots, each then set by its condition; the same row as supp_row(s, u).
+__device__ __forceinline__ uint32_t expand_support_row(const RowExp& x, uint32_t u) {
+    uint32_t r = u;
+    if (x.pb0) r = ins0(r, x.pb0);
+    if (x.pb1) r = ins0(r, x.pb1);
+    if (x.pb2) r = ins0(r, x.pb2);
+    uint32_t piv = 0u;
+    if (x.pb0) piv |= x.pb0 & (0u - (__popc(r & x.e0) & 1u));
+    if (x.pb1) piv |= x.pb1 & (0u - (__popc(r & x.e1) & 1u));
+    if (x.pb2) piv |= x.pb2 & (0u - (__popc(r & x.e2) & 1u));
+    return r | (piv ^ x.tb);
+}
+
 // Sum of one item over the block; valid in thread 0.  `sh` holds 2 * warps
 // doubles.  W is float2 (complex64: w in float32) or double2.
 template <typename T, typename W, typename V>
@@ -57,9 +116,10 @@ __device__ __forceinline__ double grad_item(const SuppRec& s, T c0, const W* __r
                                             const V* __restrict__ psi, uint32_t u0, uint32_t cnt,
                                             double* sh) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const RowExp rx = make_rowexp(s, 0);   // the representative bit is not used here
     T hi = T(0), lo = T(0);
     for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const uint32_t r = supp_row(s, u0 + i);
+        const uint32_t r = expand_support_row(rx, u0 + i);
         const uint32_t q = r ^ s.x;
         const T sg = parity32(q & s.z0) ? -c0 : c0;
         const W wr = w[r];

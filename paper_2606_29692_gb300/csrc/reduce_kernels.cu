@@ -732,6 +732,7 @@ k_line_support(HamView h, PoolView p, const typename C2<T>::type* __restrict__ p
     const T* __restrict__ val = static_cast<const T*>(h.val);
     const int k = step->selected;
     const SuppRec s = load_supp(p, k);
+    const RowExp rx = make_rowexp(s, 0);
     const T c0 = sizeof(T) == 4 ? (T)p.fc0f[k] : (T)p.fc0d[k];
     const long long nrows = 1ll << (p.nq - s.m);
     const int lane = threadIdx.x & 31, sub = lane & (L - 1), wid = threadIdx.x >> 5;
@@ -751,7 +752,7 @@ k_line_support(HamView h, PoolView p, const typename C2<T>::type* __restrict__ p
             const int slot = rd * RPW + lane / L;
             const long long i = g0 + slot;
             const bool live = i < nrows;
-            const uint32_t r = live ? supp_row(s, (uint32_t)i) : 0u;
+            const uint32_t r = live ? expand_support_row(rx, (uint32_t)i) : 0u;
             LineSums<T> out;
             if constexpr (sizeof(T) == 4) {
                 // the two sums the tie relations rest on are compensated; the
@@ -868,7 +869,7 @@ k_line_support(HamView h, PoolView p, const typename C2<T>::type* __restrict__ p
         // lane g < G finishes row g0 + g in float64
         const long long i = g0 + lane;
         if (lane < G && i < nrows) {
-            const uint32_t r = supp_row(s, (uint32_t)i);
+            const uint32_t r = expand_support_row(rx, (uint32_t)i);
             const LineSums<T> in = stash[wid][lane];
             double sx[3], sy[3];   // y_S, y_O, y_1
             if constexpr (sizeof(T) == 4) {

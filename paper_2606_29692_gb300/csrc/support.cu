@@ -38,51 +38,6 @@ namespace {
 
 constexpr int SUPP_BS = 256;
 
-// Pair u -> support row r, with the generator's masks worked out once per
-// tile: a zero inserted at the representative's bit (position hp among the
-// free bits) and at each pivot (ascending), as (v & lo) | ((v & ~lo) << 1)
-// with lo the bits below the insertion (one less than the inserted bit);
-// then each pivot set to its target xor the parity of r over its condition
-// mask (every mask holds its own pivot and no other, so the parities read
-// only free bits).  An absent condition has pivot bit 0.
-struct RowExp {
-    uint32_t hb;                   // 1 << hp
-    uint32_t pb0, pb1, pb2;        // pivot bits (0: no such condition)
-    uint32_t e0, e1, e2;           // condition masks
-    uint32_t tb;                   // target bits at the pivots
-};
-
-__device__ __forceinline__ RowExp make_rowexp(const SuppRec& s, int hp) {
-    RowExp x;
-    x.hb = 1u << hp;
-    x.pb0 = s.m > 0 ? 1u << s.p0 : 0u;
-    x.pb1 = s.m > 1 ? 1u << s.p1 : 0u;
-    x.pb2 = s.m > 2 ? 1u << s.p2 : 0u;
-    x.e0 = s.e0;
-    x.e1 = s.e1;
-    x.e2 = s.e2;
-    x.tb = ((s.target & 1) ? x.pb0 : 0u) | ((s.target & 2) ? x.pb1 : 0u) | ((s.target & 4) ? x.pb2 : 0u);
-    return x;
-}
-
-__device__ __forceinline__ uint32_t ins0(uint32_t v, uint32_t bit) {
-    const uint32_t lo = bit - 1u;
-    return (v & lo) | ((v & ~lo) << 1);
-}
-
-// supp_row(s, insert_zero(u, hp)), the same row.
-__device__ __forceinline__ uint32_t expand_row(const RowExp& x, uint32_t u) {
-    uint32_t r = ins0(u, x.hb);
-    if (x.pb0) r = ins0(r, x.pb0);
-    if (x.pb1) r = ins0(r, x.pb1);
-    if (x.pb2) r = ins0(r, x.pb2);
-    uint32_t piv = 0u;
-    if (x.pb0) piv |= x.pb0 & (0u - (__popc(r & x.e0) & 1u));
-    if (x.pb1) piv |= x.pb1 & (0u - (__popc(r & x.e1) & 1u));
-    if (x.pb2) piv |= x.pb2 & (0u - (__popc(r & x.e2) & 1u));
-    return r | (piv ^ x.tb);
-}
-
 // Conditions of the support (codimension m): the pivot bits present.
 __device__ __forceinline__ int rowexp_m(const RowExp& x) { return (x.pb0 != 0u) + (x.pb1 != 0u) + (x.pb2 != 0u); }
 
