@@ -493,9 +493,9 @@ def run_ours(args, rank, world, local_rank):
         applied[0] += 1
 
     tune = {}
-    for fetch in (32, 64):
+    for fetch in ([args.l2_fetch] if args.l2_fetch else [32, 64]):
         ctx.set_l2_fetch(fetch)
-        for occ in (0, 3, 2):
+        for occ in ([args.ctas_per_sm] if args.ctas_per_sm >= 0 else [0, 3, 2]):
             ctx.set_support_occupancy(tq.TQ_C64, occ)
             for cand in ([args.pair_schedule] if args.pair_schedule else [4, -1, -2, -4, -8]):
                 ctx.set_support_schedule(tq.TQ_C64, cand)
@@ -1715,6 +1715,10 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-sweep", type=str, default="2000,4000,8000,12000,16000,24000,32000",
                     help="offered rates (requests/s) of the saturation sweep, comma-separated ('' skips)")
+    ap.add_argument("--l2-fetch", type=int, default=0, choices=[0, 32, 64, 128],
+                    help="L2 fetch granularity of the headline (0 = tuned)")
+    ap.add_argument("--ctas-per-sm", type=int, default=-1,
+                    help="resident CTAs per SM of the headline update (-1 = tuned, 0 = as many as fit)")
     ap.add_argument("--layout", choices=["sector", "natural"], default="sector",
                     help="states in BK's qubit order relabelled for sector fill, or in BK's own order")
     ap.add_argument("--layout-bits", type=int, default=14,
