@@ -665,30 +665,26 @@ k_line_dots(const typename C2<T>::type* z, const double2* w0, const double2* w1,
 
 // The line search's matrix elements from the chosen generator's support S
 // only.  u1 = A psi and u2 = A^2 psi vanish off S, so every element but
-// <psi|H psi> is a sum over rows of S:
-//   H01 = Re<H psi|u1>, H02 = Re<H psi|u2>, H11 = Re<u1|H u1>,
-//   H12 = Re<H u1|u2>,  H22 = Re<u2|H u2>,
-// and (H psi)_r, (H u1)_r, (H u2)_r for r in S need only those rows of H.
-// u1 and u2 are not stored: on S, u1_r = A[r][r^x] psi_{r^x} and
-// u2_r = -psi_r (A^2 = -I there), so a row's entries gather psi at the
-// column c and, when c is in S, at c ^ x.  H00 is the Rayleigh quotient the
-// energy pass of the same step computed: it only shifts the curve.
+// <psi|H psi> is a sum over rows of S, and on S, u1_r = A[r][r^x] psi_{r^x}
+// and u2_r = -psi_r (A^2 = -I there).  Per row r of S the pass keeps three
+// sums over the row's entries: y_S over columns in S (H psi_S, psi_S the
+// part of psi on S), y_O over the rest, and y_1 (H u1, columns in S).  With
+// x0 = (H psi)_r = y_S + y_O + d psi_r and xS = (H psi_S)_r = y_S + d psi_r:
+//   H01 = Re<H psi|u1> = sum re(x0, u1)     H02 = Re<H psi|u2> = -sum re(x0, psi)
+//   H11 = Re<u1|H u1>  = sum re(u1, y_1 + d u1)
+//   H12 = Re<H u1|u2>  = -Re<u1|H psi_S> = -sum re(xS, u1)   (H = H^+)
+//   H22 = Re<u2|H u2>  = sum re(xS, psi)
+// H00 is the Rayleigh quotient the energy pass of the same step computed:
+// it only shifts the curve.
 //
-// The pi-periodic tie (psi inside S) depends on H22 = -H02 and
-// H12 = -H01.  The first holds bit for bit: (H psi)_r sums the entries with
-// columns in S and those outside in separate accumulators, (H u2)_r is the
-// first of them negated, and the second is exactly zero when psi lies in
-// S; both dots are then the same products with opposite signs, in the same
-// order, with no contraction.  The second holds through the compensated
-// float32 sums (about 48 bits) of complex64, or float64.
+// When psi lies in S the curve along exp(theta A) psi is pi-periodic and
+// its two minima tie, through H12 = -H01 and H22 = -H02.  Written this way
+// both hold bit for bit in any precision: y_O is then exactly zero, so x0
+// and xS are the same bits, and each pair of elements sums the same
+// products with opposite signs in the same order, with no contraction.  No
+// element needs more than the state's own precision, so the sums are plain
+// float32 (complex64) or float64 (complex128).
 //
-// One row per L lanes, rows of S in the support form's order (pivot bits
-// inserted), G rows per warp at a time (32 when the support is large
-// enough to give every warp 32 rows): their sums go to shared memory and
-// each lane then finishes one row in float64, so a float64 instruction
-// serves G rows (this part issues float64 warp instructions at a small
-// fraction of the float32 rate).  Fixed block trees; the last block
-// (ticket) sums the block partials in order.
 template <typename T>
 __device__ __forceinline__ T sup_sign(const SuppRec& s, T c0, uint32_t col) {
     return parity32(col & s.z0) ? -c0 : c0;   // A[r][col], r = col ^ x in S
@@ -711,13 +707,8 @@ __device__ __forceinline__ double re_dot(double2 a, double2 b) {
 // Row sums of one support row before its float64 finish: y_S (columns in
 // S) and y_1 (H u1 over columns in S) as compensated (hi, lo) pairs per
 // component, y_O (columns outside S) plain.  complex128: float64 sums.
-template <typename T> struct LineSums;
-template <> struct LineSums<float> {
-    float4 s, u;   // (S.x hi, S.x lo, S.y hi, S.y lo), the same for y_1
-    float2 o;
-};
-template <> struct LineSums<double> {
-    double2 s, u, o;
+template <typename T> struct LineSums {
+    typename C2<T>::type s, o, u;   // y_S, y_O, y_1
 };
 
 template <typename T, int L>
@@ -755,11 +746,7 @@ k_line_support(HamView h, PoolView p, const typename C2<T>::type* __restrict__ p
             const uint32_t r = live ? expand_support_row(rx, (uint32_t)i) : 0u;
             LineSums<T> out;
             if constexpr (sizeof(T) == 4) {
-                // the two sums the tie relations rest on are compensated; the
-                // off-support part of H psi needs no exact relation (it is
-                // zero when psi lies in S) and takes plain float32 sums
-                F32x2 ax[2], ay[2];   // [0] y_S, [1] y_1
-                float ox = 0.f, oy = 0.f;
+                float2 yS = make_float2(0.f, 0.f), yO = yS, y1 = yS;
                 if (live) {
                     // U entries per lane in flight; the next U columns and
                     // values load while this group's gathers are out
@@ -780,8 +767,8 @@ k_line_support(HamView h, PoolView p, const typename C2<T>::type* __restrict__ p
 #pragma unroll
                         for (int j = 0; j < U; ++j) {
                             ins[j] = c[j] >= 0 && in_support(s, (uint32_t)c[j]);
-                            if (c[j] >= 0) v[j] = __ldg(psi + c[j]);
-                            if (ins[j]) w[j] = __ldg(psi + ((uint32_t)c[j] ^ s.x));
+                            v[j] = c[j] >= 0 ? __ldg(psi + c[j]) : V{};
+                            w[j] = ins[j] ? __ldg(psi + ((uint32_t)c[j] ^ s.x)) : V{};
                         }
                         const int en = e0 + U * L;
                         float nav[U];
@@ -794,18 +781,13 @@ k_line_support(HamView h, PoolView p, const typename C2<T>::type* __restrict__ p
                         }
 #pragma unroll
                         for (int j = 0; j < U; ++j) {
-                            if (c[j] < 0) continue;
-                            if (ins[j]) {
-                                ax[0].add_product(av[j], v[j].x);
-                                ay[0].add_product(av[j], v[j].y);
-                                // u1_c = A[c][c ^ x] psi_{c ^ x}; exact: |c0| = 1
-                                const float sg = sup_sign<float>(s, c0, (uint32_t)c[j] ^ s.x) * av[j];
-                                ax[1].add_product(sg, w[j].x);
-                                ay[1].add_product(sg, w[j].y);
-                            } else {
-                                ox = fmaf(av[j], v[j].x, ox);
-                                oy = fmaf(av[j], v[j].y, oy);
-                            }
+                            // an entry adds to y_S or to y_O (the other gets an
+                            // exact zero); u1_c = A[c][c ^ x] psi_{c ^ x}
+                            const float aS = ins[j] ? av[j] : 0.f, aO = ins[j] ? 0.f : av[j];
+                            const float a1 = ins[j] ? sup_sign<float>(s, c0, (uint32_t)c[j] ^ s.x) * av[j] : 0.f;
+                            yS = __ffma2_rn(make_float2(aS, aS), v[j], yS);
+                            yO = __ffma2_rn(make_float2(aO, aO), v[j], yO);
+                            y1 = __ffma2_rn(make_float2(a1, a1), w[j], y1);
                         }
                         e0 = en;
 #pragma unroll
@@ -816,21 +798,17 @@ k_line_support(HamView h, PoolView p, const typename C2<T>::type* __restrict__ p
                     }
                 }
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-#pragma unroll
-                    for (int o = L / 2; o > 0; o >>= 1) {
-                        ax[q].shfl_xor(o);
-                        ay[q].shfl_xor(o);
-                    }
-                }
-#pragma unroll
                 for (int o = L / 2; o > 0; o >>= 1) {
-                    ox += __shfl_xor_sync(0xffffffffu, ox, o);
-                    oy += __shfl_xor_sync(0xffffffffu, oy, o);
+                    yS.x += __shfl_xor_sync(0xffffffffu, yS.x, o);
+                    yS.y += __shfl_xor_sync(0xffffffffu, yS.y, o);
+                    yO.x += __shfl_xor_sync(0xffffffffu, yO.x, o);
+                    yO.y += __shfl_xor_sync(0xffffffffu, yO.y, o);
+                    y1.x += __shfl_xor_sync(0xffffffffu, y1.x, o);
+                    y1.y += __shfl_xor_sync(0xffffffffu, y1.y, o);
                 }
-                out.s = make_float4(ax[0].hi, ax[0].lo, ay[0].hi, ay[0].lo);
-                out.u = make_float4(ax[1].hi, ax[1].lo, ay[1].hi, ay[1].lo);
-                out.o = make_float2(ox, oy);
+                out.s = yS;
+                out.o = yO;
+                out.u = y1;
             } else {
                 double ax[3] = {0.0, 0.0, 0.0}, ay[3] = {0.0, 0.0, 0.0};   // y_S, y_O, y_1
                 if (live) {
@@ -871,36 +849,21 @@ k_line_support(HamView h, PoolView p, const typename C2<T>::type* __restrict__ p
         if (lane < G && i < nrows) {
             const uint32_t r = expand_support_row(rx, (uint32_t)i);
             const LineSums<T> in = stash[wid][lane];
-            double sx[3], sy[3];   // y_S, y_O, y_1
-            if constexpr (sizeof(T) == 4) {
-                sx[0] = (double)in.s.x + (double)in.s.y;
-                sy[0] = (double)in.s.z + (double)in.s.w;
-                sx[2] = (double)in.u.x + (double)in.u.y;
-                sy[2] = (double)in.u.z + (double)in.u.w;
-                sx[1] = (double)in.o.x;
-                sy[1] = (double)in.o.y;
-            } else {
-                sx[0] = in.s.x;
-                sy[0] = in.s.y;
-                sx[1] = in.o.x;
-                sy[1] = in.o.y;
-                sx[2] = in.u.x;
-                sy[2] = in.u.y;
-            }
+            const double sSx = (double)in.s.x, sSy = (double)in.s.y;
             const double d = h.diag[r];
             const V pr = psi[r], pq = psi[r ^ s.x];
             const double sg = (double)sup_sign<T>(s, c0, r ^ s.x);
             const double2 p0 = make_double2((double)pr.x, (double)pr.y);
             const double2 u1 = make_double2(sg * (double)pq.x, sg * (double)pq.y);
-            const double2 u2 = make_double2(-p0.x, -p0.y);
-            const double2 x0 = make_double2(fma(d, p0.x, sx[0] + sx[1]), fma(d, p0.y, sy[0] + sy[1]));
-            const double2 x1 = make_double2(fma(d, u1.x, sx[2]), fma(d, u1.y, sy[2]));
-            const double2 x2 = make_double2(fma(d, u2.x, -sx[0]), fma(d, u2.y, -sy[0]));
-            a[0] += re_dot(x0, u1);
-            a[1] = __dadd_rn(a[1], re_dot(x0, u2));
-            a[2] += re_dot(u1, x1);
-            a[3] += re_dot(x1, u2);
-            a[4] = __dadd_rn(a[4], re_dot(x2, u2));
+            // (H psi)_r, (H psi_S)_r and (H u1)_r
+            const double2 x0 = make_double2(fma(d, p0.x, sSx + (double)in.o.x), fma(d, p0.y, sSy + (double)in.o.y));
+            const double2 xS = make_double2(fma(d, p0.x, sSx), fma(d, p0.y, sSy));
+            const double2 x1 = make_double2(fma(d, u1.x, (double)in.u.x), fma(d, u1.y, (double)in.u.y));
+            a[0] = __dadd_rn(a[0], re_dot(x0, u1));     // H01
+            a[1] = __dsub_rn(a[1], re_dot(x0, p0));     // H02
+            a[2] = __dadd_rn(a[2], re_dot(u1, x1));     // H11
+            a[3] = __dsub_rn(a[3], re_dot(xS, u1));     // H12
+            a[4] = __dadd_rn(a[4], re_dot(xS, p0));     // H22
         }
         __syncwarp();   // the stash is refilled by the next group
     }
