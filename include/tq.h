@@ -433,7 +433,9 @@ int tq_state_wrap_sector(tq_ctx* ctx, int n_spatial, int n_alpha, int n_beta,
  * with A = pool generator k, applied matrix-free from the pool layout.  The
  * five products and the running sum stay in registers; psi is read once
  * and written once.  If renormalize != 0 the result is divided by its
- * float64 norm (a second, L2-resident pass).  Async.  Errors: TQ_EINVAL
+ * float64 norm: for states of up to 2^16 amplitudes in the same launch (a
+ * thread-block cluster holds the state while the norm is reduced), for
+ * larger ones in a second, L2-resident pass.  Async.  Errors: TQ_EINVAL
  * (k out of range, qubit mismatch, non-finite theta). */
 int tq_evolve_taylor5(tq_ctx* ctx, const tq_pool* pool, int k, double theta,
                       tq_state* psi, int renormalize, void* stream);
@@ -442,12 +444,14 @@ int tq_evolve_taylor5(tq_ctx* ctx, const tq_pool* pool, int k, double theta,
  * int32[nnz], val float64 for TQ_C128 / float32 for TQ_C64 states, device
  * pointers).  The caller guarantees rowptr is non-decreasing with
  * rowptr[0] = 0 and rowptr[D] = nnz; column indices outside [0, D) are
- * skipped (treated as zero entries).  The state is staged in shared memory -- across a thread-block
- * cluster of up to 16 CTAs, read through distributed shared memory -- and
- * never returns to global memory between the five products; the float64
- * norm is reduced across the cluster and, if renormalize != 0, applied
- * before the single store.  Larger states use one L2-resident pass per
- * product.  Async. */
+ * skipped (treated as zero entries).  The state is staged in shared
+ * memory -- across a thread-block cluster of up to 16 CTAs, read through
+ * distributed shared memory, up to 2^17 complex64 or 2^16 complex128
+ * amplitudes -- and never returns to global memory between the five
+ * products; the lanes per row follow the operator's mean row length; the
+ * float64 norm is reduced across the cluster and, if renormalize != 0,
+ * applied before the single store.  Larger states use one L2-resident pass
+ * per product.  Async. */
 int tq_evolve_taylor5_csr(tq_ctx* ctx, int n_qubits, const int* rowptr,
                           const int* col, const void* val, double theta,
                           tq_state* psi, int renormalize, void* stream);

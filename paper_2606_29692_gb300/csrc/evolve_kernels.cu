@@ -16,12 +16,13 @@
 // The float64 squared norm of psi' is reduced per tile in the same pass.
 //
 // CSR path (any operator).  The state is staged in shared memory, split
-// over the CTAs of a thread-block cluster; the gather of v_{k-1} reads
-// peer CTAs' shared memory through the cluster mapping, each product is
-// followed by a cluster barrier, and the running sum lives in registers.
-// Global memory is touched by the initial load, the CSR, and the final
-// store only.  The float64 norm is reduced across the cluster and applied
-// before the store when renormalisation is asked for.
+// over the CTAs of a thread-block cluster (up to 16); the gather of v_{k-1}
+// reads peer CTAs' shared memory through the cluster mapping, L lanes share
+// a row, each product is followed by a cluster barrier, and v_{k-1}, v_k
+// and the running sum live in shared memory.  Global memory is touched by
+// the initial load, the CSR (L2-resident after the first product), and the
+// final store only.  The float64 norm is reduced across the cluster and
+// applied before the store when renormalisation is asked for.
 #include "dev.cuh"
 #include "pair.cuh"
 
@@ -126,90 +127,147 @@ __global__ void k_scale(V* psi, long long D, const double* norm2, const DevStep*
 
 // ---------------------------------------------------------------- CSR path
 
-template <typename T, typename VT, int RPT>
-__global__ void __launch_bounds__(1024)
-k_taylor5_csr_cluster(int nq, int csize, const int* __restrict__ rowptr,
-                      const int* __restrict__ col, const VT* __restrict__ val, double theta,
-                      typename C2<T>::type* psi, int renorm, double* norm2_out) {
+// One product v_k = A v_{k-1} over the CTA's rows, L lanes per row (each
+// lane takes every L-th entry, four in flight, gathers from the owning
+// CTA's shared memory through the cluster mapping), then the group's sum
+// goes to v_k and, times theta^k/k!, to the running sum (the group's first
+// lane; every row has one owner for all five products).
+template <typename T, typename VT, int L>
+__device__ __forceinline__ void csr_product(const cg::cluster_group& cl, int row0, int R, int shift, long long D,
+                                            const int* __restrict__ rowptr, const int* __restrict__ col,
+                                            const VT* __restrict__ val, T coef, const typename C2<T>::type* cur,
+                                            typename C2<T>::type* nxt, typename C2<T>::type* acc) {
     using V = typename C2<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    V* sv = reinterpret_cast<V*>(smem_raw);
-    __shared__ double red[32];
-    __shared__ double cta_part;
-    cg::cluster_group cl = cg::this_cluster();
-    const int rank = (int)cl.block_rank();
-    const long long D = 1ll << nq;
-    const int per = (int)(D / csize);
-    const int shift = 31 - __clz(per);
-    const int bs = blockDim.x;
-    const int row0 = rank * per;
-    for (int i = threadIdx.x; i < per; i += bs) sv[i] = psi[row0 + i];
-    T cf[6];
-    taylor_coefs<T>(theta, cf);
-    V acc[RPT];
+    const int sub = threadIdx.x & (L - 1);
+    const int g = threadIdx.x / L, G = blockDim.x / L;
+    for (int rl0 = 0; rl0 < R; rl0 += G) {          // uniform trip count: the shuffles below see whole warps
+        const int rl = rl0 + g;
+        T sx = T(0), sy = T(0);
+        if (rl < R) {
+            const int r = row0 + rl;
+            const int e1 = rowptr[r + 1];
+            constexpr int U = 4;
+            for (int e0 = rowptr[r] + sub; e0 < e1; e0 += U * L) {
+                int c[U];
+                T a[U];
 #pragma unroll
-    for (int j = 0; j < RPT; ++j) {
-        const int i = threadIdx.x + j * bs;
-        acc[j] = i < per ? sv[i] : V{};   // written by this thread above
-    }
-    cl.sync();
-    for (int step = 1; step <= 5; ++step) {
-        V nv[RPT];
+                for (int j = 0; j < U; ++j) {
+                    const int e = e0 + j * L;
+                    const bool ok = e < e1;
+                    c[j] = ok ? col[e] : -1;
+                    a[j] = ok ? (T)val[e] : T(0);
+                }
+                V v[U];
 #pragma unroll
-        for (int j = 0; j < RPT; ++j) {
-            const int i = threadIdx.x + j * bs;
-            V s{};
-            if (i < per) {
-                const int r = row0 + i;
-                const int e1 = rowptr[r + 1];
-                for (int e = rowptr[r]; e < e1; ++e) {
-                    const int c = col[e];
-                    if ((unsigned)c >= (unsigned)D) continue;   // column outside the state
-                    const V* src = cl.map_shared_rank(sv, c >> shift);
-                    const V v = src[c & (per - 1)];
-                    const T a = (T)val[e];
-                    s.x = fma(a, v.x, s.x);
-                    s.y = fma(a, v.y, s.y);
+                for (int j = 0; j < U; ++j) {
+                    if ((unsigned)c[j] < (unsigned)D) {   // a column outside the state is a zero entry
+                        const V* src = cl.map_shared_rank(cur, (unsigned)c[j] >> shift);
+                        v[j] = src[c[j] & (R - 1)];
+                    } else {
+                        v[j] = V{};
+                        a[j] = T(0);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < U; ++j) {
+                    sx = fma(a[j], v[j].x, sx);
+                    sy = fma(a[j], v[j].y, sy);
                 }
             }
-            nv[j] = s;
         }
-        cl.sync();   // every CTA has finished reading v_{k-1}
 #pragma unroll
-        for (int j = 0; j < RPT; ++j) {
-            const int i = threadIdx.x + j * bs;
-            if (i < per) {
-                sv[i] = nv[j];
-                axpy(acc[j], cf[step], nv[j]);
-            }
+        for (int o = L / 2; o > 0; o >>= 1) {
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
         }
-        cl.sync();   // v_k visible cluster-wide
+        if (rl < R && sub == 0) {
+            V nv;
+            nv.x = sx;
+            nv.y = sy;
+            nxt[rl] = nv;
+            V a = acc[rl];
+            axpy(a, coef, nv);
+            acc[rl] = a;
+        }
+    }
+}
+
+// The fused update for any CSR operator (Eqs. (7)-(8)): the state split
+// over the CTAs of one thread-block cluster, R = D / cluster rows each,
+// staged in shared memory as v_{k-1}, v_k and the running sum.  Each of the
+// five products gathers v_{k-1} from whichever CTA owns the column (local
+// or distributed shared memory) and writes v_k locally; one cluster
+// barrier per product.  The lanes per row follow the operator's mean row
+// length (read on the device from rowptr[D]).  The float64 norm is pushed
+// to every CTA's shared memory after the last product and, with
+// renormalisation, applied before the single store.
+template <typename T, typename VT>
+__global__ void __launch_bounds__(1024)
+k_taylor5_csr_cluster(int nq, const int* __restrict__ rowptr, const int* __restrict__ col,
+                      const VT* __restrict__ val, double theta, typename C2<T>::type* psi, int renorm,
+                      double* norm2_out) {
+    using V = typename C2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    __shared__ double cta_part;
+    __shared__ double slots[16];
+    __shared__ double scale_sh;
+    cg::cluster_group cl = cg::this_cluster();
+    const unsigned nb = cl.num_blocks(), rank = cl.block_rank();
+    const long long D = 1ll << nq;
+    const int R = (int)(D / nb);
+    const int shift = 31 - __clz(R);
+    V* vb0 = reinterpret_cast<V*>(smem_raw);
+    V* vb1 = vb0 + R;
+    V* acc = vb1 + R;
+    const int row0 = (int)rank * R;
+    for (int i = threadIdx.x; i < R; i += blockDim.x) {
+        const V v = psi[row0 + i];
+        vb0[i] = v;
+        acc[i] = v;
+    }
+    T cf[6];
+    taylor_coefs<T>(theta, cf);
+    const long long nnz = rowptr[D];
+    const long long per_row = nnz / D;
+    cl.sync();   // every CTA has started and staged its rows
+    V* cur = vb0;
+    V* nxt = vb1;
+    for (int k = 1; k <= 5; ++k) {
+        if (per_row >= 24)
+            csr_product<T, VT, 32>(cl, row0, R, shift, D, rowptr, col, val, cf[k], cur, nxt, acc);
+        else if (per_row >= 4)
+            csr_product<T, VT, 8>(cl, row0, R, shift, D, rowptr, col, val, cf[k], cur, nxt, acc);
+        else
+            csr_product<T, VT, 1>(cl, row0, R, shift, D, rowptr, col, val, cf[k], cur, nxt, acc);
+        cl.sync();   // v_k complete everywhere; nobody reads v_{k-1} any more
+        V* t = cur;
+        cur = nxt;
+        nxt = t;
     }
     double part = 0.0;
-#pragma unroll
-    for (int j = 0; j < RPT; ++j) {
-        const int i = threadIdx.x + j * bs;
-        if (i < per) part += (double)acc[j].x * acc[j].x + (double)acc[j].y * acc[j].y;
-    }
+    for (int i = threadIdx.x; i < R; i += blockDim.x)
+        part += (double)acc[i].x * acc[i].x + (double)acc[i].y * acc[i].y;
     double v[1] = {part};
     block_sum<1>(v, red);
     if (threadIdx.x == 0) cta_part = v[0];
-    cl.sync();
-    double total = 0.0;
-    for (int q = 0; q < csize; ++q) total += *cl.map_shared_rank(&cta_part, q);
-    const double sc = renorm ? 1.0 / sqrt(total) : 1.0;
-#pragma unroll
-    for (int j = 0; j < RPT; ++j) {
-        const int i = threadIdx.x + j * bs;
-        if (i < per) {
-            V o;
-            o.x = (T)((double)acc[j].x * sc);
-            o.y = (T)((double)acc[j].y * sc);
-            psi[row0 + i] = o;
-        }
+    __syncthreads();
+    if (threadIdx.x < nb) *cl.map_shared_rank(&slots[rank], threadIdx.x) = cta_part;
+    cl.sync();   // the pushes are visible; nothing reads a peer after this
+    if (threadIdx.x == 0) {
+        double total = 0.0;
+        for (unsigned q = 0; q < nb; ++q) total += slots[q];
+        scale_sh = renorm ? 1.0 / sqrt(total) : 1.0;
+        if (rank == 0 && norm2_out) *norm2_out = total;
     }
-    if (rank == 0 && threadIdx.x == 0 && norm2_out) *norm2_out = total;
-    cl.sync();   // peers may still read this CTA's shared memory
+    __syncthreads();
+    const double sc = scale_sh;
+    for (int i = threadIdx.x; i < R; i += blockDim.x) {
+        V o;
+        o.x = (T)((double)acc[i].x * sc);
+        o.y = (T)((double)acc[i].y * sc);
+        psi[row0 + i] = o;
+    }
 }
 
 // Unfused fallback for states too large for a cluster: one pass per product,
@@ -277,13 +335,12 @@ __global__ void k_finish(const V* acc, V* psi, long long D, const double* partia
     }
 }
 
-template <typename T, typename VT, int RPT>
-cudaError_t launch_cluster(int nq, int csize, int bs, const int* rowptr, const int* col,
-                           const VT* val, double theta, void* psi, int renorm, double* norm2,
-                           cudaStream_t s) {
+template <typename T, typename VT>
+cudaError_t launch_cluster(int nq, int csize, const int* rowptr, const int* col, const VT* val, double theta,
+                           void* psi, int renorm, double* norm2, cudaStream_t s) {
     using V = typename C2<T>::type;
-    auto kern = k_taylor5_csr_cluster<T, VT, RPT>;
-    const size_t smem = (size_t)((1ll << nq) / csize) * sizeof(V);
+    auto kern = k_taylor5_csr_cluster<T, VT>;
+    const size_t smem = (size_t)3 * ((1ll << nq) / csize) * sizeof(V);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (csize > 8) {
@@ -292,7 +349,7 @@ cudaError_t launch_cluster(int nq, int csize, int bs, const int* rowptr, const i
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(csize);
-    cfg.blockDim = dim3(bs);
+    cfg.blockDim = dim3(1024);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -306,29 +363,7 @@ cudaError_t launch_cluster(int nq, int csize, int bs, const int* rowptr, const i
     e = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg);
     if (e != cudaSuccess) return e;
     if (nclusters < 1) return cudaErrorInvalidConfiguration;
-    return cudaLaunchKernelEx(&cfg, kern, nq, csize, rowptr, col, val, theta,
-                              static_cast<V*>(psi), renorm, norm2);
-}
-
-template <typename T, typename VT>
-cudaError_t dispatch_cluster(int nq, int csize, const int* rowptr, const int* col,
-                             const VT* val, double theta, void* psi, int renorm,
-                             double* norm2, cudaStream_t s) {
-    const long long per = (1ll << nq) / csize;
-    const int bs = (int)(per < 1024 ? (per < 32 ? 32 : per) : 1024);
-    const int rpt = (int)((per + bs - 1) / bs);
-    // rows per thread: at most 8 (complex64) or 4 (complex128), see the
-    // slice size chosen in launch_taylor5_csr
-    switch (rpt) {
-        case 1: return launch_cluster<T, VT, 1>(nq, csize, bs, rowptr, col, val, theta, psi, renorm, norm2, s);
-        case 2: return launch_cluster<T, VT, 2>(nq, csize, bs, rowptr, col, val, theta, psi, renorm, norm2, s);
-        case 4: return launch_cluster<T, VT, 4>(nq, csize, bs, rowptr, col, val, theta, psi, renorm, norm2, s);
-        case 8:
-            if constexpr (sizeof(T) == 4)
-                return launch_cluster<T, VT, 8>(nq, csize, bs, rowptr, col, val, theta, psi, renorm, norm2, s);
-            return cudaErrorInvalidConfiguration;
-        default: return cudaErrorInvalidConfiguration;
-    }
+    return cudaLaunchKernelEx(&cfg, kern, nq, rowptr, col, val, theta, static_cast<V*>(psi), renorm, norm2);
 }
 
 template <typename T, typename VT>
@@ -473,20 +508,22 @@ int launch_taylor5_csr(int nq, int prec, const int* rowptr, const int* col, cons
                        double theta, void* psi, int renorm, double* acc, double* v0, double* v1,
                        double* partials, double* norm2, int sms, cudaStream_t s) {
     const long long D = 1ll << nq;
-    // slice per CTA: 64 KiB of shared memory, and at most 8 rows per thread
-    // so that v_k and the running sum of each row fit in registers
-    const long long per_max = prec == TQ_C128 ? 4096 : 8192;
-    long long csize = D <= per_max ? 1 : D / per_max;
-    if (csize <= 16) {
+    // rows per CTA: three vectors of them in shared memory (at most 192 KB);
+    // about 1024 rows per CTA, up to a 16-CTA cluster; a cluster size the
+    // device refuses falls back to half the CTAs with twice the rows
+    const long long vb = prec == TQ_C128 ? 16 : 8;
+    const long long rmax = (192ll << 10) / (3 * vb);
+    for (long long csize = std::min<long long>(16, std::max<long long>(1, D / 1024)); csize >= 1; csize /= 2) {
+        if (D / csize > rmax || D % csize != 0) break;
         cudaError_t e;
         if (prec == TQ_C128)
-            e = dispatch_cluster<double, double>(nq, (int)csize, rowptr, col,
-                                                 static_cast<const double*>(val), theta, psi, renorm, norm2, s);
+            e = launch_cluster<double, double>(nq, (int)csize, rowptr, col, static_cast<const double*>(val), theta,
+                                               psi, renorm, norm2, s);
         else
-            e = dispatch_cluster<float, float>(nq, (int)csize, rowptr, col,
-                                               static_cast<const float*>(val), theta, psi, renorm, norm2, s);
+            e = launch_cluster<float, float>(nq, (int)csize, rowptr, col, static_cast<const float*>(val), theta,
+                                             psi, renorm, norm2, s);
         if (e == cudaSuccess) return 1;
-        cudaGetLastError();   // clear a refused cluster configuration; fall back below
+        cudaGetLastError();   // clear a refused cluster configuration; try a smaller one
     }
     if (prec == TQ_C128)
         return run_unfused<double, double>(nq, rowptr, col, static_cast<const double*>(val), theta, psi,

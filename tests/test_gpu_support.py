@@ -250,3 +250,40 @@ def test_fp64_fma_rate(ctx):
     for bad in (0, -1, (1 << 20) + 1):
         with pytest.raises(tq.TQError):
             tq.fp64_fma_rate(ctx, bad)
+
+
+@pytest.mark.parametrize("prec", [tq.TQ_C64, tq.TQ_C128])
+def test_occupancy_knob_keeps_every_bit(ctx, prec):
+    """Resident CTAs per SM (tq_ctx_set_support_occupancy) change only the
+    persistent grid: amplitudes and carried norms are bit-identical for every
+    setting, and bad settings are refused."""
+    import torch
+    n, ne, mp = 7, 6, 1
+    pool = tq.build_pool(ctx, n, ne, mp)
+    S = 600                                      # more states than one wave of CTAs at 2 per SM
+    psi, k, th, dt = _inputs(14, S, pool.M, 71, prec)
+    outs = []
+    for occ in (0, 1, 2, 3):
+        ctx.set_support_occupancy(prec, occ)
+        d = torch.as_tensor(psi).to(dt).cuda()
+        dn = torch.ones(S, dtype=torch.float64, device="cuda")
+        tq.evolve_taylor5_batch_support(ctx, pool, d, torch.as_tensor(k).cuda(), torch.as_tensor(th).cuda(), dn,
+                                        prec=prec)
+        outs.append((d.cpu(), dn.cpu()))
+    ctx.set_support_occupancy(prec, 0)
+    for d, dn in outs[1:]:
+        assert torch.equal(torch.view_as_real(d), torch.view_as_real(outs[0][0]))
+        assert torch.equal(dn, outs[0][1])
+    for bad in (-1, 33):
+        with pytest.raises(tq.TQError):
+            ctx.set_support_occupancy(prec, bad)
+
+
+def test_l2_read_rate(ctx):
+    """The L2 read-rate probe returns a rate between the HBM copy rate's
+    order and a bound no GB300 L2 reaches, and refuses bad sizes."""
+    r = tq.l2_read_rate(ctx, 16 << 20, 16)
+    assert 1e12 < r < 1e14
+    for nbytes, reps in ((1 << 19, 4), ((256 << 20) + 16, 4), ((1 << 20) + 8, 4), (1 << 20, 0)):
+        with pytest.raises(tq.TQError):
+            tq.l2_read_rate(ctx, nbytes, reps)
