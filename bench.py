@@ -631,6 +631,8 @@ def run_ours(args, rank, world, local_rank):
                                                         applied[0], tq.relabel_index(order))
     if rank == 0 and args.layout == "sector":
         extra["natural_layout"] = measure_natural_layout(tq, ctx, pool_nat, S, k, th, prep_k, prep_th, sup_s)
+        extra["grouped_layout"] = measure_grouped_layout(tq, ctx, pool, psi, dn, k, th, sup_s,
+                                                         mapping=mp_run)
     pool = pool_nat   # the other sections use BK's own qubit order
     if rank == 0 and not args.headline_only:
         extra["precision_vs_oracle"] = measure_precision(tq, ctx)
@@ -758,6 +760,79 @@ def measure_natural_layout(tq, ctx, pool, n_states, k, th, prep_k, prep_th, ms_r
             "algorithmic_bytes_per_launch": alg, "sector_bytes_per_launch": sect,
             "frac": alg / (ms * 1e-3) / 1e9 / peak, "sector_frac": sect / (ms * 1e-3) / 1e9 / peak,
             "relabelled_speedup": ms / (ms_relabelled * 1e3)}
+
+
+def measure_grouped_layout(tq, ctx, pool, psi, dn, k, th, s_flat, mapping, reps=50):
+    """The headline batch with the states that take the same generator
+    interleaved in groups of four (tq_evolve_taylor5_batch_grouped): a
+    support row of a group is one whole 32-byte sector holding that row of
+    its four states.  The same states, generators and angles in the same
+    qubit layout; a generator's last group is filled up with theta = 0
+    copies of one of its states.  One launch is checked against the
+    per-state support update (bit-identical amplitudes) before timing."""
+    import numpy as np
+    import torch
+    G = tq.TQ_GROUP_C64
+    S = int(k.size)
+    slot_state, slot_theta, group_k = [], [], []
+    for kk in np.unique(k):
+        idx = np.flatnonzero(k == kk)
+        pad = (-idx.size) % G
+        slot_state.extend(idx.tolist() + [int(idx[-1])] * pad)
+        slot_theta.extend(th[idx].tolist() + [0.0] * pad)
+        group_k.extend([int(kk)] * ((idx.size + pad) // G))
+    n_groups = len(group_k)
+    sel = torch.as_tensor(np.asarray(slot_state, dtype=np.int64)).cuda()
+    dth = torch.as_tensor(np.asarray(slot_theta, dtype=np.float64)).cuda()
+    dkg = torch.as_tensor(np.asarray(group_k, dtype=np.int32)).cuda()
+    dks = torch.as_tensor(np.repeat(np.asarray(group_k, dtype=np.int32), G)).cuda()
+    ref = psi.index_select(0, sel)
+    n_ref = dn.index_select(0, sel)
+    gpsi = ref.view(n_groups, G, D).permute(0, 2, 1).contiguous()
+    n_g = n_ref.clone()
+    tq.evolve_taylor5_batch_support(ctx, pool, ref, dks, dth, n_ref)
+    tq.evolve_taylor5_batch_grouped(ctx, pool, gpsi, dkg, dth, n_g)
+    back = gpsi.permute(0, 2, 1).reshape(n_groups * G, D)
+    identical = bool(torch.equal(torch.view_as_real(back), torch.view_as_real(ref)))
+    norm_dev = float(((n_g - n_ref).abs() / n_ref).max().item())
+    del ref, back
+    fetch0 = ctx.l2_fetch()
+    per = {}
+    for fetch in (32, 64):
+        ctx.set_l2_fetch(fetch)
+        for lanes in (1, 2, 4):
+            for ppt in (1, 2, 4):
+                ctx.set_grouped_schedule(tq.TQ_C64, lanes, ppt)
+                for _ in range(3):
+                    tq.evolve_taylor5_batch_grouped(ctx, pool, gpsi, dkg, dth, n_g)
+                per[(fetch, lanes, ppt)] = time_launches(
+                    lambda: tq.evolve_taylor5_batch_grouped(ctx, pool, gpsi, dkg, dth, n_g), reps)
+    ctx.set_l2_fetch(fetch0)
+    best = min(per, key=per.get)
+    ctx.set_grouped_schedule(tq.TQ_C64, best[1], best[2])
+    ms = per[best]
+    finite = bool(torch.isfinite(n_g).all().item())
+    del gpsi
+    torch.cuda.empty_cache()
+    rows = support_rows(tq, N_SPATIAL, N_ELECTRONS, mapping)
+    n_rows = np.array([r.size for r in rows], dtype=np.float64)
+    alg = float((16 * n_rows[k]).sum() + 16 * S)                       # the real states' rows and norms
+    touched = float((64 * n_rows[np.asarray(group_k)]).sum() + 16 * n_groups * G)   # padding included
+    peak, _ = peaks()
+    return {"workload": f"the headline batch ({S} complex64 14-qubit states, same generators and angles, same "
+                        f"qubit layout) grouped by generator: {n_groups} groups of {G} interleaved states, "
+                        f"{n_groups * G - S} theta = 0 fill states",
+            "kernel": "k_taylor5_grouped<float>", "api": "tq_evolve_taylor5_batch_grouped",
+            "l2_fetch_bytes": best[0], "lanes_per_row": best[1], "pairs_per_lane": best[2],
+            "ms_by_fetch_lanes_and_pairs": {f"{f_}B/{l_}/{p_}": v for (f_, l_, p_), v in per.items()},
+            "ms_per_launch": ms, "updates_per_s": S / (ms * 1e-3),
+            "algorithmic_bytes_per_launch": alg, "touched_sector_bytes_per_launch": touched,
+            "frac": alg / (ms * 1e-3) / 1e9 / peak, "sector_frac": touched / (ms * 1e-3) / 1e9 / peak,
+            "speedup_over_one_state_per_vector": s_flat * 1e3 / ms,
+            "amplitudes_identical_to_per_state_update": identical,
+            "max_rel_norm_deviation_from_per_state_update": norm_dev, "norms_finite": finite,
+            "note": "applies when several states take the same generator in one step (a pool scan, "
+                    "a line search, trajectories that agree); not the headline layout"}
 
 
 def measure_full_state(tq, ctx, pool, n_states, reps=50):

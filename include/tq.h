@@ -591,6 +591,31 @@ int tq_evolve_taylor5_batch_support_host(tq_ctx* ctx, const tq_pool* pool,
  * with them staged in shared memory by asynchronous copies that run one
  * pass ahead (across states).  Defaults: 4 for TQ_C128, -1 for TQ_C64. */
 int tq_ctx_set_support_schedule(tq_ctx* ctx, int prec, int pairs_per_thread);
+/* The support-only batched update for groups of states that share a
+ * generator, in an interleaved layout (a layout choice with no counterpart
+ * in the paper; the update is that of Eqs. (6)-(8) as above).  A group is
+ * TQ_GROUP_C64 = 4 complex64 or TQ_GROUP_C128 = 2 complex128 states, the
+ * 32 bytes of one memory sector: element (g, r, s) -- group g, amplitude r
+ * (0 <= r < D), state s of the group -- is at psi[(g D + r) G + s], so one
+ * support row of a group is one whole sector and every touched sector is
+ * used in full.  k: int32[n_groups] device, the generator of each group;
+ * theta, norm2: [n_groups G] device, per state (norm2 may be null; else
+ * in/out as in tq_evolve_taylor5_batch_support).  Each state's amplitudes
+ * equal what tq_evolve_taylor5_batch_support gives it; its norm agrees to
+ * rounding (another summation order).  psi 32-byte aligned.  Async.
+ * TQ_EINVAL for a sector pool, bad sizes or alignment; an op index outside
+ * [0, M) leaves its group untouched and its norms NaN. */
+#define TQ_GROUP_C64 4
+#define TQ_GROUP_C128 2
+int tq_evolve_taylor5_batch_grouped(tq_ctx* ctx, const tq_pool* pool, int n_groups, int prec, void* psi,
+                                    const int* k, const double* theta, double* norm2, void* stream);
+/* Schedule of that update: lanes_per_row threads share each support row
+ * of a group, each holding G / lanes_per_row of its states (1 or 2, and 4
+ * for TQ_C64), with pairs_per_thread pairs each (1, 2 or 4).  Default
+ * (1, 1).  Every schedule gives the same amplitudes.  TQ_EINVAL
+ * otherwise. */
+int tq_ctx_set_grouped_schedule(tq_ctx* ctx, int prec, int lanes_per_row, int pairs_per_thread);
+
 /* Resident CTAs per SM of the support-only update (its persistent grid is
  * that many CTAs per SM): 0 (the default) takes as many as fit, 1..32
  * fewer.  Fewer concurrent states per SM can raise DRAM locality for the

@@ -177,6 +177,11 @@ class Context:
         (registers), or -1, -2, -4, -8 (shared-memory staging, pipelined)."""
         call("tq_ctx_set_support_schedule", self.handle, prec, int(pairs_per_thread))
 
+    def set_grouped_schedule(self, prec, lanes_per_row, pairs_per_thread):
+        """Schedule of the grouped-layout update: lanes sharing a row (1, 2,
+        or 4 for complex64) and pairs per lane (1, 2 or 4)."""
+        call("tq_ctx_set_grouped_schedule", self.handle, prec, int(lanes_per_row), int(pairs_per_thread))
+
     def set_support_occupancy(self, prec, ctas_per_sm):
         """Resident CTAs per SM of the support-only update (0: as many as fit)."""
         call("tq_ctx_set_support_occupancy", self.handle, prec, int(ctas_per_sm))
@@ -596,6 +601,22 @@ def evolve_taylor5_batch_support(ctx, pool, psi, k, theta, norm2=None, prec=TQ_C
     ``norm2`` (float64 CUDA tensor) is in/out: ||psi_b||^2 in, ||psi_b'||^2 out."""
     n_states = psi.shape[0]
     call("tq_evolve_taylor5_batch_support", ctx.handle, pool.handle, n_states, prec, _ptr(psi), _ptr(k),
+         _ptr(theta), _ptr(norm2), _stream(stream))
+
+
+TQ_GROUP_C64 = 4      # states per group of the grouped layout (one 32-byte sector)
+TQ_GROUP_C128 = 2
+
+
+def evolve_taylor5_batch_grouped(ctx, pool, psi, k, theta, norm2=None, prec=TQ_C64, stream=None):
+    """Support-only update of groups of states sharing a generator, stored
+    amplitude-major within each group: psi of shape (n_groups, D, G) (G = 4
+    complex64 or 2 complex128 states), k int32 [n_groups], theta and norm2
+    float64 [n_groups * G], all CUDA tensors."""
+    G = TQ_GROUP_C128 if prec == TQ_C128 else TQ_GROUP_C64
+    n_groups = int(k.numel())
+    assert psi.numel() == n_groups * (1 << pool.n_qubits) * G and theta.numel() == n_groups * G
+    call("tq_evolve_taylor5_batch_grouped", ctx.handle, pool.handle, n_groups, prec, _ptr(psi), _ptr(k),
          _ptr(theta), _ptr(norm2), _stream(stream))
 
 

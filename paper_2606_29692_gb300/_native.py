@@ -110,6 +110,8 @@ SIGNATURES = {
     "tq_ctx_set_support_schedule": [vp, i32, i32],
     "tq_autotune_support": [vp, vp, i32, i32, P(i32), P(f64)],
     "tq_fp64_fma_rate": [vp, i32, P(f64)],
+    "tq_evolve_taylor5_batch_grouped": [vp, vp, i32, i32, vp, vp, vp, vp, vp],
+    "tq_ctx_set_grouped_schedule": [vp, i32, i32, i32],
     "tq_ctx_set_support_occupancy": [vp, i32, i32],
     "tq_mapping_relabelled": [i32, i32, vp, P(i32)],
     "tq_pool_sector_order": [i32, i32, i32, i32, vp],

@@ -406,6 +406,37 @@ extern "C" int tq_ctx_set_support_schedule(tq_ctx* c, int prec, int pairs_per_th
     API_END
 }
 
+extern "C" int tq_evolve_taylor5_batch_grouped(tq_ctx* c, const tq_pool* p, int n_groups, int prec, void* psi,
+                                               const int* k, const double* theta, double* norm2, void* stream) {
+    API_BEGIN
+    TQ_REQUIRE(c && p, "null argument");
+    TQ_REQUIRE(!p->sector, "the grouped update takes full-space pools");
+    TQ_REQUIRE(n_groups >= 0, "n_groups < 0");
+    check_prec(prec);
+    if (n_groups == 0) return TQ_OK;   // an empty batch is a no-op
+    TQ_REQUIRE(psi && k && theta, "null argument");
+    TQ_REQUIRE(((uintptr_t)psi & 31u) == 0, "psi must be 32-byte aligned");
+    set_device(c);
+    cudaStream_t s = as_stream(stream);
+    launch(c, "taylor5_grouped", s, [&] {
+        return launch_taylor5_grouped(p->view, n_groups, prec, c->grouped_lanes[prec], c->grouped_ppt[prec], psi, k,
+                                      theta, norm2,
+                                      c->sm_count, s);
+    });
+    API_END
+}
+
+extern "C" int tq_ctx_set_grouped_schedule(tq_ctx* c, int prec, int lanes_per_row, int pairs_per_thread) {
+    API_BEGIN
+    TQ_REQUIRE(c, "null argument");
+    check_prec(prec);
+    TQ_REQUIRE(grouped_schedule_ok(prec, lanes_per_row, pairs_per_thread),
+               "lanes_per_row must be 1, 2 or (complex64) 4 and pairs_per_thread 1, 2 or 4");
+    c->grouped_lanes[prec] = lanes_per_row;
+    c->grouped_ppt[prec] = pairs_per_thread;
+    API_END
+}
+
 extern "C" int tq_ctx_set_support_occupancy(tq_ctx* c, int prec, int ctas_per_sm) {
     API_BEGIN
     TQ_REQUIRE(c, "null argument");

@@ -210,6 +210,13 @@ int launch_norm_carry(const double* partials, int prec, int n_states, int tiles_
 // support are not touched); partials hold the change of |psi|^2 per tile.
 // With one tile per state and norm2 set, the launch adds the change to
 // norm2 itself (nothing is left for launch_norm_carry).
+// Support-only update of groups of grouped_size(prec) states that share a
+// generator, stored amplitude-major within the group (one 32-byte sector
+// per support row of the group); k per group, theta and norm2 per state.
+int grouped_size(int prec);
+bool grouped_schedule_ok(int prec, int lanes_per_row, int pairs_per_thread);
+int launch_taylor5_grouped(const PoolView& p, int n_groups, int prec, int lanes_per_row, int pairs_per_thread,
+                           void* psi, const int* k, const double* theta, double* norm2, int sms, cudaStream_t s);
 int support_tiles(int nq, int n_states, int ppt, int sms);
 int support_parts(int tiles);
 int launch_taylor5_support(const PoolView& p, int n_states, int prec, int ppt, void* psi, const int* k,
@@ -326,6 +333,8 @@ struct tq_ctx {
     int pair_upt[2] = {2, 4};              // schedule per precision (C128, C64)
     int supp_ppt[2] = {4, -1};             // support-only update: pairs per thread per pass, < 0 pipelined (C128, C64)
     int supp_ctas[2] = {0, 0};             // its resident CTAs per SM (0: as many as fit)
+    int grouped_lanes[2] = {1, 1};         // grouped-layout update: lanes per row (C128, C64)
+    int grouped_ppt[2] = {1, 1};           // and pairs per lane
     int l2_fetch_default = 0;              // the CUDA context's L2 fetch granularity at creation (bytes)
     int spmv_lanes = 0;                    // energy SpMV: CSR lanes per row, or 0 for XOR-ELL (default)
     int test_flags = 0;                    // TQ_TEST_* (tests of the failure paths only)
