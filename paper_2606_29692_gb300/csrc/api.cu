@@ -684,6 +684,8 @@ tq_pool* make_pool(tq_ctx* c, int n_spatial, int n_electrons, int mapping) {
             }
         }
         p->nterm = nterm;
+        p->unit = true;
+        for (int k = 0; k < M; ++k) p->unit = p->unit && std::fabs(fc0d[k]) == 1.0;
         PoolView& v = p->view;
         v.M = M;
         v.nq = p->nq;

@@ -28,7 +28,7 @@ extern "C" int tq_evolve_taylor5(tq_ctx* c, const tq_pool* p, int k, double thet
     if (!p->sector && taylor5_single_ready(p->nq, psi->prec)) {
         // one launch: update, norm and rescale in one thread-block cluster
         launch(c, "taylor5_single", s, [&] {
-            return launch_taylor5_single(p->view, psi->prec, k, theta, nullptr, psi->data, renormalize,
+            return launch_taylor5_single(p->view, psi->prec, p->unit, k, theta, nullptr, psi->data, renormalize,
                                          renormalize ? &c->step->norm2 : nullptr, s);
         });
         return TQ_OK;
@@ -174,7 +174,7 @@ void enqueue_adapt_step(tq_ctx* c, const AdaptBufs& b, const tq_ham* h, const tq
     if (!p->sector && taylor5_single_ready(p->nq, psi->prec)) {
         // the update, its norm and the rescale in one launch
         launch(c, "taylor5_single_gated", s, [&] {
-            return launch_taylor5_single(p->view, psi->prec, 0, 0.0, c->step, psi->data, 1, &c->step->norm2, s);
+            return launch_taylor5_single(p->view, psi->prec, p->unit, 0, 0.0, c->step, psi->data, 1, &c->step->norm2, s);
         });
         return;
     }

@@ -281,9 +281,11 @@ int launch_step_record(DevStep* step, double* rec, int n, cudaStream_t s);
 // same launch: one thread-block cluster holds the state in registers.
 // k/theta from the arguments, or from the step record when gate is set.
 // ready: some cluster shape launches for 2^nq amplitudes in this precision.
+// unit_pool: every generator's entries are +-1, so complex128 takes the
+// closed-form kernel (norm from the input, update and rescale in one pass).
 bool taylor5_single_ready(int nq, int prec);
-int launch_taylor5_single(const PoolView& p, int prec, int k, double theta, const DevStep* gate, void* psi,
-                          int renorm, double* norm2, cudaStream_t s);
+int launch_taylor5_single(const PoolView& p, int prec, bool unit_pool, int k, double theta, const DevStep* gate,
+                          void* psi, int renorm, double* norm2, cudaStream_t s);
 int launch_taylor5_pair_gated(const PoolView& p, int prec, int upt, void* psi, const DevStep* step,
                               double* partials, int sms, cudaStream_t s);
 int launch_scale_gated(void* psi, int prec, long long D, const double* norm2,
@@ -374,6 +376,7 @@ struct tq_pool {
     std::vector<int> nterm;
     std::vector<void*> allocs;
     tq::PoolView view{};
+    bool unit = false;         // every generator's entries are +-1 (|c0| = 1)
     // on-demand CSR per (op, precision)
     std::vector<void*> csr_alloc[2];
     std::vector<const int*> csr_rowptr[2];

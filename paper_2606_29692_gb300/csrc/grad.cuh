@@ -50,6 +50,16 @@ __device__ __forceinline__ uint32_t supp_row(const SuppRec& s, uint32_t u) {
     return r;
 }
 
+// Whether row r lies in the support: every condition's parity equals its
+// target.
+__device__ __forceinline__ bool in_support(const SuppRec& s, uint32_t r) {
+    int ok = 1;
+    if (s.m > 0) ok &= (parity32(r & s.e0) == (s.target & 1));
+    if (s.m > 1) ok &= (parity32(r & s.e1) == ((s.target >> 1) & 1));
+    if (s.m > 2) ok &= (parity32(r & s.e2) == ((s.target >> 2) & 1));
+    return ok != 0;
+}
+
 // Pair u -> support row r, with the generator's masks worked out once per
 // tile: a zero inserted at the representative's bit (position hp among the
 // free bits) and at each pivot (ascending), as (v & lo) | ((v & ~lo) << 1)

@@ -690,14 +690,6 @@ __device__ __forceinline__ T sup_sign(const SuppRec& s, T c0, uint32_t col) {
     return parity32(col & s.z0) ? -c0 : c0;   // A[r][col], r = col ^ x in S
 }
 
-__device__ __forceinline__ bool in_support(const SuppRec& s, uint32_t r) {
-    int ok = 1;
-    if (s.m > 0) ok &= (parity32(r & s.e0) == (s.target & 1));
-    if (s.m > 1) ok &= (parity32(r & s.e1) == ((s.target >> 1) & 1));
-    if (s.m > 2) ok &= (parity32(r & s.e2) == ((s.target >> 2) & 1));
-    return ok != 0;
-}
-
 // Re(conj(a) b) with no contraction: the same bits for (a, b) and (-a, b)
 // up to sign.
 __device__ __forceinline__ double re_dot(double2 a, double2 b) {
