@@ -53,7 +53,13 @@ extern "C" int tq_ctx_create(int device, tq_ctx** out) {
         c->l2_fetch_default = (int)fetch;
         // the line search's sample table, filled before any call can read it
         c->line_sc = static_cast<double2*>(dev_alloc(4096 * sizeof(double2)));
-        c->line_se = static_cast<double*>(dev_alloc((4096 + 64) * sizeof(double)));
+        c->line_se = static_cast<long long*>(dev_alloc((4096 + 64) * sizeof(long long)));
+        c->line_rank = static_cast<int*>(dev_alloc(4096 * sizeof(int)));
+        {
+            std::vector<int> rank(4096);
+            line_rank_table(rank.data());
+            TQ_CUDA(cudaMemcpy(c->line_rank, rank.data(), 4096 * sizeof(int), cudaMemcpyHostToDevice));
+        }
         launch(c, "line_table", 0, [&] { return launch_line_table(c->line_sc, 0); });
         TQ_CUDA(cudaDeviceSynchronize());
     } catch (...) {
@@ -74,6 +80,7 @@ extern "C" int tq_ctx_destroy(tq_ctx* c) {
     if (c->tickets) cudaFree(c->tickets);
     if (c->line_sc) cudaFree(c->line_sc);
     if (c->line_se) cudaFree(c->line_se);
+    if (c->line_rank) cudaFree(c->line_rank);
     for (auto& s : c->aux)
         if (s) cudaStreamDestroy(s);
     for (auto& r : c->trace) {

@@ -169,7 +169,7 @@ void enqueue_adapt_step(tq_ctx* c, const AdaptBufs& b, const tq_ham* h, const tq
                                                                           b.part, c->tickets + 2, c->sm_count, s); });
         }
     }
-    launch(c, "line_search", s, [&] { return launch_line_search(c->step, theta, theta_list, c->line_sc, c->line_se,
+    launch(c, "line_search", s, [&] { return launch_line_search(c->step, theta, theta_list, c->line_sc, c->line_rank, c->line_se,
                                                                 c->tickets + 3, s); });
     if (!p->sector && taylor5_single_ready(p->nq, psi->prec)) {
         // the update, its norm and the rescale in one launch

@@ -266,12 +266,15 @@ int line_support_partials(int sms);
 int launch_line_dots(const void* z, const double2* w0, const double2* w1, const double2* w2, int prec, long long D,
                      double* partials, unsigned* ticket, DevStep* step, cudaStream_t s);
 // sc: sin and cos of the 4096 sample angles (launch_line_table fills it);
-// se: 4096 + 16 doubles of scratch; ticket: zero between calls.
+// rank: the samples' positions in the order (|theta_m|, m) (host table from
+// line_rank_table, copied to the device); se: 4096 + 16 int64 of scratch;
+// ticket: zero between calls.
 int launch_line_table(double2* sc, cudaStream_t s);
+void line_rank_table(int* rank);   // host: rank[4096]
 // theta_list (device, optional): the angle of step step->iter (overrides
 // theta_given).
-int launch_line_search(DevStep* step, double theta_given, const double* theta_list, const double2* sc, double* se,
-                       unsigned* ticket, cudaStream_t s);
+int launch_line_search(DevStep* step, double theta_given, const double* theta_list, const double2* sc,
+                       const int* rank, long long* se, unsigned* ticket, cudaStream_t s);
 // Appends the step's result to rec (6 doubles per step: energy, max|g|,
 // theta, selected, converged, bad norm) at step->iter, then advances it.
 int launch_step_record(DevStep* step, double* rec, int n, cudaStream_t s);
@@ -349,7 +352,8 @@ struct tq_ctx {
     tq::DevStep* step = nullptr;      // device
     unsigned* tickets = nullptr;      // device, zero between calls
     double2* line_sc = nullptr;       // device, sin/cos of the line search's sample angles (filled once)
-    double* line_se = nullptr;        // device, the samples' energies and per-block minima (4096 + 16)
+    long long* line_se = nullptr;     // device, the samples' energy keys and per-block minima (4096 + 16)
+    int* line_rank = nullptr;         // device, the samples' tie-rule ranks (4096)
     size_t tickets_n = 0;
     cudaStream_t aux[3] = {nullptr, nullptr, nullptr};
 };

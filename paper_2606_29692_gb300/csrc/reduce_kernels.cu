@@ -10,7 +10,10 @@
 #include "spmv.cuh"
 #include "tma.cuh"
 
+#include <algorithm>
+#include <climits>
 #include <cmath>
+#include <vector>
 
 namespace tq {
 
@@ -411,33 +414,53 @@ k_pool_grad(PoolView p, const W* __restrict__ w, const typename C2<T>::type* __r
     }
 }
 
-// Operator choice and convergence (one CTA).
-__global__ void k_select(const double* g, int M, double eps, int prec, DevStep* step) {
-    __shared__ double smax[32];
-    __shared__ int smin[32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    double m = 0.0;
-    for (int k = threadIdx.x; k < M; k += blockDim.x) m = fmax(m, fabs(g[k]));
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+// Operator choice and convergence (one CTA of SELECT_BS threads).  A
+// non-negative double orders like its bit pattern, so max |g| and the
+// threshold test run on the integer pipe (float64 compares and maxima each
+// hold the float64 pipe for a warp instruction's 64 cycles on this part);
+// NaN gradients are skipped.
+constexpr int SELECT_BS = 256;
+__global__ void __launch_bounds__(SELECT_BS) k_select(const double* g, int M, double eps, int prec, DevStep* step) {
+    constexpr int NW = SELECT_BS / 32;
+    constexpr unsigned long long kAbs = 0x7fffffffffffffffull, kInf = 0x7ff0000000000000ull;
+    __shared__ unsigned long long smax[NW];
+    __shared__ int smin[NW];
+    __shared__ unsigned long long thr_sh;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long m = 0;
+    for (int k = threadIdx.x; k < M; k += SELECT_BS) {
+        const unsigned long long a = (unsigned long long)__double_as_longlong(g[k]) & kAbs;
+        if (a <= kInf && a > m) m = a;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_down_sync(0xffffffffu, m, o);
+        m = v > m ? v : m;
+    }
     if (lane == 0) smax[wid] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double mm = 0.0;
-        for (int i = 0; i < nw; ++i) mm = fmax(mm, smax[i]);
+        unsigned long long mm = smax[0];
+        for (int i = 1; i < NW; ++i) mm = smax[i] > mm ? smax[i] : mm;
+        const double gmax = __longlong_as_double((long long)mm);
+        const double tau = prec == TQ_C128 ? 1e-9 * fmax(1.0, gmax) : 1e-5;
+        const double t = gmax - tau;
+        thr_sh = t > 0.0 ? (unsigned long long)__double_as_longlong(t) : 0ull;   // |g| >= gmax - tau
         smax[0] = mm;
     }
     __syncthreads();
-    const double gmax = smax[0];
-    const double tau = prec == TQ_C128 ? 1e-9 * fmax(1.0, gmax) : 1e-5;
+    const unsigned long long thr = thr_sh;
     int best = M;
-    for (int k = threadIdx.x; k < M; k += blockDim.x)
-        if (fabs(g[k]) >= gmax - tau && k < best) best = k;
+    for (int k = threadIdx.x; k < M; k += SELECT_BS) {
+        const unsigned long long a = (unsigned long long)__double_as_longlong(g[k]) & kAbs;
+        if (a <= kInf && a >= thr && k < best) best = k;
+    }
     for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_down_sync(0xffffffffu, best, o));
     if (lane == 0) smin[wid] = best;
     __syncthreads();
     if (threadIdx.x == 0) {
-        int b = M;
-        for (int i = 0; i < nw; ++i) b = min(b, smin[i]);
+        int b = smin[0];
+        for (int i = 1; i < NW; ++i) b = min(b, smin[i]);
+        const double gmax = __longlong_as_double((long long)smax[0]);
         step->selected = b < M ? b : 0;
         step->max_grad = gmax;
         step->converged = gmax < eps ? 1 : 0;
@@ -900,8 +923,31 @@ __device__ __forceinline__ double line_d2(const double* c, double s, double cc) 
     return -2 * s * c[1] + 2 * cc * c[2] + 2 * (cc * cc - s * s) * c[3] +
            2 * (3 * s * cc - s * u) * c[4] + 2 * (s * s + u * cc) * c[5];
 }
-__device__ __forceinline__ double sample_theta(int m) {
+__host__ __device__ __forceinline__ double sample_theta(int m) {
     return -kPi + 2.0 * kPi * (double)(m + 1) / 4096.0;
+}
+
+// sin and cos of theta0 + d from those of theta0 and the Taylor series of
+// sin d and cos d (angle addition).  The polish keeps |d| within one sample
+// spacing, 2 pi / 4096 < 1.6e-3, where the first omitted terms (d^9 / 9!,
+// d^10 / 10!) are below 1e-30: no float64 sincos per Newton step.
+__device__ __forceinline__ void sincos_near(double2 sc0, double d, double& s, double& c) {
+    const double q = d * d;
+    const double sd = d * fma(q, fma(q, fma(q, -1.0 / 5040.0, 1.0 / 120.0), -1.0 / 6.0), 1.0);
+    const double cd = fma(q, fma(q, fma(q, fma(q, 1.0 / 40320.0, -1.0 / 720.0), 1.0 / 24.0), -0.5), 1.0);
+    s = fma(sc0.x, cd, sc0.y * sd);
+    c = fma(sc0.y, cd, -(sc0.x * sd));
+}
+
+// Order-preserving int64 key of a double: the integer order of the keys is
+// the numeric order of the values (NaN last); key_value inverts it.
+__device__ __forceinline__ long long order_key(double v) {
+    if (v != v) return LLONG_MAX;
+    const long long b = __double_as_longlong(v);
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffll);
+}
+__device__ __forceinline__ double key_value(long long k) {
+    return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffll));
 }
 
 // sin and cos of the 4096 sample angles, computed once per context (float64
@@ -920,23 +966,21 @@ __global__ void k_line_table(double2* sc) {
 // smallest |theta| then lowest index, Newton polish within one spacing).
 // The samples are spread over LS_BLOCKS blocks, one per thread, from the
 // context's sin/cos table; the last block to finish (a ticket) takes the
-// minimum, applies the tie rule and polishes.
+// minimum, applies the tie rule and polishes.  Energies are kept as
+// order-preserving int64 keys, and the tie rule reads the context's rank
+// table (rank[m]: the position of sample m in the order (|theta_m|, m),
+// from the same float64 |theta_m|), so the minimum, the tolerance test and
+// the tie pick are integer work; the float64 pipe issues a warp
+// instruction only every 64 cycles on this part.
 constexpr int LS_BS = 256;
 constexpr int LS_BLOCKS = 4096 / LS_BS;
 
-// Of two sample indices (-1: none), the one the tie rule prefers.
-__device__ __forceinline__ int line_pick(int a, int b) {
-    if (a < 0) return b;
-    if (b < 0) return a;
-    const double ta = fabs(sample_theta(a)), tb = fabs(sample_theta(b));
-    return (tb < ta || (tb == ta && b < a)) ? b : a;
-}
-
 __global__ void __launch_bounds__(LS_BS)
 k_line_search(DevStep* step, double theta_given, const double* theta_list, const double2* __restrict__ sc,
-              double* se, unsigned* ticket) {
-    __shared__ double red[LS_BS / 32];
+              const int* __restrict__ rank, long long* se, unsigned* ticket) {
+    __shared__ long long red[LS_BS / 32];
     __shared__ int redi[LS_BS / 32];
+    __shared__ long long thr_sh;
     if (step->converged) return;                 // uniform over the grid
     if (theta_list) theta_given = theta_list[step->iter];
     if (!isnan(theta_given)) {
@@ -954,43 +998,48 @@ k_line_search(DevStep* step, double theta_given, const double* theta_list, const
     constexpr int NW = LS_BS / 32;
     const int m0 = blockIdx.x * LS_BS + threadIdx.x;
     const double2 t0 = sc[m0];
-    double mn = line_e_sc(c, t0.x, t0.y);
-    se[m0] = mn;
-    for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));
+    const long long key = order_key(line_e_sc(c, t0.x, t0.y));
+    se[m0] = key;
+    long long mn = key;
+    for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_down_sync(0xffffffffu, mn, o));
     if (lane == 0) red[wid] = mn;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double b = INFINITY;
-        for (int i = 0; i < NW; ++i) b = fmin(b, red[i]);
+        long long b = red[0];
+        for (int i = 1; i < NW; ++i) b = min(b, red[i]);
         se[4096 + blockIdx.x] = b;
     }
     __threadfence();                              // every sample visible before the ticket
     if (!last_block(ticket, gridDim.x)) return;
-    // the last block: global minimum, tie rule, polish
-    if (threadIdx.x == 0) {
-        double b = INFINITY;
-        for (int i = 0; i < LS_BLOCKS; ++i) b = fmin(b, __ldcg(se + 4096 + i));
-        red[0] = b;
+    // the last block: global minimum, tolerance, tie rule, polish
+    if (threadIdx.x < 32) {
+        long long b = threadIdx.x < LS_BLOCKS ? __ldcg(se + 4096 + threadIdx.x) : LLONG_MAX;
+        for (int o = 16; o > 0; o >>= 1) b = min(b, __shfl_down_sync(0xffffffffu, b, o));
+        if (threadIdx.x == 0) {
+            const double emin = key_value(b);
+            thr_sh = order_key(emin + 1e-10 * fmax(1.0, fabs(emin)));
+        }
     }
     __syncthreads();
-    const double emin = red[0];
-    const double tol = 1e-10 * fmax(1.0, fabs(emin));
-    int best = -1;
+    const long long thr = thr_sh;
+    int best = INT_MAX;   // rank * 4096 + m of the preferred sample within the tolerance
     for (int m = threadIdx.x; m < 4096; m += LS_BS)
-        if (__ldcg(se + m) <= emin + tol) best = line_pick(best, m);
-    for (int o = 16; o > 0; o >>= 1) best = line_pick(best, __shfl_down_sync(0xffffffffu, best, o));
+        if (__ldcg(se + m) <= thr) best = min(best, rank[m] * 4096 + m);
+    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_down_sync(0xffffffffu, best, o));
     if (lane == 0) redi[wid] = best;
     __syncthreads();
     if (threadIdx.x == 0) {
-        int b = -1;
-        for (int i = 0; i < NW; ++i) b = line_pick(b, redi[i]);
-        const double th0 = sample_theta(b);
-        const double e0 = __ldcg(se + b);
+        int b = redi[0];
+        for (int i = 1; i < NW; ++i) b = min(b, redi[i]);
+        const int mb = b & 4095;                  // the global minimum is always within the tolerance
+        const double th0 = sample_theta(mb);
+        const double2 s0 = sc[mb];
+        const double e0 = key_value(__ldcg(se + mb));
         const double h = 2.0 * kPi / 4096.0;
         double th = th0;
         for (int it = 0; it < 8; ++it) {
             double sn, cs;
-            sincos(th, &sn, &cs);
+            sincos_near(s0, th - th0, sn, cs);
             const double d2 = line_d2(c, sn, cs);
             if (!(d2 > 0.0)) break;
             const double stp = line_d1(c, sn, cs) / d2;
@@ -999,11 +1048,25 @@ k_line_search(DevStep* step, double theta_given, const double* theta_list, const
             th = nt;
             if (fabs(stp) < 1e-15) break;
         }
-        if (line_e(c, th) > e0) th = th0;
+        double sn, cs;
+        sincos_near(s0, th - th0, sn, cs);
+        if (line_e_sc(c, sn, cs) > e0) th = th0;
         step->theta = th;
         *ticket = 0u;
     }
 }
+
+}  // namespace
+
+void line_rank_table(int* rank) {
+    std::vector<int> idx(4096);
+    for (int m = 0; m < 4096; ++m) idx[m] = m;
+    std::stable_sort(idx.begin(), idx.end(),
+                     [](int a, int b) { return std::fabs(sample_theta(a)) < std::fabs(sample_theta(b)); });
+    for (int i = 0; i < 4096; ++i) rank[idx[i]] = i;
+}
+
+namespace {
 
 int grid_rows(long long D, int rows_per_block, int sms, int per_sm) {
     long long g = (D + rows_per_block - 1) / rows_per_block;
@@ -1156,7 +1219,7 @@ int launch_pool_gradients(const PoolView& p, const double2* w, const float2* w32
 }
 
 int launch_select(const double* g, int M, double eps, int prec, DevStep* step, cudaStream_t s) {
-    k_select<<<1, 1024, 0, s>>>(g, M, eps, prec, step);
+    k_select<<<1, SELECT_BS, 0, s>>>(g, M, eps, prec, step);
     return 1;
 }
 
@@ -1260,9 +1323,9 @@ int launch_line_table(double2* sc, cudaStream_t s) {
     return 1;
 }
 
-int launch_line_search(DevStep* step, double theta_given, const double* theta_list, const double2* sc, double* se,
-                       unsigned* ticket, cudaStream_t s) {
-    k_line_search<<<LS_BLOCKS, LS_BS, 0, s>>>(step, theta_given, theta_list, sc, se, ticket);
+int launch_line_search(DevStep* step, double theta_given, const double* theta_list, const double2* sc,
+                       const int* rank, long long* se, unsigned* ticket, cudaStream_t s) {
+    k_line_search<<<LS_BLOCKS, LS_BS, 0, s>>>(step, theta_given, theta_list, sc, rank, se, ticket);
     return 1;
 }
 
