@@ -233,7 +233,8 @@ extern "C" int tq_autotune_support(tq_ctx* c, const tq_pool* p, int prec, int n_
         const int tps = support_tiles(p->nq, n_states, u, c->sm_count);
         auto once = [&] {
             launch(c, "autotune_support", 0, [&] {
-                return launch_taylor5_support(p->view, n_states, prec, u, psi, dk, dth, part, tps, dn, c->sm_count, 0);
+                return launch_taylor5_support(p->view, n_states, prec, u, psi, dk, dth, part, tps, dn, c->sm_count, 0,
+                                              0, c->tickets + TICKET_SUPPORT_SCHED);
             });
             if (tps > 1)
                 launch(c, "autotune_support", 0, [&] {

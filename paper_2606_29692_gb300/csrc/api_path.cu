@@ -341,7 +341,7 @@ extern "C" int tq_evolve_taylor5_batch_support(tq_ctx* c, const tq_pool* p, int 
     double* part = static_cast<double*>(scratch(c, S_PART, (size_t)n_states * parts * sizeof(double)));
     launch(c, "taylor5_support", s, [&] {
         return launch_taylor5_support(p->view, n_states, prec, ppt, psi, k, theta, part, tps, norm2, c->sm_count, s,
-                                      c->supp_ctas[prec]);
+                                      c->supp_ctas[prec], c->tickets + TICKET_SUPPORT_SCHED);
     });
     if (norm2 && tps > 1)
         launch(c, "norm_carry", s, [&] { return launch_norm_carry(part, prec, n_states, parts, norm2, norm2, nullptr, s); });
@@ -387,7 +387,7 @@ extern "C" int tq_evolve_taylor5_batch_support_host(tq_ctx* c, const tq_pool* p,
     double* n2 = norm2_host ? dn : nullptr;
     launch(c, "taylor5_support_host", s, [&] {
         return launch_taylor5_support(p->view, n_states, prec, ppt, psi, dk, dth, part, tps, n2, c->sm_count, s,
-                                      c->supp_ctas[prec]);
+                                      c->supp_ctas[prec], c->tickets + TICKET_SUPPORT_SCHED);
     });
     if (n2 && tps > 1)
         launch(c, "norm_carry", s, [&] { return launch_norm_carry(part, prec, n_states, parts, n2, n2, nullptr, s); });

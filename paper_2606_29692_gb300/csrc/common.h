@@ -219,9 +219,12 @@ int launch_taylor5_grouped(const PoolView& p, int n_groups, int prec, int lanes_
                            void* psi, const int* k, const double* theta, double* norm2, int sms, cudaStream_t s);
 int support_tiles(int nq, int n_states, int ppt, int sms);
 int support_parts(int tiles);
+// sched (device, two counters at zero, left at zero; may be null): with
+// one tile per state and norm2 set, the pipelined forms hand out states
+// dynamically instead of by a fixed stride.
 int launch_taylor5_support(const PoolView& p, int n_states, int prec, int ppt, void* psi, const int* k,
                            const double* theta, double* partials, int tps, double* norm2, int sms,
-                           cudaStream_t s, int ctas_per_sm = 0);
+                           cudaStream_t s, int ctas_per_sm = 0, unsigned* sched = nullptr);
 int launch_scale(void* psi, int prec, long long D, const double* norm2, cudaStream_t s);
 
 // Taylor-5 for a general CSR operator.
@@ -324,6 +327,11 @@ int launch_apply_twice_sector(const PoolView& p, const DevStep* step, const void
 }  // namespace tq
 
 // ------------------------------------------------------------------- handles
+
+// Slots of the context's ticket array (zero between calls): 0 energy, 1
+// matrix-free energy, 2 line dots, 3 line search, 4 ansatz gradient, 8-9
+// the support update's dynamic state counters, 16.. gradients.
+constexpr int TICKET_SUPPORT_SCHED = 8;
 
 struct tq_trace_rec {
     const char* name;

@@ -376,12 +376,22 @@ __device__ __forceinline__ void warp0_finish(const double* red, double* norm2) {
 // barrier, then warp 0 adds them to norm2[b] (warp0_finish) while the
 // other warps start the next tile, whose partials go to the other buffer;
 // warp 0 reaches that tile's barrier only after reading this one.
+// In that form, with `sched` set, states are handed out dynamically: a
+// single costs four times a double, so a fixed stride leaves the CTAs that
+// drew more singles running long after the rest (a spread of about 17 % per
+// CTA over 18 states).  Thread 0 requests the state after next from
+// sched[0] while the current one is processed, and the per-state barrier
+// publishes it; the last CTA to finish (sched[1]) sets both counters back
+// to zero for the next launch.  The request goes to one of two shared
+// slots alternately (the norm buffers' parity), so each write is separated
+// by a barrier from every read of the value it replaces.
 // Complex64 with one or two pairs per thread keeps five CTAs per SM (48
-// registers, no spills); the other forms take what they need.
+// registers, no spills), with four pairs three (80); the other forms take
+// what they need.
 template <typename T, int PPT>
-__global__ void __launch_bounds__(SUPP_BS, (sizeof(T) == 4 && PPT <= 2) ? 5 : 1)
+__global__ void __launch_bounds__(SUPP_BS, sizeof(T) == 4 ? (PPT <= 2 ? 5 : (PPT == 4 ? 3 : 1)) : 1)
 k_taylor5_support_pipe(PoolView p, int n_states, typename C2<T>::type* psi, const int* kk, const double* th,
-                       double* partials, int tiles_per_state, double* norm2) {
+                       double* partials, int tiles_per_state, double* norm2, unsigned* sched) {
     using V = typename C2<T>::type;
     extern __shared__ __align__(16) unsigned char supp_smem[];
     V* stages = reinterpret_cast<V*>(supp_smem);    // [2][PPT][2][SUPP_BS]
@@ -389,15 +399,29 @@ k_taylor5_support_pipe(PoolView p, int n_states, typename C2<T>::type* psi, cons
     constexpr int STAGE = 2 * PPT * SUPP_BS;
     uint32_t* rowbuf = reinterpret_cast<uint32_t*>(stages + 2 * STAGE);   // [2][PPT][SUPP_BS]
     __shared__ double red[2][NW];
+    __shared__ unsigned next_sh[2];
     int rp = 0;
     const int warp = threadIdx.x >> 5;
     const bool fold = tiles_per_state == 1 && norm2 != nullptr;
+    const bool dyn = fold && sched != nullptr;        // uniform
     const long long D = 1ll << p.nq;
     const unsigned tps = (unsigned)tiles_per_state;
     const int lt = __ffs(tiles_per_state) - 1;        // tps is a power of two
     const unsigned total = (unsigned)n_states * tps;
     unsigned tile = blockIdx.x;
-    if (tile >= total) return;
+    if (tile >= total) {                              // not with the launcher's grid (at most one CTA per tile)
+        if (dyn && threadIdx.x == 0 && atomicAdd(sched + 1, 1u) == gridDim.x - 1) {
+            atomicExch(sched, 0u);
+            atomicExch(sched + 1, 0u);
+        }
+        return;
+    }
+    unsigned queued = tile + gridDim.x;               // the tile after the current one
+    if (dyn) {
+        if (threadIdx.x == 0) next_sh[1] = gridDim.x + atomicAdd(sched, 1u);
+        __syncthreads();
+        queued = next_sh[1];
+    }
     SupTile<T> cur = sup_tile<T>(p, kk, th, tile, lt);
     uint32_t pos = cur.i0;
     int st = 0;
@@ -408,8 +432,10 @@ k_taylor5_support_pipe(PoolView p, int n_states, typename C2<T>::type* psi, cons
         // the next pass: later in this tile, or the first of the next tile
         uint32_t npos = pos + SUPP_BS * PPT;
         const bool tile_end = cur.bad || npos >= cur.i1;
-        const unsigned ntile = tile_end ? tile + gridDim.x : tile;
+        const unsigned ntile = tile_end ? queued : tile;
         const bool more = ntile < total;
+        // the request for the tile after ntile overlaps this pass
+        if (dyn && tile_end && more && threadIdx.x == 0) next_sh[rp] = gridDim.x + atomicAdd(sched, 1u);
         SupTile<T> nxt = cur;
         if (tile_end && more) {
             nxt = sup_tile<T>(p, kk, th, ntile, lt);
@@ -430,8 +456,11 @@ k_taylor5_support_pipe(PoolView p, int n_states, typename C2<T>::type* psi, cons
             delta = T(0);
             if (fold) {
                 __syncthreads();
+                if (dyn && more) queued = next_sh[rp];   // written before the barrier
                 if (warp == 0) warp0_finish<T, NW>(red[rp], norm2 + cur.b);
                 rp ^= 1;
+            } else {
+                queued = ntile + gridDim.x;
             }
         }
         if (!more) break;
@@ -440,11 +469,20 @@ k_taylor5_support_pipe(PoolView p, int n_states, typename C2<T>::type* psi, cons
         pos = npos;
         st ^= 1;
     }
+    if (dyn && threadIdx.x == 0) {
+        // every request of this CTA has returned; the last CTA to get here
+        // resets the counters for the next launch
+        if (atomicAdd(sched + 1, 1u) == gridDim.x - 1) {
+            atomicExch(sched, 0u);
+            atomicExch(sched + 1, 0u);
+        }
+    }
 }
 
 template <typename T, int PPT>
 int launch_support_pipe(const PoolView& p, int n_states, void* psi, const int* k, const double* theta,
-                        double* partials, int tps, double* norm2, int sms, int ctas, cudaStream_t s) {
+                        double* partials, int tps, double* norm2, int sms, int ctas, cudaStream_t s,
+                        unsigned* sched) {
     using V = typename C2<T>::type;
     const long long total = (long long)n_states * tps;
     if (total >= (1ll << 31)) return -1;
@@ -460,7 +498,7 @@ int launch_support_pipe(const PoolView& p, int n_states, void* psi, const int* k
     if (grid > total) grid = total;
     if (grid < 1) grid = 1;
     k_taylor5_support_pipe<T, PPT><<<(int)grid, SUPP_BS, smem, s>>>(p, n_states, static_cast<V*>(psi), k, theta,
-                                                                     partials, tps, norm2);
+                                                                     partials, tps, norm2, sched);
     return 1;
 }
 
@@ -486,16 +524,17 @@ int launch_support(const PoolView& p, int n_states, void* psi, const int* k, con
 
 template <typename T>
 int dispatch_support(int ppt, const PoolView& p, int n_states, void* psi, const int* k, const double* theta,
-                     double* partials, int tps, double* norm2, int sms, int ctas, cudaStream_t s) {
+                     double* partials, int tps, double* norm2, int sms, int ctas, cudaStream_t s,
+                     unsigned* sched) {
     switch (ppt) {
         case 1: return launch_support<T, 1>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s);
         case 2: return launch_support<T, 2>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s);
         case 4: return launch_support<T, 4>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s);
         case 8: return launch_support<T, 8>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s);
-        case -1: return launch_support_pipe<T, 1>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s);
-        case -2: return launch_support_pipe<T, 2>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s);
-        case -4: return launch_support_pipe<T, 4>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s);
-        case -8: return launch_support_pipe<T, 8>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s);
+        case -1: return launch_support_pipe<T, 1>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s, sched);
+        case -2: return launch_support_pipe<T, 2>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s, sched);
+        case -4: return launch_support_pipe<T, 4>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s, sched);
+        case -8: return launch_support_pipe<T, 8>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s, sched);
         default: return -1;
     }
 }
@@ -523,11 +562,13 @@ int support_parts(int tiles) { return tiles * (SUPP_BS / 32); }
 
 int launch_taylor5_support(const PoolView& p, int n_states, int prec, int ppt, void* psi, const int* k,
                            const double* theta, double* partials, int tps, double* norm2, int sms,
-                           cudaStream_t s, int ctas_per_sm) {
+                           cudaStream_t s, int ctas_per_sm, unsigned* sched) {
     if (tps < 1 || (tps & (tps - 1)) != 0) return -1;   // the kernels split by shifts
     if (prec == TQ_C128)
-        return dispatch_support<double>(ppt, p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas_per_sm, s);
-    return dispatch_support<float>(ppt, p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas_per_sm, s);
+        return dispatch_support<double>(ppt, p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas_per_sm, s,
+                                        sched);
+    return dispatch_support<float>(ppt, p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas_per_sm, s,
+                                   sched);
 }
 
 }  // namespace tq
