@@ -492,6 +492,15 @@ def run_ours(args, rank, world, local_rank):
         tq.evolve_taylor5_batch_support(ctx, pool, psi, dk, dth, dn)
         applied[0] += 1
 
+    # the clock sampler starts now, so that it samples under load and the GPU
+    # never idles between the tuning, the warm-up and the timed region (a
+    # GPU left idle for a fraction of a second runs its next launches slower)
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local_rank).uuid)
+    except Exception:
+        gpu_id = str(local_rank)
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
     tune = {}
     for fetch in ([args.l2_fetch] if args.l2_fetch else [32, 64]):
         ctx.set_l2_fetch(fetch)
@@ -512,18 +521,17 @@ def run_ours(args, rank, world, local_rank):
     def max_over_ranks(x):
         return tqd.max_over_ranks(x, device="cuda")
 
+    # untimed steps until the sampler has three samples under load (at most 2 s)
+    t_wait = time.time() + 2.0
+    while clocks.proc is not None and len(clocks.lines) < 3 and time.time() < t_wait:
+        for _ in range(20):
+            step()
+        torch.cuda.synchronize()
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
-    try:
-        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local_rank).uuid)
-    except Exception:
-        gpu_id = str(local_rank)
-    clocks = ClockSampler(gpu_id)
-    clocks.start()
-    time.sleep(0.3)
     # the timed region: K steps, one launch each, no per-launch events (a
     # recorded event between launches adds a few microseconds of gap)
     launches0 = ctx.launches()
