@@ -169,22 +169,34 @@ __device__ __forceinline__ T support_tile(const SupOp<T>& op, const T (&cf)[6], 
 // complex128 with one tile per state, thread 0 also works out the next
 // tile's coefficients between the norm's two barriers, once per CTA: the
 // float64 pipe is this kernel's limit, and every warp would otherwise
-// repeat them.
+// repeat them.  With `sched` (and one tile per state, norm2 set) states
+// are handed out dynamically, as in the pipelined form below: thread 0
+// requests the state after next at the top of each state, and the value is
+// read after the state's first barrier (the second barrier separates that
+// read from the next request).
 template <typename T, int PPT>
 __global__ void __launch_bounds__(SUPP_BS)
 k_taylor5_support(PoolView p, int n_states, typename C2<T>::type* psi, const int* kk, const double* th,
-                  double* partials, int tiles_per_state, double* norm2) {
+                  double* partials, int tiles_per_state, double* norm2, unsigned* sched) {
     const int warp = threadIdx.x >> 5;
     constexpr int NW = SUPP_BS / 32;
     __shared__ double red[NW];
     __shared__ double sc[N_COEF];
+    __shared__ unsigned next_sh;
     const bool fold = tiles_per_state == 1 && norm2 != nullptr;
+    const bool dyn = fold && sched != nullptr;        // uniform
     constexpr bool wide = sizeof(T) == 8;
     const long long D = 1ll << p.nq;
     const unsigned tps = (unsigned)tiles_per_state;
     const int lt = __ffs(tiles_per_state) - 1;        // tps is a power of two
     const unsigned total = (unsigned)n_states * tps;
     unsigned tile = blockIdx.x;
+    unsigned queued = tile + gridDim.x;               // the tile after the current one
+    if (dyn) {
+        if (threadIdx.x == 0) next_sh = tile < total ? gridDim.x + atomicAdd(sched, 1u) : total;
+        __syncthreads();
+        queued = next_sh;
+    }
     int b = (int)(tile >> lt);
     int k = tile < total ? kk[b] : 0;
     double theta = tile < total ? th[b] : 0.0;
@@ -194,7 +206,8 @@ k_taylor5_support(PoolView p, int n_states, typename C2<T>::type* psi, const int
     }
     while (tile < total) {
         const unsigned tl = tile & (tps - 1);
-        const unsigned ntile = tile + gridDim.x;
+        const unsigned ntile = queued;
+        if (dyn && threadIdx.x == 0 && ntile < total) next_sh = gridDim.x + atomicAdd(sched, 1u);
         const int nb = (int)(ntile >> lt);
         int nk = 0;
         double nth = 0.0;
@@ -233,18 +246,26 @@ k_taylor5_support(PoolView p, int n_states, typename C2<T>::type* psi, const int
         }
         if (fold) {
             __syncthreads();   // the partials are in red, and every thread has read sc
+            if (dyn && ntile < total) queued = next_sh;
             if (threadIdx.x == 0) {
                 norm2[b] = norm2[b] + sum_partials<T, NW>(red);
                 if (wide && ntile < total) tile_coefs(nth, sc);
             }
             __syncthreads();
         }
+        if (!dyn) queued = ntile + gridDim.x;
         tile = ntile;
         b = nb;
         k = nk;
         theta = nth;
     }
+    if (dyn && threadIdx.x == 0 && atomicAdd(sched + 1, 1u) == gridDim.x - 1) {
+        atomicExch(sched, 0u);       // every request has returned: reset for the next launch
+        atomicExch(sched + 1, 0u);
+    }
 }
+
+
 
 // ------------------------------------------------ pipelined (cp.async) form
 //
@@ -504,7 +525,7 @@ int launch_support_pipe(const PoolView& p, int n_states, void* psi, const int* k
 
 template <typename T, int PPT>
 int launch_support(const PoolView& p, int n_states, void* psi, const int* k, const double* theta,
-                   double* partials, int tps, double* norm2, int sms, int ctas, cudaStream_t s) {
+                   double* partials, int tps, double* norm2, int sms, int ctas, cudaStream_t s, unsigned* sched) {
     using V = typename C2<T>::type;
     const long long total = (long long)n_states * tps;
     if (total >= (1ll << 31)) return -1;
@@ -518,7 +539,7 @@ int launch_support(const PoolView& p, int n_states, void* psi, const int* k, con
     if (grid > total) grid = total;
     if (grid < 1) grid = 1;
     k_taylor5_support<T, PPT><<<(int)grid, SUPP_BS, 0, s>>>(p, n_states, static_cast<V*>(psi), k, theta,
-                                                             partials, tps, norm2);
+                                                             partials, tps, norm2, sched);
     return 1;
 }
 
@@ -527,10 +548,10 @@ int dispatch_support(int ppt, const PoolView& p, int n_states, void* psi, const 
                      double* partials, int tps, double* norm2, int sms, int ctas, cudaStream_t s,
                      unsigned* sched) {
     switch (ppt) {
-        case 1: return launch_support<T, 1>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s);
-        case 2: return launch_support<T, 2>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s);
-        case 4: return launch_support<T, 4>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s);
-        case 8: return launch_support<T, 8>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s);
+        case 1: return launch_support<T, 1>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s, sched);
+        case 2: return launch_support<T, 2>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s, sched);
+        case 4: return launch_support<T, 4>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s, sched);
+        case 8: return launch_support<T, 8>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s, sched);
         case -1: return launch_support_pipe<T, 1>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s, sched);
         case -2: return launch_support_pipe<T, 2>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s, sched);
         case -4: return launch_support_pipe<T, 4>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas, s, sched);
