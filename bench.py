@@ -88,9 +88,10 @@ def kernel_source_hash(sources):
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(profile, n_states):
+def profiled_traffic(profile, n_states, layout=None):
     """DRAM bytes per launch from a committed ncu summary, if the kernel's
-    sources still hash to the value the summary records."""
+    sources still hash to the value the summary records and, when the
+    summary names the states' memory layout, the run uses the same one."""
     path, sources = profile
     if not os.path.exists(path):
         return None
@@ -98,6 +99,9 @@ def profiled_traffic(profile, n_states):
     m = re.search(r"traffic_bytes_per_state:\s*([0-9.eE+]+)", txt)
     h = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", txt)
     if not m or not h or h.group(1) != kernel_source_hash(sources):
+        return None
+    lay = re.search(r"state_layout:\s*(\w+)", txt)
+    if lay and layout is not None and lay.group(1) != layout:
         return None
     return float(m.group(1)) * n_states
 
@@ -459,17 +463,30 @@ def run_ours(args, rank, world, local_rank):
     S = args.states
     ctx = tq.Context(local_rank)
     pool_nat = tq.build_pool(ctx, N_SPATIAL, N_ELECTRONS, MAPPING)
-    # the states' memory layout: BK with its qubits relabelled so that the
-    # pool's supports fill the lowest index bits (32-byte sectors), or BK's
-    # own qubit order; every result is the same up to the index relabelling
-    if args.layout == "sector":
+    # the states' memory layout: BK with its basis index carried by an
+    # invertible GF(2) map (linear) or a qubit order (sector) chosen so that
+    # the pool's supports fill the lowest index bits (32-byte sectors), or
+    # BK's own order; every result is the same up to the index map
+    if args.layout == "linear":
+        lrows = tq.pool_sector_basis(N_SPATIAL, N_ELECTRONS, MAPPING, args.layout_bits)
+        mp_run = tq.mapping_linear(MAPPING, lrows)
+        index_map = tq.linear_index(lrows)
+        layout_desc = {"kind": "linear", "rows": [int(r) for r in lrows],
+                       "note": "Bravyi-Kitaev with basis index r stored at r' = M r over GF(2), bit i of r' the "
+                               "parity of r over rows[i] (tq_mapping_linear, rows from tq_pool_sector_basis): "
+                               "the same encoding's results, the pool's supports packed into 32-byte sectors"}
+    elif args.layout == "sector":
         order = tq.pool_sector_order(N_SPATIAL, N_ELECTRONS, MAPPING, args.layout_bits)
         mp_run = tq.mapping_relabelled(MAPPING, order)
-        pool = tq.build_pool(ctx, N_SPATIAL, N_ELECTRONS, mp_run)
+        index_map = tq.relabel_index(order)
+        layout_desc = {"kind": "sector", "bit_of_qubit": [int(o) for o in order],
+                       "note": "Bravyi-Kitaev with qubit k stored at index bit bit_of_qubit[k] "
+                               "(tq_mapping_relabelled, order from tq_pool_sector_order)"}
     else:
-        order = np.arange(NQ)
         mp_run = MAPPING
-        pool = pool_nat
+        index_map = np.arange(D)
+        layout_desc = {"kind": "natural", "note": "Bravyi-Kitaev's own qubit order"}
+    pool = pool_nat if mp_run == MAPPING else tq.build_pool(ctx, N_SPATIAL, N_ELECTRONS, mp_run)
     # every rank updates its own batch of S states (weak scaling, no exchange)
     prep_k, prep_th, k, th = synth.t5_batch(S, pool.M, seed=tqd.rank_seed(synth.SEED_T5_BATCH, rank))
     hf = tq.hf_index(NQ, N_ELECTRONS, mp_run)
@@ -574,7 +591,7 @@ def run_ours(args, rank, world, local_rank):
     line_bytes = float((128 * n_line + 32 * n_sect).sum())      # reads by line, writes by sector
     peak, peak_src = peaks()
     achieved = alg_bytes / sup_s / 1e9
-    traffic = profiled_traffic(PROFILE_SUPPORT, S)
+    traffic = profiled_traffic(PROFILE_SUPPORT, S, args.layout)
 
     # end to end: the same update on states in pinned host memory, through
     # the host-memory entry point (the kernel reads and writes each state's
@@ -636,9 +653,16 @@ def run_ours(args, rank, world, local_rank):
         idx = np.linspace(0, S - 1, args.fidelity_samples).astype(np.int64).tolist()
         # the oracle's BK order: amplitude b of the oracle is at relabel[b]
         extra["headline_vs_oracle"] = headline_fidelity(psi, dn, idx, S, tqd.rank_seed(synth.SEED_T5_BATCH, rank),
-                                                        applied[0], tq.relabel_index(order))
-    if rank == 0 and args.layout == "sector":
-        extra["natural_layout"] = measure_natural_layout(tq, ctx, pool_nat, S, k, th, prep_k, prep_th, sup_s)
+                                                        applied[0], index_map)
+    if rank == 0 and args.layout != "natural":
+        extra["natural_layout"] = measure_layout(tq, ctx, pool_nat, MAPPING, "BK's own qubit order", S, k, th,
+                                                 prep_k, prep_th, sup_s)
+    if rank == 0 and args.layout == "linear":
+        order = tq.pool_sector_order(N_SPATIAL, N_ELECTRONS, MAPPING, args.layout_bits)
+        mp_o = tq.mapping_relabelled(MAPPING, order)
+        extra["qubit_order_layout"] = measure_layout(
+            tq, ctx, tq.build_pool(ctx, N_SPATIAL, N_ELECTRONS, mp_o), mp_o,
+            "BK with its qubits reordered for sector fill (tq_pool_sector_order)", S, k, th, prep_k, prep_th, sup_s)
         extra["grouped_layout"] = measure_grouped_layout(tq, ctx, pool, psi, dn, k, th, sup_s,
                                                          mapping=mp_run)
     pool = pool_nat   # the other sections use BK's own qubit order
@@ -670,12 +694,7 @@ def run_ours(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "c64",
             "data": "synthetic",
             "config": dict(workload_config(S),
-                           qubit_layout={"kind": args.layout,
-                                         "bit_of_qubit": [int(o) for o in order],
-                                         "note": "Bravyi-Kitaev with qubit k stored at index bit bit_of_qubit[k] "
-                                                 "(tq_mapping_relabelled, order from tq_pool_sector_order): "
-                                                 "the same encoding and results, the pool's supports packed "
-                                                 "into 32-byte sectors"},
+                           qubit_layout=layout_desc,
                            schedule={"support_pairs_per_thread": upt,
                                                          "ms_per_launch_by_schedule": tune_ms,
                                                          "l2_fetch_bytes": best_fetch,
@@ -726,13 +745,14 @@ def time_launches(fn, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def measure_natural_layout(tq, ctx, pool, n_states, k, th, prep_k, prep_th, ms_relabelled, reps=50):
-    """The headline batch in BK's own qubit order (no relabelling): the same
-    states, generators and angles, the same support-only kernel, every
-    schedule timed at 32-byte L2 fetches and the fastest kept."""
+def measure_layout(tq, ctx, pool, mapping, label, n_states, k, th, prep_k, prep_th, s_headline, reps=50):
+    """The headline batch in another memory layout (mapping: BK's own order
+    or another relabelling): the same states, generators and angles, the
+    same support-only kernel, every schedule timed at 32-byte L2 fetches
+    and the fastest kept."""
     import numpy as np
     import torch
-    hf = tq.hf_index(NQ, N_ELECTRONS, MAPPING)
+    hf = tq.hf_index(NQ, N_ELECTRONS, mapping)
     psi = torch.zeros((n_states, D), dtype=torch.complex64, device="cuda")
     psi[:, hf] = 1.0
     dn = torch.ones(n_states, dtype=torch.float64, device="cuda")
@@ -755,19 +775,19 @@ def measure_natural_layout(tq, ctx, pool, n_states, k, th, prep_k, prep_th, ms_r
     ctx.set_support_occupancy(tq.TQ_C64, 0)
     best = min(per, key=per.get)
     ms = per[best]
-    rows = support_rows(tq, N_SPATIAL, N_ELECTRONS, MAPPING)
+    rows = support_rows(tq, N_SPATIAL, N_ELECTRONS, mapping)
     n_rows = np.array([r.size for r in rows], dtype=np.float64)[k]
     n_sect = np.array([np.unique(r >> 2).size for r in rows], dtype=np.float64)[k]
     alg = float((16 * n_rows).sum() + 16 * n_states)
     sect = float((64 * n_sect).sum() + 16 * n_states)
     peak, _ = peaks()
-    return {"workload": "the headline batch in BK's own qubit order",
+    return {"workload": f"the headline batch in {label}",
             "ctas_per_sm": best[0] or "as many as fit", "pairs_per_thread": best[1],
             "ms_per_launch": ms, "ms_by_schedule": {f"{o_ or 'max'}cta/{p_}": v for (o_, p_), v in per.items()},
             "updates_per_s": n_states / (ms * 1e-3),
             "algorithmic_bytes_per_launch": alg, "sector_bytes_per_launch": sect,
             "frac": alg / (ms * 1e-3) / 1e9 / peak, "sector_frac": sect / (ms * 1e-3) / 1e9 / peak,
-            "relabelled_speedup": ms / (ms_relabelled * 1e3)}
+            "headline_layout_speedup": ms / (s_headline * 1e3)}
 
 
 def measure_grouped_layout(tq, ctx, pool, psi, dn, k, th, s_flat, mapping, reps=50):
@@ -1826,10 +1846,11 @@ def main():
                     help="L2 fetch granularity of the headline (0 = tuned)")
     ap.add_argument("--ctas-per-sm", type=int, default=-1,
                     help="resident CTAs per SM of the headline update (-1 = tuned, 0 = as many as fit)")
-    ap.add_argument("--layout", choices=["sector", "natural"], default="sector",
-                    help="states in BK's qubit order relabelled for sector fill, or in BK's own order")
+    ap.add_argument("--layout", choices=["linear", "sector", "natural"], default="linear",
+                    help="states in BK with the index carried by a GF(2) map chosen for sector fill (linear), "
+                         "with its qubits reordered for it (sector), or in BK's own order")
     ap.add_argument("--layout-bits", type=int, default=14,
-                    help="index bits the sector-packing qubit order fills (tq_pool_sector_order)")
+                    help="index bits the sector-packing map fills (tq_pool_sector_basis / tq_pool_sector_order)")
     ap.add_argument("--fidelity-samples", type=int, default=64,
                     help="headline states checked against the oracle after the run (0 skips)")
     ap.add_argument("--pair-schedule", type=int, default=0,

@@ -133,6 +133,41 @@ def relabel_index(order):
     return out
 
 
+def mapping_linear(base_mapping, rows):
+    """Id of the JW/BK encoding whose basis index r is carried to r' by the
+    invertible GF(2) map with the given rows (bit i of r' = parity of r over
+    rows[i]); a memory layout, every result is the base mapping's."""
+    r = np.ascontiguousarray(rows, dtype=np.uint64)
+    out = C.c_int()
+    call("tq_mapping_linear", int(base_mapping), int(r.size), _ptr(r), C.byref(out))
+    return out.value
+
+
+def pool_sector_basis(n_spatial, n_electrons, base_mapping, low_bits=None):
+    """Rows of an index map for mapping_linear that packs the pool's
+    supports into whole 32-byte sectors (greedy over all GF(2) vectors)."""
+    n = 2 * n_spatial
+    r = np.zeros(n, dtype=np.uint64)
+    call("tq_pool_sector_basis", int(n_spatial), int(n_electrons), int(base_mapping),
+         int(n if low_bits is None else low_bits), _ptr(r))
+    return r
+
+
+def linear_index(rows):
+    """New index of every base-mapping basis index under mapping_linear's
+    map: bit i of out[b] is the parity of b over rows[i] (a state moves by
+    psi_new[out] = psi)."""
+    rows = np.asarray(rows, dtype=np.int64)
+    b = np.arange(1 << rows.size, dtype=np.int64)
+    out = np.zeros_like(b)
+    for i, r in enumerate(rows):
+        v = b & r
+        for s in (32, 16, 8, 4, 2, 1):
+            v ^= v >> s
+        out |= (v & 1) << i
+    return out
+
+
 def hf_index(n_qubits, n_electrons, mapping):
     out = C.c_longlong()
     call("tq_hf_index", n_qubits, n_electrons, mapping, C.byref(out))

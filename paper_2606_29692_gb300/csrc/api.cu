@@ -456,6 +456,25 @@ extern "C" int tq_pool_sector_order(int n_spatial, int n_electrons, int base_map
     API_END
 }
 
+extern "C" int tq_mapping_linear(int base_mapping, int n_qubits, const unsigned long long* rows, int* mapping_out) {
+    API_BEGIN
+    TQ_REQUIRE(rows && mapping_out, "null argument");
+    TQ_REQUIRE(n_qubits >= 1 && n_qubits <= 2 * TQ_MAX_SPATIAL, "n_qubits out of range [1, 30]");
+    std::vector<uint64_t> r(rows, rows + n_qubits);
+    *mapping_out = register_linear(base_mapping, n_qubits, r.data());
+    API_END
+}
+
+extern "C" int tq_pool_sector_basis(int n_spatial, int n_electrons, int base_mapping, int low_bits,
+                                    unsigned long long* rows_out) {
+    API_BEGIN
+    TQ_REQUIRE(rows_out, "null argument");
+    TQ_REQUIRE(n_spatial >= 1 && n_spatial <= TQ_MAX_SPATIAL, "n_spatial out of range [1, 15]");
+    const auto m = pool_sector_basis(n_spatial, n_electrons, base_mapping, low_bits);
+    std::copy(m.begin(), m.end(), rows_out);
+    API_END
+}
+
 extern "C" int tq_hf_index(int n_qubits, int n_electrons, int mapping, long long* index) {
     API_BEGIN
     TQ_REQUIRE(index != nullptr, "index is null");

@@ -64,6 +64,8 @@ SupportForm support_form(const SignForm& f, uint64_t x);
 void check_mapping(int mapping);
 // Registers (or finds) the relabelled encoding base + order; returns its id.
 int register_relabelled(int base, int N, const int* order);
+int register_linear(int base, int N, const uint64_t* rows);
+std::vector<uint64_t> pool_sector_basis(int n, int ne, int base, int low_bits);
 // Qubit order whose lowest low_bits index bits are the qubits, picked one at
 // a time, that leave the fewest touched segments over the pool's supports.
 std::vector<int> pool_sector_order(int n, int ne, int base, int low_bits);

@@ -29,13 +29,16 @@ namespace tq {
 
 namespace {
 
-// Relabelled encodings: a base mapping (JW or BK) whose qubit k is stored at
-// bit order[k] of the basis index.  Registered once per process, never
-// removed; ids from TQ_MAPPING_FIRST_RELABELLED on.
+// Relabelled encodings: a base mapping (JW or BK) whose basis index is
+// carried to another by an invertible linear map M over GF(2): bit i of the
+// new index is the parity of the base index over rows[i] (a qubit
+// permutation is the special case of one bit per row).  The encoding matrix
+// becomes B' = M B.  Registered once per process, never removed; ids from
+// TQ_MAPPING_FIRST_RELABELLED on.
 struct Relabelled {
     int base;
     int N;
-    std::vector<int> order;
+    std::vector<uint64_t> rows;
 };
 std::mutex g_relabel_mutex;
 std::vector<Relabelled> g_relabelled;
@@ -77,9 +80,17 @@ Enc make_encoding(int N, int mapping) {
             for (int i = lo; i <= k; ++i) base_rows[k] |= 1ull << i;
         }
     }
-    // a relabelling moves qubit k's row to bit order[k]: B' = P B
+    // a relabelling combines the base rows: row i of B' = M B is the xor of
+    // the base rows that row i of M selects
     std::vector<uint64_t> rows(N, 0);
-    for (int k = 0; k < N; ++k) rows[relabel ? rl.order[k] : k] = base_rows[k];
+    for (int i = 0; i < N; ++i) {
+        if (!relabel) {
+            rows[i] = base_rows[i];
+            continue;
+        }
+        for (int k = 0; k < N; ++k)
+            if ((rl.rows[i] >> k) & 1) rows[i] ^= base_rows[k];
+    }
     e.c.assign(N, 0);
     for (int k = 0; k < N; ++k)
         for (int j = 0; j < N; ++j)
@@ -159,7 +170,46 @@ std::vector<PauliTerm> canonicalise(std::vector<Term>& t, double rel) {
 
 void check_mapping(int mapping) {
     if (mapping != TQ_JW && mapping != TQ_BK && !find_relabelled(mapping, nullptr))
-        throw Error(TQ_EINVAL, "mapping must be TQ_JW, TQ_BK or an id from tq_mapping_relabelled");
+        throw Error(TQ_EINVAL, "mapping must be TQ_JW, TQ_BK or an id from tq_mapping_relabelled / tq_mapping_linear");
+}
+
+namespace {
+// Inverse over GF(2) of the N x N matrix with the given rows (bit j of
+// rows[i] is entry (i, j)); false when singular.
+bool gf2_inverse(std::vector<uint64_t> a, int N, std::vector<uint64_t>& inv) {
+    inv.assign(N, 0);
+    for (int k = 0; k < N; ++k) inv[k] = 1ull << k;
+    for (int col = 0; col < N; ++col) {
+        int piv = -1;
+        for (int r = col; r < N; ++r)
+            if ((a[r] >> col) & 1) { piv = r; break; }
+        if (piv < 0) return false;
+        std::swap(a[piv], a[col]);
+        std::swap(inv[piv], inv[col]);
+        for (int r = 0; r < N; ++r)
+            if (r != col && ((a[r] >> col) & 1)) { a[r] ^= a[col]; inv[r] ^= inv[col]; }
+    }
+    return true;
+}
+}  // namespace
+
+int register_linear(int base, int N, const uint64_t* rows) {
+    if (base != TQ_JW && base != TQ_BK) throw Error(TQ_EINVAL, "base mapping must be TQ_JW or TQ_BK");
+    if (N < 1 || N > 2 * TQ_MAX_SPATIAL) throw Error(TQ_EINVAL, "n_qubits out of range [1, 30]");
+    if (!rows) throw Error(TQ_EINVAL, "null rows");
+    const uint64_t full = (N == 64) ? ~0ull : ((1ull << N) - 1ull);
+    for (int i = 0; i < N; ++i)
+        if (rows[i] & ~full) throw Error(TQ_EINVAL, "a row selects a qubit beyond n_qubits");
+    std::vector<uint64_t> r(rows, rows + N), inv;
+    if (!gf2_inverse(r, N, inv)) throw Error(TQ_EINVAL, "the index map is not invertible over GF(2)");
+    std::lock_guard<std::mutex> lock(g_relabel_mutex);
+    for (size_t i = 0; i < g_relabelled.size(); ++i) {
+        const Relabelled& x = g_relabelled[i];
+        if (x.base == base && x.N == N && x.rows == r) return TQ_MAPPING_FIRST_RELABELLED + (int)i;
+    }
+    if (g_relabelled.size() >= 4096) throw Error(TQ_EINVAL, "too many relabelled mappings (4096)");
+    g_relabelled.push_back({base, N, r});
+    return TQ_MAPPING_FIRST_RELABELLED + (int)g_relabelled.size() - 1;
 }
 
 int register_relabelled(int base, int N, const int* order) {
@@ -171,15 +221,10 @@ int register_relabelled(int base, int N, const int* order) {
         if (order[k] < 0 || order[k] >= N || seen[order[k]]) throw Error(TQ_EINVAL, "order is not a permutation of 0..n_qubits-1");
         seen[order[k]] = 1;
     }
-    std::lock_guard<std::mutex> lock(g_relabel_mutex);
-    for (size_t i = 0; i < g_relabelled.size(); ++i) {
-        const Relabelled& r = g_relabelled[i];
-        if (r.base == base && r.N == N && std::equal(r.order.begin(), r.order.end(), order))
-            return TQ_MAPPING_FIRST_RELABELLED + (int)i;
-    }
-    if (g_relabelled.size() >= 4096) throw Error(TQ_EINVAL, "too many relabelled mappings (4096)");
-    g_relabelled.push_back({base, N, std::vector<int>(order, order + N)});
-    return TQ_MAPPING_FIRST_RELABELLED + (int)g_relabelled.size() - 1;
+    // qubit k at bit order[k]: row order[k] of M selects qubit k
+    std::vector<uint64_t> rows(N, 0);
+    for (int k = 0; k < N; ++k) rows[order[k]] = 1ull << k;
+    return register_linear(base, N, rows.data());
 }
 
 namespace {
@@ -246,6 +291,107 @@ std::vector<int> pool_sector_order(int n, int ne, int base, int low_bits) {
     for (int q = 0; q < N; ++q)
         if (order[q] < 0) order[q] = next++;
     return order;
+}
+
+std::vector<uint64_t> pool_sector_basis(int n, int ne, int base, int low_bits) {
+    if (base != TQ_JW && base != TQ_BK) throw Error(TQ_EINVAL, "base mapping must be TQ_JW or TQ_BK");
+    const int N = 2 * n;
+    if (n < 1 || n > TQ_MAX_SPATIAL) throw Error(TQ_EINVAL, "n_spatial out of range");
+    if (low_bits < 0 || low_bits > N) throw Error(TQ_EINVAL, "low_bits out of range [0, 2 n_spatial]");
+    const auto ex = excitations(n, ne);
+    // every generator's support conditions (masks over the base index)
+    struct Supp { int m; uint64_t e[3]; };
+    std::vector<Supp> sup;
+    for (const auto& x : ex) {
+        const auto t = pauli_generator(x, N, base);
+        const SignForm f = factor_generator(t);
+        if (!f.ok) throw Error(TQ_ENUMERIC, "generator without a factored sign form");
+        const SupportForm sf = support_form(f, t.front().x);
+        sup.push_back(Supp{sf.m, {(uint64_t)sf.e[0], (uint64_t)sf.e[1], (uint64_t)sf.e[2]}});
+    }
+    const size_t G = sup.size();
+    // candidates: every vector while 2^N x generators stays modest, else
+    // the unit vectors and their pairwise sums
+    std::vector<uint64_t> cand;
+    if ((double)(1ull << N) * (double)std::max<size_t>(G, 1) <= (double)(1ull << 26)) {
+        for (uint64_t v = 1; v < (1ull << N); ++v) cand.push_back(v);
+    } else {
+        for (int a = 0; a < N; ++a) {
+            cand.push_back(1ull << a);
+            for (int b = a + 1; b < N; ++b) cand.push_back((1ull << a) | (1ull << b));
+        }
+    }
+    // greedy: new index bit l takes the vector v (independent of those before
+    // it) that keeps the most support rows per touched segment of 2^(l+1)
+    // amplitudes; a segment is a coset of V = span(chosen), and support S_k
+    // fills |V cap K_k| of it, K_k the kernel of k's conditions.  In
+    // syndrome terms: cost = sum_k |S_k| 2^rank_k, rank_k the rank of the
+    // chosen vectors' syndromes (parities over k's condition masks).
+    std::vector<uint8_t> span(G, 1);   // bit s: syndrome s lies in the span (starts with 0)
+    std::vector<int> rank(G, 0);
+    std::vector<uint64_t> basis;       // chosen vectors, in the order of the new index bits
+    std::vector<uint64_t> echelon;     // reduced copies for the independence test
+    auto reduce = [&](uint64_t v) {
+        for (uint64_t r : echelon) {
+            const uint64_t hb = 1ull << (63 - __builtin_clzll(r));
+            if (v & hb) v ^= r;
+        }
+        return v;
+    };
+    auto add_echelon = [&](uint64_t v) {
+        v = reduce(v);
+        if (!v) return false;
+        const uint64_t hb = 1ull << (63 - __builtin_clzll(v));
+        for (auto& r : echelon)
+            if (r & hb) r ^= v;
+        echelon.push_back(v);
+        std::sort(echelon.begin(), echelon.end(), [](uint64_t a, uint64_t b) { return a > b; });
+        return true;
+    };
+    auto syndrome = [&](const Supp& s, uint64_t v) {
+        int y = 0;
+        for (int i = 0; i < s.m; ++i) y |= (__builtin_popcountll(v & s.e[i]) & 1) << i;
+        return y;
+    };
+    for (int l = 0; l < low_bits; ++l) {
+        uint64_t best = 0;
+        double best_cost = 0.0;
+        for (uint64_t v : cand) {
+            if (!reduce(v)) continue;
+            double cost = 0.0;
+            for (size_t k = 0; k < G; ++k) {
+                const int inside = (span[k] >> syndrome(sup[k], v)) & 1;
+                cost += std::ldexp(1.0, N - sup[k].m + rank[k] + (inside ? 0 : 1));
+            }
+            if (best == 0 || cost < best_cost) {
+                best = v;
+                best_cost = cost;
+            }
+        }
+        if (best == 0) break;   // no independent candidate left
+        basis.push_back(best);
+        add_echelon(best);
+        for (size_t k = 0; k < G; ++k) {
+            const int y = syndrome(sup[k], best);
+            if (!((span[k] >> y) & 1)) {
+                uint8_t grown = span[k];
+                for (int s = 0; s < 8; ++s)
+                    if ((span[k] >> s) & 1) grown |= (uint8_t)(1u << (s ^ y));
+                span[k] = grown;
+                ++rank[k];
+            }
+        }
+    }
+    // the remaining bits: unit vectors not yet spanned, in qubit order
+    for (int q = 0; q < N && (int)basis.size() < N; ++q)
+        if (add_echelon(1ull << q)) basis.push_back(1ull << q);
+    // basis[i] is new index bit i in base coordinates: the columns of M^-1
+    std::vector<uint64_t> crow(N, 0), m;
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j)
+            if ((basis[i] >> j) & 1) crow[j] |= 1ull << i;
+    if (!gf2_inverse(crow, N, m)) throw Error(TQ_ENUMERIC, "sector basis is singular");
+    return m;   // rows of M: new bit i = parity(base index & m[i])
 }
 
 std::vector<PauliTerm> pauli_hamiltonian(int n, const double* h1, const double* g2,

@@ -323,3 +323,107 @@ def test_sector_order_first_pair_is_the_brute_force_best(tq):
     # the rest keep their base order
     rest = [q for q in range(N) if q not in low]
     assert [int(order[q]) for q in rest] == list(range(2, N))
+
+
+def _dense_from_terms(x, z, c, N):
+    """Dense matrix of sum_t c_t X^{x_t} Z^{z_t} (the library's real form:
+    <s ^ x| X^x Z^z |s> = (-1)^{popcount(s & z)})."""
+    s = np.arange(1 << N, dtype=np.int64)
+    H = np.zeros((1 << N, 1 << N))
+    for xt, zt, ct in zip(np.asarray(x, dtype=np.int64), np.asarray(z, dtype=np.int64), c):
+        sign = 1.0 - 2.0 * (np.bitwise_count(s & zt) & 1)
+        np.add.at(H, (s ^ xt, s), ct * sign)
+    return H
+
+
+def _random_invertible(N, rng):
+    while True:
+        rows = rng.integers(0, 1 << N, size=N, dtype=np.int64)
+        a = [int(r) for r in rows]
+        rank = 0
+        for bit in range(N):
+            piv = next((i for i in range(rank, N) if (a[i] >> bit) & 1), None)
+            if piv is None:
+                continue
+            a[rank], a[piv] = a[piv], a[rank]
+            for i in range(N):
+                if i != rank and (a[i] >> bit) & 1:
+                    a[i] ^= a[rank]
+            rank += 1
+        if rank == N:
+            return rows.astype(np.uint64)
+
+
+@pytest.mark.parametrize("mp", [mapping.JW, mapping.BK])
+def test_linear_mapping_is_the_base_mapping_under_its_index_map(tq, mp):
+    """Under an invertible GF(2) index map r' = M r the Hamiltonian, every
+    pool generator and the Hartree-Fock state are the base mapping's with
+    rows and columns moved by the map: H'[M r, M s] = H[r, s] (8 qubits,
+    dense, from the library's own Pauli terms; the base terms are pinned
+    to the oracle by the test above)."""
+    ints, ne = synth.config0()
+    n, N = ints.n_spatial, 2 * ints.n_spatial
+    rows = _random_invertible(N, np.random.default_rng(5 + mp))
+    ml = tq.mapping_linear(mp, rows)
+    assert ml >= 16 and tq.mapping_linear(mp, rows) == ml
+    ix = tq.linear_index(rows)
+    assert np.array_equal(np.sort(ix), np.arange(1 << N))
+    Hb = _dense_from_terms(*tq.pauli_hamiltonian(ints.h, ints.g, 0.25, mp), N)
+    Hl = _dense_from_terms(*tq.pauli_hamiltonian(ints.h, ints.g, 0.25, ml), N)
+    assert np.abs(Hl[np.ix_(ix, ix)] - Hb).max() <= 1e-13 * np.abs(Hb).max()
+    bx, bnt, bz, bc = tq.pauli_pool(n, ne, mp)
+    lx, lnt, lz, lc = tq.pauli_pool(n, ne, ml)
+    for k in range(bx.size):
+        Ab = _dense_from_terms([bx[k]] * bnt[k], bz[k, : bnt[k]], bc[k, : bnt[k]], N)
+        Al = _dense_from_terms([lx[k]] * lnt[k], lz[k, : lnt[k]], lc[k, : lnt[k]], N)
+        assert np.array_equal(Al[np.ix_(ix, ix)], Ab), k          # dyadic coefficients: exact
+    assert tq.hf_index(N, ne, ml) == int(ix[tq.hf_index(N, ne, mp)])
+
+
+def test_linear_mapping_of_a_permutation_is_the_relabelled_mapping(tq):
+    order = np.random.default_rng(3).permutation(12)
+    rows = np.zeros(12, dtype=np.uint64)
+    for k, o in enumerate(order):
+        rows[o] = 1 << k
+    assert tq.mapping_linear(mapping.BK, rows) == tq.mapping_relabelled(mapping.BK, order)
+    assert np.array_equal(tq.linear_index(rows), tq.relabel_index(order))
+
+
+def test_linear_mapping_rejects_bad_maps(tq):
+    singular = np.array([1, 2, 3, 8], dtype=np.uint64)                  # row 2 = row 0 ^ row 1
+    wide = np.array([1, 2, 4, 16], dtype=np.uint64)                     # bit 4 of a 4-qubit index
+    for base, rows in [(mapping.BK, singular), (mapping.JW, wide), (2, np.array([1, 2], dtype=np.uint64))]:
+        with pytest.raises(tq.TQError) as e:
+            tq.mapping_linear(base, rows)
+        assert e.value.code == -1
+
+
+def _touched_sectors(tq, n, ne, mp):
+    """Support rows of every pool generator (numpy, from the exported support
+    form) and the 32-byte sectors (4 complex64 amplitudes) they touch."""
+    N = 2 * n
+    f = tq.pool_support_forms(n, ne, mp)
+    r = np.arange(1 << N, dtype=np.int64)
+    n_rows = n_sect = 0
+    for k in range(f["m"].size):
+        keep = np.ones(r.size, dtype=bool)
+        for i, e in enumerate(_support_masks(f, k)):
+            keep &= (np.bitwise_count(r & e) & 1) == ((int(f["target"][k]) >> i) & 1)
+        n_rows += int(keep.sum())
+        n_sect += np.unique(r[keep] >> 2).size
+    return n_rows, n_sect
+
+
+def test_sector_basis_packs_supports_tighter_than_any_qubit_order(tq):
+    """The greedy GF(2) basis for the 14-qubit BK pool: an invertible map,
+    and its supports touch fewer 32-byte sectors (counted row by row) than
+    the best qubit order's: 170496 against 201216 for 565248 rows (fill
+    0.83 against 0.70)."""
+    n, ne, mp = 7, 6, mapping.BK
+    rows = tq.pool_sector_basis(n, ne, mp)
+    ml = tq.mapping_linear(mp, rows)                                    # raises if singular
+    order = tq.pool_sector_order(n, ne, mp, 14)
+    nr_l, ns_l = _touched_sectors(tq, n, ne, ml)
+    nr_o, ns_o = _touched_sectors(tq, n, ne, tq.mapping_relabelled(mp, order))
+    assert nr_l == nr_o == 565248
+    assert (ns_l, ns_o) == (170496, 201216)

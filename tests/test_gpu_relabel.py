@@ -1,5 +1,6 @@
 """GPU parity: relabelled encodings (JW/BK with the qubits moved to other
-index bits, a memory layout only).
+index bits, or the basis index carried by an invertible GF(2) map: a
+memory layout only).
 
 A relabelled state holds the base mapping's amplitude b at index
 relabel[b].  Energies, gradients and ADAPT steps must equal the oracle's
@@ -23,21 +24,37 @@ def ctx():
     return tq.Context(0)
 
 
-def _orders(n, ne, mp):
+def _random_invertible(N, rng):
+    while True:
+        rows = rng.integers(0, 1 << N, size=N, dtype=np.int64).astype(np.uint64)
+        if np.linalg.matrix_rank(((rows[:, None] >> np.arange(N, dtype=np.uint64)) & 1).astype(np.float64)) < N:
+            continue                       # real rank below N: singular over GF(2) as well
+        try:
+            tq.mapping_linear(0, rows)     # the library's GF(2) check decides
+            return rows
+        except tq.TQError:
+            continue
+
+
+def _layout(n, ne, mp, which):
+    """(mapping id, index map) of a relabelled layout of the base mapping."""
     N = 2 * n
-    return {"sector": tq.pool_sector_order(n, ne, mp, 4),
-            "random": np.random.default_rng(5 + mp).permutation(N).astype(np.int32)}
+    if which in ("sector", "random"):
+        order = (tq.pool_sector_order(n, ne, mp, 4) if which == "sector"
+                 else np.random.default_rng(5 + mp).permutation(N).astype(np.int32))
+        return tq.mapping_relabelled(mp, order), tq.relabel_index(order)
+    rows = (tq.pool_sector_basis(n, ne, mp) if which == "linear"
+            else _random_invertible(N, np.random.default_rng(9 + mp)))
+    return tq.mapping_linear(mp, rows), tq.linear_index(rows)
 
 
-@pytest.mark.parametrize("which", ["sector", "random"])
+@pytest.mark.parametrize("which", ["sector", "random", "linear", "random_linear"])
 @pytest.mark.parametrize("mp", [0, 1])
 @pytest.mark.parametrize("prec", [tq.TQ_C128, tq.TQ_C64])
 def test_relabelled_energy_gradients_step_match_oracle(ctx, mp, prec, which):
     ints, ne = synth.config1()
     n, N = ints.n_spatial, 12
-    order = _orders(n, ne, mp)[which]
-    rl = tq.mapping_relabelled(mp, order)
-    ix = tq.relabel_index(order)
+    rl, ix = _layout(n, ne, mp, which)
     sysm = oadapt.build_system(ints, ne, mp)
     psi = synth.random_state(N, 31 + mp)
     e_ref, _ = oadapt.energy(sysm.H, psi)
@@ -63,18 +80,18 @@ def test_relabelled_energy_gradients_step_match_oracle(ctx, mp, prec, which):
         assert fidelity(got, nxt) > 0.999999
 
 
+@pytest.mark.parametrize("which", ["sector", "linear"])
 @pytest.mark.parametrize("prec", [tq.TQ_C128, tq.TQ_C64])
-def test_relabelled_support_update_is_the_natural_one_moved(ctx, prec):
+def test_relabelled_support_update_is_the_natural_one_moved(ctx, prec, which):
     """The headline shape (14 qubits, BK, pool of 204) on 512 states: the
-    support-only update in the sector-packed layout equals the natural
-    layout's result moved by the relabelling, bit for bit, for every
-    schedule; so does the full-state update."""
+    support-only update in a sector-packed layout (qubit order or GF(2)
+    map) equals the natural layout's result moved by the index map, bit for
+    bit, for every schedule; so does the full-state update."""
     import torch
     n, ne, mp = 7, 6, 1
     N = 14
-    order = tq.pool_sector_order(n, ne, mp, 4)
-    rl = tq.mapping_relabelled(mp, order)
-    ix = torch.as_tensor(tq.relabel_index(order)).cuda()
+    rl, ixn = _layout(n, ne, mp, which)
+    ix = torch.as_tensor(ixn).cuda()
     pool_n = tq.build_pool(ctx, n, ne, mp)
     pool_r = tq.build_pool(ctx, n, ne, rl)
     S = 512
