@@ -36,7 +36,7 @@ namespace tq {
 
 namespace {
 
-constexpr int SUPP_BS = 256;
+constexpr int SUPP_BS = 128;   // threads per CTA of both support-only forms
 
 // Conditions of the support (codimension m): the pivot bits present.
 __device__ __forceinline__ int rowexp_m(const RowExp& x) { return (x.pb0 != 0u) + (x.pb1 != 0u) + (x.pb2 != 0u); }
@@ -406,9 +406,12 @@ __device__ __forceinline__ void warp0_finish(const double* red, double* norm2) {
 // to zero for the next launch.  The request goes to one of two shared
 // slots alternately (the norm buffers' parity), so each write is separated
 // by a barrier from every read of the value it replaces.
-// Complex64 with one or two pairs per thread keeps five CTAs per SM (48
-// registers, no spills), with four pairs three (80); the other forms take
-// what they need.
+// CTAs are SUPP_BS = 128 threads: a state's pairs then come to about 11 per
+// thread, over which the per-state work (tile set-up, coefficients, the
+// norm partial's shuffle tree, barrier, queue) is spread (256 threads:
+// 2-3 % slower in both precisions).  The bounds leave the compiler free up
+// to 102 registers (complex64, four pairs: 86, five CTAs per SM); holding
+// the forms to 48-62 registers for more resident CTAs measured 3 % slower.
 template <typename T, int PPT>
 __global__ void __launch_bounds__(SUPP_BS, sizeof(T) == 4 ? (PPT <= 2 ? 5 : (PPT == 4 ? 3 : 1)) : 1)
 k_taylor5_support_pipe(PoolView p, int n_states, typename C2<T>::type* psi, const int* kk, const double* th,
