@@ -49,6 +49,7 @@ struct SupOp {
     RowExp rx;
     int unit;    // every entry of A is 0 or +-1
     int c0neg;
+    int px;      // parity(x & z0): the sign bit of A[r][q] is that of A[q][r] xor px
     T c0;
 };
 
@@ -62,8 +63,21 @@ __device__ __forceinline__ SupOp<T> load_supop(const PoolView& p, int k) {
     o.c0 = sizeof(T) == 4 ? (T)p.fc0f[k] : (T)p.fc0d[k];
     o.unit = fabsf(p.fc0f[k]) == 1.0f;
     o.c0neg = p.fc0f[k] < 0.0f;
+    o.px = parity32(s.x & s.z0);
     return o;
 }
+
+// A complex64 warp partial of norm changes as a (sum, 0) float pair in the
+// 8-byte slot, by a plain float32 shuffle tree: the summands are the
+// squared-norm changes of the warp's pairs (about theta^6 / 360 and
+// rounding), far below the float64 norm they are added to, so the
+// compensated tree of store_partial buys nothing here.
+__device__ __forceinline__ void store_partial_small(double* slot, float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) *reinterpret_cast<float2*>(slot) = make_float2(v, 0.f);
+}
+__device__ __forceinline__ void store_partial_small(double* slot, double v) { store_partial(slot, v); }
 
 // Start of tile tl's pair range when a generator's 2^lp support pairs are
 // split over 2^lt tiles: tl 2^lp / 2^lt by shifts (both are powers of two).
@@ -144,7 +158,7 @@ __device__ __forceinline__ T support_tile(const SupOp<T>& op, const T (&cf)[6], 
         for (int j = 0; j < PPT; ++j) {
             if (!ok[j]) continue;
             const uint32_t r = rr[j], q = r ^ op.x;
-            const int nr = parity32(q & op.z0), nq = parity32(r & op.z0);   // signs of A[r][q], A[q][r]
+            const int nq = parity32(r & op.z0), nr = nq ^ op.px;   // signs of A[q][r], A[r][q]
             V ar = a[j], aq = b[j];
             if (sup_pair<T>(op, nr, nq, cf, c5, s5, ar, aq)) {
                 nsq = pair_norm2(a[j], b[j], nsq);
@@ -242,7 +256,7 @@ k_taylor5_support(PoolView p, int n_states, typename C2<T>::type* psi, const int
                 taylor_coefs_fast<T>(theta, cf);
             }
             const T d = support_tile<T, PPT>(op, cf, c5, s5, growth, psi + (long long)b * D, i0, i1);
-            store_partial(slot, d);
+            store_partial_small(slot, d);
         }
         if (fold) {
             __syncthreads();   // the partials are in red, and every thread has read sc
@@ -344,7 +358,7 @@ __device__ __forceinline__ T sup_compute(const SupTile<T>& t, uint32_t pos, type
         if (u >= t.i1) continue;
         const uint32_t r = rows[j * SUPP_BS + threadIdx.x], q = r ^ t.op.x;
         const V a = stage[(2 * j) * SUPP_BS + threadIdx.x], b = stage[(2 * j + 1) * SUPP_BS + threadIdx.x];
-        const int nr = parity32(q & t.op.z0), nq = parity32(r & t.op.z0);
+        const int nq = parity32(r & t.op.z0), nr = nq ^ t.op.px;   // q & z0 = (r ^ x) & z0
         V ar = a, aq = b;
         if (sup_pair<T>(t.op, nr, nq, cf, c5, s5, ar, aq)) {
             nsq = pair_norm2(a, b, nsq);
@@ -476,7 +490,7 @@ k_taylor5_support_pipe(PoolView p, int n_states, typename C2<T>::type* psi, cons
         if (tile_end) {
             double* slot = fold ? &red[rp][warp] : partials + (size_t)tile * NW + warp;
             if (cur.bad) store_nan_partial(slot, T(0));
-            else store_partial(slot, delta);
+            else store_partial_small(slot, delta);
             delta = T(0);
             if (fold) {
                 __syncthreads();
