@@ -107,7 +107,7 @@ k_taylor5_grouped(PoolView p, int n_groups, typename C2<T>::type* psi, const int
             for (int j = 0; j < SPL; ++j) {
                 taylor_coefs_fast<T>(th[(long long)g * G + s0 + j], cf[j]);
                 c5[j] = s5[j] = nsq[j] = 0.0;
-                closed_coefs(cf[j], c5[j], s5[j]);
+                if constexpr (sizeof(T) == 8) closed_coefs(cf[j], c5[j], s5[j]);
             }
             const SuppRec sr = load_supp(p, k);
             const RowExp rx = make_rowexp(sr, p.supp[k].z);
@@ -137,19 +137,18 @@ k_taylor5_grouped(PoolView p, int n_groups, typename C2<T>::type* psi, const int
 #pragma unroll
                     for (int t = 0; t < SPL; ++t) {
                         V ar = A[j].a[t], aq = B[j].a[t];
-                        bool closed = false;   // the norm change in closed form (complex128)
-                        if (unit && nr != nq) {
-                            const int sgn = (nr != (int)c0neg) ? -1 : 1;
-                            closed_pair_sign(sgn, -sgn, cf[t], c5[t], s5[t], ar, aq);
-                            if constexpr (sizeof(T) == 8) {
+                        bool closed = false;
+                        if constexpr (sizeof(T) == 8) {
+                            if (unit && nr != nq) {
+                                const int sgn = (nr != (int)c0neg) ? -1 : 1;
+                                closed_pair_sign(sgn, -sgn, cf[t], c5[t], s5[t], ar, aq);
                                 closed = true;
                                 const V a = A[j].a[t], b = B[j].a[t];
                                 nsq[t] = fma(a.x, a.x, fma(a.y, a.y, fma(b.x, b.x, fma(b.y, b.y, nsq[t]))));
                             }
-                        } else {
-                            chain_pair(nr ? -c0 : c0, nq ? -c0 : c0, cf[t], ar, aq);
                         }
                         if (!closed) {
+                            chain_pair(nr ? -c0 : c0, nq ? -c0 : c0, cf[t], ar, aq);
                             const V a = A[j].a[t], b = B[j].a[t];
                             delta[t] += (ar.x - a.x) * (ar.x + a.x) + (ar.y - a.y) * (ar.y + a.y);
                             delta[t] += (aq.x - b.x) * (aq.x + b.x) + (aq.y - b.y) * (aq.y + b.y);

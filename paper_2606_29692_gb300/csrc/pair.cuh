@@ -110,11 +110,6 @@ __device__ __forceinline__ void closed_coefs(const double (&cf)[6], double& c5, 
     c5 = __dadd_rn(__dsub_rn(cf[0], cf[2]), cf[4]);
     s5 = __dadd_rn(__dsub_rn(cf[1], cf[3]), cf[5]);
 }
-// complex64: the same sums in float32, handed over widened (exactly).
-__device__ __forceinline__ void closed_coefs(const float (&cf)[6], double& c5, double& s5) {
-    c5 = (double)__fadd_rn(__fsub_rn(cf[0], cf[2]), cf[4]);
-    s5 = (double)__fadd_rn(__fsub_rn(cf[1], cf[3]), cf[5]);
-}
 
 // Per-warp norm partial: float64 sum for complex128; for complex64 a
 // TwoSum-compensated float32 warp sum stored as a (hi, lo) float pair in
@@ -267,21 +262,6 @@ __device__ __forceinline__ void closed_pair_sign(int s_r, int s_q, const double 
     }
 }
 
-// complex64: the same closed form on Blackwell's packed float32x2 pipe, two
-// products per amplitude instead of ten (c5, s5: the float32 values from
-// closed_coefs).
-__device__ __forceinline__ void closed_pair_sign(int s_r, int s_q, const float (&cf)[6], double c5, double s5,
-                                                 float2& ar, float2& aq) {
-    if (s_r != 0 && s_q == -s_r) {
-        const float c = (float)c5, s = s_r > 0 ? (float)s5 : -(float)s5;
-        const float2 vr = ar, vq = aq;
-        ar = __ffma2_rn(make_float2(s, s), vq, __fmul2_rn(make_float2(c, c), vr));
-        aq = __ffma2_rn(make_float2(-s, -s), vr, __fmul2_rn(make_float2(c, c), vq));
-    } else if (s_r != 0 || s_q != 0) {
-        chain_pair((float)s_r, (float)s_q, cf, ar, aq);
-    }
-}
-
 // Four amplitudes of one unit of the pair enumeration: rows r0, r0 + 1 and
 // their partners q0 = r0 ^ x, q0 ^ 1 (x > 1), or pairs (r0, r0 + 1) and
 // (r0 + 2, r0 + 3) (x == 1).  After unit_update, a0/a1 hold rows r0/r0 + 1
@@ -335,7 +315,7 @@ template <typename T>
 __device__ __forceinline__ void unit_update(const OpRec<T>& op, int hb, const T (&cf)[6],
                                             PairUnit<typename C2<T>::type>& w, T& tpart) {
     double c5 = 0.0, s5 = 0.0;
-    closed_coefs(cf, c5, s5);
+    if constexpr (sizeof(T) == 8) closed_coefs(cf, c5, s5);
     unit_update<T>(op, hb, cf, c5, s5, w, tpart);
 }
 
@@ -352,9 +332,14 @@ __device__ __forceinline__ void unit_update(const OpRec<T>& op, int hb, const T 
         const int c_r1 = bc ^ ((op.dcode >> 12) & 15);   // col q0^1
         const int c_q0 = bc ^ (op.dcode & 15);           // col r0
         const int c_q1 = bc ^ ((op.dcode >> 4) & 15);    // col r0+1
-        if (op.unit) {
-            closed_pair_sign(rec_sign(op, c_r0), rec_sign(op, c_q0), cf, c5, s5, w.a0, w.b0);
-            closed_pair_sign(rec_sign(op, c_r1), rec_sign(op, c_q1), cf, c5, s5, w.a1, w.b1);
+        if constexpr (sizeof(T) == 8) {
+            if (op.unit) {
+                closed_pair_sign(rec_sign(op, c_r0), rec_sign(op, c_q0), cf, c5, s5, w.a0, w.b0);
+                closed_pair_sign(rec_sign(op, c_r1), rec_sign(op, c_q1), cf, c5, s5, w.a1, w.b1);
+            } else {
+                chain_pair(rec_value(op, c_r0), rec_value(op, c_q0), cf, w.a0, w.b0);
+                chain_pair(rec_value(op, c_r1), rec_value(op, c_q1), cf, w.a1, w.b1);
+            }
         } else {
             chain_pair(rec_value(op, c_r0), rec_value(op, c_q0), cf, w.a0, w.b0);
             chain_pair(rec_value(op, c_r1), rec_value(op, c_q1), cf, w.a1, w.b1);

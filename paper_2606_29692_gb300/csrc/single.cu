@@ -102,7 +102,6 @@ k_taylor5_single(PoolView p, int k_imm, double th_imm, const DevStep* gate, type
         s5 = coef_sh[7];
     } else {
         taylor_coefs_fast<T>(theta, cf);
-        closed_coefs(cf, c5, s5);
     }
     T tpart = T(0);
 #pragma unroll

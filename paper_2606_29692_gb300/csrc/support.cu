@@ -86,19 +86,19 @@ __device__ __forceinline__ uint32_t pair_bound(int lp, unsigned tl, int lt) {
 }
 
 // The update of one support pair (r, q = r ^ x) with nr, nq the sign bits of
-// A[r][q] and A[q][r].  Pairs with entries +-1 and A[q][r] = -A[r][q] (A^2 =
-// -I on the pair) take the closed form c5 psi + s5 A psi of the same
-// fifth-order polynomial.  Returns true when the caller may add the norm
-// change in closed form, which holds exactly there, (c5^2 + s5^2 - 1) times
-// |psi_r|^2 + |psi_q|^2: complex128 does; complex64 takes the change from
-// the stored values, so the carried norm follows the state's rounding.
+// A[r][q] and A[q][r].  Returns true when the pair took the complex128
+// closed form (entries +-1, A[q][r] = -A[r][q], so A^2 = -I on the pair):
+// there |psi'_r|^2 + |psi'_q|^2 = (c5^2 + s5^2)(|psi_r|^2 + |psi_q|^2)
+// exactly, and the caller adds the norm change in closed form.
 template <typename T>
 __device__ __forceinline__ bool sup_pair(const SupOp<T>& op, int nr, int nq, const T (&cf)[6], double c5,
                                          double s5, typename C2<T>::type& ar, typename C2<T>::type& aq) {
-    if (op.unit && nr != nq) {
-        const int sr = (nr != op.c0neg) ? -1 : 1;
-        closed_pair_sign(sr, -sr, cf, c5, s5, ar, aq);
-        return sizeof(T) == 8;
+    if constexpr (sizeof(T) == 8) {
+        if (op.unit && nr != nq) {
+            const int sr = (nr != op.c0neg) ? -1 : 1;
+            closed_pair_sign(sr, -sr, cf, c5, s5, ar, aq);
+            return true;
+        }
     }
     chain_pair(nr ? -op.c0 : op.c0, nq ? -op.c0 : op.c0, cf, ar, aq);
     return false;
@@ -254,7 +254,6 @@ k_taylor5_support(PoolView p, int n_states, typename C2<T>::type* psi, const int
                 growth = w[8];
             } else {
                 taylor_coefs_fast<T>(theta, cf);
-                closed_coefs(cf, c5, s5);
             }
             const T d = support_tile<T, PPT>(op, cf, c5, s5, growth, psi + (long long)b * D, i0, i1);
             store_partial_small(slot, d);
@@ -350,7 +349,7 @@ __device__ __forceinline__ T sup_compute(const SupTile<T>& t, uint32_t pos, type
     T cf[6];
     taylor_coefs_typed<T>(t.theta, cf);
     double c5 = 0.0, s5 = 0.0;
-    closed_coefs(cf, c5, s5);
+    if constexpr (sizeof(T) == 8) closed_coefs(cf, c5, s5);
     T delta = T(0);
     double nsq = 0.0;
 #pragma unroll
