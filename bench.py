@@ -578,6 +578,13 @@ def run_ours(args, rank, world, local_rank):
     ctx.trace(False)
     sup_n, sup_ms = rep.get("taylor5_support", (0, float("nan")))
     sup_traced_s = sup_ms / max(sup_n, 1) / 1e3
+    # the access pattern's own floor: the same launch (schedule, L2 fetch,
+    # occupancy, state queue) with the update taken out, every support row
+    # written back as read; timed back to back like the steps
+    for _ in range(3):
+        tq.evolve_taylor5_batch_support_touch(ctx, pool, psi, dk, dn)
+    touch_s = time_launches(lambda: tq.evolve_taylor5_batch_support_touch(ctx, pool, psi, dk, dn),
+                            max(args.steps, 20)) / 1e3
     ctx.set_l2_fetch(0)
     # algorithmic bytes: each support amplitude read and written once, the
     # carried norm read and written once; the touched 32-byte sectors and
@@ -719,6 +726,11 @@ def run_ours(args, rank, world, local_rank):
                          "kernel_ms_per_launch_note": "the timed region's CUDA-event time over its K launches "
                                                       "(one launch per step, gaps included)",
                          "kernel_ms_per_launch_event_bracketed": sup_traced_s * 1e3,
+                         "touch_floor_ms_per_launch": touch_s * 1e3,
+                         "update_over_touch_floor": sup_s / touch_s,
+                         "touch_floor_note": "the same launch with the update taken out (every support row read "
+                                             "and written back unchanged, tq_evolve_taylor5_batch_support_touch): "
+                                             "the floor the access pattern sets",
                          "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
                          else "fallback"},
             "e2e": e2e,

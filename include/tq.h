@@ -621,6 +621,17 @@ int tq_evolve_taylor5_batch_support_host(tq_ctx* ctx, const tq_pool* pool,
  * with them staged in shared memory by asynchronous copies that run one
  * pass ahead (across states).  Defaults: 4 for TQ_C128, -1 for TQ_C64. */
 int tq_ctx_set_support_schedule(tq_ctx* ctx, int prec, int pairs_per_thread);
+/* A measurement aid with no counterpart in the paper: the support-only
+ * batched update's launch (the pipelined form with the context's pairs per
+ * pass, the same tile set-up, state queue, barriers and norm finish) with
+ * the update taken out.  Every support row it would touch is read and
+ * written back unchanged, so psi keeps its bits, and norm2 (may be null;
+ * then the states are taken in a fixed stride) keeps its values (an op
+ * index outside [0, M) makes that state's norm NaN, as in the update).  Timing
+ * it gives the floor that this access pattern sets for the update.  Async.
+ * Errors as tq_evolve_taylor5_batch_support. */
+int tq_evolve_taylor5_batch_support_touch(tq_ctx* ctx, const tq_pool* pool, int n_states, int prec, void* psi,
+                                          const int* k, double* norm2, void* stream);
 /* The support-only batched update for groups of states that share a
  * generator, in an interleaved layout (a layout choice with no counterpart
  * in the paper; the update is that of Eqs. (6)-(8) as above).  A group is

@@ -655,6 +655,14 @@ def evolve_taylor5_batch_grouped(ctx, pool, psi, k, theta, norm2=None, prec=TQ_C
          _ptr(theta), _ptr(norm2), _stream(stream))
 
 
+def evolve_taylor5_batch_support_touch(ctx, pool, psi, k, norm2=None, prec=TQ_C64, stream=None):
+    """The support-only update's launch with the update taken out: every
+    support row read and written back unchanged (a measurement aid: the
+    access pattern's own floor)."""
+    call("tq_evolve_taylor5_batch_support_touch", ctx.handle, pool.handle, int(psi.shape[0]), prec, _ptr(psi),
+         _ptr(k), _ptr(norm2), _stream(stream))
+
+
 def evolve_taylor5_batch_support_host(ctx, pool, psi, k, theta, norm2=None, prec=TQ_C64):
     """Support-only update of states in page-locked HOST memory (a pinned
     torch CPU tensor), read and written in place by the kernel; k, theta and

@@ -116,6 +116,7 @@ SIGNATURES = {
     "tq_mapping_relabelled": [i32, i32, vp, P(i32)],
     "tq_pool_sector_order": [i32, i32, i32, i32, vp],
     "tq_mapping_linear": [i32, i32, vp, P(i32)],
+    "tq_evolve_taylor5_batch_support_touch": [vp, vp, i32, i32, vp, vp, vp, vp],
     "tq_pool_sector_basis": [i32, i32, i32, i32, vp],
     "tq_l2_read_rate": [vp, i64, i32, P(f64)],
     "tq_ctx_set_l2_fetch": [vp, i32],

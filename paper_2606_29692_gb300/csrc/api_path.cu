@@ -348,6 +348,32 @@ extern "C" int tq_evolve_taylor5_batch_support(tq_ctx* c, const tq_pool* p, int 
     API_END
 }
 
+extern "C" int tq_evolve_taylor5_batch_support_touch(tq_ctx* c, const tq_pool* p, int n_states, int prec,
+                                                     void* psi, const int* k, double* norm2, void* stream) {
+    API_BEGIN
+    TQ_REQUIRE(c && p, "null argument");
+    TQ_REQUIRE(!p->sector, "the support-only update takes full-space pools");
+    TQ_REQUIRE(n_states >= 0, "n_states < 0");
+    check_prec(prec);
+    if (n_states == 0) return TQ_OK;
+    TQ_REQUIRE(psi && k, "null argument");
+    TQ_REQUIRE(((uintptr_t)psi & 15u) == 0, "psi must be 16-byte aligned");
+    set_device(c);
+    cudaStream_t s = as_stream(stream);
+    const int ppt = c->supp_ppt[prec] < 0 ? c->supp_ppt[prec] : -c->supp_ppt[prec];
+    const int tps = support_tiles(p->nq, n_states, ppt, c->sm_count);
+    const int parts = support_parts(tps);
+    double* part = static_cast<double*>(scratch(c, S_PART, (size_t)n_states * parts * sizeof(double)));
+    // theta is read by the tile set-up and not used: any finite values
+    double* th = static_cast<double*>(scratch(c, S_HOSTB, (size_t)n_states * sizeof(double)));
+    TQ_CUDA(cudaMemsetAsync(th, 0, (size_t)n_states * sizeof(double), s));
+    launch(c, "taylor5_support_touch", s, [&] {
+        return launch_taylor5_support_touch(p->view, n_states, prec, ppt, psi, k, th, part, tps, norm2, c->sm_count, s,
+                                            c->supp_ctas[prec], c->tickets + TICKET_SUPPORT_SCHED);
+    });
+    API_END
+}
+
 extern "C" int tq_evolve_taylor5_batch_support_host(tq_ctx* c, const tq_pool* p, int n_states, int prec,
                                                     void* psi_host, const int* k_host, const double* theta_host,
                                                     double* norm2_host) {

@@ -227,6 +227,12 @@ int support_parts(int tiles);
 int launch_taylor5_support(const PoolView& p, int n_states, int prec, int ppt, void* psi, const int* k,
                            const double* theta, double* partials, int tps, double* norm2, int sms,
                            cudaStream_t s, int ctas_per_sm = 0, unsigned* sched = nullptr);
+// The same launch with the update taken out (every support row written back
+// as read), in the pipelined form with |ppt| pairs per pass: the memory-only
+// floor of the support-only update.
+int launch_taylor5_support_touch(const PoolView& p, int n_states, int prec, int ppt, void* psi, const int* k,
+                                 const double* theta, double* partials, int tps, double* norm2, int sms,
+                                 cudaStream_t s, int ctas_per_sm, unsigned* sched);
 int launch_scale(void* psi, int prec, long long D, const double* norm2, cudaStream_t s);
 
 // Taylor-5 for a general CSR operator.

@@ -342,10 +342,23 @@ __device__ __forceinline__ void sup_issue(const SupTile<T>& t, uint32_t pos, con
     }
 }
 
-template <typename T, int PPT>
+// TOUCH: the memory-only floor of the same pass, every support row
+// written back as it was read (no update, no norm change).
+template <typename T, int PPT, bool TOUCH = false>
 __device__ __forceinline__ T sup_compute(const SupTile<T>& t, uint32_t pos, typename C2<T>::type* base,
                                          const typename C2<T>::type* stage, const uint32_t* rows) {
     using V = typename C2<T>::type;
+    if constexpr (TOUCH) {
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) {
+            const uint32_t u = pos + j * SUPP_BS + threadIdx.x;
+            if (u >= t.i1) continue;
+            const uint32_t r = rows[j * SUPP_BS + threadIdx.x];
+            base[r] = stage[(2 * j) * SUPP_BS + threadIdx.x];
+            base[r ^ t.op.x] = stage[(2 * j + 1) * SUPP_BS + threadIdx.x];
+        }
+        return T(0);
+    }
     T cf[6];
     taylor_coefs_typed<T>(t.theta, cf);
     double c5 = 0.0, s5 = 0.0;
@@ -426,7 +439,7 @@ __device__ __forceinline__ void warp0_finish(const double* red, double* norm2) {
 // 2-3 % slower in both precisions).  The bounds leave the compiler free up
 // to 102 registers (complex64, four pairs: 86, five CTAs per SM); holding
 // the forms to 48-62 registers for more resident CTAs measured 3 % slower.
-template <typename T, int PPT>
+template <typename T, int PPT, bool TOUCH = false>
 __global__ void __launch_bounds__(SUPP_BS, sizeof(T) == 4 ? (PPT <= 2 ? 5 : (PPT == 4 ? 3 : 1)) : 1)
 k_taylor5_support_pipe(PoolView p, int n_states, typename C2<T>::type* psi, const int* kk, const double* th,
                        double* partials, int tiles_per_state, double* norm2, unsigned* sched) {
@@ -485,7 +498,7 @@ k_taylor5_support_pipe(PoolView p, int n_states, typename C2<T>::type* psi, cons
         cp_commit();
         cp_wait_one();
         if (!cur.bad)
-            delta += sup_compute<T, PPT>(cur, pos, psi + (long long)cur.b * D, stages + st * STAGE,
+            delta += sup_compute<T, PPT, TOUCH>(cur, pos, psi + (long long)cur.b * D, stages + st * STAGE,
                                          rowbuf + st * PPT * SUPP_BS);
         if (tile_end) {
             double* slot = fold ? &red[rp][warp] : partials + (size_t)tile * NW + warp;
@@ -517,7 +530,7 @@ k_taylor5_support_pipe(PoolView p, int n_states, typename C2<T>::type* psi, cons
     }
 }
 
-template <typename T, int PPT>
+template <typename T, int PPT, bool TOUCH = false>
 int launch_support_pipe(const PoolView& p, int n_states, void* psi, const int* k, const double* theta,
                         double* partials, int tps, double* norm2, int sms, int ctas, cudaStream_t s,
                         unsigned* sched) {
@@ -527,15 +540,16 @@ int launch_support_pipe(const PoolView& p, int n_states, void* psi, const int* k
     const size_t smem = (size_t)2 * PPT * SUPP_BS * (2 * sizeof(V) + sizeof(uint32_t));
     static int per_sm = 0;
     if (per_sm == 0) {
-        cudaFuncSetAttribute(k_taylor5_support_pipe<T, PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_taylor5_support_pipe<T, PPT, TOUCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
         int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_taylor5_support_pipe<T, PPT>, SUPP_BS, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_taylor5_support_pipe<T, PPT, TOUCH>, SUPP_BS, smem);
         per_sm = n < 1 ? 1 : n;
     }
     long long grid = (long long)(ctas > 0 && ctas < per_sm ? ctas : per_sm) * sms;
     if (grid > total) grid = total;
     if (grid < 1) grid = 1;
-    k_taylor5_support_pipe<T, PPT><<<(int)grid, SUPP_BS, smem, s>>>(p, n_states, static_cast<V*>(psi), k, theta,
+    k_taylor5_support_pipe<T, PPT, TOUCH><<<(int)grid, SUPP_BS, smem, s>>>(p, n_states, static_cast<V*>(psi), k, theta,
                                                                      partials, tps, norm2, sched);
     return 1;
 }
@@ -597,6 +611,29 @@ int support_tiles(int nq, int n_states, int ppt, int sms) {
 }
 
 int support_parts(int tiles) { return tiles * (SUPP_BS / 32); }
+
+int launch_taylor5_support_touch(const PoolView& p, int n_states, int prec, int ppt, void* psi, const int* k,
+                                 const double* theta, double* partials, int tps, double* norm2, int sms,
+                                 cudaStream_t s, int ctas_per_sm, unsigned* sched) {
+    if (tps < 1 || (tps & (tps - 1)) != 0) return -1;
+    const int u = ppt < 0 ? -ppt : ppt;   // the pipelined form with the same pairs per pass
+    if (prec == TQ_C128) {
+        switch (u) {
+            case 1: return launch_support_pipe<double, 1, true>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas_per_sm, s, sched);
+            case 2: return launch_support_pipe<double, 2, true>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas_per_sm, s, sched);
+            case 4: return launch_support_pipe<double, 4, true>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas_per_sm, s, sched);
+            case 8: return launch_support_pipe<double, 8, true>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas_per_sm, s, sched);
+            default: return -1;
+        }
+    }
+    switch (u) {
+        case 1: return launch_support_pipe<float, 1, true>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas_per_sm, s, sched);
+        case 2: return launch_support_pipe<float, 2, true>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas_per_sm, s, sched);
+        case 4: return launch_support_pipe<float, 4, true>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas_per_sm, s, sched);
+        case 8: return launch_support_pipe<float, 8, true>(p, n_states, psi, k, theta, partials, tps, norm2, sms, ctas_per_sm, s, sched);
+        default: return -1;
+    }
+}
 
 int launch_taylor5_support(const PoolView& p, int n_states, int prec, int ppt, void* psi, const int* k,
                            const double* theta, double* partials, int tps, double* norm2, int sms,

@@ -287,3 +287,26 @@ def test_l2_read_rate(ctx):
     for nbytes, reps in ((1 << 19, 4), ((256 << 20) + 16, 4), ((1 << 20) + 8, 4), (1 << 20, 0)):
         with pytest.raises(tq.TQError):
             tq.l2_read_rate(ctx, nbytes, reps)
+
+
+@pytest.mark.parametrize("prec", [tq.TQ_C128, tq.TQ_C64])
+def test_support_touch_keeps_every_bit(ctx, prec):
+    """The memory-only form of the update (the bench's floor for the access
+    pattern) writes every support row back as it read it: the states and
+    the carried norms keep their bits under either schedule."""
+    import torch
+    n, ne, mp = 7, 6, 1
+    pool = tq.build_pool(ctx, n, ne, mp)
+    S = 256
+    psi, k, th, dt = _inputs(14, S, pool.M, 77, prec)
+    ref = torch.as_tensor(psi).to(dt).cuda()
+    n_in = (ref.abs().double() ** 2).sum(dim=1)
+    for ppt in (-2, 4):
+        ctx.set_support_schedule(prec, ppt)
+        a = ref.clone()
+        n2 = n_in.clone()
+        tq.evolve_taylor5_batch_support_touch(ctx, pool, a, torch.as_tensor(k).cuda(), n2, prec=prec)
+        torch.cuda.synchronize()
+        assert torch.equal(torch.view_as_real(a), torch.view_as_real(ref)), ppt
+        assert torch.equal(n2, n_in), ppt
+    ctx.set_support_schedule(prec, 4 if prec == tq.TQ_C128 else -1)
