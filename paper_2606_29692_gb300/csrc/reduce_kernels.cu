@@ -1023,8 +1023,18 @@ k_line_search(DevStep* step, double theta_given, const double* theta_list, const
     __syncthreads();
     const long long thr = thr_sh;
     int best = INT_MAX;   // rank * 4096 + m of the preferred sample within the tolerance
-    for (int m = threadIdx.x; m < 4096; m += LS_BS)
-        if (__ldcg(se + m) <= thr) best = min(best, rank[m] * 4096 + m);
+    {
+        // every key load issued before the first comparison waits on one
+        constexpr int PER = 4096 / LS_BS;
+        long long key_m[PER];
+#pragma unroll
+        for (int j = 0; j < PER; ++j) key_m[j] = __ldcg(se + threadIdx.x + j * LS_BS);
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const int m = threadIdx.x + j * LS_BS;
+            if (key_m[j] <= thr) best = min(best, rank[m] * 4096 + m);
+        }
+    }
     for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_down_sync(0xffffffffu, best, o));
     if (lane == 0) redi[wid] = best;
     __syncthreads();
