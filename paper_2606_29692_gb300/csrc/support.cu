@@ -451,6 +451,14 @@ k_taylor5_support_pipe(PoolView p, int n_states, typename C2<T>::type* psi, cons
     uint32_t* rowbuf = reinterpret_cast<uint32_t*>(stages + 2 * STAGE);   // [2][PPT][SUPP_BS]
     __shared__ double red[2][NW];
     __shared__ unsigned next_sh[2];
+    // launched with programmatic stream serialisation: the next launch in
+    // the stream may be scheduled at once, and every launch waits here,
+    // before its first global access, for the previous grid to complete
+    // (any state may be written late by it, and the state counters are
+    // reset by its last CTA); what overlaps is the launch and the CTAs'
+    // start, 1.5 % of a back-to-back step
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     int rp = 0;
     const int warp = threadIdx.x >> 5;
     const bool fold = tiles_per_state == 1 && norm2 != nullptr;
@@ -549,8 +557,19 @@ int launch_support_pipe(const PoolView& p, int n_states, void* psi, const int* k
     long long grid = (long long)(ctas > 0 && ctas < per_sm ? ctas : per_sm) * sms;
     if (grid > total) grid = total;
     if (grid < 1) grid = 1;
-    k_taylor5_support_pipe<T, PPT, TOUCH><<<(int)grid, SUPP_BS, smem, s>>>(p, n_states, static_cast<V*>(psi), k, theta,
-                                                                     partials, tps, norm2, sched);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(SUPP_BS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // a launch error stays pending for the caller's cudaGetLastError check
+    (void)cudaLaunchKernelEx(&cfg, k_taylor5_support_pipe<T, PPT, TOUCH>, p, n_states, static_cast<V*>(psi), k,
+                             theta, partials, tps, norm2, sched);
     return 1;
 }
 
