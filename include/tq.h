@@ -714,7 +714,9 @@ int tq_evolve_taylor5_batch_host(tq_ctx* ctx, const tq_pool* pool,
  * and renormalisation.  The batch owns its states and keeps the handles it
  * was given (they must outlive it).  Every iteration of every trajectory is
  * six persistent launches over static work tables; finished trajectories are
- * skipped by a device-side flag, so a run needs no host round trip. */
+ * left out on the device (the energy launch runs over the active
+ * trajectories' items, numbered by the previous iteration; the others test
+ * a flag), so a run needs no host round trip. */
 typedef struct tq_batch tq_batch;
 int tq_batch_create(tq_ctx* ctx, int n_traj, tq_ham* const* hams,
                     tq_pool* const* pools, const int* n_electrons,

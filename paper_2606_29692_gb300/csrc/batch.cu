@@ -9,9 +9,13 @@
 //   select   one warp per t: k*, max|g|, convergence, angle, record;
 //   update   items (t, tile): the fused Taylor-5 pair update with A_{k*};
 //   norm     one warp per t: ||psi'||^2, advance the iteration counter;
+//            the last block numbers the active trajectories' energy items
+//            for the next iteration (prefix counts);
 //   scale    items (t, chunk): psi /= ||psi'||.
-// Items of finished trajectories are skipped by a flag read on the device,
-// so the whole run (max length x six launches) is captured once into a CUDA
+// The energy launch runs over the numbered items only, which also spreads
+// the remaining trajectories' items evenly over the persistent grid; the
+// other launches skip finished trajectories by a flag read on the device.
+// So the whole run (max length x six launches) is captured once into a CUDA
 // graph and replayed without any host round trip.  The SpMV of the energy
 // item runs over the CSR with a lanes-per-row schedule (4, 8, 16, 32) or
 // over the XOR-ELL layout, chosen by an autotuner.
@@ -64,11 +68,28 @@ struct TrajState {
 
 namespace {
 
+// The energy launch runs over the energy items of the trajectories still
+// active, numbered 0 .. P[n].x - 1 in trajectory order.  Entry
+// P[t] = (first number of trajectory t, its first item's table index minus
+// that number): item number j belongs to the t with P[t].x <= j < P[t + 1].x
+// and is table item j + P[t].y.  `lo` is a t with P[lo].x <= j (0, or the t
+// of the block's previous item, since a block's numbers only grow).
+__device__ __forceinline__ int active_traj(const int2* __restrict__ P, int n, int lo, int j) {
+    int hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(&P[mid].x) <= j) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 constexpr int BT_BS = 256;
 // An energy item is four 64-row blocks: each item pays a descriptor fetch,
 // a block sum and a ticket, so longer items spend less on them.
 constexpr int ROWS_PER_ITEM = 4 * ENERGY_ROWS;
 constexpr int BT_UPT = 2;
+constexpr int SCALE_U = 8;
 
 template <typename T> __device__ __forceinline__ double2 d2(typename C2<T>::type v) {
     return make_double2((double)v.x, (double)v.y);
@@ -103,15 +124,17 @@ __global__ void kb_reset(const TrajDev* tr, TrajState* ts, const int4* items, in
 // float64 (diagonal, w, dots).
 template <typename T, typename VT, int LPR>
 __global__ void __launch_bounds__(BT_BS)
-kb_energy(const TrajDev* tr, TrajState* ts, const int4* items, int n_items, double* part) {
+kb_energy(const TrajDev* tr, TrajState* ts, const int4* items, const int2* pre, int n, double* part) {
     using V = typename C2<T>::type;
     __shared__ double sh[2 * (BT_BS / 32)];
     __shared__ bool last;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const int4 w4 = items[it];
-        const int t = w4.x;
-        if (!ts[t].active) continue;                     // uniform across the block
+    const int total = __ldg(&pre[n].x);
+    int t = 0;
+    for (int j = blockIdx.x; j < total; j += gridDim.x) {
+        t = active_traj(pre, n, t, j);
+        const int it = j + __ldg(&pre[t].y);
         const TrajDev& d = tr[t];
+        const int4 w4 = items[it];
         const V* psi = static_cast<const V*>(d.psi);
         const VT* val = static_cast<const VT*>(d.val);
         double num = 0.0, den = 0.0;
@@ -154,7 +177,7 @@ kb_energy(const TrajDev* tr, TrajState* ts, const int4* items, int n_items, doub
 // then finishes one of the warp's 32 rows in float64.
 template <typename T, typename VT>
 __global__ void __launch_bounds__(BT_BS)
-kbx_energy(const TrajDev* tr, TrajState* ts, const int4* items, int n_items, double* part) {
+kbx_energy(const TrajDev* tr, TrajState* ts, const int4* items, const int2* pre, int n, double* part) {
     using V = typename C2<T>::type;
     using VT2 = typename C2<VT>::type;
     constexpr int K = 4;                       // rounds of 8 pairs in flight
@@ -162,11 +185,13 @@ kbx_energy(const TrajDev* tr, TrajState* ts, const int4* items, int n_items, dou
     __shared__ bool last;
     __shared__ T stash[BT_BS / 32][32][2];      // per warp, row: (re, im) of the off-diagonal sum
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, slot = lane >> 2, u = lane & 3;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const int4 w4 = items[it];
-        const int t = w4.x;
-        if (!ts[t].active) continue;                     // uniform across the block
+    const int total = __ldg(&pre[n].x);
+    int t = 0;
+    for (int j = blockIdx.x; j < total; j += gridDim.x) {
+        t = active_traj(pre, n, t, j);
+        const int it = j + __ldg(&pre[t].y);
         const TrajDev& d = tr[t];
+        const int4 w4 = items[it];
         const V* __restrict__ psi = static_cast<const V*>(d.psi);
         const VT2* __restrict__ xv = static_cast<const VT2*>(d.xval);
         const uint32_t dmask = (uint32_t)(d.D - 1);
@@ -362,34 +387,77 @@ kb_pair(const TrajDev* tr, const TrajState* ts, const int4* items, int n_items, 
     }
 }
 
+// Numbers the energy items of the active trajectories for the next energy
+// launch (n + 1 entries, as active_traj reads them), in one block: thread i
+// owns a run of consecutive trajectories.
+__device__ void number_active(const TrajDev* tr, const TrajState* ts, int n, int2* pre) {
+    __shared__ int wsum[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int c = (n + blockDim.x - 1) / blockDim.x;
+    const int a = min(n, (int)threadIdx.x * c), b = min(n, a + c);
+    int own = 0;
+    for (int t = a; t < b; ++t)
+        if (__ldcg(&ts[t].active)) own += tr[t].ecnt;
+    int inc = own;                             // inclusive scan over the warp
+    for (int o = 1; o < 32; o <<= 1) {
+        const int x = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += x;
+    }
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < nw; ++w) {
+        if (w < wid) before += wsum[w];
+        total += wsum[w];
+    }
+    int e = before + inc - own;                // exclusive prefix of this thread's run
+    for (int t = a; t < b; ++t) {
+        const TrajDev& d = tr[t];
+        pre[t] = make_int2(e, d.eoff - e);
+        if (__ldcg(&ts[t].active)) e += d.ecnt;
+    }
+    if (threadIdx.x == 0) pre[n] = make_int2(total, 0);
+}
+
 // One warp per trajectory: norm of the update, then advance the counter.
+// The last block to finish numbers the next iteration's energy items.
 template <bool PAIRS>
-__global__ void kb_norm(const TrajDev* tr, TrajState* ts, int n, const double* npart) {
+__global__ void kb_norm(const TrajDev* tr, TrajState* ts, int n, const double* npart, int2* pre,
+                        unsigned* ticket) {
+    __shared__ bool last;
     const int lane = threadIdx.x & 31;
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (t >= n) return;
-    TrajState& s = ts[t];
-    if (!s.active) return;
-    const TrajDev& d = tr[t];
-    double acc = 0.0;
-    if (s.do_update) {
-        const int slots = d.pcnt * (PAIR_BS / 32);
-        for (int i = lane; i < slots; i += 32) {
-            const double* slot = npart + d.nbase + i;
-            if (PAIRS) {
-                const float2 hl = *reinterpret_cast<const float2*>(slot);
-                acc += (double)hl.x + (double)hl.y;
-            } else {
-                acc += *slot;
+    if (t < n && ts[t].active) {
+        TrajState& s = ts[t];
+        const TrajDev& d = tr[t];
+        double acc = 0.0;
+        if (s.do_update) {
+            const int slots = d.pcnt * (PAIR_BS / 32);
+            for (int i = lane; i < slots; i += 32) {
+                const double* slot = npart + d.nbase + i;
+                if (PAIRS) {
+                    const float2 hl = *reinterpret_cast<const float2*>(slot);
+                    acc += (double)hl.x + (double)hl.y;
+                } else {
+                    acc += *slot;
+                }
             }
+            acc = warp_sum(acc);
         }
-        acc = warp_sum(acc);
+        if (lane == 0) {
+            if (s.do_update) s.norm2 = acc;
+            s.iter += 1;
+            s.active = (!s.converged && s.iter < d.len) ? 1 : 0;
+            __threadfence();
+        }
     }
-    if (lane == 0) {
-        if (s.do_update) s.norm2 = acc;
-        s.iter += 1;
-        s.active = (!s.converged && s.iter < d.len) ? 1 : 0;
-    }
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    number_active(tr, ts, n, pre);
+    if (threadIdx.x == 0) *ticket = 0u;
 }
 
 template <typename T>
@@ -400,13 +468,26 @@ __global__ void kb_scale(const TrajDev* tr, const TrajState* ts, const int4* ite
         const TrajState& s = ts[w.x];
         if (!s.do_update) continue;
         const TrajDev& d = tr[w.x];
-        const double sc = 1.0 / sqrt(s.norm2);
-        V* psi = static_cast<V*>(d.psi);
-        for (int i = threadIdx.x; i < w.z; i += blockDim.x) {
-            V v = psi[w.y + i];
-            v.x = (T)((double)v.x * sc);
-            v.y = (T)((double)v.y * sc);
-            psi[w.y + i] = v;
+        // the factor is formed in float64 and applied in the state's precision
+        const T sc = (T)(1.0 / sqrt(s.norm2));
+        V* psi = static_cast<V*>(d.psi) + w.y;
+        // SCALE_U loads in flight per thread before their stores
+        for (int i0 = threadIdx.x; i0 < w.z; i0 += SCALE_U * blockDim.x) {
+            V v[SCALE_U];
+#pragma unroll
+            for (int u = 0; u < SCALE_U; ++u) {
+                const int i = i0 + u * blockDim.x;
+                v[u] = i < w.z ? psi[i] : V{};
+            }
+#pragma unroll
+            for (int u = 0; u < SCALE_U; ++u) {
+                const int i = i0 + u * blockDim.x;
+                if (i < w.z) {
+                    v[u].x *= sc;
+                    v[u].y *= sc;
+                    psi[i] = v[u];
+                }
+            }
         }
     }
 }
@@ -435,6 +516,9 @@ struct tq_batch {
     int n_e = 0, n_g = 0, n_p = 0, n_s = 0;
     double* epart = nullptr;
     double* npart = nullptr;
+    int2* pre = nullptr;            // the active trajectories' energy items, numbered (n + 1 entries)
+    int2* pre0 = nullptr;           // the same before the first iteration
+    unsigned* nticket = nullptr;    // blocks of the norm launch done
     std::vector<void*> allocs;
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
@@ -465,12 +549,12 @@ template <typename T, typename VT>
 int launch_energy(tq_batch* b, cudaStream_t s) {
     switch (b->lpr) {
         case TQ_SPMV_XELL:
-            kbx_energy<T, VT><<<b->grid_x, BT_BS, 0, s>>>(b->d_td, b->d_ts, b->eitems, b->n_e, b->epart);
+            kbx_energy<T, VT><<<b->grid_x, BT_BS, 0, s>>>(b->d_td, b->d_ts, b->eitems, b->pre, b->n, b->epart);
             break;
-        case 4: kb_energy<T, VT, 4><<<b->grid_e[0], BT_BS, 0, s>>>(b->d_td, b->d_ts, b->eitems, b->n_e, b->epart); break;
-        case 8: kb_energy<T, VT, 8><<<b->grid_e[1], BT_BS, 0, s>>>(b->d_td, b->d_ts, b->eitems, b->n_e, b->epart); break;
-        case 16: kb_energy<T, VT, 16><<<b->grid_e[2], BT_BS, 0, s>>>(b->d_td, b->d_ts, b->eitems, b->n_e, b->epart); break;
-        default: kb_energy<T, VT, 32><<<b->grid_e[3], BT_BS, 0, s>>>(b->d_td, b->d_ts, b->eitems, b->n_e, b->epart); break;
+        case 4: kb_energy<T, VT, 4><<<b->grid_e[0], BT_BS, 0, s>>>(b->d_td, b->d_ts, b->eitems, b->pre, b->n, b->epart); break;
+        case 8: kb_energy<T, VT, 8><<<b->grid_e[1], BT_BS, 0, s>>>(b->d_td, b->d_ts, b->eitems, b->pre, b->n, b->epart); break;
+        case 16: kb_energy<T, VT, 16><<<b->grid_e[2], BT_BS, 0, s>>>(b->d_td, b->d_ts, b->eitems, b->pre, b->n, b->epart); break;
+        default: kb_energy<T, VT, 32><<<b->grid_e[3], BT_BS, 0, s>>>(b->d_td, b->d_ts, b->eitems, b->pre, b->n, b->epart); break;
     }
     return 1;
 }
@@ -514,7 +598,8 @@ void enqueue_iteration(tq_batch* b, cudaStream_t s) {
         return 1;
     });
     launch(c, "batch_norm", s, [&] {
-        kb_norm<sizeof(T) == 4><<<(b->n * 32 + 255) / 256, 256, 0, s>>>(b->d_td, b->d_ts, b->n, b->npart);
+        kb_norm<sizeof(T) == 4><<<(b->n * 32 + 255) / 256, 256, 0, s>>>(b->d_td, b->d_ts, b->n, b->npart, b->pre,
+                                                                      b->nticket);
         return 1;
     });
     launch(c, "batch_scale", s, [&] {
@@ -531,6 +616,7 @@ void enqueue_all(tq_batch* b, cudaStream_t s) {
 }
 
 void reset(tq_batch* b, cudaStream_t s) {
+    TQ_CUDA(cudaMemcpyAsync(b->pre, b->pre0, (size_t)(b->n + 1) * sizeof(int2), cudaMemcpyDeviceToDevice, s));
     launch(b->ctx, "batch_reset", s, [&] {
         return b->prec == TQ_C128 ? launch_reset<double>(b, s) : launch_reset<float>(b, s);
     });
@@ -638,6 +724,21 @@ extern "C" int tq_batch_create(tq_ctx* c, int n_traj, tq_ham* const* hams, tq_po
         b->n_s = (int)si.size();
         b->epart = dalloc<double>(b, 2 * ei.size());
         b->npart = dalloc<double>(b, (size_t)nslots);
+        {
+            // before the first iteration the active trajectories are those of length > 0
+            std::vector<int2> p0((size_t)n_traj + 1);
+            int e = 0;
+            for (int t = 0; t < n_traj; ++t) {
+                const TrajDev& d = b->td[t];
+                p0[t] = make_int2(e, d.eoff - e);
+                if (d.len > 0) e += d.ecnt;
+            }
+            p0[n_traj] = make_int2(e, 0);
+            b->pre0 = dupload(b, p0);
+            b->pre = dupload(b, p0);
+            b->nticket = dalloc<unsigned>(b, 1);
+            TQ_CUDA(cudaMemset(b->nticket, 0, sizeof(unsigned)));
+        }
         b->d_td = dupload(b, b->td);
         b->d_ts = dalloc<TrajState>(b, n_traj);
         TQ_CUDA(cudaMemset(b->d_ts, 0, n_traj * sizeof(TrajState)));
