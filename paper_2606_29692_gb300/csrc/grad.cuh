@@ -119,17 +119,32 @@ __device__ __forceinline__ uint32_t expand_support_row(const RowExp& x, uint32_t
     return r | (piv ^ x.tb);
 }
 
-// Sum of one item over the block; valid in thread 0.  `sh` holds 2 * warps
-// doubles.  W is float2 (complex64: w in float32) or double2.
+// Sum of one item over the block of GRAD_TPB threads; valid in thread 0.
+// `sh` holds 2 * warps doubles.  W is float2 (complex64: w in float32) or
+// double2.
+//
+// The map u -> support row is affine over GF(2) (zeros inserted, then each
+// pivot set to a parity of the row plus its target), so
+// row(a ^ b) = row(a) ^ row(b) ^ row(0), with row(0) the target bits.  The
+// thread's rows are u = (u0 + GRAD_TPB k) ^ tid, u0 and GRAD_TPB k clear of
+// the thread bits, hence row = R_k ^ L with L = row(tid) ^ row(0) worked out
+// once and R_k = row(u0 + GRAD_TPB k) by lane k of the warp (k < 32), read
+// with a shuffle: the same rows, visited in the same order, as expanding
+// every u.
+static_assert(GRAD_CHUNK % GRAD_TPB == 0 && GRAD_CHUNK <= 32 * GRAD_TPB, "one row base per lane");
 template <typename T, typename W, typename V>
 __device__ __forceinline__ double grad_item(const SuppRec& s, T c0, const W* __restrict__ w,
                                             const V* __restrict__ psi, uint32_t u0, uint32_t cnt,
                                             double* sh) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = GRAD_TPB >> 5;
     const RowExp rx = make_rowexp(s, 0);   // the representative bit is not used here
+    const uint32_t L = expand_support_row(rx, threadIdx.x) ^ rx.tb;
+    const uint32_t Rl = expand_support_row(rx, u0 + (uint32_t)lane * GRAD_TPB);
+    const uint32_t nk = (cnt + GRAD_TPB - 1) / GRAD_TPB;
     T hi = T(0), lo = T(0);
-    for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const uint32_t r = expand_support_row(rx, u0 + i);
+    for (uint32_t k = 0; k < nk; ++k) {
+        const uint32_t r = __shfl_sync(0xffffffffu, Rl, k) ^ L;
+        if (threadIdx.x + k * GRAD_TPB >= cnt) break;   // the last round only
         const uint32_t q = r ^ s.x;
         const T sg = parity32(q & s.z0) ? -c0 : c0;
         const W wr = w[r];
