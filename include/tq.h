@@ -710,10 +710,13 @@ int tq_evolve_taylor5_batch_host(tq_ctx* ctx, const tq_pool* pool,
  * n_electrons[t] under mappings[t], and runs at most lengths[t] iterations,
  * iteration i using angle thetas[off_t + i] (off_t = sum of the earlier
  * lengths) unless max|g| < eps stops it first.  Each iteration is energy,
- * all gradients, selection (tie rule of tq_adapt_step), the Taylor-5 update
- * and renormalisation.  The batch owns its states and keeps the handles it
- * was given (they must outlive it).  Every iteration of every trajectory is
- * six persistent launches over static work tables; finished trajectories are
+ * all gradients, selection (tie rule of tq_adapt_step) and the Taylor-5
+ * update; the energy and gradients are divided by <psi|psi>, so the state
+ * is renormalised once, after the last iteration, which changes only
+ * rounding against renormalising every step.  The batch owns its states and
+ * keeps the handles it was given (they must outlive it).  Every iteration of
+ * every trajectory is five persistent launches over static work tables, and
+ * the run ends with one renormalisation launch; finished trajectories are
  * left out on the device (the energy launch runs over the active
  * trajectories' items, numbered by the previous iteration; the others test
  * a flag), so a run needs no host round trip. */

@@ -2,7 +2,7 @@
 // advanced together.
 //
 // Every trajectory t has its own Hamiltonian, pool, state, angle list and
-// convergence test.  One iteration of all of them is six persistent
+// convergence test.  One iteration of all of them is five persistent
 // launches, each spanning every trajectory through a static work table:
 //   energy   items (t, row block): w_t = H_t psi_t, <psi|w>, <psi|psi>;
 //   grads    items (t, op, chunk): g_t[k] = 2 Re<w_t|A_k psi_t>/<psi|psi>;
@@ -10,12 +10,16 @@
 //   update   items (t, tile): the fused Taylor-5 pair update with A_{k*};
 //   norm     one warp per t: ||psi'||^2, advance the iteration counter;
 //            the last block numbers the active trajectories' energy items
-//            for the next iteration (prefix counts);
-//   scale    items (t, chunk): psi /= ||psi'||.
+//            for the next iteration (prefix counts).
+// The state is renormalised once, after the last iteration (items
+// (t, chunk): psi /= ||psi||): every quantity an iteration computes is
+// independent of the state's scale (the energy is <psi|H|psi>/<psi|psi>,
+// each gradient is divided by <psi|psi>, and the Taylor-5 update is linear),
+// so the per-step renormalisation of Sec. III-D changes only rounding.
 // The energy launch runs over the numbered items only, which also spreads
 // the remaining trajectories' items evenly over the persistent grid; the
 // other launches skip finished trajectories by a flag read on the device.
-// So the whole run (max length x six launches) is captured once into a CUDA
+// So the whole run (max length x five launches, and the scale) is captured once into a CUDA
 // graph and replayed without any host round trip.  The SpMV of the energy
 // item runs over the CSR with a lanes-per-row schedule (4, 8, 16, 32) or
 // over the XOR-ELL layout, chosen by an autotuner.
@@ -466,7 +470,7 @@ __global__ void kb_scale(const TrajDev* tr, const TrajState* ts, const int4* ite
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const int4 w = items[it];
         const TrajState& s = ts[w.x];
-        if (!s.do_update) continue;
+        if (!(s.norm2 > 0.0)) continue;     // never updated: still the normalised reference state
         const TrajDev& d = tr[w.x];
         // the factor is formed in float64 and applied in the state's precision
         const T sc = (T)(1.0 / sqrt(s.norm2));
@@ -579,11 +583,10 @@ int launch_reset(tq_batch* b, cudaStream_t s) {
     return 1;
 }
 
-// One iteration of every trajectory: six launches.
+// One iteration of every trajectory: five launches.
 template <typename T, typename VT>
 void enqueue_iteration(tq_batch* b, cudaStream_t s) {
     tq_ctx* c = b->ctx;
-    const int sms = c->sm_count;
     launch(c, "batch_energy", s, [&] { return launch_energy<T, VT>(b, s); });
     launch(c, "batch_gradients", s, [&] {
         kb_grad<T><<<b->grid_g, GRAD_TPB, 0, s>>>(b->d_td, b->d_ts, b->gitems, b->n_g);
@@ -602,16 +605,27 @@ void enqueue_iteration(tq_batch* b, cudaStream_t s) {
                                                                       b->nticket);
         return 1;
     });
-    launch(c, "batch_scale", s, [&] {
-        kb_scale<T><<<std::min(b->n_s, sms * 8), 256, 0, s>>>(b->d_td, b->d_ts, b->sitems, b->n_s);
+}
+
+template <typename T>
+void enqueue_scale(tq_batch* b, cudaStream_t s) {
+    launch(b->ctx, "batch_scale", s, [&] {
+        kb_scale<T><<<std::min(b->n_s, b->ctx->sm_count * 8), 256, 0, s>>>(b->d_td, b->d_ts, b->sitems, b->n_s);
         return 1;
     });
 }
+
+// Launches of one run after the reset.
+long long run_launches(const tq_batch* b) { return b->max_len > 0 ? 5ll * b->max_len + 1 : 0; }
 
 void enqueue_all(tq_batch* b, cudaStream_t s) {
     for (int i = 0; i < b->max_len; ++i) {
         if (b->prec == TQ_C128) enqueue_iteration<double, double>(b, s);
         else enqueue_iteration<float, float>(b, s);
+    }
+    if (b->max_len > 0) {
+        if (b->prec == TQ_C128) enqueue_scale<double>(b, s);
+        else enqueue_scale<float>(b, s);
     }
 }
 
@@ -833,13 +847,13 @@ extern "C" int tq_batch_run(tq_batch* b, int use_graph, void* stream) {
         TQ_CUDA(cudaStreamEndCapture(b->cap, &b->graph));
         TQ_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
         b->graph_lpr = b->lpr;
-        b->ctx->launches -= 6ll * b->max_len;   // counted again at each replay below
+        b->ctx->launches -= run_launches(b);   // counted again at each replay below
     }
     {
         Traced t(b->ctx, "batch_graph", s);
         TQ_CUDA(cudaGraphLaunch(b->exec, s));
     }
-    b->ctx->launches += 6ll * b->max_len;
+    b->ctx->launches += run_launches(b);
     API_END
 }
 
