@@ -1541,7 +1541,7 @@ def measure_trajectories(tq, ctx, n_traj):
             "build_s": build_s, "lanes_per_row": lpr, "ms_per_run": ms,
             "iterations_per_run": iters, "iterations_per_s": iters / (ms * 1e-3),
             "converged": int(sum(r["converged"] for r in res)),
-            "graph_launches_per_run": 5 * max(len(t.thetas) for t in trajs) + 1,
+            "graph_launches_per_run": 4 * max(len(t.thetas) for t in trajs) + 1,
             "kernel_ms_untimed_direct_run": {k: round(v[1], 3) for k, v in split.items()},
             "energy_roofline": {"layout": "XOR-ELL" if lpr == tq.TQ_SPMV_XELL else f"CSR, {lpr} lanes per row",
                                 "bytes_per_run": e_bytes, "ms": e_ms,

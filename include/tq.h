@@ -715,7 +715,7 @@ int tq_evolve_taylor5_batch_host(tq_ctx* ctx, const tq_pool* pool,
  * is renormalised once, after the last iteration, which changes only
  * rounding against renormalising every step.  The batch owns its states and
  * keeps the handles it was given (they must outlive it).  Every iteration of
- * every trajectory is five persistent launches over static work tables, and
+ * every trajectory is four persistent launches over static work tables, and
  * the run ends with one renormalisation launch; finished trajectories are
  * left out on the device (the energy launch runs over the active
  * trajectories' items, numbered by the previous iteration; the others test

@@ -2,15 +2,16 @@
 // advanced together.
 //
 // Every trajectory t has its own Hamiltonian, pool, state, angle list and
-// convergence test.  One iteration of all of them is five persistent
+// convergence test.  One iteration of all of them is four persistent
 // launches, each spanning every trajectory through a static work table:
 //   energy   items (t, row block): w_t = H_t psi_t, <psi|w>, <psi|psi>;
 //   grads    items (t, op, chunk): g_t[k] = 2 Re<w_t|A_k psi_t>/<psi|psi>;
-//   select   one warp per t: k*, max|g|, convergence, angle, record;
-//   update   items (t, tile): the fused Taylor-5 pair update with A_{k*};
-//   norm     one warp per t: ||psi'||^2, advance the iteration counter;
-//            the last block numbers the active trajectories' energy items
-//            for the next iteration (prefix counts).
+//   select   one warp per t: k*, max|g|, convergence, angle, record, and
+//            the iteration counter advanced; the last block numbers the
+//            active trajectories' energy items for the next iteration
+//            (prefix counts);
+//   update   items (t, tile): the fused Taylor-5 pair update with A_{k*}
+//            and the partials of ||psi'||^2.
 // The state is renormalised once, after the last iteration (items
 // (t, chunk): psi /= ||psi||): every quantity an iteration computes is
 // independent of the state's scale (the energy is <psi|H|psi>/<psi|psi>,
@@ -19,10 +20,11 @@
 // The energy launch runs over the numbered items only, which also spreads
 // the remaining trajectories' items evenly over the persistent grid; the
 // other launches skip finished trajectories by a flag read on the device.
-// So the whole run (max length x five launches, and the scale) is captured once into a CUDA
-// graph and replayed without any host round trip.  The SpMV of the energy
-// item runs over the CSR with a lanes-per-row schedule (4, 8, 16, 32) or
-// over the XOR-ELL layout, chosen by an autotuner.
+// So the whole run (max length x four launches, then the renormalisation)
+// is captured once into a CUDA graph and replayed without any host round
+// trip.  The SpMV of the energy item runs over the CSR with a lanes-per-row
+// schedule (4, 8, 16, 32) or over the XOR-ELL layout, chosen by an
+// autotuner.
 #include "dev.cuh"
 #include "host_util.h"
 #include "pair.cuh"
@@ -65,8 +67,8 @@ struct TrajDev {
 };
 
 struct TrajState {
-    double e_num, e_den, energy, max_grad, theta, norm2;
-    int selected, converged, iter, active, do_update;
+    double e_num, e_den, energy, max_grad, theta;
+    int selected, converged, iter, active, do_update, updated;
     unsigned etick;
 };
 
@@ -340,57 +342,6 @@ kb_grad(const TrajDev* tr, TrajState* ts, const int4* items, int n_items) {
     }
 }
 
-// One warp per trajectory: choice, convergence, angle, record.
-__global__ void kb_select(const TrajDev* tr, TrajState* ts, int n, double eps, int prec) {
-    const int lane = threadIdx.x & 31;
-    const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (t >= n) return;
-    TrajState& s = ts[t];
-    if (!s.active) {
-        if (lane == 0) s.do_update = 0;
-        return;
-    }
-    const TrajDev& d = tr[t];
-    double m = 0.0;
-    for (int k = lane; k < d.M; k += 32) m = fmax(m, fabs(d.g[k]));
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    const double tau = prec == TQ_C128 ? 1e-9 * fmax(1.0, m) : 1e-5;
-    int best = d.M;
-    for (int k = lane; k < d.M; k += 32)
-        if (fabs(d.g[k]) >= m - tau && k < best) best = k;
-    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
-    if (lane == 0) {
-        const int it = s.iter;
-        s.selected = best < d.M ? best : 0;
-        s.max_grad = m;
-        s.converged = m < eps ? 1 : 0;
-        s.theta = s.converged ? 0.0 : d.thetas[it];
-        s.do_update = !s.converged;
-        d.res_e[it] = s.energy;
-        d.res_g[it] = m;
-        d.res_sel[it] = s.selected;
-        d.res_th[it] = s.theta;
-    }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(PAIR_BS)
-kb_pair(const TrajDev* tr, const TrajState* ts, const int4* items, int n_items, double* npart) {
-    constexpr int NW = PAIR_BS / 32;
-    const int warp = threadIdx.x >> 5;
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-        const int4 w4 = items[it];
-        const int t = w4.x, tl = w4.y;
-        const TrajState& s = ts[t];
-        if (!s.do_update) continue;
-        const TrajDev& d = tr[t];
-        const OpRec<T> op = make_rec<T>(d.pool, s.selected);
-        const T tp = pair_tile<T, BT_UPT>(op, s.theta, static_cast<typename C2<T>::type*>(d.psi),
-                                          (uint32_t)tl, (uint32_t)(d.D >> 2));
-        store_partial(npart + d.nbase + (long long)tl * NW + warp, tp);
-    }
-}
-
 // Numbers the energy items of the active trajectories for the next energy
 // launch (n + 1 entries, as active_traj reads them), in one block: thread i
 // owns a run of consecutive trajectories.
@@ -423,36 +374,44 @@ __device__ void number_active(const TrajDev* tr, const TrajState* ts, int n, int
     if (threadIdx.x == 0) pre[n] = make_int2(total, 0);
 }
 
-// One warp per trajectory: norm of the update, then advance the counter.
-// The last block to finish numbers the next iteration's energy items.
-template <bool PAIRS>
-__global__ void kb_norm(const TrajDev* tr, TrajState* ts, int n, const double* npart, int2* pre,
-                        unsigned* ticket) {
+// One warp per trajectory: choice, convergence, angle, record, and the
+// iteration counter advanced.  The last block to finish numbers the next
+// iteration's energy items.
+__global__ void kb_select(const TrajDev* tr, TrajState* ts, int n, double eps, int prec, int2* pre,
+                          unsigned* ticket) {
     __shared__ bool last;
     const int lane = threadIdx.x & 31;
     const int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (t < n && ts[t].active) {
+    if (t < n) {
         TrajState& s = ts[t];
-        const TrajDev& d = tr[t];
-        double acc = 0.0;
-        if (s.do_update) {
-            const int slots = d.pcnt * (PAIR_BS / 32);
-            for (int i = lane; i < slots; i += 32) {
-                const double* slot = npart + d.nbase + i;
-                if (PAIRS) {
-                    const float2 hl = *reinterpret_cast<const float2*>(slot);
-                    acc += (double)hl.x + (double)hl.y;
-                } else {
-                    acc += *slot;
-                }
+        if (!s.active) {
+            if (lane == 0) s.do_update = 0;
+        } else {
+            const TrajDev& d = tr[t];
+            double m = 0.0;
+            for (int k = lane; k < d.M; k += 32) m = fmax(m, fabs(d.g[k]));
+            for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+            const double tau = prec == TQ_C128 ? 1e-9 * fmax(1.0, m) : 1e-5;
+            int best = d.M;
+            for (int k = lane; k < d.M; k += 32)
+                if (fabs(d.g[k]) >= m - tau && k < best) best = k;
+            for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+            if (lane == 0) {
+                const int it = s.iter;
+                s.selected = best < d.M ? best : 0;
+                s.max_grad = m;
+                s.converged = m < eps ? 1 : 0;
+                s.theta = s.converged ? 0.0 : d.thetas[it];
+                s.do_update = !s.converged;
+                if (s.do_update) s.updated = 1;
+                d.res_e[it] = s.energy;
+                d.res_g[it] = m;
+                d.res_sel[it] = s.selected;
+                d.res_th[it] = s.theta;
+                s.iter = it + 1;
+                s.active = (!s.converged && it + 1 < d.len) ? 1 : 0;
+                __threadfence();
             }
-            acc = warp_sum(acc);
-        }
-        if (lane == 0) {
-            if (s.do_update) s.norm2 = acc;
-            s.iter += 1;
-            s.active = (!s.converged && s.iter < d.len) ? 1 : 0;
-            __threadfence();
         }
     }
     __syncthreads();
@@ -465,15 +424,54 @@ __global__ void kb_norm(const TrajDev* tr, TrajState* ts, int n, const double* n
 }
 
 template <typename T>
-__global__ void kb_scale(const TrajDev* tr, const TrajState* ts, const int4* items, int n_items) {
+__global__ void __launch_bounds__(PAIR_BS)
+kb_pair(const TrajDev* tr, const TrajState* ts, const int4* items, int n_items, double* npart) {
+    constexpr int NW = PAIR_BS / 32;
+    const int warp = threadIdx.x >> 5;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int4 w4 = items[it];
+        const int t = w4.x, tl = w4.y;
+        const TrajState& s = ts[t];
+        if (!s.do_update) continue;
+        const TrajDev& d = tr[t];
+        const OpRec<T> op = make_rec<T>(d.pool, s.selected);
+        const T tp = pair_tile<T, BT_UPT>(op, s.theta, static_cast<typename C2<T>::type*>(d.psi),
+                                          (uint32_t)tl, (uint32_t)(d.D >> 2));
+        store_partial(npart + d.nbase + (long long)tl * NW + warp, tp);
+    }
+}
+
+// The final renormalisation, items (t, chunk of rows).  ||psi||^2 is the
+// sum of the norm partials of the trajectory's last update (a trajectory's
+// slots are written only by its own updates).
+template <typename T>
+__global__ void kb_scale(const TrajDev* tr, const TrajState* ts, const int4* items, int n_items,
+                         const double* npart) {
     using V = typename C2<T>::type;
+    __shared__ double sh[256 / 32];
+    __shared__ double norm2;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const int4 w = items[it];
         const TrajState& s = ts[w.x];
-        if (!(s.norm2 > 0.0)) continue;     // never updated: still the normalised reference state
+        if (!s.updated) continue;           // never updated: still the normalised reference state
         const TrajDev& d = tr[w.x];
+        double acc[1] = {0.0};
+        const int slots = d.pcnt * (PAIR_BS / 32);
+        for (int i = threadIdx.x; i < slots; i += blockDim.x) {
+            const double* slot = npart + d.nbase + i;
+            if constexpr (sizeof(T) == 4) {
+                const float2 hl = *reinterpret_cast<const float2*>(slot);
+                acc[0] += (double)hl.x + (double)hl.y;
+            } else {
+                acc[0] += *slot;
+            }
+        }
+        block_sum<1>(acc, sh);
+        if (threadIdx.x == 0) norm2 = acc[0];
+        __syncthreads();
         // the factor is formed in float64 and applied in the state's precision
-        const T sc = (T)(1.0 / sqrt(s.norm2));
+        const T sc = (T)(1.0 / sqrt(norm2));
+        __syncthreads();                    // norm2 is rewritten by the next item
         V* psi = static_cast<V*>(d.psi) + w.y;
         // SCALE_U loads in flight per thread before their stores
         for (int i0 = threadIdx.x; i0 < w.z; i0 += SCALE_U * blockDim.x) {
@@ -522,7 +520,7 @@ struct tq_batch {
     double* npart = nullptr;
     int2* pre = nullptr;            // the active trajectories' energy items, numbered (n + 1 entries)
     int2* pre0 = nullptr;           // the same before the first iteration
-    unsigned* nticket = nullptr;    // blocks of the norm launch done
+    unsigned* nticket = nullptr;    // blocks of the select launch done
     std::vector<void*> allocs;
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
@@ -583,7 +581,7 @@ int launch_reset(tq_batch* b, cudaStream_t s) {
     return 1;
 }
 
-// One iteration of every trajectory: five launches.
+// One iteration of every trajectory: four launches.
 template <typename T, typename VT>
 void enqueue_iteration(tq_batch* b, cudaStream_t s) {
     tq_ctx* c = b->ctx;
@@ -593,16 +591,12 @@ void enqueue_iteration(tq_batch* b, cudaStream_t s) {
         return 1;
     });
     launch(c, "batch_select", s, [&] {
-        kb_select<<<(b->n * 32 + 255) / 256, 256, 0, s>>>(b->d_td, b->d_ts, b->n, b->eps, b->prec);
+        kb_select<<<(b->n * 32 + 255) / 256, 256, 0, s>>>(b->d_td, b->d_ts, b->n, b->eps, b->prec, b->pre,
+                                                          b->nticket);
         return 1;
     });
     launch(c, "batch_taylor5_pair", s, [&] {
         kb_pair<T><<<b->grid_p, PAIR_BS, 0, s>>>(b->d_td, b->d_ts, b->pitems, b->n_p, b->npart);
-        return 1;
-    });
-    launch(c, "batch_norm", s, [&] {
-        kb_norm<sizeof(T) == 4><<<(b->n * 32 + 255) / 256, 256, 0, s>>>(b->d_td, b->d_ts, b->n, b->npart, b->pre,
-                                                                      b->nticket);
         return 1;
     });
 }
@@ -610,13 +604,14 @@ void enqueue_iteration(tq_batch* b, cudaStream_t s) {
 template <typename T>
 void enqueue_scale(tq_batch* b, cudaStream_t s) {
     launch(b->ctx, "batch_scale", s, [&] {
-        kb_scale<T><<<std::min(b->n_s, b->ctx->sm_count * 8), 256, 0, s>>>(b->d_td, b->d_ts, b->sitems, b->n_s);
+        kb_scale<T><<<std::min(b->n_s, b->ctx->sm_count * 8), 256, 0, s>>>(b->d_td, b->d_ts, b->sitems, b->n_s,
+                                                                           b->npart);
         return 1;
     });
 }
 
 // Launches of one run after the reset.
-long long run_launches(const tq_batch* b) { return b->max_len > 0 ? 5ll * b->max_len + 1 : 0; }
+long long run_launches(const tq_batch* b) { return b->max_len > 0 ? 4ll * b->max_len + 1 : 0; }
 
 void enqueue_all(tq_batch* b, cudaStream_t s) {
     for (int i = 0; i < b->max_len; ++i) {
