@@ -17,6 +17,7 @@ namespace tq {
 
 constexpr int GRAD_CHUNK = 8192;   // support rows per work item
 constexpr int GRAD_TPB = 256;
+constexpr int GRAD_U = 4;          // rounds of support rows with loads in flight
 
 struct SuppRec {
     uint32_t x, z0, e0, e1, e2;
@@ -142,22 +143,38 @@ __device__ __forceinline__ double grad_item(const SuppRec& s, T c0, const W* __r
     const uint32_t Rl = expand_support_row(rx, u0 + (uint32_t)lane * GRAD_TPB);
     const uint32_t nk = (cnt + GRAD_TPB - 1) / GRAD_TPB;
     T hi = T(0), lo = T(0);
-    for (uint32_t k = 0; k < nk; ++k) {
-        const uint32_t r = __shfl_sync(0xffffffffu, Rl, k) ^ L;
-        if (threadIdx.x + k * GRAD_TPB >= cnt) break;   // the last round only
-        const uint32_t q = r ^ s.x;
-        const T sg = parity32(q & s.z0) ? -c0 : c0;
-        const W wr = w[r];
-        const V v = psi[q];
-        const T prod = sg * fma((T)wr.x, (T)v.x, (T)wr.y * (T)v.y);
-        if constexpr (sizeof(T) == 4) {
-            T sum, err;
-            two_sum(hi, prod, sum, err);
-            hi = sum;
-            lo += err;
-        } else {
-            hi += prod;
+    // GRAD_U rounds' loads are issued before their products are summed (in
+    // round order); k + u < 32 since nk <= 32 and GRAD_U divides 32
+    for (uint32_t k = 0; k < nk; k += GRAD_U) {
+        uint32_t r[GRAD_U];
+        bool in[GRAD_U];
+        W wr[GRAD_U];
+        V v[GRAD_U];
+#pragma unroll
+        for (int u = 0; u < GRAD_U; ++u) {
+            r[u] = __shfl_sync(0xffffffffu, Rl, k + u) ^ L;
+            in[u] = threadIdx.x + (k + u) * GRAD_TPB < cnt;
         }
+#pragma unroll
+        for (int u = 0; u < GRAD_U; ++u)
+            if (in[u]) {
+                wr[u] = w[r[u]];
+                v[u] = psi[r[u] ^ s.x];
+            }
+#pragma unroll
+        for (int u = 0; u < GRAD_U; ++u)
+            if (in[u]) {
+                const T sg = parity32((r[u] ^ s.x) & s.z0) ? -c0 : c0;
+                const T prod = sg * fma((T)wr[u].x, (T)v[u].x, (T)wr[u].y * (T)v[u].y);
+                if constexpr (sizeof(T) == 4) {
+                    T sum, err;
+                    two_sum(hi, prod, sum, err);
+                    hi = sum;
+                    lo += err;
+                } else {
+                    hi += prod;
+                }
+            }
     }
     double part;
     if constexpr (sizeof(T) == 4) part = warp_sum_compensated_pair(hi, lo);
