@@ -4,12 +4,14 @@
 // Every trajectory t has its own Hamiltonian, pool, state, angle list and
 // convergence test.  One iteration of all of them is four persistent
 // launches, each spanning every trajectory through a static work table:
-//   energy   items (t, row block): w_t = H_t psi_t, <psi|w>, <psi|psi>;
-//   grads    items (t, op, chunk): g_t[k] = 2 Re<w_t|A_k psi_t>/<psi|psi>;
-//   select   one warp per t: k*, max|g|, convergence, angle, record, and
-//            the iteration counter advanced; the last block numbers the
-//            active trajectories' energy items for the next iteration
-//            (prefix counts);
+//   energy   items (t, row block): w_t = H_t psi_t, <psi|w>, <psi|psi>
+//            (the trajectory's last item sums its items' parts);
+//   grads    items (t, op, chunk): the chunk's part of 2 Re<w_t|A_k psi_t>;
+//   select   one warp per t: g_t[k] (divided by <psi|psi>) summed from the
+//            chunk parts in a fixed order, k*, max|g|, convergence, angle,
+//            record, and the iteration counter advanced; the last block
+//            numbers the active trajectories' energy items for the next
+//            iteration (prefix counts);
 //   update   items (t, tile): the fused Taylor-5 pair update with A_{k*}
 //            and the partials of ||psi'||^2.
 // The state is renormalised once, after the last iteration (items
@@ -20,6 +22,10 @@
 // The energy launch runs over the numbered items only, which also spreads
 // the remaining trajectories' items evenly over the persistent grid; the
 // other launches skip finished trajectories by a flag read on the device.
+// A gradient item only writes its part (no ticket, fence or finishing
+// block): the op's sum waits for the select launch.  The energy items keep
+// their ticket, whose end-of-item wait measured faster for the XOR-ELL
+// schedule than running on.
 // So the whole run (max length x four launches, then the renormalisation)
 // is captured once into a CUDA graph and replayed without any host round
 // trip.  The SpMV of the energy item runs over the CSR with a lanes-per-row
@@ -58,7 +64,7 @@ struct TrajDev {
     const double* thetas;
     double* g;
     double* gpart;           // one partial per gradient item of this trajectory
-    unsigned* gtick;
+    const int* gfirst;       // first gradient item of each op (M + 1, the pool's table)
     int gbase;               // first gradient item of this trajectory
     double* res_e;
     double* res_g;
@@ -306,10 +312,9 @@ kbx_energy(const TrajDev* tr, TrajState* ts, const int4* items, const int2* pre,
 // Gradient item: (t, op, chunk of the op's support rows).
 template <typename T>
 __global__ void __launch_bounds__(GRAD_TPB)
-kb_grad(const TrajDev* tr, TrajState* ts, const int4* items, int n_items) {
+kb_grad(const TrajDev* tr, const TrajState* ts, const int4* items, int n_items) {
     using V = typename C2<T>::type;
     __shared__ double sh[GRAD_TPB / 32];
-    __shared__ bool last;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const int4 w4 = items[it];          // (t, op, chunk, chunks of this op)
         const int t = w4.x, k = w4.y;
@@ -325,20 +330,9 @@ kb_grad(const TrajDev* tr, TrajState* ts, const int4* items, int n_items) {
             v = grad_item<T>(s, c0, d.w32, static_cast<const V*>(d.psi), u0, cnt, sh);
         else
             v = grad_item<T>(s, c0, d.w, static_cast<const V*>(d.psi), u0, cnt, sh);
-        const int first = it - w4.z;        // the op's items are consecutive
-        if (threadIdx.x == 0) {
-            d.gpart[first - d.gbase + w4.z] = v;
-            __threadfence();
-            last = atomicAdd(&d.gtick[k], 1u) == (unsigned)w4.w - 1;
-        }
-        __syncthreads();
-        if (last && threadIdx.x == 0) {
-            double acc = 0.0;
-            for (int i = 0; i < w4.w; ++i) acc += __ldcg(d.gpart + (first - d.gbase) + i);
-            d.g[k] = 2.0 * acc / ts[t].e_den;
-            d.gtick[k] = 0u;
-        }
-        __syncthreads();
+        // the select launch sums the op's chunks (grad_item ends with a
+        // barrier, so sh is free again)
+        if (threadIdx.x == 0) d.gpart[it - d.gbase] = v;
     }
 }
 
@@ -374,9 +368,10 @@ __device__ void number_active(const TrajDev* tr, const TrajState* ts, int n, int
     if (threadIdx.x == 0) pre[n] = make_int2(total, 0);
 }
 
-// One warp per trajectory: choice, convergence, angle, record, and the
-// iteration counter advanced.  The last block to finish numbers the next
-// iteration's energy items.
+// One warp per trajectory: each gradient from its op's chunk partials
+// (Eq. (5), divided by <psi|psi>), then choice, convergence, angle, record,
+// and the iteration counter advanced.  The last block to finish numbers the
+// next iteration's energy items.
 __global__ void kb_select(const TrajDev* tr, TrajState* ts, int n, double eps, int prec, int2* pre,
                           unsigned* ticket) {
     __shared__ bool last;
@@ -388,8 +383,15 @@ __global__ void kb_select(const TrajDev* tr, TrajState* ts, int n, double eps, i
             if (lane == 0) s.do_update = 0;
         } else {
             const TrajDev& d = tr[t];
+            const double inv = 1.0 / s.e_den;
             double m = 0.0;
-            for (int k = lane; k < d.M; k += 32) m = fmax(m, fabs(d.g[k]));
+            for (int k = lane; k < d.M; k += 32) {
+                double acc = 0.0;
+                for (int i = d.gfirst[k]; i < d.gfirst[k + 1]; ++i) acc += d.gpart[i];
+                const double g = 2.0 * acc * inv;
+                d.g[k] = g;                    // read back below by this lane only
+                m = fmax(m, fabs(g));
+            }
             for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
             const double tau = prec == TQ_C128 ? 1e-9 * fmax(1.0, m) : 1e-5;
             int best = d.M;
@@ -692,10 +694,12 @@ extern "C" int tq_batch_create(tq_ctx* c, int n_traj, tq_ham* const* hams, tq_po
                 ei.push_back(make_int4(t, (int)r, (int)std::min<long long>(ROWS_PER_ITEM, d.D - r), 0));
             d.ecnt = (int)ei.size() - d.eoff;
             d.gbase = (int)gi.size();
+            // the pool's own item table: op k's chunks are items gf[k] .. gf[k + 1] - 1
+            std::vector<int> gf((size_t)d.M + 1);
+            TQ_CUDA(cudaMemcpy(gf.data(), p->view.gfirst, gf.size() * sizeof(int), cudaMemcpyDeviceToHost));
             for (int k = 0; k < d.M; ++k) {
-                const int m = p->nterm[k] == 2 ? 1 : 3;    // conditions of a single / double
-                const long long size = d.D >> m;
-                const int nchunks = (int)((size + GRAD_CHUNK - 1) / GRAD_CHUNK);
+                const int nchunks = gf[k + 1] - gf[k];
+                TQ_REQUIRE(gf[k] == (int)gi.size() - d.gbase && nchunks >= 1, "pool gradient table is inconsistent");
                 for (int ch = 0; ch < nchunks; ++ch) gi.push_back(make_int4(t, k, ch, nchunks));
             }
             const int n_gitems_t = (int)gi.size() - d.gbase;
@@ -714,8 +718,7 @@ extern "C" int tq_batch_create(tq_ctx* c, int n_traj, tq_ham* const* hams, tq_po
             toff += d.len;
             d.g = dalloc<double>(b, d.M);
             d.gpart = dalloc<double>(b, (size_t)n_gitems_t);
-            d.gtick = dalloc<unsigned>(b, d.M);
-            TQ_CUDA(cudaMemset(d.gtick, 0, d.M * sizeof(unsigned)));
+            d.gfirst = p->view.gfirst;
             d.res_e = dalloc<double>(b, std::max(1, d.len));
             d.res_g = dalloc<double>(b, std::max(1, d.len));
             d.res_th = dalloc<double>(b, std::max(1, d.len));
