@@ -102,6 +102,7 @@ constexpr int BT_BS = 256;
 constexpr int ROWS_PER_ITEM = 4 * ENERGY_ROWS;
 constexpr int BT_UPT = 2;
 constexpr int SCALE_U = 8;
+constexpr int SEL_U = 4;
 
 template <typename T> __device__ __forceinline__ double2 d2(typename C2<T>::type v) {
     return make_double2((double)v.x, (double)v.y);
@@ -385,12 +386,30 @@ __global__ void kb_select(const TrajDev* tr, TrajState* ts, int n, double eps, i
             const TrajDev& d = tr[t];
             const double inv = 1.0 / s.e_den;
             double m = 0.0;
-            for (int k = lane; k < d.M; k += 32) {
-                double acc = 0.0;
-                for (int i = d.gfirst[k]; i < d.gfirst[k + 1]; ++i) acc += d.gpart[i];
-                const double g = 2.0 * acc * inv;
-                d.g[k] = g;                    // read back below by this lane only
-                m = fmax(m, fabs(g));
+            // the lane's ops k = lane + 32 j, four at a time so that their
+            // bounds and first chunks load together; each op's chunks are
+            // summed in item order (every op has at least one)
+            for (int k0 = lane; k0 < d.M; k0 += 32 * SEL_U) {
+                int f[SEL_U], e[SEL_U];
+                double acc[SEL_U];
+#pragma unroll
+                for (int u = 0; u < SEL_U; ++u) {
+                    const int k = k0 + 32 * u;
+                    f[u] = k < d.M ? d.gfirst[k] : 0;
+                    e[u] = k < d.M ? d.gfirst[k + 1] : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < SEL_U; ++u) acc[u] = k0 + 32 * u < d.M ? d.gpart[f[u]] : 0.0;
+#pragma unroll
+                for (int u = 0; u < SEL_U; ++u) {
+                    const int k = k0 + 32 * u;
+                    if (k < d.M) {
+                        for (int i = f[u] + 1; i < e[u]; ++i) acc[u] += d.gpart[i];
+                        const double g = 2.0 * acc[u] * inv;
+                        d.g[k] = g;            // read back below by this lane only
+                        m = fmax(m, fabs(g));
+                    }
+                }
             }
             for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
             const double tau = prec == TQ_C128 ? 1e-9 * fmax(1.0, m) : 1e-5;
