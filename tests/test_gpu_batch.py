@@ -87,6 +87,26 @@ def test_graph_direct_and_schedules_agree(ctx):
     assert [x["n_iter"] for x in b.results()] == [x["n_iter"] for x in base]
 
 
+@pytest.mark.parametrize("prec", [tq.TQ_C128, tq.TQ_C64])
+def test_repeated_runs_are_bit_identical(ctx, prec):
+    """Every sum of the batch is taken in a fixed order (energy items, the
+    gradient chunks of each op, the final norm), and the device-side item
+    numbering and tickets start afresh each run: graph replays and a direct
+    run give the same bits."""
+    b, _ = _build(ctx, SMALL, prec)
+    runs = []
+    for use_graph in (True, True, False):
+        b.run(use_graph=use_graph)
+        runs.append((b.results(), [b.state(t) for t in range(len(SMALL))]))
+    (r0, s0) = runs[0]
+    for r, st in runs[1:]:
+        for t in range(len(SMALL)):
+            assert r[t]["n_iter"] == r0[t]["n_iter"]
+            for key in ("energy", "max_grad", "selected", "theta"):
+                assert np.array_equal(r[t][key], r0[t][key]), (t, key)
+            assert np.array_equal(st[t], s0[t]), t
+
+
 def test_immediate_convergence_keeps_hf(ctx):
     spec = [(4, 4, 0, 11, 3), (3, 2, 1, 15, 2)]
     b, th = _build(ctx, spec, tq.TQ_C128, eps=1e3)
